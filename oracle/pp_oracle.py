@@ -1,0 +1,424 @@
+"""FP64 CPU oracle for polynomial-preconditioned FISTA on multi-coil SENSE.
+
+TEST INFRASTRUCTURE.  Only the test-suite, the smoke check and the benchmark's
+CPU-baseline leg may import this module; the product path never does.  It
+shares no code with the CUDA library: every function below restates the
+paper's definitions in plain, slow numpy (complex128), with numpy's FFT as
+the only library primitive.
+
+Problem (Eq. "ucopt", Sec. 1):  min_x 1/2 ||A x - b||_2^2 + lambda ||W x||_1
+  A = [M F S_1; ...; M F S_C]      Cartesian SENSE (Sec. 5.1 operator)
+  A = [N S_1; ...; N S_C]          non-Cartesian SENSE with a Kaiser-Bessel
+                                   gridding NUFFT N (Sec. 5.2 operator)
+  W = orthonormal Haar wavelet (the paper's experiments use Daubechies-4;
+      the workload here fixes a 2-level Haar).
+Method: Algorithm "pfista" (Sec. 3.1) with p from Eq. "l2cost", evaluated by
+the recursion of Listing "pcode" (Sec. 3.6), on the normalised problem of
+Sec. 5 (A scaled to unit induced norm, b to unit l2 norm).
+
+Readings where the paper is silent or ambiguous (each is listed in the design
+notes of the repository):
+  * FFT: orthonormal and centred (ifftshift -> FFT -> fftshift).
+  * Momentum: z_{k+1} = y_{k+1} + beta_k (y_{k+1} - y_k), beta_k = k/(k+3)
+    (the printed z_{k+1} = y_k + beta_k(y_k - y_{k-1}) is read as an index
+    slip).
+  * Soft threshold of a complex v: v * max(0, 1 - lambda/|v|), 0 at v = 0;
+    every Haar coefficient, the coarsest approximation band included, is
+    thresholded.
+  * Induced norm: L = lambda_max(A^H A) from 50 power-iteration steps started
+    from a SplitMix64 vector; L is the last Rayleigh quotient.
+  * NUFFT: grid G = ceil(sigma*n) per axis, KB kernel of width W with
+    beta = pi*sqrt((W/sigma)^2 (sigma-1/2)^2 - 0.8) (Beatty et al. 2005),
+    taps m in (s - W/2, s + W/2] at grid coordinate s = kappa*G/n, and
+    deapodisation by the kernel's continuous Fourier transform.
+
+Parity unpinned: nothing.  Every function here is checked by the CPU tests
+against closed forms, brute force or library routines (see tests/).
+"""
+from __future__ import annotations
+
+import math
+from fractions import Fraction
+
+import numpy as np
+
+# --------------------------------------------------------------------------
+# Fourier transforms (Sec. 5.1: "2D-Fourier transform"; reading: unitary,
+# centred)
+# --------------------------------------------------------------------------
+
+
+def cfft(x, axes):
+    """Centred orthonormal DFT over `axes`."""
+    return np.fft.fftshift(np.fft.fftn(np.fft.ifftshift(x, axes=axes), axes=axes, norm="ortho"),
+                           axes=axes)
+
+
+def cifft(x, axes):
+    """Inverse of cfft (its adjoint)."""
+    return np.fft.fftshift(np.fft.ifftn(np.fft.ifftshift(x, axes=axes), axes=axes, norm="ortho"),
+                           axes=axes)
+
+
+# --------------------------------------------------------------------------
+# Cartesian SENSE (Sec. 5.1): A_c = M F S_c
+# --------------------------------------------------------------------------
+
+
+def _img_axes(x):
+    return tuple(range(-x.ndim, 0))
+
+
+def cart_forward(x, sens, mask):
+    """y_c = M * F(S_c * x); x [*img], sens [C, *img], mask [*img] (0/1)."""
+    x = np.asarray(x, dtype=np.complex128)
+    s = np.asarray(sens, dtype=np.complex128)
+    m = np.asarray(mask).astype(np.float64)
+    return m[None] * cfft(s * x[None], axes=_img_axes(x))
+
+
+def cart_adjoint(y, sens, mask):
+    """x = sum_c conj(S_c) * F^H(M * y_c)."""
+    y = np.asarray(y, dtype=np.complex128)
+    s = np.asarray(sens, dtype=np.complex128)
+    m = np.asarray(mask).astype(np.float64)
+    ax = tuple(range(-(y.ndim - 1), 0))
+    return np.sum(np.conj(s) * cifft(m[None] * y, axes=ax), axis=0)
+
+
+def cart_normal(x, sens, mask):
+    """A^H A x with the full multi-dimensional FFT (no readout shortcut)."""
+    return cart_adjoint(cart_forward(x, sens, mask), sens, mask)
+
+
+# --------------------------------------------------------------------------
+# Kaiser-Bessel gridding NUFFT (Sec. 5.2 uses a NUFFT; parameters per the
+# workload: width W, oversampling sigma)
+# --------------------------------------------------------------------------
+
+
+def kb_beta(width, oversamp):
+    """Beatty et al. (2005) shape parameter for width W and oversampling sigma."""
+    w, s = float(width), float(oversamp)
+    return math.pi * math.sqrt((w / s) ** 2 * (s - 0.5) ** 2 - 0.8)
+
+
+def bessel_i0(x):
+    """Modified Bessel function I0 by its power series sum_k ((x/2)^k / k!)^2."""
+    x = np.asarray(x, dtype=np.float64)
+    q = (x / 2.0) ** 2
+    term = np.ones_like(x)
+    total = np.ones_like(x)
+    for k in range(1, 80):
+        term = term * q / (k * k)
+        total = total + term
+    return total
+
+
+def kb_kernel(u, width, beta):
+    """phi(u) = I0(beta * sqrt(1 - (2u/W)^2)) for |u| <= W/2, else 0."""
+    u = np.asarray(u, dtype=np.float64)
+    t = 1.0 - (2.0 * u / width) ** 2
+    inside = t >= 0.0
+    return np.where(inside, bessel_i0(beta * np.sqrt(np.where(inside, t, 0.0))), 0.0)
+
+
+def kb_transform(nu, width, beta):
+    """Continuous Fourier transform of kb_kernel at frequency nu (cycles per
+    grid sample): W sinh(sqrt(a))/sqrt(a), a = beta^2 - (pi W nu)^2 (sin for
+    a < 0, W at a = 0)."""
+    nu = np.asarray(nu, dtype=np.float64)
+    a = beta ** 2 - (math.pi * width * nu) ** 2
+    out = np.empty_like(a)
+    pos, neg = a > 0, a < 0
+    out[pos] = width * np.sinh(np.sqrt(a[pos])) / np.sqrt(a[pos])
+    out[neg] = width * np.sin(np.sqrt(-a[neg])) / np.sqrt(-a[neg])
+    out[~(pos | neg)] = width
+    return out
+
+
+def _grid_size(n, oversamp):
+    return int(math.ceil(oversamp * n))
+
+
+def _nufft_taps(traj, shape, width, oversamp):
+    """Per-sample taps: list over (ty, tx) of (grid row, grid col, weight),
+    grid indices centred (index = m + G/2, wrapped mod G)."""
+    ny, nx = shape
+    gy, gx = _grid_size(ny, oversamp), _grid_size(nx, oversamp)
+    beta = kb_beta(width, oversamp)
+    t = np.asarray(traj, dtype=np.float64)
+    sx = t[:, 0] * (gx / nx)
+    sy = t[:, 1] * (gy / ny)
+    mx0 = np.floor(sx - width / 2.0).astype(np.int64) + 1
+    my0 = np.floor(sy - width / 2.0).astype(np.int64) + 1
+    taps = []
+    for b in range(width):
+        my = my0 + b
+        wy = kb_kernel(sy - my, width, beta)
+        for a in range(width):
+            mx = mx0 + a
+            wx = kb_kernel(sx - mx, width, beta)
+            taps.append(((my + gy // 2) % gy, (mx + gx // 2) % gx, wy * wx))
+    return taps, (gy, gx), beta
+
+
+def _apodisation(shape, grid, width, beta):
+    ny, nx = shape
+    gy, gx = grid
+    ry = np.arange(ny) - ny // 2
+    rx = np.arange(nx) - nx // 2
+    return kb_transform(ry / gy, width, beta)[:, None] * kb_transform(rx / gx, width, beta)[None, :]
+
+
+def nufft_forward(x, traj, width=4, oversamp=1.25):
+    """Gridding approximation of y_k = 1/sqrt(n) sum_r x(r) exp(-2 pi i kappa_k.r/n):
+    deapodise, zero-pad (centred) to the oversampled grid, centred unnormalised
+    DFT, interpolate with the separable KB kernel.  x [ny, nx]; traj [K, 2]."""
+    x = np.asarray(x, dtype=np.complex128)
+    ny, nx = x.shape
+    taps, (gy, gx), beta = _nufft_taps(traj, (ny, nx), width, oversamp)
+    apod = _apodisation((ny, nx), (gy, gx), width, beta)
+    xp = np.zeros((gy, gx), dtype=np.complex128)
+    oy, ox = gy // 2 - ny // 2, gx // 2 - nx // 2
+    xp[oy:oy + ny, ox:ox + nx] = x / apod
+    X = np.fft.fftshift(np.fft.fft2(np.fft.ifftshift(xp)))
+    y = np.zeros(len(traj), dtype=np.complex128)
+    for iy, ix, w in taps:
+        y += w * X[iy, ix]
+    return y / math.sqrt(ny * nx)
+
+
+def nufft_adjoint(y, traj, shape, width=4, oversamp=1.25):
+    """Exact adjoint of nufft_forward: spread, centred inverse DFT (unscaled),
+    crop, deapodise."""
+    y = np.asarray(y, dtype=np.complex128)
+    ny, nx = shape
+    taps, (gy, gx), beta = _nufft_taps(traj, (ny, nx), width, oversamp)
+    apod = _apodisation((ny, nx), (gy, gx), width, beta)
+    Xg = np.zeros((gy, gx), dtype=np.complex128)
+    for iy, ix, w in taps:
+        np.add.at(Xg, (iy, ix), w * y)
+    xp = np.fft.fftshift(np.fft.ifft2(np.fft.ifftshift(Xg))) * (gy * gx)
+    oy, ox = gy // 2 - ny // 2, gx // 2 - nx // 2
+    return xp[oy:oy + ny, ox:ox + nx] / apod / math.sqrt(ny * nx)
+
+
+def ndft_forward(x, traj):
+    """Exact non-uniform DFT y_k = 1/sqrt(n) sum_r x(r) exp(-2 pi i (kx rx/nx + ky ry/ny)),
+    r centred.  O(K n); for small pins only."""
+    x = np.asarray(x, dtype=np.complex128)
+    ny, nx = x.shape
+    ry = (np.arange(ny) - ny // 2).astype(np.float64)
+    rx = (np.arange(nx) - nx // 2).astype(np.float64)
+    t = np.asarray(traj, dtype=np.float64)
+    ey = np.exp(-2j * math.pi * np.outer(t[:, 1], ry) / ny)   # [K, ny]
+    ex = np.exp(-2j * math.pi * np.outer(t[:, 0], rx) / nx)   # [K, nx]
+    return np.einsum("ky,yx,kx->k", ey, x, ex) / math.sqrt(ny * nx)
+
+
+def nc_forward(x, sens, traj, width=4, oversamp=1.25):
+    """y_c = N(S_c x) for each coil; returns [C, K]."""
+    s = np.asarray(sens, dtype=np.complex128)
+    x = np.asarray(x, dtype=np.complex128)
+    return np.stack([nufft_forward(s[c] * x, traj, width, oversamp) for c in range(s.shape[0])])
+
+
+def nc_adjoint(y, sens, traj, width=4, oversamp=1.25):
+    """x = sum_c conj(S_c) N^H y_c."""
+    s = np.asarray(sens, dtype=np.complex128)
+    shape = s.shape[1:]
+    out = np.zeros(shape, dtype=np.complex128)
+    for c in range(s.shape[0]):
+        out += np.conj(s[c]) * nufft_adjoint(y[c], traj, shape, width, oversamp)
+    return out
+
+
+def nc_normal(x, sens, traj, width=4, oversamp=1.25):
+    return nc_adjoint(nc_forward(x, sens, traj, width, oversamp), sens, traj, width, oversamp)
+
+
+# --------------------------------------------------------------------------
+# Orthonormal Haar wavelet and the l1 prox (Eq. "proxdef", Sec. 2.1)
+# --------------------------------------------------------------------------
+
+_R2 = math.sqrt(0.5)
+
+
+def haar_fwd(x, levels):
+    """Separable orthonormal Haar over every axis, `levels` levels, Mallat
+    layout (approximation band in the low corner)."""
+    out = np.array(x, dtype=np.complex128, copy=True)
+    for lev in range(levels):
+        region = tuple(slice(0, s >> lev) for s in out.shape)
+        sub = out[region]
+        for ax in range(out.ndim):
+            a = np.take(sub, np.arange(0, sub.shape[ax], 2), axis=ax)
+            b = np.take(sub, np.arange(1, sub.shape[ax], 2), axis=ax)
+            sub = np.concatenate([(a + b) * _R2, (a - b) * _R2], axis=ax)
+        out[region] = sub
+    return out
+
+
+def haar_inv(c, levels):
+    """Inverse (transpose) of haar_fwd."""
+    out = np.array(c, dtype=np.complex128, copy=True)
+    for lev in reversed(range(levels)):
+        region = tuple(slice(0, s >> lev) for s in out.shape)
+        sub = out[region]
+        for ax in reversed(range(out.ndim)):
+            h = sub.shape[ax] // 2
+            lo = np.take(sub, np.arange(0, h), axis=ax)
+            hi = np.take(sub, np.arange(h, 2 * h), axis=ax)
+            a = (lo + hi) * _R2
+            b = (lo - hi) * _R2
+            shp = list(sub.shape)
+            res = np.empty(shp, dtype=np.complex128)
+            idx_a = [slice(None)] * sub.ndim
+            idx_b = [slice(None)] * sub.ndim
+            idx_a[ax] = slice(0, None, 2)
+            idx_b[ax] = slice(1, None, 2)
+            res[tuple(idx_a)] = a
+            res[tuple(idx_b)] = b
+            sub = res
+        out[region] = sub
+    return out
+
+
+def soft_threshold(v, lam):
+    """prox of lam*|.| for complex entries: v * max(0, 1 - lam/|v|), 0 at v = 0."""
+    v = np.asarray(v, dtype=np.complex128)
+    mag = np.abs(v)
+    safe = np.where(mag > 0, mag, 1.0)
+    scale = np.where(mag > lam, 1.0 - lam / safe, 0.0)
+    return v * scale
+
+
+def prox_l1_haar(v, lam, levels=2):
+    """prox_{lam ||W .||_1}(v) = W^T soft_lam(W v) for orthonormal W."""
+    return haar_inv(soft_threshold(haar_fwd(v, levels), lam), levels)
+
+
+# --------------------------------------------------------------------------
+# Polynomial preconditioner: Eq. "l2cost" and the recursion of Listing "pcode"
+# --------------------------------------------------------------------------
+
+
+def poly_coeffs_l2(d):
+    """Exact minimiser c[0..d] of int_0^1 (1 - z sum_i c_i z^i)^2 dz.
+
+    Expanding the square, the cost is 1 - 2 sum_i c_i/(i+2)
+    + sum_ij c_i c_j/(i+j+3); setting its gradient to zero gives the normal
+    equations G c = h with G_ij = 1/(i+j+3) and h_i = 1/(i+2), solved here
+    in exact rational arithmetic.  Returns a list of Fractions."""
+    n = d + 1
+    a = [[Fraction(1, i + j + 3) for j in range(n)] + [Fraction(1, i + 2)] for i in range(n)]
+    for col in range(n):
+        piv = next(r for r in range(col, n) if a[r][col] != 0)
+        a[col], a[piv] = a[piv], a[col]
+        for r in range(n):
+            if r != col and a[r][col] != 0:
+                f = a[r][col] / a[col][col]
+                a[r] = [a[r][k] - f * a[col][k] for k in range(n + 1)]
+    return [a[i][n] / a[i][i] for i in range(n)]
+
+
+def poly_eval(c, z):
+    """p(z) = sum_i c[i] z^i (coefficient order of Sec. 3.6)."""
+    z = np.asarray(z, dtype=np.float64)
+    out = np.zeros_like(z)
+    for ci in reversed(list(c)):
+        out = out * z + float(ci)
+    return out
+
+
+def horner_apply(c, normal, g):
+    """p(N) g = c0 g + N(c1 g + N(c2 g + ...)) by the recursion of Listing
+    "pcode": u = c_d g, then u = c_i g + N u for i = d-1 .. 0."""
+    c = [float(ci) for ci in c]
+    u = c[-1] * g
+    for ci in reversed(c[:-1]):
+        u = ci * g + normal(u)
+    return u
+
+
+# --------------------------------------------------------------------------
+# Induced-norm estimate (Sec. 5: A normalised to unit induced norm)
+# --------------------------------------------------------------------------
+
+_SM_GAMMA = 0x9E3779B97F4A7C15
+_SM_M1 = 0xBF58476D1CE4E5B9
+_SM_M2 = 0x94D049BB133111EB
+_MASK64 = (1 << 64) - 1
+
+
+def splitmix64(seed, count):
+    """SplitMix64 (Steele, Lea & Flood, OOPSLA 2014) as a counter-based
+    generator: output i mixes seed + (i+1)*gamma.  Returns uint64 array."""
+    out = np.empty(count, dtype=np.uint64)
+    for i in range(count):
+        z = (int(seed) + (i + 1) * _SM_GAMMA) & _MASK64
+        z = ((z ^ (z >> 30)) * _SM_M1) & _MASK64
+        z = ((z ^ (z >> 27)) * _SM_M2) & _MASK64
+        out[i] = z ^ (z >> 31)
+    return out
+
+
+def start_vector(seed, n):
+    """Power-iteration start: entry i = (2u_{2i} - 1) + 1j (2u_{2i+1} - 1),
+    u_j = (splitmix64_j >> 11) * 2^-53."""
+    r = splitmix64(seed, 2 * n)
+    u = (r >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+    return (2.0 * u[0::2] - 1.0) + 1j * (2.0 * u[1::2] - 1.0)
+
+
+def power_iteration(normal, shape, seed, iters=50):
+    """L = lambda_max(A^H A): v <- N v / ||N v|| from a unit SplitMix64 start;
+    L is the Rayleigh quotient Re<v, N v> of the last step."""
+    n = int(np.prod(shape))
+    v = start_vector(seed, n).reshape(shape)
+    v = v / np.linalg.norm(v)
+    lam = 0.0
+    for _ in range(iters):
+        w = normal(v)
+        lam = float(np.real(np.vdot(v, w)))
+        v = w / np.linalg.norm(w)
+    return lam
+
+
+# --------------------------------------------------------------------------
+# Algorithm "pfista" (and "fista" with p = 1; "ppgd"/"pgd" with beta = 0)
+# --------------------------------------------------------------------------
+
+
+def pfista(normal, adjoint, b, lam, coeffs, iters, L, levels=2, normalize_b=True,
+           momentum=True, history=None):
+    """Polynomial-preconditioned FISTA on the normalised problem.
+
+    A_hat = A/sqrt(L), b_hat = b/||b|| (when normalize_b), N_hat = A_hat^H A_hat.
+    y_{-1} = y_0 = z_0 = 0; for k = 0..iters-1:
+        g       = N_hat z_k - A_hat^H b_hat
+        u       = p(N_hat) g            (coeffs None: p = 1)
+        y_{k+1} = prox_{lam ||W.||_1}(z_k - u)
+        beta_k  = k/(k+3)               (0 when momentum is False: Alg. "ppgd")
+        z_{k+1} = y_{k+1} + beta_k (y_{k+1} - y_k)
+    Returns y_iters.  `history`, if a list, receives every y_{k+1}."""
+    b = np.asarray(b, dtype=np.complex128)
+    bn = float(np.linalg.norm(b)) if normalize_b else 1.0
+    ahb = adjoint(b) / (math.sqrt(L) * bn)
+
+    def nhat(v):
+        return normal(v) / L
+
+    y = np.zeros_like(ahb)
+    z = np.zeros_like(ahb)
+    for k in range(iters):
+        g = nhat(z) - ahb
+        u = g if coeffs is None else horner_apply(coeffs, nhat, g)
+        y_new = prox_l1_haar(z - u, lam, levels)
+        beta = k / (k + 3.0) if momentum else 0.0
+        z = y_new + beta * (y_new - y)
+        y = y_new
+        if history is not None:
+            history.append(y.copy())
+    return y

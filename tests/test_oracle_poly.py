@@ -1,0 +1,114 @@
+"""Pins for the polynomial preconditioner: Eq. "l2cost" (Sec. 3.1),
+Thm. "ppos" (Sec. 3.4), the recursion of Listing "pcode" (Sec. 3.6),
+Lemma "permute" (Sec. 3.3) and Fig. "complexity" (Sec. 3.6)."""
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from oracle import pp_oracle as O
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def load_coeff_table():
+    out = {}
+    with open(os.path.join(GOLDEN, "l2_coeffs.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            d, rest = line.split(":")
+            out[int(d)] = [Fraction(t) for t in rest.split()]
+    return out
+
+
+def cost_by_quadrature(c):
+    # Gauss-Legendre on [0, 1] with 40 nodes is exact for degree <= 79.
+    t, w = np.polynomial.legendre.leggauss(40)
+    z = 0.5 * (t + 1.0)
+    r = 1.0 - z * O.poly_eval(c, z)
+    return 0.5 * float(np.sum(w * r * r))
+
+
+@pytest.mark.parametrize("d", range(0, 9))
+def test_golden_table_is_the_oracle(d):
+    assert load_coeff_table()[d] == O.poly_coeffs_l2(d)
+
+
+@pytest.mark.parametrize("d", range(0, 9))
+def test_minimum_cost_closed_form(d):
+    # the minimum of the l2 cost is 1/(d+2)^2
+    c = O.poly_coeffs_l2(d)
+    assert abs(cost_by_quadrature(c) - 1.0 / (d + 2) ** 2) <= 1e-12
+
+
+@pytest.mark.parametrize("d", range(0, 6))
+def test_coefficients_match_discretised_least_squares(d):
+    # Independent route: weighted least squares on Gauss-Legendre nodes,
+    # min sum_j w_j (1 - sum_i c_i z_j^{i+1})^2, which equals the integral.
+    t, w = np.polynomial.legendre.leggauss(40)
+    z = 0.5 * (t + 1.0)
+    sw = np.sqrt(0.5 * w)
+    V = np.stack([z ** (i + 1) for i in range(d + 1)], axis=1)
+    c_ls, *_ = np.linalg.lstsq(sw[:, None] * V, sw, rcond=None)
+    c = np.array([float(x) for x in O.poly_coeffs_l2(d)])
+    assert np.max(np.abs(c - c_ls)) <= 1e-7 * np.max(np.abs(c))
+
+
+@pytest.mark.parametrize("d", range(0, 9))
+def test_positivity_on_unit_interval(d):
+    z = np.linspace(1e-6, 1.0, 20001)
+    assert np.all(O.poly_eval(O.poly_coeffs_l2(d), z) > 0.0)
+
+
+def test_figure_complexity_regions():
+    c3 = O.poly_coeffs_l2(3)
+    with open(os.path.join(GOLDEN, "fig_complexity.txt")) as f:
+        rows = [l.split() for l in f if l.strip() and not l.startswith("#")]
+    for z, region in rows:
+        z = float(z)
+        pgd = (1.0 - z) ** 4
+        pp = abs(1.0 - z * O.poly_eval(c3, np.array([z]))[0])
+        if region == "low":
+            assert pp < pgd
+        else:
+            assert pp > pgd
+
+
+@pytest.mark.parametrize("d", [0, 1, 3, 5])
+def test_horner_on_diagonal_operator(d):
+    # For N = diag(lam_i), p(N) g = p(lam_i) g_i, with exactly d applies of N.
+    rng = np.random.default_rng(d)
+    lam = rng.uniform(0.0, 1.0, 64)
+    g = rng.standard_normal(64) + 1j * rng.standard_normal(64)
+    calls = []
+
+    def normal(v):
+        calls.append(1)
+        return lam * v
+
+    c = O.poly_coeffs_l2(d)
+    got = O.horner_apply(c, normal, g)
+    ref = O.poly_eval(c, lam) * g
+    assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
+    assert len(calls) == d
+
+
+def test_permutability_lemma():
+    # A^H p(A A^H) = p(A^H A) A^H for a dense A (Lemma "permute").
+    rng = np.random.default_rng(0)
+    A = rng.standard_normal((7, 5)) + 1j * rng.standard_normal((7, 5))
+    A /= np.linalg.norm(A, 2)
+    c = [float(x) for x in O.poly_coeffs_l2(3)]
+
+    def pmat(M):
+        out = c[-1] * np.eye(M.shape[0])
+        for ci in reversed(c[:-1]):
+            out = ci * np.eye(M.shape[0]) + M @ out
+        return out
+
+    AH = A.conj().T
+    lhs = AH @ pmat(A @ AH)
+    rhs = pmat(AH @ A) @ AH
+    assert np.max(np.abs(lhs - rhs)) <= 1e-12 * np.max(np.abs(lhs))
