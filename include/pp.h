@@ -1,0 +1,177 @@
+/*
+ * pp.h - C ABI of the polynomial-preconditioned FISTA library (libpp).
+ *
+ * Iyer et al., "Polynomial Preconditioners for Regularized Linear Inverse
+ * Problems": solve  min_x 1/2 ||A x - b||_2^2 + lambda ||W x||_1  (Eq. "ucopt",
+ * Sec. 1) with Algorithm "pfista" (Sec. 3.1), where A is a multi-coil SENSE
+ * operator (Sec. 5.1 Cartesian, Sec. 5.2 non-Cartesian), W an orthonormal
+ * Haar wavelet and p(A^H A) the preconditioner of Eq. "l2cost", applied by the
+ * recursion of Listing "pcode" (Sec. 3.6).
+ *
+ * Conventions shared by every call
+ *  - Complex data are interleaved complex64 (pp_c64: re, im), C order with
+ *    the readout axis x fastest:
+ *      image           [nz][ny][nx]          (nz = 1 in 2-D)
+ *      sensitivities   [C][nz][ny][nx]
+ *      Cartesian k     [C][nz][ny][nx]       centred order, zero off-mask
+ *      non-Cartesian k [C][K]                sample order of the trajectory
+ *  - "device" pointers are CUDA global memory on the current device; "host"
+ *    pointers are ordinary CPU memory.  The library never takes ownership of
+ *    caller memory.  A plan owns the device workspace it allocates.
+ *  - pp_stream is a cudaStream_t (NULL = legacy default stream).  Device
+ *    work is enqueued on that stream; calls return without synchronising
+ *    except where they return a value computed on the device (plan creation,
+ *    pp_fista_solve when info->history is set).
+ *  - Every call returns a pp_status.  On failure pp_last_error() gives a
+ *    thread-local message.  No call throws, aborts or traps.
+ *  - Input and output arrays of one call must not overlap unless the call
+ *    says otherwise.
+ */
+#ifndef PP_H
+#define PP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PP_OK = 0,
+    PP_ERR_INVALID_ARG = 1,  /* null pointer, bad size, bad enum          */
+    PP_ERR_UNSUPPORTED = 2,  /* valid but not implemented (see each call) */
+    PP_ERR_OOM = 3,          /* device allocation failed                  */
+    PP_ERR_CUDA = 4,         /* a CUDA runtime call failed                */
+    PP_ERR_NONFINITE = 5,    /* NaN/Inf met in a reduction                */
+    PP_ERR_TIMEOUT = 6       /* reserved: a bounded device wait expired   */
+} pp_status;
+
+typedef struct { float re, im; } pp_c64;
+typedef void* pp_stream;
+
+/* Image size: n[0] = nx (fastest), n[1] = ny, n[2] = nz (used when ndim == 3). */
+typedef struct { int ndim; int n[3]; } pp_dims;
+
+enum { PP_CARTESIAN = 0, PP_NONCARTESIAN = 1 };
+
+/* Sampling pattern (the M of Sec. 5.1, or the trajectory of Sec. 5.2).
+ *  kind == PP_CARTESIAN:    mask = host uint8 [nz][ny][nx], centred order,
+ *                           nonzero = sampled.  It must be constant along x
+ *                           (readout); otherwise PP_ERR_UNSUPPORTED.
+ *  kind == PP_NONCARTESIAN: traj = host float [K][2] = (kx, ky) in cycles per
+ *                           field of view, each in [-n/2, n/2); 2-D only.
+ *                           Gridding uses a Kaiser-Bessel kernel of width
+ *                           kb_width (must be 4) on a grid of
+ *                           ceil(oversamp * n) points per axis (oversamp in
+ *                           [1.125, 2]); the grid size must be even, have no
+ *                           prime factor above 5 and be at least 40.
+ *  The plan copies what it needs; the host arrays may be freed on return. */
+typedef struct {
+    int kind;
+    const uint8_t* mask;
+    const float* traj;
+    int64_t K;
+    int kb_width;
+    float oversamp;
+} pp_sampling;
+
+typedef struct pp_plan pp_plan;
+
+/* Build a plan for the operator A = [P S_1; ...; P S_C] (Sec. 5.1/5.2) and
+ * estimate L = lambda_max(A^H A) by power_iters steps of power iteration
+ * from a SplitMix64 start vector drawn from `seed` (Sec. 5 normalises A to
+ * unit induced norm; the solver divides by L).  power_iters = 0 leaves L = 1
+ * (set it with pp_plan_set_scale).
+ *   dims   2-D (ndim 2) or 3-D (ndim 3, Cartesian only).  Every FFT length
+ *          (ny, nz; and nx plus the grid size for non-Cartesian) must have no
+ *          prime factor above 5 and be even; nx and ny (and nz) must be
+ *          multiples of 4 (the 2-level Haar tile).  Else PP_ERR_UNSUPPORTED.
+ *   coils  1..64.
+ *   sens   device [C][nz][ny][nx] complex64, BORROWED: it must stay valid and
+ *          unchanged until pp_plan_destroy.
+ *   s      sampling pattern, see pp_sampling.
+ * Synchronises `stream` once (to read L).  On failure *out is NULL. */
+pp_status pp_plan_create(pp_plan** out, pp_dims dims, int coils, const pp_c64* sens,
+                         const pp_sampling* s, uint64_t seed, int power_iters, pp_stream stream);
+
+/* Free the plan and its device workspace.  Call after the plan's last
+ * enqueued work has finished.  NULL is accepted. */
+pp_status pp_plan_destroy(pp_plan* plan);
+
+/* L used for A_hat = A / sqrt(L) (host double out). */
+pp_status pp_plan_scale(const pp_plan* plan, double* L);
+
+/* Replace L (L > 0, finite); used to share one estimate between runs. */
+pp_status pp_plan_set_scale(pp_plan* plan, double L);
+
+/* Element counts of the image ([nz][ny][nx]) and of the k-space array
+ * ([C][...] as above); either pointer may be NULL. */
+pp_status pp_plan_sizes(const pp_plan* plan, int64_t* image_elems, int64_t* kspace_elems);
+
+/* y = A x (unscaled forward model; Sec. 5.1: M F S_c x with the centred
+ * orthonormal FFT; Sec. 5.2: gridding NUFFT of S_c x).
+ * x device image, y device k-space. */
+pp_status pp_forward_apply(const pp_plan* plan, const pp_c64* x, pp_c64* y, pp_stream stream);
+
+/* x = A^H y (unscaled adjoint).  y device k-space, x device image. */
+pp_status pp_adjoint_apply(const pp_plan* plan, const pp_c64* y, pp_c64* x, pp_stream stream);
+
+/* y = (A^H A / L) x, the normalised normal operator N_hat of Algorithm
+ * "pfista".  x, y device images.  Cartesian plans use the readout
+ * shortcut F_x^H (F_yz^H M F_yz) F_x = F_yz^H M F_yz, exact because M is
+ * constant along x. */
+pp_status pp_normal_apply(const pp_plan* plan, const pp_c64* x, pp_c64* y, pp_stream stream);
+
+/* c[0..d] (host double) minimising int_0^1 (1 - z p(z))^2 dz, Eq. "l2cost"
+ * (Sec. 3.1), p(z) = sum_i c[i] z^i (order of Sec. 3.6).  0 <= d <= 8.
+ * Computed in closed form as exact integer ratios (shifted-Legendre
+ * Christoffel-Darboux kernel), each rounded once to double.  Host only; no
+ * device work. */
+pp_status pp_poly_coeffs_l2(int d, double* c);
+
+/* out = p(N_hat) v by the recursion of Listing "pcode": u = c_d v, then
+ * u = c_i v + N_hat u for i = d-1..0 (d applies of N_hat).  c host double
+ * [d+1], 0 <= d <= 16.  v, out device images. */
+pp_status pp_poly_apply(const pp_plan* plan, const double* c, int d, const pp_c64* v,
+                        pp_c64* out, pp_stream stream);
+
+/* out = prox_{lambda ||W.||_1}(in) = W^T soft_lambda(W in) (Eq. "proxdef",
+ * Sec. 2.1) with W the orthonormal separable Haar wavelet of `levels` levels
+ * (1 or 2) over every image axis; soft_lambda(v) = v max(0, 1 - lambda/|v|)
+ * on every coefficient.  Each image axis must be a multiple of 2^levels.
+ * in, out device images; in == out is allowed. */
+pp_status pp_prox_l1_haar(pp_dims dims, int levels, float lambda, const pp_c64* in, pp_c64* out,
+                          pp_stream stream);
+
+/* Optional solve outputs.  history, if non-NULL, is host double [iters][2]
+ * receiving ||y_{k+1} - y_k||_2^2 and ||y_{k+1}||_2^2 per iteration (FP64
+ * reductions on the device); setting it makes the call synchronise. */
+typedef struct {
+    int rescale;        /* in: 1 = multiply x_out by ||b|| / sqrt(L)        */
+    int levels;         /* in: Haar levels (0 means 2)                      */
+    double* history;    /* in: optional host buffer, see above              */
+    double bnorm;       /* out: ||b||_2 (valid when history != NULL)        */
+    double L;           /* out: the L used                                  */
+} pp_solve_info;
+
+/* Algorithm "pfista" on the normalised problem (Sec. 5): A_hat = A/sqrt(L),
+ * b_hat = b/||b||_2, y_{-1} = y_0 = z_0 = 0, for k = 0..iters-1:
+ *   g = N_hat z_k - A_hat^H b_hat;  u = p(N_hat) g;
+ *   y_{k+1} = prox_{lambda ||W.||_1}(z_k - u);
+ *   z_{k+1} = y_{k+1} + (k/(k+3)) (y_{k+1} - y_k).
+ * c host double [d+1] (Eq. "l2cost" coefficients or any other); c == NULL
+ * with d == 0 is plain FISTA (Algorithm "fista", p = 1).  b device k-space,
+ * x_out device image (y_iters).  info may be NULL.  The iteration loop runs
+ * as one CUDA graph, captured on first use and reused while iters, c, d,
+ * lambda and levels are unchanged. */
+pp_status pp_fista_solve(pp_plan* plan, const pp_c64* b, float lambda, int iters, const double* c,
+                         int d, pp_c64* x_out, pp_solve_info* info, pp_stream stream);
+
+/* Message for the last failing call on this thread ("" if none). */
+const char* pp_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PP_H */

@@ -1,0 +1,269 @@
+"""Thin ctypes binding of libpp (include/pp.h): argument marshalling only.
+
+Every function below has the name and argument order of the C entry point
+it wraps.  Device arrays are torch complex64 CUDA tensors (PyTorch provides
+memory and streams; all arithmetic runs in libpp's kernels).  A call that
+returns a status other than PP_OK raises PPError with pp_last_error().
+There is no fallback: when libpp.so is missing or cannot be loaded, the
+first call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libpp.so")
+
+PP_OK, PP_ERR_INVALID_ARG, PP_ERR_UNSUPPORTED, PP_ERR_OOM, PP_ERR_CUDA, PP_ERR_NONFINITE, \
+    PP_ERR_TIMEOUT = range(7)
+PP_CARTESIAN, PP_NONCARTESIAN = 0, 1
+STATUS_NAMES = {0: "PP_OK", 1: "PP_ERR_INVALID_ARG", 2: "PP_ERR_UNSUPPORTED", 3: "PP_ERR_OOM",
+                4: "PP_ERR_CUDA", 5: "PP_ERR_NONFINITE", 6: "PP_ERR_TIMEOUT"}
+
+
+class PPError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        super().__init__("%s: %s (%s)" % (where, message, STATUS_NAMES.get(status, status)))
+        self.status = status
+
+
+class pp_dims(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int), ("n", ctypes.c_int * 3)]
+
+
+class pp_sampling(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("mask", ctypes.c_void_p), ("traj", ctypes.c_void_p),
+                ("K", ctypes.c_int64), ("kb_width", ctypes.c_int), ("oversamp", ctypes.c_float)]
+
+
+class pp_solve_info(ctypes.Structure):
+    _fields_ = [("rescale", ctypes.c_int), ("levels", ctypes.c_int),
+                ("history", ctypes.c_void_p), ("bnorm", ctypes.c_double), ("L", ctypes.c_double)]
+
+
+_lib = None
+
+_SIGS = {
+    "pp_plan_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), pp_dims, ctypes.c_int,
+                                      ctypes.c_void_p, ctypes.POINTER(pp_sampling), ctypes.c_uint64,
+                                      ctypes.c_int, ctypes.c_void_p]),
+    "pp_plan_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "pp_plan_scale": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
+    "pp_plan_set_scale": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
+    "pp_plan_sizes": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
+                                     ctypes.POINTER(ctypes.c_int64)]),
+    "pp_forward_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "pp_adjoint_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "pp_normal_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "pp_poly_coeffs_l2": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+    "pp_poly_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int,
+                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "pp_prox_l1_haar": (ctypes.c_int, [pp_dims, ctypes.c_int, ctypes.c_float, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_void_p]),
+    "pp_fista_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_float, ctypes.c_int,
+                                      ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_void_p,
+                                      ctypes.POINTER(pp_solve_info), ctypes.c_void_p]),
+    "pp_last_error": (ctypes.c_char_p, []),
+}
+
+
+def lib(path: Optional[str] = None):
+    """Load libpp.so (once).  Raises when it is missing: there is no fallback."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError("libpp.so not found at %s: build it with "
+                           "paper_2204_10252_gb300.build.build_library()" % p)
+    L = ctypes.CDLL(p)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(status: int, where: str):
+    if status != PP_OK:
+        msg = lib().pp_last_error()
+        raise PPError(status, where, msg.decode() if msg else "")
+
+
+def _dims(shape: Sequence[int]) -> pp_dims:
+    """Image shape in C order ([ny, nx] or [nz, ny, nx]) -> pp_dims."""
+    shape = tuple(int(s) for s in shape)
+    d = pp_dims()
+    d.ndim = len(shape)
+    rev = list(reversed(shape)) + [1] * (3 - len(shape))
+    for i in range(3):
+        d.n[i] = rev[i]
+    return d
+
+
+def _dev_ptr(t, what: str) -> int:
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("%s must be a torch tensor" % what)
+    if not t.is_cuda or t.dtype != torch.complex64 or not t.is_contiguous():
+        raise ValueError("%s must be a contiguous complex64 CUDA tensor" % what)
+    return t.data_ptr()
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class Plan:
+    """Handle of a pp_plan.  Keeps the borrowed sensitivity tensor alive."""
+
+    def __init__(self, handle: int, shape, coils: int, sens, kspace_shape):
+        self.handle = ctypes.c_void_p(handle)
+        self.shape = tuple(shape)
+        self.coils = coils
+        self.kspace_shape = tuple(kspace_shape)
+        self._sens = sens
+
+    def destroy(self):
+        if self.handle:
+            _check(lib().pp_plan_destroy(self.handle), "pp_plan_destroy")
+            self.handle = ctypes.c_void_p(0)
+            self._sens = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.destroy()
+
+    def __del__(self):
+        try:
+            if self.handle:
+                lib().pp_plan_destroy(self.handle)
+        except Exception:
+            pass
+
+
+def pp_plan_create(shape, coils: int, sens, mask=None, traj=None, kb_width: int = 4,
+                   oversamp: float = 1.25, seed: int = 0, power_iters: int = 50,
+                   stream=None) -> Plan:
+    """shape: image shape [ny, nx] or [nz, ny, nx]; sens: CUDA complex64
+    [C, *shape]; mask: uint8 array of the image shape (Cartesian) or
+    traj: float32 [K, 2] (non-Cartesian)."""
+    s = pp_sampling()
+    keep = []
+    if mask is not None:
+        m = np.ascontiguousarray(mask, dtype=np.uint8)
+        keep.append(m)
+        s.kind = PP_CARTESIAN
+        s.mask = m.ctypes.data
+        s.traj = None
+        s.K = 0
+        kshape = (coils,) + tuple(shape)
+    elif traj is not None:
+        t = np.ascontiguousarray(traj, dtype=np.float32)
+        keep.append(t)
+        s.kind = PP_NONCARTESIAN
+        s.mask = None
+        s.traj = t.ctypes.data
+        s.K = int(t.shape[0])
+        kshape = (coils, int(t.shape[0]))
+    else:
+        raise ValueError("need a mask or a trajectory")
+    s.kb_width = int(kb_width)
+    s.oversamp = float(oversamp)
+    out = ctypes.c_void_p(0)
+    _check(lib().pp_plan_create(ctypes.byref(out), _dims(shape), int(coils), _dev_ptr(sens, "sens"),
+                                ctypes.byref(s), ctypes.c_uint64(seed), int(power_iters),
+                                _stream(stream)), "pp_plan_create")
+    return Plan(out.value, shape, coils, sens, kshape)
+
+
+def pp_plan_destroy(plan: Plan):
+    plan.destroy()
+
+
+def pp_plan_scale(plan: Plan) -> float:
+    L = ctypes.c_double(0.0)
+    _check(lib().pp_plan_scale(plan.handle, ctypes.byref(L)), "pp_plan_scale")
+    return L.value
+
+
+def pp_plan_set_scale(plan: Plan, L: float):
+    _check(lib().pp_plan_set_scale(plan.handle, float(L)), "pp_plan_set_scale")
+
+
+def pp_plan_sizes(plan: Plan):
+    a, b = ctypes.c_int64(0), ctypes.c_int64(0)
+    _check(lib().pp_plan_sizes(plan.handle, ctypes.byref(a), ctypes.byref(b)), "pp_plan_sizes")
+    return a.value, b.value
+
+
+def pp_forward_apply(plan: Plan, x, y, stream=None):
+    _check(lib().pp_forward_apply(plan.handle, _dev_ptr(x, "x"), _dev_ptr(y, "y"), _stream(stream)),
+           "pp_forward_apply")
+
+
+def pp_adjoint_apply(plan: Plan, y, x, stream=None):
+    _check(lib().pp_adjoint_apply(plan.handle, _dev_ptr(y, "y"), _dev_ptr(x, "x"), _stream(stream)),
+           "pp_adjoint_apply")
+
+
+def pp_normal_apply(plan: Plan, x, y, stream=None):
+    _check(lib().pp_normal_apply(plan.handle, _dev_ptr(x, "x"), _dev_ptr(y, "y"), _stream(stream)),
+           "pp_normal_apply")
+
+
+def pp_poly_coeffs_l2(d: int) -> np.ndarray:
+    c = (ctypes.c_double * (d + 1))() if d >= 0 else (ctypes.c_double * 1)()
+    _check(lib().pp_poly_coeffs_l2(int(d), c), "pp_poly_coeffs_l2")
+    return np.array(list(c), dtype=np.float64)
+
+
+def _cvec(c):
+    c = np.ascontiguousarray(c, dtype=np.float64)
+    return (ctypes.c_double * len(c))(*c.tolist())
+
+
+def pp_poly_apply(plan: Plan, c, d: int, v, out, stream=None):
+    _check(lib().pp_poly_apply(plan.handle, _cvec(c), int(d), _dev_ptr(v, "v"), _dev_ptr(out, "out"),
+                               _stream(stream)), "pp_poly_apply")
+
+
+def pp_prox_l1_haar(shape, levels: int, lam: float, x_in, x_out, stream=None):
+    _check(lib().pp_prox_l1_haar(_dims(shape), int(levels), float(lam), _dev_ptr(x_in, "in"),
+                                 _dev_ptr(x_out, "out"), _stream(stream)), "pp_prox_l1_haar")
+
+
+def pp_fista_solve(plan: Plan, b, lam: float, iters: int, c, d: int, x_out, stream=None,
+                   history: bool = False, rescale: bool = False, levels: int = 2):
+    """Returns (history array [iters, 2] or None, ||b||, L)."""
+    info = pp_solve_info()
+    info.rescale = 1 if rescale else 0
+    info.levels = int(levels)
+    hist = None
+    if history:
+        hist = np.zeros((max(iters, 1), 2), dtype=np.float64)
+        info.history = hist.ctypes.data
+    else:
+        info.history = None
+    cptr = _cvec(c) if c is not None else None
+    _check(lib().pp_fista_solve(plan.handle, _dev_ptr(b, "b"), float(lam), int(iters), cptr, int(d),
+                                _dev_ptr(x_out, "x_out"), ctypes.byref(info), _stream(stream)),
+           "pp_fista_solve")
+    return (hist[:iters] if hist is not None else None), info.bnorm, info.L
+
+
+def pp_last_error() -> str:
+    m = lib().pp_last_error()
+    return m.decode() if m else ""

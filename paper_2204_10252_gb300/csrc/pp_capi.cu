@@ -1,0 +1,789 @@
+// C ABI of libpp: plan set-up on the host, operator orchestration, the
+// Horner recursion of Listing "pcode" and Algorithm "pfista" (Sec. 3.1, 3.6).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "pp_internal.h"
+
+namespace pp {
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local std::string g_last_error;
+
+void set_error(const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+}
+
+pp_status cuda_status(cudaError_t e, const char* what) {
+    set_error("%s: %s", what, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? PP_ERR_OOM : PP_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------------------
+// host helpers
+// ---------------------------------------------------------------------------
+// Stage radices for length n: as many 8s as the power of two allows (a
+// remainder of 2^1 becomes 4*4 in place of one 8, or a single 2), then 5s and
+// 3s.  Returns false when n has a prime factor above 5.
+static bool factorize(int n, FftDesc& d) {
+    if (n < 2) return false;
+    int e2 = 0, m = n;
+    while (m % 2 == 0) { m /= 2; ++e2; }
+    int n5 = 0, n3 = 0;
+    while (m % 5 == 0) { m /= 5; ++n5; }
+    while (m % 3 == 0) { m /= 3; ++n3; }
+    if (m != 1) return false;
+    std::vector<int> r;
+    int q = e2 / 3, rem = e2 % 3;
+    if (rem == 1 && q >= 1) { for (int i = 0; i < q - 1; ++i) r.push_back(8); r.push_back(4); r.push_back(4); }
+    else { for (int i = 0; i < q; ++i) r.push_back(8); if (rem == 2) r.push_back(4); if (rem == 1) r.push_back(2); }
+    for (int i = 0; i < n5; ++i) r.push_back(5);
+    for (int i = 0; i < n3; ++i) r.push_back(3);
+    if ((int)r.size() > 8) return false;
+    d.n = n;
+    d.nst = (int)r.size();
+    for (int i = 0; i < 8; ++i) d.rad[i] = i < d.nst ? r[i] : 0;
+    return true;
+}
+
+static pp_status dev_alloc(Plan& p, void** ptr, size_t bytes) {
+    *ptr = nullptr;
+    if (bytes == 0) return PP_OK;
+    cudaError_t e = cudaMalloc(ptr, bytes);
+    if (e != cudaSuccess) {
+        *ptr = nullptr;
+        cudaGetLastError();
+        return cuda_status(e, "cudaMalloc");
+    }
+    p.allocs.push_back(*ptr);
+    return PP_OK;
+}
+
+template <class T>
+static pp_status alloc_n(Plan& p, T** ptr, size_t n) {
+    return dev_alloc(p, reinterpret_cast<void**>(ptr), n * sizeof(T));
+}
+
+static pp_status make_fft(Plan& p, int n, DevFft& f) {
+    if (!factorize(n, f.d)) {
+        set_error("FFT length %d has a prime factor above 5", n);
+        return PP_ERR_UNSUPPORTED;
+    }
+    std::vector<float2> tw(n);
+    for (int t = 0; t < n; ++t) {
+        const double a = -2.0 * M_PI * (double)t / (double)n;
+        tw[t] = make_float2((float)cos(a), (float)sin(a));
+    }
+    PP_TRY(alloc_n(p, &f.tw, n));
+    PP_TRY_CUDA(cudaMemcpy(f.tw, tw.data(), n * sizeof(float2), cudaMemcpyHostToDevice));
+    return PP_OK;
+}
+
+template <class T>
+static pp_status upload(Plan& p, T** dst, const std::vector<T>& src) {
+    PP_TRY(alloc_n(p, dst, src.size()));
+    PP_TRY_CUDA(cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return PP_OK;
+}
+
+// Kaiser-Bessel pieces (width W, shape beta):
+//   kernel  phi(u) = I0(beta sqrt(1 - (2u/W)^2)), |u| <= W/2
+//   its Fourier transform psi(nu) = W sinh(sqrt(a))/sqrt(a), a = beta^2 - (pi W nu)^2
+static double bessel_i0(double x) {
+    const double q = 0.25 * x * x;
+    double term = 1.0, sum = 1.0;
+    for (int k = 1; k < 200; ++k) {
+        term *= q / ((double)k * k);
+        sum += term;
+        if (term < 1e-17 * sum) break;
+    }
+    return sum;
+}
+static double kb_phi(double u, double W, double beta) {
+    const double t = 1.0 - (2.0 * u / W) * (2.0 * u / W);
+    return t < 0.0 ? 0.0 : bessel_i0(beta * sqrt(t));
+}
+static double kb_psi(double nu, double W, double beta) {
+    const double a = beta * beta - (M_PI * W * nu) * (M_PI * W * nu);
+    if (a > 0) return W * sinh(sqrt(a)) / sqrt(a);
+    if (a < 0) return W * sin(sqrt(-a)) / sqrt(-a);
+    return W;
+}
+
+static inline int wrap_host(int a, int G) {
+    a %= G;
+    return a < 0 ? a + G : a;
+}
+
+// ---------------------------------------------------------------------------
+// operator orchestration
+// ---------------------------------------------------------------------------
+static ColArgs col_args(int Hin, int Hout, int G, int off_in, int off_out, int ncols,
+                        int64_t ibs, int64_t obs, int nbatch, float scale) {
+    ColArgs a;
+    a.Hin = Hin; a.Hout = Hout; a.G = G; a.off_in = off_in; a.off_out = off_out;
+    a.ncols = ncols; a.in_batch_stride = ibs; a.out_batch_stride = obs; a.nbatch = nbatch;
+    a.scale = scale; a.mul_in = nullptr; a.mul_out = nullptr; a.mo_q = 0; a.mo_c = 0; a.mo_cdiv = 1;
+    a.mi_q = 1; a.mi_c = 0; a.mi_cdiv = 1;
+    return a;
+}
+
+static RowArgs row_args(int n, int G, int off_in, int off_out, int nrows, int64_t cis, float scale) {
+    RowArgs a;
+    a.n = n; a.G = G; a.off_in = off_in; a.off_out = off_out; a.nrows = nrows;
+    a.coil_img_stride = cis; a.scale = scale;
+    return a;
+}
+
+// out = scale * (A^H A x) + alpha * operand   (operand may be NULL)
+static pp_status normal_into(const Plan& p, const float2* x, float2* out, float scale,
+                             const float2* operand, float alpha, cudaStream_t st) {
+    const int nx = p.nx, ny = p.ny, nz = p.nz;
+    const int64_t n = p.nimg;
+    if (p.kind == PP_CARTESIAN && p.ndim == 2)
+        return launch_cart2d_normal(p, x, out, scale, operand, alpha, st);
+    if (p.kind == PP_CARTESIAN) {
+        // 3-D: per coil, y FFT -> (z FFT, mask, z IFFT) -> y IFFT -> conj accumulate
+        for (int c = 0; c < p.C; ++c) {
+            const float2* sc = p.sens + (int64_t)c * n;
+            PP_TRY(launch_expand(x, sc, p.wk_a, n, st));
+            ColArgs ay = col_args(ny, ny, ny, 0, 0, nx, (int64_t)ny * nx, (int64_t)ny * nx, nz, 1.f);
+            PP_TRY(launch_cols(p.fy, ay, p.wk_a, p.wk_b, false, st));
+            ColArgs az = col_args(nz, nz, nz, 0, 0, ny * nx, 0, 0, 1, 1.f);
+            az.mo_q = ny; az.mo_c = 1; az.mo_cdiv = nx;
+            PP_TRY(launch_cols_roundtrip(p.fz, az, p.mask_fo, p.wk_b, p.wk_a, st));
+            PP_TRY(launch_cols(p.fy, ay, p.wk_a, p.wk_b, true, st));
+            PP_TRY(launch_conj_accum(sc, p.wk_b, out, n, c == 0, scale, operand, alpha, c == p.C - 1, st));
+        }
+        return PP_OK;
+    }
+    // non-Cartesian: rows -> cols -> tile degrid/grid -> cols^H -> rows^H
+    const int Gx = p.G_x, Gy = p.G_y;
+    RowArgs rf = row_args(nx, Gx, nx / 2, 0, ny, (int64_t)ny * nx, 1.f);
+    PP_TRY(launch_rows_fwd(p, p.gx, rf, x, p.sens, p.deapod_y, p.deapod_x, p.wk_a, p.C, 0, st));
+    ColArgs cf = col_args(ny, Gy, Gy, ny / 2, 0, Gx, (int64_t)ny * Gx, (int64_t)Gy * Gx, p.C, 1.f);
+    PP_TRY(launch_cols(p.gy, cf, p.wk_a, p.wk_b, false, st));
+    PP_TRY(launch_nufft_tile_normal(p, p.wk_b, p.wk_c, st));
+    ColArgs ci = col_args(Gy, ny, Gy, 0, ny / 2, Gx, (int64_t)Gy * Gx, (int64_t)ny * Gx, p.C, 1.f);
+    PP_TRY(launch_cols(p.gy, ci, p.wk_c, p.wk_a, true, st));
+    RowArgs ra = row_args(nx, Gx, 0, nx / 2, ny, (int64_t)ny * nx, scale);
+    return launch_rows_adj(p, p.gx, ra, p.wk_a, p.sens, p.deapod_y, p.deapod_x, out, operand, alpha,
+                           p.C, st);
+}
+
+// y = A x (unscaled)
+static pp_status forward_into(const Plan& p, const float2* x, float2* y, cudaStream_t st) {
+    const int nx = p.nx, ny = p.ny, nz = p.nz;
+    const int64_t n = p.nimg;
+    if (p.kind == PP_CARTESIAN) {
+        // centred orthonormal FFT along x, then y (then z), mask on the last axis pass
+        RowArgs rf = row_args(nx, nx, nx / 2, nx / 2, ny * nz, n, (float)(1.0 / sqrt((double)nx)));
+        PP_TRY(launch_rows_fwd(p, p.fx, rf, x, p.sens, nullptr, nullptr, y, p.C, 0, st));
+        ColArgs ay = col_args(ny, ny, ny, ny / 2, ny / 2, nx, (int64_t)ny * nx, (int64_t)ny * nx,
+                              p.C * nz, (float)(1.0 / sqrt((double)ny)));
+        if (p.ndim == 2) {
+            ay.mul_out = p.mask_c; ay.mo_q = 1; ay.mo_c = 0; ay.mo_cdiv = 1;
+            return launch_cols(p.fy, ay, y, y, false, st);
+        }
+        PP_TRY(launch_cols(p.fy, ay, y, y, false, st));
+        ColArgs az = col_args(nz, nz, nz, nz / 2, nz / 2, ny * nx, n, n, p.C,
+                              (float)(1.0 / sqrt((double)nz)));
+        az.mul_out = p.mask_c; az.mo_q = ny; az.mo_c = 1; az.mo_cdiv = nx;
+        return launch_cols(p.fz, az, y, y, false, st);
+    }
+    const int Gx = p.G_x, Gy = p.G_y;
+    RowArgs rf = row_args(nx, Gx, nx / 2, 0, ny, (int64_t)ny * nx, 1.f);
+    PP_TRY(launch_rows_fwd(p, p.gx, rf, x, p.sens, p.deapod_y, p.deapod_x, p.wk_a, p.C, 0, st));
+    ColArgs cf = col_args(ny, Gy, Gy, ny / 2, 0, Gx, (int64_t)ny * Gx, (int64_t)Gy * Gx, p.C, 1.f);
+    PP_TRY(launch_cols(p.gy, cf, p.wk_a, p.wk_b, false, st));
+    return launch_nufft_degrid(p, p.wk_b, y, st);
+}
+
+// x = A^H y (unscaled)
+static pp_status adjoint_into(const Plan& p, const float2* y, float2* x, cudaStream_t st) {
+    const int nx = p.nx, ny = p.ny, nz = p.nz;
+    const int64_t n = p.nimg;
+    if (p.kind == PP_CARTESIAN && p.ndim == 2) {
+        ColArgs ay = col_args(ny, ny, ny, ny / 2, ny / 2, nx, (int64_t)ny * nx, (int64_t)ny * nx, p.C,
+                              (float)(1.0 / sqrt((double)ny)));
+        ay.mul_in = p.mask_c;   // centred mask indexed by the input row ky
+        PP_TRY(launch_cols(p.fy, ay, y, p.wk_a, true, st));
+        RowArgs ra = row_args(nx, nx, nx / 2, nx / 2, ny, n, (float)(1.0 / sqrt((double)nx)));
+        return launch_rows_adj(p, p.fx, ra, p.wk_a, p.sens, nullptr, nullptr, x, nullptr, 0.f, p.C, st);
+    }
+    if (p.kind == PP_CARTESIAN) {
+        // 3-D, per coil: mask and inverse centred FFT along z, then y, then
+        // the x rows with the conjugate sensitivity, accumulated into x.
+        for (int c = 0; c < p.C; ++c) {
+            const float2* yc = y + (int64_t)c * n;
+            ColArgs az = col_args(nz, nz, nz, nz / 2, nz / 2, ny * nx, 0, 0, 1,
+                                  (float)(1.0 / sqrt((double)nz)));
+            az.mul_in = p.mask_c; az.mi_q = ny; az.mi_c = 1; az.mi_cdiv = nx;
+            PP_TRY(launch_cols(p.fz, az, yc, p.wk_a, true, st));
+            ColArgs ay = col_args(ny, ny, ny, ny / 2, ny / 2, nx, (int64_t)ny * nx, (int64_t)ny * nx,
+                                  nz, (float)(1.0 / sqrt((double)ny)));
+            PP_TRY(launch_cols(p.fy, ay, p.wk_a, p.wk_b, true, st));
+            RowArgs ra = row_args(nx, nx, nx / 2, nx / 2, ny * nz, 0, (float)(1.0 / sqrt((double)nx)));
+            PP_TRY(launch_rows_adj(p, p.fx, ra, p.wk_b, p.sens + (int64_t)c * n, nullptr, nullptr, x,
+                                   c == 0 ? nullptr : x, 1.f, 1, st));
+        }
+        return PP_OK;
+    }
+    const int Gx = p.G_x, Gy = p.G_y;
+    PP_TRY(launch_nufft_spread(p, y, p.wk_b, st));
+    ColArgs ci = col_args(Gy, ny, Gy, 0, ny / 2, Gx, (int64_t)Gy * Gx, (int64_t)ny * Gx, p.C, 1.f);
+    PP_TRY(launch_cols(p.gy, ci, p.wk_b, p.wk_a, true, st));
+    RowArgs ra = row_args(nx, Gx, 0, nx / 2, ny, (int64_t)ny * nx, 1.f);
+    return launch_rows_adj(p, p.gx, ra, p.wk_a, p.sens, p.deapod_y, p.deapod_x, x, nullptr, 0.f,
+                           p.C, st);
+}
+
+// ---------------------------------------------------------------------------
+// plan construction
+// ---------------------------------------------------------------------------
+static pp_status build_cartesian(Plan& p, const uint8_t* mask) {
+    const int nx = p.nx, ny = p.ny, nz = p.nz;
+    // readout invariance: mask[z][y][x] == mask[z][y][0]
+    std::vector<float> mc((size_t)nz * ny), mfo((size_t)nz * ny);
+    for (int z = 0; z < nz; ++z)
+        for (int yy = 0; yy < ny; ++yy) {
+            const uint8_t* row = mask + ((size_t)z * ny + yy) * nx;
+            const uint8_t m0 = row[0] ? 1 : 0;
+            for (int x = 1; x < nx; ++x)
+                if ((row[x] ? 1 : 0) != m0) {
+                    set_error("Cartesian mask varies along the readout axis x (z=%d, y=%d)", z, yy);
+                    return PP_ERR_UNSUPPORTED;
+                }
+            mc[(size_t)z * ny + yy] = (float)m0;
+        }
+    // FFT order: centred index q holds frequency q - n/2, stored at (q - n/2) mod n
+    const double norm = 1.0 / ((double)ny * (double)nz);
+    for (int z = 0; z < nz; ++z)
+        for (int yy = 0; yy < ny; ++yy) {
+            const int zf = wrap_host(z - nz / 2, nz), yf = wrap_host(yy - ny / 2, ny);
+            mfo[(size_t)zf * ny + yf] = (float)(mc[(size_t)z * ny + yy] * norm);
+        }
+    PP_TRY(upload(p, &p.mask_c, mc));
+    PP_TRY(upload(p, &p.mask_fo, mfo));
+    PP_TRY(make_fft(p, nx, p.fx));
+    PP_TRY(make_fft(p, ny, p.fy));
+    if (p.ndim == 3) PP_TRY(make_fft(p, nz, p.fz));
+    if (p.ndim == 2) {
+        PP_TRY(alloc_n(p, &p.wk_a, (size_t)p.C * p.nimg));
+    } else {
+        PP_TRY(alloc_n(p, &p.wk_a, (size_t)p.nimg));
+        PP_TRY(alloc_n(p, &p.wk_b, (size_t)p.nimg));
+    }
+    p.nksp = (int64_t)p.C * p.nimg;
+    return PP_OK;
+}
+
+static pp_status build_noncartesian(Plan& p, const pp_sampling* s) {
+    const int nx = p.nx, ny = p.ny;
+    const int W = s->kb_width;
+    const double sigma = s->oversamp;
+    if (W != 4) {
+        set_error("kb_width must be 4");
+        return PP_ERR_UNSUPPORTED;
+    }
+    if (!(sigma >= 1.125 && sigma <= 2.0)) {
+        set_error("oversamp must lie in [1.125, 2]");
+        return PP_ERR_INVALID_ARG;
+    }
+    if (s->K < 1 || s->K > (1 << 26)) {
+        set_error("K out of range");
+        return PP_ERR_INVALID_ARG;
+    }
+    const int Gx = (int)ceil(sigma * nx - 1e-9), Gy = (int)ceil(sigma * ny - 1e-9);
+    if ((Gx & 1) || (Gy & 1)) {
+        set_error("oversampled grid %dx%d must be even", Gy, Gx);
+        return PP_ERR_UNSUPPORTED;
+    }
+    p.G_x = Gx; p.G_y = Gy; p.W = W; p.K = (int)s->K;
+    if (Gx < p.T + 2 * W || Gy < p.T + 2 * W) {
+        set_error("oversampled grid too small for gridding tiles");
+        return PP_ERR_UNSUPPORTED;
+    }
+    PP_TRY(make_fft(p, Gx, p.gx));
+    PP_TRY(make_fft(p, Gy, p.gy));
+    // Beatty et al. (2005) shape parameter
+    const double beta = M_PI * sqrt((W / sigma) * (W / sigma) * (sigma - 0.5) * (sigma - 0.5) - 0.8);
+    std::vector<float> dx(nx), dy(ny);
+    for (int i = 0; i < nx; ++i)
+        dx[i] = (float)(1.0 / (sqrt((double)nx) * kb_psi((double)(i - nx / 2) / Gx, W, beta)));
+    for (int i = 0; i < ny; ++i)
+        dy[i] = (float)(1.0 / (sqrt((double)ny) * kb_psi((double)(i - ny / 2) / Gy, W, beta)));
+    PP_TRY(upload(p, &p.deapod_x, dx));
+    PP_TRY(upload(p, &p.deapod_y, dy));
+    // per-sample taps: m in (s - W/2, s + W/2], s = kappa * G / n
+    const int K = p.K;
+    std::vector<SampleTaps> st(K);
+    for (int k = 0; k < K; ++k) {
+        const double kx = s->traj[2 * k], ky = s->traj[2 * k + 1];
+        if (!(kx >= -nx / 2.0 && kx < nx / 2.0 && ky >= -ny / 2.0 && ky < ny / 2.0)) {
+            set_error("trajectory sample %d (%g, %g) outside [-n/2, n/2)", k, kx, ky);
+            return PP_ERR_INVALID_ARG;
+        }
+        const double sx = kx * Gx / nx, sy = ky * Gy / ny;
+        const int ix0 = (int)floor(sx - W / 2.0) + 1, iy0 = (int)floor(sy - W / 2.0) + 1;
+        float w[2][4];
+        for (int a = 0; a < 4; ++a) {
+            w[0][a] = (float)kb_phi(sx - (ix0 + a), W, beta);
+            w[1][a] = (float)kb_phi(sy - (iy0 + a), W, beta);
+        }
+        st[k].wx = make_float4(w[0][0], w[0][1], w[0][2], w[0][3]);
+        st[k].wy = make_float4(w[1][0], w[1][1], w[1][2], w[1][3]);
+        st[k].ix0 = ix0;
+        st[k].iy0 = iy0;
+    }
+    PP_TRY(upload(p, &p.samp, st));
+    // tile lists (with halo): every tile whose rows and columns meet the footprint
+    const int T = p.T, H = W - 1;
+    p.ntx = (Gx + T - 1) / T;
+    p.nty = (Gy + T - 1) / T;
+    const int ntiles = p.ntx * p.nty;
+    std::vector<std::vector<TileEntry>> lists(ntiles);
+    for (int k = 0; k < K; ++k) {
+        int trow[4], tcol[4], nr = 0, nc = 0;
+        for (int b = 0; b < W; ++b) {
+            const int ty = wrap_host(st[k].iy0 + b, Gy) / T;
+            if (std::find(trow, trow + nr, ty) == trow + nr) trow[nr++] = ty;
+            const int tx = wrap_host(st[k].ix0 + b, Gx) / T;
+            if (std::find(tcol, tcol + nc, tx) == tcol + nc) tcol[nc++] = tx;
+        }
+        for (int i = 0; i < nr; ++i)
+            for (int j = 0; j < nc; ++j) {
+                const int ty0 = trow[i] * T, tx0 = tcol[j] * T;
+                const int ly0 = wrap_host(st[k].iy0 - ty0 + H, Gy);
+                const int lx0 = wrap_host(st[k].ix0 - tx0 + H, Gx);
+                TileEntry e;
+                e.wx = st[k].wx;
+                e.wy = st[k].wy;
+                e.lyx = ly0 | (lx0 << 16);
+                e.k = k;
+                lists[trow[i] * p.ntx + tcol[j]].push_back(e);
+            }
+    }
+    std::vector<int> start(ntiles + 1, 0);
+    std::vector<TileEntry> flat;
+    for (int t = 0; t < ntiles; ++t) {
+        start[t] = (int)flat.size();
+        p.max_tile_len = std::max(p.max_tile_len, (int)lists[t].size());
+        flat.insert(flat.end(), lists[t].begin(), lists[t].end());
+    }
+    start[ntiles] = (int)flat.size();
+    if (flat.empty()) flat.push_back(TileEntry());
+    PP_TRY(upload(p, &p.tiles, flat));
+    PP_TRY(upload(p, &p.tile_start, start));
+    PP_TRY(alloc_n(p, &p.wk_a, (size_t)p.C * ny * Gx));
+    PP_TRY(alloc_n(p, &p.wk_b, (size_t)p.C * Gy * Gx));
+    PP_TRY(alloc_n(p, &p.wk_c, (size_t)p.C * Gy * Gx));
+    p.nksp = (int64_t)p.C * K;
+    return PP_OK;
+}
+
+static pp_status power_iteration(Plan& p, uint64_t seed, int iters, cudaStream_t st) {
+    const int64_t n = p.nimg;
+    PP_TRY(launch_start_vector(p.v, n, seed, st));
+    PP_TRY(launch_norm2(p.v, n, p.red, p.red_blocks, p.scal + 2, st));
+    PP_TRY(launch_scale_by_rnorm(p.v, p.v, n, p.scal + 2, 1.0, 1, st));
+    for (int it = 0; it < iters; ++it) {
+        PP_TRY(normal_into(p, p.v, p.t, 1.f, nullptr, 0.f, st));
+        PP_TRY(launch_dot(p.v, p.t, n, p.red, p.red_blocks, p.scal + 1, p.scal + 2, st));
+        PP_TRY(launch_scale_by_rnorm(p.t, p.v, n, p.scal + 2, 1.0, 1, st));
+    }
+    double L = 0.0;
+    PP_TRY_CUDA(cudaMemcpyAsync(&L, p.scal + 1, sizeof(double), cudaMemcpyDeviceToHost, st));
+    PP_TRY_CUDA(cudaStreamSynchronize(st));
+    if (!(L > 0.0) || !isfinite(L)) {
+        set_error("power iteration gave a non-positive or non-finite norm estimate (%g)", L);
+        return PP_ERR_NONFINITE;
+    }
+    p.L = L;
+    return PP_OK;
+}
+
+static bool fft_len_ok(int n) {
+    FftDesc d;
+    return factorize(n, d);
+}
+
+// ---------------------------------------------------------------------------
+// Horner recursion (Listing "pcode"): u = c_d v; u = c_i v + N_hat u.
+// The first step folds c_d into the apply: u = c_{d-1} v + (c_d/L) N v.
+// Writes the result into `out`; bufA/bufB are scratch images.
+// ---------------------------------------------------------------------------
+static pp_status horner_into(const Plan& p, const double* c, int d, const float2* v, float2* out,
+                             float2* bufA, float2* bufB, cudaStream_t st) {
+    const float invL = (float)(1.0 / p.L);
+    if (d == 0) return launch_axpby(v, (float)c[0], nullptr, 0.f, out, p.nimg, st);
+    const float2* cur = v;
+    float scale = (float)(c[d] / p.L);
+    for (int i = d - 1; i >= 0; --i) {
+        float2* dst = (i == 0) ? out : ((cur == bufA) ? bufB : bufA);
+        PP_TRY(normal_into(p, cur, dst, scale, v, (float)c[i], st));
+        cur = dst;
+        scale = invL;
+    }
+    return PP_OK;
+}
+
+static pp_status fista_iterations(Plan& p, float lambda, int iters, const double* c, int d,
+                                  int levels, bool hist, cudaStream_t st) {
+    const float invL = (float)(1.0 / p.L);
+    for (int k = 0; k < iters; ++k) {
+        // g = N_hat z - A_hat^H b_hat
+        PP_TRY(normal_into(p, p.z, p.g, invL, p.ahb, -1.f, st));
+        const float2* u = p.g;
+        float gamma = 1.f;
+        if (c && d >= 1) {
+            PP_TRY(horner_into(p, c, d, p.g, p.u, p.t, p.w3, st));
+            u = p.u;
+        } else if (c) {
+            gamma = (float)c[0];
+        }
+        const float beta = (float)((double)k / (k + 3.0));
+        PP_TRY(launch_prox_fista(p, levels, lambda, gamma, beta, u, hist ? p.hist + 2 * k : nullptr, st));
+    }
+    return PP_OK;
+}
+
+}  // namespace pp
+
+// ===========================================================================
+// extern "C" entry points
+// ===========================================================================
+using namespace pp;
+
+struct pp_plan {
+    Plan impl;
+};
+
+extern "C" {
+
+const char* pp_last_error(void) { return g_last_error.c_str(); }
+
+pp_status pp_poly_coeffs_l2(int d, double* c) {
+    if (!c || d < 0 || d > 8) {
+        set_error("pp_poly_coeffs_l2: need 0 <= d <= 8 and c != NULL");
+        return PP_ERR_INVALID_ARG;
+    }
+    // r(z) = 1 - z p(z) is the degree-(d+1) polynomial with r(0) = 1 of least
+    // L2([0,1]) norm.  With the orthonormal shifted Legendre polynomials
+    // Q_j(z) = sqrt(2j+1) P_j(2z-1) this is the normalised Christoffel-Darboux
+    // kernel r(z) = sum_j Q_j(0) Q_j(z) / sum_j Q_j(0)^2, j = 0..m, m = d+1.
+    // Since P_j(2z-1) = sum_k (-1)^(j+k) C(j,k) C(j+k,k) z^k and Q_j(0)^2 = 2j+1,
+    //   [z^k] r = (-1)^k sum_{j=k..m} (2j+1) C(j,k) C(j+k,k) / (m+1)^2,
+    // an exact integer ratio; c_i = -[z^(i+1)] r.
+    const int m = d + 1;
+    auto binom = [](int a, int b) {
+        long long r = 1;
+        for (int t = 1; t <= b; ++t) r = r * (a - b + t) / t;
+        return r;
+    };
+    const double den = (double)((m + 1) * (m + 1));
+    for (int i = 0; i <= d; ++i) {
+        const int k = i + 1;
+        long long S = 0;
+        for (int j = k; j <= m; ++j) S += (long long)(2 * j + 1) * binom(j, k) * binom(j + k, k);
+        c[i] = ((k + 1) % 2 == 0 ? 1.0 : -1.0) * (double)S / den;
+    }
+    return PP_OK;
+}
+
+pp_status pp_plan_create(pp_plan** out, pp_dims dims, int coils, const pp_c64* sens,
+                         const pp_sampling* s, uint64_t seed, int power_iters, pp_stream stream) {
+    if (!out) {
+        set_error("pp_plan_create: out is NULL");
+        return PP_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    if (!sens || !s) {
+        set_error("pp_plan_create: sens and sampling must be non-NULL");
+        return PP_ERR_INVALID_ARG;
+    }
+    if (dims.ndim != 2 && dims.ndim != 3) {
+        set_error("pp_plan_create: ndim must be 2 or 3");
+        return PP_ERR_UNSUPPORTED;
+    }
+    const int nx = dims.n[0], ny = dims.n[1], nz = dims.ndim == 3 ? dims.n[2] : 1;
+    if (nx < 4 || ny < 4 || nz < 1 || (dims.ndim == 3 && nz < 4) || nx > 512 || ny > 512 ||
+        nz > 512) {
+        set_error("pp_plan_create: image size out of range (4..512 per axis)");
+        return PP_ERR_INVALID_ARG;
+    }
+    if ((nx % 4) || (ny % 4) || (dims.ndim == 3 && (nz % 4))) {
+        set_error("pp_plan_create: every image axis must be a multiple of 4");
+        return PP_ERR_UNSUPPORTED;
+    }
+    if (coils < 1 || coils > 64) {
+        set_error("pp_plan_create: coils must be in 1..64");
+        return PP_ERR_INVALID_ARG;
+    }
+    if (power_iters < 0 || power_iters > 100000) {
+        set_error("pp_plan_create: power_iters out of range");
+        return PP_ERR_INVALID_ARG;
+    }
+    if (s->kind == PP_CARTESIAN) {
+        if (!s->mask) {
+            set_error("pp_plan_create: Cartesian sampling needs a mask");
+            return PP_ERR_INVALID_ARG;
+        }
+        if (!fft_len_ok(nx) || !fft_len_ok(ny) || (dims.ndim == 3 && !fft_len_ok(nz))) {
+            set_error("pp_plan_create: FFT lengths need prime factors <= 5");
+            return PP_ERR_UNSUPPORTED;
+        }
+    } else if (s->kind == PP_NONCARTESIAN) {
+        if (!s->traj) {
+            set_error("pp_plan_create: non-Cartesian sampling needs a trajectory");
+            return PP_ERR_INVALID_ARG;
+        }
+        if (dims.ndim != 2) {
+            set_error("pp_plan_create: non-Cartesian plans are 2-D only");
+            return PP_ERR_UNSUPPORTED;
+        }
+    } else {
+        set_error("pp_plan_create: unknown sampling kind %d", s->kind);
+        return PP_ERR_INVALID_ARG;
+    }
+    static std::once_flag once;
+    static pp_status cfg = PP_OK;
+    std::call_once(once, [] { cfg = configure_kernels(); });
+    if (cfg != PP_OK) return cfg;
+
+    pp_plan* h = new pp_plan();
+    Plan& p = h->impl;
+    p.ndim = dims.ndim; p.nx = nx; p.ny = ny; p.nz = nz; p.C = coils; p.kind = s->kind;
+    p.nimg = (int64_t)nx * ny * nz;
+    p.sens = reinterpret_cast<const float2*>(sens);
+    cudaGetDevice(&p.dev);
+    cudaStream_t st = (cudaStream_t)stream;
+    pp_status rc = (s->kind == PP_CARTESIAN) ? build_cartesian(p, s->mask) : build_noncartesian(p, s);
+    if (rc == PP_OK) {
+        const size_t n = (size_t)p.nimg;
+        p.red_blocks = 2 * 152;
+        if ((rc = alloc_n(p, &p.z, n)) == PP_OK && (rc = alloc_n(p, &p.y, n)) == PP_OK &&
+            (rc = alloc_n(p, &p.g, n)) == PP_OK && (rc = alloc_n(p, &p.u, n)) == PP_OK &&
+            (rc = alloc_n(p, &p.t, n)) == PP_OK && (rc = alloc_n(p, &p.ahb, n)) == PP_OK &&
+            (rc = alloc_n(p, &p.v, n)) == PP_OK && (rc = alloc_n(p, &p.w3, n)) == PP_OK &&
+            (rc = alloc_n(p, &p.red, (size_t)3 * p.red_blocks)) == PP_OK &&
+            (rc = alloc_n(p, &p.scal, 8)) == PP_OK) {
+            cudaError_t e = cudaStreamCreateWithFlags(&p.cap_stream, cudaStreamNonBlocking);
+            if (e != cudaSuccess) rc = cuda_status(e, "cudaStreamCreate");
+        }
+    }
+    if (rc == PP_OK && power_iters > 0) rc = power_iteration(p, seed, power_iters, st);
+    if (rc != PP_OK) {
+        cudaStreamSynchronize(st);
+        for (void* a : p.allocs) cudaFree(a);
+        if (p.cap_stream) cudaStreamDestroy(p.cap_stream);
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return PP_OK;
+}
+
+pp_status pp_plan_destroy(pp_plan* plan) {
+    if (!plan) return PP_OK;
+    Plan& p = plan->impl;
+    if (p.gexec) cudaGraphExecDestroy(p.gexec);
+    if (p.cap_stream) cudaStreamDestroy(p.cap_stream);
+    for (void* a : p.allocs) cudaFree(a);
+    delete plan;
+    return PP_OK;
+}
+
+pp_status pp_plan_scale(const pp_plan* plan, double* L) {
+    if (!plan || !L) {
+        set_error("pp_plan_scale: NULL argument");
+        return PP_ERR_INVALID_ARG;
+    }
+    *L = plan->impl.L;
+    return PP_OK;
+}
+
+pp_status pp_plan_set_scale(pp_plan* plan, double L) {
+    if (!plan || !(L > 0.0) || !isfinite(L)) {
+        set_error("pp_plan_set_scale: need a plan and a finite L > 0");
+        return PP_ERR_INVALID_ARG;
+    }
+    if (plan->impl.L != L) {
+        plan->impl.L = L;
+        plan->impl.gkey.clear();   // captured graphs bake 1/L into their kernels
+    }
+    return PP_OK;
+}
+
+pp_status pp_plan_sizes(const pp_plan* plan, int64_t* image_elems, int64_t* kspace_elems) {
+    if (!plan) {
+        set_error("pp_plan_sizes: NULL plan");
+        return PP_ERR_INVALID_ARG;
+    }
+    if (image_elems) *image_elems = plan->impl.nimg;
+    if (kspace_elems) *kspace_elems = plan->impl.nksp;
+    return PP_OK;
+}
+
+pp_status pp_forward_apply(const pp_plan* plan, const pp_c64* x, pp_c64* y, pp_stream stream) {
+    if (!plan || !x || !y) {
+        set_error("pp_forward_apply: NULL argument");
+        return PP_ERR_INVALID_ARG;
+    }
+    return forward_into(plan->impl, reinterpret_cast<const float2*>(x), reinterpret_cast<float2*>(y),
+                        (cudaStream_t)stream);
+}
+
+pp_status pp_adjoint_apply(const pp_plan* plan, const pp_c64* y, pp_c64* x, pp_stream stream) {
+    if (!plan || !x || !y) {
+        set_error("pp_adjoint_apply: NULL argument");
+        return PP_ERR_INVALID_ARG;
+    }
+    return adjoint_into(plan->impl, reinterpret_cast<const float2*>(y), reinterpret_cast<float2*>(x),
+                        (cudaStream_t)stream);
+}
+
+pp_status pp_normal_apply(const pp_plan* plan, const pp_c64* x, pp_c64* y, pp_stream stream) {
+    if (!plan || !x || !y || (const void*)x == (const void*)y) {
+        set_error("pp_normal_apply: NULL or aliased argument");
+        return PP_ERR_INVALID_ARG;
+    }
+    const Plan& p = plan->impl;
+    return normal_into(p, reinterpret_cast<const float2*>(x), reinterpret_cast<float2*>(y),
+                       (float)(1.0 / p.L), nullptr, 0.f, (cudaStream_t)stream);
+}
+
+pp_status pp_poly_apply(const pp_plan* plan, const double* c, int d, const pp_c64* v, pp_c64* out,
+                        pp_stream stream) {
+    if (!plan || !c || !v || !out || d < 0 || d > 16 || (const void*)v == (const void*)out) {
+        set_error("pp_poly_apply: bad argument (NULL, aliased, or d outside 0..16)");
+        return PP_ERR_INVALID_ARG;
+    }
+    Plan& p = const_cast<Plan&>(plan->impl);
+    return horner_into(p, c, d, reinterpret_cast<const float2*>(v), reinterpret_cast<float2*>(out),
+                       p.t, p.w3, (cudaStream_t)stream);
+}
+
+pp_status pp_prox_l1_haar(pp_dims dims, int levels, float lambda, const pp_c64* in, pp_c64* out,
+                          pp_stream stream) {
+    if (!in || !out || (dims.ndim != 2 && dims.ndim != 3) || !(lambda >= 0.f) || !isfinite(lambda)) {
+        set_error("pp_prox_l1_haar: bad argument");
+        return PP_ERR_INVALID_ARG;
+    }
+    if (levels < 1 || levels > 2) {
+        set_error("pp_prox_l1_haar: levels must be 1 or 2");
+        return PP_ERR_UNSUPPORTED;
+    }
+    const int ts = 1 << levels;
+    const int nx = dims.n[0], ny = dims.n[1], nz = dims.ndim == 3 ? dims.n[2] : 1;
+    if (nx <= 0 || ny <= 0 || nz <= 0 || nx % ts || ny % ts || (dims.ndim == 3 && nz % ts)) {
+        set_error("pp_prox_l1_haar: every axis must be a positive multiple of 2^levels");
+        return PP_ERR_UNSUPPORTED;
+    }
+    return launch_prox(dims.ndim, nx, ny, nz, levels, lambda, reinterpret_cast<const float2*>(in),
+                       reinterpret_cast<float2*>(out), (cudaStream_t)stream);
+}
+
+pp_status pp_fista_solve(pp_plan* plan, const pp_c64* b, float lambda, int iters, const double* c,
+                         int d, pp_c64* x_out, pp_solve_info* info, pp_stream stream) {
+    if (!plan || !b || !x_out || iters < 0 || iters > 1000000 || !(lambda >= 0.f) ||
+        !isfinite(lambda) || d < 0 || d > 16 || (!c && d != 0)) {
+        set_error("pp_fista_solve: bad argument");
+        return PP_ERR_INVALID_ARG;
+    }
+    Plan& p = plan->impl;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int levels = (info && info->levels) ? info->levels : 2;
+    if (levels < 1 || levels > 2 || p.nx % (1 << levels) || p.ny % (1 << levels) ||
+        (p.ndim == 3 && p.nz % (1 << levels))) {
+        set_error("pp_fista_solve: unsupported Haar levels");
+        return PP_ERR_UNSUPPORTED;
+    }
+    const bool hist = info && info->history;
+    const int64_t n = p.nimg;
+    // A_hat^H b_hat = A^H b / (sqrt(L) ||b||)
+    PP_TRY(launch_norm2(reinterpret_cast<const float2*>(b), p.nksp, p.red, p.red_blocks, p.scal + 0, st));
+    PP_TRY(adjoint_into(p, reinterpret_cast<const float2*>(b), p.ahb, st));
+    PP_TRY(launch_scale_by_rnorm(p.ahb, p.ahb, n, p.scal + 0, 1.0 / sqrt(p.L), 1, st));
+    PP_TRY_CUDA(cudaMemsetAsync(p.y, 0, n * sizeof(float2), st));
+    PP_TRY_CUDA(cudaMemsetAsync(p.z, 0, n * sizeof(float2), st));
+    if (hist) {
+        if (p.hist_cap < iters) {
+            if (p.hist) {
+                cudaStreamSynchronize(st);
+                cudaFree(p.hist);
+                p.allocs.erase(std::remove(p.allocs.begin(), p.allocs.end(), (void*)p.hist), p.allocs.end());
+                p.hist = nullptr;
+            }
+            PP_TRY(alloc_n(p, &p.hist, (size_t)2 * std::max(iters, 1)));
+            p.hist_cap = iters;
+            p.gkey.clear();
+        }
+        PP_TRY_CUDA(cudaMemsetAsync(p.hist, 0, sizeof(double) * 2 * std::max(iters, 1), st));
+    }
+    if (iters > 0) {
+        std::vector<double> key = {(double)iters, (double)d, (double)lambda, (double)levels,
+                                   hist ? 1.0 : 0.0, c ? 1.0 : 0.0, p.L,
+                                   (double)(uintptr_t)p.hist};
+        if (c)
+            for (int i = 0; i <= d; ++i) key.push_back(c[i]);
+        if (!p.gexec || key != p.gkey) {
+            if (p.gexec) {
+                cudaGraphExecDestroy(p.gexec);
+                p.gexec = nullptr;
+            }
+            p.gkey.clear();
+            cudaGraph_t graph = nullptr;
+            PP_TRY_CUDA(cudaStreamBeginCapture(p.cap_stream, cudaStreamCaptureModeThreadLocal));
+            pp_status rc = fista_iterations(p, lambda, iters, c, d, levels, hist, p.cap_stream);
+            cudaError_t e = cudaStreamEndCapture(p.cap_stream, &graph);
+            if (rc != PP_OK) {
+                if (graph) cudaGraphDestroy(graph);
+                return rc;
+            }
+            if (e != cudaSuccess) return cuda_status(e, "cudaStreamEndCapture");
+            e = cudaGraphInstantiate(&p.gexec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) {
+                p.gexec = nullptr;
+                return cuda_status(e, "cudaGraphInstantiate");
+            }
+            p.gkey = key;
+        }
+        PP_TRY_CUDA(cudaGraphLaunch(p.gexec, st));
+    }
+    float2* xo = reinterpret_cast<float2*>(x_out);
+    if (info && info->rescale)
+        PP_TRY(launch_scale_by_rnorm(p.y, xo, n, p.scal + 0, 1.0 / sqrt(p.L), 0, st));
+    else
+        PP_TRY_CUDA(cudaMemcpyAsync(xo, p.y, n * sizeof(float2), cudaMemcpyDeviceToDevice, st));
+    if (info) {
+        info->L = p.L;
+        if (hist) {
+            double bn2 = 0.0;
+            PP_TRY_CUDA(cudaMemcpyAsync(&bn2, p.scal + 0, sizeof(double), cudaMemcpyDeviceToHost, st));
+            PP_TRY_CUDA(cudaMemcpyAsync(info->history, p.hist, sizeof(double) * 2 * iters,
+                                        cudaMemcpyDeviceToHost, st));
+            PP_TRY_CUDA(cudaStreamSynchronize(st));
+            info->bnorm = sqrt(bn2);
+        }
+    }
+    return PP_OK;
+}
+
+}  // extern "C"

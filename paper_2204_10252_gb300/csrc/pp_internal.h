@@ -1,0 +1,161 @@
+// Internal declarations shared by the libpp translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "pp.h"
+#include "pp_fft.cuh"
+
+namespace pp {
+
+void set_error(const char* fmt, ...);
+pp_status cuda_status(cudaError_t e, const char* what);
+
+#define PP_TRY_CUDA(call)                                         \
+    do {                                                          \
+        cudaError_t _e = (call);                                  \
+        if (_e != cudaSuccess) return ::pp::cuda_status(_e, #call); \
+    } while (0)
+#define PP_TRY(call)                          \
+    do {                                      \
+        pp_status _s = (call);                \
+        if (_s != PP_OK) return _s;           \
+    } while (0)
+
+constexpr int kThreads = 256;
+
+// Device FFT: stage plan plus the table w^t = exp(-2 pi i t / n), t < n.
+struct DevFft {
+    FftDesc d;
+    float2* tw = nullptr;
+};
+
+// One (tile, sample) pair of the gridding tile lists.  Taps of the sample are
+// at halo rows ly0 .. ly0+W-1 and columns lx0 .. lx0+W-1, where halo row 0
+// is grid row ty0 - H (H = W-1 the halo width) of the tile starting at ty0.
+struct TileEntry {
+    float4 wx;   // x-tap weights a = 0..3 (unused taps are 0)
+    float4 wy;   // y-tap weights
+    int lyx;     // ly0 | (lx0 << 16)
+    int k;       // sample index (trajectory order)
+};
+
+// Per-sample gridding metadata in trajectory order.
+struct SampleTaps {
+    float4 wx;
+    float4 wy;
+    int iy0, ix0;   // first tap's grid index (unwrapped; wrap mod G)
+};
+
+// Row stage: per row, FFT along the contiguous axis between an image row of
+// length n and a k-space row of length G, with circular placement
+// pos = (i - off) mod G.
+struct RowArgs {
+    int n;          // image row length
+    int G;          // transform length (>= n)
+    int off_in;     // input index i -> transform position (i - off_in) mod G
+    int off_out;    // output index q <- transform position (q - off_out) mod G
+    int nrows;      // rows per coil
+    int64_t coil_img_stride;   // elements between coils in the sensitivity array (0 = none)
+    float scale;
+};
+
+struct ColArgs {
+    int Hin, Hout, G;
+    int off_in, off_out;
+    int ncols;                  // columns (contiguous axis length)
+    int64_t in_batch_stride;    // elements between batches (coils) in src
+    int64_t out_batch_stride;
+    int nbatch;
+    float scale;
+    const float* mul_in;        // input multiplier: mul_in[r * mi_q + (col / mi_cdiv) * mi_c]
+    int mi_q, mi_c, mi_cdiv;
+    const float* mul_out;       // mask value for output row q and column col:
+                                // mul_out[q * mo_q + (col / mo_cdiv) * mo_c]
+    int mo_q, mo_c, mo_cdiv;
+};
+
+struct Plan {
+    int ndim = 2, nx = 0, ny = 0, nz = 1, C = 0, kind = PP_CARTESIAN;
+    int64_t nimg = 0, nksp = 0;
+    const float2* sens = nullptr;
+    double L = 1.0;
+    int dev = 0;
+
+    // FFTs
+    DevFft fx, fy, fz, gx, gy;
+
+    // Cartesian masks: centred order (forward/adjoint) and FFT order with the
+    // 1/n normalisation folded in (normal operator round trip).
+    float* mask_c = nullptr;    // 2-D: [ny]; 3-D: [nz][ny]
+    float* mask_fo = nullptr;   // same shape, FFT order, times 1/(ny nz)
+
+    // Non-Cartesian
+    int G_x = 0, G_y = 0, W = 0, K = 0, T = 32, ntx = 0, nty = 0;
+    float* deapod_x = nullptr;   // [nx] 1/(sqrt(nx) psi_x)
+    float* deapod_y = nullptr;   // [ny]
+    TileEntry* tiles = nullptr;
+    int* tile_start = nullptr;   // [ntiles + 1]
+    int max_tile_len = 0;
+    SampleTaps* samp = nullptr;  // [K]
+
+    // Workspace
+    float2* wk_a = nullptr;   // C * ny * G_x (rows) or C * n (Cartesian)
+    float2* wk_b = nullptr;   // C * G_y * G_x (grid)
+    float2* wk_c = nullptr;   // C * G_y * G_x (grid)
+    float2 *z = nullptr, *y = nullptr, *g = nullptr, *u = nullptr, *t = nullptr, *ahb = nullptr,
+           *v = nullptr, *w3 = nullptr;
+    double* red = nullptr;    // reduction partials
+    double* scal = nullptr;   // device scalars: [0] |b|^2, [1] rayleigh, [2] |w|^2, [3..] history
+    int red_blocks = 0;
+    int hist_cap = 0;
+    double* hist = nullptr;   // [hist_cap][2]
+
+    // Graph cache for the solve loop
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<double> gkey;
+
+    std::vector<void*> allocs;
+};
+
+// ---- launchers (pp_kernels.cu) -------------------------------------------
+pp_status configure_kernels();
+pp_status launch_rows_fwd(const Plan& p, const DevFft& f, const RowArgs& a, const float2* x,
+                          const float2* sens, const float* wrow, const float* wcol, float2* out,
+                          int ncoils, int64_t img_batch_stride, cudaStream_t st);
+pp_status launch_rows_adj(const Plan& p, const DevFft& f, const RowArgs& a, const float2* src,
+                          const float2* sens, const float* wrow, const float* wcol, float2* out,
+                          const float2* operand, float alpha, int ncoils, cudaStream_t st);
+pp_status launch_cols(const DevFft& f, const ColArgs& a, const float2* src, float2* dst, bool inv,
+                      cudaStream_t st);
+pp_status launch_cols_roundtrip(const DevFft& f, const ColArgs& a, const float* mask_fo,
+                                const float2* src, float2* dst, cudaStream_t st);
+pp_status launch_cart2d_normal(const Plan& p, const float2* x, float2* out, float scale,
+                               const float2* operand, float alpha, cudaStream_t st);
+pp_status launch_expand(const float2* x, const float2* s, float2* out, int64_t n, cudaStream_t st);
+pp_status launch_conj_accum(const float2* s, const float2* wv, float2* out, int64_t n, int first,
+                            float scale, const float2* operand, float alpha, int last,
+                            cudaStream_t st);
+pp_status launch_nufft_tile_normal(const Plan& p, const float2* grid_in, float2* grid_out,
+                                   cudaStream_t st);
+pp_status launch_nufft_spread(const Plan& p, const float2* ksp, float2* grid_out, cudaStream_t st);
+pp_status launch_nufft_degrid(const Plan& p, const float2* grid_in, float2* ksp, cudaStream_t st);
+pp_status launch_prox(int ndim, int nx, int ny, int nz, int levels, float lambda,
+                      const float2* in, float2* out, cudaStream_t st);
+pp_status launch_prox_fista(const Plan& p, int levels, float lambda, float gamma, float beta,
+                            const float2* u, double* hist_slot, cudaStream_t st);
+pp_status launch_dot(const float2* a, const float2* b, int64_t n, double* partials, int nblocks,
+                     double* out_re, double* out_norm_b, cudaStream_t st);
+pp_status launch_norm2(const float2* a, int64_t n, double* partials, int nblocks, double* out,
+                       cudaStream_t st);
+pp_status launch_scale_by_rnorm(const float2* in, float2* out, int64_t n, const double* norm2,
+                                double factor, int invert, cudaStream_t st);
+pp_status launch_axpby(const float2* x, float a, const float2* y, float b, float2* out, int64_t n,
+                       cudaStream_t st);
+pp_status launch_start_vector(float2* v, int64_t n, uint64_t seed, cudaStream_t st);
+
+}  // namespace pp

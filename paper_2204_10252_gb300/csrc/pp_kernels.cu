@@ -1,0 +1,952 @@
+// CUDA kernels of the SENSE operators (Sec. 5.1 Cartesian, Sec. 5.2
+// non-Cartesian with Kaiser-Bessel gridding) and of the solver's elementwise
+// and reduction steps (Algorithm "pfista", Sec. 3.1).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pp_internal.h"
+
+namespace pp {
+
+namespace {
+
+constexpr int RB = 8;        // rows per CTA in the row stages
+constexpr int LGRB = 3;
+constexpr int TX = 8;        // columns per CTA in the column stages
+constexpr int LGTX = 3;
+constexpr int KMAX = 16;     // owned elements per thread (rows: RB*n/256, n <= 512)
+
+__device__ __forceinline__ int wrapG(int a, int G) {
+    a %= G;
+    return a < 0 ? a + G : a;
+}
+
+__device__ __forceinline__ void load_table(float2* dst, const float2* __restrict__ src, int n) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+}
+
+__host__ __device__ __forceinline__ int row_stride(int G) { return G + 2; }
+
+// ---------------------------------------------------------------------------
+// Row stage, image -> k rows.  CTA (bx, by): rows bx*RB .. +RB of batch by.
+//   v(i) = scale * wrow[r] * wcol[i] * x_by[r][i] * S_by[r][i]
+//   transform position (i - off_in) mod G, FFT of length G,
+//   out_by[r][q] = V((q - off_out) mod G).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads)
+rows_fwd_kernel(FftDesc fd, const float2* __restrict__ tw, RowArgs a,
+                const float2* __restrict__ x, int64_t x_batch_stride,
+                const float2* __restrict__ sens, const float* __restrict__ wrow,
+                const float* __restrict__ wcol, float2* __restrict__ out) {
+    extern __shared__ float2 sm[];
+    const int G = a.G, n = a.n, bs = row_stride(G);
+    float2* tws = sm;
+    float2* b0 = sm + G;
+    float2* b1 = b0 + RB * bs;
+    load_table(tws, tw, G);
+    const int c = blockIdx.y;
+    const int row0 = blockIdx.x * RB;
+    const float2* xc = x + (int64_t)c * x_batch_stride;
+    const float2* sc = sens ? sens + (int64_t)c * a.coil_img_stride : nullptr;
+    for (int idx = threadIdx.x; idx < RB * G; idx += blockDim.x) {
+        const int b = idx / G;
+        const int p = idx - b * G;
+        const int r = row0 + b;
+        int i = p + a.off_in;
+        if (i >= G) i -= G;
+        float2 v = make_float2(0.f, 0.f);
+        if (r < a.nrows && i < n) {
+            const int64_t o = (int64_t)r * n + i;
+            v = xc[o];
+            if (sc) v = cmul(v, sc[o]);
+            float w = a.scale;
+            if (wrow) w *= wrow[r];
+            if (wcol) w *= wcol[i];
+            v = cscale(v, w);
+        }
+        b0[p + b * bs] = v;
+    }
+    __syncthreads();
+    float2* res = fft_batch<false>(b0, b1, fd, 1, bs, LGRB, tws, nullptr);
+    float2* oc = out + (int64_t)c * a.nrows * G;
+    for (int idx = threadIdx.x; idx < RB * G; idx += blockDim.x) {
+        const int b = idx / G;
+        const int q = idx - b * G;
+        const int r = row0 + b;
+        if (r < a.nrows) {
+            int p = q - a.off_out;
+            if (p < 0) p += G;
+            oc[(int64_t)r * G + q] = res[p + b * bs];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Row stage, k rows -> image, with the conjugate-coil reduction and an axpy
+// epilogue:  out[r][i] = scale * sum_c conj(S_c[r][i]) wrow[r] wcol[i]
+//                        * IFFT(src_c[r])((i - off_out) mod G)
+//                        + alpha * operand[r][i].
+// src_c[r][s] sits at transform position (s - off_in) mod G.
+// ---------------------------------------------------------------------------
+template <int KM>
+__global__ void __launch_bounds__(kThreads)
+rows_adj_kernel(FftDesc fd, const float2* __restrict__ tw, RowArgs a,
+                const float2* __restrict__ src, const float2* __restrict__ sens,
+                const float* __restrict__ wrow, const float* __restrict__ wcol,
+                float2* out, const float2* operand, float alpha, int ncoils) {
+    extern __shared__ float2 sm[];
+    const int G = a.G, n = a.n, bs = row_stride(G);
+    float2* tws = sm;
+    float2* b0 = sm + G;
+    float2* b1 = b0 + RB * bs;
+    load_table(tws, tw, G);
+    const int row0 = blockIdx.x * RB;
+    float2 acc[KM];
+#pragma unroll
+    for (int k = 0; k < KM; ++k) acc[k] = make_float2(0.f, 0.f);
+    for (int c = 0; c < ncoils; ++c) {
+        const float2* scn = src + (int64_t)c * a.nrows * G;
+        for (int idx = threadIdx.x; idx < RB * G; idx += blockDim.x) {
+            const int b = idx / G;
+            const int p = idx - b * G;
+            const int r = row0 + b;
+            int s = p + a.off_in;
+            if (s >= G) s -= G;
+            b0[p + b * bs] = (r < a.nrows) ? scn[(int64_t)r * G + s] : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        float2* res = fft_batch<true>(b0, b1, fd, 1, bs, LGRB, tws, nullptr);
+        const float2* sc = sens ? sens + (int64_t)c * a.coil_img_stride : nullptr;
+#pragma unroll
+        for (int k = 0; k < KM; ++k) {
+            const int e = threadIdx.x + k * kThreads;
+            if (e < RB * n) {
+                const int b = e / n;
+                const int i = e - b * n;
+                const int r = row0 + b;
+                if (r < a.nrows) {
+                    int p = i - a.off_out;
+                    if (p < 0) p += G;
+                    float2 v = res[p + b * bs];
+                    float w = 1.f;
+                    if (wrow) w *= wrow[r];
+                    if (wcol) w *= wcol[i];
+                    v = cscale(v, w);
+                    if (sc) v = cmulc(sc[(int64_t)r * n + i], v);
+                    acc[k] = cadd(acc[k], v);
+                }
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int k = 0; k < KM; ++k) {
+        const int e = threadIdx.x + k * kThreads;
+        if (e < RB * n) {
+            const int b = e / n;
+            const int i = e - b * n;
+            const int r = row0 + b;
+            if (r < a.nrows) {
+                const int64_t o = (int64_t)r * n + i;
+                float2 v = cscale(acc[k], a.scale);
+                if (operand) v = cadd(v, cscale(operand[o], alpha));
+                out[o] = v;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Column stage: FFT along the strided axis for TX adjacent columns of one
+// batch.  Input row r -> position (r - off_in) mod G (rows >= Hin are zero);
+// output row q <- position (q - off_out) mod G, q < Hout.
+// ---------------------------------------------------------------------------
+template <bool INV>
+__global__ void __launch_bounds__(kThreads)
+cols_kernel(FftDesc fd, const float2* __restrict__ tw, ColArgs a, const float2* src, float2* dst) {
+    // src == dst is allowed: a CTA reads all of its columns before writing them.
+    extern __shared__ float2 sm[];
+    const int G = a.G;
+    float2* tws = sm;
+    float2* b0 = sm + G;
+    float2* b1 = b0 + G * TX;
+    load_table(tws, tw, G);
+    const int col0 = blockIdx.x * TX;
+    const float2* sb = src + (int64_t)blockIdx.y * a.in_batch_stride;
+    float2* db = dst + (int64_t)blockIdx.y * a.out_batch_stride;
+    for (int idx = threadIdx.x; idx < G * TX; idx += blockDim.x) {
+        const int p = idx >> LGTX;
+        const int b = idx & (TX - 1);
+        int r = p + a.off_in;
+        if (r >= G) r -= G;
+        const int col = col0 + b;
+        float2 v = make_float2(0.f, 0.f);
+        if (r < a.Hin && col < a.ncols) {
+            v = sb[(int64_t)r * a.ncols + col];
+            if (a.mul_in) v = cscale(v, a.mul_in[r * a.mi_q + (col / a.mi_cdiv) * a.mi_c]);
+        }
+        b0[idx] = v;
+    }
+    __syncthreads();
+    float2* res = fft_batch<INV>(b0, b1, fd, TX, 1, LGTX, tws, nullptr);
+    for (int idx = threadIdx.x; idx < a.Hout * TX; idx += blockDim.x) {
+        const int q = idx >> LGTX;
+        const int b = idx & (TX - 1);
+        const int col = col0 + b;
+        if (col < a.ncols) {
+            int p = q - a.off_out;
+            p = wrapG(p, G);
+            float s = a.scale;
+            if (a.mul_out) s *= a.mul_out[q * a.mo_q + (col / a.mo_cdiv) * a.mo_c];
+            db[(int64_t)q * a.ncols + col] = cscale(res[(p << LGTX) + b], s);
+        }
+    }
+}
+
+// Column round trip in FFT order: IFFT(mask . FFT(col)), mask value of
+// transform position p for column col: mask_fo[p * mo_q + (col / mo_cdiv) * mo_c]
+// (normalisation folded into the mask).  Used along z by the 3-D operator.
+__global__ void __launch_bounds__(kThreads)
+cols_roundtrip_kernel(FftDesc fd, const float2* __restrict__ tw, ColArgs a,
+                      const float* __restrict__ mask_fo, const float2* __restrict__ src,
+                      float2* __restrict__ dst) {
+    extern __shared__ float2 sm[];
+    const int G = a.G;
+    float2* tws = sm;
+    float2* b0 = sm + G;
+    float2* b1 = b0 + G * TX;
+    load_table(tws, tw, G);
+    const int col0 = blockIdx.x * TX;
+    const float2* sb = src + (int64_t)blockIdx.y * a.in_batch_stride;
+    float2* db = dst + (int64_t)blockIdx.y * a.out_batch_stride;
+    for (int idx = threadIdx.x; idx < G * TX; idx += blockDim.x) {
+        const int p = idx >> LGTX;
+        const int col = col0 + (idx & (TX - 1));
+        b0[idx] = (col < a.ncols) ? sb[(int64_t)p * a.ncols + col] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    float2* r1 = fft_batch<false>(b0, b1, fd, TX, 1, LGTX, tws, nullptr);
+    for (int idx = threadIdx.x; idx < G * TX; idx += blockDim.x) {
+        const int p = idx >> LGTX;
+        const int col = col0 + (idx & (TX - 1));
+        const float m = (col < a.ncols) ? mask_fo[p * a.mo_q + (col / a.mo_cdiv) * a.mo_c] : 0.f;
+        r1[idx] = cscale(r1[idx], m);
+    }
+    __syncthreads();
+    float2* other = (r1 == b0) ? b1 : b0;
+    float2* r2 = fft_batch<true>(r1, other, fd, TX, 1, LGTX, tws, nullptr);
+    for (int idx = threadIdx.x; idx < G * TX; idx += blockDim.x) {
+        const int p = idx >> LGTX;
+        const int col = col0 + (idx & (TX - 1));
+        if (col < a.ncols) db[(int64_t)p * a.ncols + col] = r2[idx];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Fused 2-D Cartesian normal operator for a mask constant along x:
+//   out = scale * sum_c conj(S_c) F_y^H (M_fo/ny) F_y (S_c x) + alpha * operand
+// One CTA owns TX columns and loops over every coil; S_c is read once and
+// kept in registers between the coil expansion and the conjugate product.
+// ---------------------------------------------------------------------------
+template <int KM>
+__global__ void __launch_bounds__(kThreads)
+cart2d_normal_kernel(FftDesc fd, const float2* __restrict__ tw, const float2* __restrict__ x,
+                     const float2* __restrict__ sens, int C, int ny, int nx,
+                     const float* __restrict__ mask_fo, float2* __restrict__ out, float scale,
+                     const float2* __restrict__ operand, float alpha) {
+    extern __shared__ float2 sm[];
+    float2* tws = sm;
+    float2* b0 = sm + ny;
+    float2* b1 = b0 + ny * TX;
+    float* pm = reinterpret_cast<float*>(b1 + ny * TX);
+    load_table(tws, tw, ny);
+    for (int i = threadIdx.x; i < ny; i += blockDim.x) pm[i] = mask_fo[i];
+    const int col0 = blockIdx.x * TX;
+    const int nel = ny * TX;
+    float2 xr[KM], sr[KM], acc[KM];
+#pragma unroll
+    for (int k = 0; k < KM; ++k) {
+        const int e = threadIdx.x + k * kThreads;
+        const int yy = e >> LGTX;
+        const int col = col0 + (e & (TX - 1));
+        xr[k] = (e < nel && col < nx) ? x[(int64_t)yy * nx + col] : make_float2(0.f, 0.f);
+        acc[k] = make_float2(0.f, 0.f);
+    }
+    const int64_t cs = (int64_t)ny * nx;
+    for (int c = 0; c < C; ++c) {
+#pragma unroll
+        for (int k = 0; k < KM; ++k) {
+            const int e = threadIdx.x + k * kThreads;
+            if (e < nel) {
+                const int yy = e >> LGTX;
+                const int col = col0 + (e & (TX - 1));
+                sr[k] = (col < nx) ? sens[c * cs + (int64_t)yy * nx + col] : make_float2(0.f, 0.f);
+                b0[e] = cmul(sr[k], xr[k]);
+            }
+        }
+        __syncthreads();
+        float2* r1 = fft_batch<false>(b0, b1, fd, TX, 1, LGTX, tws, nullptr);
+        float2* other = (r1 == b0) ? b1 : b0;
+        float2* r2 = fft_batch<true>(r1, other, fd, TX, 1, LGTX, tws, pm);
+#pragma unroll
+        for (int k = 0; k < KM; ++k) {
+            const int e = threadIdx.x + k * kThreads;
+            if (e < nel) acc[k] = cadd(acc[k], cmulc(sr[k], r2[e]));
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int k = 0; k < KM; ++k) {
+        const int e = threadIdx.x + k * kThreads;
+        const int yy = e >> LGTX;
+        const int col = col0 + (e & (TX - 1));
+        if (e < nel && col < nx) {
+            const int64_t o = (int64_t)yy * nx + col;
+            float2 v = cscale(acc[k], scale);
+            if (operand) v = cadd(v, cscale(operand[o], alpha));
+            out[o] = v;
+        }
+    }
+}
+
+__global__ void expand_kernel(const float2* __restrict__ x, const float2* __restrict__ s,
+                              float2* __restrict__ out, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = cmul(s[i], x[i]);
+}
+
+// out (+)= conj(s) * w; on the last coil out = scale * out + alpha * operand.
+__global__ void conj_accum_kernel(const float2* __restrict__ s, const float2* __restrict__ wv,
+                                  float2* __restrict__ out, int64_t n, int first, float scale,
+                                  const float2* __restrict__ operand, float alpha, int last) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        float2 v = cmulc(s[i], wv[i]);
+        if (!first) v = cadd(v, out[i]);
+        if (last) {
+            v = cscale(v, scale);
+            if (operand) v = cadd(v, cscale(operand[i], alpha));
+        }
+        out[i] = v;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Kaiser-Bessel gridding on tiles of the oversampled grid (FFT order).
+// A CTA owns one T x T output tile and a chunk of coils.  For each coil it
+// stages the (T+2H) x (T+2H) halo of the input grid (H = W-1) in shared
+// memory, interpolates every sample whose W x W footprint meets the tile
+// (degridding, G^T), and spreads the value back onto the taps that fall in
+// the tile (gridding, G) with shared-memory atomics.  No global atomics.
+// ---------------------------------------------------------------------------
+template <int W, bool DEGRID>
+__global__ void __launch_bounds__(kThreads)
+nufft_tile_kernel(const TileEntry* __restrict__ entries, const int* __restrict__ tile_start,
+                  int T, int ntx, int Gx, int Gy, int C, int coils_per_cta,
+                  const float2* __restrict__ grid_in, const float2* __restrict__ ksp, int K,
+                  float2* __restrict__ grid_out) {
+    extern __shared__ float2 sm[];
+    constexpr int H = W - 1;
+    const int HW = T + 2 * H;
+    float2* halo = sm;
+    float* acc = reinterpret_cast<float*>(DEGRID ? sm + HW * HW : sm);
+    const int tile = blockIdx.x;
+    const int tyi = tile / ntx, txi = tile - tyi * ntx;
+    const int ty0 = tyi * T, tx0 = txi * T;
+    const int th = min(T, Gy - ty0), tw_ = min(T, Gx - tx0);
+    const int e0 = tile_start[tile], e1 = tile_start[tile + 1];
+    const int64_t gsz = (int64_t)Gx * Gy;
+    const int c0 = blockIdx.y * coils_per_cta;
+    const int c1 = min(C, c0 + coils_per_cta);
+    for (int c = c0; c < c1; ++c) {
+        if (DEGRID) {
+            const float2* gin = grid_in + c * gsz;
+            for (int idx = threadIdx.x; idx < HW * HW; idx += blockDim.x) {
+                const int hy = idx / HW, hx = idx - hy * HW;
+                const int gy = wrapG(ty0 - H + hy, Gy), gx = wrapG(tx0 - H + hx, Gx);
+                halo[idx] = gin[(int64_t)gy * Gx + gx];
+            }
+        }
+        for (int idx = threadIdx.x; idx < 2 * T * T; idx += blockDim.x) acc[idx] = 0.f;
+        __syncthreads();
+        for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+            const TileEntry te = entries[e];
+            const float wx[4] = {te.wx.x, te.wx.y, te.wx.z, te.wx.w};
+            const float wy[4] = {te.wy.x, te.wy.y, te.wy.z, te.wy.w};
+            const int ly0 = te.lyx & 0xffff, lx0 = te.lyx >> 16;
+            float2 v;
+            if (DEGRID) {
+                v = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int b = 0; b < W; ++b) {
+                    float2 rs = make_float2(0.f, 0.f);
+                    const float2* hrow = halo + (ly0 + b) * HW + lx0;
+#pragma unroll
+                    for (int a = 0; a < W; ++a) {
+                        const float2 hv = hrow[a];
+                        rs.x += wx[a] * hv.x;
+                        rs.y += wx[a] * hv.y;
+                    }
+                    v.x += wy[b] * rs.x;
+                    v.y += wy[b] * rs.y;
+                }
+            } else {
+                v = ksp[(int64_t)c * K + te.k];
+            }
+#pragma unroll
+            for (int b = 0; b < W; ++b) {
+                const int yy = ly0 + b - H;
+                if (yy < 0 || yy >= th) continue;
+                const float vyx = wy[b] * v.x, vyy = wy[b] * v.y;
+#pragma unroll
+                for (int a = 0; a < W; ++a) {
+                    const int xx = lx0 + a - H;
+                    if (xx < 0 || xx >= tw_) continue;
+                    atomicAdd(&acc[2 * (yy * T + xx)], wx[a] * vyx);
+                    atomicAdd(&acc[2 * (yy * T + xx) + 1], wx[a] * vyy);
+                }
+            }
+        }
+        __syncthreads();
+        float2* gout = grid_out + c * gsz;
+        for (int idx = threadIdx.x; idx < th * T; idx += blockDim.x) {
+            const int yy = idx / T, xx = idx - yy * T;
+            if (xx < tw_)
+                gout[(int64_t)(ty0 + yy) * Gx + tx0 + xx] =
+                    make_float2(acc[2 * idx], acc[2 * idx + 1]);
+        }
+        __syncthreads();
+    }
+}
+
+// Degridding in trajectory order: ksp[c][k] = sum_ab wy_b wx_a grid_c[iy0+b][ix0+a].
+template <int W>
+__global__ void nufft_degrid_kernel(const SampleTaps* __restrict__ st, int K, int Gx, int Gy,
+                                    const float2* __restrict__ grid, float2* __restrict__ ksp) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = blockIdx.y;
+    if (k >= K) return;
+    const SampleTaps s = st[k];
+    const float wx[4] = {s.wx.x, s.wx.y, s.wx.z, s.wx.w};
+    const float wy[4] = {s.wy.x, s.wy.y, s.wy.z, s.wy.w};
+    const float2* gc = grid + (int64_t)c * Gx * Gy;
+    float2 v = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int b = 0; b < W; ++b) {
+        const int gy = wrapG(s.iy0 + b, Gy);
+        float2 rs = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int a = 0; a < W; ++a) {
+            const int gx = wrapG(s.ix0 + a, Gx);
+            const float2 g = gc[(int64_t)gy * Gx + gx];
+            rs.x += wx[a] * g.x;
+            rs.y += wx[a] * g.y;
+        }
+        v.x += wy[b] * rs.x;
+        v.y += wy[b] * rs.y;
+    }
+    ksp[(int64_t)c * K + k] = v;
+}
+
+// ---------------------------------------------------------------------------
+// Orthonormal Haar prox on 2^L-tiles.  The one-level 2-D (3-D) Haar of a 2x2
+// (2x2x2) block is H (x) H ((x) H) with H = [[1,1],[1,-1]]/sqrt(2): symmetric
+// and orthogonal, so it is its own inverse.  Level 2 applies the same block
+// transform to the level-1 approximation coefficients of a 4x4 (4x4x4) tile;
+// the inverse runs the levels in reverse order.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void haar2x2(float2& a, float2& b, float2& c, float2& d) {
+    // [a b; c d] (rows y, columns x) -> [LL HL; LH HH]
+    const float2 s0 = cadd(a, b), d0 = csub(a, b), s1 = cadd(c, d), d1 = csub(c, d);
+    a = cscale(cadd(s0, s1), 0.5f);
+    b = cscale(cadd(d0, d1), 0.5f);
+    c = cscale(csub(s0, s1), 0.5f);
+    d = cscale(csub(d0, d1), 0.5f);
+}
+
+__device__ __forceinline__ void haar2x2x2(float2* t /*[z][y][x], 8*/) {
+    haar2x2(t[0], t[1], t[2], t[3]);
+    haar2x2(t[4], t[5], t[6], t[7]);
+    const float r = 0.70710678118654752f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float2 a = t[i], b = t[4 + i];
+        t[i] = cscale(cadd(a, b), r);
+        t[4 + i] = cscale(csub(a, b), r);
+    }
+}
+
+// Block transform on the 2x2(x2) blocks with corner (sz, sy, sx) step `st`
+// inside a TS-tile held in registers, index (z*TS + y)*TS + x.
+template <int NDIM, int TS>
+__device__ __forceinline__ void haar_blocks(float2* v, int st) {
+    if (NDIM == 2) {
+#pragma unroll
+        for (int by = 0; by < TS; by += 2 * st)
+#pragma unroll
+            for (int bx = 0; bx < TS; bx += 2 * st)
+                haar2x2(v[by * TS + bx], v[by * TS + bx + st], v[(by + st) * TS + bx],
+                        v[(by + st) * TS + bx + st]);
+    } else {
+#pragma unroll
+        for (int bz = 0; bz < TS; bz += 2 * st)
+#pragma unroll
+            for (int by = 0; by < TS; by += 2 * st)
+#pragma unroll
+                for (int bx = 0; bx < TS; bx += 2 * st) {
+                    float2 t[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q)
+                        t[q] = v[((bz + (q >> 2) * st) * TS + by + ((q >> 1) & 1) * st) * TS + bx +
+                                 (q & 1) * st];
+                    haar2x2x2(t);
+#pragma unroll
+                    for (int q = 0; q < 8; ++q)
+                        v[((bz + (q >> 2) * st) * TS + by + ((q >> 1) & 1) * st) * TS + bx +
+                          (q & 1) * st] = t[q];
+                }
+    }
+}
+
+__device__ __forceinline__ float2 soft(float2 v, float lam) {
+    const float m2 = v.x * v.x + v.y * v.y;
+    if (!(m2 > lam * lam)) return make_float2(0.f, 0.f);
+    return cscale(v, 1.f - lam * rsqrtf(m2));
+}
+
+template <int NDIM, int LEVELS>
+__device__ __forceinline__ void prox_tile(float2* v, float lam) {
+    constexpr int TS = 1 << LEVELS;
+    haar_blocks<NDIM, TS>(v, 1);
+    if (LEVELS == 2) haar_blocks<NDIM, TS>(v, 2);
+    constexpr int NV = (NDIM == 2) ? TS * TS : TS * TS * TS;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) v[i] = soft(v[i], lam);
+    if (LEVELS == 2) haar_blocks<NDIM, TS>(v, 2);
+    haar_blocks<NDIM, TS>(v, 1);
+}
+
+// Tile (thread) t covers x in [tx*TS, +TS), y in [ty*TS, +TS), z in [tz*TS, +TS).
+template <int NDIM, int LEVELS>
+__device__ __forceinline__ int64_t tile_origin(int64_t t, int nx, int ny, int nz, bool& ok) {
+    constexpr int TS = 1 << LEVELS;
+    const int64_t ntx = nx / TS, nty = ny / TS, ntz = (NDIM == 3) ? nz / TS : 1;
+    ok = t < ntx * nty * ntz;
+    const int64_t tx = t % ntx;
+    const int64_t r = t / ntx;
+    const int64_t ty = r % nty;
+    const int64_t tz = r / nty;
+    return ((tz * TS) * ny + ty * TS) * (int64_t)nx + tx * TS;
+}
+
+template <int NDIM, int LEVELS>
+__global__ void __launch_bounds__(kThreads)
+prox_kernel(int nx, int ny, int nz, float lam, const float2* __restrict__ in,
+            float2* __restrict__ out) {
+    constexpr int TS = 1 << LEVELS;
+    constexpr int ZS = (NDIM == 3) ? TS : 1;
+    bool ok;
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t o = tile_origin<NDIM, LEVELS>(t, nx, ny, nz, ok);
+    if (!ok) return;
+    float2 v[ZS * TS * TS];
+#pragma unroll
+    for (int z = 0; z < ZS; ++z)
+#pragma unroll
+        for (int y = 0; y < TS; ++y)
+#pragma unroll
+            for (int x = 0; x < TS; ++x)
+                v[(z * TS + y) * TS + x] = in[o + ((int64_t)z * ny + y) * nx + x];
+    prox_tile<NDIM, LEVELS>(v, lam);
+#pragma unroll
+    for (int z = 0; z < ZS; ++z)
+#pragma unroll
+        for (int y = 0; y < TS; ++y)
+#pragma unroll
+            for (int x = 0; x < TS; ++x)
+                out[o + ((int64_t)z * ny + y) * nx + x] = v[(z * TS + y) * TS + x];
+}
+
+// Fused prox + momentum of Algorithm "pfista":
+//   y_new = prox(z - gamma*u);  z <- y_new + beta (y_new - y);  y <- y_new.
+// Optional FP64 statistics ||y_new - y||^2, ||y_new||^2 into hist[0..1].
+template <int NDIM, int LEVELS>
+__global__ void __launch_bounds__(kThreads)
+prox_fista_kernel(int nx, int ny, int nz, float lam, float gamma, float beta,
+                  float2* __restrict__ z, const float2* __restrict__ u, float2* __restrict__ y,
+                  double* __restrict__ hist) {
+    constexpr int TS = 1 << LEVELS;
+    constexpr int ZS = (NDIM == 3) ? TS : 1;
+    bool ok;
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t o = tile_origin<NDIM, LEVELS>(t, nx, ny, nz, ok);
+    double dd = 0.0, yy = 0.0;
+    if (ok) {
+        float2 v[ZS * TS * TS];
+#pragma unroll
+        for (int zz = 0; zz < ZS; ++zz)
+#pragma unroll
+            for (int r = 0; r < TS; ++r)
+#pragma unroll
+                for (int x = 0; x < TS; ++x) {
+                    const int64_t a = o + ((int64_t)zz * ny + r) * nx + x;
+                    const float2 zv = z[a], uv = u[a];
+                    v[(zz * TS + r) * TS + x] = make_float2(zv.x - gamma * uv.x, zv.y - gamma * uv.y);
+                }
+        prox_tile<NDIM, LEVELS>(v, lam);
+#pragma unroll
+        for (int zz = 0; zz < ZS; ++zz)
+#pragma unroll
+            for (int r = 0; r < TS; ++r)
+#pragma unroll
+                for (int x = 0; x < TS; ++x) {
+                    const int64_t a = o + ((int64_t)zz * ny + r) * nx + x;
+                    const float2 yn = v[(zz * TS + r) * TS + x];
+                    const float2 yo = y[a];
+                    const float2 df = csub(yn, yo);
+                    z[a] = make_float2(yn.x + beta * df.x, yn.y + beta * df.y);
+                    y[a] = yn;
+                    dd += (double)df.x * df.x + (double)df.y * df.y;
+                    yy += (double)yn.x * yn.x + (double)yn.y * yn.y;
+                }
+    }
+    if (hist) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            dd += __shfl_down_sync(0xffffffffu, dd, off);
+            yy += __shfl_down_sync(0xffffffffu, yy, off);
+        }
+        __shared__ double sd[kThreads / 32], sy[kThreads / 32];
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        if (lane == 0) {
+            sd[wid] = dd;
+            sy[wid] = yy;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double a = 0.0, b = 0.0;
+            for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+                a += sd[i];
+                b += sy[i];
+            }
+            atomicAdd(&hist[0], a);
+            atomicAdd(&hist[1], b);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 reductions (deterministic: fixed grid, per-block partials, one
+// finishing block).  partial layout [nblocks][3] = Re<a,b>, Im<a,b>, |b|^2.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads)
+dot_partial_kernel(const float2* __restrict__ a, const float2* __restrict__ b, int64_t n,
+                   double* __restrict__ partials) {
+    double re = 0.0, im = 0.0, nb = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 bv = b[i];
+        if (a) {
+            const float2 av = a[i];
+            re += (double)av.x * bv.x + (double)av.y * bv.y;
+            im += (double)av.x * bv.y - (double)av.y * bv.x;
+        }
+        nb += (double)bv.x * bv.x + (double)bv.y * bv.y;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        re += __shfl_down_sync(0xffffffffu, re, off);
+        im += __shfl_down_sync(0xffffffffu, im, off);
+        nb += __shfl_down_sync(0xffffffffu, nb, off);
+    }
+    __shared__ double s[3][kThreads / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        s[0][wid] = re;
+        s[1][wid] = im;
+        s[2][wid] = nb;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double r0 = 0, r1 = 0, r2 = 0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+            r0 += s[0][i];
+            r1 += s[1][i];
+            r2 += s[2][i];
+        }
+        partials[3 * blockIdx.x + 0] = r0;
+        partials[3 * blockIdx.x + 1] = r1;
+        partials[3 * blockIdx.x + 2] = r2;
+    }
+}
+
+__global__ void dot_final_kernel(const double* __restrict__ partials, int nblocks,
+                                 double* __restrict__ out_re, double* __restrict__ out_nb) {
+    __shared__ double s[2][kThreads];
+    double re = 0.0, nb = 0.0;
+    for (int i = threadIdx.x; i < nblocks; i += blockDim.x) {
+        re += partials[3 * i];
+        nb += partials[3 * i + 2];
+    }
+    s[0][threadIdx.x] = re;
+    s[1][threadIdx.x] = nb;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) {
+            s[0][threadIdx.x] += s[0][threadIdx.x + h];
+            s[1][threadIdx.x] += s[1][threadIdx.x + h];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        if (out_re) *out_re = s[0][0];
+        if (out_nb) *out_nb = s[1][0];
+    }
+}
+
+// out = in * factor / sqrt(norm2) (invert) or in * factor * sqrt(norm2)
+__global__ void scale_by_norm_kernel(const float2* __restrict__ in, float2* __restrict__ out,
+                                     int64_t n, const double* __restrict__ norm2, double factor,
+                                     int invert) {
+    const double nv = sqrt(*norm2);
+    const float f = (float)(invert ? (nv > 0.0 ? factor / nv : 0.0) : factor * nv);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = cscale(in[i], f);
+}
+
+__global__ void axpby_kernel(const float2* __restrict__ x, float a, const float2* __restrict__ y,
+                             float b, float2* __restrict__ out, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        float2 v = cscale(x[i], a);
+        if (y) v = cadd(v, cscale(y[i], b));
+        out[i] = v;
+    }
+}
+
+// SplitMix64 (Steele, Lea & Flood 2014) as a counter-based generator:
+// output j mixes seed + (j+1) * 0x9E3779B97F4A7C15.  Entry i of the start
+// vector is (2u_{2i} - 1) + i (2u_{2i+1} - 1), u_j = (out_j >> 11) 2^-53.
+__device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t j) {
+    uint64_t z = seed + (j + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__global__ void start_vector_kernel(float2* __restrict__ v, int64_t n, uint64_t seed) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double u0 = (double)(splitmix64_at(seed, 2 * i) >> 11) * 0x1.0p-53;
+        const double u1 = (double)(splitmix64_at(seed, 2 * i + 1) >> 11) * 0x1.0p-53;
+        v[i] = make_float2((float)(2.0 * u0 - 1.0), (float)(2.0 * u1 - 1.0));
+    }
+}
+
+inline int ew_blocks(int64_t n) {
+    int64_t b = (n + kThreads - 1) / kThreads;
+    if (b > 152 * 16) b = 152 * 16;
+    return (int)(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+// ===========================================================================
+// Launchers
+// ===========================================================================
+static pp_status check_launch(const char* what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_status(e, what);
+    return PP_OK;
+}
+
+static size_t rows_smem(int G) { return sizeof(float2) * (size_t)(G + 2 * RB * row_stride(G)); }
+static size_t cols_smem(int G) { return sizeof(float2) * (size_t)(G + 2 * G * TX); }
+
+pp_status configure_kernels() {
+    const int big = 200 * 1024;
+    PP_TRY_CUDA(cudaFuncSetAttribute(rows_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    PP_TRY_CUDA(cudaFuncSetAttribute(rows_adj_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    PP_TRY_CUDA(cudaFuncSetAttribute(rows_adj_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    PP_TRY_CUDA(cudaFuncSetAttribute(rows_adj_kernel<12>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    PP_TRY_CUDA(cudaFuncSetAttribute(rows_adj_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    PP_TRY_CUDA(cudaFuncSetAttribute(cols_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    PP_TRY_CUDA(cudaFuncSetAttribute(cols_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    PP_TRY_CUDA(cudaFuncSetAttribute(cols_roundtrip_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    PP_TRY_CUDA(cudaFuncSetAttribute(cart2d_normal_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    PP_TRY_CUDA(cudaFuncSetAttribute(cart2d_normal_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    PP_TRY_CUDA(cudaFuncSetAttribute(cart2d_normal_kernel<12>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    PP_TRY_CUDA(cudaFuncSetAttribute(cart2d_normal_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    PP_TRY_CUDA(cudaFuncSetAttribute(nufft_tile_kernel<4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    PP_TRY_CUDA(cudaFuncSetAttribute(nufft_tile_kernel<4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    return PP_OK;
+}
+
+pp_status launch_rows_fwd(const Plan& p, const DevFft& f, const RowArgs& a, const float2* x,
+                          const float2* sens, const float* wrow, const float* wcol, float2* out,
+                          int ncoils, int64_t img_batch_stride, cudaStream_t st) {
+    (void)p;
+    dim3 grid((a.nrows + RB - 1) / RB, ncoils);
+    rows_fwd_kernel<<<grid, kThreads, rows_smem(a.G), st>>>(f.d, f.tw, a, x, img_batch_stride, sens,
+                                                            wrow, wcol, out);
+    return check_launch("rows_fwd_kernel");
+}
+
+pp_status launch_rows_adj(const Plan& p, const DevFft& f, const RowArgs& a, const float2* src,
+                          const float2* sens, const float* wrow, const float* wcol, float2* out,
+                          const float2* operand, float alpha, int ncoils, cudaStream_t st) {
+    (void)p;
+    if (RB * a.n > KMAX * kThreads) {
+        set_error("row length %d exceeds the row stage limit", a.n);
+        return PP_ERR_UNSUPPORTED;
+    }
+    dim3 grid((a.nrows + RB - 1) / RB);
+    const int need = (RB * a.n + kThreads - 1) / kThreads;
+    const size_t sm = rows_smem(a.G);
+#define PP_ROWS_ADJ(KM_) rows_adj_kernel<KM_><<<grid, kThreads, sm, st>>>(f.d, f.tw, a, src, sens, wrow, wcol, out, operand, alpha, ncoils)
+    if (need <= 4) PP_ROWS_ADJ(4);
+    else if (need <= 8) PP_ROWS_ADJ(8);
+    else if (need <= 12) PP_ROWS_ADJ(12);
+    else PP_ROWS_ADJ(16);
+#undef PP_ROWS_ADJ
+    return check_launch("rows_adj_kernel");
+}
+
+pp_status launch_cols(const DevFft& f, const ColArgs& a, const float2* src, float2* dst, bool inv,
+                      cudaStream_t st) {
+    dim3 grid((a.ncols + TX - 1) / TX, a.nbatch);
+    if (inv)
+        cols_kernel<true><<<grid, kThreads, cols_smem(a.G), st>>>(f.d, f.tw, a, src, dst);
+    else
+        cols_kernel<false><<<grid, kThreads, cols_smem(a.G), st>>>(f.d, f.tw, a, src, dst);
+    return check_launch("cols_kernel");
+}
+
+pp_status launch_cols_roundtrip(const DevFft& f, const ColArgs& a, const float* mask_fo,
+                                const float2* src, float2* dst, cudaStream_t st) {
+    dim3 grid((a.ncols + TX - 1) / TX, a.nbatch);
+    cols_roundtrip_kernel<<<grid, kThreads, cols_smem(a.G), st>>>(f.d, f.tw, a, mask_fo, src, dst);
+    return check_launch("cols_roundtrip_kernel");
+}
+
+pp_status launch_cart2d_normal(const Plan& p, const float2* x, float2* out, float scale,
+                               const float2* operand, float alpha, cudaStream_t st) {
+    if (p.ny * TX > KMAX * kThreads) {
+        set_error("ny = %d exceeds the fused Cartesian kernel limit", p.ny);
+        return PP_ERR_UNSUPPORTED;
+    }
+    dim3 grid((p.nx + TX - 1) / TX);
+    const size_t smem = sizeof(float2) * (size_t)(p.ny + 2 * p.ny * TX) + sizeof(float) * p.ny;
+    const int need = (p.ny * TX + kThreads - 1) / kThreads;
+#define PP_CART(KM_) cart2d_normal_kernel<KM_><<<grid, kThreads, smem, st>>>(p.fy.d, p.fy.tw, x, p.sens, p.C, p.ny, p.nx, p.mask_fo, out, scale, operand, alpha)
+    if (need <= 4) PP_CART(4);
+    else if (need <= 8) PP_CART(8);
+    else if (need <= 12) PP_CART(12);
+    else PP_CART(16);
+#undef PP_CART
+    return check_launch("cart2d_normal_kernel");
+}
+
+pp_status launch_expand(const float2* x, const float2* s, float2* out, int64_t n, cudaStream_t st) {
+    expand_kernel<<<ew_blocks(n), kThreads, 0, st>>>(x, s, out, n);
+    return check_launch("expand_kernel");
+}
+
+pp_status launch_conj_accum(const float2* s, const float2* wv, float2* out, int64_t n, int first,
+                            float scale, const float2* operand, float alpha, int last,
+                            cudaStream_t st) {
+    conj_accum_kernel<<<ew_blocks(n), kThreads, 0, st>>>(s, wv, out, n, first, scale, operand, alpha,
+                                                          last);
+    return check_launch("conj_accum_kernel");
+}
+
+static size_t tile_smem(const Plan& p, bool degrid) {
+    const int HW = p.T + 2 * (p.W - 1);
+    return sizeof(float2) * (size_t)((degrid ? HW * HW : 0) + p.T * p.T);
+}
+
+pp_status launch_nufft_tile_normal(const Plan& p, const float2* grid_in, float2* grid_out,
+                                   cudaStream_t st) {
+    const int cpc = 4;
+    dim3 grid(p.ntx * p.nty, (p.C + cpc - 1) / cpc);
+    nufft_tile_kernel<4, true><<<grid, kThreads, tile_smem(p, true), st>>>(
+        p.tiles, p.tile_start, p.T, p.ntx, p.G_x, p.G_y, p.C, cpc, grid_in, nullptr, p.K, grid_out);
+    return check_launch("nufft_tile_kernel<degrid>");
+}
+
+pp_status launch_nufft_spread(const Plan& p, const float2* ksp, float2* grid_out, cudaStream_t st) {
+    const int cpc = 4;
+    dim3 grid(p.ntx * p.nty, (p.C + cpc - 1) / cpc);
+    nufft_tile_kernel<4, false><<<grid, kThreads, tile_smem(p, false), st>>>(
+        p.tiles, p.tile_start, p.T, p.ntx, p.G_x, p.G_y, p.C, cpc, nullptr, ksp, p.K, grid_out);
+    return check_launch("nufft_tile_kernel<spread>");
+}
+
+pp_status launch_nufft_degrid(const Plan& p, const float2* grid_in, float2* ksp, cudaStream_t st) {
+    dim3 grid((p.K + kThreads - 1) / kThreads, p.C);
+    nufft_degrid_kernel<4><<<grid, kThreads, 0, st>>>(p.samp, p.K, p.G_x, p.G_y, grid_in, ksp);
+    return check_launch("nufft_degrid_kernel");
+}
+
+pp_status launch_prox(int ndim, int nx, int ny, int nz, int levels, float lambda,
+                      const float2* in, float2* out, cudaStream_t st) {
+    const int ts = 1 << levels;
+    const int64_t ntiles = (int64_t)(nx / ts) * (ny / ts) * (ndim == 3 ? nz / ts : 1);
+    const int blocks = (int)((ntiles + kThreads - 1) / kThreads);
+    if (blocks == 0) return PP_OK;
+    if (ndim == 2 && levels == 1) prox_kernel<2, 1><<<blocks, kThreads, 0, st>>>(nx, ny, nz, lambda, in, out);
+    else if (ndim == 2) prox_kernel<2, 2><<<blocks, kThreads, 0, st>>>(nx, ny, nz, lambda, in, out);
+    else if (levels == 1) prox_kernel<3, 1><<<blocks, kThreads, 0, st>>>(nx, ny, nz, lambda, in, out);
+    else prox_kernel<3, 2><<<blocks, kThreads, 0, st>>>(nx, ny, nz, lambda, in, out);
+    return check_launch("prox_kernel");
+}
+
+pp_status launch_prox_fista(const Plan& p, int levels, float lambda, float gamma, float beta,
+                            const float2* u, double* hist_slot, cudaStream_t st) {
+    const int ts = 1 << levels;
+    const int64_t ntiles = (int64_t)(p.nx / ts) * (p.ny / ts) * (p.ndim == 3 ? p.nz / ts : 1);
+    const int blocks = (int)((ntiles + kThreads - 1) / kThreads);
+    if (p.ndim == 2 && levels == 1)
+        prox_fista_kernel<2, 1><<<blocks, kThreads, 0, st>>>(p.nx, p.ny, p.nz, lambda, gamma, beta, p.z, u, p.y, hist_slot);
+    else if (p.ndim == 2)
+        prox_fista_kernel<2, 2><<<blocks, kThreads, 0, st>>>(p.nx, p.ny, p.nz, lambda, gamma, beta, p.z, u, p.y, hist_slot);
+    else if (levels == 1)
+        prox_fista_kernel<3, 1><<<blocks, kThreads, 0, st>>>(p.nx, p.ny, p.nz, lambda, gamma, beta, p.z, u, p.y, hist_slot);
+    else
+        prox_fista_kernel<3, 2><<<blocks, kThreads, 0, st>>>(p.nx, p.ny, p.nz, lambda, gamma, beta, p.z, u, p.y, hist_slot);
+    return check_launch("prox_fista_kernel");
+}
+
+pp_status launch_dot(const float2* a, const float2* b, int64_t n, double* partials, int nblocks,
+                     double* out_re, double* out_norm_b, cudaStream_t st) {
+    dot_partial_kernel<<<nblocks, kThreads, 0, st>>>(a, b, n, partials);
+    PP_TRY(check_launch("dot_partial_kernel"));
+    dot_final_kernel<<<1, kThreads, 0, st>>>(partials, nblocks, out_re, out_norm_b);
+    return check_launch("dot_final_kernel");
+}
+
+pp_status launch_norm2(const float2* a, int64_t n, double* partials, int nblocks, double* out,
+                       cudaStream_t st) {
+    return launch_dot(nullptr, a, n, partials, nblocks, nullptr, out, st);
+}
+
+pp_status launch_scale_by_rnorm(const float2* in, float2* out, int64_t n, const double* norm2,
+                                double factor, int invert, cudaStream_t st) {
+    scale_by_norm_kernel<<<ew_blocks(n), kThreads, 0, st>>>(in, out, n, norm2, factor, invert);
+    return check_launch("scale_by_norm_kernel");
+}
+
+pp_status launch_axpby(const float2* x, float a, const float2* y, float b, float2* out, int64_t n,
+                       cudaStream_t st) {
+    axpby_kernel<<<ew_blocks(n), kThreads, 0, st>>>(x, a, y, b, out, n);
+    return check_launch("axpby_kernel");
+}
+
+pp_status launch_start_vector(float2* v, int64_t n, uint64_t seed, cudaStream_t st) {
+    start_vector_kernel<<<ew_blocks(n), kThreads, 0, st>>>(v, n, seed);
+    return check_launch("start_vector_kernel");
+}
+
+}  // namespace pp

@@ -1,0 +1,92 @@
+"""The C ABI library loads, exports every entry point include/pp.h declares,
+and its host-only logic (argument validation, Eq. "l2cost" coefficients)
+behaves as documented.  No device work is issued here."""
+import ctypes
+import os
+import re
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2204_10252_gb300.build import build_library
+    import paper_2204_10252_gb300 as pp
+    build_library()
+    return pp.lib()
+
+
+def declared_symbols():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(pp_[a-z0-9_]+)\s*\(", txt))
+    return names
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = declared_symbols()
+    assert len(names) >= 13
+    for n in sorted(names):
+        assert hasattr(L, n), "missing export %s" % n
+
+
+def test_binding_covers_every_symbol():
+    import paper_2204_10252_gb300.binding as b
+    for n in declared_symbols():
+        assert n in b._SIGS, "binding lacks %s" % n
+
+
+def test_poly_coeffs_match_golden_rationals(L):
+    import paper_2204_10252_gb300 as pp
+    table = {}
+    with open(os.path.join(ROOT, "tests", "golden", "l2_coeffs.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                d, rest = line.split(":")
+                table[int(d)] = [float(Fraction(t)) for t in rest.split()]
+    for d in range(0, 9):
+        got = pp.pp_poly_coeffs_l2(d)
+        ref = np.array(table[d])
+        # exact integer ratios, rounded once to double
+        assert np.max(np.abs(got - ref) / np.abs(ref)) <= 2e-16, d
+
+
+def test_invalid_arguments_are_rejected_without_device_work(L):
+    import paper_2204_10252_gb300 as pp
+    from paper_2204_10252_gb300.binding import pp_dims, pp_sampling
+    with pytest.raises(pp.PPError) as e:
+        pp.pp_poly_coeffs_l2(9)
+    assert e.value.status == 1
+    out = ctypes.c_void_p(0)
+    d = pp_dims()
+    d.ndim = 2
+    d.n[0] = d.n[1] = 64
+    s = pp_sampling()
+    assert L.pp_plan_create(None, d, 4, ctypes.c_void_p(16), ctypes.byref(s), 0, 0, None) == 1
+    assert L.pp_plan_create(ctypes.byref(out), d, 4, None, ctypes.byref(s), 0, 0, None) == 1
+    d.ndim = 4
+    assert L.pp_plan_create(ctypes.byref(out), d, 4, ctypes.c_void_p(16), ctypes.byref(s), 0, 0, None) == 2
+    assert "ndim" in pp.pp_last_error()
+    d.ndim = 2
+    assert L.pp_plan_create(ctypes.byref(out), d, 0, ctypes.c_void_p(16), ctypes.byref(s), 0, 0, None) == 1
+    d.n[0] = 66
+    assert L.pp_plan_create(ctypes.byref(out), d, 4, ctypes.c_void_p(16), ctypes.byref(s), 0, 0, None) == 2
+    assert out.value is None
+    # prox: levels outside 1..2 and axes not multiples of 2^levels
+    d.n[0] = 64
+    assert L.pp_prox_l1_haar(d, 3, ctypes.c_float(0.1), ctypes.c_void_p(16), ctypes.c_void_p(16), None) == 2
+    d.n[0] = 62
+    assert L.pp_prox_l1_haar(d, 2, ctypes.c_float(0.1), ctypes.c_void_p(16), ctypes.c_void_p(16), None) == 2
+    assert L.pp_prox_l1_haar(d, 1, ctypes.c_float(-1.0), ctypes.c_void_p(16), ctypes.c_void_p(16), None) == 1
+    # solve / applies with NULL plans
+    assert L.pp_normal_apply(None, ctypes.c_void_p(16), ctypes.c_void_p(32), None) == 1
+    assert L.pp_fista_solve(None, ctypes.c_void_p(16), ctypes.c_float(0.1), 1, None, 0,
+                            ctypes.c_void_p(16), None, None) == 1
+    assert L.pp_plan_destroy(None) == 0

@@ -1,0 +1,242 @@
+"""GPU parity: every libpp entry point against the FP64 oracle on the same
+seeded inputs.  Tolerances: relative L2 <= 1e-5 per operator apply, <= 1e-4
+after a full solve (FP32 arithmetic throughout on the device, FP64
+reductions)."""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import pp_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+TOL_APPLY = 1e-5
+TOL_SOLVE = 1e-4
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.complex128) - b) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module")
+def pp():
+    from paper_2204_10252_gb300.build import build_library
+    build_library()
+    import paper_2204_10252_gb300 as m
+    m.lib()
+    return m
+
+
+def dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.complex64)).cuda()
+
+
+def host(t):
+    import torch
+    torch.cuda.synchronize()
+    return t.cpu().numpy().astype(np.complex128)
+
+
+def empty(shape):
+    import torch
+    return torch.zeros(tuple(shape), dtype=torch.complex64, device="cuda")
+
+
+class Problem:
+    """Oracle-side operator closures plus the GPU plan for one case."""
+
+    def __init__(self, pp, kind, shape, coils, seed, **kw):
+        self.kind, self.shape, self.C = kind, tuple(shape), coils
+        self.sens = synth.coil_maps(shape, coils, seed)
+        self.sens_t = dev(self.sens)
+        if kind == "cart":
+            if len(shape) == 2:
+                self.mask = synth.line_mask(shape, kw.get("R", 4), kw.get("acs", 8), seed)
+            else:
+                self.mask = synth.poisson_disc_mask(shape, kw.get("R", 3), kw.get("calib", 4), seed)
+            self.fwd = lambda x: O.cart_forward(x, self.sens, self.mask)
+            self.adj = lambda y: O.cart_adjoint(y, self.sens, self.mask)
+            self.kshape = (coils,) + self.shape
+            self.plan = pp.pp_plan_create(shape, coils, self.sens_t, mask=self.mask, seed=seed,
+                                          power_iters=0)
+        else:
+            self.traj = synth.spiral_traj(kw["interleaves"], kw["samples"], kw.get("turns", 4.0),
+                                          kw.get("kmax", shape[0] / 2.0))
+            self.fwd = lambda x: O.nc_forward(x, self.sens, self.traj)
+            self.adj = lambda y: O.nc_adjoint(y, self.sens, self.traj)
+            self.kshape = (coils, len(self.traj))
+            self.plan = pp.pp_plan_create(shape, coils, self.sens_t, traj=self.traj, seed=seed,
+                                          power_iters=0)
+        self.normal = lambda x: self.adj(self.fwd(x))
+
+    def ksp(self, seed):
+        y = synth.crandn(self.kshape, seed)
+        if self.kind == "cart":
+            y = y * self.mask[None]
+        return y.astype(np.complex64)
+
+
+CASES = [
+    ("cart", (64, 48), 3, dict(R=3, acs=6)),
+    ("cart", (128, 128), 8, dict(R=4, acs=24)),
+    ("cart", (16, 24, 20), 3, dict(R=3, calib=4)),
+    ("noncart", (64, 64), 4, dict(interleaves=4, samples=512)),
+    ("noncart", (72, 80), 2, dict(interleaves=3, samples=700, turns=3.0, kmax=35.9)),
+]
+IDS = ["cart2d_64x48", "cart2d_128", "cart3d_16x24x20", "spiral_64", "spiral_72x80_ragged"]
+
+
+@pytest.fixture(scope="module", params=list(range(len(CASES))), ids=IDS)
+def prob(request, pp):
+    kind, shape, C, kw = CASES[request.param]
+    p = Problem(pp, kind, shape, C, 100 + request.param, **kw)
+    yield p
+    p.plan.destroy()
+
+
+def test_forward_parity(pp, prob):
+    x = synth.crandn(prob.shape, 1)
+    y = empty(prob.kshape)
+    pp.pp_forward_apply(prob.plan, dev(x), y)
+    assert rel(host(y), prob.fwd(x)) <= TOL_APPLY
+
+
+def test_adjoint_parity(pp, prob):
+    yk = prob.ksp(2)
+    x = empty(prob.shape)
+    pp.pp_adjoint_apply(prob.plan, dev(yk), x)
+    assert rel(host(x), prob.adj(yk)) <= TOL_APPLY
+
+
+def test_normal_parity_with_shared_scale(pp, prob):
+    x = synth.crandn(prob.shape, 3)
+    L = 0.731
+    pp.pp_plan_set_scale(prob.plan, L)
+    out = empty(prob.shape)
+    pp.pp_normal_apply(prob.plan, dev(x), out)
+    assert rel(host(out), prob.normal(x) / L) <= TOL_APPLY
+
+
+@pytest.mark.parametrize("d", [0, 1, 3, 5])
+def test_poly_apply_parity(pp, prob, d):
+    x = synth.crandn(prob.shape, 4)
+    L = float(O.power_iteration(prob.normal, prob.shape, 9, iters=10))
+    pp.pp_plan_set_scale(prob.plan, L)
+    c = [float(v) for v in O.poly_coeffs_l2(d)]
+    out = empty(prob.shape)
+    pp.pp_poly_apply(prob.plan, c, d, dev(x), out)
+    ref = O.horner_apply(c, lambda v: prob.normal(v) / L, x.astype(np.complex128))
+    assert rel(host(out), ref) <= TOL_APPLY
+
+
+def test_power_iteration_matches_oracle(pp, prob):
+    import torch
+    L_ref = O.power_iteration(prob.normal, prob.shape, 77, iters=50)
+    plan = pp.pp_plan_create(prob.shape, prob.C, prob.sens_t,
+                             mask=getattr(prob, "mask", None) if prob.kind == "cart" else None,
+                             traj=getattr(prob, "traj", None) if prob.kind != "cart" else None,
+                             seed=77, power_iters=50)
+    try:
+        L = pp.pp_plan_scale(plan)
+    finally:
+        plan.destroy()
+    assert abs(L - L_ref) <= 1e-5 * L_ref
+
+
+@pytest.mark.parametrize("d", [None, 3])
+def test_solve_parity(pp, prob, d):
+    x0 = synth.phantom(prob.shape, 5)
+    b = (prob.fwd(x0) + prob.ksp(6) * 1e-3).astype(np.complex64)
+    L = float(O.power_iteration(prob.normal, prob.shape, 9, iters=30))
+    pp.pp_plan_set_scale(prob.plan, L)
+    lam, iters = 1e-3, 12
+    c = None if d is None else [float(v) for v in O.poly_coeffs_l2(d)]
+    hist_ref = []
+    ref = O.pfista(prob.normal, prob.adj, b.astype(np.complex128), lam, c, iters, L,
+                   history=hist_ref)
+    out = empty(prob.shape)
+    hist, bnorm, Lused = pp.pp_fista_solve(prob.plan, dev(b), lam, iters, c, 0 if d is None else d,
+                                           out, history=True)
+    assert Lused == L
+    assert abs(bnorm - np.linalg.norm(b.astype(np.complex128))) <= 1e-9 * bnorm
+    assert rel(host(out), ref) <= TOL_SOLVE
+    # FP64 statistics: ||y_{k+1}||^2 per iteration
+    yy_ref = np.array([np.linalg.norm(h) ** 2 for h in hist_ref])
+    assert np.max(np.abs(hist[:, 1] - yy_ref) / yy_ref) <= 2 * TOL_SOLVE
+
+
+@pytest.mark.parametrize("shape,levels", [((64, 48), 2), ((64, 48), 1), ((8, 16, 12), 2),
+                                          ((6, 10, 14), 1), ((4, 4), 2)])
+@pytest.mark.parametrize("inplace", [False, True])
+def test_prox_parity(pp, shape, levels, inplace):
+    x = synth.crandn(shape, 7)
+    lam = 0.4
+    xin = dev(x)
+    out = xin if inplace else empty(shape)
+    pp.pp_prox_l1_haar(shape, levels, lam, xin, out)
+    assert rel(host(out), O.prox_l1_haar(x, lam, levels)) <= TOL_APPLY
+
+
+def test_solve_edge_cases(pp):
+    shape, C = (32, 32), 1
+    p = Problem(pp, "cart", shape, C, 3, R=2, acs=8)
+    try:
+        x0 = synth.phantom(shape, 1)
+        b = (p.fwd(x0)).astype(np.complex64)
+        L = float(O.power_iteration(p.normal, shape, 9, iters=30))
+        pp.pp_plan_set_scale(p.plan, L)
+        out = empty(shape)
+        # zero iterations: y_0 = 0
+        pp.pp_fista_solve(p.plan, dev(b), 1e-3, 0, None, 0, out)
+        assert np.all(host(out) == 0)
+        # lambda = 0, d = 0 with c0 != 1 (scaled gradient step)
+        ref = O.pfista(p.normal, p.adj, b.astype(np.complex128), 0.0, [0.5], 6, L)
+        pp.pp_fista_solve(p.plan, dev(b), 0.0, 6, [0.5], 0, out)
+        assert rel(host(out), ref) <= TOL_SOLVE
+        # rescale to the units of the original problem
+        ref = O.pfista(p.normal, p.adj, b.astype(np.complex128), 1e-3, None, 5, L)
+        ref = ref * np.linalg.norm(b.astype(np.complex128)) / math.sqrt(L)
+        pp.pp_fista_solve(p.plan, dev(b), 1e-3, 5, None, 0, out, rescale=True)
+        assert rel(host(out), ref) <= TOL_SOLVE
+    finally:
+        p.plan.destroy()
+
+
+def test_unsupported_sizes_raise(pp):
+    import torch
+    sens = dev(synth.coil_maps((28, 28), 2, 0))
+    with pytest.raises(pp.PPError) as e:   # 28 = 4 * 7: prime factor 7
+        pp.pp_plan_create((28, 28), 2, sens, mask=np.ones((28, 28), np.uint8), power_iters=0)
+    assert e.value.status == 2
+    m = np.ones((32, 32), np.uint8)
+    m[3, 5] = 0   # not constant along x
+    sens = dev(synth.coil_maps((32, 32), 2, 0))
+    with pytest.raises(pp.PPError) as e:
+        pp.pp_plan_create((32, 32), 2, sens, mask=m, power_iters=0)
+    assert e.value.status == 2
+    traj = np.array([[40.0, 0.0]], np.float32)   # outside [-n/2, n/2)
+    with pytest.raises(pp.PPError) as e:
+        pp.pp_plan_create((64, 64), 2, dev(synth.coil_maps((64, 64), 2, 0)), traj=traj, power_iters=0)
+    assert e.value.status == 1
+
+
+def test_full_size_spiral_normal_apply(pp):
+    # 256^2, 32 coils, 16 x 4096 spiral: the workload the benchmark times.
+    cfg = synth.CONFIGS["spiral2d_256_c32"]
+    shape, C = cfg["shape"], cfg["coils"]
+    sens = synth.coil_maps(shape, C, cfg["seed"])
+    traj = synth.spiral_traj(cfg["interleaves"], cfg["samples"], cfg["turns"], 128.0)
+    plan = pp.pp_plan_create(shape, C, dev(sens), traj=traj, power_iters=0)
+    try:
+        L = 123.0
+        pp.pp_plan_set_scale(plan, L)
+        x = synth.crandn(shape, 11)
+        out = empty(shape)
+        pp.pp_normal_apply(plan, dev(x), out)
+        ref = O.nc_normal(x, sens, traj) / L
+        assert rel(host(out), ref) <= TOL_APPLY
+    finally:
+        plan.destroy()
