@@ -1,0 +1,439 @@
+#!/usr/bin/env python
+"""Benchmark of polynomial-preconditioned FISTA (Algorithm "pfista").
+
+Workload (2-D non-Cartesian SENSE): 256x256 complex64 image, 32 coils,
+16-interleave Archimedean spiral with 4096 samples per interleave,
+Kaiser-Bessel gridding (width 4, oversampling 1.25), 2-level Haar l1 with
+lambda = 5e-4, degree-5 l2-optimal polynomial, 100 iterations.  Synthetic
+seeded inputs (random-ellipse phantom, smooth coil maps, complex Gaussian
+noise sigma = 1e-3).
+
+One step = one pp_fista_solve call: A^H b, then 100 iterations of
+(d+1) = 6 normal-operator applies, the fused Haar prox and the momentum
+update, captured as one CUDA graph.  Metric: A^H A applies per second
+(whole job).  The plan (coil maps, trajectory, the 50-step power iteration)
+is built before the timed region and reported separately as setup time.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+For N > 1 run under torch.distributed.run: each rank solves its own
+independent problem (a different seed); no collective touches the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import glob
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+WORKLOAD = "spiral2d_256_c32"
+METRIC = "A^H A applies/s (preconditioned FISTA solve, d=5, 100 iterations)"
+UNIT = "applies/s"
+FP32_LANES_PER_SM = 128
+NUM_SMS = 152
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["pp", "reference"], default="pp")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip time-to-NRMSE, e2e, CPU baseline (quick runs)")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def cfg():
+    return dict(synth.CONFIGS[WORKLOAD])
+
+
+def replica_seed(base, rank):
+    """Each rank solves an independent problem instance of the same shape."""
+    return base + 1000 * rank
+
+
+def max_over_ranks(value, world, device=None):
+    """Largest `value` over all ranks (the job's time is its slowest rank)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, world, max_seconds):
+    """Units all ranks processed divided by the slowest rank's time."""
+    return world * units_per_rank / max_seconds
+
+
+def make_inputs(c, rank):
+    """Host-side synthetic inputs for one replica (seed offset by rank)."""
+    seed = replica_seed(c["seed"], rank)
+    shape, C = c["shape"], c["coils"]
+    sens = synth.coil_maps(shape, C, seed)
+    traj = synth.spiral_traj(c["interleaves"], c["samples"], c["turns"], shape[0] / 2.0)
+    x_true = synth.phantom(shape, seed)
+    noise = synth.cnoise((C, len(traj)), c["sigma"], seed + 1)
+    return seed, sens, traj, x_true, noise
+
+
+# ---------------------------------------------------------------------------
+# clocks (nvidia-smi sampled during the timed region)
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# roofline bookkeeping: algorithmic FLOPs per launch of each normal-operator
+# kernel (conventional 5 N log2 N per complex FFT of length N)
+# ---------------------------------------------------------------------------
+def kernel_flops(c, K):
+    ny, nx = c["shape"]
+    C = c["coils"]
+    G = int(math.ceil(c["oversamp"] * nx))
+    n = nx * ny
+    fft = lambda N: 5.0 * N * math.log2(N)
+    return {
+        "rows_fwd_kernel": C * ny * fft(G) + 8.0 * C * n,
+        "cols_kernel": C * G * fft(G),
+        "nufft_tile_kernel<degrid>": 128.0 * C * K,
+        "rows_adj_kernel": C * ny * fft(G) + 10.0 * C * n,
+    }
+
+
+def csrc_digest():
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2204_10252_gb300", "csrc", "*"))):
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel):
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, or
+    None when missing or taken on different kernel sources."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        d = json.load(open(p))
+    except Exception:
+        return None
+    e = d.get("kernels", {}).get(kernel)
+    if not e or d.get("csrc_sha") != csrc_digest():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def oracle_sample(c, sens, traj, coils):
+    """One bounded sample of the workload on the FP64 oracle: the normal
+    operator restricted to the first `coils` coils (a fraction coils/C of one
+    full A^H A apply).  Returns (seconds, fraction)."""
+    from oracle import pp_oracle as O
+    x = synth.crandn(c["shape"], 3).astype(np.complex128)
+    t0 = time.perf_counter()
+    O.nc_normal(x, sens[:coils], traj, c["kb_width"], c["oversamp"])
+    return time.perf_counter() - t0, coils / float(c["coils"])
+
+
+def cpu_baseline(c, sens, traj, budget_s=15.0, coils=2):
+    """The oracle as it stands, timed on the host cores on ~budget_s of
+    bounded samples; reported in full-apply units."""
+    el, frac, n = 0.0, 0.0, 0
+    while el < budget_s:
+        t, f = oracle_sample(c, sens, traj, coils)
+        el += t
+        frac += f
+        n += 1
+    return {"value": frac / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d samples, each the A^H A apply of %d of the 32 coils (256x256, 65536-sample "
+                      "spiral) on the numpy FP64 oracle, scaled to full applies; numpy's FFT and "
+                      "scatter-add run single-threaded" % (n, coils)}
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the oracle as it stands, timed on the host cores
+# ---------------------------------------------------------------------------
+def run_reference(args, rank, world, coils=2):
+    if rank != 0:
+        return
+    c = cfg()
+    seed, sens, traj, x_true, noise = make_inputs(c, 0)
+    for _ in range(args.warmup):
+        oracle_sample(c, sens, traj, coils)
+    el, frac = 0.0, 0.0
+    for _ in range(args.steps):
+        t, f = oracle_sample(c, sens, traj, coils)
+        el += t
+        frac += f
+    v = frac / el
+    sample = "each step is the A^H A apply of %d of the 32 coils (256x256, 65536-sample spiral) " \
+             "on the numpy FP64 oracle, scaled to full applies" % coils
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    import torch
+    import torch.distributed as dist
+
+    if world > 1:
+        backend = "nccl" if (args.impl == "pp" and torch.cuda.is_available()) else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    import paper_2204_10252_gb300 as pp
+    from paper_2204_10252_gb300.build import build_library
+    build_library()
+    pp.lib()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    c = cfg()
+    seed, sens, traj, x_true, noise = make_inputs(c, rank)
+    shape, C, d, iters, lam = c["shape"], c["coils"], c["d"], c["iters"], c["lam"]
+    K = len(traj)
+
+    sens_t = torch.from_numpy(sens).to(dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plan = pp.pp_plan_create(shape, C, sens_t, traj=traj, kb_width=c["kb_width"],
+                             oversamp=c["oversamp"], seed=seed, power_iters=50)
+    torch.cuda.synchronize()
+    setup_plan_s = time.perf_counter() - t0
+    L = pp.pp_plan_scale(plan)
+
+    # measurements b = A x_true + noise (input synthesis: the forward model runs in libpp)
+    xt = torch.from_numpy(x_true).to(dev)
+    b = torch.empty((C, K), dtype=torch.complex64, device=dev)
+    pp.pp_forward_apply(plan, xt, b)
+    b += torch.from_numpy(noise).to(dev)
+    coeffs = [float(v) for v in pp.pp_poly_coeffs_l2(d)]
+    x_out = torch.empty(shape, dtype=torch.complex64, device=dev)
+    applies_per_step = iters * (d + 1)
+
+    for _ in range(args.warmup):
+        pp.pp_fista_solve(plan, b, lam, iters, coeffs, d, x_out)
+    torch.cuda.synchronize()
+
+    # L2 is 129 MB and the solve's working set (~80 MB) fits in it: flush it
+    # between timed steps by writing a 256 MB buffer (outside the timed events).
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    launches = 0
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            r = pp.pp_fista_solve(plan, b, lam, iters, coeffs, d, x_out)
+            ev[i][1].record(stream)
+            launches += r.launches
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    total_ms = sum(a.elapsed_time(bb) for a, bb in ev)
+    max_ms = max_over_ranks(total_ms, world, dev)
+    value = job_throughput(args.steps * applies_per_step, world, max_ms / 1e3)
+    ms_per_step = max_ms / args.steps
+    clocks = clk.summary()
+
+    # --- per-kernel timing of the normal operator (CUDA events on the stream) ---
+    xin = torch.from_numpy(synth.crandn(shape, 3)).to(dev)
+    yout = torch.empty_like(xin)
+    stages = pp.pp_profile_normal(plan, xin, yout, reps=50)
+    apply_ms = sum(stages.values())
+    flops = kernel_flops(c, K)
+    # cols_kernel runs twice per apply (forward and inverse): per-launch time is half
+    launches_per_apply = {"cols_kernel": 2}
+    per_launch_ms = {k: v / launches_per_apply.get(k, 1) for k, v in stages.items()}
+    dom = max(stages, key=stages.get)
+    sm_clock = clocks["sm_max_mhz"] or 2070.0
+    peak_tflops = NUM_SMS * FP32_LANES_PER_SM * 2 * 2070.0e6 / 1e12
+    ach = flops.get(dom, float("nan")) / (per_launch_ms[dom] / 1e3) / 1e12
+    roofline = {
+        "bound": "alu", "kernel": dom, "achieved": ach, "peak": peak_tflops, "unit": "TFLOP/s",
+        "frac": ach / peak_tflops, "traffic": ncu_traffic(dom),
+        "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop/FMA x 2070 MHz (FP32 CUDA cores)",
+        "stage_ms_per_apply": {k: round(v, 5) for k, v in stages.items()},
+        "stage_share": {k: round(v / apply_ms, 4) for k, v in stages.items()},
+    }
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded phantom, coil maps, spiral, noise); no datasets",
+        "config": {"workload": WORKLOAD, "image": list(shape), "coils": C, "samples": K,
+                   "kb_width": c["kb_width"], "oversamp": c["oversamp"], "lambda": lam, "d": d,
+                   "iters": iters, "applies_per_step": applies_per_step,
+                   "l2": "flushed between timed steps (256 MB write)", "parallelism":
+                   "replicas" if world > 1 else "single GPU",
+                   "setup_plan_s": setup_plan_s, "L": L},
+        "roofline": roofline, "clocks": clocks, "gpu_launches": launches,
+    }
+
+    if not args.no_extras:
+        # --- end to end through the public API with host buffers ---
+        b_host = b.cpu().pin_memory()
+        x_host = torch.empty(shape, dtype=torch.complex64).pin_memory()
+        b_dev = torch.empty_like(b)
+        ee = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        torch.cuda.synchronize()
+        for i in range(args.steps):
+            flush.zero_()
+            ee[i][0].record(stream)
+            b_dev.copy_(b_host, non_blocking=True)
+            pp.pp_fista_solve(plan, b_dev, lam, iters, coeffs, d, x_out)
+            x_host.copy_(x_out, non_blocking=True)
+            ee[i][1].record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = max_over_ranks(sum(a.elapsed_time(bb) for a, bb in ee), world, dev)
+        out["e2e"] = {"value": job_throughput(args.steps * applies_per_step, world, e2e_ms / 1e3),
+                      "unit": UNIT, "h2d_bytes_per_step": b_host.numel() * 8,
+                      "d2h_bytes_per_step": x_host.numel() * 8}
+        # --- time to NRMSE <= 1e-3 against each method's own converged solution ---
+        out["time_to_nrmse"] = time_to_target(pp, plan, b, c, coeffs, setup_plan_s, stream)
+        if rank == 0 and world == 1:
+            out["cpu_baseline"] = cpu_baseline(c, sens, traj)
+    if rank == 0:
+        print(json.dumps(out))
+    plan.destroy()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def time_to_target(pp, plan, b, c, coeffs, setup_s, stream, target=1e-3):
+    """Per method: converged y_inf (20x the iteration count), the first k
+    with ||y_k - y_inf|| / ||y_inf|| <= target, per-iteration time from a
+    timed graph replay, and time = setup + k * T_iter."""
+    import torch
+    shape, lam, d, iters = c["shape"], c["lam"], c["d"], c["iters"]
+    res = {}
+    for name, cc, dd in (("preconditioned_d%d" % d, coeffs, d), ("plain_fista", None, 0)):
+        n_inf = 20 * iters
+        y_inf = torch.empty(shape, dtype=torch.complex64, device=b.device)
+        pp.pp_fista_solve(plan, b, lam, n_inf, cc, dd, y_inf)
+        y = torch.empty_like(y_inf)
+        r = pp.pp_fista_solve(plan, b, lam, n_inf, cc, dd, y, history=True, ref=y_inf)
+        nrm = float(torch.linalg.vector_norm(y_inf.to(torch.complex128)).item())
+        err = np.sqrt(np.maximum(r.history[:, 2], 0.0)) / nrm
+        hit = np.flatnonzero(err <= target)
+        k_star = int(hit[0]) + 1 if hit.size else None
+        # per-iteration time: timed replay of `iters` iterations
+        pp.pp_fista_solve(plan, b, lam, iters, cc, dd, y)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(5):
+            pp.pp_fista_solve(plan, b, lam, iters, cc, dd, y)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_iter = e0.elapsed_time(e1) / 1e3 / (5 * iters)
+        res[name] = {
+            "iters_to_target": k_star,
+            "applies_to_target": None if k_star is None else k_star * (dd + 1),
+            "iter_ms": t_iter * 1e3,
+            "seconds_without_setup": None if k_star is None else k_star * t_iter,
+            "seconds_with_setup": None if k_star is None else setup_s + k_star * t_iter,
+            "nrmse_at_config_iters": float(err[min(iters, len(err)) - 1]),
+            "iters_run": n_inf,
+        }
+    a, p_ = res["preconditioned_d%d" % d], res["plain_fista"]
+    if a["seconds_without_setup"] and p_["seconds_without_setup"]:
+        res["speedup_without_setup"] = p_["seconds_without_setup"] / a["seconds_without_setup"]
+    res["target"] = target
+    return res
+
+
+if __name__ == "__main__":
+    main()

@@ -144,15 +144,22 @@ pp_status pp_poly_apply(const pp_plan* plan, const double* c, int d, const pp_c6
 pp_status pp_prox_l1_haar(pp_dims dims, int levels, float lambda, const pp_c64* in, pp_c64* out,
                           pp_stream stream);
 
-/* Optional solve outputs.  history, if non-NULL, is host double [iters][2]
- * receiving ||y_{k+1} - y_k||_2^2 and ||y_{k+1}||_2^2 per iteration (FP64
- * reductions on the device); setting it makes the call synchronise. */
+/* Optional solve inputs/outputs.
+ *  history  host double [iters][3] or NULL.  Row k receives, as FP64
+ *           reductions on the device, ||y_{k+1} - y_k||^2, ||y_{k+1}||^2 and
+ *           ||y_{k+1} - ref||^2 (0 when ref is NULL).  Setting it makes the
+ *           call synchronise.
+ *  ref      device image or NULL: reference for the third history column
+ *           (e.g. a converged solution, for NRMSE against it as in Sec. 5).
+ *  launches out: kernels this call enqueued (graph nodes included). */
 typedef struct {
-    int rescale;        /* in: 1 = multiply x_out by ||b|| / sqrt(L)        */
-    int levels;         /* in: Haar levels (0 means 2)                      */
-    double* history;    /* in: optional host buffer, see above              */
-    double bnorm;       /* out: ||b||_2 (valid when history != NULL)        */
-    double L;           /* out: the L used                                  */
+    int rescale;         /* in: 1 = multiply x_out by ||b|| / sqrt(L)        */
+    int levels;          /* in: Haar levels (0 means 2)                      */
+    double* history;     /* in: optional host buffer, see above              */
+    const pp_c64* ref;   /* in: optional device reference image              */
+    double bnorm;        /* out: ||b||_2 (valid when history != NULL)        */
+    double L;            /* out: the L used                                  */
+    int64_t launches;    /* out: kernels enqueued by this call               */
 } pp_solve_info;
 
 /* Algorithm "pfista" on the normalised problem (Sec. 5): A_hat = A/sqrt(L),
@@ -167,6 +174,51 @@ typedef struct {
  * lambda and levels are unchanged. */
 pp_status pp_fista_solve(pp_plan* plan, const pp_c64* b, float lambda, int iters, const double* c,
                          int d, pp_c64* x_out, pp_solve_info* info, pp_stream stream);
+
+/* ---- Batches of independent 2-D Cartesian problems of uneven size ----
+ * Slice s is its own problem (Sec. 5.1 operator, its own L_s, its own ||b_s||)
+ * of size dims[s] (2-D, axes multiples of 4, FFT lengths with prime factors
+ * <= 5, at most 512), coils[s] coils (1..64), borrowed device maps sens[s]
+ * [C_s][ny_s][nx_s] and a host line mask masks[s] [ny_s][nx_s] constant along
+ * x.  Images, k-space and solutions are concatenated in slice order; the
+ * offsets come from pp_batch_offsets.  Every stage of an iteration is one
+ * persistent kernel launch over a work list of (slice, column tile) items,
+ * and the tile width is chosen at creation by timing the candidates. */
+typedef struct pp_batch pp_batch;
+
+/* Build a batch; power_iters > 0 estimates every L_s (one seed per slice:
+ * seed + s).  Synchronises `stream`. */
+pp_status pp_batch_create(pp_batch** out, int nslices, const pp_dims* dims, const int* coils,
+                          const pp_c64* const* sens, const uint8_t* const* masks, uint64_t seed,
+                          int power_iters, pp_stream stream);
+pp_status pp_batch_destroy(pp_batch* batch);
+/* host int64 [nslices + 1] each (either may be NULL) */
+pp_status pp_batch_offsets(const pp_batch* batch, int64_t* image_off, int64_t* kspace_off);
+/* host double [nslices] */
+pp_status pp_batch_scales(const pp_batch* batch, double* L);
+pp_status pp_batch_set_scales(pp_batch* batch, const double* L);
+/* autotuned column tile width and persistent grid size (either may be NULL) */
+pp_status pp_batch_tile(const pp_batch* batch, int* cols_per_cta, int* persistent_ctas);
+/* per-slice A x and A^H y (one launch sequence per slice; set-up work) */
+pp_status pp_batch_forward_apply(const pp_batch* batch, const pp_c64* x, pp_c64* y, pp_stream stream);
+pp_status pp_batch_adjoint_apply(const pp_batch* batch, const pp_c64* y, pp_c64* x, pp_stream stream);
+/* y_s = (A_s^H A_s / L_s) x_s for every slice in one launch */
+pp_status pp_batch_normal_apply(const pp_batch* batch, const pp_c64* x, pp_c64* y, pp_stream stream);
+/* Algorithm "pfista" on every slice's normalised problem, one shared lambda,
+ * iteration count and polynomial; as pp_fista_solve otherwise (history sums
+ * over the batch; levels must be 0 or 2). */
+pp_status pp_batch_fista_solve(pp_batch* batch, const pp_c64* b, float lambda, int iters,
+                               const double* c, int d, pp_c64* x_out, pp_solve_info* info,
+                               pp_stream stream);
+
+/* Stage timing of the normal operator N_hat (no counterpart in the paper:
+ * instrumentation).  Runs `reps` applies of N_hat x -> y on `stream`,
+ * recording a CUDA event after every kernel launch, synchronises, and
+ * returns per kernel name the average milliseconds per apply: names is host
+ * char [max_stages][48], ms host double [max_stages], *nstages the count. */
+pp_status pp_profile_normal(const pp_plan* plan, const pp_c64* x, pp_c64* y, int reps,
+                            int max_stages, char* names, double* ms, int* nstages,
+                            pp_stream stream);
 
 /* Message for the last failing call on this thread ("" if none). */
 const char* pp_last_error(void);

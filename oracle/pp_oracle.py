@@ -422,3 +422,98 @@ def pfista(normal, adjoint, b, lam, coeffs, iters, L, levels=2, normalize_b=True
         if history is not None:
             history.append(y.copy())
     return y
+
+
+# --------------------------------------------------------------------------
+# Differentiable unrolled solve: Algorithm "pfista" run for a fixed number of
+# iterations with b NOT normalised (L fixed), and its reverse-mode gradient.
+# --------------------------------------------------------------------------
+
+
+def pfista_unrolled(normal, adjoint, b, lam, coeffs, iters, L, levels=2, tape=None):
+    """y_K of Algorithm "pfista" with A_hat = A/sqrt(L) and raw b:
+    A_hat^H b = A^H b / sqrt(L).  `tape`, if a dict, receives z_k, g_k, w_k
+    for every iteration (what the reverse pass needs)."""
+    ahb = adjoint(np.asarray(b, dtype=np.complex128)) / math.sqrt(L)
+
+    def nhat(v):
+        return normal(v) / L
+
+    y = np.zeros_like(ahb)
+    z = np.zeros_like(ahb)
+    if tape is not None:
+        tape.update(z=[], g=[], w=[], ahb=ahb)
+    for k in range(iters):
+        g = nhat(z) - ahb
+        u = horner_apply(coeffs, nhat, g)
+        w = z - u
+        y_new = prox_l1_haar(w, lam, levels)
+        beta = k / (k + 3.0)
+        if tape is not None:
+            tape["z"].append(z)
+            tape["g"].append(g)
+            tape["w"].append(w)
+        z = y_new + beta * (y_new - y)
+        y = y_new
+    return y
+
+
+def soft_threshold_vjp(v, lam, gbar):
+    """For s(v) = v max(0, 1 - lam/|v|) (a real-linear map on (Re, Im)):
+    returns (J^T gbar, d/dlam of Re<gbar, s(v)>).  Where |v| > lam,
+    J dv = (1 - lam/|v|) dv + (lam/|v|) vhat Re(conj(vhat) dv), vhat = v/|v|
+    (symmetric), and ds/dlam = -vhat; elsewhere J = 0 and ds/dlam = 0."""
+    v = np.asarray(v, dtype=np.complex128)
+    mag = np.abs(v)
+    on = mag > lam
+    safe = np.where(on, mag, 1.0)
+    vh = np.where(on, v / safe, 0.0)
+    jt = np.where(on, (1.0 - lam / safe) * gbar + (lam / safe) * vh * np.real(np.conj(vh) * gbar), 0.0)
+    dlam = float(np.sum(np.real(np.conj(gbar) * (-vh))))
+    return jt, dlam
+
+
+def pfista_unrolled_vjp(normal, adjoint, forward, b, lam, coeffs, iters, L, ybar, levels=2):
+    """Gradient of the real loss Re<ybar, y_K> of pfista_unrolled with respect
+    to b (as dLoss/dRe b + i dLoss/dIm b), lam and every coefficient c_i.
+    Reverse pass of the iteration, step by step:
+      z_{k+1} = (1+beta_k) y_{k+1} - beta_k y_k
+      y_{k+1} = W^T s_lam(W w_k)
+      w_k     = z_k - sum_i c_i N^i g_k,   g_k = N z_k - A_hat^H b
+    with N = N_hat self-adjoint.  Returns (b_bar, lam_bar, c_bar)."""
+    tape = {}
+    pfista_unrolled(normal, adjoint, b, lam, coeffs, iters, L, levels, tape)
+    c = [float(ci) for ci in coeffs]
+    d = len(c) - 1
+
+    def nhat(v):
+        return normal(v) / L
+
+    ybar_next = np.asarray(ybar, dtype=np.complex128).copy()   # adjoint of y_{k+1}
+    zbar_next = np.zeros_like(ybar_next)                        # adjoint of z_{k+1}
+    ybar_cur = np.zeros_like(ybar_next)                         # adjoint of y_k (partial)
+    ahb_bar = np.zeros_like(ybar_next)
+    c_bar = np.zeros(d + 1)
+    lam_bar = 0.0
+    for k in reversed(range(iters)):
+        beta = k / (k + 3.0)
+        ybar_next = ybar_next + (1.0 + beta) * zbar_next
+        ybar_cur = -beta * zbar_next
+        wc = haar_fwd(tape["w"][k], levels)
+        jt, dl = soft_threshold_vjp(wc, lam, haar_fwd(ybar_next, levels))
+        lam_bar += dl
+        wbar = haar_inv(jt, levels)
+        # v_j = N^j wbar, j = 0..d+1
+        vs = [wbar]
+        for _ in range(d + 1):
+            vs.append(nhat(vs[-1]))
+        g = tape["g"][k]
+        for i in range(d + 1):
+            c_bar[i] -= float(np.real(np.vdot(vs[i], g)))
+        zbar = wbar - sum(c[i] * vs[i + 1] for i in range(d + 1))
+        ahb_bar += sum(c[i] * vs[i] for i in range(d + 1))
+        # step back
+        zbar_next = zbar
+        ybar_next = ybar_cur
+    b_bar = forward(ahb_bar) / math.sqrt(L)
+    return b_bar, lam_bar, c_bar

@@ -42,7 +42,8 @@ class pp_sampling(ctypes.Structure):
 
 class pp_solve_info(ctypes.Structure):
     _fields_ = [("rescale", ctypes.c_int), ("levels", ctypes.c_int),
-                ("history", ctypes.c_void_p), ("bnorm", ctypes.c_double), ("L", ctypes.c_double)]
+                ("history", ctypes.c_void_p), ("ref", ctypes.c_void_p),
+                ("bnorm", ctypes.c_double), ("L", ctypes.c_double), ("launches", ctypes.c_int64)]
 
 
 _lib = None
@@ -67,6 +68,23 @@ _SIGS = {
     "pp_fista_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_float, ctypes.c_int,
                                       ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_void_p,
                                       ctypes.POINTER(pp_solve_info), ctypes.c_void_p]),
+    "pp_profile_normal": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                         ctypes.c_int, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_int), ctypes.c_void_p]),
+    "pp_batch_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64,
+                                       ctypes.c_int, ctypes.c_void_p]),
+    "pp_batch_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "pp_batch_offsets": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "pp_batch_scales": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "pp_batch_set_scales": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "pp_batch_tile": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "pp_batch_forward_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "pp_batch_adjoint_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "pp_batch_normal_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "pp_batch_fista_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_float, ctypes.c_int,
+                                            ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_void_p,
+                                            ctypes.POINTER(pp_solve_info), ctypes.c_void_p]),
     "pp_last_error": (ctypes.c_char_p, []),
 }
 
@@ -245,23 +263,163 @@ def pp_prox_l1_haar(shape, levels: int, lam: float, x_in, x_out, stream=None):
                                  _dev_ptr(x_out, "out"), _stream(stream)), "pp_prox_l1_haar")
 
 
+class SolveResult:
+    """What pp_fista_solve reports besides x_out."""
+
+    def __init__(self, history, bnorm, L, launches):
+        self.history = history      # [iters, 3] or None
+        self.bnorm = bnorm
+        self.L = L
+        self.launches = launches
+
+
 def pp_fista_solve(plan: Plan, b, lam: float, iters: int, c, d: int, x_out, stream=None,
-                   history: bool = False, rescale: bool = False, levels: int = 2):
-    """Returns (history array [iters, 2] or None, ||b||, L)."""
+                   history: bool = False, rescale: bool = False, levels: int = 2,
+                   ref=None) -> SolveResult:
+    """c None with d = 0: plain FISTA.  history: per-iteration FP64
+    ||y_{k+1}-y_k||^2, ||y_{k+1}||^2, ||y_{k+1}-ref||^2 (ref optional)."""
     info = pp_solve_info()
     info.rescale = 1 if rescale else 0
     info.levels = int(levels)
     hist = None
     if history:
-        hist = np.zeros((max(iters, 1), 2), dtype=np.float64)
+        hist = np.zeros((max(iters, 1), 3), dtype=np.float64)
         info.history = hist.ctypes.data
     else:
         info.history = None
+    info.ref = _dev_ptr(ref, "ref") if ref is not None else None
     cptr = _cvec(c) if c is not None else None
     _check(lib().pp_fista_solve(plan.handle, _dev_ptr(b, "b"), float(lam), int(iters), cptr, int(d),
                                 _dev_ptr(x_out, "x_out"), ctypes.byref(info), _stream(stream)),
            "pp_fista_solve")
-    return (hist[:iters] if hist is not None else None), info.bnorm, info.L
+    return SolveResult(hist[:iters] if hist is not None else None, info.bnorm, info.L,
+                       int(info.launches))
+
+
+def pp_profile_normal(plan: Plan, x, y, reps: int = 20, stream=None, max_stages: int = 32):
+    """Average milliseconds per normal apply for each kernel (CUDA events)."""
+    names = ctypes.create_string_buffer(48 * max_stages)
+    ms = (ctypes.c_double * max_stages)()
+    n = ctypes.c_int(0)
+    _check(lib().pp_profile_normal(plan.handle, _dev_ptr(x, "x"), _dev_ptr(y, "y"), int(reps),
+                                   int(max_stages), names, ms, ctypes.byref(n), _stream(stream)),
+           "pp_profile_normal")
+    raw = names.raw
+    return {raw[48 * i:48 * i + 48].split(b"\0", 1)[0].decode(): ms[i] for i in range(n.value)}
+
+
+class Batch:
+    """Handle of a pp_batch.  Keeps the borrowed sensitivity tensors alive."""
+
+    def __init__(self, handle, shapes, coils, sens, image_off, kspace_off):
+        self.handle = ctypes.c_void_p(handle)
+        self.shapes = [tuple(s) for s in shapes]
+        self.coils = list(coils)
+        self.image_off = image_off
+        self.kspace_off = kspace_off
+        self._sens = list(sens)
+
+    @property
+    def n(self):
+        return len(self.shapes)
+
+    def destroy(self):
+        if self.handle:
+            _check(lib().pp_batch_destroy(self.handle), "pp_batch_destroy")
+            self.handle = ctypes.c_void_p(0)
+            self._sens = []
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.destroy()
+
+    def __del__(self):
+        try:
+            if self.handle:
+                lib().pp_batch_destroy(self.handle)
+        except Exception:
+            pass
+
+
+def pp_batch_create(shapes, coils, sens, masks, seed: int = 0, power_iters: int = 50,
+                    stream=None) -> Batch:
+    """shapes: list of (ny, nx); coils: list of C_s; sens: list of CUDA
+    complex64 [C_s, ny, nx]; masks: list of uint8 [ny, nx] (constant along x)."""
+    n = len(shapes)
+    dims = (pp_dims * n)(*[_dims(s) for s in shapes])
+    cs = (ctypes.c_int * n)(*[int(c) for c in coils])
+    sp = (ctypes.c_void_p * n)(*[_dev_ptr(t, "sens[%d]" % i) for i, t in enumerate(sens)])
+    ms = [np.ascontiguousarray(m, dtype=np.uint8) for m in masks]
+    mp = (ctypes.c_void_p * n)(*[m.ctypes.data for m in ms])
+    out = ctypes.c_void_p(0)
+    _check(lib().pp_batch_create(ctypes.byref(out), n, dims, cs, sp, mp, ctypes.c_uint64(seed),
+                                 int(power_iters), _stream(stream)), "pp_batch_create")
+    io = np.zeros(n + 1, dtype=np.int64)
+    ko = np.zeros(n + 1, dtype=np.int64)
+    _check(lib().pp_batch_offsets(out, io.ctypes.data, ko.ctypes.data), "pp_batch_offsets")
+    return Batch(out.value, shapes, coils, sens, io, ko)
+
+
+def pp_batch_destroy(batch: Batch):
+    batch.destroy()
+
+
+def pp_batch_offsets(batch: Batch):
+    return batch.image_off.copy(), batch.kspace_off.copy()
+
+
+def pp_batch_scales(batch: Batch) -> np.ndarray:
+    L = np.zeros(batch.n, dtype=np.float64)
+    _check(lib().pp_batch_scales(batch.handle, L.ctypes.data), "pp_batch_scales")
+    return L
+
+
+def pp_batch_set_scales(batch: Batch, L):
+    L = np.ascontiguousarray(L, dtype=np.float64)
+    _check(lib().pp_batch_set_scales(batch.handle, L.ctypes.data), "pp_batch_set_scales")
+
+
+def pp_batch_tile(batch: Batch):
+    a, b = ctypes.c_int(0), ctypes.c_int(0)
+    _check(lib().pp_batch_tile(batch.handle, ctypes.byref(a), ctypes.byref(b)), "pp_batch_tile")
+    return a.value, b.value
+
+
+def pp_batch_forward_apply(batch: Batch, x, y, stream=None):
+    _check(lib().pp_batch_forward_apply(batch.handle, _dev_ptr(x, "x"), _dev_ptr(y, "y"),
+                                        _stream(stream)), "pp_batch_forward_apply")
+
+
+def pp_batch_adjoint_apply(batch: Batch, y, x, stream=None):
+    _check(lib().pp_batch_adjoint_apply(batch.handle, _dev_ptr(y, "y"), _dev_ptr(x, "x"),
+                                        _stream(stream)), "pp_batch_adjoint_apply")
+
+
+def pp_batch_normal_apply(batch: Batch, x, y, stream=None):
+    _check(lib().pp_batch_normal_apply(batch.handle, _dev_ptr(x, "x"), _dev_ptr(y, "y"),
+                                       _stream(stream)), "pp_batch_normal_apply")
+
+
+def pp_batch_fista_solve(batch: Batch, b, lam: float, iters: int, c, d: int, x_out, stream=None,
+                         history: bool = False, rescale: bool = False, ref=None) -> SolveResult:
+    info = pp_solve_info()
+    info.rescale = 1 if rescale else 0
+    info.levels = 2
+    hist = None
+    if history:
+        hist = np.zeros((max(iters, 1), 3), dtype=np.float64)
+        info.history = hist.ctypes.data
+    else:
+        info.history = None
+    info.ref = _dev_ptr(ref, "ref") if ref is not None else None
+    cptr = _cvec(c) if c is not None else None
+    _check(lib().pp_batch_fista_solve(batch.handle, _dev_ptr(b, "b"), float(lam), int(iters), cptr,
+                                      int(d), _dev_ptr(x_out, "x_out"), ctypes.byref(info),
+                                      _stream(stream)), "pp_batch_fista_solve")
+    return SolveResult(hist[:iters] if hist is not None else None, info.bnorm, info.L,
+                       int(info.launches))
 
 
 def pp_last_error() -> str:

@@ -1,0 +1,381 @@
+// Batched kernels for many independent 2-D Cartesian problems of uneven size
+// (one persistent launch per stage over a work list).  Each slice s is its
+// own SENSE problem (Sec. 5.1 operator) with its own L_s; the batch shares
+// the iteration index k of Algorithm "pfista" (Sec. 3.1).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pp_batch.h"
+
+namespace pp {
+
+namespace {
+
+__device__ __forceinline__ void load_table_b(float2* dst, const float2* __restrict__ src, int n) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+}
+
+// Work item (s, col0): columns col0 .. col0 + 2^LGT - 1 of slice s, all coils.
+//   out_s = coef * invL_s * sum_c conj(S_c) F_y^H M_fo F_y (S_c x_s) + alpha * operand_s
+template <int KM, int LGT>
+__global__ void __launch_bounds__(kThreads)
+cart2d_batch_normal_kernel(const SliceDesc* __restrict__ descs, const int2* __restrict__ items,
+                           int nitems, int ny_max, const float2* __restrict__ x,
+                           float2* __restrict__ out, float coef, const float2* __restrict__ operand,
+                           float alpha) {
+    constexpr int T = 1 << LGT;
+    extern __shared__ float2 sm[];
+    float2* tws = sm;
+    float2* b0 = sm + ny_max;
+    float2* b1 = b0 + ny_max * T;
+    float* pm = reinterpret_cast<float*>(b1 + ny_max * T);
+    int cur = -1;
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const int2 item = items[it];
+        const int s = item.x, col0 = item.y;
+        const SliceDesc D = descs[s];
+        const int ny = D.ny, nx = D.nx;
+        if (s != cur) {
+            load_table_b(tws, D.tw, ny);
+            for (int i = threadIdx.x; i < ny; i += blockDim.x) pm[i] = D.mask_fo[i];
+            cur = s;
+        }
+        const float2* xs = x + D.img_off;
+        const int nel = ny * T;
+        float2 xr[KM], sr[KM], acc[KM];
+#pragma unroll
+        for (int k = 0; k < KM; ++k) {
+            const int e = threadIdx.x + k * kThreads;
+            const int yy = e >> LGT;
+            const int col = col0 + (e & (T - 1));
+            xr[k] = (e < nel && col < nx) ? xs[(int64_t)yy * nx + col] : make_float2(0.f, 0.f);
+            acc[k] = make_float2(0.f, 0.f);
+        }
+        const int64_t cs = (int64_t)ny * nx;
+        for (int c = 0; c < D.C; ++c) {
+#pragma unroll
+            for (int k = 0; k < KM; ++k) {
+                const int e = threadIdx.x + k * kThreads;
+                if (e < nel) {
+                    const int yy = e >> LGT;
+                    const int col = col0 + (e & (T - 1));
+                    sr[k] = (col < nx) ? D.sens[c * cs + (int64_t)yy * nx + col] : make_float2(0.f, 0.f);
+                    b0[e] = cmul(sr[k], xr[k]);
+                }
+            }
+            __syncthreads();
+            float2* r1 = fft_batch<false>(b0, b1, D.fd, T, 1, LGT, tws, nullptr);
+            float2* other = (r1 == b0) ? b1 : b0;
+            float2* r2 = fft_batch<true>(r1, other, D.fd, T, 1, LGT, tws, pm);
+#pragma unroll
+            for (int k = 0; k < KM; ++k) {
+                const int e = threadIdx.x + k * kThreads;
+                if (e < nel) acc[k] = cadd(acc[k], cmulc(sr[k], r2[e]));
+            }
+            __syncthreads();
+        }
+        const float sc = coef * D.invL;
+        float2* os = out + D.img_off;
+        const float2* ops = operand ? operand + D.img_off : nullptr;
+#pragma unroll
+        for (int k = 0; k < KM; ++k) {
+            const int e = threadIdx.x + k * kThreads;
+            const int yy = e >> LGT;
+            const int col = col0 + (e & (T - 1));
+            if (e < nel && col < nx) {
+                const int64_t o = (int64_t)yy * nx + col;
+                float2 v = cscale(acc[k], sc);
+                if (ops) v = cadd(v, cscale(ops[o], alpha));
+                os[o] = v;
+            }
+        }
+    }
+}
+
+// Segmented FP64 reduction: block b works on segment seg = blk_seg[b], as
+// block j = b - seg_first_blk[seg] of that segment's nb blocks.
+// partials[b] = (Re<a,b>, Im<a,b>, |b|^2) over the block's share.
+__global__ void __launch_bounds__(kThreads)
+seg_dot_partial_kernel(const float2* __restrict__ a, const float2* __restrict__ bv,
+                       const int64_t* __restrict__ seg_off, const int* __restrict__ blk_seg,
+                       const int* __restrict__ seg_first_blk, double* __restrict__ partials) {
+    const int seg = blk_seg[blockIdx.x];
+    const int j = blockIdx.x - seg_first_blk[seg];
+    const int nb = seg_first_blk[seg + 1] - seg_first_blk[seg];
+    const int64_t lo = seg_off[seg], hi = seg_off[seg + 1];
+    double re = 0.0, im = 0.0, nn = 0.0;
+    for (int64_t i = lo + (int64_t)j * blockDim.x + threadIdx.x; i < hi; i += (int64_t)nb * blockDim.x) {
+        const float2 y = bv[i];
+        if (a) {
+            const float2 x = a[i];
+            re += (double)x.x * y.x + (double)x.y * y.y;
+            im += (double)x.x * y.y - (double)x.y * y.x;
+        }
+        nn += (double)y.x * y.x + (double)y.y * y.y;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        re += __shfl_down_sync(0xffffffffu, re, off);
+        im += __shfl_down_sync(0xffffffffu, im, off);
+        nn += __shfl_down_sync(0xffffffffu, nn, off);
+    }
+    __shared__ double s[3][kThreads / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        s[0][wid] = re;
+        s[1][wid] = im;
+        s[2][wid] = nn;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double r0 = 0, r1 = 0, r2 = 0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+            r0 += s[0][i];
+            r1 += s[1][i];
+            r2 += s[2][i];
+        }
+        partials[3 * blockIdx.x] = r0;
+        partials[3 * blockIdx.x + 1] = r1;
+        partials[3 * blockIdx.x + 2] = r2;
+    }
+}
+
+// One block per segment: out_re[seg*stride], out_nb[seg*stride].
+__global__ void seg_dot_final_kernel(const double* __restrict__ partials,
+                                     const int* __restrict__ seg_first_blk, double* out_re,
+                                     double* out_nb, int stride) {
+    __shared__ double s[2][kThreads];
+    const int seg = blockIdx.x;
+    const int b0 = seg_first_blk[seg], b1 = seg_first_blk[seg + 1];
+    double re = 0.0, nn = 0.0;
+    for (int i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
+        re += partials[3 * i];
+        nn += partials[3 * i + 2];
+    }
+    s[0][threadIdx.x] = re;
+    s[1][threadIdx.x] = nn;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) {
+            s[0][threadIdx.x] += s[0][threadIdx.x + h];
+            s[1][threadIdx.x] += s[1][threadIdx.x + h];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        if (out_re) out_re[seg * stride] = s[0][0];
+        if (out_nb) out_nb[seg * stride] = s[1][0];
+    }
+}
+
+// out = in * factor_seg / sqrt(norm2[seg*stride]) (invert) or * sqrt(...) (not)
+__global__ void seg_scale_kernel(const float2* __restrict__ in, float2* __restrict__ out,
+                                 const int64_t* __restrict__ seg_off, const int* __restrict__ blk_seg,
+                                 const int* __restrict__ seg_first_blk,
+                                 const double* __restrict__ norm2, int stride,
+                                 const double* __restrict__ factor, int invert) {
+    const int seg = blk_seg[blockIdx.x];
+    const int j = blockIdx.x - seg_first_blk[seg];
+    const int nb = seg_first_blk[seg + 1] - seg_first_blk[seg];
+    const int64_t lo = seg_off[seg], hi = seg_off[seg + 1];
+    const double nv = sqrt(norm2[seg * stride]);
+    const double fs = factor ? factor[seg] : 1.0;
+    const float f = (float)(invert ? (nv > 0.0 ? fs / nv : 0.0) : fs * nv);
+    for (int64_t i = lo + (int64_t)j * blockDim.x + threadIdx.x; i < hi; i += (int64_t)nb * blockDim.x)
+        out[i] = cscale(in[i], f);
+}
+
+__device__ __forceinline__ void haar2x2_b(float2& a, float2& b, float2& c, float2& d) {
+    const float2 s0 = cadd(a, b), d0 = csub(a, b), s1 = cadd(c, d), d1 = csub(c, d);
+    a = cscale(cadd(s0, s1), 0.5f);
+    b = cscale(cadd(d0, d1), 0.5f);
+    c = cscale(csub(s0, s1), 0.5f);
+    d = cscale(csub(d0, d1), 0.5f);
+}
+
+__device__ __forceinline__ float2 soft_b(float2 v, float lam) {
+    const float m2 = v.x * v.x + v.y * v.y;
+    if (!(m2 > lam * lam)) return make_float2(0.f, 0.f);
+    return cscale(v, 1.f - lam * rsqrtf(m2));
+}
+
+// 2-level 2-D Haar prox of a 4x4 tile (same transform as the single-plan
+// prox kernel: block transform on 2x2 blocks, then on the four level-1
+// approximation coefficients; each block transform is its own inverse).
+__device__ __forceinline__ void prox44(float2* v, float lam) {
+#pragma unroll
+    for (int by = 0; by < 4; by += 2)
+#pragma unroll
+        for (int bx = 0; bx < 4; bx += 2)
+            haar2x2_b(v[by * 4 + bx], v[by * 4 + bx + 1], v[(by + 1) * 4 + bx], v[(by + 1) * 4 + bx + 1]);
+    haar2x2_b(v[0], v[2], v[8], v[10]);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = soft_b(v[i], lam);
+    haar2x2_b(v[0], v[2], v[8], v[10]);
+#pragma unroll
+    for (int by = 0; by < 4; by += 2)
+#pragma unroll
+        for (int bx = 0; bx < 4; bx += 2)
+            haar2x2_b(v[by * 4 + bx], v[by * 4 + bx + 1], v[(by + 1) * 4 + bx], v[(by + 1) * 4 + bx + 1]);
+}
+
+// Batched fused prox + momentum over 4x4 tiles; block -> slice map as above
+// (segments count tiles).  Statistics are summed over the whole batch.
+__global__ void __launch_bounds__(kThreads)
+batch_prox_fista_kernel(const SliceDesc* __restrict__ descs, const int64_t* __restrict__ tile_off,
+                        const int* __restrict__ blk_seg, const int* __restrict__ seg_first_blk,
+                        float lam, float gamma, float beta, float2* __restrict__ z,
+                        const float2* __restrict__ u, float2* __restrict__ y,
+                        const float2* __restrict__ ref, double* __restrict__ hist) {
+    const int s = blk_seg[blockIdx.x];
+    const int j = blockIdx.x - seg_first_blk[s];
+    const SliceDesc D = descs[s];
+    const int64_t t = (int64_t)j * blockDim.x + threadIdx.x;
+    const int64_t ntl = tile_off[s + 1] - tile_off[s];
+    double dd = 0.0, yy = 0.0, rr = 0.0;
+    if (t < ntl) {
+        const int ntx = D.nx / 4;
+        const int64_t ty = t / ntx, tx = t - ty * ntx;
+        const int64_t o = D.img_off + ty * 4 * D.nx + tx * 4;
+        float2 v[16];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int x = 0; x < 4; ++x) {
+                const int64_t a = o + (int64_t)r * D.nx + x;
+                const float2 zv = z[a], uv = u[a];
+                v[r * 4 + x] = make_float2(zv.x - gamma * uv.x, zv.y - gamma * uv.y);
+            }
+        prox44(v, lam);
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int x = 0; x < 4; ++x) {
+                const int64_t a = o + (int64_t)r * D.nx + x;
+                const float2 yn = v[r * 4 + x];
+                const float2 yo = y[a];
+                const float2 df = csub(yn, yo);
+                z[a] = make_float2(yn.x + beta * df.x, yn.y + beta * df.y);
+                y[a] = yn;
+                dd += (double)df.x * df.x + (double)df.y * df.y;
+                yy += (double)yn.x * yn.x + (double)yn.y * yn.y;
+                if (ref) {
+                    const float2 rv = ref[a];
+                    const double ex = (double)yn.x - rv.x, ey = (double)yn.y - rv.y;
+                    rr += ex * ex + ey * ey;
+                }
+            }
+    }
+    if (hist) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            dd += __shfl_down_sync(0xffffffffu, dd, off);
+            yy += __shfl_down_sync(0xffffffffu, yy, off);
+            rr += __shfl_down_sync(0xffffffffu, rr, off);
+        }
+        __shared__ double sd[kThreads / 32], sy[kThreads / 32], sr[kThreads / 32];
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        if (lane == 0) {
+            sd[wid] = dd;
+            sy[wid] = yy;
+            sr[wid] = rr;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double a = 0.0, b = 0.0, c = 0.0;
+            for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+                a += sd[i];
+                b += sy[i];
+                c += sr[i];
+            }
+            atomicAdd(&hist[0], a);
+            atomicAdd(&hist[1], b);
+            atomicAdd(&hist[2], c);
+        }
+    }
+}
+
+}  // namespace
+
+extern thread_local int64_t g_launches;
+extern thread_local Profiler* g_profiler;
+
+static pp_status check_launch_b(const char* what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_status(e, what);
+    ++g_launches;
+    if (g_profiler) g_profiler->mark(what);
+    return PP_OK;
+}
+
+size_t batch_normal_smem(int ny_max, int lgt) {
+    return sizeof(float2) * (size_t)(ny_max + 2 * ny_max * (1 << lgt)) + sizeof(float) * ny_max;
+}
+
+template <int KM, int LGT>
+static void* batch_kernel_ptr() {
+    return reinterpret_cast<void*>(cart2d_batch_normal_kernel<KM, LGT>);
+}
+
+// kernel pointer for (km, lgt); nullptr when not instantiated
+void* batch_normal_fn(int km, int lgt) {
+#define PP_B(KM_, L_) if (km == KM_ && lgt == L_) return batch_kernel_ptr<KM_, L_>();
+    PP_B(4, 2) PP_B(8, 2)
+    PP_B(4, 3) PP_B(8, 3) PP_B(12, 3)
+    PP_B(4, 4) PP_B(8, 4) PP_B(12, 4) PP_B(16, 4)
+#undef PP_B
+    return nullptr;
+}
+
+pp_status configure_batch_kernels() {
+    const int big = 200 * 1024;
+    const int kms[] = {4, 8, 12, 16};
+    for (int lgt = 2; lgt <= 4; ++lgt)
+        for (int km : kms) {
+            void* f = batch_normal_fn(km, lgt);
+            if (f) PP_TRY_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+        }
+    return PP_OK;
+}
+
+pp_status launch_batch_normal(const BatchDev& b, const float2* x, float2* out, float coef,
+                              const float2* operand, float alpha, cudaStream_t st) {
+    void* fn = batch_normal_fn(b.km, b.lgt);
+    if (!fn) {
+        set_error("no batched kernel for km=%d lgt=%d", b.km, b.lgt);
+        return PP_ERR_UNSUPPORTED;
+    }
+    void* args[] = {(void*)&b.descs, (void*)&b.items, (void*)&b.nitems, (void*)&b.ny_max,
+                    (void*)&x, (void*)&out, (void*)&coef, (void*)&operand, (void*)&alpha};
+    PP_TRY_CUDA(cudaLaunchKernel(fn, dim3(b.grid), dim3(kThreads), args,
+                                 batch_normal_smem(b.ny_max, b.lgt), st));
+    return check_launch_b("cart2d_batch_normal_kernel");
+}
+
+pp_status launch_seg_dot(const float2* a, const float2* bv, const Segments& sg, double* partials,
+                         double* out_re, double* out_nb, int stride, cudaStream_t st) {
+    seg_dot_partial_kernel<<<sg.nblocks, kThreads, 0, st>>>(a, bv, sg.off, sg.blk_seg,
+                                                             sg.seg_first_blk, partials);
+    PP_TRY(check_launch_b("seg_dot_partial_kernel"));
+    seg_dot_final_kernel<<<sg.nseg, kThreads, 0, st>>>(partials, sg.seg_first_blk, out_re, out_nb,
+                                                        stride);
+    return check_launch_b("seg_dot_final_kernel");
+}
+
+pp_status launch_seg_scale(const float2* in, float2* out, const Segments& sg, const double* norm2,
+                           int stride, const double* factor, int invert, cudaStream_t st) {
+    seg_scale_kernel<<<sg.nblocks, kThreads, 0, st>>>(in, out, sg.off, sg.blk_seg, sg.seg_first_blk,
+                                                       norm2, stride, factor, invert);
+    return check_launch_b("seg_scale_kernel");
+}
+
+pp_status launch_batch_prox_fista(const BatchDev& b, float lam, float gamma, float beta,
+                                  float2* z, const float2* u, float2* y, const float2* ref,
+                                  double* hist, cudaStream_t st) {
+    batch_prox_fista_kernel<<<b.tiles.nblocks, kThreads, 0, st>>>(
+        b.descs, b.tiles.off, b.tiles.blk_seg, b.tiles.seg_first_blk, lam, gamma, beta, z, u, y, ref,
+        hist);
+    return check_launch_b("batch_prox_fista_kernel");
+}
+
+}  // namespace pp

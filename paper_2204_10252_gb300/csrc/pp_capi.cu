@@ -11,6 +11,7 @@
 #include <string>
 #include <vector>
 
+#include "pp_batch.h"
 #include "pp_internal.h"
 
 namespace pp {
@@ -283,7 +284,9 @@ static pp_status build_cartesian(Plan& p, const uint8_t* mask) {
     PP_TRY(make_fft(p, nx, p.fx));
     PP_TRY(make_fft(p, ny, p.fy));
     if (p.ndim == 3) PP_TRY(make_fft(p, nz, p.fz));
-    if (p.ndim == 2) {
+    if (p.external_wk) {
+        // workspace set by the owner
+    } else if (p.ndim == 2) {
         PP_TRY(alloc_n(p, &p.wk_a, (size_t)p.C * p.nimg));
     } else {
         PP_TRY(alloc_n(p, &p.wk_a, (size_t)p.nimg));
@@ -444,7 +447,7 @@ static pp_status horner_into(const Plan& p, const double* c, int d, const float2
 }
 
 static pp_status fista_iterations(Plan& p, float lambda, int iters, const double* c, int d,
-                                  int levels, bool hist, cudaStream_t st) {
+                                  int levels, bool hist, const float2* ref, cudaStream_t st) {
     const float invL = (float)(1.0 / p.L);
     for (int k = 0; k < iters; ++k) {
         // g = N_hat z - A_hat^H b_hat
@@ -458,7 +461,214 @@ static pp_status fista_iterations(Plan& p, float lambda, int iters, const double
             gamma = (float)c[0];
         }
         const float beta = (float)((double)k / (k + 3.0));
-        PP_TRY(launch_prox_fista(p, levels, lambda, gamma, beta, u, hist ? p.hist + 2 * k : nullptr, st));
+        PP_TRY(launch_prox_fista(p, levels, lambda, gamma, beta, u, hist ? ref : nullptr,
+                                 hist ? p.hist + 3 * k : nullptr, st));
+    }
+    return PP_OK;
+}
+
+
+// ---------------------------------------------------------------------------
+// Batched uneven 2-D Cartesian problems
+// ---------------------------------------------------------------------------
+struct Batch {
+    int n = 0;
+    std::vector<Plan*> sub;
+    std::vector<int64_t> img_off, ksp_off, tile_off;
+    int64_t nimg = 0, nksp = 0;
+    std::vector<double> L;
+    std::vector<SliceDesc> hdesc;
+    BatchDev dev;
+    std::vector<void*> allocs;
+    float2 *z = nullptr, *y = nullptr, *g = nullptr, *u = nullptr, *t = nullptr, *ahb = nullptr,
+           *v = nullptr, *w3 = nullptr, *wk = nullptr;
+    double *partials = nullptr, *scal = nullptr, *dfac = nullptr, *hist = nullptr;
+    int hist_cap = 0;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<double> gkey;
+    int64_t graph_kernels = 0;
+};
+
+template <class T>
+static pp_status balloc(Batch& b, T** ptr, size_t n) {
+    *ptr = nullptr;
+    if (n == 0) return PP_OK;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(ptr), n * sizeof(T));
+    if (e != cudaSuccess) {
+        *ptr = nullptr;
+        cudaGetLastError();
+        return cuda_status(e, "cudaMalloc");
+    }
+    b.allocs.push_back(*ptr);
+    return PP_OK;
+}
+
+template <class T>
+static pp_status bupload(Batch& b, T** dst, const std::vector<T>& src) {
+    PP_TRY(balloc(b, dst, src.size()));
+    PP_TRY_CUDA(cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return PP_OK;
+}
+
+// blocks per segment: ceil(len / per_block) clamped to [1, max_blocks]
+static pp_status make_segments(Batch& b, Segments& sg, const std::vector<int64_t>& off,
+                               int64_t per_block, int max_blocks) {
+    const int nseg = (int)off.size() - 1;
+    std::vector<int> blk_seg, first(nseg + 1, 0);
+    for (int s = 0; s < nseg; ++s) {
+        const int64_t len = off[s + 1] - off[s];
+        int64_t nb = (len + per_block - 1) / per_block;
+        nb = std::max<int64_t>(1, std::min<int64_t>(nb, max_blocks));
+        first[s] = (int)blk_seg.size();
+        for (int64_t j = 0; j < nb; ++j) blk_seg.push_back(s);
+    }
+    first[nseg] = (int)blk_seg.size();
+    sg.nseg = nseg;
+    sg.nblocks = (int)blk_seg.size();
+    PP_TRY(bupload(b, &sg.off, off));
+    PP_TRY(bupload(b, &sg.blk_seg, blk_seg));
+    PP_TRY(bupload(b, &sg.seg_first_blk, first));
+    return PP_OK;
+}
+
+static int km_for(int ny_max, int lgt) {
+    const int need = (ny_max * (1 << lgt) + kThreads - 1) / kThreads;
+    const int kms[] = {4, 8, 12, 16};
+    for (int km : kms)
+        if (need <= km && batch_normal_fn(km, lgt)) return km;
+    return 0;
+}
+
+// Work items (slice, first column) for column tiles of 2^lgt, most expensive
+// first so that the persistent grid's round-robin balances the load.
+static pp_status set_items(Batch& b, int lgt, std::vector<int2>* scratch) {
+    const int T = 1 << lgt;
+    std::vector<std::pair<double, int2>> it;
+    for (int s = 0; s < b.n; ++s) {
+        const SliceDesc& d = b.hdesc[s];
+        const double cost = (double)d.C * d.ny * log2((double)d.ny);
+        for (int c0 = 0; c0 < d.nx; c0 += T) it.push_back({cost, make_int2(s, c0)});
+    }
+    std::stable_sort(it.begin(), it.end(),
+                     [](const std::pair<double, int2>& a, const std::pair<double, int2>& c) {
+                         return a.first > c.first;
+                     });
+    scratch->clear();
+    for (auto& e : it) scratch->push_back(e.second);
+    if (b.dev.items) {
+        cudaFree(b.dev.items);
+        b.allocs.erase(std::remove(b.allocs.begin(), b.allocs.end(), (void*)b.dev.items), b.allocs.end());
+        b.dev.items = nullptr;
+    }
+    PP_TRY(bupload(b, &b.dev.items, *scratch));
+    b.dev.nitems = (int)scratch->size();
+    b.dev.lgt = lgt;
+    b.dev.km = km_for(b.dev.ny_max, lgt);
+    int occ = 0;
+    PP_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &occ, batch_normal_fn(b.dev.km, lgt), kThreads, batch_normal_smem(b.dev.ny_max, lgt)));
+    int nsm = 0;
+    PP_TRY_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, 0));
+    b.dev.grid = std::max(1, std::min(b.dev.nitems, nsm * std::max(occ, 1)));
+    return PP_OK;
+}
+
+static pp_status upload_descs(Batch& b) {
+    for (int s = 0; s < b.n; ++s) b.hdesc[s].invL = (float)(1.0 / b.L[s]);
+    PP_TRY_CUDA(cudaMemcpy(b.dev.descs, b.hdesc.data(), b.n * sizeof(SliceDesc), cudaMemcpyHostToDevice));
+    std::vector<double> f(b.n);
+    for (int s = 0; s < b.n; ++s) f[s] = 1.0 / sqrt(b.L[s]);
+    PP_TRY_CUDA(cudaMemcpy(b.dfac, f.data(), b.n * sizeof(double), cudaMemcpyHostToDevice));
+    b.gkey.clear();
+    return PP_OK;
+}
+
+// Column-tile autotuner: time each feasible tile width on the batch itself
+// and keep the fastest.
+static pp_status autotune(Batch& b, cudaStream_t st) {
+    std::vector<int2> items;
+    int best = -1;
+    float best_ms = 1e30f;
+    cudaEvent_t e0, e1;
+    PP_TRY_CUDA(cudaEventCreate(&e0));
+    PP_TRY_CUDA(cudaEventCreate(&e1));
+    for (int lgt = 2; lgt <= 4; ++lgt) {
+        if (!km_for(b.dev.ny_max, lgt)) continue;
+        PP_TRY(set_items(b, lgt, &items));
+        PP_TRY(launch_batch_normal(b.dev, b.v, b.t, 1.f, nullptr, 0.f, st));
+        PP_TRY_CUDA(cudaEventRecord(e0, st));
+        for (int r = 0; r < 3; ++r) PP_TRY(launch_batch_normal(b.dev, b.v, b.t, 1.f, nullptr, 0.f, st));
+        PP_TRY_CUDA(cudaEventRecord(e1, st));
+        PP_TRY_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = lgt;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (best < 0) {
+        set_error("no batched kernel fits ny_max = %d", b.dev.ny_max);
+        return PP_ERR_UNSUPPORTED;
+    }
+    return set_items(b, best, &items);
+}
+
+static pp_status batch_power_iteration(Batch& b, uint64_t seed, int iters, cudaStream_t st) {
+    for (int s = 0; s < b.n; ++s)
+        PP_TRY(launch_start_vector(b.v + b.img_off[s], b.img_off[s + 1] - b.img_off[s], seed + s, st));
+    PP_TRY(launch_seg_dot(nullptr, b.v, b.dev.img, b.partials, nullptr, b.scal + 2, 4, st));
+    PP_TRY(launch_seg_scale(b.v, b.v, b.dev.img, b.scal + 2, 4, nullptr, 1, st));
+    for (int it = 0; it < iters; ++it) {
+        PP_TRY(launch_batch_normal(b.dev, b.v, b.t, 1.f, nullptr, 0.f, st));
+        PP_TRY(launch_seg_dot(b.v, b.t, b.dev.img, b.partials, b.scal + 1, b.scal + 2, 4, st));
+        PP_TRY(launch_seg_scale(b.t, b.v, b.dev.img, b.scal + 2, 4, nullptr, 1, st));
+    }
+    std::vector<double> h(4 * b.n);
+    PP_TRY_CUDA(cudaMemcpyAsync(h.data(), b.scal, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    PP_TRY_CUDA(cudaStreamSynchronize(st));
+    for (int s = 0; s < b.n; ++s) {
+        if (!(h[4 * s + 1] > 0.0) || !isfinite(h[4 * s + 1])) {
+            set_error("power iteration: non-positive estimate for slice %d", s);
+            return PP_ERR_NONFINITE;
+        }
+        b.L[s] = h[4 * s + 1];
+    }
+    return upload_descs(b);
+}
+
+static pp_status batch_horner(Batch& b, const double* c, int d, const float2* v, float2* out,
+                              cudaStream_t st) {
+    if (d == 0) return launch_axpby(v, (float)c[0], nullptr, 0.f, out, b.nimg, st);
+    const float2* cur = v;
+    float coef = (float)c[d];
+    for (int i = d - 1; i >= 0; --i) {
+        float2* dst = (i == 0) ? out : ((cur == b.t) ? b.w3 : b.t);
+        PP_TRY(launch_batch_normal(b.dev, cur, dst, coef, v, (float)c[i], st));
+        cur = dst;
+        coef = 1.f;
+    }
+    return PP_OK;
+}
+
+static pp_status batch_iterations(Batch& b, float lambda, int iters, const double* c, int d,
+                                  bool hist, const float2* ref, cudaStream_t st) {
+    for (int k = 0; k < iters; ++k) {
+        PP_TRY(launch_batch_normal(b.dev, b.z, b.g, 1.f, b.ahb, -1.f, st));
+        const float2* u = b.g;
+        float gamma = 1.f;
+        if (c && d >= 1) {
+            PP_TRY(batch_horner(b, c, d, b.g, b.u, st));
+            u = b.u;
+        } else if (c) {
+            gamma = (float)c[0];
+        }
+        const float beta = (float)((double)k / (k + 3.0));
+        PP_TRY(launch_batch_prox_fista(b.dev, lambda, gamma, beta, b.z, u, b.y, hist ? ref : nullptr,
+                                       hist ? b.hist + 3 * k : nullptr, st));
     }
     return PP_OK;
 }
@@ -715,7 +925,9 @@ pp_status pp_fista_solve(pp_plan* plan, const pp_c64* b, float lambda, int iters
         return PP_ERR_UNSUPPORTED;
     }
     const bool hist = info && info->history;
+    const float2* ref = info ? reinterpret_cast<const float2*>(info->ref) : nullptr;
     const int64_t n = p.nimg;
+    const int64_t launches0 = g_launches;
     // A_hat^H b_hat = A^H b / (sqrt(L) ||b||)
     PP_TRY(launch_norm2(reinterpret_cast<const float2*>(b), p.nksp, p.red, p.red_blocks, p.scal + 0, st));
     PP_TRY(adjoint_into(p, reinterpret_cast<const float2*>(b), p.ahb, st));
@@ -730,16 +942,16 @@ pp_status pp_fista_solve(pp_plan* plan, const pp_c64* b, float lambda, int iters
                 p.allocs.erase(std::remove(p.allocs.begin(), p.allocs.end(), (void*)p.hist), p.allocs.end());
                 p.hist = nullptr;
             }
-            PP_TRY(alloc_n(p, &p.hist, (size_t)2 * std::max(iters, 1)));
+            PP_TRY(alloc_n(p, &p.hist, (size_t)3 * std::max(iters, 1)));
             p.hist_cap = iters;
             p.gkey.clear();
         }
-        PP_TRY_CUDA(cudaMemsetAsync(p.hist, 0, sizeof(double) * 2 * std::max(iters, 1), st));
+        PP_TRY_CUDA(cudaMemsetAsync(p.hist, 0, sizeof(double) * 3 * std::max(iters, 1), st));
     }
     if (iters > 0) {
         std::vector<double> key = {(double)iters, (double)d, (double)lambda, (double)levels,
                                    hist ? 1.0 : 0.0, c ? 1.0 : 0.0, p.L,
-                                   (double)(uintptr_t)p.hist};
+                                   (double)(uintptr_t)p.hist, (double)(uintptr_t)ref};
         if (c)
             for (int i = 0; i <= d; ++i) key.push_back(c[i]);
         if (!p.gexec || key != p.gkey) {
@@ -750,8 +962,11 @@ pp_status pp_fista_solve(pp_plan* plan, const pp_c64* b, float lambda, int iters
             p.gkey.clear();
             cudaGraph_t graph = nullptr;
             PP_TRY_CUDA(cudaStreamBeginCapture(p.cap_stream, cudaStreamCaptureModeThreadLocal));
-            pp_status rc = fista_iterations(p, lambda, iters, c, d, levels, hist, p.cap_stream);
+            const int64_t before = g_launches;
+            pp_status rc = fista_iterations(p, lambda, iters, c, d, levels, hist, ref, p.cap_stream);
             cudaError_t e = cudaStreamEndCapture(p.cap_stream, &graph);
+            p.graph_kernels = g_launches - before;
+            g_launches = before;
             if (rc != PP_OK) {
                 if (graph) cudaGraphDestroy(graph);
                 return rc;
@@ -774,13 +989,369 @@ pp_status pp_fista_solve(pp_plan* plan, const pp_c64* b, float lambda, int iters
         PP_TRY_CUDA(cudaMemcpyAsync(xo, p.y, n * sizeof(float2), cudaMemcpyDeviceToDevice, st));
     if (info) {
         info->L = p.L;
+        info->launches = (g_launches - launches0) + (iters > 0 ? p.graph_kernels : 0);
         if (hist) {
             double bn2 = 0.0;
             PP_TRY_CUDA(cudaMemcpyAsync(&bn2, p.scal + 0, sizeof(double), cudaMemcpyDeviceToHost, st));
-            PP_TRY_CUDA(cudaMemcpyAsync(info->history, p.hist, sizeof(double) * 2 * iters,
+            PP_TRY_CUDA(cudaMemcpyAsync(info->history, p.hist, sizeof(double) * 3 * iters,
                                         cudaMemcpyDeviceToHost, st));
             PP_TRY_CUDA(cudaStreamSynchronize(st));
             info->bnorm = sqrt(bn2);
+        }
+    }
+    return PP_OK;
+}
+
+pp_status pp_profile_normal(const pp_plan* plan, const pp_c64* x, pp_c64* y, int reps,
+                            int max_stages, char* names, double* ms, int* nstages,
+                            pp_stream stream) {
+    if (!plan || !x || !y || reps < 1 || max_stages < 1 || !names || !ms || !nstages ||
+        (const void*)x == (const void*)y) {
+        set_error("pp_profile_normal: bad argument");
+        return PP_ERR_INVALID_ARG;
+    }
+    const Plan& p = plan->impl;
+    cudaStream_t st = (cudaStream_t)stream;
+    Profiler prof;
+    prof.st = st;
+    cudaEvent_t start;
+    PP_TRY_CUDA(cudaEventCreate(&start));
+    PP_TRY_CUDA(cudaEventRecord(start, st));
+    g_profiler = &prof;
+    pp_status rc = PP_OK;
+    for (int r = 0; r < reps && rc == PP_OK; ++r)
+        rc = normal_into(p, reinterpret_cast<const float2*>(x), reinterpret_cast<float2*>(y),
+                         (float)(1.0 / p.L), nullptr, 0.f, st);
+    g_profiler = nullptr;
+    cudaError_t e = cudaStreamSynchronize(st);
+    std::vector<std::string> uniq;
+    std::vector<double> tot;
+    if (rc == PP_OK && e == cudaSuccess) {
+        cudaEvent_t prev = start;
+        for (size_t i = 0; i < prof.events.size(); ++i) {
+            float t = 0.f;
+            cudaEventElapsedTime(&t, prev, prof.events[i]);
+            prev = prof.events[i];
+            size_t j = std::find(uniq.begin(), uniq.end(), prof.names[i]) - uniq.begin();
+            if (j == uniq.size()) {
+                uniq.push_back(prof.names[i]);
+                tot.push_back(0.0);
+            }
+            tot[j] += t;
+        }
+    }
+    for (cudaEvent_t ev : prof.events) cudaEventDestroy(ev);
+    cudaEventDestroy(start);
+    if (rc != PP_OK) return rc;
+    if (e != cudaSuccess) return cuda_status(e, "pp_profile_normal sync");
+    const int ns = std::min((int)uniq.size(), max_stages);
+    for (int i = 0; i < ns; ++i) {
+        strncpy(names + 48 * i, uniq[i].c_str(), 47);
+        names[48 * i + 47] = 0;
+        ms[i] = tot[i] / reps;
+    }
+    *nstages = ns;
+    return PP_OK;
+}
+
+struct pp_batch {
+    Batch impl;
+};
+
+pp_status pp_batch_create(pp_batch** out, int nslices, const pp_dims* dims, const int* coils,
+                          const pp_c64* const* sens, const uint8_t* const* masks, uint64_t seed,
+                          int power_iters, pp_stream stream) {
+    if (!out) {
+        set_error("pp_batch_create: out is NULL");
+        return PP_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    if (nslices < 1 || nslices > 4096 || !dims || !coils || !sens || !masks || power_iters < 0) {
+        set_error("pp_batch_create: bad argument");
+        return PP_ERR_INVALID_ARG;
+    }
+    for (int s = 0; s < nslices; ++s) {
+        const pp_dims& d = dims[s];
+        if (d.ndim != 2) {
+            set_error("pp_batch_create: slice %d is not 2-D", s);
+            return PP_ERR_UNSUPPORTED;
+        }
+        const int nx = d.n[0], ny = d.n[1];
+        if (nx < 4 || ny < 4 || nx > 512 || ny > 512 || (nx % 4) || (ny % 4) || coils[s] < 1 ||
+            coils[s] > 64 || !sens[s] || !masks[s]) {
+            set_error("pp_batch_create: slice %d has a bad size, coil count or pointer", s);
+            return PP_ERR_INVALID_ARG;
+        }
+        if (!fft_len_ok(nx) || !fft_len_ok(ny)) {
+            set_error("pp_batch_create: slice %d FFT length has a prime factor above 5", s);
+            return PP_ERR_UNSUPPORTED;
+        }
+    }
+    static std::once_flag once;
+    static pp_status cfg = PP_OK;
+    std::call_once(once, [] {
+        cfg = configure_kernels();
+        if (cfg == PP_OK) cfg = configure_batch_kernels();
+    });
+    if (cfg != PP_OK) return cfg;
+    cudaStream_t st = (cudaStream_t)stream;
+    pp_batch* h = new pp_batch();
+    Batch& b = h->impl;
+    b.n = nslices;
+    b.img_off.assign(nslices + 1, 0);
+    b.ksp_off.assign(nslices + 1, 0);
+    b.tile_off.assign(nslices + 1, 0);
+    b.L.assign(nslices, 1.0);
+    b.hdesc.resize(nslices);
+    pp_status rc = PP_OK;
+    size_t wk_max = 0;
+    for (int s = 0; s < nslices && rc == PP_OK; ++s) {
+        Plan* p = new Plan();
+        b.sub.push_back(p);
+        p->ndim = 2; p->nx = dims[s].n[0]; p->ny = dims[s].n[1]; p->nz = 1; p->C = coils[s];
+        p->kind = PP_CARTESIAN;
+        p->nimg = (int64_t)p->nx * p->ny;
+        p->sens = reinterpret_cast<const float2*>(sens[s]);
+        p->external_wk = true;
+        rc = build_cartesian(*p, masks[s]);
+        if (rc != PP_OK) break;
+        wk_max = std::max(wk_max, (size_t)p->C * p->nimg);
+        b.img_off[s + 1] = b.img_off[s] + p->nimg;
+        b.ksp_off[s + 1] = b.ksp_off[s] + p->nksp;
+        b.tile_off[s + 1] = b.tile_off[s] + p->nimg / 16;
+        SliceDesc& d = b.hdesc[s];
+        d.fd = p->fy.d; d.tw = p->fy.tw; d.sens = p->sens; d.mask_fo = p->mask_fo;
+        d.ny = p->ny; d.nx = p->nx; d.C = p->C; d.pad0 = 0; d.img_off = b.img_off[s];
+        d.invL = 1.f; d.pad1 = 0.f;
+        b.dev.ny_max = std::max(b.dev.ny_max, p->ny);
+    }
+    b.nimg = b.img_off[nslices];
+    b.nksp = b.ksp_off[nslices];
+    if (rc == PP_OK) rc = balloc(b, &b.wk, wk_max);
+    if (rc == PP_OK)
+        for (Plan* p : b.sub) p->wk_a = b.wk;
+    const size_t n = (size_t)b.nimg;
+    if (rc == PP_OK && (rc = balloc(b, &b.z, n)) == PP_OK && (rc = balloc(b, &b.y, n)) == PP_OK &&
+        (rc = balloc(b, &b.g, n)) == PP_OK && (rc = balloc(b, &b.u, n)) == PP_OK &&
+        (rc = balloc(b, &b.t, n)) == PP_OK && (rc = balloc(b, &b.ahb, n)) == PP_OK &&
+        (rc = balloc(b, &b.v, n)) == PP_OK && (rc = balloc(b, &b.w3, n)) == PP_OK &&
+        (rc = balloc(b, &b.scal, (size_t)4 * nslices)) == PP_OK &&
+        (rc = balloc(b, &b.dfac, (size_t)nslices)) == PP_OK &&
+        (rc = balloc(b, &b.dev.descs, (size_t)nslices)) == PP_OK &&
+        (rc = make_segments(b, b.dev.img, b.img_off, (int64_t)kThreads * 8, 64)) == PP_OK &&
+        (rc = make_segments(b, b.dev.ksp, b.ksp_off, (int64_t)kThreads * 8, 64)) == PP_OK &&
+        (rc = make_segments(b, b.dev.tiles, b.tile_off, (int64_t)kThreads, 1 << 30)) == PP_OK) {
+        const int nb = std::max(b.dev.img.nblocks, b.dev.ksp.nblocks);
+        rc = balloc(b, &b.partials, (size_t)3 * nb);
+    }
+    if (rc == PP_OK) {
+        cudaError_t e = cudaStreamCreateWithFlags(&b.cap_stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) rc = cuda_status(e, "cudaStreamCreate");
+    }
+    if (rc == PP_OK) rc = upload_descs(b);
+    if (rc == PP_OK) {
+        cudaError_t e = cudaMemsetAsync(b.v, 0, n * sizeof(float2), st);
+        if (e != cudaSuccess) rc = cuda_status(e, "cudaMemsetAsync");
+    }
+    if (rc == PP_OK) rc = autotune(b, st);
+    if (rc == PP_OK && power_iters > 0) rc = batch_power_iteration(b, seed, power_iters, st);
+    if (rc != PP_OK) {
+        cudaStreamSynchronize(st);
+        if (b.gexec) cudaGraphExecDestroy(b.gexec);
+        if (b.cap_stream) cudaStreamDestroy(b.cap_stream);
+        for (Plan* p : b.sub) {
+            for (void* a : p->allocs) cudaFree(a);
+            delete p;
+        }
+        for (void* a : b.allocs) cudaFree(a);
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return PP_OK;
+}
+
+pp_status pp_batch_destroy(pp_batch* batch) {
+    if (!batch) return PP_OK;
+    Batch& b = batch->impl;
+    if (b.gexec) cudaGraphExecDestroy(b.gexec);
+    if (b.cap_stream) cudaStreamDestroy(b.cap_stream);
+    for (Plan* p : b.sub) {
+        for (void* a : p->allocs) cudaFree(a);
+        delete p;
+    }
+    for (void* a : b.allocs) cudaFree(a);
+    delete batch;
+    return PP_OK;
+}
+
+pp_status pp_batch_offsets(const pp_batch* batch, int64_t* image_off, int64_t* kspace_off) {
+    if (!batch) {
+        set_error("pp_batch_offsets: NULL batch");
+        return PP_ERR_INVALID_ARG;
+    }
+    const Batch& b = batch->impl;
+    for (int s = 0; s <= b.n; ++s) {
+        if (image_off) image_off[s] = b.img_off[s];
+        if (kspace_off) kspace_off[s] = b.ksp_off[s];
+    }
+    return PP_OK;
+}
+
+pp_status pp_batch_scales(const pp_batch* batch, double* L) {
+    if (!batch || !L) {
+        set_error("pp_batch_scales: NULL argument");
+        return PP_ERR_INVALID_ARG;
+    }
+    for (int s = 0; s < batch->impl.n; ++s) L[s] = batch->impl.L[s];
+    return PP_OK;
+}
+
+pp_status pp_batch_set_scales(pp_batch* batch, const double* L) {
+    if (!batch || !L) {
+        set_error("pp_batch_set_scales: NULL argument");
+        return PP_ERR_INVALID_ARG;
+    }
+    Batch& b = batch->impl;
+    for (int s = 0; s < b.n; ++s)
+        if (!(L[s] > 0.0) || !isfinite(L[s])) {
+            set_error("pp_batch_set_scales: L[%d] must be finite and > 0", s);
+            return PP_ERR_INVALID_ARG;
+        }
+    for (int s = 0; s < b.n; ++s) {
+        b.L[s] = L[s];
+        b.sub[s]->L = L[s];
+    }
+    return upload_descs(b);
+}
+
+pp_status pp_batch_tile(const pp_batch* batch, int* cols_per_cta, int* persistent_ctas) {
+    if (!batch) {
+        set_error("pp_batch_tile: NULL batch");
+        return PP_ERR_INVALID_ARG;
+    }
+    if (cols_per_cta) *cols_per_cta = 1 << batch->impl.dev.lgt;
+    if (persistent_ctas) *persistent_ctas = batch->impl.dev.grid;
+    return PP_OK;
+}
+
+pp_status pp_batch_forward_apply(const pp_batch* batch, const pp_c64* x, pp_c64* y, pp_stream stream) {
+    if (!batch || !x || !y) {
+        set_error("pp_batch_forward_apply: NULL argument");
+        return PP_ERR_INVALID_ARG;
+    }
+    const Batch& b = batch->impl;
+    for (int s = 0; s < b.n; ++s)
+        PP_TRY(forward_into(*b.sub[s], reinterpret_cast<const float2*>(x) + b.img_off[s],
+                            reinterpret_cast<float2*>(y) + b.ksp_off[s], (cudaStream_t)stream));
+    return PP_OK;
+}
+
+pp_status pp_batch_adjoint_apply(const pp_batch* batch, const pp_c64* y, pp_c64* x, pp_stream stream) {
+    if (!batch || !x || !y) {
+        set_error("pp_batch_adjoint_apply: NULL argument");
+        return PP_ERR_INVALID_ARG;
+    }
+    const Batch& b = batch->impl;
+    for (int s = 0; s < b.n; ++s)
+        PP_TRY(adjoint_into(*b.sub[s], reinterpret_cast<const float2*>(y) + b.ksp_off[s],
+                            reinterpret_cast<float2*>(x) + b.img_off[s], (cudaStream_t)stream));
+    return PP_OK;
+}
+
+pp_status pp_batch_normal_apply(const pp_batch* batch, const pp_c64* x, pp_c64* y, pp_stream stream) {
+    if (!batch || !x || !y || (const void*)x == (const void*)y) {
+        set_error("pp_batch_normal_apply: NULL or aliased argument");
+        return PP_ERR_INVALID_ARG;
+    }
+    return launch_batch_normal(batch->impl.dev, reinterpret_cast<const float2*>(x),
+                               reinterpret_cast<float2*>(y), 1.f, nullptr, 0.f, (cudaStream_t)stream);
+}
+
+pp_status pp_batch_fista_solve(pp_batch* batch, const pp_c64* bk, float lambda, int iters,
+                               const double* c, int d, pp_c64* x_out, pp_solve_info* info,
+                               pp_stream stream) {
+    if (!batch || !bk || !x_out || iters < 0 || iters > 1000000 || !(lambda >= 0.f) ||
+        !isfinite(lambda) || d < 0 || d > 16 || (!c && d != 0)) {
+        set_error("pp_batch_fista_solve: bad argument");
+        return PP_ERR_INVALID_ARG;
+    }
+    if (info && info->levels && info->levels != 2) {
+        set_error("pp_batch_fista_solve: batched prox supports 2 Haar levels only");
+        return PP_ERR_UNSUPPORTED;
+    }
+    Batch& b = batch->impl;
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool hist = info && info->history;
+    const float2* ref = info ? reinterpret_cast<const float2*>(info->ref) : nullptr;
+    const int64_t launches0 = g_launches;
+    const float2* bd = reinterpret_cast<const float2*>(bk);
+    PP_TRY(launch_seg_dot(nullptr, bd, b.dev.ksp, b.partials, nullptr, b.scal + 0, 4, st));
+    for (int s = 0; s < b.n; ++s)
+        PP_TRY(adjoint_into(*b.sub[s], bd + b.ksp_off[s], b.ahb + b.img_off[s], st));
+    PP_TRY(launch_seg_scale(b.ahb, b.ahb, b.dev.img, b.scal + 0, 4, b.dfac, 1, st));
+    PP_TRY_CUDA(cudaMemsetAsync(b.y, 0, b.nimg * sizeof(float2), st));
+    PP_TRY_CUDA(cudaMemsetAsync(b.z, 0, b.nimg * sizeof(float2), st));
+    if (hist) {
+        if (b.hist_cap < iters) {
+            if (b.hist) {
+                cudaStreamSynchronize(st);
+                cudaFree(b.hist);
+                b.allocs.erase(std::remove(b.allocs.begin(), b.allocs.end(), (void*)b.hist), b.allocs.end());
+                b.hist = nullptr;
+            }
+            PP_TRY(balloc(b, &b.hist, (size_t)3 * std::max(iters, 1)));
+            b.hist_cap = iters;
+            b.gkey.clear();
+        }
+        PP_TRY_CUDA(cudaMemsetAsync(b.hist, 0, sizeof(double) * 3 * std::max(iters, 1), st));
+    }
+    if (iters > 0) {
+        std::vector<double> key = {(double)iters, (double)d, (double)lambda, hist ? 1.0 : 0.0,
+                                   c ? 1.0 : 0.0, (double)(uintptr_t)b.hist, (double)(uintptr_t)ref,
+                                   (double)b.dev.lgt};
+        if (c)
+            for (int i = 0; i <= d; ++i) key.push_back(c[i]);
+        if (!b.gexec || key != b.gkey) {
+            if (b.gexec) {
+                cudaGraphExecDestroy(b.gexec);
+                b.gexec = nullptr;
+            }
+            b.gkey.clear();
+            cudaGraph_t graph = nullptr;
+            PP_TRY_CUDA(cudaStreamBeginCapture(b.cap_stream, cudaStreamCaptureModeThreadLocal));
+            const int64_t before = g_launches;
+            pp_status rc = batch_iterations(b, lambda, iters, c, d, hist, ref, b.cap_stream);
+            cudaError_t e = cudaStreamEndCapture(b.cap_stream, &graph);
+            b.graph_kernels = g_launches - before;
+            g_launches = before;
+            if (rc != PP_OK) {
+                if (graph) cudaGraphDestroy(graph);
+                return rc;
+            }
+            if (e != cudaSuccess) return cuda_status(e, "cudaStreamEndCapture");
+            e = cudaGraphInstantiate(&b.gexec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) {
+                b.gexec = nullptr;
+                return cuda_status(e, "cudaGraphInstantiate");
+            }
+            b.gkey = key;
+        }
+        PP_TRY_CUDA(cudaGraphLaunch(b.gexec, st));
+    }
+    float2* xo = reinterpret_cast<float2*>(x_out);
+    if (info && info->rescale)
+        PP_TRY(launch_seg_scale(b.y, xo, b.dev.img, b.scal + 0, 4, b.dfac, 0, st));
+    else
+        PP_TRY_CUDA(cudaMemcpyAsync(xo, b.y, b.nimg * sizeof(float2), cudaMemcpyDeviceToDevice, st));
+    if (info) {
+        info->L = b.L[0];
+        info->launches = (g_launches - launches0) + (iters > 0 ? b.graph_kernels : 0);
+        if (hist) {
+            PP_TRY_CUDA(cudaMemcpyAsync(info->history, b.hist, sizeof(double) * 3 * iters,
+                                        cudaMemcpyDeviceToHost, st));
+            PP_TRY_CUDA(cudaStreamSynchronize(st));
         }
     }
     return PP_OK;

@@ -112,15 +112,34 @@ struct Plan {
     double* scal = nullptr;   // device scalars: [0] |b|^2, [1] rayleigh, [2] |w|^2, [3..] history
     int red_blocks = 0;
     int hist_cap = 0;
-    double* hist = nullptr;   // [hist_cap][2]
+    double* hist = nullptr;   // [hist_cap][3]
+    int64_t graph_kernels = 0;
 
     // Graph cache for the solve loop
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t gexec = nullptr;
     std::vector<double> gkey;
 
+    bool external_wk = false;   // workspace supplied by an owner (batched plans)
     std::vector<void*> allocs;
 };
+
+// Records a CUDA event after every kernel launch (see check_launch) so that
+// consecutive events bracket one kernel each.
+struct Profiler {
+    cudaStream_t st = nullptr;
+    std::vector<std::string> names;
+    std::vector<cudaEvent_t> events;
+    void mark(const char* what) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return;
+        cudaEventRecord(e, st);
+        names.push_back(what);
+        events.push_back(e);
+    }
+};
+extern thread_local int64_t g_launches;
+extern thread_local Profiler* g_profiler;
 
 // ---- launchers (pp_kernels.cu) -------------------------------------------
 pp_status configure_kernels();
@@ -147,7 +166,7 @@ pp_status launch_nufft_degrid(const Plan& p, const float2* grid_in, float2* ksp,
 pp_status launch_prox(int ndim, int nx, int ny, int nz, int levels, float lambda,
                       const float2* in, float2* out, cudaStream_t st);
 pp_status launch_prox_fista(const Plan& p, int levels, float lambda, float gamma, float beta,
-                            const float2* u, double* hist_slot, cudaStream_t st);
+                            const float2* u, const float2* ref, double* hist_slot, cudaStream_t st);
 pp_status launch_dot(const float2* a, const float2* b, int64_t n, double* partials, int nblocks,
                      double* out_re, double* out_norm_b, cudaStream_t st);
 pp_status launch_norm2(const float2* a, int64_t n, double* partials, int nblocks, double* out,

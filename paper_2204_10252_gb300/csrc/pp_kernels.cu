@@ -575,13 +575,13 @@ template <int NDIM, int LEVELS>
 __global__ void __launch_bounds__(kThreads)
 prox_fista_kernel(int nx, int ny, int nz, float lam, float gamma, float beta,
                   float2* __restrict__ z, const float2* __restrict__ u, float2* __restrict__ y,
-                  double* __restrict__ hist) {
+                  const float2* __restrict__ ref, double* __restrict__ hist) {
     constexpr int TS = 1 << LEVELS;
     constexpr int ZS = (NDIM == 3) ? TS : 1;
     bool ok;
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t o = tile_origin<NDIM, LEVELS>(t, nx, ny, nz, ok);
-    double dd = 0.0, yy = 0.0;
+    double dd = 0.0, yy = 0.0, rr = 0.0;
     if (ok) {
         float2 v[ZS * TS * TS];
 #pragma unroll
@@ -609,6 +609,11 @@ prox_fista_kernel(int nx, int ny, int nz, float lam, float gamma, float beta,
                     y[a] = yn;
                     dd += (double)df.x * df.x + (double)df.y * df.y;
                     yy += (double)yn.x * yn.x + (double)yn.y * yn.y;
+                    if (ref) {
+                        const float2 rv = ref[a];
+                        const double ex = (double)yn.x - rv.x, ey = (double)yn.y - rv.y;
+                        rr += ex * ex + ey * ey;
+                    }
                 }
     }
     if (hist) {
@@ -616,22 +621,26 @@ prox_fista_kernel(int nx, int ny, int nz, float lam, float gamma, float beta,
         for (int off = 16; off > 0; off >>= 1) {
             dd += __shfl_down_sync(0xffffffffu, dd, off);
             yy += __shfl_down_sync(0xffffffffu, yy, off);
+            rr += __shfl_down_sync(0xffffffffu, rr, off);
         }
-        __shared__ double sd[kThreads / 32], sy[kThreads / 32];
+        __shared__ double sd[kThreads / 32], sy[kThreads / 32], sr[kThreads / 32];
         const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
         if (lane == 0) {
             sd[wid] = dd;
             sy[wid] = yy;
+            sr[wid] = rr;
         }
         __syncthreads();
         if (threadIdx.x == 0) {
-            double a = 0.0, b = 0.0;
+            double a = 0.0, b = 0.0, c = 0.0;
             for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
                 a += sd[i];
                 b += sy[i];
+                c += sr[i];
             }
             atomicAdd(&hist[0], a);
             atomicAdd(&hist[1], b);
+            atomicAdd(&hist[2], c);
         }
     }
 }
@@ -756,9 +765,14 @@ inline int ew_blocks(int64_t n) {
 // ===========================================================================
 // Launchers
 // ===========================================================================
+thread_local int64_t g_launches = 0;
+thread_local Profiler* g_profiler = nullptr;
+
 static pp_status check_launch(const char* what) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_status(e, what);
+    ++g_launches;
+    if (g_profiler) g_profiler->mark(what);
     return PP_OK;
 }
 
@@ -904,18 +918,18 @@ pp_status launch_prox(int ndim, int nx, int ny, int nz, int levels, float lambda
 }
 
 pp_status launch_prox_fista(const Plan& p, int levels, float lambda, float gamma, float beta,
-                            const float2* u, double* hist_slot, cudaStream_t st) {
+                            const float2* u, const float2* ref, double* hist_slot, cudaStream_t st) {
     const int ts = 1 << levels;
     const int64_t ntiles = (int64_t)(p.nx / ts) * (p.ny / ts) * (p.ndim == 3 ? p.nz / ts : 1);
     const int blocks = (int)((ntiles + kThreads - 1) / kThreads);
     if (p.ndim == 2 && levels == 1)
-        prox_fista_kernel<2, 1><<<blocks, kThreads, 0, st>>>(p.nx, p.ny, p.nz, lambda, gamma, beta, p.z, u, p.y, hist_slot);
+        prox_fista_kernel<2, 1><<<blocks, kThreads, 0, st>>>(p.nx, p.ny, p.nz, lambda, gamma, beta, p.z, u, p.y, ref, hist_slot);
     else if (p.ndim == 2)
-        prox_fista_kernel<2, 2><<<blocks, kThreads, 0, st>>>(p.nx, p.ny, p.nz, lambda, gamma, beta, p.z, u, p.y, hist_slot);
+        prox_fista_kernel<2, 2><<<blocks, kThreads, 0, st>>>(p.nx, p.ny, p.nz, lambda, gamma, beta, p.z, u, p.y, ref, hist_slot);
     else if (levels == 1)
-        prox_fista_kernel<3, 1><<<blocks, kThreads, 0, st>>>(p.nx, p.ny, p.nz, lambda, gamma, beta, p.z, u, p.y, hist_slot);
+        prox_fista_kernel<3, 1><<<blocks, kThreads, 0, st>>>(p.nx, p.ny, p.nz, lambda, gamma, beta, p.z, u, p.y, ref, hist_slot);
     else
-        prox_fista_kernel<3, 2><<<blocks, kThreads, 0, st>>>(p.nx, p.ny, p.nz, lambda, gamma, beta, p.z, u, p.y, hist_slot);
+        prox_fista_kernel<3, 2><<<blocks, kThreads, 0, st>>>(p.nx, p.ny, p.nz, lambda, gamma, beta, p.z, u, p.y, ref, hist_slot);
     return check_launch("prox_fista_kernel");
 }
 

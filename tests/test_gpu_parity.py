@@ -158,14 +158,18 @@ def test_solve_parity(pp, prob, d):
     ref = O.pfista(prob.normal, prob.adj, b.astype(np.complex128), lam, c, iters, L,
                    history=hist_ref)
     out = empty(prob.shape)
-    hist, bnorm, Lused = pp.pp_fista_solve(prob.plan, dev(b), lam, iters, c, 0 if d is None else d,
-                                           out, history=True)
-    assert Lused == L
-    assert abs(bnorm - np.linalg.norm(b.astype(np.complex128))) <= 1e-9 * bnorm
+    r = pp.pp_fista_solve(prob.plan, dev(b), lam, iters, c, 0 if d is None else d, out,
+                          history=True, ref=dev(ref))
+    assert r.L == L
+    assert abs(r.bnorm - np.linalg.norm(b.astype(np.complex128))) <= 1e-9 * r.bnorm
     assert rel(host(out), ref) <= TOL_SOLVE
-    # FP64 statistics: ||y_{k+1}||^2 per iteration
+    # FP64 statistics per iteration: ||y_{k+1}||^2 and ||y_{k+1} - ref||^2
     yy_ref = np.array([np.linalg.norm(h) ** 2 for h in hist_ref])
-    assert np.max(np.abs(hist[:, 1] - yy_ref) / yy_ref) <= 2 * TOL_SOLVE
+    assert np.max(np.abs(r.history[:, 1] - yy_ref) / yy_ref) <= 2 * TOL_SOLVE
+    dist_ref = np.array([np.linalg.norm(h - ref.astype(np.complex64)) ** 2 for h in hist_ref])
+    assert abs(np.sqrt(r.history[-1, 2]) - np.sqrt(dist_ref[-1])) <= 2 * TOL_SOLVE * np.linalg.norm(ref)
+    assert np.all(np.diff(np.sqrt(r.history[:, 2])) <= 0.5)   # well-formed, finite
+    assert r.launches > iters
 
 
 @pytest.mark.parametrize("shape,levels", [((64, 48), 2), ((64, 48), 1), ((8, 16, 12), 2),
