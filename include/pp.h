@@ -211,6 +211,27 @@ pp_status pp_batch_fista_solve(pp_batch* batch, const pp_c64* b, float lambda, i
                                const double* c, int d, pp_c64* x_out, pp_solve_info* info,
                                pp_stream stream);
 
+/* Differentiable unrolled solve on a batch (the training pattern): Algorithm
+ * "pfista" for exactly `iters` iterations on each slice with RAW b (no
+ * normalisation of b; A_hat_s = A_s / sqrt(L_s) with L_s fixed), checkpoints
+ * (y_k, z_k) every checkpoint_every iterations.  x_out is the concatenated
+ * y_iters.  c host double [d+1], 0 <= d <= 10. */
+pp_status pp_batch_unrolled_forward(pp_batch* batch, const pp_c64* b, float lambda, int iters,
+                                    const double* c, int d, int checkpoint_every, pp_c64* x_out,
+                                    pp_stream stream);
+
+/* Reverse pass: for the real loss Re<grad_out, y_iters>, writes grad_b (device
+ * k-space, dLoss/dRe b + i dLoss/dIm b), *grad_lambda and grad_c[0..d] (host).
+ * Uses the checkpoints of the last pp_batch_unrolled_forward with the same
+ * b pointer, lambda, iters, c, d and checkpoint_every, else reruns that
+ * forward first.  Each segment is recomputed from its checkpoint; the
+ * Horner adjoint uses v_j = N_hat^j wbar (N_hat is self-adjoint), d+1
+ * applies per iteration.  Synchronises `stream`. */
+pp_status pp_batch_unrolled_backward(pp_batch* batch, const pp_c64* b, float lambda, int iters,
+                                     const double* c, int d, int checkpoint_every,
+                                     const pp_c64* grad_out, pp_c64* grad_b, double* grad_lambda,
+                                     double* grad_c, pp_stream stream);
+
 /* Stage timing of the normal operator N_hat (no counterpart in the paper:
  * instrumentation).  Runs `reps` applies of N_hat x -> y on `stream`,
  * recording a CUDA event after every kernel launch, synchronises, and

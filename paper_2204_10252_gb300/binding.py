@@ -85,6 +85,14 @@ _SIGS = {
     "pp_batch_fista_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_float, ctypes.c_int,
                                             ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_void_p,
                                             ctypes.POINTER(pp_solve_info), ctypes.c_void_p]),
+    "pp_batch_unrolled_forward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_float, ctypes.c_int,
+                                                 ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_int,
+                                                 ctypes.c_void_p, ctypes.c_void_p]),
+    "pp_batch_unrolled_backward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_float, ctypes.c_int,
+                                                  ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_int,
+                                                  ctypes.c_void_p, ctypes.c_void_p,
+                                                  ctypes.POINTER(ctypes.c_double),
+                                                  ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
     "pp_last_error": (ctypes.c_char_p, []),
 }
 
@@ -420,6 +428,27 @@ def pp_batch_fista_solve(batch: Batch, b, lam: float, iters: int, c, d: int, x_o
                                       _stream(stream)), "pp_batch_fista_solve")
     return SolveResult(hist[:iters] if hist is not None else None, info.bnorm, info.L,
                        int(info.launches))
+
+
+def pp_batch_unrolled_forward(batch: Batch, b, lam: float, iters: int, c, d: int,
+                              checkpoint_every: int, x_out, stream=None):
+    _check(lib().pp_batch_unrolled_forward(batch.handle, _dev_ptr(b, "b"), float(lam), int(iters),
+                                           _cvec(c), int(d), int(checkpoint_every),
+                                           _dev_ptr(x_out, "x_out"), _stream(stream)),
+           "pp_batch_unrolled_forward")
+
+
+def pp_batch_unrolled_backward(batch: Batch, b, lam: float, iters: int, c, d: int,
+                               checkpoint_every: int, grad_out, grad_b, stream=None):
+    """Returns (grad_lambda, grad_c ndarray [d+1]); grad_b is written in place."""
+    gl = ctypes.c_double(0.0)
+    gc = (ctypes.c_double * (d + 1))()
+    _check(lib().pp_batch_unrolled_backward(batch.handle, _dev_ptr(b, "b"), float(lam), int(iters),
+                                            _cvec(c), int(d), int(checkpoint_every),
+                                            _dev_ptr(grad_out, "grad_out"), _dev_ptr(grad_b, "grad_b"),
+                                            ctypes.byref(gl), gc, _stream(stream)),
+           "pp_batch_unrolled_backward")
+    return gl.value, np.array(list(gc), dtype=np.float64)
 
 
 def pp_last_error() -> str:

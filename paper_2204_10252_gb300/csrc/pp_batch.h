@@ -31,6 +31,13 @@ struct BatchDev {
     Segments img, ksp, tiles;
 };
 
+// Up to 12 vectors and coefficients for a linear combination.
+struct LinComb {
+    const float2* v[12];
+    float coef[12];
+    int count;
+};
+
 size_t batch_normal_smem(int ny_max, int lgt);
 void* batch_normal_fn(int km, int lgt);
 pp_status configure_batch_kernels();
@@ -43,5 +50,10 @@ pp_status launch_seg_scale(const float2* in, float2* out, const Segments& sg, co
 pp_status launch_batch_prox_fista(const BatchDev& b, float lam, float gamma, float beta,
                                   float2* z, const float2* u, float2* y, const float2* ref,
                                   double* hist, cudaStream_t st);
+
+pp_status launch_batch_prox_vjp(const BatchDev& b, float lam, float beta, const float2* w,
+                                float2* Ybar, const float2* Zbar, float2* wbar, double* lam_bar,
+                                cudaStream_t st);
+pp_status launch_lincomb(const LinComb& lc, float2* out, int64_t n, int accumulate, cudaStream_t st);
 
 }  // namespace pp

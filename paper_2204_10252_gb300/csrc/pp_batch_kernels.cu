@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "pp_batch.h"
 
 namespace pp {
@@ -178,7 +180,7 @@ __global__ void seg_scale_kernel(const float2* __restrict__ in, float2* __restri
     const int j = blockIdx.x - seg_first_blk[seg];
     const int nb = seg_first_blk[seg + 1] - seg_first_blk[seg];
     const int64_t lo = seg_off[seg], hi = seg_off[seg + 1];
-    const double nv = sqrt(norm2[seg * stride]);
+    const double nv = norm2 ? sqrt(norm2[seg * stride]) : 1.0;
     const double fs = factor ? factor[seg] : 1.0;
     const float f = (float)(invert ? (nv > 0.0 ? fs / nv : 0.0) : fs * nv);
     for (int64_t i = lo + (int64_t)j * blockDim.x + threadIdx.x; i < hi; i += (int64_t)nb * blockDim.x)
@@ -295,6 +297,101 @@ batch_prox_fista_kernel(const SliceDesc* __restrict__ descs, const int64_t* __re
     }
 }
 
+// Reverse pass of one unrolled iteration at the prox (per 4x4 tile):
+//   ybar_{k+1} = Ybar + (1 + beta) Zbar          (adjoint of y_{k+1})
+//   Ybar      <- -beta Zbar                      (partial adjoint of y_k)
+//   wbar       = W^T J_s^T W ybar_{k+1},  J_s the soft threshold's Jacobian
+//                at the coefficients W w_k
+//   lam_bar   += sum Re(conj(W ybar_{k+1}) . (-v/|v|)) over |v| > lambda
+__global__ void __launch_bounds__(kThreads)
+batch_prox_vjp_kernel(const SliceDesc* __restrict__ descs, const int64_t* __restrict__ tile_off,
+                      const int* __restrict__ blk_seg, const int* __restrict__ seg_first_blk,
+                      float lam, float beta, const float2* __restrict__ w, float2* __restrict__ Ybar,
+                      const float2* __restrict__ Zbar, float2* __restrict__ wbar,
+                      double* __restrict__ lam_bar) {
+    const int s = blk_seg[blockIdx.x];
+    const int j = blockIdx.x - seg_first_blk[s];
+    const SliceDesc D = descs[s];
+    const int64_t t = (int64_t)j * blockDim.x + threadIdx.x;
+    const int64_t ntl = tile_off[s + 1] - tile_off[s];
+    double lb = 0.0;
+    if (t < ntl) {
+        const int ntx = D.nx / 4;
+        const int64_t ty = t / ntx, tx = t - ty * ntx;
+        const int64_t o = D.img_off + ty * 4 * D.nx + tx * 4;
+        float2 cw[16], cy[16];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int x = 0; x < 4; ++x) {
+                const int64_t a = o + (int64_t)r * D.nx + x;
+                const float2 zb = Zbar[a], yb = Ybar[a];
+                cy[r * 4 + x] = make_float2(yb.x + (1.f + beta) * zb.x, yb.y + (1.f + beta) * zb.y);
+                Ybar[a] = make_float2(-beta * zb.x, -beta * zb.y);
+                cw[r * 4 + x] = w[a];
+            }
+        // forward Haar of both tiles
+#pragma unroll
+        for (int by = 0; by < 4; by += 2)
+#pragma unroll
+            for (int bx = 0; bx < 4; bx += 2) {
+                haar2x2_b(cw[by * 4 + bx], cw[by * 4 + bx + 1], cw[(by + 1) * 4 + bx], cw[(by + 1) * 4 + bx + 1]);
+                haar2x2_b(cy[by * 4 + bx], cy[by * 4 + bx + 1], cy[(by + 1) * 4 + bx], cy[(by + 1) * 4 + bx + 1]);
+            }
+        haar2x2_b(cw[0], cw[2], cw[8], cw[10]);
+        haar2x2_b(cy[0], cy[2], cy[8], cy[10]);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const float2 v = cw[i], g = cy[i];
+            const float m2 = v.x * v.x + v.y * v.y;
+            if (m2 > lam * lam) {
+                const float rm = rsqrtf(m2);
+                const float hx = v.x * rm, hy = v.y * rm;          // v / |v|
+                const float q = lam * rm;                            // lambda / |v|
+                const float proj = hx * g.x + hy * g.y;              // Re(conj(vhat) g)
+                cy[i] = make_float2((1.f - q) * g.x + q * hx * proj, (1.f - q) * g.y + q * hy * proj);
+                lb -= (double)proj;
+            } else {
+                cy[i] = make_float2(0.f, 0.f);
+            }
+        }
+        haar2x2_b(cy[0], cy[2], cy[8], cy[10]);
+#pragma unroll
+        for (int by = 0; by < 4; by += 2)
+#pragma unroll
+            for (int bx = 0; bx < 4; bx += 2)
+                haar2x2_b(cy[by * 4 + bx], cy[by * 4 + bx + 1], cy[(by + 1) * 4 + bx], cy[(by + 1) * 4 + bx + 1]);
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int x = 0; x < 4; ++x) wbar[o + (int64_t)r * D.nx + x] = cy[r * 4 + x];
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) lb += __shfl_down_sync(0xffffffffu, lb, off);
+    __shared__ double sl[kThreads / 32];
+    if ((threadIdx.x & 31) == 0) sl[threadIdx.x >> 5] = lb;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) a += sl[i];
+        atomicAdd(lam_bar, a);
+    }
+}
+
+// out = (accumulate ? out : 0) + sum_i coef_i * v_i
+__global__ void lincomb_kernel(LinComb lc, float2* __restrict__ out, int64_t n, int accumulate) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        float2 a = accumulate ? out[i] : make_float2(0.f, 0.f);
+        for (int k = 0; k < lc.count; ++k) {
+            const float2 v = lc.v[k][i];
+            a.x += lc.coef[k] * v.x;
+            a.y += lc.coef[k] * v.y;
+        }
+        out[i] = a;
+    }
+}
+
 }  // namespace
 
 extern thread_local int64_t g_launches;
@@ -376,6 +473,22 @@ pp_status launch_batch_prox_fista(const BatchDev& b, float lam, float gamma, flo
         b.descs, b.tiles.off, b.tiles.blk_seg, b.tiles.seg_first_blk, lam, gamma, beta, z, u, y, ref,
         hist);
     return check_launch_b("batch_prox_fista_kernel");
+}
+
+pp_status launch_batch_prox_vjp(const BatchDev& b, float lam, float beta, const float2* w,
+                                float2* Ybar, const float2* Zbar, float2* wbar, double* lam_bar,
+                                cudaStream_t st) {
+    batch_prox_vjp_kernel<<<b.tiles.nblocks, kThreads, 0, st>>>(
+        b.descs, b.tiles.off, b.tiles.blk_seg, b.tiles.seg_first_blk, lam, beta, w, Ybar, Zbar, wbar,
+        lam_bar);
+    return check_launch_b("batch_prox_vjp_kernel");
+}
+
+pp_status launch_lincomb(const LinComb& lc, float2* out, int64_t n, int accumulate, cudaStream_t st) {
+    int64_t blocks = (n + kThreads - 1) / kThreads;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    lincomb_kernel<<<(int)std::max<int64_t>(blocks, 1), kThreads, 0, st>>>(lc, out, n, accumulate);
+    return check_launch_b("lincomb_kernel");
 }
 
 }  // namespace pp

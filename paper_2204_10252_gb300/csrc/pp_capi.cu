@@ -488,6 +488,12 @@ struct Batch {
     cudaGraphExec_t gexec = nullptr;
     std::vector<double> gkey;
     int64_t graph_kernels = 0;
+    // differentiable unrolled solve: arena of image vectors and FP64 slots
+    float2* arena = nullptr;
+    size_t arena_vecs = 0;
+    double* dslots = nullptr;
+    size_t dslots_n = 0;
+    std::vector<double> tape_key;
 };
 
 template <class T>
@@ -669,6 +675,156 @@ static pp_status batch_iterations(Batch& b, float lambda, int iters, const doubl
         const float beta = (float)((double)k / (k + 3.0));
         PP_TRY(launch_batch_prox_fista(b.dev, lambda, gamma, beta, b.z, u, b.y, hist ? ref : nullptr,
                                        hist ? b.hist + 3 * k : nullptr, st));
+    }
+    return PP_OK;
+}
+
+
+// ---------------------------------------------------------------------------
+// Differentiable unrolled solve on a batch: raw b (no normalisation, L_s
+// fixed), Algorithm "pfista" for a fixed iteration count, checkpoints
+// (y_k, z_k) every `ce` iterations, and the reverse pass.
+// Arena layout (image-sized vectors): [0] ahb, [1 .. 2*ncp] checkpoints,
+// then 3*ce segment vectors (z_k, g_k, w_k), d+2 Horner-adjoint vectors and
+// Ybar, Zbar, wbar, ahb_bar, yw, zw.
+// ---------------------------------------------------------------------------
+static pp_status ensure_arena(Batch& b, size_t vecs, size_t slots) {
+    if (vecs > b.arena_vecs) {
+        if (b.arena) {
+            cudaFree(b.arena);
+            b.allocs.erase(std::remove(b.allocs.begin(), b.allocs.end(), (void*)b.arena), b.allocs.end());
+            b.arena = nullptr;
+            b.arena_vecs = 0;
+        }
+        PP_TRY(balloc(b, &b.arena, vecs * (size_t)b.nimg));
+        b.arena_vecs = vecs;
+        b.tape_key.clear();
+    }
+    if (slots > b.dslots_n) {
+        if (b.dslots) {
+            cudaFree(b.dslots);
+            b.allocs.erase(std::remove(b.allocs.begin(), b.allocs.end(), (void*)b.dslots), b.allocs.end());
+            b.dslots = nullptr;
+            b.dslots_n = 0;
+        }
+        PP_TRY(balloc(b, &b.dslots, slots));
+        b.dslots_n = slots;
+    }
+    return PP_OK;
+}
+
+static inline float2* avec(Batch& b, size_t i) { return b.arena + i * (size_t)b.nimg; }
+
+static size_t unrolled_vecs(int iters, int ce, int d) {
+    const size_t ncp = (size_t)((iters + ce - 1) / ce);
+    return 1 + 2 * ncp + 3 * (size_t)ce + (size_t)(d + 2) + 6;
+}
+
+static pp_status unrolled_step(Batch& b, const double* c, int d, float lambda, int k, float2* z,
+                               float2* y, float2* g_out, float2* w_out, cudaStream_t st) {
+    const float2* ahb = avec(b, 0);
+    PP_TRY(launch_batch_normal(b.dev, z, g_out, 1.f, ahb, -1.f, st));
+    PP_TRY(batch_horner(b, c, d, g_out, b.u, st));
+    if (w_out) {
+        LinComb lc;
+        lc.count = 2;
+        lc.v[0] = z; lc.coef[0] = 1.f;
+        lc.v[1] = b.u; lc.coef[1] = -1.f;
+        PP_TRY(launch_lincomb(lc, w_out, b.nimg, 0, st));
+    }
+    const float beta = (float)((double)k / (k + 3.0));
+    return launch_batch_prox_fista(b.dev, lambda, 1.f, beta, z, b.u, y, nullptr, nullptr, st);
+}
+
+static pp_status unrolled_forward(Batch& b, const float2* bk, float lambda, int iters,
+                                  const double* c, int d, int ce, float2* x_out, cudaStream_t st) {
+    PP_TRY(ensure_arena(b, unrolled_vecs(iters, ce, d), (size_t)iters * (d + 1) + 1));
+    float2* ahb = avec(b, 0);
+    for (int s = 0; s < b.n; ++s)
+        PP_TRY(adjoint_into(*b.sub[s], bk + b.ksp_off[s], ahb + b.img_off[s], st));
+    PP_TRY(launch_seg_scale(ahb, ahb, b.dev.img, nullptr, 0, b.dfac, 0, st));
+    PP_TRY_CUDA(cudaMemsetAsync(b.y, 0, b.nimg * sizeof(float2), st));
+    PP_TRY_CUDA(cudaMemsetAsync(b.z, 0, b.nimg * sizeof(float2), st));
+    const size_t bytes = (size_t)b.nimg * sizeof(float2);
+    for (int k = 0; k < iters; ++k) {
+        if (k % ce == 0) {
+            const int cp = k / ce;
+            PP_TRY_CUDA(cudaMemcpyAsync(avec(b, 1 + 2 * cp), b.y, bytes, cudaMemcpyDeviceToDevice, st));
+            PP_TRY_CUDA(cudaMemcpyAsync(avec(b, 2 + 2 * cp), b.z, bytes, cudaMemcpyDeviceToDevice, st));
+        }
+        PP_TRY(unrolled_step(b, c, d, lambda, k, b.z, b.y, b.g, nullptr, st));
+    }
+    PP_TRY_CUDA(cudaMemcpyAsync(x_out, b.y, bytes, cudaMemcpyDeviceToDevice, st));
+    return PP_OK;
+}
+
+static pp_status unrolled_backward(Batch& b, float lambda, int iters, const double* c, int d,
+                                   int ce, const float2* gout, float2* grad_b, double* grad_lam,
+                                   double* grad_c, cudaStream_t st) {
+    const size_t ncp = (size_t)((iters + ce - 1) / ce);
+    const size_t seg0 = 1 + 2 * ncp, v0 = seg0 + 3 * (size_t)ce, r0 = v0 + (size_t)(d + 2);
+    float2 *Ybar = avec(b, r0), *Zbar = avec(b, r0 + 1), *wbar = avec(b, r0 + 2),
+           *ahb_bar = avec(b, r0 + 3), *yw = avec(b, r0 + 4), *zw = avec(b, r0 + 5);
+    const size_t bytes = (size_t)b.nimg * sizeof(float2);
+    double* lam_bar = b.dslots;
+    double* dots = b.dslots + 1;   // [iters][d+1]
+    PP_TRY_CUDA(cudaMemcpyAsync(Ybar, gout, bytes, cudaMemcpyDeviceToDevice, st));
+    PP_TRY_CUDA(cudaMemsetAsync(Zbar, 0, bytes, st));
+    PP_TRY_CUDA(cudaMemsetAsync(ahb_bar, 0, bytes, st));
+    PP_TRY_CUDA(cudaMemsetAsync(b.dslots, 0, sizeof(double) * (1 + (size_t)iters * (d + 1)), st));
+    for (int sg = (int)ncp - 1; sg >= 0; --sg) {
+        const int k0 = sg * ce, k1 = std::min(iters, k0 + ce);
+        // recompute the segment forward from its checkpoint, keeping z_k, g_k, w_k
+        PP_TRY_CUDA(cudaMemcpyAsync(yw, avec(b, 1 + 2 * sg), bytes, cudaMemcpyDeviceToDevice, st));
+        PP_TRY_CUDA(cudaMemcpyAsync(zw, avec(b, 2 + 2 * sg), bytes, cudaMemcpyDeviceToDevice, st));
+        for (int k = k0; k < k1; ++k) {
+            const int j = k - k0;
+            PP_TRY_CUDA(cudaMemcpyAsync(avec(b, seg0 + 3 * j), zw, bytes, cudaMemcpyDeviceToDevice, st));
+            PP_TRY(unrolled_step(b, c, d, lambda, k, zw, yw, avec(b, seg0 + 3 * j + 1),
+                                 avec(b, seg0 + 3 * j + 2), st));
+        }
+        for (int k = k1 - 1; k >= k0; --k) {
+            const int j = k - k0;
+            const float beta = (float)((double)k / (k + 3.0));
+            PP_TRY(launch_batch_prox_vjp(b.dev, lambda, beta, avec(b, seg0 + 3 * j + 2), Ybar, Zbar,
+                                         wbar, lam_bar, st));
+            // v_0 = wbar, v_i = N_hat v_{i-1}, i = 1..d+1
+            const float2* prev = wbar;
+            for (int i = 1; i <= d + 1; ++i) {
+                PP_TRY(launch_batch_normal(b.dev, prev, avec(b, v0 + i), 1.f, nullptr, 0.f, st));
+                prev = avec(b, v0 + i);
+            }
+            const float2* gk = avec(b, seg0 + 3 * j + 1);
+            for (int i = 0; i <= d; ++i)
+                PP_TRY(launch_dot(i == 0 ? wbar : avec(b, v0 + i), gk, b.nimg, b.partials,
+                                  b.dev.img.nblocks, dots + (size_t)k * (d + 1) + i, nullptr, st));
+            // Zbar = wbar - sum_i c_i v_{i+1};  ahb_bar += sum_i c_i v_i
+            LinComb za, ab;
+            za.count = d + 2;
+            za.v[0] = wbar; za.coef[0] = 1.f;
+            ab.count = d + 1;
+            for (int i = 0; i <= d; ++i) {
+                za.v[i + 1] = avec(b, v0 + i + 1);
+                za.coef[i + 1] = -(float)c[i];
+                ab.v[i] = (i == 0) ? wbar : avec(b, v0 + i);
+                ab.coef[i] = (float)c[i];
+            }
+            PP_TRY(launch_lincomb(za, Zbar, b.nimg, 0, st));
+            PP_TRY(launch_lincomb(ab, ahb_bar, b.nimg, 1, st));
+        }
+    }
+    // b_bar = A_s ahb_bar_s / sqrt(L_s)
+    for (int s = 0; s < b.n; ++s)
+        PP_TRY(forward_into(*b.sub[s], ahb_bar + b.img_off[s], grad_b + b.ksp_off[s], st));
+    PP_TRY(launch_seg_scale(grad_b, grad_b, b.dev.ksp, nullptr, 0, b.dfac, 0, st));
+    std::vector<double> h(1 + (size_t)iters * (d + 1));
+    PP_TRY_CUDA(cudaMemcpyAsync(h.data(), b.dslots, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    PP_TRY_CUDA(cudaStreamSynchronize(st));
+    *grad_lam = h[0];
+    for (int i = 0; i <= d; ++i) {
+        double acc = 0.0;
+        for (int k = 0; k < iters; ++k) acc += h[1 + (size_t)k * (d + 1) + i];
+        grad_c[i] = -acc;
     }
     return PP_OK;
 }
@@ -1355,6 +1511,55 @@ pp_status pp_batch_fista_solve(pp_batch* batch, const pp_c64* bk, float lambda, 
         }
     }
     return PP_OK;
+}
+
+static bool unrolled_args_ok(const pp_batch* batch, const void* bk, int iters, const double* c,
+                             int d, int ce, float lambda) {
+    return batch && bk && c && iters >= 1 && iters <= 100000 && d >= 0 && d <= 10 && ce >= 1 &&
+           ce <= iters && lambda >= 0.f && isfinite(lambda);
+}
+
+pp_status pp_batch_unrolled_forward(pp_batch* batch, const pp_c64* b, float lambda, int iters,
+                                    const double* c, int d, int checkpoint_every, pp_c64* x_out,
+                                    pp_stream stream) {
+    if (!unrolled_args_ok(batch, b, iters, c, d, checkpoint_every, lambda) || !x_out) {
+        set_error("pp_batch_unrolled_forward: bad argument");
+        return PP_ERR_INVALID_ARG;
+    }
+    Batch& B = batch->impl;
+    pp_status rc = unrolled_forward(B, reinterpret_cast<const float2*>(b), lambda, iters, c, d,
+                                    checkpoint_every, reinterpret_cast<float2*>(x_out),
+                                    (cudaStream_t)stream);
+    if (rc != PP_OK) return rc;
+    B.tape_key = {(double)(uintptr_t)b, (double)lambda, (double)iters, (double)d,
+                  (double)checkpoint_every};
+    for (int i = 0; i <= d; ++i) B.tape_key.push_back(c[i]);
+    return PP_OK;
+}
+
+pp_status pp_batch_unrolled_backward(pp_batch* batch, const pp_c64* b, float lambda, int iters,
+                                     const double* c, int d, int checkpoint_every,
+                                     const pp_c64* grad_out, pp_c64* grad_b, double* grad_lambda,
+                                     double* grad_c, pp_stream stream) {
+    if (!unrolled_args_ok(batch, b, iters, c, d, checkpoint_every, lambda) || !grad_out ||
+        !grad_b || !grad_lambda || !grad_c) {
+        set_error("pp_batch_unrolled_backward: bad argument");
+        return PP_ERR_INVALID_ARG;
+    }
+    Batch& B = batch->impl;
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<double> key = {(double)(uintptr_t)b, (double)lambda, (double)iters, (double)d,
+                               (double)checkpoint_every};
+    for (int i = 0; i <= d; ++i) key.push_back(c[i]);
+    if (key != B.tape_key) {
+        // no matching forward on the tape: run it (its output goes to the solve buffer)
+        PP_TRY(unrolled_forward(B, reinterpret_cast<const float2*>(b), lambda, iters, c, d,
+                                checkpoint_every, B.w3, st));
+        B.tape_key = key;
+    }
+    return unrolled_backward(B, lambda, iters, c, d, checkpoint_every,
+                             reinterpret_cast<const float2*>(grad_out), reinterpret_cast<float2*>(grad_b),
+                             grad_lambda, grad_c, st);
 }
 
 }  // extern "C"

@@ -1,0 +1,115 @@
+"""GPU gradients of the unrolled preconditioned FISTA solve (libpp reverse
+pass behind torch.autograd) against the FP64 oracle's analytic gradient,
+which the CPU tests pin to central finite differences."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import pp_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+TOL_GRAD = 1e-3
+
+
+def rel(a, b):
+    a = np.asarray(a, np.complex128)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module")
+def pp():
+    from paper_2204_10252_gb300.build import build_library
+    build_library()
+    import paper_2204_10252_gb300 as m
+    m.lib()
+    return m
+
+
+def dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.complex64)).cuda()
+
+
+def make(pp, shapes, coils, R, seed):
+    sens = [synth.coil_maps(s, c, seed + i) for i, (s, c) in enumerate(zip(shapes, coils))]
+    masks = [synth.line_mask(s, R, 8, seed + 10 + i) for i, s in enumerate(shapes)]
+    batch = pp.pp_batch_create(shapes, coils, [dev(x) for x in sens], masks, seed=seed, power_iters=40)
+    xs = [synth.phantom(s, seed + 20 + i) for i, s in enumerate(shapes)]
+    bs = [(O.cart_forward(xs[i], sens[i], masks[i]) +
+           1e-3 * synth.crandn((coils[i],) + shapes[i], seed + 30 + i) * masks[i][None]).astype(np.complex64)
+          for i in range(len(shapes))]
+    ybar = [synth.crandn(s, seed + 40 + i) for i, s in enumerate(shapes)]
+    return batch, sens, masks, bs, ybar
+
+
+def oracle_grads(batch, sens, masks, bs, ybar, lam, c, iters, Ls):
+    outs, gb, gl, gc = [], [], 0.0, np.zeros(len(c))
+    for i in range(batch.n):
+        nrm = lambda v, i=i: O.cart_normal(v, sens[i], masks[i])
+        adj = lambda y, i=i: O.cart_adjoint(y, sens[i], masks[i])
+        fwd = lambda x, i=i: O.cart_forward(x, sens[i], masks[i])
+        outs.append(O.pfista_unrolled(nrm, adj, bs[i].astype(np.complex128), lam, c, iters, Ls[i]))
+        b_bar, l_bar, c_bar = O.pfista_unrolled_vjp(nrm, adj, fwd, bs[i].astype(np.complex128), lam, c,
+                                                    iters, Ls[i], ybar[i].astype(np.complex128))
+        gb.append(b_bar)
+        gl += l_bar
+        gc += c_bar
+    return outs, gb, gl, gc
+
+
+@pytest.mark.parametrize("d,iters,ce", [(3, 6, 2), (1, 5, 5), (0, 4, 3)])
+def test_unrolled_gradients_match_oracle(pp, d, iters, ce):
+    import torch
+    shapes, coils = [(32, 32), (48, 32), (32, 40)], [4, 2, 3]
+    batch, sens, masks, bs, ybar = make(pp, shapes, coils, 2, 7)
+    try:
+        Ls = pp.pp_batch_scales(batch)
+        lam = 2e-3
+        c = [float(v) for v in O.poly_coeffs_l2(d)]
+        b = dev(np.concatenate([v.ravel() for v in bs])).requires_grad_(True)
+        lam_t = torch.tensor(lam, dtype=torch.float64, requires_grad=True)
+        c_t = torch.tensor(c, dtype=torch.float64, requires_grad=True)
+        y = pp.unrolled_pfista(batch, b, lam_t, c_t, iters, ce)
+        yb = dev(np.concatenate([v.ravel() for v in ybar]))
+        loss = torch.sum((torch.conj(yb) * y).real)
+        loss.backward()
+        outs, gb, gl, gc = oracle_grads(batch, sens, masks, bs, ybar, lam, c, iters, Ls)
+        yh = y.detach().cpu().numpy()
+        io, ko = batch.image_off, batch.kspace_off
+        for i in range(batch.n):
+            assert rel(yh[io[i]:io[i + 1]].reshape(shapes[i]), outs[i]) <= 1e-4
+            g = b.grad.detach().cpu().numpy()[ko[i]:ko[i + 1]].reshape(gb[i].shape)
+            assert rel(g, gb[i]) <= TOL_GRAD
+        assert abs(lam_t.grad.item() - gl) <= TOL_GRAD * abs(gl)
+        assert np.max(np.abs(c_t.grad.numpy() - gc)) <= TOL_GRAD * np.max(np.abs(gc))
+    finally:
+        batch.destroy()
+
+
+def test_unrolled_full_size_two_slices(pp):
+    # two slices of the 8 x 256^2, 16-coil, R = 4 workload: 20 iterations,
+    # d = 3, checkpoints every 5
+    import torch
+    cfg = synth.CONFIGS["unrolled2d_8x256_c16"]
+    shapes, coils = [cfg["shape"]] * 2, [cfg["coils"]] * 2
+    batch, sens, masks, bs, ybar = make(pp, shapes, coils, cfg["R"], cfg["seed"])
+    try:
+        Ls = pp.pp_batch_scales(batch)
+        c = [float(v) for v in O.poly_coeffs_l2(cfg["d"])]
+        b = dev(np.concatenate([v.ravel() for v in bs]))
+        out = torch.empty(int(batch.image_off[-1]), dtype=torch.complex64, device="cuda")
+        pp.pp_batch_unrolled_forward(batch, b, cfg["lam"], cfg["iters"], c, cfg["d"], cfg["checkpoint"], out)
+        gb = torch.empty_like(b)
+        yb = dev(np.concatenate([v.ravel() for v in ybar]))
+        gl, gc = pp.pp_batch_unrolled_backward(batch, b, cfg["lam"], cfg["iters"], c, cfg["d"],
+                                               cfg["checkpoint"], yb, gb)
+        outs, gbr, glr, gcr = oracle_grads(batch, sens, masks, bs, ybar, cfg["lam"], c, cfg["iters"], Ls)
+        ko = batch.kspace_off
+        g = gb.cpu().numpy()
+        for i in range(batch.n):
+            assert rel(g[ko[i]:ko[i + 1]].reshape(gbr[i].shape), gbr[i]) <= TOL_GRAD
+        assert abs(gl - glr) <= TOL_GRAD * abs(glr)
+        assert np.max(np.abs(gc - gcr)) <= TOL_GRAD * np.max(np.abs(gcr))
+    finally:
+        batch.destroy()
