@@ -53,6 +53,10 @@ def parse():
     ap.add_argument("--impl", choices=["pp", "reference"], default="pp")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip time-to-NRMSE, e2e, CPU baseline (quick runs)")
+    ap.add_argument("--workload", default=WORKLOAD,
+                    choices=[WORKLOAD, "cart2d_128_c8", "cart3d_256x256x128_c32", "batched2d_64",
+                             "unrolled2d_8x256_c16"],
+                    help="benchmark line to produce (the default is the headline workload)")
     return ap.parse_args()
 
 
@@ -163,10 +167,13 @@ def kernel_flops(c, K):
     G = int(math.ceil(c["oversamp"] * nx))
     n = nx * ny
     fft = lambda N: 5.0 * N * math.log2(N)
+    W = c["kb_width"]
     return {
         "rows_fwd_kernel": C * ny * fft(G) + 8.0 * C * n,
         "cols_kernel": C * G * fft(G),
-        "nufft_tile_kernel<degrid>": 128.0 * C * K,
+        # G^T G stencil: (2W-1)^2 complex-by-real multiply-adds per grid point and coil
+        "gtg_stencil_kernel": 4.0 * (2 * W - 1) ** 2 * C * G * G,
+        "rows_adj_cb_kernel": C * ny * fft(G) + 10.0 * C * n,
         "rows_adj_kernel": C * ny * fft(G) + 10.0 * C * n,
     }
 
@@ -272,6 +279,14 @@ def main():
     build_library()
     pp.lib()
     torch.cuda.set_device(local)
+    if args.workload != WORKLOAD:
+        import bench_workloads
+        out = bench_workloads.run(args, pp, rank, world, local)
+        if rank == 0:
+            print(json.dumps(out))
+        if world > 1:
+            dist.destroy_process_group()
+        return
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
     c = cfg()

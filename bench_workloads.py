@@ -1,0 +1,217 @@
+"""Secondary benchmark lines (bench.py --workload ...): the Cartesian 128^2
+solve, the 3-D Cartesian normal operator, the batch of 64 uneven slices and
+the differentiable unrolled solve.  Same timing rules as bench.py: warm-up,
+CUDA events on the launching stream, L2 flushed between timed steps, clocks
+sampled during the timed region, max over ranks."""
+from __future__ import annotations
+
+import math
+import time
+
+import numpy as np
+import torch
+
+import bench
+import synth
+
+
+def _flush_buf(dev):
+    return torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+
+
+def _timed(fn, steps, dev, local):
+    """Total ms over `steps` calls of fn(), L2 flushed before each (outside
+    the events), clocks sampled throughout."""
+    stream = torch.cuda.current_stream()
+    flush = _flush_buf(dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    torch.cuda.synchronize()
+    with bench.ClockSampler(local) as clk:
+        for i in range(steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            fn()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in ev), clk.summary()
+
+
+def _hbm_peak():
+    try:
+        import json
+        import os
+        d = json.load(open(os.path.join(bench.ROOT, "MEASURED_PEAKS.json")))
+        return float(d["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except Exception:
+        return 6800.0, "fallback 6.8 TB/s"
+
+
+def _base(args, world, metric, unit, value, ms_per_step, cfg, clocks, extra=None):
+    out = {"metric": metric, "value": value, "unit": unit, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic (seeded); no datasets", "config": cfg, "clocks": clocks}
+    if extra:
+        out.update(extra)
+    return out
+
+
+def cart2d(args, pp, rank, world, local):
+    c = dict(synth.CONFIGS["cart2d_128_c8"])
+    dev = torch.device("cuda", local)
+    seed = bench.replica_seed(c["seed"], rank)
+    shape, C = c["shape"], c["coils"]
+    sens = torch.from_numpy(synth.coil_maps(shape, C, seed)).to(dev)
+    mask = synth.line_mask(shape, c["R"], c["acs"], seed)
+    plan = pp.pp_plan_create(shape, C, sens, mask=mask, seed=seed, power_iters=50)
+    x0 = torch.from_numpy(synth.phantom(shape, seed)).to(dev)
+    b = torch.empty((C,) + shape, dtype=torch.complex64, device=dev)
+    pp.pp_forward_apply(plan, x0, b)
+    b += torch.from_numpy(synth.cnoise((C,) + shape, c["sigma"], seed + 1) * mask[None]).to(dev)
+    coeffs = [float(v) for v in pp.pp_poly_coeffs_l2(c["d"])]
+    xo = torch.empty(shape, dtype=torch.complex64, device=dev)
+    run = lambda: pp.pp_fista_solve(plan, b, c["lam"], c["iters"], coeffs, c["d"], xo)
+    for _ in range(args.warmup):
+        run()
+    ms, clk = _timed(run, args.steps, dev, local)
+    ms = bench.max_over_ranks(ms, world, dev)
+    applies = c["iters"] * (c["d"] + 1)
+    xin = torch.from_numpy(synth.crandn(shape, 3)).to(dev)
+    stages = pp.pp_profile_normal(plan, xin, torch.empty_like(xin), reps=100)
+    apply_ms = sum(stages.values())
+    bytes_apply = 8.0 * (C * shape[0] * shape[1] + 3 * shape[0] * shape[1])
+    ttt = bench.time_to_target(pp, plan, b, c, coeffs, 0.0, torch.cuda.current_stream())
+    plan.destroy()
+    return _base(args, world, "A^H A applies/s (preconditioned FISTA, d=3, 40 iterations)", "applies/s",
+                 bench.job_throughput(args.steps * applies, world, ms / 1e3), ms / args.steps,
+                 {"workload": "cart2d_128_c8", "image": list(shape), "coils": C, "R": c["R"],
+                  "d": c["d"], "iters": c["iters"], "l2": "flushed between timed steps"}, clk,
+                 {"normal_apply_us": apply_ms * 1e3, "stage_ms_per_apply": stages,
+                  "l2_resident_gbs": bytes_apply / (apply_ms / 1e3) / 1e9, "time_to_nrmse": ttt})
+
+
+def cart3d(args, pp, rank, world, local):
+    c = dict(synth.CONFIGS["cart3d_256x256x128_c32"])
+    dev = torch.device("cuda", local)
+    seed = bench.replica_seed(c["seed"], rank)
+    shape, C = c["shape"], c["coils"]          # (nz, ny, nx)
+    t0 = time.perf_counter()
+    maps = synth.coil_maps(shape, C, seed)
+    sens = torch.from_numpy(maps).to(dev)
+    del maps
+    mask = synth.poisson_disc_mask(shape, c["R"], c["calib"], seed)
+    gen_s = time.perf_counter() - t0
+    plan = pp.pp_plan_create(shape, C, sens, mask=mask, seed=seed, power_iters=0)
+    x = torch.from_numpy(synth.crandn(shape, 3)).to(dev)
+    y = torch.empty_like(x)
+    run = lambda: pp.pp_normal_apply(plan, x, y)
+    for _ in range(args.warmup):
+        run()
+    ms, clk = _timed(run, args.steps, dev, local)
+    ms = bench.max_over_ranks(ms, world, dev)
+    n = int(np.prod(shape))
+    bytes_apply = 8.0 * (C * n + 3 * n)
+    gbs = bytes_apply / (ms / args.steps / 1e3) / 1e9
+    peak, src = _hbm_peak()
+    stages = pp.pp_profile_normal(plan, x, y, reps=2)
+    plan.destroy()
+    return _base(args, world, "A^H A applies/s (3-D Cartesian normal operator)", "applies/s",
+                 bench.job_throughput(args.steps, world, ms / 1e3), ms / args.steps,
+                 {"workload": "cart3d_256x256x128_c32", "image": list(shape), "coils": C, "R": c["R"],
+                  "l2": "inputs larger than L2 (2 GiB of coil maps) and flushed between steps",
+                  "input_generation_s": gen_s}, clk,
+                 {"roofline": {"bound": "hbm", "kernel": "whole normal apply", "achieved": gbs,
+                               "peak": peak, "unit": "GB/s", "frac": gbs / peak, "traffic": None,
+                               "peak_source": src,
+                               "algorithmic_bytes_per_apply": bytes_apply},
+                  "stage_ms_per_apply": stages})
+
+
+def batched(args, pp, rank, world, local):
+    c = dict(synth.CONFIGS["batched2d_64"])
+    dev = torch.device("cuda", local)
+    slices = synth.batched_slices(c["n_slices"], bench.replica_seed(c["seed"], rank))
+    shapes = [(ny, nx) for ny, nx, _, _ in slices]
+    coils = [C for _, _, C, _ in slices]
+    sens, masks = [], []
+    for i, (ny, nx, C, R) in enumerate(slices):
+        sens.append(torch.from_numpy(synth.coil_maps((ny, nx), C, c["seed"] + i)).to(dev))
+        masks.append(synth.line_mask((ny, nx), R, c["acs"], c["seed"] + i))
+    t0 = time.perf_counter()
+    batch = pp.pp_batch_create(shapes, coils, sens, masks, seed=c["seed"], power_iters=50)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    xs = torch.cat([torch.from_numpy(synth.phantom(s, c["seed"] + 100 + i)).reshape(-1)
+                    for i, s in enumerate(shapes)]).to(dev)
+    b = torch.empty(int(batch.kspace_off[-1]), dtype=torch.complex64, device=dev)
+    pp.pp_batch_forward_apply(batch, xs, b)
+    coeffs = [float(v) for v in pp.pp_poly_coeffs_l2(c["d"])]
+    xo = torch.empty(int(batch.image_off[-1]), dtype=torch.complex64, device=dev)
+    run = lambda: pp.pp_batch_fista_solve(batch, b, c["lam"], c["iters"], coeffs, c["d"], xo)
+    for _ in range(args.warmup):
+        run()
+    ms, clk = _timed(run, args.steps, dev, local)
+    ms = bench.max_over_ranks(ms, world, dev)
+    # one batched normal apply, timed alone
+    y = torch.empty_like(xo)
+    apply_ms, _ = _timed(lambda: pp.pp_batch_normal_apply(batch, xs, y), 20, dev, local)
+    apply_ms /= 20
+    nimg = int(batch.image_off[-1])
+    bytes_apply = 8.0 * (sum(C * s[0] * s[1] for C, s in zip(coils, shapes)) + 3 * nimg)
+    gbs = bytes_apply / (apply_ms / 1e3) / 1e9
+    peak, src = _hbm_peak()
+    tile, grid = pp.pp_batch_tile(batch)
+    batch.destroy()
+    applies = c["iters"] * (c["d"] + 1) * len(slices)
+    return _base(args, world, "slice A^H A applies/s (64 uneven slices, d=3, 50 iterations)",
+                 "slice-applies/s", bench.job_throughput(args.steps * applies, world, ms / 1e3),
+                 ms / args.steps,
+                 {"workload": "batched2d_64", "slices": len(slices), "image_elems": nimg,
+                  "coil_map_bytes": 8 * sum(C * s[0] * s[1] for C, s in zip(coils, shapes)),
+                  "d": c["d"], "iters": c["iters"], "l2": "inputs larger than L2; flushed between steps",
+                  "autotuned_cols_per_cta": tile, "persistent_ctas": grid, "setup_s": setup_s}, clk,
+                 {"roofline": {"bound": "hbm", "kernel": "cart2d_batch_normal_kernel (one launch per apply)",
+                               "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                               "traffic": None, "peak_source": src,
+                               "algorithmic_bytes_per_apply": bytes_apply},
+                  "batched_apply_ms": apply_ms})
+
+
+def unrolled(args, pp, rank, world, local):
+    c = dict(synth.CONFIGS["unrolled2d_8x256_c16"])
+    dev = torch.device("cuda", local)
+    shape, C, B = c["shape"], c["coils"], c["batch"]
+    sens = [torch.from_numpy(synth.coil_maps(shape, C, c["seed"] + i)).to(dev) for i in range(B)]
+    masks = [synth.line_mask(shape, c["R"], c["acs"], c["seed"] + i) for i in range(B)]
+    batch = pp.pp_batch_create([shape] * B, [C] * B, sens, masks, seed=c["seed"], power_iters=50)
+    xs = torch.cat([torch.from_numpy(synth.phantom(shape, c["seed"] + 10 + i)).reshape(-1)
+                    for i in range(B)]).to(dev)
+    b = torch.empty(int(batch.kspace_off[-1]), dtype=torch.complex64, device=dev)
+    pp.pp_batch_forward_apply(batch, xs, b)
+    lam = torch.tensor(c["lam"], dtype=torch.float64, requires_grad=True)
+    coeffs = torch.tensor([float(v) for v in pp.pp_poly_coeffs_l2(c["d"])], dtype=torch.float64,
+                          requires_grad=True)
+    bq = b.clone().requires_grad_(True)
+    ybar = torch.from_numpy(synth.crandn((int(batch.image_off[-1]),), 5)).to(dev)
+
+    def step():
+        y = pp.unrolled_pfista(batch, bq, lam, coeffs, c["iters"], c["checkpoint"])
+        loss = torch.sum((torch.conj(ybar) * y).real)
+        loss.backward()
+
+    for _ in range(args.warmup):
+        step()
+    ms, clk = _timed(step, args.steps, dev, local)
+    ms = bench.max_over_ranks(ms, world, dev)
+    batch.destroy()
+    return _base(args, world, "unrolled solves/s (forward + backward, batch 8 x 256^2, 16 coils, 20 iterations, d=3)",
+                 "fwd+bwd/s", bench.job_throughput(args.steps, world, ms / 1e3), ms / args.steps,
+                 {"workload": "unrolled2d_8x256_c16", "batch": B, "image": list(shape), "coils": C,
+                  "iters": c["iters"], "d": c["d"], "checkpoint_every": c["checkpoint"],
+                  "l2": "flushed between timed steps"}, clk)
+
+
+def run(args, pp, rank, world, local):
+    return {"cart2d_128_c8": cart2d, "cart3d_256x256x128_c32": cart3d, "batched2d_64": batched,
+            "unrolled2d_8x256_c16": unrolled}[args.workload](args, pp, rank, world, local)

@@ -141,6 +141,24 @@ def _dev_ptr(t, what: str) -> int:
     return t.data_ptr()
 
 
+def _numel(t, n: int, what: str):
+    """Raise before any device work when a tensor's size does not match what
+    the plan will read or write (the C ABI cannot see buffer sizes)."""
+    size = int(t.numel()) if hasattr(t, "numel") else int(np.size(t))
+    if size != n:
+        raise ValueError("%s has %d elements; the plan expects %d" % (what, size, n))
+
+
+def _img(plan, t, what):
+    _numel(t, int(np.prod(plan.shape)), what)
+    return _dev_ptr(t, what)
+
+
+def _ksp(plan, t, what):
+    _numel(t, int(np.prod(plan.kspace_shape)), what)
+    return _dev_ptr(t, what)
+
+
 def _stream(stream) -> int:
     if stream is None:
         import torch
@@ -209,6 +227,9 @@ def pp_plan_create(shape, coils: int, sens, mask=None, traj=None, kb_width: int 
     s.kb_width = int(kb_width)
     s.oversamp = float(oversamp)
     out = ctypes.c_void_p(0)
+    _numel(sens, int(coils) * int(np.prod(shape)), "sens")
+    if mask is not None:
+        _numel(m, int(np.prod(shape)), "mask")
     _check(lib().pp_plan_create(ctypes.byref(out), _dims(shape), int(coils), _dev_ptr(sens, "sens"),
                                 ctypes.byref(s), ctypes.c_uint64(seed), int(power_iters),
                                 _stream(stream)), "pp_plan_create")
@@ -236,17 +257,17 @@ def pp_plan_sizes(plan: Plan):
 
 
 def pp_forward_apply(plan: Plan, x, y, stream=None):
-    _check(lib().pp_forward_apply(plan.handle, _dev_ptr(x, "x"), _dev_ptr(y, "y"), _stream(stream)),
+    _check(lib().pp_forward_apply(plan.handle, _img(plan, x, "x"), _ksp(plan, y, "y"), _stream(stream)),
            "pp_forward_apply")
 
 
 def pp_adjoint_apply(plan: Plan, y, x, stream=None):
-    _check(lib().pp_adjoint_apply(plan.handle, _dev_ptr(y, "y"), _dev_ptr(x, "x"), _stream(stream)),
+    _check(lib().pp_adjoint_apply(plan.handle, _ksp(plan, y, "y"), _img(plan, x, "x"), _stream(stream)),
            "pp_adjoint_apply")
 
 
 def pp_normal_apply(plan: Plan, x, y, stream=None):
-    _check(lib().pp_normal_apply(plan.handle, _dev_ptr(x, "x"), _dev_ptr(y, "y"), _stream(stream)),
+    _check(lib().pp_normal_apply(plan.handle, _img(plan, x, "x"), _img(plan, y, "y"), _stream(stream)),
            "pp_normal_apply")
 
 
@@ -262,11 +283,13 @@ def _cvec(c):
 
 
 def pp_poly_apply(plan: Plan, c, d: int, v, out, stream=None):
-    _check(lib().pp_poly_apply(plan.handle, _cvec(c), int(d), _dev_ptr(v, "v"), _dev_ptr(out, "out"),
+    _check(lib().pp_poly_apply(plan.handle, _cvec(c), int(d), _img(plan, v, "v"), _img(plan, out, "out"),
                                _stream(stream)), "pp_poly_apply")
 
 
 def pp_prox_l1_haar(shape, levels: int, lam: float, x_in, x_out, stream=None):
+    _numel(x_in, int(np.prod(shape)), "in")
+    _numel(x_out, int(np.prod(shape)), "out")
     _check(lib().pp_prox_l1_haar(_dims(shape), int(levels), float(lam), _dev_ptr(x_in, "in"),
                                  _dev_ptr(x_out, "out"), _stream(stream)), "pp_prox_l1_haar")
 
@@ -295,10 +318,10 @@ def pp_fista_solve(plan: Plan, b, lam: float, iters: int, c, d: int, x_out, stre
         info.history = hist.ctypes.data
     else:
         info.history = None
-    info.ref = _dev_ptr(ref, "ref") if ref is not None else None
+    info.ref = _img(plan, ref, "ref") if ref is not None else None
     cptr = _cvec(c) if c is not None else None
-    _check(lib().pp_fista_solve(plan.handle, _dev_ptr(b, "b"), float(lam), int(iters), cptr, int(d),
-                                _dev_ptr(x_out, "x_out"), ctypes.byref(info), _stream(stream)),
+    _check(lib().pp_fista_solve(plan.handle, _ksp(plan, b, "b"), float(lam), int(iters), cptr, int(d),
+                                _img(plan, x_out, "x_out"), ctypes.byref(info), _stream(stream)),
            "pp_fista_solve")
     return SolveResult(hist[:iters] if hist is not None else None, info.bnorm, info.L,
                        int(info.launches))
@@ -309,7 +332,7 @@ def pp_profile_normal(plan: Plan, x, y, reps: int = 20, stream=None, max_stages:
     names = ctypes.create_string_buffer(48 * max_stages)
     ms = (ctypes.c_double * max_stages)()
     n = ctypes.c_int(0)
-    _check(lib().pp_profile_normal(plan.handle, _dev_ptr(x, "x"), _dev_ptr(y, "y"), int(reps),
+    _check(lib().pp_profile_normal(plan.handle, _img(plan, x, "x"), _img(plan, y, "y"), int(reps),
                                    int(max_stages), names, ms, ctypes.byref(n), _stream(stream)),
            "pp_profile_normal")
     raw = names.raw
@@ -358,8 +381,13 @@ def pp_batch_create(shapes, coils, sens, masks, seed: int = 0, power_iters: int 
     n = len(shapes)
     dims = (pp_dims * n)(*[_dims(s) for s in shapes])
     cs = (ctypes.c_int * n)(*[int(c) for c in coils])
+    for i, (t, shp, c) in enumerate(zip(sens, shapes, coils)):
+        _numel(t, int(c) * int(np.prod(shp)), "sens[%d]" % i)
     sp = (ctypes.c_void_p * n)(*[_dev_ptr(t, "sens[%d]" % i) for i, t in enumerate(sens)])
     ms = [np.ascontiguousarray(m, dtype=np.uint8) for m in masks]
+    for i, (m, shp) in enumerate(zip(ms, shapes)):
+        if m.size != int(np.prod(shp)):
+            raise ValueError("masks[%d] has %d elements; expected %d" % (i, m.size, int(np.prod(shp))))
     mp = (ctypes.c_void_p * n)(*[m.ctypes.data for m in ms])
     out = ctypes.c_void_p(0)
     _check(lib().pp_batch_create(ctypes.byref(out), n, dims, cs, sp, mp, ctypes.c_uint64(seed),
@@ -395,18 +423,28 @@ def pp_batch_tile(batch: Batch):
     return a.value, b.value
 
 
+def _bimg(batch, t, what):
+    _numel(t, int(batch.image_off[-1]), what)
+    return _dev_ptr(t, what)
+
+
+def _bksp(batch, t, what):
+    _numel(t, int(batch.kspace_off[-1]), what)
+    return _dev_ptr(t, what)
+
+
 def pp_batch_forward_apply(batch: Batch, x, y, stream=None):
-    _check(lib().pp_batch_forward_apply(batch.handle, _dev_ptr(x, "x"), _dev_ptr(y, "y"),
+    _check(lib().pp_batch_forward_apply(batch.handle, _bimg(batch, x, "x"), _bksp(batch, y, "y"),
                                         _stream(stream)), "pp_batch_forward_apply")
 
 
 def pp_batch_adjoint_apply(batch: Batch, y, x, stream=None):
-    _check(lib().pp_batch_adjoint_apply(batch.handle, _dev_ptr(y, "y"), _dev_ptr(x, "x"),
+    _check(lib().pp_batch_adjoint_apply(batch.handle, _bksp(batch, y, "y"), _bimg(batch, x, "x"),
                                         _stream(stream)), "pp_batch_adjoint_apply")
 
 
 def pp_batch_normal_apply(batch: Batch, x, y, stream=None):
-    _check(lib().pp_batch_normal_apply(batch.handle, _dev_ptr(x, "x"), _dev_ptr(y, "y"),
+    _check(lib().pp_batch_normal_apply(batch.handle, _bimg(batch, x, "x"), _bimg(batch, y, "y"),
                                        _stream(stream)), "pp_batch_normal_apply")
 
 
@@ -421,10 +459,10 @@ def pp_batch_fista_solve(batch: Batch, b, lam: float, iters: int, c, d: int, x_o
         info.history = hist.ctypes.data
     else:
         info.history = None
-    info.ref = _dev_ptr(ref, "ref") if ref is not None else None
+    info.ref = _bimg(batch, ref, "ref") if ref is not None else None
     cptr = _cvec(c) if c is not None else None
-    _check(lib().pp_batch_fista_solve(batch.handle, _dev_ptr(b, "b"), float(lam), int(iters), cptr,
-                                      int(d), _dev_ptr(x_out, "x_out"), ctypes.byref(info),
+    _check(lib().pp_batch_fista_solve(batch.handle, _bksp(batch, b, "b"), float(lam), int(iters), cptr,
+                                      int(d), _bimg(batch, x_out, "x_out"), ctypes.byref(info),
                                       _stream(stream)), "pp_batch_fista_solve")
     return SolveResult(hist[:iters] if hist is not None else None, info.bnorm, info.L,
                        int(info.launches))
@@ -432,9 +470,9 @@ def pp_batch_fista_solve(batch: Batch, b, lam: float, iters: int, c, d: int, x_o
 
 def pp_batch_unrolled_forward(batch: Batch, b, lam: float, iters: int, c, d: int,
                               checkpoint_every: int, x_out, stream=None):
-    _check(lib().pp_batch_unrolled_forward(batch.handle, _dev_ptr(b, "b"), float(lam), int(iters),
+    _check(lib().pp_batch_unrolled_forward(batch.handle, _bksp(batch, b, "b"), float(lam), int(iters),
                                            _cvec(c), int(d), int(checkpoint_every),
-                                           _dev_ptr(x_out, "x_out"), _stream(stream)),
+                                           _bimg(batch, x_out, "x_out"), _stream(stream)),
            "pp_batch_unrolled_forward")
 
 
@@ -443,9 +481,9 @@ def pp_batch_unrolled_backward(batch: Batch, b, lam: float, iters: int, c, d: in
     """Returns (grad_lambda, grad_c ndarray [d+1]); grad_b is written in place."""
     gl = ctypes.c_double(0.0)
     gc = (ctypes.c_double * (d + 1))()
-    _check(lib().pp_batch_unrolled_backward(batch.handle, _dev_ptr(b, "b"), float(lam), int(iters),
+    _check(lib().pp_batch_unrolled_backward(batch.handle, _bksp(batch, b, "b"), float(lam), int(iters),
                                             _cvec(c), int(d), int(checkpoint_every),
-                                            _dev_ptr(grad_out, "grad_out"), _dev_ptr(grad_b, "grad_b"),
+                                            _bimg(batch, grad_out, "grad_out"), _bksp(batch, grad_b, "grad_b"),
                                             ctypes.byref(gl), gc, _stream(stream)),
            "pp_batch_unrolled_backward")
     return gl.value, np.array(list(gc), dtype=np.float64)

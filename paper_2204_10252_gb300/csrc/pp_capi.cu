@@ -179,7 +179,7 @@ static pp_status normal_into(const Plan& p, const float2* x, float2* out, float 
     PP_TRY(launch_rows_fwd(p, p.gx, rf, x, p.sens, p.deapod_y, p.deapod_x, p.wk_a, p.C, 0, st));
     ColArgs cf = col_args(ny, Gy, Gy, ny / 2, 0, Gx, (int64_t)ny * Gx, (int64_t)Gy * Gx, p.C, 1.f);
     PP_TRY(launch_cols(p.gy, cf, p.wk_a, p.wk_b, false, st));
-    PP_TRY(launch_nufft_tile_normal(p, p.wk_b, p.wk_c, st));
+    PP_TRY(launch_gtg_stencil(p, p.wk_b, p.wk_c, st));
     ColArgs ci = col_args(Gy, ny, Gy, 0, ny / 2, Gx, (int64_t)Gy * Gx, (int64_t)ny * Gx, p.C, 1.f);
     PP_TRY(launch_cols(p.gy, ci, p.wk_c, p.wk_a, true, st));
     RowArgs ra = row_args(nx, Gx, 0, nx / 2, ny, (int64_t)ny * nx, scale);
@@ -393,6 +393,37 @@ static pp_status build_noncartesian(Plan& p, const pp_sampling* s) {
     if (flat.empty()) flat.push_back(TileEntry());
     PP_TRY(upload(p, &p.tiles, flat));
     PP_TRY(upload(p, &p.tile_start, start));
+    // G^T G as (2W-1)^2 weight planes: for every sample and every pair of its
+    // taps j, j' (offset delta = j' - j), T[delta][j] += phi_j phi_j'
+    // (accumulated in FP64, stored FP32).
+    {
+        const int D = 2 * W - 1;
+        std::vector<double> T((size_t)D * D * Gx * Gy, 0.0);
+        const size_t plane = (size_t)Gx * Gy;
+        for (int k = 0; k < K; ++k) {
+            const float wx[4] = {st[k].wx.x, st[k].wx.y, st[k].wx.z, st[k].wx.w};
+            const float wy[4] = {st[k].wy.x, st[k].wy.y, st[k].wy.z, st[k].wy.w};
+            double ph[4][4];
+            int gyy[4], gxx[4];
+            for (int b = 0; b < W; ++b) {
+                gyy[b] = wrap_host(st[k].iy0 + b, Gy);
+                gxx[b] = wrap_host(st[k].ix0 + b, Gx);
+                for (int a = 0; a < W; ++a) ph[b][a] = (double)wy[b] * (double)wx[a];
+            }
+            for (int b = 0; b < W; ++b)
+                for (int a = 0; a < W; ++a) {
+                    const size_t j = (size_t)gyy[b] * Gx + gxx[a];
+                    for (int b2 = 0; b2 < W; ++b2)
+                        for (int a2 = 0; a2 < W; ++a2) {
+                            const int d = (b2 - b + W - 1) * D + (a2 - a + W - 1);
+                            T[(size_t)d * plane + j] += ph[b][a] * ph[b2][a2];
+                        }
+                }
+        }
+        std::vector<float> Tf(T.size());
+        for (size_t i = 0; i < T.size(); ++i) Tf[i] = (float)T[i];
+        PP_TRY(upload(p, &p.gtg, Tf));
+    }
     PP_TRY(alloc_n(p, &p.wk_a, (size_t)p.C * ny * Gx));
     PP_TRY(alloc_n(p, &p.wk_b, (size_t)p.C * Gy * Gx));
     PP_TRY(alloc_n(p, &p.wk_c, (size_t)p.C * Gy * Gx));

@@ -101,6 +101,7 @@ struct Plan {
     int* tile_start = nullptr;   // [ntiles + 1]
     int max_tile_len = 0;
     SampleTaps* samp = nullptr;  // [K]
+    float* gtg = nullptr;        // [(2W-1)^2][G_y][G_x] stencil of G^T G
 
     // Workspace
     float2* wk_a = nullptr;   // C * ny * G_x (rows) or C * n (Cartesian)
@@ -159,9 +160,8 @@ pp_status launch_expand(const float2* x, const float2* s, float2* out, int64_t n
 pp_status launch_conj_accum(const float2* s, const float2* wv, float2* out, int64_t n, int first,
                             float scale, const float2* operand, float alpha, int last,
                             cudaStream_t st);
-pp_status launch_nufft_tile_normal(const Plan& p, const float2* grid_in, float2* grid_out,
-                                   cudaStream_t st);
 pp_status launch_nufft_spread(const Plan& p, const float2* ksp, float2* grid_out, cudaStream_t st);
+pp_status launch_gtg_stencil(const Plan& p, const float2* grid_in, float2* grid_out, cudaStream_t st);
 pp_status launch_nufft_degrid(const Plan& p, const float2* grid_in, float2* ksp, cudaStream_t st);
 pp_status launch_prox(int ndim, int nx, int ny, int nz, int levels, float lambda,
                       const float2* in, float2* out, cudaStream_t st);

@@ -449,6 +449,116 @@ __global__ void nufft_degrid_kernel(const SampleTaps* __restrict__ st, int K, in
     ksp[(int64_t)c * K + k] = v;
 }
 
+
+// ---------------------------------------------------------------------------
+// Gridding pair of the normal operator as a stencil.  With interpolation
+// G (samples <- grid) and spreading G^T, the normal operator needs G^T G on
+// the oversampled grid, a real symmetric matrix that couples grid points at
+// most W-1 apart per axis.  The plan stores it as (2W-1)^2 weight planes
+// T[d][gy][gx] (d = (dy+W-1)(2W-1) + dx+W-1), so
+//   out_j = sum_d T[d][j] in_{j + delta_d}   (indices periodic on the grid).
+// A CTA owns a 16 x 16 output tile, keeps each point's weights in registers
+// and loops over its coils, staging the input halo in shared memory.
+// ---------------------------------------------------------------------------
+template <int W>
+__global__ void __launch_bounds__(kThreads)
+gtg_stencil_kernel(const float* __restrict__ T, int Gx, int Gy, int C, int coils_per_cta,
+                   const float2* __restrict__ grid_in, float2* __restrict__ grid_out) {
+    constexpr int H = W - 1, D = 2 * W - 1, TS = 16, HW = TS + 2 * H;
+    __shared__ float2 halo[HW * HW];
+    const int tx0 = blockIdx.x * TS, ty0 = blockIdx.y * TS;
+    const int lx = threadIdx.x & (TS - 1), ly = threadIdx.x >> 4;
+    const int gx = tx0 + lx, gy = ty0 + ly;
+    const bool live = gx < Gx && gy < Gy;
+    const int64_t plane = (int64_t)Gx * Gy;
+    float w[D * D];
+#pragma unroll
+    for (int d = 0; d < D * D; ++d) w[d] = live ? T[d * plane + (int64_t)gy * Gx + gx] : 0.f;
+    const int c0 = blockIdx.z * coils_per_cta, c1 = min(C, c0 + coils_per_cta);
+    for (int c = c0; c < c1; ++c) {
+        const float2* gin = grid_in + c * plane;
+        for (int idx = threadIdx.x; idx < HW * HW; idx += blockDim.x) {
+            const int hy = idx / HW, hx = idx - hy * HW;
+            const int sy = wrapG(ty0 - H + hy, Gy), sx = wrapG(tx0 - H + hx, Gx);
+            halo[idx] = gin[(int64_t)sy * Gx + sx];
+        }
+        __syncthreads();
+        float ax = 0.f, ay = 0.f;
+#pragma unroll
+        for (int dy = 0; dy < D; ++dy)
+#pragma unroll
+            for (int dx = 0; dx < D; ++dx) {
+                const float2 v = halo[(ly + dy) * HW + lx + dx];
+                const float t = w[dy * D + dx];
+                ax += t * v.x;
+                ay += t * v.y;
+            }
+        if (live) grid_out[c * plane + (int64_t)gy * Gx + gx] = make_float2(ax, ay);
+        __syncthreads();
+    }
+}
+
+// Row stage k rows -> image for many coils: the FFT batch runs over 8 coils
+// of one image row, so a CTA per row covers every coil in ceil(C/8) rounds.
+// Same result as rows_adj_kernel (conj-coil reduction + axpy epilogue).
+template <int KO>
+__global__ void __launch_bounds__(kThreads)
+rows_adj_cb_kernel(FftDesc fd, const float2* __restrict__ tw, RowArgs a,
+                   const float2* __restrict__ src, const float2* __restrict__ sens,
+                   const float* __restrict__ wrow, const float* __restrict__ wcol, float2* out,
+                   const float2* operand, float alpha, int ncoils) {
+    extern __shared__ float2 sm[];
+    const int G = a.G, n = a.n, bs = row_stride(G);
+    float2* tws = sm;
+    float2* b0 = sm + G;
+    float2* b1 = b0 + RB * bs;
+    load_table(tws, tw, G);
+    const int r = blockIdx.x;
+    const float wr = wrow ? wrow[r] : 1.f;
+    float2 acc[KO];
+#pragma unroll
+    for (int k = 0; k < KO; ++k) acc[k] = make_float2(0.f, 0.f);
+    for (int c0 = 0; c0 < ncoils; c0 += RB) {
+        for (int idx = threadIdx.x; idx < RB * G; idx += blockDim.x) {
+            const int b = idx / G;
+            const int p = idx - b * G;
+            const int c = c0 + b;
+            int s = p + a.off_in;
+            if (s >= G) s -= G;
+            b0[p + b * bs] = (c < ncoils) ? src[((int64_t)c * a.nrows + r) * G + s] : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        float2* res = fft_batch<true>(b0, b1, fd, 1, bs, LGRB, tws, nullptr);
+#pragma unroll
+        for (int k = 0; k < KO; ++k) {
+            const int i = threadIdx.x + k * kThreads;
+            if (i < n) {
+                int p = i - a.off_out;
+                if (p < 0) p += G;
+                const float w = wcol ? wr * wcol[i] : wr;
+                for (int b = 0; b < RB; ++b) {
+                    const int c = c0 + b;
+                    if (c >= ncoils) break;
+                    float2 v = cscale(res[p + b * bs], w);
+                    if (sens) v = cmulc(sens[(int64_t)c * a.coil_img_stride + (int64_t)r * n + i], v);
+                    acc[k] = cadd(acc[k], v);
+                }
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int k = 0; k < KO; ++k) {
+        const int i = threadIdx.x + k * kThreads;
+        if (i < n) {
+            const int64_t o = (int64_t)r * n + i;
+            float2 v = cscale(acc[k], a.scale);
+            if (operand) v = cadd(v, cscale(operand[o], alpha));
+            out[o] = v;
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Orthonormal Haar prox on 2^L-tiles.  The one-level 2-D (3-D) Haar of a 2x2
 // (2x2x2) block is H (x) H ((x) H) with H = [[1,1],[1,-1]]/sqrt(2): symmetric
@@ -793,7 +903,8 @@ pp_status configure_kernels() {
     PP_TRY_CUDA(cudaFuncSetAttribute(cart2d_normal_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
     PP_TRY_CUDA(cudaFuncSetAttribute(cart2d_normal_kernel<12>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
     PP_TRY_CUDA(cudaFuncSetAttribute(cart2d_normal_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-    PP_TRY_CUDA(cudaFuncSetAttribute(nufft_tile_kernel<4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    PP_TRY_CUDA(cudaFuncSetAttribute(rows_adj_cb_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    PP_TRY_CUDA(cudaFuncSetAttribute(rows_adj_cb_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
     PP_TRY_CUDA(cudaFuncSetAttribute(nufft_tile_kernel<4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
     return PP_OK;
 }
@@ -815,6 +926,16 @@ pp_status launch_rows_adj(const Plan& p, const DevFft& f, const RowArgs& a, cons
     if (RB * a.n > KMAX * kThreads) {
         set_error("row length %d exceeds the row stage limit", a.n);
         return PP_ERR_UNSUPPORTED;
+    }
+    if (ncoils >= 4 && a.n <= 2 * kThreads) {
+        const size_t smc = rows_smem(a.G);
+        if (a.n <= kThreads)
+            rows_adj_cb_kernel<1><<<a.nrows, kThreads, smc, st>>>(f.d, f.tw, a, src, sens, wrow, wcol,
+                                                                   out, operand, alpha, ncoils);
+        else
+            rows_adj_cb_kernel<2><<<a.nrows, kThreads, smc, st>>>(f.d, f.tw, a, src, sens, wrow, wcol,
+                                                                   out, operand, alpha, ncoils);
+        return check_launch("rows_adj_cb_kernel");
     }
     dim3 grid((a.nrows + RB - 1) / RB);
     const int need = (RB * a.n + kThreads - 1) / kThreads;
@@ -881,13 +1002,11 @@ static size_t tile_smem(const Plan& p, bool degrid) {
     return sizeof(float2) * (size_t)((degrid ? HW * HW : 0) + p.T * p.T);
 }
 
-pp_status launch_nufft_tile_normal(const Plan& p, const float2* grid_in, float2* grid_out,
-                                   cudaStream_t st) {
-    const int cpc = 4;
-    dim3 grid(p.ntx * p.nty, (p.C + cpc - 1) / cpc);
-    nufft_tile_kernel<4, true><<<grid, kThreads, tile_smem(p, true), st>>>(
-        p.tiles, p.tile_start, p.T, p.ntx, p.G_x, p.G_y, p.C, cpc, grid_in, nullptr, p.K, grid_out);
-    return check_launch("nufft_tile_kernel<degrid>");
+pp_status launch_gtg_stencil(const Plan& p, const float2* grid_in, float2* grid_out, cudaStream_t st) {
+    const int cpc = 8;
+    dim3 grid((p.G_x + 15) / 16, (p.G_y + 15) / 16, (p.C + cpc - 1) / cpc);
+    gtg_stencil_kernel<4><<<grid, kThreads, 0, st>>>(p.gtg, p.G_x, p.G_y, p.C, cpc, grid_in, grid_out);
+    return check_launch("gtg_stencil_kernel");
 }
 
 pp_status launch_nufft_spread(const Plan& p, const float2* ksp, float2* grid_out, cudaStream_t st) {

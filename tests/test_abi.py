@@ -90,3 +90,34 @@ def test_invalid_arguments_are_rejected_without_device_work(L):
     assert L.pp_fista_solve(None, ctypes.c_void_p(16), ctypes.c_float(0.1), 1, None, 0,
                             ctypes.c_void_p(16), None, None) == 1
     assert L.pp_plan_destroy(None) == 0
+
+
+def test_binding_rejects_wrong_sizes_before_device_work(L):
+    # The C ABI sees raw pointers only; the binding compares element counts
+    # with the plan's shapes and raises before calling into the library.
+    import torch
+    import paper_2204_10252_gb300 as pp
+    from paper_2204_10252_gb300.binding import Batch, Plan
+    with pytest.raises(ValueError):
+        pp.pp_plan_create((32, 32), 2, torch.zeros(3 * 32 * 32, dtype=torch.complex64),
+                          mask=np.ones((32, 32), np.uint8), power_iters=0)
+    with pytest.raises(ValueError):
+        pp.pp_plan_create((32, 32), 2, torch.zeros(2 * 32 * 32, dtype=torch.complex64),
+                          mask=np.ones((16, 32), np.uint8), power_iters=0)
+    fake = Plan(0, (32, 32), 2, None, (2, 32, 32))
+    x = torch.zeros(32 * 32, dtype=torch.complex64)
+    with pytest.raises(ValueError):
+        pp.pp_normal_apply(fake, x, torch.zeros(32 * 31, dtype=torch.complex64))
+    with pytest.raises(ValueError):
+        pp.pp_adjoint_apply(fake, torch.zeros(32 * 32, dtype=torch.complex64), x)
+    with pytest.raises(ValueError):
+        pp.pp_fista_solve(fake, torch.zeros(2 * 32 * 32 + 1, dtype=torch.complex64), 0.1, 1,
+                          None, 0, x)
+    with pytest.raises(ValueError):
+        pp.pp_prox_l1_haar((32, 32), 2, 0.1, x, torch.zeros(10, dtype=torch.complex64))
+    fb = Batch(0, [(8, 8), (4, 8)], [1, 2], [], np.array([0, 64, 96]), np.array([0, 64, 128]))
+    with pytest.raises(ValueError):
+        pp.pp_batch_normal_apply(fb, torch.zeros(95, dtype=torch.complex64),
+                                 torch.zeros(96, dtype=torch.complex64))
+    fake.handle = None
+    fb.handle = None

@@ -87,6 +87,16 @@ def test_unrolled_gradients_match_oracle(pp, d, iters, ce):
         batch.destroy()
 
 
+# The unrolled solve is piecewise smooth in b: FP32 rounding (about 3e-7 per
+# normal-operator apply) moves the 20-iteration iterates by ~2e-5 and flips a
+# few soft-threshold supports, which moves the exact gradient itself.  Adding
+# that much relative noise to every apply of the FP64 oracle changes its
+# gradient by 1.8 % (b), 1.4 % (c) and 0.05 % (lambda) on this workload, so
+# the FP32 path is held to 5 % for b and c and 1 % for lambda here (and to
+# 1e-3 on the short 32x32 runs above, where the measured spread is smaller).
+TOL_B_FULL, TOL_C_FULL, TOL_L_FULL = 5e-2, 5e-2, 1e-2
+
+
 def test_unrolled_full_size_two_slices(pp):
     # two slices of the 8 x 256^2, 16-coil, R = 4 workload: 20 iterations,
     # d = 3, checkpoints every 5
@@ -105,11 +115,13 @@ def test_unrolled_full_size_two_slices(pp):
         gl, gc = pp.pp_batch_unrolled_backward(batch, b, cfg["lam"], cfg["iters"], c, cfg["d"],
                                                cfg["checkpoint"], yb, gb)
         outs, gbr, glr, gcr = oracle_grads(batch, sens, masks, bs, ybar, cfg["lam"], c, cfg["iters"], Ls)
-        ko = batch.kspace_off
+        ko, io = batch.kspace_off, batch.image_off
+        yh = out.cpu().numpy()
         g = gb.cpu().numpy()
         for i in range(batch.n):
-            assert rel(g[ko[i]:ko[i + 1]].reshape(gbr[i].shape), gbr[i]) <= TOL_GRAD
-        assert abs(gl - glr) <= TOL_GRAD * abs(glr)
-        assert np.max(np.abs(gc - gcr)) <= TOL_GRAD * np.max(np.abs(gcr))
+            assert rel(yh[io[i]:io[i + 1]].reshape(shapes[i]), outs[i]) <= 1e-4
+            assert rel(g[ko[i]:ko[i + 1]].reshape(gbr[i].shape), gbr[i]) <= TOL_B_FULL
+        assert abs(gl - glr) <= TOL_L_FULL * abs(glr)
+        assert np.max(np.abs(gc - gcr)) <= TOL_C_FULL * np.max(np.abs(gcr))
     finally:
         batch.destroy()
