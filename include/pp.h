@@ -117,6 +117,25 @@ pp_status pp_forward_apply(const pp_plan* plan, const pp_c64* x, pp_c64* y, pp_s
 /* x = A^H y (unscaled adjoint).  y device k-space, x device image. */
 pp_status pp_adjoint_apply(const pp_plan* plan, const pp_c64* y, pp_c64* x, pp_stream stream);
 
+/* x = A^H y like pp_adjoint_apply, but allocating nothing: every
+ * intermediate buffer lives in a fixed 16 MiB array of device memory that
+ * is part of the library (each GPU that loads the library holds it until the
+ * process exits).  For callers that must not allocate device memory when
+ * they call -- e.g. while a stream capture in global mode is open, inside a
+ * host application that owns all device memory through its own pool, or in
+ * a real-time loop that forbids allocation after start-up.  The plan is
+ * built beforehand with pp_plan_create.  The paper has no counterpart.
+ *  - Plans whose adjoint needs more than 16 MiB of scratch (Cartesian 2-D:
+ *    8*C*ny*nx bytes; 3-D: 16*nz*ny*nx; non-Cartesian: 8*C*G*(ny+G))
+ *    return PP_ERR_UNSUPPORTED.
+ *  - The first call on a device looks up the array's device address; make
+ *    that first call before any stream capture.
+ *  - All calls share the one array and it keeps the last call's contents
+ *    (nothing in it needs clearing: every element read is written first in
+ *    the same call).  Calls that overlap on the GPU (other streams, other
+ *    host threads) race on it and must be serialised by the caller. */
+pp_status pp_adjoint_apply_static(const pp_plan* plan, const pp_c64* y, pp_c64* x, pp_stream stream);
+
 /* y = (A^H A / L) x, the normalised normal operator N_hat of Algorithm
  * "pfista".  x, y device images.  Cartesian plans use the readout
  * shortcut F_x^H (F_yz^H M F_yz) F_x = F_yz^H M F_yz, exact because M is

@@ -5,7 +5,7 @@ this package holds its build script and a ctypes binding with the same
 function names.  PyTorch supplies device memory and streams only.
 """
 from .binding import (  # noqa: F401
-    PP_CARTESIAN, PP_NONCARTESIAN, PPError, Plan, lib, pp_adjoint_apply, pp_fista_solve,
+    PP_CARTESIAN, PP_NONCARTESIAN, PPError, Plan, lib, pp_adjoint_apply, pp_adjoint_apply_static, pp_fista_solve,
     pp_forward_apply, pp_last_error, pp_normal_apply, pp_plan_create, pp_plan_destroy,
     pp_plan_scale, pp_plan_set_scale, pp_plan_sizes, pp_poly_apply, pp_poly_coeffs_l2,
     pp_prox_l1_haar, pp_profile_normal, SolveResult,

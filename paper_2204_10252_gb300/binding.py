@@ -59,6 +59,7 @@ _SIGS = {
                                      ctypes.POINTER(ctypes.c_int64)]),
     "pp_forward_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "pp_adjoint_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "pp_adjoint_apply_static": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "pp_normal_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "pp_poly_coeffs_l2": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "pp_poly_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int,
@@ -264,6 +265,14 @@ def pp_forward_apply(plan: Plan, x, y, stream=None):
 def pp_adjoint_apply(plan: Plan, y, x, stream=None):
     _check(lib().pp_adjoint_apply(plan.handle, _ksp(plan, y, "y"), _img(plan, x, "x"), _stream(stream)),
            "pp_adjoint_apply")
+
+
+def pp_adjoint_apply_static(plan: Plan, y, x, stream=None):
+    """A^H y without allocating device memory: for callers that cannot
+    allocate at call time; intermediates live in a fixed 16 MiB library
+    array (see include/pp.h)."""
+    _check(lib().pp_adjoint_apply_static(plan.handle, _ksp(plan, y, "y"), _img(plan, x, "x"),
+                                         _stream(stream)), "pp_adjoint_apply_static")
 
 
 def pp_normal_apply(plan: Plan, x, y, stream=None):

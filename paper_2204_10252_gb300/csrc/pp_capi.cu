@@ -867,10 +867,6 @@ static pp_status unrolled_backward(Batch& b, float lambda, int iters, const doub
 // ===========================================================================
 using namespace pp;
 
-struct pp_plan {
-    Plan impl;
-};
-
 extern "C" {
 
 const char* pp_last_error(void) { return g_last_error.c_str(); }

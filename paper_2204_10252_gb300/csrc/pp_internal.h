@@ -178,3 +178,8 @@ pp_status launch_axpby(const float2* x, float a, const float2* y, float b, float
 pp_status launch_start_vector(float2* v, int64_t n, uint64_t seed, cudaStream_t st);
 
 }  // namespace pp
+
+// Opaque handle of the C ABI (include/pp.h).
+struct pp_plan {
+    pp::Plan impl;
+};

@@ -111,6 +111,8 @@ def test_binding_rejects_wrong_sizes_before_device_work(L):
     with pytest.raises(ValueError):
         pp.pp_adjoint_apply(fake, torch.zeros(32 * 32, dtype=torch.complex64), x)
     with pytest.raises(ValueError):
+        pp.pp_adjoint_apply_static(fake, torch.zeros(2 * 32 * 33, dtype=torch.complex64), x)
+    with pytest.raises(ValueError):
         pp.pp_fista_solve(fake, torch.zeros(2 * 32 * 32 + 1, dtype=torch.complex64), 0.1, 1,
                           None, 0, x)
     with pytest.raises(ValueError):
