@@ -10,7 +10,7 @@ from .binding import (  # noqa: F401
     pp_plan_scale, pp_plan_set_scale, pp_plan_sizes, pp_poly_apply, pp_poly_coeffs_l2,
     pp_prox_l1_haar, pp_profile_normal, SolveResult,
     Batch, pp_batch_create, pp_batch_destroy, pp_batch_offsets, pp_batch_scales, pp_batch_set_scales,
-    pp_batch_tile, pp_batch_forward_apply, pp_batch_adjoint_apply, pp_batch_normal_apply,
+    pp_batch_tile, pp_batch_set_tile, pp_batch_forward_apply, pp_batch_adjoint_apply, pp_batch_normal_apply,
     pp_batch_fista_solve, pp_batch_unrolled_forward, pp_batch_unrolled_backward,
 )
 from .autograd import UnrolledPFISTA, unrolled_pfista  # noqa: F401

@@ -80,6 +80,7 @@ _SIGS = {
     "pp_batch_scales": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "pp_batch_set_scales": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "pp_batch_tile": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "pp_batch_set_tile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "pp_batch_forward_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "pp_batch_adjoint_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "pp_batch_normal_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
@@ -440,6 +441,10 @@ def _bimg(batch, t, what):
 def _bksp(batch, t, what):
     _numel(t, int(batch.kspace_off[-1]), what)
     return _dev_ptr(t, what)
+
+
+def pp_batch_set_tile(batch: Batch, cols_per_cta: int):
+    _check(lib().pp_batch_set_tile(batch.handle, int(cols_per_cta)), "pp_batch_set_tile")
 
 
 def pp_batch_forward_apply(batch: Batch, x, y, stream=None):

@@ -10,7 +10,7 @@ struct SliceDesc {
     const float2* tw;        // its twiddle table
     const float2* sens;      // [C][ny][nx] (borrowed)
     const float* mask_fo;    // [ny], FFT order, times 1/ny
-    int ny, nx, C, pad0;
+    int ny, nx, C, n2;       // n2 = ny / 16 when ny has a register FFT, else 0
     int64_t img_off;         // offset of the slice in concatenated images
     float invL, pad1;
 };
@@ -28,6 +28,7 @@ struct BatchDev {
     SliceDesc* descs = nullptr;
     int2* items = nullptr;   // (slice, first column), most expensive first
     int nitems = 0, ny_max = 0, km = 0, lgt = 3, grid = 0;
+    int fast4 = 0;           // 1: the four-step register-FFT kernel runs the items
     Segments img, ksp, tiles;
 };
 
@@ -41,6 +42,7 @@ struct LinComb {
 size_t batch_normal_smem(int ny_max, int lgt);
 void* batch_normal_fn(int km, int lgt);
 pp_status configure_batch_kernels();
+int batch4_grid();   // persistent grid of the four-step batched kernel
 pp_status launch_batch_normal(const BatchDev& b, const float2* x, float2* out, float coef,
                               const float2* operand, float alpha, cudaStream_t st);
 pp_status launch_seg_dot(const float2* a, const float2* bv, const Segments& sg, double* partials,

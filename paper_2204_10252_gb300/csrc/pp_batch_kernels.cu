@@ -8,6 +8,7 @@
 #include <algorithm>
 
 #include "pp_batch.h"
+#include "pp_fft4.cuh"
 
 namespace pp {
 
@@ -392,6 +393,43 @@ __global__ void lincomb_kernel(LinComb lc, float2* __restrict__ out, int64_t n, 
     }
 }
 
+// Four-step register-FFT version of cart2d_batch_normal_kernel: every slice
+// must have ny = 16 * n2 with n2 in {8, 12, 16, 20, 24}; items are 8 columns.
+__global__ void __launch_bounds__(192, 2)
+cart2d_batch4_kernel(const SliceDesc* __restrict__ descs, const int2* __restrict__ items, int nitems,
+                     const float2* __restrict__ x, float2* out, float coef, const float2* operand,
+                     float alpha) {
+    __shared__ float2 tws[384];
+    __shared__ float pm[384];
+    __shared__ float2 Y[16 * 24 * 8];
+    int cur = -1;
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const int2 item = items[it];
+        const int s = item.x;
+        const SliceDesc D = descs[s];
+        if (s != cur) {
+            __syncthreads();
+            for (int i = threadIdx.x; i < D.ny; i += blockDim.x) {
+                tws[i] = D.tw[i];
+                pm[i] = D.mask_fo[i];
+            }
+            __syncthreads();
+            cur = s;
+        }
+        const float2* xs = x + D.img_off;
+        float2* os = out + D.img_off;
+        const float2* ops = operand ? operand + D.img_off : nullptr;
+        const float sc = coef * D.invL;
+        switch (D.n2) {
+            case 8: cart_item4<8>(tws, pm, Y, xs, D.sens, D.C, D.nx, item.y, os, sc, ops, alpha); break;
+            case 12: cart_item4<12>(tws, pm, Y, xs, D.sens, D.C, D.nx, item.y, os, sc, ops, alpha); break;
+            case 16: cart_item4<16>(tws, pm, Y, xs, D.sens, D.C, D.nx, item.y, os, sc, ops, alpha); break;
+            case 20: cart_item4<20>(tws, pm, Y, xs, D.sens, D.C, D.nx, item.y, os, sc, ops, alpha); break;
+            default: cart_item4<24>(tws, pm, Y, xs, D.sens, D.C, D.nx, item.y, os, sc, ops, alpha); break;
+        }
+    }
+}
+
 }  // namespace
 
 extern thread_local int64_t g_launches;
@@ -435,8 +473,21 @@ pp_status configure_batch_kernels() {
     return PP_OK;
 }
 
+int batch4_grid() {
+    int occ = 0, nsm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, cart2d_batch4_kernel, 192, 0) != cudaSuccess)
+        occ = 1;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, 0) != cudaSuccess) nsm = 152;
+    return std::max(1, occ) * nsm;
+}
+
 pp_status launch_batch_normal(const BatchDev& b, const float2* x, float2* out, float coef,
                               const float2* operand, float alpha, cudaStream_t st) {
+    if (b.fast4) {
+        cart2d_batch4_kernel<<<std::min(b.grid, b.nitems), 192, 0, st>>>(b.descs, b.items, b.nitems, x,
+                                                                        out, coef, operand, alpha);
+        return check_launch_b("cart2d_batch4_kernel");
+    }
     void* fn = batch_normal_fn(b.km, b.lgt);
     if (!fn) {
         set_error("no batched kernel for km=%d lgt=%d", b.km, b.lgt);

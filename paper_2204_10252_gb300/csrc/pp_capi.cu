@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "pp_batch.h"
+#include "pp_fft4.cuh"
 #include "pp_internal.h"
 
 namespace pp {
@@ -159,6 +160,9 @@ static pp_status normal_into(const Plan& p, const float2* x, float2* out, float 
     if (p.kind == PP_CARTESIAN && p.ndim == 2)
         return launch_cart2d_normal(p, x, out, scale, operand, alpha, st);
     if (p.kind == PP_CARTESIAN) {
+        bool done = false;
+        PP_TRY(cart3d4_normal(p, x, out, scale, operand, alpha, p.wk_a, st, &done));
+        if (done) return PP_OK;
         // 3-D: per coil, y FFT -> (z FFT, mask, z IFFT) -> y IFFT -> conj accumulate
         for (int c = 0; c < p.C; ++c) {
             const float2* sc = p.sens + (int64_t)c * n;
@@ -431,6 +435,51 @@ static pp_status build_noncartesian(Plan& p, const pp_sampling* s) {
     return PP_OK;
 }
 
+// Plan-time autotuning of the non-Cartesian operator's launch shapes: the
+// row-IFFT cluster size and the stencil's coils per CTA are each timed on the
+// plan's own buffers (3 launches after one warm-up) and the fastest is kept.
+static pp_status tune_noncartesian(Plan& p, cudaStream_t st) {
+    cudaEvent_t e0, e1;
+    PP_TRY_CUDA(cudaEventCreate(&e0));
+    PP_TRY_CUDA(cudaEventCreate(&e1));
+    auto timeit = [&](auto&& fn, float* ms) -> pp_status {
+        PP_TRY(fn());
+        PP_TRY_CUDA(cudaEventRecord(e0, st));
+        for (int r = 0; r < 3; ++r) PP_TRY(fn());
+        PP_TRY_CUDA(cudaEventRecord(e1, st));
+        PP_TRY_CUDA(cudaEventSynchronize(e1));
+        PP_TRY_CUDA(cudaEventElapsedTime(ms, e0, e1));
+        return PP_OK;
+    };
+    PP_TRY_CUDA(cudaMemsetAsync(p.wk_a, 0, sizeof(float2) * (size_t)p.C * p.ny * p.G_x, st));
+    PP_TRY_CUDA(cudaMemsetAsync(p.wk_b, 0, sizeof(float2) * (size_t)p.C * p.G_y * p.G_x, st));
+    const int nx = p.nx, ny = p.ny, Gx = p.G_x;
+    RowArgs ra = row_args(nx, Gx, 0, nx / 2, ny, (int64_t)ny * nx, 1.f);
+    float best = 1e30f;
+    int best_cl = 1;
+    for (int cl : {1, 2, 4}) {
+        p.tune_rows_adj_cl = cl;
+        float ms = 0.f;
+        PP_TRY(timeit([&]() { return launch_rows_adj(p, p.gx, ra, p.wk_a, p.sens, p.deapod_y, p.deapod_x,
+                                                     p.t, nullptr, 0.f, p.C, st); }, &ms));
+        if (ms < best) { best = ms; best_cl = cl; }
+    }
+    p.tune_rows_adj_cl = best_cl;
+    best = 1e30f;
+    int best_cpc = 8;
+    for (int cpc : {2, 4, 8, 16, 32}) {
+        if (cpc > p.C && cpc != 2) continue;
+        p.tune_stencil_cpc = cpc;
+        float ms = 0.f;
+        PP_TRY(timeit([&]() { return launch_gtg_stencil(p, p.wk_b, p.wk_c, st); }, &ms));
+        if (ms < best) { best = ms; best_cpc = cpc; }
+    }
+    p.tune_stencil_cpc = best_cpc;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return PP_OK;
+}
+
 static pp_status power_iteration(Plan& p, uint64_t seed, int iters, cudaStream_t st) {
     const int64_t n = p.nimg;
     PP_TRY(launch_start_vector(p.v, n, seed, st));
@@ -630,9 +679,21 @@ static pp_status autotune(Batch& b, cudaStream_t st) {
     cudaEvent_t e0, e1;
     PP_TRY_CUDA(cudaEventCreate(&e0));
     PP_TRY_CUDA(cudaEventCreate(&e1));
-    for (int lgt = 2; lgt <= 4; ++lgt) {
-        if (!km_for(b.dev.ny_max, lgt)) continue;
-        PP_TRY(set_items(b, lgt, &items));
+    bool all_fast = true;
+    for (const SliceDesc& d : b.hdesc) all_fast = all_fast && d.n2 != 0;
+    // candidates: Stockham kernels with 4, 8 or 16 columns per item (lgt 2..4)
+    // and, when every slice length has one, the register four-step kernel (5)
+    for (int lgt = 2; lgt <= 5; ++lgt) {
+        if (lgt == 5) {
+            if (!all_fast) continue;
+            PP_TRY(set_items(b, 3, &items));
+            b.dev.fast4 = 1;
+            b.dev.grid = batch4_grid();
+        } else {
+            if (!km_for(b.dev.ny_max, lgt)) continue;
+            b.dev.fast4 = 0;
+            PP_TRY(set_items(b, lgt, &items));
+        }
         PP_TRY(launch_batch_normal(b.dev, b.v, b.t, 1.f, nullptr, 0.f, st));
         PP_TRY_CUDA(cudaEventRecord(e0, st));
         for (int r = 0; r < 3; ++r) PP_TRY(launch_batch_normal(b.dev, b.v, b.t, 1.f, nullptr, 0.f, st));
@@ -651,6 +712,13 @@ static pp_status autotune(Batch& b, cudaStream_t st) {
         set_error("no batched kernel fits ny_max = %d", b.dev.ny_max);
         return PP_ERR_UNSUPPORTED;
     }
+    if (best == 5) {
+        PP_TRY(set_items(b, 3, &items));
+        b.dev.fast4 = 1;
+        b.dev.grid = batch4_grid();
+        return PP_OK;
+    }
+    b.dev.fast4 = 0;
     return set_items(b, best, &items);
 }
 
@@ -980,6 +1048,7 @@ pp_status pp_plan_create(pp_plan** out, pp_dims dims, int coils, const pp_c64* s
             if (e != cudaSuccess) rc = cuda_status(e, "cudaStreamCreate");
         }
     }
+    if (rc == PP_OK && p.kind == PP_NONCARTESIAN) rc = tune_noncartesian(p, st);
     if (rc == PP_OK && power_iters > 0) rc = power_iteration(p, seed, power_iters, st);
     if (rc != PP_OK) {
         cudaStreamSynchronize(st);
@@ -1304,7 +1373,7 @@ pp_status pp_batch_create(pp_batch** out, int nslices, const pp_dims* dims, cons
         b.tile_off[s + 1] = b.tile_off[s] + p->nimg / 16;
         SliceDesc& d = b.hdesc[s];
         d.fd = p->fy.d; d.tw = p->fy.tw; d.sens = p->sens; d.mask_fo = p->mask_fo;
-        d.ny = p->ny; d.nx = p->nx; d.C = p->C; d.pad0 = 0; d.img_off = b.img_off[s];
+        d.ny = p->ny; d.nx = p->nx; d.C = p->C; d.n2 = fft4_n2(p->ny); d.img_off = b.img_off[s];
         d.invL = 1.f; d.pad1 = 0.f;
         b.dev.ny_max = std::max(b.dev.ny_max, p->ny);
     }
@@ -1413,8 +1482,37 @@ pp_status pp_batch_tile(const pp_batch* batch, int* cols_per_cta, int* persisten
         set_error("pp_batch_tile: NULL batch");
         return PP_ERR_INVALID_ARG;
     }
-    if (cols_per_cta) *cols_per_cta = 1 << batch->impl.dev.lgt;
+    if (cols_per_cta) *cols_per_cta = batch->impl.dev.fast4 ? -8 : 1 << batch->impl.dev.lgt;
     if (persistent_ctas) *persistent_ctas = batch->impl.dev.grid;
+    return PP_OK;
+}
+
+pp_status pp_batch_set_tile(pp_batch* batch, int cols_per_cta) {
+    if (!batch) {
+        set_error("pp_batch_set_tile: NULL batch");
+        return PP_ERR_INVALID_ARG;
+    }
+    Batch& b = batch->impl;
+    std::vector<int2> items;
+    if (cols_per_cta == -8) {
+        for (const SliceDesc& d : b.hdesc)
+            if (!d.n2) {
+                set_error("pp_batch_set_tile: slice length %d has no register FFT kernel", d.ny);
+                return PP_ERR_UNSUPPORTED;
+            }
+        PP_TRY(set_items(b, 3, &items));
+        b.dev.fast4 = 1;
+        b.dev.grid = batch4_grid();
+    } else {
+        const int lgt = cols_per_cta == 4 ? 2 : cols_per_cta == 8 ? 3 : cols_per_cta == 16 ? 4 : -1;
+        if (lgt < 0 || !km_for(b.dev.ny_max, lgt)) {
+            set_error("pp_batch_set_tile: unsupported tile width %d", cols_per_cta);
+            return PP_ERR_UNSUPPORTED;
+        }
+        b.dev.fast4 = 0;
+        PP_TRY(set_items(b, lgt, &items));
+    }
+    b.gkey.clear();
     return PP_OK;
 }
 

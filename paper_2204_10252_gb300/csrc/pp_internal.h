@@ -122,6 +122,9 @@ struct Plan {
     std::vector<double> gkey;
 
     bool external_wk = false;   // workspace supplied by an owner (batched plans)
+    // plan-time autotuned launch shapes (0 = default)
+    int tune_rows_adj_cl = 0;   // row-IFFT cluster size (1, 2 or 4)
+    int tune_stencil_cpc = 0;   // coils per CTA of the G^T G stencil
     std::vector<void*> allocs;
 };
 
@@ -144,6 +147,20 @@ extern thread_local Profiler* g_profiler;
 
 // ---- launchers (pp_kernels.cu) -------------------------------------------
 pp_status configure_kernels();
+// register four-step FFT stages (pp_kernels4.cu); *done = false when the
+// transform length has no register kernel
+pp_status launch_cols4(const DevFft& f, const ColArgs& a, const float2* src, float2* dst, bool inv,
+                       cudaStream_t st, bool* done);
+pp_status launch_rows4_fwd(const DevFft& f, const RowArgs& a, const float2* x, const float2* sens,
+                           const float* wrow, const float* wcol, float2* out, int ncoils,
+                           int64_t img_batch_stride, cudaStream_t st, bool* done);
+pp_status cart3d4_normal(const Plan& p, const float2* x, float2* out, float scale,
+                         const float2* operand, float alpha, float2* W, cudaStream_t st, bool* done);
+pp_status launch_cart2d4_normal(const Plan& p, const float2* x, float2* out, float scale,
+                                const float2* operand, float alpha, cudaStream_t st, bool* done);
+pp_status launch_rows4_adj(const DevFft& f, const RowArgs& a, const float2* src, const float2* sens,
+                           const float* wrow, const float* wcol, float2* out, const float2* operand,
+                           float alpha, int ncoils, cudaStream_t st, bool* done, int cluster = 0);
 pp_status launch_rows_fwd(const Plan& p, const DevFft& f, const RowArgs& a, const float2* x,
                           const float2* sens, const float* wrow, const float* wcol, float2* out,
                           int ncoils, int64_t img_batch_stride, cudaStream_t st);

@@ -465,36 +465,59 @@ __global__ void __launch_bounds__(kThreads)
 gtg_stencil_kernel(const float* __restrict__ T, int Gx, int Gy, int C, int coils_per_cta,
                    const float2* __restrict__ grid_in, float2* __restrict__ grid_out) {
     constexpr int H = W - 1, D = 2 * W - 1, TS = 16, HW = TS + 2 * H;
-    __shared__ float2 halo[HW * HW];
+    constexpr int HE = (HW * HW + kThreads - 1) / kThreads;   // halo elements per thread
+    __shared__ float2 halo[2][HW * HW];
     const int tx0 = blockIdx.x * TS, ty0 = blockIdx.y * TS;
     const int lx = threadIdx.x & (TS - 1), ly = threadIdx.x >> 4;
     const int gx = tx0 + lx, gy = ty0 + ly;
     const bool live = gx < Gx && gy < Gy;
     const int64_t plane = (int64_t)Gx * Gy;
+    // halo source offsets of this thread's elements (fixed for every coil)
+    int64_t hsrc[HE];
+#pragma unroll
+    for (int e = 0; e < HE; ++e) {
+        const int idx = threadIdx.x + e * kThreads;
+        const int hy = idx / HW, hx = idx - hy * HW;
+        hsrc[e] = (idx < HW * HW)
+                      ? (int64_t)wrapG(ty0 - H + hy, Gy) * Gx + wrapG(tx0 - H + hx, Gx)
+                      : -1;
+    }
     float w[D * D];
 #pragma unroll
     for (int d = 0; d < D * D; ++d) w[d] = live ? T[d * plane + (int64_t)gy * Gx + gx] : 0.f;
     const int c0 = blockIdx.z * coils_per_cta, c1 = min(C, c0 + coils_per_cta);
+    if (c0 >= c1) return;
+    float2 pre[HE];
+#pragma unroll
+    for (int e = 0; e < HE; ++e)
+        pre[e] = hsrc[e] >= 0 ? grid_in[c0 * plane + hsrc[e]] : make_float2(0.f, 0.f);
     for (int c = c0; c < c1; ++c) {
-        const float2* gin = grid_in + c * plane;
-        for (int idx = threadIdx.x; idx < HW * HW; idx += blockDim.x) {
-            const int hy = idx / HW, hx = idx - hy * HW;
-            const int sy = wrapG(ty0 - H + hy, Gy), sx = wrapG(tx0 - H + hx, Gx);
-            halo[idx] = gin[(int64_t)sy * Gx + sx];
+        float2* hb = halo[(c - c0) & 1];
+#pragma unroll
+        for (int e = 0; e < HE; ++e) {
+            const int idx = threadIdx.x + e * kThreads;
+            if (idx < HW * HW) hb[idx] = pre[e];
         }
         __syncthreads();
+        // prefetch the next coil's halo while this one is computed
+        if (c + 1 < c1) {
+#pragma unroll
+            for (int e = 0; e < HE; ++e)
+                pre[e] = hsrc[e] >= 0 ? grid_in[(c + 1) * plane + hsrc[e]] : make_float2(0.f, 0.f);
+        }
         float ax = 0.f, ay = 0.f;
 #pragma unroll
         for (int dy = 0; dy < D; ++dy)
 #pragma unroll
             for (int dx = 0; dx < D; ++dx) {
-                const float2 v = halo[(ly + dy) * HW + lx + dx];
+                const float2 v = hb[(ly + dy) * HW + lx + dx];
                 const float t = w[dy * D + dx];
                 ax += t * v.x;
                 ay += t * v.y;
             }
         if (live) grid_out[c * plane + (int64_t)gy * Gx + gx] = make_float2(ax, ay);
-        __syncthreads();
+        // the next iteration writes the other buffer; the one after that
+        // rewrites this one only after the next __syncthreads
     }
 }
 
@@ -913,6 +936,9 @@ pp_status launch_rows_fwd(const Plan& p, const DevFft& f, const RowArgs& a, cons
                           const float2* sens, const float* wrow, const float* wcol, float2* out,
                           int ncoils, int64_t img_batch_stride, cudaStream_t st) {
     (void)p;
+    bool done = false;
+    PP_TRY(launch_rows4_fwd(f, a, x, sens, wrow, wcol, out, ncoils, img_batch_stride, st, &done));
+    if (done) return PP_OK;
     dim3 grid((a.nrows + RB - 1) / RB, ncoils);
     rows_fwd_kernel<<<grid, kThreads, rows_smem(a.G), st>>>(f.d, f.tw, a, x, img_batch_stride, sens,
                                                             wrow, wcol, out);
@@ -923,6 +949,10 @@ pp_status launch_rows_adj(const Plan& p, const DevFft& f, const RowArgs& a, cons
                           const float2* sens, const float* wrow, const float* wcol, float2* out,
                           const float2* operand, float alpha, int ncoils, cudaStream_t st) {
     (void)p;
+    bool done = false;
+    PP_TRY(launch_rows4_adj(f, a, src, sens, wrow, wcol, out, operand, alpha, ncoils, st, &done,
+                            p.tune_rows_adj_cl));
+    if (done) return PP_OK;
     if (RB * a.n > KMAX * kThreads) {
         set_error("row length %d exceeds the row stage limit", a.n);
         return PP_ERR_UNSUPPORTED;
@@ -951,6 +981,9 @@ pp_status launch_rows_adj(const Plan& p, const DevFft& f, const RowArgs& a, cons
 
 pp_status launch_cols(const DevFft& f, const ColArgs& a, const float2* src, float2* dst, bool inv,
                       cudaStream_t st) {
+    bool done = false;
+    PP_TRY(launch_cols4(f, a, src, dst, inv, st, &done));
+    if (done) return PP_OK;
     dim3 grid((a.ncols + TX - 1) / TX, a.nbatch);
     if (inv)
         cols_kernel<true><<<grid, kThreads, cols_smem(a.G), st>>>(f.d, f.tw, a, src, dst);
@@ -968,6 +1001,9 @@ pp_status launch_cols_roundtrip(const DevFft& f, const ColArgs& a, const float* 
 
 pp_status launch_cart2d_normal(const Plan& p, const float2* x, float2* out, float scale,
                                const float2* operand, float alpha, cudaStream_t st) {
+    bool done = false;
+    PP_TRY(launch_cart2d4_normal(p, x, out, scale, operand, alpha, st, &done));
+    if (done) return PP_OK;
     if (p.ny * TX > KMAX * kThreads) {
         set_error("ny = %d exceeds the fused Cartesian kernel limit", p.ny);
         return PP_ERR_UNSUPPORTED;
@@ -1003,7 +1039,7 @@ static size_t tile_smem(const Plan& p, bool degrid) {
 }
 
 pp_status launch_gtg_stencil(const Plan& p, const float2* grid_in, float2* grid_out, cudaStream_t st) {
-    const int cpc = 8;
+    const int cpc = p.tune_stencil_cpc > 0 ? p.tune_stencil_cpc : 8;
     dim3 grid((p.G_x + 15) / 16, (p.G_y + 15) / 16, (p.C + cpc - 1) / cpc);
     gtg_stencil_kernel<4><<<grid, kThreads, 0, st>>>(p.gtg, p.G_x, p.G_y, p.C, cpc, grid_in, grid_out);
     return check_launch("gtg_stencil_kernel");

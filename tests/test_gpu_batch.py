@@ -111,4 +111,36 @@ def test_batch_solve(pp, batch, d):
 
 def test_batch_tile_is_one_of_the_candidates(pp, batch):
     t, grid = pp.pp_batch_tile(batch)
-    assert t in (4, 8, 16) and grid >= 1
+    assert t in (4, 8, 16, -8) and grid >= 1
+
+
+# every slice length has a register FFT (16 x {8, 12, 16, 20, 24}); nx ragged
+FAST = [((128, 24), 3, 3), ((192, 40), 2, 4), ((256, 16), 4, 3), ((320, 20), 2, 5), ((384, 12), 3, 4)]
+
+
+@pytest.mark.parametrize("tile", [-8, 4, 8, 16])
+def test_batch_variants_agree_with_oracle(pp, tile):
+    import torch
+    shapes = [s for s, _, _ in FAST]
+    coils = [c for _, c, _ in FAST]
+    sens = [synth.coil_maps(s, c, 70 + i) for i, (s, c, _) in enumerate(FAST)]
+    masks = [synth.line_mask(s, R, 8, 80 + i) for i, (s, _, R) in enumerate(FAST)]
+    b = pp.pp_batch_create(shapes, coils, [dev(x) for x in sens], masks, seed=1, power_iters=0)
+    try:
+        if tile == 16 and max(s[0] for s in shapes) > 256:
+            with pytest.raises(pp.PPError):
+                pp.pp_batch_set_tile(b, tile)
+            return
+        pp.pp_batch_set_tile(b, tile)
+        assert pp.pp_batch_tile(b)[0] == tile
+        L = np.linspace(0.7, 1.3, b.n)
+        pp.pp_batch_set_scales(b, L)
+        xs = [synth.crandn(s, 90 + i) for i, s in enumerate(shapes)]
+        x = dev(np.concatenate([v.ravel() for v in xs]))
+        y = torch.empty_like(x)
+        pp.pp_batch_normal_apply(b, x, y)
+        got = split(host(y), b.image_off, shapes)
+        for i in range(b.n):
+            assert rel(got[i], O.cart_normal(xs[i], sens[i], masks[i]) / L[i]) <= 1e-5
+    finally:
+        b.destroy()

@@ -85,8 +85,12 @@ CASES = [
     ("cart", (16, 24, 20), 3, dict(R=3, calib=4)),
     ("noncart", (64, 64), 4, dict(interleaves=4, samples=512)),
     ("noncart", (72, 80), 2, dict(interleaves=3, samples=700, turns=3.0, kmax=35.9)),
+    ("cart", (192, 256), 4, dict(R=3, acs=12)),
+    ("cart", (384, 128), 5, dict(R=4, acs=16)),
+    ("cart", (128, 192, 20), 2, dict(R=4, calib=8)),
 ]
-IDS = ["cart2d_64x48", "cart2d_128", "cart3d_16x24x20", "spiral_64", "spiral_72x80_ragged"]
+IDS = ["cart2d_64x48", "cart2d_128", "cart3d_16x24x20", "spiral_64", "spiral_72x80_ragged",
+       "cart2d_192x256", "cart2d_384x128", "cart3d_128x192x20"]
 
 
 @pytest.fixture(scope="module", params=list(range(len(CASES))), ids=IDS)
