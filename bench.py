@@ -179,6 +179,7 @@ def kernel_flops(c, K):
         "cols4_kernel": C * G * fft(G),
         "rows4_adj_kernel": C * ny * fft(G) + 10.0 * C * n,
         "rows4_adj_cl_kernel": C * ny * fft(G) + 10.0 * C * n,
+        "rows4_inv_kernel": C * ny * fft(G) + 8.0 * C * n,
     }
 
 

@@ -109,6 +109,16 @@ pp_status pp_plan_set_scale(pp_plan* plan, double L);
  * ([C][...] as above); either pointer may be NULL. */
 pp_status pp_plan_sizes(const pp_plan* plan, int64_t* image_elems, int64_t* kspace_elems);
 
+/* Launch shapes the plan chose by timing at creation (non-Cartesian plans):
+ * the row-IFFT stage of the normal operator (1, 2 or 4 = CTAs per image row,
+ * coil groups reduced through distributed shared memory; -1 = one IFFT per
+ * coil and row followed by a coil sum) and the G^T G stencil's coils per CTA
+ * (negative: the variant with two outputs per thread).
+ * pp_plan_set_tuning overrides them (results are identical up to rounding
+ * order).  No counterpart in the paper. */
+pp_status pp_plan_tuning(const pp_plan* plan, int* row_ifft_variant, int* stencil_coils);
+pp_status pp_plan_set_tuning(pp_plan* plan, int row_ifft_variant, int stencil_coils);
+
 /* y = A x (unscaled forward model; Sec. 5.1: M F S_c x with the centred
  * orthonormal FFT; Sec. 5.2: gridding NUFFT of S_c x).
  * x device image, y device k-space. */
@@ -149,6 +159,13 @@ pp_status pp_normal_apply(const pp_plan* plan, const pp_c64* x, pp_c64* y, pp_st
  * device work. */
 pp_status pp_poly_coeffs_l2(int d, double* c);
 
+/* c[0..d] (host double) of the Chebyshev minimax preconditioner of Sec. 3.4:
+ * with a = (1 + mu)/(1 - mu), r(z) = T_{d+1}(a - 2z/(1 - mu)) / T_{d+1}(a)
+ * (T the Chebyshev polynomial of the first kind) and p(z) = (1 - r(z))/z,
+ * which minimises max |1 - z p(z)| over [mu, 1].  0 < mu < 1, 0 <= d <= 8.
+ * Host only. */
+pp_status pp_poly_coeffs_cheb(int d, double mu, double* c);
+
 /* out = p(N_hat) v by the recursion of Listing "pcode": u = c_d v, then
  * u = c_i v + N_hat u for i = d-1..0 (d applies of N_hat).  c host double
  * [d+1], 0 <= d <= 16.  v, out device images. */
@@ -174,6 +191,7 @@ pp_status pp_prox_l1_haar(pp_dims dims, int levels, float lambda, const pp_c64* 
 typedef struct {
     int rescale;         /* in: 1 = multiply x_out by ||b|| / sqrt(L)        */
     int levels;          /* in: Haar levels (0 means 2)                      */
+    int no_momentum;     /* in: 1 = beta_k = 0, i.e. Algorithms "pgd"/"ppgd" */
     double* history;     /* in: optional host buffer, see above              */
     const pp_c64* ref;   /* in: optional device reference image              */
     double bnorm;        /* out: ||b||_2 (valid when history != NULL)        */

@@ -517,3 +517,14 @@ def pfista_unrolled_vjp(normal, adjoint, forward, b, lam, coeffs, iters, L, ybar
         ybar_next = ybar_cur
     b_bar = forward(ahb_bar) / math.sqrt(L)
     return b_bar, lam_bar, c_bar
+
+
+def poly_coeffs_cheb(d, mu):
+    """Chebyshev minimax preconditioner of Sec. 3.4 (Eq. "linfcost"):
+    r(z) = T_{d+1}((1 + mu - 2z)/(1 - mu)) / T_{d+1}((1 + mu)/(1 - mu)),
+    p(z) = (1 - r(z))/z, built with numpy's Chebyshev series mapped from
+    [mu, 1] onto [1, -1] and converted to the monomial basis."""
+    T = np.polynomial.Chebyshev.basis(d + 1, domain=[mu, 1.0], window=[1.0, -1.0])
+    r = T.convert(kind=np.polynomial.Polynomial).coef
+    r = r / r[0]
+    return [-float(v) for v in r[1:]]

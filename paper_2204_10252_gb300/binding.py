@@ -41,7 +41,7 @@ class pp_sampling(ctypes.Structure):
 
 
 class pp_solve_info(ctypes.Structure):
-    _fields_ = [("rescale", ctypes.c_int), ("levels", ctypes.c_int),
+    _fields_ = [("rescale", ctypes.c_int), ("levels", ctypes.c_int), ("no_momentum", ctypes.c_int),
                 ("history", ctypes.c_void_p), ("ref", ctypes.c_void_p),
                 ("bnorm", ctypes.c_double), ("L", ctypes.c_double), ("launches", ctypes.c_int64)]
 
@@ -55,6 +55,8 @@ _SIGS = {
     "pp_plan_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "pp_plan_scale": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     "pp_plan_set_scale": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
+    "pp_plan_tuning": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "pp_plan_set_tuning": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     "pp_plan_sizes": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
                                      ctypes.POINTER(ctypes.c_int64)]),
     "pp_forward_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
@@ -62,6 +64,7 @@ _SIGS = {
     "pp_adjoint_apply_static": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "pp_normal_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "pp_poly_coeffs_l2": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+    "pp_poly_coeffs_cheb": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]),
     "pp_poly_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int,
                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "pp_prox_l1_haar": (ctypes.c_int, [pp_dims, ctypes.c_int, ctypes.c_float, ctypes.c_void_p,
@@ -252,6 +255,17 @@ def pp_plan_set_scale(plan: Plan, L: float):
     _check(lib().pp_plan_set_scale(plan.handle, float(L)), "pp_plan_set_scale")
 
 
+def pp_plan_tuning(plan: Plan):
+    a, b = ctypes.c_int(0), ctypes.c_int(0)
+    _check(lib().pp_plan_tuning(plan.handle, ctypes.byref(a), ctypes.byref(b)), "pp_plan_tuning")
+    return a.value, b.value
+
+
+def pp_plan_set_tuning(plan: Plan, row_ifft_variant: int, stencil_coils: int):
+    _check(lib().pp_plan_set_tuning(plan.handle, int(row_ifft_variant), int(stencil_coils)),
+           "pp_plan_set_tuning")
+
+
 def pp_plan_sizes(plan: Plan):
     a, b = ctypes.c_int64(0), ctypes.c_int64(0)
     _check(lib().pp_plan_sizes(plan.handle, ctypes.byref(a), ctypes.byref(b)), "pp_plan_sizes")
@@ -287,6 +301,12 @@ def pp_poly_coeffs_l2(d: int) -> np.ndarray:
     return np.array(list(c), dtype=np.float64)
 
 
+def pp_poly_coeffs_cheb(d: int, mu: float) -> np.ndarray:
+    c = (ctypes.c_double * (max(d, 0) + 1))()
+    _check(lib().pp_poly_coeffs_cheb(int(d), float(mu), c), "pp_poly_coeffs_cheb")
+    return np.array(list(c), dtype=np.float64)
+
+
 def _cvec(c):
     c = np.ascontiguousarray(c, dtype=np.float64)
     return (ctypes.c_double * len(c))(*c.tolist())
@@ -316,12 +336,13 @@ class SolveResult:
 
 def pp_fista_solve(plan: Plan, b, lam: float, iters: int, c, d: int, x_out, stream=None,
                    history: bool = False, rescale: bool = False, levels: int = 2,
-                   ref=None) -> SolveResult:
+                   ref=None, momentum: bool = True) -> SolveResult:
     """c None with d = 0: plain FISTA.  history: per-iteration FP64
     ||y_{k+1}-y_k||^2, ||y_{k+1}||^2, ||y_{k+1}-ref||^2 (ref optional)."""
     info = pp_solve_info()
     info.rescale = 1 if rescale else 0
     info.levels = int(levels)
+    info.no_momentum = 0 if momentum else 1
     hist = None
     if history:
         hist = np.zeros((max(iters, 1), 3), dtype=np.float64)
@@ -463,10 +484,12 @@ def pp_batch_normal_apply(batch: Batch, x, y, stream=None):
 
 
 def pp_batch_fista_solve(batch: Batch, b, lam: float, iters: int, c, d: int, x_out, stream=None,
-                         history: bool = False, rescale: bool = False, ref=None) -> SolveResult:
+                         history: bool = False, rescale: bool = False, ref=None,
+                         momentum: bool = True) -> SolveResult:
     info = pp_solve_info()
     info.rescale = 1 if rescale else 0
     info.levels = 2
+    info.no_momentum = 0 if momentum else 1
     hist = None
     if history:
         hist = np.zeros((max(iters, 1), 3), dtype=np.float64)

@@ -187,6 +187,12 @@ static pp_status normal_into(const Plan& p, const float2* x, float2* out, float 
     ColArgs ci = col_args(Gy, ny, Gy, 0, ny / 2, Gx, (int64_t)Gy * Gx, (int64_t)ny * Gx, p.C, 1.f);
     PP_TRY(launch_cols(p.gy, ci, p.wk_c, p.wk_a, true, st));
     RowArgs ra = row_args(nx, Gx, 0, nx / 2, ny, (int64_t)ny * nx, scale);
+    if (p.tune_rows_adj_cl == -1) {
+        bool done = false;
+        PP_TRY(launch_rows4_adj_split(p.gx, ra, p.wk_a, p.sens, p.deapod_y, p.deapod_x, p.wk_c, out,
+                                      operand, alpha, p.C, st, &done));
+        if (done) return PP_OK;
+    }
     return launch_rows_adj(p, p.gx, ra, p.wk_a, p.sens, p.deapod_y, p.deapod_x, out, operand, alpha,
                            p.C, st);
 }
@@ -457,24 +463,37 @@ static pp_status tune_noncartesian(Plan& p, cudaStream_t st) {
     RowArgs ra = row_args(nx, Gx, 0, nx / 2, ny, (int64_t)ny * nx, 1.f);
     float best = 1e30f;
     int best_cl = 1;
-    for (int cl : {1, 2, 4}) {
+    for (int cl : {1, 2, 4, -1}) {
         p.tune_rows_adj_cl = cl;
         float ms = 0.f;
-        PP_TRY(timeit([&]() { return launch_rows_adj(p, p.gx, ra, p.wk_a, p.sens, p.deapod_y, p.deapod_x,
-                                                     p.t, nullptr, 0.f, p.C, st); }, &ms));
+        if (cl == -1) {
+            bool ok = fft4_n2(Gx) != 0;
+            if (!ok) continue;
+            PP_TRY(timeit([&]() {
+                bool done = false;
+                return launch_rows4_adj_split(p.gx, ra, p.wk_a, p.sens, p.deapod_y, p.deapod_x, p.wk_c,
+                                              p.t, nullptr, 0.f, p.C, st, &done);
+            }, &ms));
+        } else {
+            PP_TRY(timeit([&]() { return launch_rows_adj(p, p.gx, ra, p.wk_a, p.sens, p.deapod_y,
+                                                         p.deapod_x, p.t, nullptr, 0.f, p.C, st); }, &ms));
+        }
         if (ms < best) { best = ms; best_cl = cl; }
     }
     p.tune_rows_adj_cl = best_cl;
     best = 1e30f;
-    int best_cpc = 8;
-    for (int cpc : {2, 4, 8, 16, 32}) {
-        if (cpc > p.C && cpc != 2) continue;
-        p.tune_stencil_cpc = cpc;
-        float ms = 0.f;
-        PP_TRY(timeit([&]() { return launch_gtg_stencil(p, p.wk_b, p.wk_c, st); }, &ms));
-        if (ms < best) { best = ms; best_cpc = cpc; }
-    }
+    int best_cpc = 8, best_two = 0;
+    for (int two : {0, 1})
+        for (int cpc : {2, 4, 8, 16, 32}) {
+            if (cpc > p.C && cpc != 2) continue;
+            p.tune_stencil_cpc = cpc;
+            p.tune_stencil_two = two;
+            float ms = 0.f;
+            PP_TRY(timeit([&]() { return launch_gtg_stencil(p, p.wk_b, p.wk_c, st); }, &ms));
+            if (ms < best) { best = ms; best_cpc = cpc; best_two = two; }
+        }
     p.tune_stencil_cpc = best_cpc;
+    p.tune_stencil_two = best_two;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return PP_OK;
@@ -527,7 +546,8 @@ static pp_status horner_into(const Plan& p, const double* c, int d, const float2
 }
 
 static pp_status fista_iterations(Plan& p, float lambda, int iters, const double* c, int d,
-                                  int levels, bool hist, const float2* ref, cudaStream_t st) {
+                                  int levels, bool hist, const float2* ref, bool momentum,
+                                  cudaStream_t st) {
     const float invL = (float)(1.0 / p.L);
     for (int k = 0; k < iters; ++k) {
         // g = N_hat z - A_hat^H b_hat
@@ -540,7 +560,7 @@ static pp_status fista_iterations(Plan& p, float lambda, int iters, const double
         } else if (c) {
             gamma = (float)c[0];
         }
-        const float beta = (float)((double)k / (k + 3.0));
+        const float beta = momentum ? (float)((double)k / (k + 3.0)) : 0.f;
         PP_TRY(launch_prox_fista(p, levels, lambda, gamma, beta, u, hist ? ref : nullptr,
                                  hist ? p.hist + 3 * k : nullptr, st));
     }
@@ -760,7 +780,7 @@ static pp_status batch_horner(Batch& b, const double* c, int d, const float2* v,
 }
 
 static pp_status batch_iterations(Batch& b, float lambda, int iters, const double* c, int d,
-                                  bool hist, const float2* ref, cudaStream_t st) {
+                                  bool hist, const float2* ref, bool momentum, cudaStream_t st) {
     for (int k = 0; k < iters; ++k) {
         PP_TRY(launch_batch_normal(b.dev, b.z, b.g, 1.f, b.ahb, -1.f, st));
         const float2* u = b.g;
@@ -771,7 +791,7 @@ static pp_status batch_iterations(Batch& b, float lambda, int iters, const doubl
         } else if (c) {
             gamma = (float)c[0];
         }
-        const float beta = (float)((double)k / (k + 3.0));
+        const float beta = momentum ? (float)((double)k / (k + 3.0)) : 0.f;
         PP_TRY(launch_batch_prox_fista(b.dev, lambda, gamma, beta, b.z, u, b.y, hist ? ref : nullptr,
                                        hist ? b.hist + 3 * k : nullptr, st));
     }
@@ -967,6 +987,39 @@ pp_status pp_poly_coeffs_l2(int d, double* c) {
     return PP_OK;
 }
 
+pp_status pp_poly_coeffs_cheb(int d, double mu, double* c) {
+    if (!c || d < 0 || d > 8 || !(mu > 0.0 && mu < 1.0)) {
+        set_error("pp_poly_coeffs_cheb: need 0 <= d <= 8, 0 < mu < 1, c != NULL");
+        return PP_ERR_INVALID_ARG;
+    }
+    // T_k(a + b z) as monomial coefficients in z by T_{k+1} = 2 (a + b z) T_k - T_{k-1}
+    const double a = (1.0 + mu) / (1.0 - mu), bz = -2.0 / (1.0 - mu);
+    const int m = d + 1;
+    double Tm1[10] = {0}, T0[10] = {0}, T1[10] = {0};
+    T0[0] = 1.0;                         // T_0
+    T1[0] = a; T1[1] = bz;               // T_1
+    if (m == 1) {
+        for (int i = 0; i < 10; ++i) Tm1[i] = T1[i];
+    } else {
+        double prev[10], cur[10];
+        for (int i = 0; i < 10; ++i) { prev[i] = T0[i]; cur[i] = T1[i]; }
+        for (int k = 1; k < m; ++k) {
+            double next[10] = {0};
+            for (int i = 0; i <= k; ++i) {
+                next[i] += 2.0 * a * cur[i];
+                next[i + 1] += 2.0 * bz * cur[i];
+            }
+            for (int i = 0; i < 10; ++i) next[i] -= prev[i];
+            for (int i = 0; i < 10; ++i) { prev[i] = cur[i]; cur[i] = next[i]; }
+        }
+        for (int i = 0; i < 10; ++i) Tm1[i] = cur[i];
+    }
+    // r = T_m(a + b z) / T_m(a); T_m(a) is the constant term
+    const double t0 = Tm1[0];
+    for (int i = 0; i <= d; ++i) c[i] = -Tm1[i + 1] / t0;
+    return PP_OK;
+}
+
 pp_status pp_plan_create(pp_plan** out, pp_dims dims, int coils, const pp_c64* sens,
                          const pp_sampling* s, uint64_t seed, int power_iters, pp_stream stream) {
     if (!out) {
@@ -1092,6 +1145,39 @@ pp_status pp_plan_set_scale(pp_plan* plan, double L) {
     return PP_OK;
 }
 
+pp_status pp_plan_tuning(const pp_plan* plan, int* row_ifft_variant, int* stencil_coils) {
+    if (!plan) {
+        set_error("pp_plan_tuning: NULL plan");
+        return PP_ERR_INVALID_ARG;
+    }
+    if (row_ifft_variant) *row_ifft_variant = plan->impl.tune_rows_adj_cl ? plan->impl.tune_rows_adj_cl : 1;
+    if (stencil_coils) {
+        const int cpc = plan->impl.tune_stencil_cpc ? plan->impl.tune_stencil_cpc : 8;
+        *stencil_coils = plan->impl.tune_stencil_two ? -cpc : cpc;
+    }
+    return PP_OK;
+}
+
+pp_status pp_plan_set_tuning(pp_plan* plan, int row_ifft_variant, int stencil_coils) {
+    if (!plan || !(row_ifft_variant == 1 || row_ifft_variant == 2 || row_ifft_variant == 4 ||
+                   row_ifft_variant == -1) ||
+        stencil_coils == 0 || stencil_coils > 64 || stencil_coils < -64) {
+        set_error("pp_plan_set_tuning: row variant must be 1, 2, 4 or -1; stencil coils +-1..64");
+        return PP_ERR_INVALID_ARG;
+    }
+    Plan& p = plan->impl;
+    if (row_ifft_variant == -1 && (p.kind != PP_NONCARTESIAN || !fft4_n2(p.G_x))) {
+        set_error("pp_plan_set_tuning: the split row IFFT needs a non-Cartesian plan with a "
+                  "register-FFT grid length");
+        return PP_ERR_UNSUPPORTED;
+    }
+    p.tune_rows_adj_cl = row_ifft_variant;
+    p.tune_stencil_cpc = stencil_coils > 0 ? stencil_coils : -stencil_coils;
+    p.tune_stencil_two = stencil_coils < 0;
+    p.gkey.clear();
+    return PP_OK;
+}
+
 pp_status pp_plan_sizes(const pp_plan* plan, int64_t* image_elems, int64_t* kspace_elems) {
     if (!plan) {
         set_error("pp_plan_sizes: NULL plan");
@@ -1177,6 +1263,7 @@ pp_status pp_fista_solve(pp_plan* plan, const pp_c64* b, float lambda, int iters
         return PP_ERR_UNSUPPORTED;
     }
     const bool hist = info && info->history;
+    const bool momentum = !(info && info->no_momentum);
     const float2* ref = info ? reinterpret_cast<const float2*>(info->ref) : nullptr;
     const int64_t n = p.nimg;
     const int64_t launches0 = g_launches;
@@ -1203,7 +1290,8 @@ pp_status pp_fista_solve(pp_plan* plan, const pp_c64* b, float lambda, int iters
     if (iters > 0) {
         std::vector<double> key = {(double)iters, (double)d, (double)lambda, (double)levels,
                                    hist ? 1.0 : 0.0, c ? 1.0 : 0.0, p.L,
-                                   (double)(uintptr_t)p.hist, (double)(uintptr_t)ref};
+                                   (double)(uintptr_t)p.hist, (double)(uintptr_t)ref,
+                                   momentum ? 1.0 : 0.0};
         if (c)
             for (int i = 0; i <= d; ++i) key.push_back(c[i]);
         if (!p.gexec || key != p.gkey) {
@@ -1215,7 +1303,8 @@ pp_status pp_fista_solve(pp_plan* plan, const pp_c64* b, float lambda, int iters
             cudaGraph_t graph = nullptr;
             PP_TRY_CUDA(cudaStreamBeginCapture(p.cap_stream, cudaStreamCaptureModeThreadLocal));
             const int64_t before = g_launches;
-            pp_status rc = fista_iterations(p, lambda, iters, c, d, levels, hist, ref, p.cap_stream);
+            pp_status rc = fista_iterations(p, lambda, iters, c, d, levels, hist, ref, momentum,
+                                            p.cap_stream);
             cudaError_t e = cudaStreamEndCapture(p.cap_stream, &graph);
             p.graph_kernels = g_launches - before;
             g_launches = before;
@@ -1564,6 +1653,7 @@ pp_status pp_batch_fista_solve(pp_batch* batch, const pp_c64* bk, float lambda, 
     Batch& b = batch->impl;
     cudaStream_t st = (cudaStream_t)stream;
     const bool hist = info && info->history;
+    const bool momentum = !(info && info->no_momentum);
     const float2* ref = info ? reinterpret_cast<const float2*>(info->ref) : nullptr;
     const int64_t launches0 = g_launches;
     const float2* bd = reinterpret_cast<const float2*>(bk);
@@ -1590,7 +1680,7 @@ pp_status pp_batch_fista_solve(pp_batch* batch, const pp_c64* bk, float lambda, 
     if (iters > 0) {
         std::vector<double> key = {(double)iters, (double)d, (double)lambda, hist ? 1.0 : 0.0,
                                    c ? 1.0 : 0.0, (double)(uintptr_t)b.hist, (double)(uintptr_t)ref,
-                                   (double)b.dev.lgt};
+                                   (double)b.dev.lgt, (double)b.dev.fast4, momentum ? 1.0 : 0.0};
         if (c)
             for (int i = 0; i <= d; ++i) key.push_back(c[i]);
         if (!b.gexec || key != b.gkey) {
@@ -1602,7 +1692,7 @@ pp_status pp_batch_fista_solve(pp_batch* batch, const pp_c64* bk, float lambda, 
             cudaGraph_t graph = nullptr;
             PP_TRY_CUDA(cudaStreamBeginCapture(b.cap_stream, cudaStreamCaptureModeThreadLocal));
             const int64_t before = g_launches;
-            pp_status rc = batch_iterations(b, lambda, iters, c, d, hist, ref, b.cap_stream);
+            pp_status rc = batch_iterations(b, lambda, iters, c, d, hist, ref, momentum, b.cap_stream);
             cudaError_t e = cudaStreamEndCapture(b.cap_stream, &graph);
             b.graph_kernels = g_launches - before;
             g_launches = before;

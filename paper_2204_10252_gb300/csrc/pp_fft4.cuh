@@ -16,6 +16,20 @@
 
 namespace pp {
 
+// W_N^m = exp(-2 pi i m / N) for the register DFT lengths (mathematical
+// constants, rounded to float); indexed with compile-time m after unrolling,
+// so they become constant-bank operands.
+static __constant__ float2 c_w12[12] = {{1.000000000e+00f, -0.000000000e+00f}, {8.660254038e-01f, -5.000000000e-01f}, {5.000000000e-01f, -8.660254038e-01f}, {6.123233996e-17f, -1.000000000e+00f}, {-5.000000000e-01f, -8.660254038e-01f}, {-8.660254038e-01f, -5.000000000e-01f}, {-1.000000000e+00f, -1.224646799e-16f}, {-8.660254038e-01f, 5.000000000e-01f}, {-5.000000000e-01f, 8.660254038e-01f}, {-1.836970199e-16f, 1.000000000e+00f}, {5.000000000e-01f, 8.660254038e-01f}, {8.660254038e-01f, 5.000000000e-01f}};
+static __constant__ float2 c_w16[16] = {{1.000000000e+00f, -0.000000000e+00f}, {9.238795325e-01f, -3.826834324e-01f}, {7.071067812e-01f, -7.071067812e-01f}, {3.826834324e-01f, -9.238795325e-01f}, {6.123233996e-17f, -1.000000000e+00f}, {-3.826834324e-01f, -9.238795325e-01f}, {-7.071067812e-01f, -7.071067812e-01f}, {-9.238795325e-01f, -3.826834324e-01f}, {-1.000000000e+00f, -1.224646799e-16f}, {-9.238795325e-01f, 3.826834324e-01f}, {-7.071067812e-01f, 7.071067812e-01f}, {-3.826834324e-01f, 9.238795325e-01f}, {-1.836970199e-16f, 1.000000000e+00f}, {3.826834324e-01f, 9.238795325e-01f}, {7.071067812e-01f, 7.071067812e-01f}, {9.238795325e-01f, 3.826834324e-01f}};
+static __constant__ float2 c_w20[20] = {{1.000000000e+00f, -0.000000000e+00f}, {9.510565163e-01f, -3.090169944e-01f}, {8.090169944e-01f, -5.877852523e-01f}, {5.877852523e-01f, -8.090169944e-01f}, {3.090169944e-01f, -9.510565163e-01f}, {6.123233996e-17f, -1.000000000e+00f}, {-3.090169944e-01f, -9.510565163e-01f}, {-5.877852523e-01f, -8.090169944e-01f}, {-8.090169944e-01f, -5.877852523e-01f}, {-9.510565163e-01f, -3.090169944e-01f}, {-1.000000000e+00f, -1.224646799e-16f}, {-9.510565163e-01f, 3.090169944e-01f}, {-8.090169944e-01f, 5.877852523e-01f}, {-5.877852523e-01f, 8.090169944e-01f}, {-3.090169944e-01f, 9.510565163e-01f}, {-1.836970199e-16f, 1.000000000e+00f}, {3.090169944e-01f, 9.510565163e-01f}, {5.877852523e-01f, 8.090169944e-01f}, {8.090169944e-01f, 5.877852523e-01f}, {9.510565163e-01f, 3.090169944e-01f}};
+static __constant__ float2 c_w24[24] = {{1.000000000e+00f, -0.000000000e+00f}, {9.659258263e-01f, -2.588190451e-01f}, {8.660254038e-01f, -5.000000000e-01f}, {7.071067812e-01f, -7.071067812e-01f}, {5.000000000e-01f, -8.660254038e-01f}, {2.588190451e-01f, -9.659258263e-01f}, {6.123233996e-17f, -1.000000000e+00f}, {-2.588190451e-01f, -9.659258263e-01f}, {-5.000000000e-01f, -8.660254038e-01f}, {-7.071067812e-01f, -7.071067812e-01f}, {-8.660254038e-01f, -5.000000000e-01f}, {-9.659258263e-01f, -2.588190451e-01f}, {-1.000000000e+00f, -1.224646799e-16f}, {-9.659258263e-01f, 2.588190451e-01f}, {-8.660254038e-01f, 5.000000000e-01f}, {-7.071067812e-01f, 7.071067812e-01f}, {-5.000000000e-01f, 8.660254038e-01f}, {-2.588190451e-01f, 9.659258263e-01f}, {-1.836970199e-16f, 1.000000000e+00f}, {2.588190451e-01f, 9.659258263e-01f}, {5.000000000e-01f, 8.660254038e-01f}, {7.071067812e-01f, 7.071067812e-01f}, {8.660254038e-01f, 5.000000000e-01f}, {9.659258263e-01f, 2.588190451e-01f}};
+
+template <int L> __device__ __forceinline__ float2 cw(int m);
+template <> __device__ __forceinline__ float2 cw<12>(int m) { return c_w12[m]; }
+template <> __device__ __forceinline__ float2 cw<16>(int m) { return c_w16[m]; }
+template <> __device__ __forceinline__ float2 cw<20>(int m) { return c_w20[m]; }
+template <> __device__ __forceinline__ float2 cw<24>(int m) { return c_w24[m]; }
+
 template <int N, bool INV> struct RegFft;
 
 template <bool INV> struct RegFft<2, INV> {
@@ -51,7 +65,7 @@ __device__ __forceinline__ void reg_fft_ab(float2* v, const float2* __restrict__
     for (int b = 1; b < B; ++b)
 #pragma unroll
         for (int k1 = 1; k1 < A; ++k1) {
-            float2 w = tw[b * k1 * step];
+            float2 w = cw<A * B>(b * k1);
             if (INV) w.y = -w.y;
             t[b * A + k1] = cmul(t[b * A + k1], w);
         }
@@ -91,11 +105,18 @@ __host__ __device__ __forceinline__ int fft4_n2(int n) {
 template <int N1, int N2, bool INV>
 __device__ __forceinline__ void fft4_phase1(float2* v, int m2, const float2* __restrict__ tw) {
     RegFft<N1, INV>::run(v, tw, N2);
+    // W_n^(m2 k1): four table loads (k1 = 1..4), the rest by w_k = w_(k-4) w_4
+    float2 w[N1];
+    w[0] = make_float2(1.f, 0.f);
+#pragma unroll
+    for (int k1 = 1; k1 <= 4 && k1 < N1; ++k1) w[k1] = tw[m2 * k1];
+#pragma unroll
+    for (int k1 = 5; k1 < N1; ++k1) w[k1] = cmul(w[k1 - 4], w[4]);
 #pragma unroll
     for (int k1 = 1; k1 < N1; ++k1) {
-        float2 w = tw[m2 * k1];
-        if (INV) w.y = -w.y;
-        v[k1] = cmul(v[k1], w);
+        float2 ww = w[k1];
+        if (INV) ww.y = -ww.y;
+        v[k1] = cmul(v[k1], ww);
     }
 }
 

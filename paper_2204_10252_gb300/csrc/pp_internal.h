@@ -123,8 +123,10 @@ struct Plan {
 
     bool external_wk = false;   // workspace supplied by an owner (batched plans)
     // plan-time autotuned launch shapes (0 = default)
-    int tune_rows_adj_cl = 0;   // row-IFFT cluster size (1, 2 or 4)
+    int tune_rows_adj_cl = 0;   // row-IFFT variant: cluster size 1, 2 or 4, or -1 = split
+                                // into per-coil IFFTs plus a coil sum (normal operator only)
     int tune_stencil_cpc = 0;   // coils per CTA of the G^T G stencil
+    int tune_stencil_two = 0;   // 1: two outputs per thread (gtg_stencil2_kernel)
     std::vector<void*> allocs;
 };
 
@@ -154,6 +156,10 @@ pp_status launch_cols4(const DevFft& f, const ColArgs& a, const float2* src, flo
 pp_status launch_rows4_fwd(const DevFft& f, const RowArgs& a, const float2* x, const float2* sens,
                            const float* wrow, const float* wcol, float2* out, int ncoils,
                            int64_t img_batch_stride, cudaStream_t st, bool* done);
+pp_status launch_rows4_adj_split(const DevFft& f, const RowArgs& a, const float2* src,
+                                 const float2* sens, const float* wrow, const float* wcol,
+                                 float2* contrib, float2* out, const float2* operand, float alpha,
+                                 int ncoils, cudaStream_t st, bool* done);
 pp_status cart3d4_normal(const Plan& p, const float2* x, float2* out, float scale,
                          const float2* operand, float alpha, float2* W, cudaStream_t st, bool* done);
 pp_status launch_cart2d4_normal(const Plan& p, const float2* x, float2* out, float scale,

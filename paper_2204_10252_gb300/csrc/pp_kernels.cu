@@ -333,24 +333,21 @@ __global__ void conj_accum_kernel(const float2* __restrict__ s, const float2* __
 }
 
 // ---------------------------------------------------------------------------
-// Kaiser-Bessel gridding on tiles of the oversampled grid (FFT order).
-// A CTA owns one T x T output tile and a chunk of coils.  For each coil it
-// stages the (T+2H) x (T+2H) halo of the input grid (H = W-1) in shared
-// memory, interpolates every sample whose W x W footprint meets the tile
-// (degridding, G^T), and spreads the value back onto the taps that fall in
-// the tile (gridding, G) with shared-memory atomics.  No global atomics.
+// Kaiser-Bessel spreading (the adjoint's gridding, G^T) on tiles of the
+// oversampled grid (FFT order).  A CTA owns one T x T output tile and a chunk
+// of coils; every sample whose W x W footprint meets the tile is listed for
+// it (plan time), and the CTA adds the sample's value times the tap weights
+// that fall inside the tile into a shared-memory accumulator (shared-memory
+// atomics), then writes the tile once.  No global atomics.
 // ---------------------------------------------------------------------------
-template <int W, bool DEGRID>
+template <int W>
 __global__ void __launch_bounds__(kThreads)
-nufft_tile_kernel(const TileEntry* __restrict__ entries, const int* __restrict__ tile_start,
-                  int T, int ntx, int Gx, int Gy, int C, int coils_per_cta,
-                  const float2* __restrict__ grid_in, const float2* __restrict__ ksp, int K,
-                  float2* __restrict__ grid_out) {
+nufft_spread_tile_kernel(const TileEntry* __restrict__ entries, const int* __restrict__ tile_start,
+                         int T, int ntx, int Gx, int Gy, int C, int coils_per_cta,
+                         const float2* __restrict__ ksp, int K, float2* __restrict__ grid_out) {
     extern __shared__ float2 sm[];
     constexpr int H = W - 1;
-    const int HW = T + 2 * H;
-    float2* halo = sm;
-    float* acc = reinterpret_cast<float*>(DEGRID ? sm + HW * HW : sm);
+    float* acc = reinterpret_cast<float*>(sm);
     const int tile = blockIdx.x;
     const int tyi = tile / ntx, txi = tile - tyi * ntx;
     const int ty0 = tyi * T, tx0 = txi * T;
@@ -360,14 +357,6 @@ nufft_tile_kernel(const TileEntry* __restrict__ entries, const int* __restrict__
     const int c0 = blockIdx.y * coils_per_cta;
     const int c1 = min(C, c0 + coils_per_cta);
     for (int c = c0; c < c1; ++c) {
-        if (DEGRID) {
-            const float2* gin = grid_in + c * gsz;
-            for (int idx = threadIdx.x; idx < HW * HW; idx += blockDim.x) {
-                const int hy = idx / HW, hx = idx - hy * HW;
-                const int gy = wrapG(ty0 - H + hy, Gy), gx = wrapG(tx0 - H + hx, Gx);
-                halo[idx] = gin[(int64_t)gy * Gx + gx];
-            }
-        }
         for (int idx = threadIdx.x; idx < 2 * T * T; idx += blockDim.x) acc[idx] = 0.f;
         __syncthreads();
         for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
@@ -375,25 +364,7 @@ nufft_tile_kernel(const TileEntry* __restrict__ entries, const int* __restrict__
             const float wx[4] = {te.wx.x, te.wx.y, te.wx.z, te.wx.w};
             const float wy[4] = {te.wy.x, te.wy.y, te.wy.z, te.wy.w};
             const int ly0 = te.lyx & 0xffff, lx0 = te.lyx >> 16;
-            float2 v;
-            if (DEGRID) {
-                v = make_float2(0.f, 0.f);
-#pragma unroll
-                for (int b = 0; b < W; ++b) {
-                    float2 rs = make_float2(0.f, 0.f);
-                    const float2* hrow = halo + (ly0 + b) * HW + lx0;
-#pragma unroll
-                    for (int a = 0; a < W; ++a) {
-                        const float2 hv = hrow[a];
-                        rs.x += wx[a] * hv.x;
-                        rs.y += wx[a] * hv.y;
-                    }
-                    v.x += wy[b] * rs.x;
-                    v.y += wy[b] * rs.y;
-                }
-            } else {
-                v = ksp[(int64_t)c * K + te.k];
-            }
+            const float2 v = ksp[(int64_t)c * K + te.k];
 #pragma unroll
             for (int b = 0; b < W; ++b) {
                 const int yy = ly0 + b - H;
@@ -413,8 +384,7 @@ nufft_tile_kernel(const TileEntry* __restrict__ entries, const int* __restrict__
         for (int idx = threadIdx.x; idx < th * T; idx += blockDim.x) {
             const int yy = idx / T, xx = idx - yy * T;
             if (xx < tw_)
-                gout[(int64_t)(ty0 + yy) * Gx + tx0 + xx] =
-                    make_float2(acc[2 * idx], acc[2 * idx + 1]);
+                gout[(int64_t)(ty0 + yy) * Gx + tx0 + xx] = make_float2(acc[2 * idx], acc[2 * idx + 1]);
         }
         __syncthreads();
     }
@@ -518,6 +488,75 @@ gtg_stencil_kernel(const float* __restrict__ T, int Gx, int Gy, int C, int coils
         if (live) grid_out[c * plane + (int64_t)gy * Gx + gx] = make_float2(ax, ay);
         // the next iteration writes the other buffer; the one after that
         // rewrites this one only after the next __syncthreads
+    }
+}
+
+// Variant of gtg_stencil_kernel with two vertically adjacent outputs per
+// thread (16 x 16 tile, 128 threads): their 7 x 7 windows share 6 rows, so a
+// thread reads 8 x 7 halo values for 2 outputs instead of 2 x 49.
+template <int W>
+__global__ void __launch_bounds__(128)
+gtg_stencil2_kernel(const float* __restrict__ T, int Gx, int Gy, int C, int coils_per_cta,
+                    const float2* __restrict__ grid_in, float2* __restrict__ grid_out) {
+    constexpr int H = W - 1, D = 2 * W - 1, TS = 16, HW = TS + 2 * H;
+    constexpr int HE = (HW * HW + 127) / 128;
+    __shared__ float2 halo[2][HW * HW];
+    const int tx0 = blockIdx.x * TS, ty0 = blockIdx.y * TS;
+    const int lx = threadIdx.x & (TS - 1), ly = (threadIdx.x >> 4) * 2;   // rows ly, ly + 1
+    const int gx = tx0 + lx, gy = ty0 + ly;
+    const bool live0 = gx < Gx && gy < Gy, live1 = gx < Gx && gy + 1 < Gy;
+    const int64_t plane = (int64_t)Gx * Gy;
+    int64_t hsrc[HE];
+#pragma unroll
+    for (int e = 0; e < HE; ++e) {
+        const int idx = threadIdx.x + e * 128;
+        const int hy = idx / HW, hx = idx - hy * HW;
+        hsrc[e] = (idx < HW * HW)
+                      ? (int64_t)wrapG(ty0 - H + hy, Gy) * Gx + wrapG(tx0 - H + hx, Gx)
+                      : -1;
+    }
+    float w0[D * D], w1[D * D];
+#pragma unroll
+    for (int d = 0; d < D * D; ++d) {
+        w0[d] = live0 ? T[d * plane + (int64_t)gy * Gx + gx] : 0.f;
+        w1[d] = live1 ? T[d * plane + (int64_t)(gy + 1) * Gx + gx] : 0.f;
+    }
+    const int c0 = blockIdx.z * coils_per_cta, c1 = min(C, c0 + coils_per_cta);
+    if (c0 >= c1) return;
+    float2 pre[HE];
+#pragma unroll
+    for (int e = 0; e < HE; ++e)
+        pre[e] = hsrc[e] >= 0 ? grid_in[c0 * plane + hsrc[e]] : make_float2(0.f, 0.f);
+    for (int c = c0; c < c1; ++c) {
+        float2* hb = halo[(c - c0) & 1];
+#pragma unroll
+        for (int e = 0; e < HE; ++e) {
+            const int idx = threadIdx.x + e * 128;
+            if (idx < HW * HW) hb[idx] = pre[e];
+        }
+        __syncthreads();
+        if (c + 1 < c1) {
+#pragma unroll
+            for (int e = 0; e < HE; ++e)
+                pre[e] = hsrc[e] >= 0 ? grid_in[(c + 1) * plane + hsrc[e]] : make_float2(0.f, 0.f);
+        }
+        float a0x = 0.f, a0y = 0.f, a1x = 0.f, a1y = 0.f;
+#pragma unroll
+        for (int hy = 0; hy < D + 1; ++hy)
+#pragma unroll
+            for (int dx = 0; dx < D; ++dx) {
+                const float2 v = hb[(ly + hy) * HW + lx + dx];
+                if (hy < D) {
+                    a0x += w0[hy * D + dx] * v.x;
+                    a0y += w0[hy * D + dx] * v.y;
+                }
+                if (hy > 0) {
+                    a1x += w1[(hy - 1) * D + dx] * v.x;
+                    a1y += w1[(hy - 1) * D + dx] * v.y;
+                }
+            }
+        if (live0) grid_out[c * plane + (int64_t)gy * Gx + gx] = make_float2(a0x, a0y);
+        if (live1) grid_out[c * plane + (int64_t)(gy + 1) * Gx + gx] = make_float2(a1x, a1y);
     }
 }
 
@@ -928,7 +967,7 @@ pp_status configure_kernels() {
     PP_TRY_CUDA(cudaFuncSetAttribute(cart2d_normal_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
     PP_TRY_CUDA(cudaFuncSetAttribute(rows_adj_cb_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
     PP_TRY_CUDA(cudaFuncSetAttribute(rows_adj_cb_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-    PP_TRY_CUDA(cudaFuncSetAttribute(nufft_tile_kernel<4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    PP_TRY_CUDA(cudaFuncSetAttribute(nufft_spread_tile_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
     return PP_OK;
 }
 
@@ -1033,13 +1072,15 @@ pp_status launch_conj_accum(const float2* s, const float2* wv, float2* out, int6
     return check_launch("conj_accum_kernel");
 }
 
-static size_t tile_smem(const Plan& p, bool degrid) {
-    const int HW = p.T + 2 * (p.W - 1);
-    return sizeof(float2) * (size_t)((degrid ? HW * HW : 0) + p.T * p.T);
-}
+static size_t tile_smem(const Plan& p) { return sizeof(float2) * (size_t)p.T * p.T; }
 
 pp_status launch_gtg_stencil(const Plan& p, const float2* grid_in, float2* grid_out, cudaStream_t st) {
     const int cpc = p.tune_stencil_cpc > 0 ? p.tune_stencil_cpc : 8;
+    if (p.tune_stencil_two) {
+        dim3 grid((p.G_x + 15) / 16, (p.G_y + 15) / 16, (p.C + cpc - 1) / cpc);
+        gtg_stencil2_kernel<4><<<grid, 128, 0, st>>>(p.gtg, p.G_x, p.G_y, p.C, cpc, grid_in, grid_out);
+        return check_launch("gtg_stencil2_kernel");
+    }
     dim3 grid((p.G_x + 15) / 16, (p.G_y + 15) / 16, (p.C + cpc - 1) / cpc);
     gtg_stencil_kernel<4><<<grid, kThreads, 0, st>>>(p.gtg, p.G_x, p.G_y, p.C, cpc, grid_in, grid_out);
     return check_launch("gtg_stencil_kernel");
@@ -1048,9 +1089,9 @@ pp_status launch_gtg_stencil(const Plan& p, const float2* grid_in, float2* grid_
 pp_status launch_nufft_spread(const Plan& p, const float2* ksp, float2* grid_out, cudaStream_t st) {
     const int cpc = 4;
     dim3 grid(p.ntx * p.nty, (p.C + cpc - 1) / cpc);
-    nufft_tile_kernel<4, false><<<grid, kThreads, tile_smem(p, false), st>>>(
-        p.tiles, p.tile_start, p.T, p.ntx, p.G_x, p.G_y, p.C, cpc, nullptr, ksp, p.K, grid_out);
-    return check_launch("nufft_tile_kernel<spread>");
+    nufft_spread_tile_kernel<4><<<grid, kThreads, tile_smem(p), st>>>(
+        p.tiles, p.tile_start, p.T, p.ntx, p.G_x, p.G_y, p.C, cpc, ksp, p.K, grid_out);
+    return check_launch("nufft_spread_tile_kernel");
 }
 
 pp_status launch_nufft_degrid(const Plan& p, const float2* grid_in, float2* ksp, cudaStream_t st) {

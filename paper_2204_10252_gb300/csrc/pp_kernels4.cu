@@ -316,6 +316,69 @@ rows4_adj_cl_kernel(const float2* __restrict__ tw, RowArgs a, const float2* __re
     cluster.sync();   // keep every CTA's partial sums alive until rank 0 has read them
 }
 
+// Row IFFT per (coil, row) with the crop, deapodisation and conj(S_c)
+// product fused into the store: contrib[c][row][i] = w conj(S_c) IFFT(src_c[row])
+// at image index i.  The coil sum follows in coil_sum_kernel.
+template <int N2>
+__global__ void __launch_bounds__(RBF * tpr<N2>())
+rows4_inv_kernel(const float2* __restrict__ tw, RowArgs a, const float2* __restrict__ src,
+                 const float2* __restrict__ sens, const float* __restrict__ wrow,
+                 const float* __restrict__ wcol, float2* __restrict__ contrib) {
+    constexpr int n = N1 * N2, T = tpr<N2>(), YS = N2 + 1;
+    __shared__ float2 tws[n];
+    __shared__ float2 Y[RBF * N1 * YS];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) tws[i] = tw[i];
+    __syncthreads();
+    const int b = threadIdx.x / T, r = threadIdx.x - (threadIdx.x / T) * T;
+    const int c = blockIdx.y;
+    const int row = blockIdx.x * RBF + b;
+    const bool live = row < a.nrows;
+    if (r < N2) {
+        float2 v[N1];
+#pragma unroll
+        for (int m1 = 0; m1 < N1; ++m1) {
+            int sidx = N2 * m1 + r + a.off_in;
+            if (sidx >= n) sidx -= n;
+            v[m1] = live ? src[((int64_t)c * a.nrows + row) * n + sidx] : make_float2(0.f, 0.f);
+        }
+        fft4_phase1<N1, N2, true>(v, r, tws);
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) Y[(b * N1 + k1) * YS + r] = v[k1];
+    }
+    __syncthreads();
+    if (r < N1 && live) {
+        float2 u[N2];
+#pragma unroll
+        for (int m2 = 0; m2 < N2; ++m2) u[m2] = Y[(b * N1 + r) * YS + m2];
+        fft4_phase2<N1, N2, true>(u, tws);
+        const float wr = wrow ? wrow[row] : 1.f;
+        const float2* sc = sens + (int64_t)c * a.coil_img_stride + (int64_t)row * a.n;
+        float2* oc = contrib + ((int64_t)c * a.nrows + row) * a.n;
+#pragma unroll
+        for (int k2 = 0; k2 < N2; ++k2) {
+            int i = r + N1 * k2 + a.off_out;
+            if (i >= n) i -= n;
+            if (i < a.n) {
+                const float w = wcol ? wr * wcol[i] : wr;
+                oc[i] = cmulc(sc[i], cscale(u[k2], w));
+            }
+        }
+    }
+}
+
+// out[o] = scale * sum_c contrib[c][o] + alpha * operand[o]
+__global__ void coil_sum_kernel(const float2* __restrict__ contrib, int C, int64_t n, float scale,
+                                const float2* operand, float alpha, float2* out) {
+    for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < n;
+         o += (int64_t)gridDim.x * blockDim.x) {
+        float2 acc = make_float2(0.f, 0.f);
+        for (int c = 0; c < C; ++c) acc = cadd(acc, contrib[(int64_t)c * n + o]);
+        acc = cscale(acc, scale);
+        if (operand) acc = cadd(acc, cscale(operand[o], alpha));
+        out[o] = acc;
+    }
+}
+
 // Fused 2-D Cartesian normal operator (one CTA per 8 columns, all coils).
 template <int N2>
 __global__ void __launch_bounds__(8 * tpr<N2>(), 2)
@@ -344,17 +407,17 @@ cart2d4_normal_kernel(const float2* __restrict__ tw, const float2* __restrict__ 
 //   ypass_inv:  out[z][:, x] (+)= conj(S_c) F_y^H W[z][:, x]; on the last
 //               coil out = scale * out + alpha * operand
 // ---------------------------------------------------------------------------
-template <int N2>
-__global__ void __launch_bounds__(8 * tpr<N2>())
+template <int N2, int TX>
+__global__ void __launch_bounds__(TX * tpr<N2>())
 c3_ypass_fwd_kernel(const float2* __restrict__ tw, const float2* __restrict__ x,
                     const float2* __restrict__ S, float2* __restrict__ W, int nx, int x0) {
     constexpr int n = N1 * N2;
     __shared__ float2 tws[n];
-    __shared__ float2 Y[N1 * N2 * 8];
+    __shared__ float2 Y[N1 * N2 * TX];
     for (int i = threadIdx.x; i < n; i += blockDim.x) tws[i] = tw[i];
     __syncthreads();
-    const int lane = threadIdx.x & 7, r = threadIdx.x >> 3;
-    const int col = x0 + blockIdx.x * 8 + lane;
+    const int lane = threadIdx.x % TX, r = threadIdx.x / TX;
+    const int col = x0 + blockIdx.x * TX + lane;
     const bool ok = col < nx;
     const int64_t plane = (int64_t)blockIdx.y * n * nx;
     if (r < N2) {
@@ -366,30 +429,30 @@ c3_ypass_fwd_kernel(const float2* __restrict__ tw, const float2* __restrict__ x,
         }
         fft4_phase1<N1, N2, false>(v, r, tws);
 #pragma unroll
-        for (int k1 = 0; k1 < N1; ++k1) Y[(k1 * N2 + r) * 8 + lane] = v[k1];
+        for (int k1 = 0; k1 < N1; ++k1) Y[(k1 * N2 + r) * TX + lane] = v[k1];
     }
     __syncthreads();
     if (r < N1 && ok) {
         float2 u[N2];
 #pragma unroll
-        for (int m2 = 0; m2 < N2; ++m2) u[m2] = Y[(r * N2 + m2) * 8 + lane];
+        for (int m2 = 0; m2 < N2; ++m2) u[m2] = Y[(r * N2 + m2) * TX + lane];
         fft4_phase2<N1, N2, false>(u, tws);
 #pragma unroll
         for (int k2 = 0; k2 < N2; ++k2) W[plane + (int64_t)(r + N1 * k2) * nx + col] = u[k2];
     }
 }
 
-template <int N2>
-__global__ void __launch_bounds__(8 * tpr<N2>())
+template <int N2, int TX>
+__global__ void __launch_bounds__(TX * tpr<N2>())
 c3_zpass_kernel(const float2* __restrict__ tw, float2* W, const float* __restrict__ mask_fo,
                 int ny, int nx, int x0) {
     constexpr int n = N1 * N2;   // nz
     __shared__ float2 tws[n];
-    __shared__ float2 Y[N1 * N2 * 8];
+    __shared__ float2 Y[N1 * N2 * TX];
     for (int i = threadIdx.x; i < n; i += blockDim.x) tws[i] = tw[i];
     __syncthreads();
-    const int lane = threadIdx.x & 7, r = threadIdx.x >> 3;
-    const int col = x0 + blockIdx.x * 8 + lane;
+    const int lane = threadIdx.x % TX, r = threadIdx.x / TX;
+    const int col = x0 + blockIdx.x * TX + lane;
     const int ky = blockIdx.y;
     const bool ok = col < nx;
     const int64_t zs = (int64_t)ny * nx, base = (int64_t)ky * nx + col;
@@ -399,13 +462,13 @@ c3_zpass_kernel(const float2* __restrict__ tw, float2* W, const float* __restric
         for (int m1 = 0; m1 < N1; ++m1) v[m1] = ok ? W[(N2 * m1 + r) * zs + base] : make_float2(0.f, 0.f);
         fft4_phase1<N1, N2, false>(v, r, tws);
 #pragma unroll
-        for (int k1 = 0; k1 < N1; ++k1) Y[(k1 * N2 + r) * 8 + lane] = v[k1];
+        for (int k1 = 0; k1 < N1; ++k1) Y[(k1 * N2 + r) * TX + lane] = v[k1];
     }
     __syncthreads();
     if (r < N1) {
         float2 u[N2];
 #pragma unroll
-        for (int m2 = 0; m2 < N2; ++m2) u[m2] = Y[(r * N2 + m2) * 8 + lane];
+        for (int m2 = 0; m2 < N2; ++m2) u[m2] = Y[(r * N2 + m2) * TX + lane];
         fft4_phase2<N1, N2, false>(u, tws);
 #pragma unroll
         for (int k2 = 0; k2 < N2; ++k2) u[k2] = cscale(u[k2], mask_fo[(r + N1 * k2) * ny + ky]);
@@ -417,31 +480,31 @@ c3_zpass_kernel(const float2* __restrict__ tw, float2* W, const float* __restric
             u[m2] = cmul(u[m2], w);
         }
 #pragma unroll
-        for (int m2 = 0; m2 < N2; ++m2) Y[(r * N2 + m2) * 8 + lane] = u[m2];
+        for (int m2 = 0; m2 < N2; ++m2) Y[(r * N2 + m2) * TX + lane] = u[m2];
     }
     __syncthreads();
     if (r < N2 && ok) {
         float2 v[N1];
 #pragma unroll
-        for (int k1 = 0; k1 < N1; ++k1) v[k1] = Y[(k1 * N2 + r) * 8 + lane];
+        for (int k1 = 0; k1 < N1; ++k1) v[k1] = Y[(k1 * N2 + r) * TX + lane];
         RegFft<N1, true>::run(v, tws, N2);
 #pragma unroll
         for (int m1 = 0; m1 < N1; ++m1) W[(N2 * m1 + r) * zs + base] = v[m1];
     }
 }
 
-template <int N2>
-__global__ void __launch_bounds__(8 * tpr<N2>())
+template <int N2, int TX>
+__global__ void __launch_bounds__(TX * tpr<N2>())
 c3_ypass_inv_kernel(const float2* __restrict__ tw, const float2* __restrict__ W,
                     const float2* __restrict__ S, float2* out, int nx, int x0, int first, int last,
                     float scale, const float2* operand, float alpha) {
     constexpr int n = N1 * N2;
     __shared__ float2 tws[n];
-    __shared__ float2 Y[N1 * N2 * 8];
+    __shared__ float2 Y[N1 * N2 * TX];
     for (int i = threadIdx.x; i < n; i += blockDim.x) tws[i] = tw[i];
     __syncthreads();
-    const int lane = threadIdx.x & 7, r = threadIdx.x >> 3;
-    const int col = x0 + blockIdx.x * 8 + lane;
+    const int lane = threadIdx.x % TX, r = threadIdx.x / TX;
+    const int col = x0 + blockIdx.x * TX + lane;
     const bool ok = col < nx;
     const int64_t plane = (int64_t)blockIdx.y * n * nx;
     if (r < N2) {
@@ -451,13 +514,13 @@ c3_ypass_inv_kernel(const float2* __restrict__ tw, const float2* __restrict__ W,
             v[m1] = ok ? W[plane + (int64_t)(N2 * m1 + r) * nx + col] : make_float2(0.f, 0.f);
         fft4_phase1<N1, N2, true>(v, r, tws);
 #pragma unroll
-        for (int k1 = 0; k1 < N1; ++k1) Y[(k1 * N2 + r) * 8 + lane] = v[k1];
+        for (int k1 = 0; k1 < N1; ++k1) Y[(k1 * N2 + r) * TX + lane] = v[k1];
     }
     __syncthreads();
     if (r < N1 && ok) {
         float2 u[N2];
 #pragma unroll
-        for (int m2 = 0; m2 < N2; ++m2) u[m2] = Y[(r * N2 + m2) * 8 + lane];
+        for (int m2 = 0; m2 < N2; ++m2) u[m2] = Y[(r * N2 + m2) * TX + lane];
         fft4_phase2<N1, N2, true>(u, tws);
 #pragma unroll
         for (int k2 = 0; k2 < N2; ++k2) {
@@ -583,6 +646,45 @@ pp_status launch_cart2d4_normal(const Plan& p, const float2* x, float2* out, flo
     return check4("cart2d4_normal_kernel");
 }
 
+// Launch helpers for the 3-D passes: 16 columns per CTA only where the
+// shared tile stays within the 48 KiB static limit (N2 <= 16).
+template <int N2>
+static void c3_yf(int tx, dim3 g, cudaStream_t st, const float2* tw, const float2* x, const float2* S,
+                  float2* W, int nx, int x0) {
+    if constexpr (N2 <= 16) {
+        if (tx == 16) {
+            c3_ypass_fwd_kernel<N2, 16><<<g, 16 * tpr<N2>(), 0, st>>>(tw, x, S, W, nx, x0);
+            return;
+        }
+    }
+    c3_ypass_fwd_kernel<N2, 8><<<g, 8 * tpr<N2>(), 0, st>>>(tw, x, S, W, nx, x0);
+}
+template <int N2>
+static void c3_z(int tx, dim3 g, cudaStream_t st, const float2* tw, float2* W, const float* m, int ny,
+                 int nx, int x0) {
+    if constexpr (N2 <= 16) {
+        if (tx == 16) {
+            c3_zpass_kernel<N2, 16><<<g, 16 * tpr<N2>(), 0, st>>>(tw, W, m, ny, nx, x0);
+            return;
+        }
+    }
+    c3_zpass_kernel<N2, 8><<<g, 8 * tpr<N2>(), 0, st>>>(tw, W, m, ny, nx, x0);
+}
+template <int N2>
+static void c3_yi(int tx, dim3 g, cudaStream_t st, const float2* tw, const float2* W, const float2* S,
+                  float2* out, int nx, int x0, int first, int last, float scale, const float2* op,
+                  float alpha) {
+    if constexpr (N2 <= 16) {
+        if (tx == 16) {
+            c3_ypass_inv_kernel<N2, 16><<<g, 16 * tpr<N2>(), 0, st>>>(tw, W, S, out, nx, x0, first, last,
+                                                                      scale, op, alpha);
+            return;
+        }
+    }
+    c3_ypass_inv_kernel<N2, 8><<<g, 8 * tpr<N2>(), 0, st>>>(tw, W, S, out, nx, x0, first, last, scale,
+                                                            op, alpha);
+}
+
 // 3-D normal operator on L2-sized x-blocks (see the kernels above); false
 // in *done when ny or nz has no register FFT.
 pp_status cart3d4_normal(const Plan& p, const float2* x, float2* out, float scale,
@@ -597,24 +699,51 @@ pp_status cart3d4_normal(const Plan& p, const float2* x, float2* out, float scal
     const int64_t n = p.nimg;
     for (int x0 = 0; x0 < nx; x0 += wb) {
         const int w = std::min(wb, nx - x0);
-        const dim3 gy((w + 7) / 8, nz), gz((w + 7) / 8, ny);
+        // 16 columns per CTA (whole 128-byte lines of the maps) when the
+        // shared tile fits the static limit, else 8
+        const int tyx = ny2 <= 16 ? 16 : 8, tzx = nz2 <= 16 ? 16 : 8;
+        const dim3 gy((w + tyx - 1) / tyx, nz), gz((w + tzx - 1) / tzx, ny);
         for (int c = 0; c < p.C; ++c) {
             const float2* S = p.sens + (int64_t)c * n;
-#define PP_Y(N2_) if (ny2 == N2_) c3_ypass_fwd_kernel<N2_><<<gy, 8 * tpr<N2_>(), 0, st>>>(p.fy.tw, x, S, W, nx, x0);
+#define PP_Y(N2_) if (ny2 == N2_) c3_yf<N2_>(tyx, gy, st, p.fy.tw, x, S, W, nx, x0);
             PP_Y(8) PP_Y(12) PP_Y(16) PP_Y(20) PP_Y(24)
 #undef PP_Y
             PP_TRY(check4("c3_ypass_fwd_kernel"));
-#define PP_Z(N2_) if (nz2 == N2_) c3_zpass_kernel<N2_><<<gz, 8 * tpr<N2_>(), 0, st>>>(p.fz.tw, W, p.mask_fo, ny, nx, x0);
+#define PP_Z(N2_) if (nz2 == N2_) c3_z<N2_>(tzx, gz, st, p.fz.tw, W, p.mask_fo, ny, nx, x0);
             PP_Z(8) PP_Z(12) PP_Z(16) PP_Z(20) PP_Z(24)
 #undef PP_Z
             PP_TRY(check4("c3_zpass_kernel"));
             const int first = c == 0, last = c == p.C - 1;
-#define PP_I(N2_) if (ny2 == N2_) c3_ypass_inv_kernel<N2_><<<gy, 8 * tpr<N2_>(), 0, st>>>(p.fy.tw, W, S, out, nx, x0, first, last, scale, operand, alpha);
+#define PP_I(N2_) if (ny2 == N2_) c3_yi<N2_>(tyx, gy, st, p.fy.tw, W, S, out, nx, x0, first, last, scale, operand, alpha);
             PP_I(8) PP_I(12) PP_I(16) PP_I(20) PP_I(24)
 #undef PP_I
             PP_TRY(check4("c3_ypass_inv_kernel"));
         }
     }
+    *done = true;
+    return PP_OK;
+}
+
+pp_status launch_rows4_adj_split(const DevFft& f, const RowArgs& a, const float2* src,
+                                 const float2* sens, const float* wrow, const float* wcol,
+                                 float2* contrib, float2* out, const float2* operand, float alpha,
+                                 int ncoils, cudaStream_t st, bool* done) {
+    *done = false;
+    const int n2 = fft4_n2(a.G);
+    if (!n2 || !sens || !contrib) return PP_OK;
+    dim3 grid((a.nrows + RBF - 1) / RBF, ncoils);
+#define PP_S4(N2_)                                                                              \
+    if (n2 == N2_)                                                                              \
+        rows4_inv_kernel<N2_><<<grid, RBF * tpr<N2_>(), 0, st>>>(f.tw, a, src, sens, wrow, wcol, \
+                                                                 contrib);
+    PP_S4(8) PP_S4(12) PP_S4(16) PP_S4(20) PP_S4(24)
+#undef PP_S4
+    PP_TRY(check4("rows4_inv_kernel"));
+    const int64_t n = (int64_t)a.nrows * a.n;
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    coil_sum_kernel<<<(int)blocks, 256, 0, st>>>(contrib, ncoils, n, a.scale, operand, alpha, out);
+    PP_TRY(check4("coil_sum_kernel"));
     *done = true;
     return PP_OK;
 }

@@ -123,3 +123,14 @@ def test_binding_rejects_wrong_sizes_before_device_work(L):
                                  torch.zeros(96, dtype=torch.complex64))
     fake.handle = None
     fb.handle = None
+
+
+@pytest.mark.parametrize("d,mu", [(0, 0.2), (1, 0.1), (3, 0.05), (5, 0.02), (8, 0.3)])
+def test_chebyshev_coefficients_match_oracle(L, d, mu):
+    import paper_2204_10252_gb300 as pp
+    from oracle import pp_oracle as O
+    got = pp.pp_poly_coeffs_cheb(d, mu)
+    ref = np.array(O.poly_coeffs_cheb(d, mu))
+    assert np.max(np.abs(got - ref)) <= 1e-10 * np.max(np.abs(ref))
+    with pytest.raises(pp.PPError):
+        pp.pp_poly_coeffs_cheb(3, 1.5)

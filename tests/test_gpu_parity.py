@@ -176,6 +176,20 @@ def test_solve_parity(pp, prob, d):
     assert r.launches > iters
 
 
+@pytest.mark.parametrize("coeffs", ["l2", "cheb"])
+def test_ppgd_without_momentum(pp, prob, coeffs):
+    # Algorithm "ppgd" (beta_k = 0) with the l2 or the Chebyshev polynomial
+    x0 = synth.phantom(prob.shape, 8)
+    b = (prob.fwd(x0) + prob.ksp(9) * 1e-3).astype(np.complex64)
+    L = float(O.power_iteration(prob.normal, prob.shape, 9, iters=30))
+    pp.pp_plan_set_scale(prob.plan, L)
+    c = [float(v) for v in (O.poly_coeffs_l2(3) if coeffs == "l2" else O.poly_coeffs_cheb(3, 0.05))]
+    ref = O.pfista(prob.normal, prob.adj, b.astype(np.complex128), 1e-3, c, 8, L, momentum=False)
+    out = empty(prob.shape)
+    pp.pp_fista_solve(prob.plan, dev(b), 1e-3, 8, c, 3, out, momentum=False)
+    assert rel(host(out), ref) <= TOL_SOLVE
+
+
 @pytest.mark.parametrize("shape,levels", [((64, 48), 2), ((64, 48), 1), ((8, 16, 12), 2),
                                           ((6, 10, 14), 1), ((4, 4), 2)])
 @pytest.mark.parametrize("inplace", [False, True])
@@ -231,20 +245,38 @@ def test_unsupported_sizes_raise(pp):
     assert e.value.status == 1
 
 
-def test_full_size_spiral_normal_apply(pp):
+@pytest.fixture(scope="module")
+def full_spiral(pp):
     # 256^2, 32 coils, 16 x 4096 spiral: the workload the benchmark times.
     cfg = synth.CONFIGS["spiral2d_256_c32"]
     shape, C = cfg["shape"], cfg["coils"]
     sens = synth.coil_maps(shape, C, cfg["seed"])
     traj = synth.spiral_traj(cfg["interleaves"], cfg["samples"], cfg["turns"], 128.0)
     plan = pp.pp_plan_create(shape, C, dev(sens), traj=traj, power_iters=0)
+    L = 123.0
+    pp.pp_plan_set_scale(plan, L)
+    x = synth.crandn(shape, 11)
+    ref = O.nc_normal(x, sens, traj) / L
+    yield plan, x, ref
+    plan.destroy()
+
+
+def test_full_size_spiral_normal_apply(pp, full_spiral):
+    plan, x, ref = full_spiral
+    out = empty(x.shape)
+    pp.pp_normal_apply(plan, dev(x), out)
+    assert rel(host(out), ref) <= TOL_APPLY
+
+
+@pytest.mark.parametrize("row_variant,cpc", [(1, 8), (2, 4), (4, 16), (-1, 32), (-1, 2), (1, -8), (2, -3)])
+def test_full_size_spiral_every_launch_variant(pp, full_spiral, row_variant, cpc):
+    plan, x, ref = full_spiral
+    tuned = pp.pp_plan_tuning(plan)
     try:
-        L = 123.0
-        pp.pp_plan_set_scale(plan, L)
-        x = synth.crandn(shape, 11)
-        out = empty(shape)
+        pp.pp_plan_set_tuning(plan, row_variant, cpc)
+        assert pp.pp_plan_tuning(plan) == (row_variant, cpc)
+        out = empty(x.shape)
         pp.pp_normal_apply(plan, dev(x), out)
-        ref = O.nc_normal(x, sens, traj) / L
         assert rel(host(out), ref) <= TOL_APPLY
     finally:
-        plan.destroy()
+        pp.pp_plan_set_tuning(plan, *tuned)

@@ -112,3 +112,31 @@ def test_permutability_lemma():
     lhs = AH @ pmat(A @ AH)
     rhs = pmat(AH @ A) @ AH
     assert np.max(np.abs(lhs - rhs)) <= 1e-12 * np.max(np.abs(lhs))
+
+
+@pytest.mark.parametrize("d,mu", [(1, 0.1), (3, 0.05), (5, 0.02), (3, 0.3)])
+def test_chebyshev_equioscillates_on_mu_1(d, mu):
+    # Sec. 3.4: r(z) = 1 - z p(z) is T_{d+1} on [mu, 1] scaled by 1/T_{d+1}(a),
+    # a = (1+mu)/(1-mu): it takes +-1/T_{d+1}(a) alternately at the d+2
+    # points where (1+mu-2z)/(1-mu) = cos(j pi/(d+1)), and r(0) = 1.
+    c = O.poly_coeffs_cheb(d, mu)
+    a = (1 + mu) / (1 - mu)
+    Ta = np.cosh((d + 1) * np.arccosh(a))
+    j = np.arange(d + 2)
+    w = np.cos(j * np.pi / (d + 1))
+    z = (1 + mu - w * (1 - mu)) / 2
+    r = 1 - z * O.poly_eval(c, z)
+    assert np.max(np.abs(r - (-1.0) ** j / Ta)) <= 1e-9
+    zz = np.linspace(mu, 1, 4001)
+    assert np.max(np.abs(1 - zz * O.poly_eval(c, zz))) <= 1 / Ta + 1e-9
+    # p > 0 on (0, 1] (Thm "ppos")
+    assert np.all(O.poly_eval(c, np.linspace(1e-6, 1, 4001)) > 0)
+
+
+@pytest.mark.parametrize("d", [1, 3, 5])
+def test_chebyshev_beats_l2_in_the_max_norm_on_mu_1(d):
+    mu = 0.1
+    zz = np.linspace(mu, 1, 4001)
+    cheb = np.max(np.abs(1 - zz * O.poly_eval(O.poly_coeffs_cheb(d, mu), zz)))
+    l2 = np.max(np.abs(1 - zz * O.poly_eval(O.poly_coeffs_l2(d), zz)))
+    assert cheb < l2
