@@ -173,6 +173,10 @@ def kernel_flops(c, K):
         "cols_kernel": C * G * fft(G),
         # G^T G stencil: (2W-1)^2 complex-by-real multiply-adds per grid point and coil
         "gtg_stencil_kernel": 4.0 * (2 * W - 1) ** 2 * C * G * G,
+        "gtg_stencil2_kernel": 4.0 * (2 * W - 1) ** 2 * C * G * G,
+        "gtg_stencil_rb_kernel": 4.0 * (2 * W - 1) ** 2 * C * G * G,
+        "gtg_stencil_cl_kernel": 4.0 * (2 * W - 1) ** 2 * C * G * G,
+        "coil_sum_kernel": 2.0 * C * n,
         "rows_adj_cb_kernel": C * ny * fft(G) + 10.0 * C * n,
         "rows_adj_kernel": C * ny * fft(G) + 10.0 * C * n,
         "rows4_fwd_kernel": C * ny * fft(G) + 8.0 * C * n,

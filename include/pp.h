@@ -110,14 +110,22 @@ pp_status pp_plan_set_scale(pp_plan* plan, double L);
 pp_status pp_plan_sizes(const pp_plan* plan, int64_t* image_elems, int64_t* kspace_elems);
 
 /* Launch shapes the plan chose by timing at creation (non-Cartesian plans):
- * the row-IFFT stage of the normal operator (1, 2 or 4 = CTAs per image row,
- * coil groups reduced through distributed shared memory; -1 = one IFFT per
- * coil and row followed by a coil sum) and the G^T G stencil's coils per CTA
- * (negative: the variant with two outputs per thread).
+ *  - row_ifft_variant: the row-IFFT stage of the normal operator (1, 2 or
+ *    4 = CTAs per image row, coil groups reduced through distributed shared
+ *    memory; -1 = one IFFT per coil and row followed by a coil sum);
+ *  - stencil_kind: the G^T G stencil kernel (0 = one output per thread,
+ *    1 = two outputs per thread, both staging one coil at a time with
+ *    stencil_coils coils per CTA; 2..5 = register-blocked, a thread holding
+ *    R outputs of CG coils with (R, CG) = (4, 4), (8, 4), (4, 8), (2, 8), on
+ *    a persistent grid; stencil_coils is then ignored);
+ *  - stencil_coils: 1..64.
  * pp_plan_set_tuning overrides them (results are identical up to rounding
- * order).  No counterpart in the paper. */
-pp_status pp_plan_tuning(const pp_plan* plan, int* row_ifft_variant, int* stencil_coils);
-pp_status pp_plan_set_tuning(pp_plan* plan, int row_ifft_variant, int stencil_coils);
+ * order; PP_ERR_UNSUPPORTED for a variant the plan cannot run).  Any output
+ * pointer may be NULL.  No counterpart in the paper. */
+pp_status pp_plan_tuning(const pp_plan* plan, int* row_ifft_variant, int* stencil_kind,
+                         int* stencil_coils);
+pp_status pp_plan_set_tuning(pp_plan* plan, int row_ifft_variant, int stencil_kind,
+                             int stencil_coils);
 
 /* y = A x (unscaled forward model; Sec. 5.1: M F S_c x with the centred
  * orthonormal FFT; Sec. 5.2: gridding NUFFT of S_c x).

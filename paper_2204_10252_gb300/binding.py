@@ -55,8 +55,9 @@ _SIGS = {
     "pp_plan_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "pp_plan_scale": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     "pp_plan_set_scale": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
-    "pp_plan_tuning": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
-    "pp_plan_set_tuning": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
+    "pp_plan_tuning": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "pp_plan_set_tuning": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "pp_plan_sizes": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
                                      ctypes.POINTER(ctypes.c_int64)]),
     "pp_forward_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
@@ -256,14 +257,16 @@ def pp_plan_set_scale(plan: Plan, L: float):
 
 
 def pp_plan_tuning(plan: Plan):
-    a, b = ctypes.c_int(0), ctypes.c_int(0)
-    _check(lib().pp_plan_tuning(plan.handle, ctypes.byref(a), ctypes.byref(b)), "pp_plan_tuning")
-    return a.value, b.value
+    """(row_ifft_variant, stencil_kind, stencil_coils) chosen at plan creation."""
+    a, b, c = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+    _check(lib().pp_plan_tuning(plan.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+           "pp_plan_tuning")
+    return a.value, b.value, c.value
 
 
-def pp_plan_set_tuning(plan: Plan, row_ifft_variant: int, stencil_coils: int):
-    _check(lib().pp_plan_set_tuning(plan.handle, int(row_ifft_variant), int(stencil_coils)),
-           "pp_plan_set_tuning")
+def pp_plan_set_tuning(plan: Plan, row_ifft_variant: int, stencil_kind: int, stencil_coils: int = 8):
+    _check(lib().pp_plan_set_tuning(plan.handle, int(row_ifft_variant), int(stencil_kind),
+                                    int(stencil_coils)), "pp_plan_set_tuning")
 
 
 def pp_plan_sizes(plan: Plan):

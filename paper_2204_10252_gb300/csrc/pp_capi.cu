@@ -433,6 +433,7 @@ static pp_status build_noncartesian(Plan& p, const pp_sampling* s) {
         std::vector<float> Tf(T.size());
         for (size_t i = 0; i < T.size(); ++i) Tf[i] = (float)T[i];
         PP_TRY(upload(p, &p.gtg, Tf));
+        PP_TRY(prepare_gtg_stencil(p));
     }
     PP_TRY(alloc_n(p, &p.wk_a, (size_t)p.C * ny * Gx));
     PP_TRY(alloc_n(p, &p.wk_b, (size_t)p.C * Gy * Gx));
@@ -442,16 +443,17 @@ static pp_status build_noncartesian(Plan& p, const pp_sampling* s) {
 }
 
 // Plan-time autotuning of the non-Cartesian operator's launch shapes: the
-// row-IFFT cluster size and the stencil's coils per CTA are each timed on the
-// plan's own buffers (3 launches after one warm-up) and the fastest is kept.
+// row-IFFT variant and the stencil's shape are each timed on the plan's own
+// buffers (10 launches after two warm-ups) and the fastest is kept.
 static pp_status tune_noncartesian(Plan& p, cudaStream_t st) {
     cudaEvent_t e0, e1;
     PP_TRY_CUDA(cudaEventCreate(&e0));
     PP_TRY_CUDA(cudaEventCreate(&e1));
     auto timeit = [&](auto&& fn, float* ms) -> pp_status {
         PP_TRY(fn());
+        PP_TRY(fn());
         PP_TRY_CUDA(cudaEventRecord(e0, st));
-        for (int r = 0; r < 3; ++r) PP_TRY(fn());
+        for (int r = 0; r < 10; ++r) PP_TRY(fn());
         PP_TRY_CUDA(cudaEventRecord(e1, st));
         PP_TRY_CUDA(cudaEventSynchronize(e1));
         PP_TRY_CUDA(cudaEventElapsedTime(ms, e0, e1));
@@ -482,18 +484,19 @@ static pp_status tune_noncartesian(Plan& p, cudaStream_t st) {
     }
     p.tune_rows_adj_cl = best_cl;
     best = 1e30f;
-    int best_cpc = 8, best_two = 0;
-    for (int two : {0, 1})
+    int best_cpc = 8, best_kind = 0;
+    for (int kind = 0; kind <= 5; ++kind)
         for (int cpc : {2, 4, 8, 16, 32}) {
+            if (kind >= 2 && (cpc != 8 || p.stencil_rb_grid[kind - 2] == 0)) continue;
             if (cpc > p.C && cpc != 2) continue;
             p.tune_stencil_cpc = cpc;
-            p.tune_stencil_two = two;
+            p.tune_stencil_kind = kind;
             float ms = 0.f;
             PP_TRY(timeit([&]() { return launch_gtg_stencil(p, p.wk_b, p.wk_c, st); }, &ms));
-            if (ms < best) { best = ms; best_cpc = cpc; best_two = two; }
+            if (ms < best) { best = ms; best_cpc = cpc; best_kind = kind; }
         }
     p.tune_stencil_cpc = best_cpc;
-    p.tune_stencil_two = best_two;
+    p.tune_stencil_kind = best_kind;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return PP_OK;
@@ -1145,24 +1148,24 @@ pp_status pp_plan_set_scale(pp_plan* plan, double L) {
     return PP_OK;
 }
 
-pp_status pp_plan_tuning(const pp_plan* plan, int* row_ifft_variant, int* stencil_coils) {
+pp_status pp_plan_tuning(const pp_plan* plan, int* row_ifft_variant, int* stencil_kind,
+                         int* stencil_coils) {
     if (!plan) {
         set_error("pp_plan_tuning: NULL plan");
         return PP_ERR_INVALID_ARG;
     }
     if (row_ifft_variant) *row_ifft_variant = plan->impl.tune_rows_adj_cl ? plan->impl.tune_rows_adj_cl : 1;
-    if (stencil_coils) {
-        const int cpc = plan->impl.tune_stencil_cpc ? plan->impl.tune_stencil_cpc : 8;
-        *stencil_coils = plan->impl.tune_stencil_two ? -cpc : cpc;
-    }
+    if (stencil_kind) *stencil_kind = plan->impl.tune_stencil_kind;
+    if (stencil_coils) *stencil_coils = plan->impl.tune_stencil_cpc ? plan->impl.tune_stencil_cpc : 8;
     return PP_OK;
 }
 
-pp_status pp_plan_set_tuning(pp_plan* plan, int row_ifft_variant, int stencil_coils) {
+pp_status pp_plan_set_tuning(pp_plan* plan, int row_ifft_variant, int stencil_kind, int stencil_coils) {
     if (!plan || !(row_ifft_variant == 1 || row_ifft_variant == 2 || row_ifft_variant == 4 ||
                    row_ifft_variant == -1) ||
-        stencil_coils == 0 || stencil_coils > 64 || stencil_coils < -64) {
-        set_error("pp_plan_set_tuning: row variant must be 1, 2, 4 or -1; stencil coils +-1..64");
+        stencil_kind < 0 || stencil_kind > 5 || stencil_coils < 1 || stencil_coils > 64) {
+        set_error("pp_plan_set_tuning: row variant must be 1, 2, 4 or -1; stencil kind 0..5; "
+                  "stencil coils 1..64");
         return PP_ERR_INVALID_ARG;
     }
     Plan& p = plan->impl;
@@ -1171,9 +1174,14 @@ pp_status pp_plan_set_tuning(pp_plan* plan, int row_ifft_variant, int stencil_co
                   "register-FFT grid length");
         return PP_ERR_UNSUPPORTED;
     }
+    if (stencil_kind >= 2 && (p.kind != PP_NONCARTESIAN || p.stencil_rb_grid[stencil_kind - 2] == 0)) {
+        set_error("pp_plan_set_tuning: register-blocked stencil kinds need a non-Cartesian plan "
+                  "whose 49 weight planes hold fewer than 2^31 values");
+        return PP_ERR_UNSUPPORTED;
+    }
     p.tune_rows_adj_cl = row_ifft_variant;
-    p.tune_stencil_cpc = stencil_coils > 0 ? stencil_coils : -stencil_coils;
-    p.tune_stencil_two = stencil_coils < 0;
+    p.tune_stencil_kind = stencil_kind;
+    p.tune_stencil_cpc = stencil_coils;
     p.gkey.clear();
     return PP_OK;
 }

@@ -125,8 +125,10 @@ struct Plan {
     // plan-time autotuned launch shapes (0 = default)
     int tune_rows_adj_cl = 0;   // row-IFFT variant: cluster size 1, 2 or 4, or -1 = split
                                 // into per-coil IFFTs plus a coil sum (normal operator only)
-    int tune_stencil_cpc = 0;   // coils per CTA of the G^T G stencil
-    int tune_stencil_two = 0;   // 1: two outputs per thread (gtg_stencil2_kernel)
+    int tune_stencil_kind = 0;  // G^T G stencil kernel: 0 one output per thread, 1 two,
+                                // 2..5 register-blocked (R x CG = 4x4, 8x4, 4x8, 2x8)
+    int tune_stencil_cpc = 0;   // coils per CTA of kinds 0 and 1
+    int stencil_rb_grid[4] = {0, 0, 0, 0};   // persistent grid of kinds 2..5 (0: unavailable)
     std::vector<void*> allocs;
 };
 
@@ -185,6 +187,7 @@ pp_status launch_conj_accum(const float2* s, const float2* wv, float2* out, int6
                             cudaStream_t st);
 pp_status launch_nufft_spread(const Plan& p, const float2* ksp, float2* grid_out, cudaStream_t st);
 pp_status launch_gtg_stencil(const Plan& p, const float2* grid_in, float2* grid_out, cudaStream_t st);
+pp_status prepare_gtg_stencil(Plan& p);
 pp_status launch_nufft_degrid(const Plan& p, const float2* grid_in, float2* ksp, cudaStream_t st);
 pp_status launch_prox(int ndim, int nx, int ny, int nz, int levels, float lambda,
                       const float2* in, float2* out, cudaStream_t st);

@@ -560,6 +560,118 @@ gtg_stencil2_kernel(const float* __restrict__ T, int Gx, int Gy, int C, int coil
     }
 }
 
+// Asynchronous 8-byte global -> shared copy (zero-filled when !valid).
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem, bool valid) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    const int n = valid ? 8 : 0;
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(s), "l"(gmem), "r"(n)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Register-blocked variant of the G^T G stencil.  Work item = (32 x TY
+// output tile, group of CG coils); a persistent CTA takes a contiguous run
+// of items (tile-major, so consecutive items reuse the tile's weights) and
+// stages the next item's halo with cp.async while it computes the current
+// one.  A warp covers 32 adjacent columns; a thread holds R vertically
+// adjacent outputs of CG coils, so each halo word (two coils, 16 bytes) is
+// read once for every output whose window contains it, and each weight once
+// for CG coils.
+template <int R, int CG, int NWY>
+__global__ void __launch_bounds__(32 * NWY)
+gtg_stencil_rb_kernel(const float* __restrict__ T, int Gx, int Gy, int C,
+                      const float2* __restrict__ grid_in, float2* __restrict__ grid_out) {
+    constexpr int W = 4, H = W - 1, D = 2 * W - 1;
+    constexpr int TX = 32, TY = R * NWY, HX = TX + 2 * H, HY = TY + 2 * H, NP = CG / 2;
+    constexpr int BUF = NP * HY * HX;   // float4 words per halo buffer
+    extern __shared__ float4 hs[];
+    const int ntx = (Gx + TX - 1) / TX, nty = (Gy + TY - 1) / TY, ngrp = (C + CG - 1) / CG;
+    const int nitems = ntx * nty * ngrp;
+    const int it0 = (int)((int64_t)blockIdx.x * nitems / gridDim.x);
+    const int it1 = (int)((int64_t)(blockIdx.x + 1) * nitems / gridDim.x);
+    if (it0 >= it1) return;
+    const int plane = Gx * Gy;
+    const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
+    // halo rows are spread over the warps, halo columns over the lanes
+    auto stage = [&](int it, float4* buf) {
+        const int g = it % ngrp, tile = it / ngrp;
+        const int tx0 = (tile % ntx) * TX, ty0 = (tile / ntx) * TY, c0 = g * CG;
+        const int gx0 = wrapG(tx0 - H + lane, Gx);
+        const int gx1 = lane < HX - 32 ? wrapG(tx0 - H + 32 + lane, Gx) : 0;
+        float2* b2 = reinterpret_cast<float2*>(buf);
+        for (int rr = wy; rr < CG * HY; rr += NWY) {
+            const int j = rr / HY, hy = rr - j * HY;
+            const bool ok = c0 + j < C;
+            const float2* src = grid_in + (int64_t)(ok ? c0 + j : 0) * plane +
+                                (int64_t)wrapG(ty0 - H + hy, Gy) * Gx;
+            float2* dst = b2 + (size_t)(((j >> 1) * HY + hy) * HX) * 2 + (j & 1);
+            cp_async8(dst + 2 * lane, src + gx0, ok);
+            if (lane < HX - 32) cp_async8(dst + 2 * (32 + lane), src + gx1, ok);
+        }
+    };
+    stage(it0, hs);
+    cp_async_commit();
+    for (int it = it0; it < it1; ++it) {
+        const float4* cur = hs + ((it - it0) & 1) * BUF;
+        if (it + 1 < it1) stage(it + 1, hs + ((it + 1 - it0) & 1) * BUF);
+        cp_async_commit();
+        cp_async_wait<1>();
+        __syncthreads();
+        const int g = it % ngrp, tile = it / ngrp;
+        const int tx0 = (tile % ntx) * TX, ty0 = (tile / ntx) * TY, c0 = g * CG;
+        const int x = tx0 + lane, y0 = ty0 + wy * R;
+        // weight offsets, clamped into the grid for outputs that are not stored
+        int off[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) off[r] = min(y0 + r, Gy - 1) * Gx + min(x, Gx - 1);
+        float2 acc[R][CG];
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int j = 0; j < CG; ++j) acc[r][j] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int iy = 0; iy < R + D - 1; ++iy)
+#pragma unroll
+            for (int dx = 0; dx < D; ++dx) {
+                float4 v[NP];
+#pragma unroll
+                for (int q = 0; q < NP; ++q) v[q] = cur[(q * HY + wy * R + iy) * HX + lane + dx];
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const int dy = iy - r;
+                    if (dy < 0 || dy >= D) continue;
+                    const float w = __ldg(T + (dy * D + dx) * plane + off[r]);
+#pragma unroll
+                    for (int q = 0; q < NP; ++q) {
+                        acc[r][2 * q].x += w * v[q].x;
+                        acc[r][2 * q].y += w * v[q].y;
+                        acc[r][2 * q + 1].x += w * v[q].z;
+                        acc[r][2 * q + 1].y += w * v[q].w;
+                    }
+                }
+            }
+        if (x < Gx) {
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                if (y0 + r < Gy) {
+#pragma unroll
+                    for (int j = 0; j < CG; ++j)
+                        if (c0 + j < C)
+                            grid_out[(int64_t)(c0 + j) * plane + (y0 + r) * Gx + x] = acc[r][j];
+                }
+        }
+        __syncthreads();   // the next iteration restages the buffer read here
+    }
+}
+
+template <int R, int CG, int NWY>
+constexpr size_t rb_smem() {
+    return sizeof(float4) * 2 * (CG / 2) * (R * NWY + 6) * (32 + 6);
+}
+
 // Row stage k rows -> image for many coils: the FFT batch runs over 8 coils
 // of one image row, so a CTA per row covers every coil in ceil(C/8) rounds.
 // Same result as rows_adj_kernel (conj-coil reduction + axpy epilogue).
@@ -1074,9 +1186,51 @@ pp_status launch_conj_accum(const float2* s, const float2* wv, float2* out, int6
 
 static size_t tile_smem(const Plan& p) { return sizeof(float2) * (size_t)p.T * p.T; }
 
+template <int R, int CG, int NWY>
+static pp_status rb_prepare(const Plan& p, int* grid) {
+    auto fn = gtg_stencil_rb_kernel<R, CG, NWY>;
+    constexpr size_t sm = rb_smem<R, CG, NWY>();
+    PP_TRY_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    int occ = 0, nsm = 0, dev = 0;
+    PP_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 32 * NWY, sm));
+    PP_TRY_CUDA(cudaGetDevice(&dev));
+    PP_TRY_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const int64_t nitems = (int64_t)((p.G_x + 31) / 32) * ((p.G_y + R * NWY - 1) / (R * NWY)) *
+                           ((p.C + CG - 1) / CG);
+    *grid = (int)std::max<int64_t>(1, std::min<int64_t>(nitems, (int64_t)std::max(occ, 1) * nsm));
+    return PP_OK;
+}
+
+template <int R, int CG, int NWY>
+static pp_status rb_launch(const Plan& p, int grid, const float2* in, float2* out, cudaStream_t st) {
+    gtg_stencil_rb_kernel<R, CG, NWY><<<grid, 32 * NWY, rb_smem<R, CG, NWY>(), st>>>(
+        p.gtg, p.G_x, p.G_y, p.C, in, out);
+    return check_launch("gtg_stencil_rb_kernel");
+}
+
+pp_status prepare_gtg_stencil(Plan& p) {
+    // the register-blocked kernels index the weight planes with 32-bit offsets
+    if ((int64_t)49 * p.G_x * p.G_y >= ((int64_t)1 << 31)) return PP_OK;
+    PP_TRY((rb_prepare<4, 4, 4>(p, &p.stencil_rb_grid[0])));
+    PP_TRY((rb_prepare<8, 4, 2>(p, &p.stencil_rb_grid[1])));
+    PP_TRY((rb_prepare<4, 8, 4>(p, &p.stencil_rb_grid[2])));
+    PP_TRY((rb_prepare<2, 8, 4>(p, &p.stencil_rb_grid[3])));
+    return PP_OK;
+}
+
 pp_status launch_gtg_stencil(const Plan& p, const float2* grid_in, float2* grid_out, cudaStream_t st) {
     const int cpc = p.tune_stencil_cpc > 0 ? p.tune_stencil_cpc : 8;
-    if (p.tune_stencil_two) {
+    const int kind = p.tune_stencil_kind;
+    if (kind >= 2 && p.stencil_rb_grid[kind - 2] > 0) {
+        const int g = p.stencil_rb_grid[kind - 2];
+        switch (kind) {
+            case 2: return rb_launch<4, 4, 4>(p, g, grid_in, grid_out, st);
+            case 3: return rb_launch<8, 4, 2>(p, g, grid_in, grid_out, st);
+            case 4: return rb_launch<4, 8, 4>(p, g, grid_in, grid_out, st);
+            default: return rb_launch<2, 8, 4>(p, g, grid_in, grid_out, st);
+        }
+    }
+    if (kind == 1) {
         dim3 grid((p.G_x + 15) / 16, (p.G_y + 15) / 16, (p.C + cpc - 1) / cpc);
         gtg_stencil2_kernel<4><<<grid, 128, 0, st>>>(p.gtg, p.G_x, p.G_y, p.C, cpc, grid_in, grid_out);
         return check_launch("gtg_stencil2_kernel");

@@ -22,6 +22,10 @@ constexpr int RBF = 8;      // rows / coils per CTA (row stages)
 
 
 template <int N2> __host__ __device__ constexpr int tpr() { return N2 > N1 ? N2 : N1; }
+// Minimum resident CTAs of the row stages: for N2 = 20 this caps them at 56
+// registers, so that 7 CTAs of 160 threads fit an SM and the 1024 CTAs of a
+// 256-row, 32-coil stage run in one wave on 152 SMs.
+template <int N2> __host__ __device__ constexpr int row_min_ctas() { return N2 == 20 ? 7 : 1; }
 
 // Column stage: TXF adjacent columns of one batch, transform along rows.
 template <int N2, bool INV>
@@ -80,7 +84,7 @@ cols4_kernel(const float2* __restrict__ tw, ColArgs a, const float2* src, float2
 
 // Row stage image -> k rows (coil expansion, weights, circular placement).
 template <int N2>
-__global__ void __launch_bounds__(RBF * tpr<N2>())
+__global__ void __launch_bounds__(RBF * tpr<N2>(), row_min_ctas<N2>())
 rows4_fwd_kernel(const float2* __restrict__ tw, RowArgs a, const float2* __restrict__ x,
                  int64_t x_batch_stride, const float2* __restrict__ sens,
                  const float* __restrict__ wrow, const float* __restrict__ wcol,
@@ -320,7 +324,7 @@ rows4_adj_cl_kernel(const float2* __restrict__ tw, RowArgs a, const float2* __re
 // product fused into the store: contrib[c][row][i] = w conj(S_c) IFFT(src_c[row])
 // at image index i.  The coil sum follows in coil_sum_kernel.
 template <int N2>
-__global__ void __launch_bounds__(RBF * tpr<N2>())
+__global__ void __launch_bounds__(RBF * tpr<N2>(), row_min_ctas<N2>())
 rows4_inv_kernel(const float2* __restrict__ tw, RowArgs a, const float2* __restrict__ src,
                  const float2* __restrict__ sens, const float* __restrict__ wrow,
                  const float* __restrict__ wcol, float2* __restrict__ contrib) {
@@ -366,16 +370,28 @@ rows4_inv_kernel(const float2* __restrict__ tw, RowArgs a, const float2* __restr
     }
 }
 
-// out[o] = scale * sum_c contrib[c][o] + alpha * operand[o]
-__global__ void coil_sum_kernel(const float2* __restrict__ contrib, int C, int64_t n, float scale,
-                                const float2* operand, float alpha, float2* out) {
-    for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < n;
-         o += (int64_t)gridDim.x * blockDim.x) {
+// out[o] = scale * sum_c contrib[c][o] + alpha * operand[o].  A block of
+// 64 x 4 threads covers 64 outputs; thread row g sums coils g, g + 4, ...,
+// and the four partial sums meet in shared memory (fixed order).
+__global__ void __launch_bounds__(256)
+coil_sum_kernel(const float2* __restrict__ contrib, int C, int64_t n, float scale,
+                const float2* operand, float alpha, float2* out) {
+    __shared__ float2 part[4][64];
+    const int lx = threadIdx.x & 63, g = threadIdx.x >> 6;
+    for (int64_t base = (int64_t)blockIdx.x * 64; base < n; base += (int64_t)gridDim.x * 64) {
+        const int64_t o = base + lx;
         float2 acc = make_float2(0.f, 0.f);
-        for (int c = 0; c < C; ++c) acc = cadd(acc, contrib[(int64_t)c * n + o]);
-        acc = cscale(acc, scale);
-        if (operand) acc = cadd(acc, cscale(operand[o], alpha));
-        out[o] = acc;
+        if (o < n)
+            for (int c = g; c < C; c += 4) acc = cadd(acc, contrib[(int64_t)c * n + o]);
+        part[g][lx] = acc;
+        __syncthreads();
+        if (g == 0 && o < n) {
+            float2 v = cadd(cadd(part[0][lx], part[1][lx]), cadd(part[2][lx], part[3][lx]));
+            v = cscale(v, scale);
+            if (operand) v = cadd(v, cscale(operand[o], alpha));
+            out[o] = v;
+        }
+        __syncthreads();
     }
 }
 
@@ -740,8 +756,8 @@ pp_status launch_rows4_adj_split(const DevFft& f, const RowArgs& a, const float2
 #undef PP_S4
     PP_TRY(check4("rows4_inv_kernel"));
     const int64_t n = (int64_t)a.nrows * a.n;
-    int64_t blocks = (n + 255) / 256;
-    if (blocks > 152 * 8) blocks = 152 * 8;
+    int64_t blocks = (n + 63) / 64;
+    if (blocks > 152 * 16) blocks = 152 * 16;
     coil_sum_kernel<<<(int)blocks, 256, 0, st>>>(contrib, ncoils, n, a.scale, operand, alpha, out);
     PP_TRY(check4("coil_sum_kernel"));
     *done = true;

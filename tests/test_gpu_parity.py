@@ -101,6 +101,33 @@ def prob(request, pp):
     p.plan.destroy()
 
 
+SMALL_NC = [((64, 64), 5, dict(interleaves=4, samples=512)),
+            ((72, 80), 2, dict(interleaves=3, samples=700, turns=3.0, kmax=35.9)),
+            ((32, 40), 3, dict(interleaves=2, samples=300, turns=2.0, kmax=15.9))]
+
+
+@pytest.mark.parametrize("case", range(len(SMALL_NC)), ids=["spiral64_c5", "spiral72x80_c2",
+                                                            "spiral32x40_c3"])
+def test_every_stencil_kind_small_grids(pp, case):
+    # Grids that end inside a tile (32 x 40 -> 40 x 50: the smallest grid a
+    # plan accepts) and coil counts that leave a coil group part empty.
+    shape, C, kw = SMALL_NC[case]
+    p = Problem(pp, "noncart", shape, C, 300 + case, **kw)
+    try:
+        x = synth.crandn(shape, 5)
+        L = 2.5
+        pp.pp_plan_set_scale(p.plan, L)
+        ref = p.normal(x) / L
+        for kind in range(6):
+            for cpc in ((1, 3) if kind < 2 else (8,)):
+                pp.pp_plan_set_tuning(p.plan, 1, kind, cpc)
+                out = empty(shape)
+                pp.pp_normal_apply(p.plan, dev(x), out)
+                assert rel(host(out), ref) <= TOL_APPLY, (kind, cpc)
+    finally:
+        p.plan.destroy()
+
+
 def test_forward_parity(pp, prob):
     x = synth.crandn(prob.shape, 1)
     y = empty(prob.kshape)
@@ -268,13 +295,15 @@ def test_full_size_spiral_normal_apply(pp, full_spiral):
     assert rel(host(out), ref) <= TOL_APPLY
 
 
-@pytest.mark.parametrize("row_variant,cpc", [(1, 8), (2, 4), (4, 16), (-1, 32), (-1, 2), (1, -8), (2, -3)])
-def test_full_size_spiral_every_launch_variant(pp, full_spiral, row_variant, cpc):
+@pytest.mark.parametrize("row_variant,kind,cpc", [
+    (1, 0, 8), (2, 0, 4), (4, 0, 16), (-1, 0, 32), (-1, 0, 2), (1, 1, 8), (2, 1, 3),
+    (1, 2, 8), (-1, 3, 8), (2, 4, 8), (-1, 5, 8)])
+def test_full_size_spiral_every_launch_variant(pp, full_spiral, row_variant, kind, cpc):
     plan, x, ref = full_spiral
     tuned = pp.pp_plan_tuning(plan)
     try:
-        pp.pp_plan_set_tuning(plan, row_variant, cpc)
-        assert pp.pp_plan_tuning(plan) == (row_variant, cpc)
+        pp.pp_plan_set_tuning(plan, row_variant, kind, cpc)
+        assert pp.pp_plan_tuning(plan) == (row_variant, kind, cpc)
         out = empty(x.shape)
         pp.pp_normal_apply(plan, dev(x), out)
         assert rel(host(out), ref) <= TOL_APPLY
