@@ -117,7 +117,12 @@ pp_status pp_plan_sizes(const pp_plan* plan, int64_t* image_elems, int64_t* kspa
  *    1 = two outputs per thread, both staging one coil at a time with
  *    stencil_coils coils per CTA; 2..5 = register-blocked, a thread holding
  *    R outputs of CG coils with (R, CG) = (4, 4), (8, 4), (4, 8), (2, 8), on
- *    a persistent grid; stencil_coils is then ignored);
+ *    a persistent grid; 6 = coil-lane, the 32 lanes of a warp being 32
+ *    coils of 8 adjacent outputs; 7, 8 = the whole normal operator on
+ *    coil-innermost ([row][col][coil], 32-coil pitch) copies with a
+ *    coil-lane stencil of 1 or 2 rows per warp, row_ifft_variant then
+ *    unused (plans with at most 32 coils and register-FFT grid lengths);
+ *    stencil_coils is ignored for kinds 2..8);
  *  - stencil_coils: 1..64.
  * pp_plan_set_tuning overrides them (results are identical up to rounding
  * order; PP_ERR_UNSUPPORTED for a variant the plan cannot run).  Any output

@@ -177,7 +177,9 @@ static pp_status normal_into(const Plan& p, const float2* x, float2* out, float 
         }
         return PP_OK;
     }
-    // non-Cartesian: rows -> cols -> tile degrid/grid -> cols^H -> rows^H
+    // non-Cartesian: rows -> cols -> G^T G stencil -> cols^H -> rows^H
+    if (p.tune_stencil_kind >= 7 && p.ci_sens)
+        return ci_normal(p, x, out, scale, operand, alpha, p.tune_stencil_kind == 8 ? 2 : 1, st);
     const int Gx = p.G_x, Gy = p.G_y;
     RowArgs rf = row_args(nx, Gx, nx / 2, 0, ny, (int64_t)ny * nx, 1.f);
     PP_TRY(launch_rows_fwd(p, p.gx, rf, x, p.sens, p.deapod_y, p.deapod_x, p.wk_a, p.C, 0, st));
@@ -433,6 +435,15 @@ static pp_status build_noncartesian(Plan& p, const pp_sampling* s) {
         std::vector<float> Tf(T.size());
         for (size_t i = 0; i < T.size(); ++i) Tf[i] = (float)T[i];
         PP_TRY(upload(p, &p.gtg, Tf));
+        // [row][col/8][tap][8] copy for the coil-lane kernel (zero past G_x)
+        const int nxb = (Gx + 7) / 8;
+        std::vector<float> T8((size_t)Gy * nxb * D * D * 8, 0.f);
+        for (int y = 0; y < Gy; ++y)
+            for (int x = 0; x < Gx; ++x)
+                for (int d = 0; d < D * D; ++d)
+                    T8[(((size_t)y * nxb + x / 8) * D * D + d) * 8 + (x & 7)] =
+                        Tf[(size_t)d * plane + (size_t)y * Gx + x];
+        PP_TRY(upload(p, &p.gtg8, T8));
         PP_TRY(prepare_gtg_stencil(p));
     }
     PP_TRY(alloc_n(p, &p.wk_a, (size_t)p.C * ny * Gx));
@@ -443,8 +454,9 @@ static pp_status build_noncartesian(Plan& p, const pp_sampling* s) {
 }
 
 // Plan-time autotuning of the non-Cartesian operator's launch shapes: the
-// row-IFFT variant and the stencil's shape are each timed on the plan's own
-// buffers (10 launches after two warm-ups) and the fastest is kept.
+// row-IFFT variant and the stencil kernel are each timed on the plan's own
+// buffers (10 launches after two warm-ups, three rounds over all candidates,
+// best round kept per candidate) and the fastest is kept.
 static pp_status tune_noncartesian(Plan& p, cudaStream_t st) {
     cudaEvent_t e0, e1;
     PP_TRY_CUDA(cudaEventCreate(&e0));
@@ -463,43 +475,87 @@ static pp_status tune_noncartesian(Plan& p, cudaStream_t st) {
     PP_TRY_CUDA(cudaMemsetAsync(p.wk_b, 0, sizeof(float2) * (size_t)p.C * p.G_y * p.G_x, st));
     const int nx = p.nx, ny = p.ny, Gx = p.G_x;
     RowArgs ra = row_args(nx, Gx, 0, nx / 2, ny, (int64_t)ny * nx, 1.f);
-    float best = 1e30f;
-    int best_cl = 1;
-    for (int cl : {1, 2, 4, -1}) {
-        p.tune_rows_adj_cl = cl;
-        float ms = 0.f;
-        if (cl == -1) {
-            bool ok = fft4_n2(Gx) != 0;
-            if (!ok) continue;
-            PP_TRY(timeit([&]() {
-                bool done = false;
-                return launch_rows4_adj_split(p.gx, ra, p.wk_a, p.sens, p.deapod_y, p.deapod_x, p.wk_c,
-                                              p.t, nullptr, 0.f, p.C, st, &done);
-            }, &ms));
-        } else {
-            PP_TRY(timeit([&]() { return launch_rows_adj(p, p.gx, ra, p.wk_a, p.sens, p.deapod_y,
-                                                         p.deapod_x, p.t, nullptr, 0.f, p.C, st); }, &ms));
+    constexpr int kRounds = 3;
+    std::vector<int> rows;
+    for (int cl : {1, 2, 4, -1})
+        if (cl != -1 || fft4_n2(Gx)) rows.push_back(cl);
+    std::vector<float> rbest(rows.size(), 1e30f);
+    for (int round = 0; round < kRounds; ++round)
+        for (size_t i = 0; i < rows.size(); ++i) {
+            const int cl = rows[i];
+            p.tune_rows_adj_cl = cl;
+            float ms = 0.f;
+            if (cl == -1) {
+                PP_TRY(timeit([&]() {
+                    bool done = false;
+                    return launch_rows4_adj_split(p.gx, ra, p.wk_a, p.sens, p.deapod_y, p.deapod_x,
+                                                  p.wk_c, p.t, nullptr, 0.f, p.C, st, &done);
+                }, &ms));
+            } else {
+                PP_TRY(timeit([&]() { return launch_rows_adj(p, p.gx, ra, p.wk_a, p.sens, p.deapod_y,
+                                                             p.deapod_x, p.t, nullptr, 0.f, p.C, st); },
+                              &ms));
+            }
+            rbest[i] = std::min(rbest[i], ms);
         }
-        if (ms < best) { best = ms; best_cl = cl; }
-    }
-    p.tune_rows_adj_cl = best_cl;
-    best = 1e30f;
-    int best_cpc = 8, best_kind = 0;
-    for (int kind = 0; kind <= 5; ++kind)
+    p.tune_rows_adj_cl = rows[std::min_element(rbest.begin(), rbest.end()) - rbest.begin()];
+    std::vector<std::pair<int, int>> sten;   // (kind, coils per CTA)
+    for (int kind = 0; kind <= 6; ++kind)
         for (int cpc : {2, 4, 8, 16, 32}) {
-            if (kind >= 2 && (cpc != 8 || p.stencil_rb_grid[kind - 2] == 0)) continue;
+            if (kind >= 2 && cpc != 8) continue;
+            if (kind >= 2 && kind <= 5 && p.stencil_rb_grid[kind - 2] == 0) continue;
+            if (kind == 6 && (!p.gtg8 || p.stencil_rb_grid[0] == 0)) continue;
             if (cpc > p.C && cpc != 2) continue;
-            p.tune_stencil_cpc = cpc;
-            p.tune_stencil_kind = kind;
+            sten.push_back({kind, cpc});
+        }
+    std::vector<float> sbest(sten.size(), 1e30f);
+    for (int round = 0; round < kRounds; ++round)
+        for (size_t i = 0; i < sten.size(); ++i) {
+            p.tune_stencil_kind = sten[i].first;
+            p.tune_stencil_cpc = sten[i].second;
             float ms = 0.f;
             PP_TRY(timeit([&]() { return launch_gtg_stencil(p, p.wk_b, p.wk_c, st); }, &ms));
-            if (ms < best) { best = ms; best_cpc = cpc; best_kind = kind; }
+            sbest[i] = std::min(sbest[i], ms);
         }
-    p.tune_stencil_cpc = best_cpc;
-    p.tune_stencil_kind = best_kind;
+    const size_t bi = std::min_element(sbest.begin(), sbest.end()) - sbest.begin();
+    p.tune_stencil_kind = sten[bi].first;
+    p.tune_stencil_cpc = sten[bi].second;
+    // whole operator: the tuned [coil][row][col] pipeline against the
+    // coil-innermost one (kinds 7, 8)
+    if (p.ci_sens) {
+        const int base = p.tune_stencil_kind;
+        PP_TRY_CUDA(cudaMemsetAsync(p.v, 0, sizeof(float2) * (size_t)p.nimg, st));
+        std::vector<int> whole = {base, 7, 8};
+        std::vector<float> wbest(whole.size(), 1e30f);
+        for (int round = 0; round < kRounds; ++round)
+            for (size_t i = 0; i < whole.size(); ++i) {
+                p.tune_stencil_kind = whole[i];
+                float ms = 0.f;
+                PP_TRY(timeit([&]() { return normal_into(p, p.v, p.t, 1.f, nullptr, 0.f, st); }, &ms));
+                wbest[i] = std::min(wbest[i], ms);
+            }
+        p.tune_stencil_kind = whole[std::min_element(wbest.begin(), wbest.end()) - wbest.begin()];
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return PP_OK;
+}
+
+// Buffers of the coil-innermost pipeline (when the plan supports it).
+static pp_status setup_ci(Plan& p, cudaStream_t st) {
+    if (!ci_supported(p)) return PP_OK;
+    PP_TRY(alloc_n(p, &p.ci_sens, ci_sens_elems(p)));
+    PP_TRY(alloc_n(p, &p.ci_part, ci_partial_elems(p)));
+    if (p.C == 32) {
+        p.ci_a = p.wk_a;
+        p.ci_b = p.wk_b;
+        p.ci_c = p.wk_c;
+    } else {
+        PP_TRY(alloc_n(p, &p.ci_a, ci_rows_elems(p)));
+        PP_TRY(alloc_n(p, &p.ci_b, ci_grid_elems(p)));
+        PP_TRY(alloc_n(p, &p.ci_c, ci_grid_elems(p)));
+    }
+    return ci_prepare(p, st);
 }
 
 static pp_status power_iteration(Plan& p, uint64_t seed, int iters, cudaStream_t st) {
@@ -1104,6 +1160,7 @@ pp_status pp_plan_create(pp_plan** out, pp_dims dims, int coils, const pp_c64* s
             if (e != cudaSuccess) rc = cuda_status(e, "cudaStreamCreate");
         }
     }
+    if (rc == PP_OK && p.kind == PP_NONCARTESIAN) rc = setup_ci(p, st);
     if (rc == PP_OK && p.kind == PP_NONCARTESIAN) rc = tune_noncartesian(p, st);
     if (rc == PP_OK && power_iters > 0) rc = power_iteration(p, seed, power_iters, st);
     if (rc != PP_OK) {
@@ -1163,8 +1220,8 @@ pp_status pp_plan_tuning(const pp_plan* plan, int* row_ifft_variant, int* stenci
 pp_status pp_plan_set_tuning(pp_plan* plan, int row_ifft_variant, int stencil_kind, int stencil_coils) {
     if (!plan || !(row_ifft_variant == 1 || row_ifft_variant == 2 || row_ifft_variant == 4 ||
                    row_ifft_variant == -1) ||
-        stencil_kind < 0 || stencil_kind > 5 || stencil_coils < 1 || stencil_coils > 64) {
-        set_error("pp_plan_set_tuning: row variant must be 1, 2, 4 or -1; stencil kind 0..5; "
+        stencil_kind < 0 || stencil_kind > 8 || stencil_coils < 1 || stencil_coils > 64) {
+        set_error("pp_plan_set_tuning: row variant must be 1, 2, 4 or -1; stencil kind 0..8; "
                   "stencil coils 1..64");
         return PP_ERR_INVALID_ARG;
     }
@@ -1174,9 +1231,15 @@ pp_status pp_plan_set_tuning(pp_plan* plan, int row_ifft_variant, int stencil_ki
                   "register-FFT grid length");
         return PP_ERR_UNSUPPORTED;
     }
-    if (stencil_kind >= 2 && (p.kind != PP_NONCARTESIAN || p.stencil_rb_grid[stencil_kind - 2] == 0)) {
+    if (stencil_kind >= 2 && (p.kind != PP_NONCARTESIAN || p.stencil_rb_grid[0] == 0 ||
+                              (stencil_kind <= 5 && p.stencil_rb_grid[stencil_kind - 2] == 0))) {
         set_error("pp_plan_set_tuning: register-blocked stencil kinds need a non-Cartesian plan "
                   "whose 49 weight planes hold fewer than 2^31 values");
+        return PP_ERR_UNSUPPORTED;
+    }
+    if (stencil_kind >= 7 && !p.ci_sens) {
+        set_error("pp_plan_set_tuning: the coil-innermost pipeline needs at most 32 coils and "
+                  "register-FFT grid lengths");
         return PP_ERR_UNSUPPORTED;
     }
     p.tune_rows_adj_cl = row_ifft_variant;

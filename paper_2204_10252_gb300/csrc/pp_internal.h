@@ -102,6 +102,11 @@ struct Plan {
     int max_tile_len = 0;
     SampleTaps* samp = nullptr;  // [K]
     float* gtg = nullptr;        // [(2W-1)^2][G_y][G_x] stencil of G^T G
+    float* gtg8 = nullptr;       // the same weights as [G_y][ceil(G_x/8)][(2W-1)^2][8]
+    // coil-innermost pipeline ([row][col][32 coils]; ci_a/b/c alias wk_a/b/c when C = 32)
+    float2* ci_sens = nullptr;   // [ny][nx][32]
+    float2 *ci_a = nullptr, *ci_b = nullptr, *ci_c = nullptr;
+    float2* ci_part = nullptr;   // [4][ny][nx] coil-block partial sums
 
     // Workspace
     float2* wk_a = nullptr;   // C * ny * G_x (rows) or C * n (Cartesian)
@@ -126,7 +131,9 @@ struct Plan {
     int tune_rows_adj_cl = 0;   // row-IFFT variant: cluster size 1, 2 or 4, or -1 = split
                                 // into per-coil IFFTs plus a coil sum (normal operator only)
     int tune_stencil_kind = 0;  // G^T G stencil kernel: 0 one output per thread, 1 two,
-                                // 2..5 register-blocked (R x CG = 4x4, 8x4, 4x8, 2x8)
+                                // 2..5 register-blocked (R x CG = 4x4, 8x4, 4x8, 2x8),
+                                // 6 coil-lane, 7 / 8 coil-innermost pipeline with a
+                                // 1- / 2-row coil-lane stencil
     int tune_stencil_cpc = 0;   // coils per CTA of kinds 0 and 1
     int stencil_rb_grid[4] = {0, 0, 0, 0};   // persistent grid of kinds 2..5 (0: unavailable)
     std::vector<void*> allocs;
@@ -188,6 +195,14 @@ pp_status launch_conj_accum(const float2* s, const float2* wv, float2* out, int6
 pp_status launch_nufft_spread(const Plan& p, const float2* ksp, float2* grid_out, cudaStream_t st);
 pp_status launch_gtg_stencil(const Plan& p, const float2* grid_in, float2* grid_out, cudaStream_t st);
 pp_status prepare_gtg_stencil(Plan& p);
+bool ci_supported(const Plan& p);
+size_t ci_grid_elems(const Plan& p);
+size_t ci_rows_elems(const Plan& p);
+size_t ci_sens_elems(const Plan& p);
+size_t ci_partial_elems(const Plan& p);
+pp_status ci_prepare(Plan& p, cudaStream_t st);
+pp_status ci_normal(const Plan& p, const float2* x, float2* out, float scale, const float2* operand,
+                    float alpha, int ry, cudaStream_t st);
 pp_status launch_nufft_degrid(const Plan& p, const float2* grid_in, float2* ksp, cudaStream_t st);
 pp_status launch_prox(int ndim, int nx, int ny, int nz, int levels, float lambda,
                       const float2* in, float2* out, cudaStream_t st);

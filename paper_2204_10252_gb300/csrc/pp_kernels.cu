@@ -560,6 +560,10 @@ gtg_stencil2_kernel(const float* __restrict__ T, int Gx, int Gy, int C, int coil
     }
 }
 
+// Periodic wrap for a in [-G, 2G) (halo coordinates of a grid at least as
+// large as the halo; plans guarantee G >= 40).
+__device__ __forceinline__ int wrap1(int a, int G) { return a < 0 ? a + G : (a >= G ? a - G : a); }
+
 // Asynchronous 8-byte global -> shared copy (zero-filled when !valid).
 __device__ __forceinline__ void cp_async8(void* smem, const void* gmem, bool valid) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -599,14 +603,14 @@ gtg_stencil_rb_kernel(const float* __restrict__ T, int Gx, int Gy, int C,
     auto stage = [&](int it, float4* buf) {
         const int g = it % ngrp, tile = it / ngrp;
         const int tx0 = (tile % ntx) * TX, ty0 = (tile / ntx) * TY, c0 = g * CG;
-        const int gx0 = wrapG(tx0 - H + lane, Gx);
-        const int gx1 = lane < HX - 32 ? wrapG(tx0 - H + 32 + lane, Gx) : 0;
+        const int gx0 = wrap1(tx0 - H + lane, Gx);
+        const int gx1 = wrap1(tx0 - H + 32 + lane, Gx);
         float2* b2 = reinterpret_cast<float2*>(buf);
         for (int rr = wy; rr < CG * HY; rr += NWY) {
             const int j = rr / HY, hy = rr - j * HY;
             const bool ok = c0 + j < C;
-            const float2* src = grid_in + (int64_t)(ok ? c0 + j : 0) * plane +
-                                (int64_t)wrapG(ty0 - H + hy, Gy) * Gx;
+            const float2* src = grid_in + (int64_t)min(c0 + j, C - 1) * plane +
+                                (int64_t)wrap1(ty0 - H + hy, Gy) * Gx;
             float2* dst = b2 + (size_t)(((j >> 1) * HY + hy) * HX) * 2 + (j & 1);
             cp_async8(dst + 2 * lane, src + gx0, ok);
             if (lane < HX - 32) cp_async8(dst + 2 * (32 + lane), src + gx1, ok);
@@ -664,6 +668,102 @@ gtg_stencil_rb_kernel(const float* __restrict__ T, int Gx, int Gy, int C,
                 }
         }
         __syncthreads();   // the next iteration restages the buffer read here
+    }
+}
+
+// Coil-lane G^T G stencil: lanes are coils, so every weight is one
+// shared-memory broadcast serving 32 coils.  A CTA owns a 16 x 4 output
+// tile for a chunk of 32 coils.  cp.async stages the input halo as
+// [row][col][coil] (coil stride 33 float2: conflict-free both for the
+// transposing copy and for the per-position coil reads) and the tile's
+// weights from the plan's [row][col/8][tap][8] copy of the planes.  A warp
+// computes 8 adjacent outputs of one row; the results return through
+// shared memory so that they leave coalesced along x.
+constexpr int CL_TX = 16, CL_TY = 4, CL_CS = 33;
+constexpr int CL_HX = CL_TX + 6, CL_HY = CL_TY + 6;
+constexpr size_t CL_HALO_BYTES = sizeof(float2) * CL_HY * CL_HX * CL_CS;       // 58080
+constexpr size_t CL_SMEM = CL_HALO_BYTES + sizeof(float) * CL_TY * CL_TX * 49;  // + 12544
+
+__global__ void __launch_bounds__(256, 3)
+gtg_stencil_cl_kernel(const float* __restrict__ T8, int Gx, int Gy, int C, int nxb,
+                      const float2* __restrict__ grid_in, float2* __restrict__ grid_out) {
+    constexpr int H = 3, D = 7;
+    extern __shared__ float4 sm4[];
+    float2* halo = reinterpret_cast<float2*>(sm4);
+    const float4* wts = sm4 + CL_HALO_BYTES / sizeof(float4);
+    const int ntx = (Gx + CL_TX - 1) / CL_TX, nch = (C + 31) / 32;
+    const int ch = blockIdx.x % nch, tile = blockIdx.x / nch;
+    const int tx0 = (tile % ntx) * CL_TX, ty0 = (tile / ntx) * CL_TY, c0 = ch * 32;
+    const int plane = Gx * Gy;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // halo: warp w copies coils w, w + 8, w + 16, w + 24 of every halo row,
+    // lane = column
+    if (lane < CL_HX) {
+        const int gx = wrap1(tx0 - H + lane, Gx);
+        const float2* src[4];
+        bool ok[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            ok[k] = c0 + w + 8 * k < C;
+            src[k] = grid_in + (int64_t)min(c0 + w + 8 * k, C - 1) * plane + gx;
+        }
+        float2* dst = halo + lane * CL_CS + w;
+#pragma unroll 2
+        for (int hy = 0; hy < CL_HY; ++hy) {
+            const int roff = wrap1(ty0 - H + hy, Gy) * Gx;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) cp_async8(dst + hy * CL_HX * CL_CS + 8 * k, src[k] + roff, ok[k]);
+        }
+    }
+    // weights: per tile row, the two 8-column blocks are 2 x 49 x 8 contiguous floats
+    {
+        const int xb0 = tx0 / 8;
+        for (int e = threadIdx.x; e < CL_TY * 2 * 49 * 2; e += blockDim.x) {
+            const int yy = e / 196, rem = e - yy * 196;   // rem = (s * 49 + d) * 2 + half
+            const int s = rem / 98;
+            const int y = ty0 + yy, xb = xb0 + s;
+            const bool ok = y < Gy && xb < nxb;
+            const float* src = T8 + (ok ? ((int64_t)y * nxb + xb0) * 392 + rem * 4 : 0);
+            const unsigned dst = (unsigned)__cvta_generic_to_shared(wts + e);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src),
+                         "r"(ok ? 16 : 0)
+                         : "memory");
+        }
+    }
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncthreads();
+    const int yy = w >> 1, s = w & 1;
+    const float4* wq = wts + (yy * 2 + s) * 49 * 2;
+    float2 acc[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) acc[r] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int dy = 0; dy < D; ++dy) {
+        const float2* hrow = halo + ((yy + dy) * CL_HX + 8 * s) * CL_CS + lane;
+        float2 xv[14];
+#pragma unroll
+        for (int j = 0; j < 14; ++j) xv[j] = hrow[j * CL_CS];
+#pragma unroll
+        for (int dx = 0; dx < D; ++dx) {
+            const float4 wa = wq[(dy * D + dx) * 2], wb = wq[(dy * D + dx) * 2 + 1];
+            const float wr[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                acc[r].x += wr[r] * xv[r + dx].x;
+                acc[r].y += wr[r] * xv[r + dx].y;
+            }
+        }
+    }
+    __syncthreads();   // every warp is done with the halo: reuse it for the transpose
+#pragma unroll
+    for (int r = 0; r < 8; ++r) halo[(yy * CL_TX + 8 * s + r) * CL_CS + lane] = acc[r];
+    __syncthreads();
+    for (int e = threadIdx.x; e < 32 * CL_TY * CL_TX; e += blockDim.x) {
+        const int x = e & (CL_TX - 1), y2 = (e / CL_TX) & (CL_TY - 1), c = e / (CL_TX * CL_TY);
+        const int gx = tx0 + x, gy = ty0 + y2;
+        if (c0 + c < C && gx < Gx && gy < Gy)
+            grid_out[(int64_t)(c0 + c) * plane + gy * Gx + gx] = halo[(y2 * CL_TX + x) * CL_CS + c];
     }
 }
 
@@ -1211,6 +1311,9 @@ static pp_status rb_launch(const Plan& p, int grid, const float2* in, float2* ou
 pp_status prepare_gtg_stencil(Plan& p) {
     // the register-blocked kernels index the weight planes with 32-bit offsets
     if ((int64_t)49 * p.G_x * p.G_y >= ((int64_t)1 << 31)) return PP_OK;
+    if (p.gtg8)
+        PP_TRY_CUDA(cudaFuncSetAttribute(gtg_stencil_cl_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CL_SMEM));
     PP_TRY((rb_prepare<4, 4, 4>(p, &p.stencil_rb_grid[0])));
     PP_TRY((rb_prepare<8, 4, 2>(p, &p.stencil_rb_grid[1])));
     PP_TRY((rb_prepare<4, 8, 4>(p, &p.stencil_rb_grid[2])));
@@ -1221,7 +1324,14 @@ pp_status prepare_gtg_stencil(Plan& p) {
 pp_status launch_gtg_stencil(const Plan& p, const float2* grid_in, float2* grid_out, cudaStream_t st) {
     const int cpc = p.tune_stencil_cpc > 0 ? p.tune_stencil_cpc : 8;
     const int kind = p.tune_stencil_kind;
-    if (kind >= 2 && p.stencil_rb_grid[kind - 2] > 0) {
+    if (kind == 6 && p.gtg8 && p.stencil_rb_grid[0] > 0) {
+        const int64_t nitems = (int64_t)((p.G_x + CL_TX - 1) / CL_TX) * ((p.G_y + CL_TY - 1) / CL_TY) *
+                               ((p.C + 31) / 32);
+        gtg_stencil_cl_kernel<<<(unsigned)nitems, 256, CL_SMEM, st>>>(p.gtg8, p.G_x, p.G_y, p.C,
+                                                                     (p.G_x + 7) / 8, grid_in, grid_out);
+        return check_launch("gtg_stencil_cl_kernel");
+    }
+    if (kind >= 2 && kind <= 5 && p.stencil_rb_grid[kind - 2] > 0) {
         const int g = p.stencil_rb_grid[kind - 2];
         switch (kind) {
             case 2: return rb_launch<4, 4, 4>(p, g, grid_in, grid_out, st);

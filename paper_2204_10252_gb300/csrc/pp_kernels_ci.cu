@@ -1,0 +1,385 @@
+// Coil-innermost pipeline of the non-Cartesian normal operator (Sec. 5.2):
+//   out = scale * sum_c conj(S_c) D F^H G^T G F D (S_c x) + alpha * operand
+// with every per-coil array stored as [row][col][coil] and the coil count
+// padded to CP = 32.  The row and column FFT stages run one transform per
+// (line, coil) with the 8 coils of a CTA in adjacent lanes, so every global
+// access is a 64-byte coil run; the G^T G stencil puts the 32 coils of one
+// grid point in the 32 lanes of a warp, so each stencil weight is a single
+// shared-memory broadcast and each halo row a contiguous copy; the row IFFT
+// reduces its 8 coils in shared memory and leaves one partial sum per CTA.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "pp_fft4.cuh"
+#include "pp_internal.h"
+
+namespace pp {
+namespace {
+
+constexpr int N1 = 16;
+constexpr int CB = 8;    // coils per CTA in the FFT stages
+constexpr int CP = 32;   // coil pitch of the coil-innermost arrays
+constexpr int NCB = CP / CB;
+
+template <int N2> __host__ __device__ constexpr int tpr() { return N2 > N1 ? N2 : N1; }
+// k1 pitch of the transpose buffer Y[k1][m2][coil]: an odd multiple of 8
+// float2 apart, so the two k1 rows of a half-warp fall on disjoint banks
+template <int N2> __host__ __device__ constexpr int ypitch() { return N2 * CB + 8; }
+template <int N2> __host__ __device__ constexpr int min_ctas() { return N2 == 20 ? 7 : 1; }
+
+__device__ __forceinline__ int wrap1(int a, int G) { return a < 0 ? a + G : (a >= G ? a - G : a); }
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool valid) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem),
+                 "r"(valid ? 16 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_wait_all() {
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+// S_ci[(y nx + x) CP + c] = S[c][y][x] (zero for c >= C)
+__global__ void ci_pack_sens_kernel(const float2* __restrict__ S, int C, int64_t n,
+                                    float2* __restrict__ Sci) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * CP;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(e % CP);
+        const int64_t o = e / CP;
+        Sci[e] = c < C ? S[c * n + o] : make_float2(0.f, 0.f);
+    }
+}
+
+// Row stage image -> k rows: A[row][q][c] = F_G(place(w S_c x[row]))[q].
+// grid (nrows, NCB), block CB * tpr(N2); lane j = threadIdx % 8 is the coil.
+template <int N2>
+__global__ void __launch_bounds__(CB * tpr<N2>(), min_ctas<N2>())
+ci_rows_fwd_kernel(const float2* __restrict__ tw, RowArgs a, const float2* __restrict__ x,
+                   const float2* __restrict__ S, const float* __restrict__ wrow,
+                   const float* __restrict__ wcol, float2* __restrict__ out) {
+    constexpr int n = N1 * N2, YP = ypitch<N2>();
+    __shared__ float2 tws[n];
+    __shared__ float2 Y[N1 * YP];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) tws[i] = tw[i];
+    __syncthreads();
+    const int j = threadIdx.x & (CB - 1), r = threadIdx.x / CB;
+    const int row = blockIdx.x, c = blockIdx.y * CB + j;
+    if (r < N2) {
+        const float wr = a.scale * (wrow ? wrow[row] : 1.f);
+        float2 v[N1];
+#pragma unroll
+        for (int m1 = 0; m1 < N1; ++m1) {
+            int i = N2 * m1 + r + a.off_in;
+            if (i >= n) i -= n;
+            float2 val = make_float2(0.f, 0.f);
+            if (i < a.n) {
+                const int64_t o = (int64_t)row * a.n + i;
+                val = cscale(cmul(x[o], S[o * CP + c]), wcol ? wr * wcol[i] : wr);
+            }
+            v[m1] = val;
+        }
+        fft4_phase1<N1, N2, false>(v, r, tws);
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) Y[k1 * YP + r * CB + j] = v[k1];
+    }
+    __syncthreads();
+    if (r < N1) {
+        float2 u[N2];
+#pragma unroll
+        for (int m2 = 0; m2 < N2; ++m2) u[m2] = Y[r * YP + m2 * CB + j];
+        fft4_phase2<N1, N2, false>(u, tws);
+        float2* orow = out + (int64_t)row * n * CP + c;
+#pragma unroll
+        for (int k2 = 0; k2 < N2; ++k2) {
+            int q = r + N1 * k2 + a.off_out;
+            if (q >= n) q -= n;
+            orow[(int64_t)q * CP] = u[k2];
+        }
+    }
+}
+
+// Column stage along rows of [H][Gx][CP]: input row (p + off_in) mod n of
+// transform position p (zero at or past Hin), output position k at row
+// (k + off_out) mod n when below Hout.  grid (Gx, NCB), block CB * tpr(N2).
+template <int N2, bool INV>
+__global__ void __launch_bounds__(CB * tpr<N2>(), min_ctas<N2>())
+ci_cols_kernel(const float2* __restrict__ tw, int Hin, int Hout, int off_in, int off_out, int Gx,
+               const float2* __restrict__ src, float2* __restrict__ dst) {
+    constexpr int n = N1 * N2, YP = ypitch<N2>();
+    __shared__ float2 tws[n];
+    __shared__ float2 Y[N1 * YP];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) tws[i] = tw[i];
+    __syncthreads();
+    const int j = threadIdx.x & (CB - 1), r = threadIdx.x / CB;
+    const int64_t rs = (int64_t)Gx * CP;
+    const int64_t cofs = (int64_t)blockIdx.x * CP + blockIdx.y * CB + j;
+    if (r < N2) {
+        float2 v[N1];
+#pragma unroll
+        for (int m1 = 0; m1 < N1; ++m1) {
+            int row = N2 * m1 + r + off_in;
+            if (row >= n) row -= n;
+            v[m1] = row < Hin ? src[row * rs + cofs] : make_float2(0.f, 0.f);
+        }
+        fft4_phase1<N1, N2, INV>(v, r, tws);
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) Y[k1 * YP + r * CB + j] = v[k1];
+    }
+    __syncthreads();
+    if (r < N1) {
+        float2 u[N2];
+#pragma unroll
+        for (int m2 = 0; m2 < N2; ++m2) u[m2] = Y[r * YP + m2 * CB + j];
+        fft4_phase2<N1, N2, INV>(u, tws);
+#pragma unroll
+        for (int k2 = 0; k2 < N2; ++k2) {
+            int q = r + N1 * k2 + off_out;
+            if (q >= n) q -= n;
+            if (q < Hout) dst[q * rs + cofs] = u[k2];
+        }
+    }
+}
+
+// G^T G stencil on [Gy][Gx][CP] grids: out_j = sum_d T[d][j] in_{j + delta_d}
+// (periodic).  A CTA owns a 16 x (4 RY) output tile; warp w covers the 8
+// columns 8 (w & 1) .. and the RY rows (w >> 1) RY .. of it, lane = coil.
+// cp.async stages the halo rows (contiguous [col][coil] runs) and the tile's
+// weights from the [row][col/8][tap][8] copy.
+template <int RY> struct CiStencil {
+    static constexpr int TX = 16, TY = 4 * RY, HX = TX + 6, HY = TY + 6;
+    static constexpr size_t HALO = sizeof(float2) * HY * HX * CP;
+    static constexpr size_t SMEM = HALO + sizeof(float) * TY * TX * 49;
+};
+
+template <int RY>
+__global__ void __launch_bounds__(256)
+ci_stencil_kernel(const float* __restrict__ T8, int Gx, int Gy, int nxb,
+                  const float2* __restrict__ in, float2* __restrict__ out) {
+    using S = CiStencil<RY>;
+    constexpr int TX = S::TX, TY = S::TY, HX = S::HX, HY = S::HY, D = 7, H = 3;
+    extern __shared__ float4 sm4[];
+    float2* halo = reinterpret_cast<float2*>(sm4);
+    float4* wts = sm4 + S::HALO / sizeof(float4);
+    const int ntx = (Gx + TX - 1) / TX;
+    const int tx0 = (blockIdx.x % ntx) * TX, ty0 = (blockIdx.x / ntx) * TY;
+    // halo: HY rows of HX points x 32 coils = 16 sixteen-byte chunks per point
+    for (int e = threadIdx.x; e < HY * HX * 16; e += blockDim.x) {
+        const int hp = e >> 4, q = e & 15;
+        const int hy = hp / HX, hx = hp - hy * HX;
+        const int gy = wrap1(ty0 - H + hy, Gy), gx = wrap1(tx0 - H + hx, Gx);
+        cp_async16(halo + (size_t)hp * CP + 2 * q, in + ((int64_t)gy * Gx + gx) * CP + 2 * q, true);
+    }
+    // weights: per tile row, blocks xb0 and xb0 + 1 are 2 x 49 x 8 contiguous floats
+    const int xb0 = tx0 / 8;
+    for (int e = threadIdx.x; e < TY * 196; e += blockDim.x) {
+        const int yy = e / 196, rem = e - yy * 196, s = rem / 98;
+        const int y = ty0 + yy;
+        const bool ok = y < Gy && xb0 + s < nxb;
+        cp_async16(wts + e, T8 + (ok ? ((int64_t)y * nxb + xb0) * 392 + rem * 4 : 0), ok);
+    }
+    cp_async_commit_wait_all();
+    __syncthreads();
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, s = w & 1, yb = (w >> 1) * RY;
+    float2 acc[RY][8];
+#pragma unroll
+    for (int ry = 0; ry < RY; ++ry)
+#pragma unroll
+        for (int r = 0; r < 8; ++r) acc[ry][r] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int i = 0; i < RY + D - 1; ++i) {
+        const float2* hrow = halo + ((yb + i) * HX + 8 * s) * CP + lane;
+        float2 xv[14];
+#pragma unroll
+        for (int jx = 0; jx < 14; ++jx) xv[jx] = hrow[jx * CP];
+#pragma unroll
+        for (int ry = 0; ry < RY; ++ry) {
+            const int dy = i - ry;
+            if (dy < 0 || dy >= D) continue;
+            const float4* wq = wts + ((yb + ry) * 2 + s) * 98 + dy * 14;
+#pragma unroll
+            for (int dx = 0; dx < D; ++dx) {
+                const float4 wa = wq[2 * dx], wb = wq[2 * dx + 1];
+                const float wr[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+#pragma unroll
+                for (int r = 0; r < 8; ++r) {
+                    acc[ry][r].x += wr[r] * xv[r + dx].x;
+                    acc[ry][r].y += wr[r] * xv[r + dx].y;
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int ry = 0; ry < RY; ++ry) {
+        const int gy = ty0 + yb + ry;
+        if (gy >= Gy) continue;
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int gx = tx0 + 8 * s + r;
+            if (gx < Gx) out[((int64_t)gy * Gx + gx) * CP + lane] = acc[ry][r];
+        }
+    }
+}
+
+// Row stage k rows -> image with the coil reduction of one coil block:
+// P[cb][row][i] = sum_{c in block cb} w conj(S_c) IFFT(src_c[row])[place(i)].
+template <int N2> __host__ __device__ constexpr int inv_buf() {
+    return N1 * ypitch<N2>() > N1 * N2 * 9 ? N1 * ypitch<N2>() : N1 * N2 * 9;
+}
+
+template <int N2>
+__global__ void __launch_bounds__(CB * tpr<N2>(), min_ctas<N2>())
+ci_rows_inv_kernel(const float2* __restrict__ tw, RowArgs a, const float2* __restrict__ src,
+                   const float2* __restrict__ S, const float* __restrict__ wrow,
+                   const float* __restrict__ wcol, float2* __restrict__ P) {
+    constexpr int n = N1 * N2, YP = ypitch<N2>();
+    __shared__ float2 tws[n];
+    __shared__ float2 Y[inv_buf<N2>()];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) tws[i] = tw[i];
+    __syncthreads();
+    const int j = threadIdx.x & (CB - 1), r = threadIdx.x / CB;
+    const int row = blockIdx.x, c = blockIdx.y * CB + j;
+    if (r < N2) {
+        float2 v[N1];
+        const float2* srow = src + (int64_t)row * n * CP + c;
+#pragma unroll
+        for (int m1 = 0; m1 < N1; ++m1) {
+            int sidx = N2 * m1 + r + a.off_in;
+            if (sidx >= n) sidx -= n;
+            v[m1] = srow[(int64_t)sidx * CP];
+        }
+        fft4_phase1<N1, N2, true>(v, r, tws);
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) Y[k1 * YP + r * CB + j] = v[k1];
+    }
+    __syncthreads();
+    float2 u[N2];
+    if (r < N1) {
+#pragma unroll
+        for (int m2 = 0; m2 < N2; ++m2) u[m2] = Y[r * YP + m2 * CB + j];
+        fft4_phase2<N1, N2, true>(u, tws);
+    }
+    __syncthreads();   // Y is reused below as R[i][9]
+    float2* R = Y;
+    if (r < N1) {
+        const float wr = a.scale * (wrow ? wrow[row] : 1.f);
+        const float2* srow = S + (int64_t)row * a.n * CP + c;
+#pragma unroll
+        for (int k2 = 0; k2 < N2; ++k2) {
+            int i = r + N1 * k2 + a.off_out;
+            if (i >= n) i -= n;
+            if (i < a.n)
+                R[i * 9 + j] = cmulc(srow[(int64_t)i * CP], cscale(u[k2], wcol ? wr * wcol[i] : wr));
+        }
+    }
+    __syncthreads();
+    float2* prow = P + ((int64_t)blockIdx.y * a.nrows + row) * a.n;
+    for (int i = threadIdx.x; i < a.n; i += blockDim.x) {
+        float2 acc = R[i * 9];
+#pragma unroll
+        for (int jj = 1; jj < CB; ++jj) acc = cadd(acc, R[i * 9 + jj]);
+        prow[i] = acc;
+    }
+}
+
+// out[o] = scale * sum_b P[b][o] + alpha * operand[o]
+__global__ void ci_sum_kernel(const float2* __restrict__ P, int64_t n, float scale,
+                              const float2* operand, float alpha, float2* out) {
+    for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < n;
+         o += (int64_t)gridDim.x * blockDim.x) {
+        float2 acc = P[o];
+#pragma unroll
+        for (int b = 1; b < NCB; ++b) acc = cadd(acc, P[b * n + o]);
+        acc = cscale(acc, scale);
+        if (operand) acc = cadd(acc, cscale(operand[o], alpha));
+        out[o] = acc;
+    }
+}
+
+static pp_status check_ci(const char* what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_status(e, what);
+    ++g_launches;
+    if (g_profiler) g_profiler->mark(what);
+    return PP_OK;
+}
+
+}  // namespace
+
+bool ci_supported(const Plan& p) {
+    return p.kind == PP_NONCARTESIAN && p.ndim == 2 && p.C <= CP && fft4_n2(p.G_x) &&
+           fft4_n2(p.G_y) && p.gtg8 != nullptr;
+}
+
+size_t ci_grid_elems(const Plan& p) { return (size_t)p.G_y * p.G_x * CP; }
+size_t ci_rows_elems(const Plan& p) { return (size_t)p.ny * p.G_x * CP; }
+size_t ci_sens_elems(const Plan& p) { return (size_t)p.ny * p.nx * CP; }
+size_t ci_partial_elems(const Plan& p) { return (size_t)NCB * p.ny * p.nx; }
+
+pp_status ci_prepare(Plan& p, cudaStream_t st) {
+    PP_TRY_CUDA(cudaFuncSetAttribute(ci_stencil_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)CiStencil<1>::SMEM));
+    PP_TRY_CUDA(cudaFuncSetAttribute(ci_stencil_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)CiStencil<2>::SMEM));
+    const int64_t n = (int64_t)p.ny * p.nx;
+    ci_pack_sens_kernel<<<152 * 4, 256, 0, st>>>(p.sens, p.C, n, p.ci_sens);
+    return check_ci("ci_pack_sens_kernel");
+}
+
+// out = scale * A^H A x + alpha * operand on the coil-innermost buffers
+pp_status ci_normal(const Plan& p, const float2* x, float2* out, float scale, const float2* operand,
+                    float alpha, int ry, cudaStream_t st) {
+    const int nx = p.nx, ny = p.ny, Gx = p.G_x, Gy = p.G_y;
+    const int n2x = fft4_n2(Gx), n2y = fft4_n2(Gy);
+    RowArgs rf{};
+    rf.n = nx; rf.G = Gx; rf.off_in = nx / 2; rf.off_out = 0; rf.nrows = ny; rf.scale = 1.f;
+#define PP_CIR(N2_)                                                                                \
+    if (n2x == N2_)                                                                                \
+        ci_rows_fwd_kernel<N2_><<<dim3(ny, NCB), CB * tpr<N2_>(), 0, st>>>(                        \
+            p.gx.tw, rf, x, p.ci_sens, p.deapod_y, p.deapod_x, p.ci_a);
+    PP_CIR(8) PP_CIR(12) PP_CIR(16) PP_CIR(20) PP_CIR(24)
+#undef PP_CIR
+    PP_TRY(check_ci("ci_rows_fwd_kernel"));
+#define PP_CIC(N2_, INV_, HIN, HOUT, OIN, OOUT, SRC, DST)                                          \
+    if (n2y == N2_)                                                                                \
+        ci_cols_kernel<N2_, INV_><<<dim3(Gx, NCB), CB * tpr<N2_>(), 0, st>>>(                      \
+            p.gy.tw, HIN, HOUT, OIN, OOUT, Gx, SRC, DST);
+    PP_CIC(8, false, ny, Gy, ny / 2, 0, p.ci_a, p.ci_b)
+    PP_CIC(12, false, ny, Gy, ny / 2, 0, p.ci_a, p.ci_b)
+    PP_CIC(16, false, ny, Gy, ny / 2, 0, p.ci_a, p.ci_b)
+    PP_CIC(20, false, ny, Gy, ny / 2, 0, p.ci_a, p.ci_b)
+    PP_CIC(24, false, ny, Gy, ny / 2, 0, p.ci_a, p.ci_b)
+    PP_TRY(check_ci("ci_cols_kernel"));
+    const int ntiles = ((Gx + 15) / 16) * ((Gy + 4 * ry - 1) / (4 * ry));
+    if (ry == 2)
+        ci_stencil_kernel<2><<<ntiles, 256, CiStencil<2>::SMEM, st>>>(p.gtg8, Gx, Gy, (Gx + 7) / 8,
+                                                                     p.ci_b, p.ci_c);
+    else
+        ci_stencil_kernel<1><<<ntiles, 256, CiStencil<1>::SMEM, st>>>(p.gtg8, Gx, Gy, (Gx + 7) / 8,
+                                                                     p.ci_b, p.ci_c);
+    PP_TRY(check_ci("ci_stencil_kernel"));
+    PP_CIC(8, true, Gy, ny, 0, ny / 2, p.ci_c, p.ci_a)
+    PP_CIC(12, true, Gy, ny, 0, ny / 2, p.ci_c, p.ci_a)
+    PP_CIC(16, true, Gy, ny, 0, ny / 2, p.ci_c, p.ci_a)
+    PP_CIC(20, true, Gy, ny, 0, ny / 2, p.ci_c, p.ci_a)
+    PP_CIC(24, true, Gy, ny, 0, ny / 2, p.ci_c, p.ci_a)
+#undef PP_CIC
+    PP_TRY(check_ci("ci_cols_kernel"));
+    RowArgs ra = rf;
+    ra.off_in = 0; ra.off_out = nx / 2;
+#define PP_CII(N2_)                                                                                \
+    if (n2x == N2_)                                                                                \
+        ci_rows_inv_kernel<N2_><<<dim3(ny, NCB), CB * tpr<N2_>(), 0, st>>>(                        \
+            p.gx.tw, ra, p.ci_a, p.ci_sens, p.deapod_y, p.deapod_x, p.ci_part);
+    PP_CII(8) PP_CII(12) PP_CII(16) PP_CII(20) PP_CII(24)
+#undef PP_CII
+    PP_TRY(check_ci("ci_rows_inv_kernel"));
+    const int64_t n = (int64_t)ny * nx;
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 8);
+    ci_sum_kernel<<<blocks, 256, 0, st>>>(p.ci_part, n, scale, operand, alpha, out);
+    return check_ci("ci_sum_kernel");
+}
+
+}  // namespace pp

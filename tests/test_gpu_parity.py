@@ -118,7 +118,7 @@ def test_every_stencil_kind_small_grids(pp, case):
         L = 2.5
         pp.pp_plan_set_scale(p.plan, L)
         ref = p.normal(x) / L
-        for kind in range(6):
+        for kind in range(7):
             for cpc in ((1, 3) if kind < 2 else (8,)):
                 pp.pp_plan_set_tuning(p.plan, 1, kind, cpc)
                 out = empty(shape)
@@ -126,6 +126,42 @@ def test_every_stencil_kind_small_grids(pp, case):
                 assert rel(host(out), ref) <= TOL_APPLY, (kind, cpc)
     finally:
         p.plan.destroy()
+
+
+CI_CASES = [((64, 64), 5, 2.0, dict(interleaves=4, samples=512)),
+            ((96, 128), 32, 2.0, dict(interleaves=4, samples=600, turns=3.0, kmax=47.9)),
+            ((64, 64), 17, 2.0, dict(interleaves=3, samples=400, turns=3.0, kmax=31.9))]
+
+
+@pytest.mark.parametrize("case", range(len(CI_CASES)), ids=["64_c5", "96x128_c32", "64_c17"])
+def test_coil_innermost_pipeline(pp, case):
+    # Oversampling 2 gives grids of register-FFT length (128, 192, 256); 32
+    # coils run on the aliased workspaces, fewer on padded copies.
+    shape, C, sigma, kw = CI_CASES[case]
+    sens = synth.coil_maps(shape, C, 400 + case)
+    traj = synth.spiral_traj(kw["interleaves"], kw["samples"], kw["turns"] if "turns" in kw else 4.0,
+                             kw.get("kmax", shape[0] / 2.0))
+    plan = pp.pp_plan_create(shape, C, dev(sens), traj=traj, oversamp=sigma, seed=1, power_iters=0)
+    try:
+        x = synth.crandn(shape, 6)
+        normal = lambda v: O.nc_normal(v, sens, traj, oversamp=sigma)
+        L = float(O.power_iteration(normal, shape, 9, iters=10))
+        pp.pp_plan_set_scale(plan, L)
+        ref = normal(x) / L
+        for kind in (7, 8, 2):
+            pp.pp_plan_set_tuning(plan, 1, kind, 8)
+            out = empty(shape)
+            pp.pp_normal_apply(plan, dev(x), out)
+            assert rel(host(out), ref) <= TOL_APPLY, kind
+        # axpy epilogue of the Horner recursion goes through the same path
+        pp.pp_plan_set_tuning(plan, 1, 7, 8)
+        c = [float(v) for v in O.poly_coeffs_l2(3)]
+        out = empty(shape)
+        pp.pp_poly_apply(plan, c, 3, dev(x), out)
+        ref = O.horner_apply(c, lambda v: normal(v) / L, x.astype(np.complex128))
+        assert rel(host(out), ref) <= TOL_APPLY
+    finally:
+        plan.destroy()
 
 
 def test_forward_parity(pp, prob):
@@ -297,7 +333,7 @@ def test_full_size_spiral_normal_apply(pp, full_spiral):
 
 @pytest.mark.parametrize("row_variant,kind,cpc", [
     (1, 0, 8), (2, 0, 4), (4, 0, 16), (-1, 0, 32), (-1, 0, 2), (1, 1, 8), (2, 1, 3),
-    (1, 2, 8), (-1, 3, 8), (2, 4, 8), (-1, 5, 8)])
+    (1, 2, 8), (-1, 3, 8), (2, 4, 8), (-1, 5, 8), (1, 6, 8), (-1, 6, 8), (1, 7, 8), (1, 8, 8)])
 def test_full_size_spiral_every_launch_variant(pp, full_spiral, row_variant, kind, cpc):
     plan, x, ref = full_spiral
     tuned = pp.pp_plan_tuning(plan)
