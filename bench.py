@@ -177,6 +177,11 @@ def kernel_flops(c, K):
         "gtg_stencil_rb_kernel": 4.0 * (2 * W - 1) ** 2 * C * G * G,
         "gtg_stencil_cl_kernel": 4.0 * (2 * W - 1) ** 2 * C * G * G,
         "coil_sum_kernel": 2.0 * C * n,
+        "ci_rows_fwd_kernel": C * ny * fft(G) + 8.0 * C * n,
+        "ci_cols_kernel": C * G * fft(G),
+        "ci_stencil_kernel": 4.0 * (2 * W - 1) ** 2 * C * G * G,
+        "ci_rows_inv_kernel": C * ny * fft(G) + 10.0 * C * n,
+        "ci_sum_kernel": 4.0 * 2.0 * n,
         "rows_adj_cb_kernel": C * ny * fft(G) + 10.0 * C * n,
         "rows_adj_kernel": C * ny * fft(G) + 10.0 * C * n,
         "rows4_fwd_kernel": C * ny * fft(G) + 8.0 * C * n,
@@ -357,7 +362,7 @@ def main():
     apply_ms = sum(stages.values())
     flops = kernel_flops(c, K)
     # cols_kernel runs twice per apply (forward and inverse): per-launch time is half
-    launches_per_apply = {"cols_kernel": 2, "cols4_kernel": 2}
+    launches_per_apply = {"cols_kernel": 2, "cols4_kernel": 2, "ci_cols_kernel": 2}
     per_launch_ms = {k: v / launches_per_apply.get(k, 1) for k, v in stages.items()}
     dom = max(stages, key=stages.get)
     sm_clock = clocks["sm_max_mhz"] or 2070.0

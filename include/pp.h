@@ -120,8 +120,10 @@ pp_status pp_plan_sizes(const pp_plan* plan, int64_t* image_elems, int64_t* kspa
  *    a persistent grid; 6 = coil-lane, the 32 lanes of a warp being 32
  *    coils of 8 adjacent outputs; 7, 8 = the whole normal operator on
  *    coil-innermost ([row][col][coil], 32-coil pitch) copies with a
- *    coil-lane stencil of 1 or 2 rows per warp, row_ifft_variant then
- *    unused (plans with at most 32 coils and register-FFT grid lengths);
+ *    coil-lane stencil of 1 or 2 rows per warp (plans with at most 32
+ *    coils and register-FFT grid lengths); there row_ifft_variant 4 sums
+ *    the four 8-coil blocks of a row in a thread-block cluster, any other
+ *    value through a partial-sum buffer;
  *    stencil_coils is ignored for kinds 2..8);
  *  - stencil_coils: 1..64.
  * pp_plan_set_tuning overrides them (results are identical up to rounding

@@ -523,18 +523,23 @@ static pp_status tune_noncartesian(Plan& p, cudaStream_t st) {
     // whole operator: the tuned [coil][row][col] pipeline against the
     // coil-innermost one (kinds 7, 8)
     if (p.ci_sens) {
-        const int base = p.tune_stencil_kind;
+        // (stencil kind, row variant): for kinds 7 and 8 the row variant 4
+        // reduces the four 8-coil blocks of a row in a thread-block cluster
+        std::vector<std::pair<int, int>> whole = {{p.tune_stencil_kind, p.tune_rows_adj_cl},
+                                                  {7, 1}, {7, 4}, {8, 1}, {8, 4}};
         PP_TRY_CUDA(cudaMemsetAsync(p.v, 0, sizeof(float2) * (size_t)p.nimg, st));
-        std::vector<int> whole = {base, 7, 8};
         std::vector<float> wbest(whole.size(), 1e30f);
         for (int round = 0; round < kRounds; ++round)
             for (size_t i = 0; i < whole.size(); ++i) {
-                p.tune_stencil_kind = whole[i];
+                p.tune_stencil_kind = whole[i].first;
+                p.tune_rows_adj_cl = whole[i].second;
                 float ms = 0.f;
                 PP_TRY(timeit([&]() { return normal_into(p, p.v, p.t, 1.f, nullptr, 0.f, st); }, &ms));
                 wbest[i] = std::min(wbest[i], ms);
             }
-        p.tune_stencil_kind = whole[std::min_element(wbest.begin(), wbest.end()) - wbest.begin()];
+        const size_t wi = std::min_element(wbest.begin(), wbest.end()) - wbest.begin();
+        p.tune_stencil_kind = whole[wi].first;
+        p.tune_rows_adj_cl = whole[wi].second;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

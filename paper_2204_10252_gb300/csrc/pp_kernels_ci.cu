@@ -12,8 +12,12 @@
 
 #include <algorithm>
 
+#include <cooperative_groups.h>
+
 #include "pp_fft4.cuh"
 #include "pp_internal.h"
+
+namespace cg = cooperative_groups;
 
 namespace pp {
 namespace {
@@ -204,10 +208,8 @@ ci_stencil_kernel(const float* __restrict__ T8, int Gx, int Gy, int nxb,
                 const float4 wa = wq[2 * dx], wb = wq[2 * dx + 1];
                 const float wr[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
 #pragma unroll
-                for (int r = 0; r < 8; ++r) {
-                    acc[ry][r].x += wr[r] * xv[r + dx].x;
-                    acc[ry][r].y += wr[r] * xv[r + dx].y;
-                }
+                for (int r = 0; r < 8; ++r)   // packed two-lane FP32 FMA (re, im)
+                    acc[ry][r] = __ffma2_rn(make_float2(wr[r], wr[r]), xv[r + dx], acc[ry][r]);
             }
         }
     }
@@ -229,18 +231,21 @@ template <int N2> __host__ __device__ constexpr int inv_buf() {
     return N1 * ypitch<N2>() > N1 * N2 * 9 ? N1 * ypitch<N2>() : N1 * N2 * 9;
 }
 
+// Body shared by both row-IFFT kernels: leaves R[i * 9 + j] = w conj(S_c)
+// IFFT(src_c[row])[place(i)] for the CTA's 8 coils c = cb * 8 + j, and
+// R[i * 9 + 8] = their sum (i < a.n); ends with a barrier.
 template <int N2>
-__global__ void __launch_bounds__(CB * tpr<N2>(), min_ctas<N2>())
-ci_rows_inv_kernel(const float2* __restrict__ tw, RowArgs a, const float2* __restrict__ src,
-                   const float2* __restrict__ S, const float* __restrict__ wrow,
-                   const float* __restrict__ wcol, float2* __restrict__ P) {
+__device__ __forceinline__ void ci_rows_inv_body(const float2* __restrict__ tw, const RowArgs& a,
+                                                 const float2* __restrict__ src,
+                                                 const float2* __restrict__ S,
+                                                 const float* __restrict__ wrow,
+                                                 const float* __restrict__ wcol, int row, int cb,
+                                                 float2* tws, float2* Y) {
     constexpr int n = N1 * N2, YP = ypitch<N2>();
-    __shared__ float2 tws[n];
-    __shared__ float2 Y[inv_buf<N2>()];
     for (int i = threadIdx.x; i < n; i += blockDim.x) tws[i] = tw[i];
     __syncthreads();
     const int j = threadIdx.x & (CB - 1), r = threadIdx.x / CB;
-    const int row = blockIdx.x, c = blockIdx.y * CB + j;
+    const int c = cb * CB + j;
     if (r < N2) {
         float2 v[N1];
         const float2* srow = src + (int64_t)row * n * CP + c;
@@ -275,13 +280,60 @@ ci_rows_inv_kernel(const float2* __restrict__ tw, RowArgs a, const float2* __res
         }
     }
     __syncthreads();
-    float2* prow = P + ((int64_t)blockIdx.y * a.nrows + row) * a.n;
     for (int i = threadIdx.x; i < a.n; i += blockDim.x) {
         float2 acc = R[i * 9];
 #pragma unroll
         for (int jj = 1; jj < CB; ++jj) acc = cadd(acc, R[i * 9 + jj]);
-        prow[i] = acc;
+        R[i * 9 + 8] = acc;
     }
+    __syncthreads();
+}
+
+// Row stage k rows -> image, one coil block per CTA:
+// P[cb][row][i] = sum_{c in block cb} w conj(S_c) IFFT(src_c[row])[place(i)].
+// grid (nrows, NCB).
+template <int N2>
+__global__ void __launch_bounds__(CB * tpr<N2>(), min_ctas<N2>())
+ci_rows_inv_kernel(const float2* __restrict__ tw, RowArgs a, const float2* __restrict__ src,
+                   const float2* __restrict__ S, const float* __restrict__ wrow,
+                   const float* __restrict__ wcol, float2* __restrict__ P) {
+    __shared__ float2 tws[N1 * N2];
+    __shared__ float2 Y[inv_buf<N2>()];
+    const int row = blockIdx.x, cb = blockIdx.y;
+    ci_rows_inv_body<N2>(tw, a, src, S, wrow, wcol, row, cb, tws, Y);
+    float2* prow = P + ((int64_t)cb * a.nrows + row) * a.n;
+    for (int i = threadIdx.x; i < a.n; i += blockDim.x) prow[i] = Y[i * 9 + 8];
+}
+
+// The same with the NCB coil blocks of a row in one thread-block cluster:
+// CTA q of the cluster sums the four blocks' partials for its quarter of the
+// row through distributed shared memory (fixed order) and writes
+// out = scale * sum + alpha * operand.  grid (NCB, nrows), cluster (NCB, 1, 1).
+template <int N2>
+__global__ void __launch_bounds__(CB * tpr<N2>(), min_ctas<N2>())
+ci_rows_inv_cl_kernel(const float2* __restrict__ tw, RowArgs a, const float2* __restrict__ src,
+                      const float2* __restrict__ S, const float* __restrict__ wrow,
+                      const float* __restrict__ wcol, float2* out, float scale,
+                      const float2* operand, float alpha) {
+    __shared__ float2 tws[N1 * N2];
+    __shared__ float2 Y[inv_buf<N2>()];
+    cg::cluster_group cluster = cg::this_cluster();
+    const int q = (int)cluster.block_rank();
+    const int row = blockIdx.y;
+    ci_rows_inv_body<N2>(tw, a, src, S, wrow, wcol, row, q, tws, Y);
+    cluster.sync();
+    const int chunk = (a.n + NCB - 1) / NCB;
+    const int i0 = q * chunk, i1 = min(a.n, i0 + chunk);
+    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+        float2 v = cluster.map_shared_rank(Y, 0)[i * 9 + 8];
+#pragma unroll
+        for (int b = 1; b < NCB; ++b) v = cadd(v, cluster.map_shared_rank(Y, b)[i * 9 + 8]);
+        v = cscale(v, scale);
+        const int64_t o = (int64_t)row * a.n + i;
+        if (operand) v = cadd(v, cscale(operand[o], alpha));
+        out[o] = v;
+    }
+    cluster.sync();   // keep every CTA's partials alive until the others have read them
 }
 
 // out[o] = scale * sum_b P[b][o] + alpha * operand[o]
@@ -369,6 +421,32 @@ pp_status ci_normal(const Plan& p, const float2* x, float2* out, float scale, co
     PP_TRY(check_ci("ci_cols_kernel"));
     RowArgs ra = rf;
     ra.off_in = 0; ra.off_out = nx / 2;
+    if (p.tune_rows_adj_cl == 4) {
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = NCB;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(NCB, ny);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = st;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        cudaError_t e = cudaSuccess;
+#define PP_CIL(N2_)                                                                          \
+        if (n2x == N2_) {                                                                    \
+            cfg.blockDim = dim3(CB * tpr<N2_>());                                            \
+            e = cudaLaunchKernelEx(&cfg, ci_rows_inv_cl_kernel<N2_>, (const float2*)p.gx.tw, \
+                                   ra, (const float2*)p.ci_a, (const float2*)p.ci_sens,      \
+                                   (const float*)p.deapod_y, (const float*)p.deapod_x, out,  \
+                                   scale, operand, alpha);                                   \
+        }
+        PP_CIL(8) PP_CIL(12) PP_CIL(16) PP_CIL(20) PP_CIL(24)
+#undef PP_CIL
+        if (e != cudaSuccess) return cuda_status(e, "ci_rows_inv_cl_kernel launch");
+        return check_ci("ci_rows_inv_cl_kernel");
+    }
 #define PP_CII(N2_)                                                                                \
     if (n2x == N2_)                                                                                \
         ci_rows_inv_kernel<N2_><<<dim3(ny, NCB), CB * tpr<N2_>(), 0, st>>>(                        \
