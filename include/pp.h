@@ -88,8 +88,9 @@ typedef struct pp_plan pp_plan;
  *          prime factor above 5 and be even; nx and ny (and nz) must be
  *          multiples of 4 (the 2-level Haar tile).  Else PP_ERR_UNSUPPORTED.
  *   coils  1..64.
- *   sens   device [C][nz][ny][nx] complex64, BORROWED: it must stay valid and
- *          unchanged until pp_plan_destroy.
+ *   sens   device [C][nz][ny][nx] complex64, 16-byte aligned (else
+ *          PP_ERR_INVALID_ARG), BORROWED: it must stay valid and unchanged
+ *          until pp_plan_destroy.
  *   s      sampling pattern, see pp_sampling.
  * Synchronises `stream` once (to read L).  On failure *out is NULL. */
 pp_status pp_plan_create(pp_plan** out, pp_dims dims, int coils, const pp_c64* sens,
@@ -230,8 +231,8 @@ pp_status pp_fista_solve(pp_plan* plan, const pp_c64* b, float lambda, int iters
 /* ---- Batches of independent 2-D Cartesian problems of uneven size ----
  * Slice s is its own problem (Sec. 5.1 operator, its own L_s, its own ||b_s||)
  * of size dims[s] (2-D, axes multiples of 4, FFT lengths with prime factors
- * <= 5, at most 512), coils[s] coils (1..64), borrowed device maps sens[s]
- * [C_s][ny_s][nx_s] and a host line mask masks[s] [ny_s][nx_s] constant along
+ * <= 5, at most 512), coils[s] coils (1..64), borrowed 16-byte aligned device maps
+ * sens[s] [C_s][ny_s][nx_s] and a host line mask masks[s] [ny_s][nx_s] constant along
  * x.  Images, k-space and solutions are concatenated in slice order; the
  * offsets come from pp_batch_offsets.  Every stage of an iteration is one
  * persistent kernel launch over a work list of (slice, column tile) items,

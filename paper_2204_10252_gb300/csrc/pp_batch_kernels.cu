@@ -402,6 +402,8 @@ cart2d_batch4_kernel(const SliceDesc* __restrict__ descs, const int2* __restrict
     __shared__ float2 tws[384];
     __shared__ float pm[384];
     __shared__ float2 Y[16 * 24 * 8];
+    extern __shared__ float4 sb4[];   // double-buffered coil-map tiles, 2 * 384 * 8 float2
+    float2* Sb = reinterpret_cast<float2*>(sb4);
     int cur = -1;
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         const int2 item = items[it];
@@ -421,11 +423,11 @@ cart2d_batch4_kernel(const SliceDesc* __restrict__ descs, const int2* __restrict
         const float2* ops = operand ? operand + D.img_off : nullptr;
         const float sc = coef * D.invL;
         switch (D.n2) {
-            case 8: cart_item4<8>(tws, pm, Y, xs, D.sens, D.C, D.nx, item.y, os, sc, ops, alpha); break;
-            case 12: cart_item4<12>(tws, pm, Y, xs, D.sens, D.C, D.nx, item.y, os, sc, ops, alpha); break;
-            case 16: cart_item4<16>(tws, pm, Y, xs, D.sens, D.C, D.nx, item.y, os, sc, ops, alpha); break;
-            case 20: cart_item4<20>(tws, pm, Y, xs, D.sens, D.C, D.nx, item.y, os, sc, ops, alpha); break;
-            default: cart_item4<24>(tws, pm, Y, xs, D.sens, D.C, D.nx, item.y, os, sc, ops, alpha); break;
+            case 8: cart_item4<8>(tws, pm, Y, Sb, xs, D.sens, D.C, D.nx, item.y, os, sc, ops, alpha); break;
+            case 12: cart_item4<12>(tws, pm, Y, Sb, xs, D.sens, D.C, D.nx, item.y, os, sc, ops, alpha); break;
+            case 16: cart_item4<16>(tws, pm, Y, Sb, xs, D.sens, D.C, D.nx, item.y, os, sc, ops, alpha); break;
+            case 20: cart_item4<20>(tws, pm, Y, Sb, xs, D.sens, D.C, D.nx, item.y, os, sc, ops, alpha); break;
+            default: cart_item4<24>(tws, pm, Y, Sb, xs, D.sens, D.C, D.nx, item.y, os, sc, ops, alpha); break;
         }
     }
 }
@@ -473,9 +475,14 @@ pp_status configure_batch_kernels() {
     return PP_OK;
 }
 
+constexpr size_t kBatch4Dyn = sizeof(float2) * 2 * 384 * 8;
+
 int batch4_grid() {
     int occ = 0, nsm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, cart2d_batch4_kernel, 192, 0) != cudaSuccess)
+    cudaFuncSetAttribute(cart2d_batch4_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kBatch4Dyn);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, cart2d_batch4_kernel, 192, kBatch4Dyn) !=
+        cudaSuccess)
         occ = 1;
     if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, 0) != cudaSuccess) nsm = 152;
     return std::max(1, occ) * nsm;
@@ -484,8 +491,8 @@ int batch4_grid() {
 pp_status launch_batch_normal(const BatchDev& b, const float2* x, float2* out, float coef,
                               const float2* operand, float alpha, cudaStream_t st) {
     if (b.fast4) {
-        cart2d_batch4_kernel<<<std::min(b.grid, b.nitems), 192, 0, st>>>(b.descs, b.items, b.nitems, x,
-                                                                        out, coef, operand, alpha);
+        cart2d_batch4_kernel<<<std::min(b.grid, b.nitems), 192, kBatch4Dyn, st>>>(
+            b.descs, b.items, b.nitems, x, out, coef, operand, alpha);
         return check_launch_b("cart2d_batch4_kernel");
     }
     void* fn = batch_normal_fn(b.km, b.lgt);

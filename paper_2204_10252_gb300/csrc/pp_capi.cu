@@ -1095,6 +1095,10 @@ pp_status pp_plan_create(pp_plan** out, pp_dims dims, int coils, const pp_c64* s
         set_error("pp_plan_create: sens and sampling must be non-NULL");
         return PP_ERR_INVALID_ARG;
     }
+    if ((uintptr_t)sens & 15) {
+        set_error("pp_plan_create: sens must be 16-byte aligned");
+        return PP_ERR_INVALID_ARG;
+    }
     if (dims.ndim != 2 && dims.ndim != 3) {
         set_error("pp_plan_create: ndim must be 2 or 3");
         return PP_ERR_UNSUPPORTED;
@@ -1152,6 +1156,7 @@ pp_status pp_plan_create(pp_plan** out, pp_dims dims, int coils, const pp_c64* s
     cudaGetDevice(&p.dev);
     cudaStream_t st = (cudaStream_t)stream;
     pp_status rc = (s->kind == PP_CARTESIAN) ? build_cartesian(p, s->mask) : build_noncartesian(p, s);
+    if (rc == PP_OK && s->kind == PP_CARTESIAN && p.ndim == 2) rc = prepare_cart4();
     if (rc == PP_OK) {
         const size_t n = (size_t)p.nimg;
         p.red_blocks = 2 * 152;
@@ -1495,7 +1500,7 @@ pp_status pp_batch_create(pp_batch** out, int nslices, const pp_dims* dims, cons
         }
         const int nx = d.n[0], ny = d.n[1];
         if (nx < 4 || ny < 4 || nx > 512 || ny > 512 || (nx % 4) || (ny % 4) || coils[s] < 1 ||
-            coils[s] > 64 || !sens[s] || !masks[s]) {
+            coils[s] > 64 || !sens[s] || ((uintptr_t)sens[s] & 15) || !masks[s]) {
             set_error("pp_batch_create: slice %d has a bad size, coil count or pointer", s);
             return PP_ERR_INVALID_ARG;
         }

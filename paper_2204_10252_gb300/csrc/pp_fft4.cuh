@@ -131,6 +131,29 @@ __device__ __forceinline__ void fft4_phase2(float2* u, const float2* __restrict_
 
 namespace pp {
 
+// 16-byte asynchronous global -> shared copy, zero-filled when !valid.
+__device__ __forceinline__ void cpa16(void* smem, const void* gmem, bool valid) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem),
+                 "r"(valid ? 16 : 0)
+                 : "memory");
+}
+
+// Stage the n x 8 tile S[0..n)[col0 .. col0+8) of one coil map (row pitch
+// nx, nx even) into dst[row * 8 + j] with cp.async and commit it as one group;
+// columns at or past nx read as zero.
+template <int N2>
+__device__ __forceinline__ void stage_s_tile(float2* dst, const float2* __restrict__ S, int nx,
+                                             int col0) {
+    constexpr int n = 16 * N2;
+    for (int e = threadIdx.x; e < n * 4; e += blockDim.x) {
+        const int row = e >> 2, q = e & 3, c = col0 + 2 * q;
+        const bool ok = c < nx;
+        cpa16(dst + row * 8 + 2 * q, S + (ok ? (int64_t)row * nx + c : 0), ok);
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
 // Fused Cartesian normal-operator work item on the four-step FFT:
 //   out[:, col] = sc * sum_c conj(S_c) F^H (mask_fo . F (S_c x)) + alpha * operand
 // for TXF = 8 columns col0.. of an ny x nx image, ny = 16 * N2, transform
@@ -140,11 +163,14 @@ namespace pp {
 //   I1 (same (k1, col) threads): inverse length-N2 DFT over k2, times
 //      W_n^(-m2 k1);   I2 ((m2, col) threads): inverse length-16 DFT over k1,
 // which leaves x'[N2 m1 + m2] with the thread that loaded S_c at those rows.
+// The coil maps' n x 8 tiles are double-buffered in shared memory: coil
+// c + 1's tile streams in by cp.async while coil c is transformed.
 // Shared memory: tws[n] twiddles, pm[n] mask (FFT order, 1/ny folded in),
-// Y[16 * N2 * 8].  Threads: 8 * max(16, N2); all threads must call it.
+// Y[16 * N2 * 8], Sb[2 * n * 8].  Threads: 8 * max(16, N2); all threads
+// must call it.
 template <int N2>
 __device__ __forceinline__ void cart_item4(const float2* __restrict__ tws,
-                                           const float* __restrict__ pm, float2* Y,
+                                           const float* __restrict__ pm, float2* Y, float2* Sb,
                                            const float2* __restrict__ x,
                                            const float2* __restrict__ sens, int C, int nx,
                                            int col0, float2* out, float sc,
@@ -155,20 +181,25 @@ __device__ __forceinline__ void cart_item4(const float2* __restrict__ tws,
     const bool p1 = r < N2, p2 = r < N1;
     const int64_t cs = (int64_t)n * nx;
     float2 xr[N1], acc[N1];
+    stage_s_tile<N2>(Sb, sens, nx, col0);
 #pragma unroll
     for (int m1 = 0; m1 < N1; ++m1) {
         xr[m1] = (p1 && colok) ? x[(int64_t)(N2 * m1 + r) * nx + col] : make_float2(0.f, 0.f);
         acc[m1] = make_float2(0.f, 0.f);
     }
     for (int c = 0; c < C; ++c) {
-        const float2* S = sens + c * cs;
+        const float2* St = Sb + (c & 1) * n * 8;
+        // the other buffer was last read in coil c - 1, before its final barrier
+        if (c + 1 < C)
+            stage_s_tile<N2>(Sb + ((c + 1) & 1) * n * 8, sens + (c + 1) * cs, nx, col0);
+        else
+            asm volatile("cp.async.commit_group;\n" ::: "memory");
+        asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+        __syncthreads();
         if (p1) {
             float2 v[N1];
 #pragma unroll
-            for (int m1 = 0; m1 < N1; ++m1) {
-                const float2 s = colok ? S[(int64_t)(N2 * m1 + r) * nx + col] : make_float2(0.f, 0.f);
-                v[m1] = cmul(s, xr[m1]);
-            }
+            for (int m1 = 0; m1 < N1; ++m1) v[m1] = cmul(St[(N2 * m1 + r) * 8 + lane], xr[m1]);
             fft4_phase1<N1, N2, false>(v, r, tws);
 #pragma unroll
             for (int k1 = 0; k1 < N1; ++k1) Y[(k1 * N2 + r) * 8 + lane] = v[k1];
@@ -198,10 +229,8 @@ __device__ __forceinline__ void cart_item4(const float2* __restrict__ tws,
             for (int k1 = 0; k1 < N1; ++k1) v[k1] = Y[(k1 * N2 + r) * 8 + lane];
             RegFft<N1, true>::run(v, tws, N2);
 #pragma unroll
-            for (int m1 = 0; m1 < N1; ++m1) {
-                const float2 s = colok ? S[(int64_t)(N2 * m1 + r) * nx + col] : make_float2(0.f, 0.f);
-                acc[m1] = cadd(acc[m1], cmulc(s, v[m1]));
-            }
+            for (int m1 = 0; m1 < N1; ++m1)
+                acc[m1] = cadd(acc[m1], cmulc(St[(N2 * m1 + r) * 8 + lane], v[m1]));
         }
         __syncthreads();
     }

@@ -26,6 +26,11 @@ template <int N2> __host__ __device__ constexpr int tpr() { return N2 > N1 ? N2 
 // registers, so that 7 CTAs of 160 threads fit an SM and the 1024 CTAs of a
 // 256-row, 32-coil stage run in one wave on 152 SMs.
 template <int N2> __host__ __device__ constexpr int row_min_ctas() { return N2 == 20 ? 7 : 1; }
+// Minimum resident CTAs of the 3-D z pass (TX columns per CTA): at most 80
+// registers per thread.
+template <int N2, int TX> __host__ __device__ constexpr int c3_min_ctas() {
+    return 65536 / (TX * tpr<N2>() * 80);
+}
 
 // Column stage: TXF adjacent columns of one batch, transform along rows.
 template <int N2, bool INV>
@@ -395,7 +400,8 @@ coil_sum_kernel(const float2* __restrict__ contrib, int C, int64_t n, float scal
     }
 }
 
-// Fused 2-D Cartesian normal operator (one CTA per 8 columns, all coils).
+// Fused 2-D Cartesian normal operator (one CTA per 8 columns, all coils);
+// dynamic shared memory: the double-buffered coil-map tiles, 2 * n * 8 float2.
 template <int N2>
 __global__ void __launch_bounds__(8 * tpr<N2>(), 2)
 cart2d4_normal_kernel(const float2* __restrict__ tw, const float2* __restrict__ x,
@@ -406,13 +412,17 @@ cart2d4_normal_kernel(const float2* __restrict__ tw, const float2* __restrict__ 
     __shared__ float2 tws[n];
     __shared__ float pm[n];
     __shared__ float2 Y[N1 * N2 * 8];
+    extern __shared__ float4 sb4[];
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         tws[i] = tw[i];
         pm[i] = mask_fo[i];
     }
     __syncthreads();
-    cart_item4<N2>(tws, pm, Y, x, sens, C, nx, blockIdx.x * 8, out, scale, operand, alpha);
+    cart_item4<N2>(tws, pm, Y, reinterpret_cast<float2*>(sb4), x, sens, C, nx, blockIdx.x * 8, out,
+                   scale, operand, alpha);
 }
+
+template <int N2> constexpr size_t cart4_dyn_smem() { return sizeof(float2) * 2 * 16 * N2 * 8; }
 
 // ---------------------------------------------------------------------------
 // 3-D Cartesian normal operator, x-block by x-block and coil by coil, with
@@ -459,7 +469,7 @@ c3_ypass_fwd_kernel(const float2* __restrict__ tw, const float2* __restrict__ x,
 }
 
 template <int N2, int TX>
-__global__ void __launch_bounds__(TX * tpr<N2>())
+__global__ void __launch_bounds__(TX * tpr<N2>(), c3_min_ctas<N2, TX>())
 c3_zpass_kernel(const float2* __restrict__ tw, float2* W, const float* __restrict__ mask_fo,
                 int ny, int nx, int x0) {
     constexpr int n = N1 * N2;   // nz
@@ -645,25 +655,32 @@ pp_status launch_rows4_adj(const DevFft& f, const RowArgs& a, const float2* src,
     return check4("rows4_adj_kernel");
 }
 
+pp_status prepare_cart4() {
+#define PP_P4(N2_)                                                                                \
+    PP_TRY_CUDA(cudaFuncSetAttribute(cart2d4_normal_kernel<N2_>,                                  \
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize,               \
+                                     (int)cart4_dyn_smem<N2_>()));
+    PP_P4(8) PP_P4(12) PP_P4(16) PP_P4(20) PP_P4(24)
+#undef PP_P4
+    return PP_OK;
+}
+
 pp_status launch_cart2d4_normal(const Plan& p, const float2* x, float2* out, float scale,
                                 const float2* operand, float alpha, cudaStream_t st, bool* done) {
     *done = false;
     const int n2 = fft4_n2(p.ny);
     if (!n2) return PP_OK;
     const int grid = (p.nx + 7) / 8;
-#define PP_K4(N2_)                                                                              \
-    if (n2 == N2_)                                                                              \
-        cart2d4_normal_kernel<N2_><<<grid, 8 * tpr<N2_>(), 0, st>>>(p.fy.tw, x, p.sens, p.C, p.nx, \
-                                                                    p.mask_fo, out, scale,        \
-                                                                    operand, alpha);
+#define PP_K4(N2_)                                                                                 \
+    if (n2 == N2_)                                                                                 \
+        cart2d4_normal_kernel<N2_><<<grid, 8 * tpr<N2_>(), cart4_dyn_smem<N2_>(), st>>>(           \
+            p.fy.tw, x, p.sens, p.C, p.nx, p.mask_fo, out, scale, operand, alpha);
     PP_K4(8) PP_K4(12) PP_K4(16) PP_K4(20) PP_K4(24)
 #undef PP_K4
     *done = true;
     return check4("cart2d4_normal_kernel");
 }
 
-// Launch helpers for the 3-D passes: 16 columns per CTA only where the
-// shared tile stays within the 48 KiB static limit (N2 <= 16).
 template <int N2>
 static void c3_yf(int tx, dim3 g, cudaStream_t st, const float2* tw, const float2* x, const float2* S,
                   float2* W, int nx, int x0) {
