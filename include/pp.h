@@ -110,10 +110,13 @@ pp_status pp_plan_set_scale(pp_plan* plan, double L);
  * ([C][...] as above); either pointer may be NULL. */
 pp_status pp_plan_sizes(const pp_plan* plan, int64_t* image_elems, int64_t* kspace_elems);
 
-/* Launch shapes the plan chose by timing at creation (non-Cartesian plans):
- *  - row_ifft_variant: the row-IFFT stage of the normal operator (1, 2 or
- *    4 = CTAs per image row, coil groups reduced through distributed shared
- *    memory; -1 = one IFFT per coil and row followed by a coil sum);
+/* Launch shapes the plan chose by timing at creation:
+ *  - row_ifft_variant: for non-Cartesian plans the row-IFFT stage of the
+ *    normal operator (1, 2 or 4 = CTAs per image row, coil groups reduced
+ *    through distributed shared memory; -1 = one IFFT per coil and row
+ *    followed by a coil sum); for 3-D Cartesian plans 16 = the whole normal
+ *    operator as one kernel on 16-CTA clusters (nz = 128, ny in {128, 192,
+ *    256}), 1 = three passes per coil;
  *  - stencil_kind: the G^T G stencil kernel (0 = one output per thread,
  *    1 = two outputs per thread, both staging one coil at a time with
  *    stencil_coils coils per CTA; 2..5 = register-blocked, a thread holding

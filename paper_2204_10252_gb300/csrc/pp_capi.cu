@@ -160,6 +160,7 @@ static pp_status normal_into(const Plan& p, const float2* x, float2* out, float 
     if (p.kind == PP_CARTESIAN && p.ndim == 2)
         return launch_cart2d_normal(p, x, out, scale, operand, alpha, st);
     if (p.kind == PP_CARTESIAN) {
+        if (p.tune_c3 && p.c3cl_clusters > 0) return c3cl_normal(p, x, out, scale, operand, alpha, st);
         bool done = false;
         PP_TRY(cart3d4_normal(p, x, out, scale, operand, alpha, p.wk_a, st, &done));
         if (done) return PP_OK;
@@ -541,6 +542,34 @@ static pp_status tune_noncartesian(Plan& p, cudaStream_t st) {
         p.tune_stencil_kind = whole[wi].first;
         p.tune_rows_adj_cl = whole[wi].second;
     }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return PP_OK;
+}
+
+// 3-D Cartesian: the one-kernel cluster operator against the three passes
+// per coil, timed on the plan's buffers (two rounds of 3 applies after one
+// warm-up); the faster is kept.
+static pp_status tune_cart3d(Plan& p, cudaStream_t st) {
+    if (p.c3cl_clusters <= 0) return PP_OK;
+    cudaEvent_t e0, e1;
+    PP_TRY_CUDA(cudaEventCreate(&e0));
+    PP_TRY_CUDA(cudaEventCreate(&e1));
+    PP_TRY_CUDA(cudaMemsetAsync(p.v, 0, sizeof(float2) * (size_t)p.nimg, st));
+    float best[2] = {1e30f, 1e30f};
+    for (int round = 0; round < 2; ++round)
+        for (int cand = 0; cand < 2; ++cand) {
+            p.tune_c3 = cand;
+            PP_TRY(normal_into(p, p.v, p.t, 1.f, nullptr, 0.f, st));
+            PP_TRY_CUDA(cudaEventRecord(e0, st));
+            for (int r = 0; r < 3; ++r) PP_TRY(normal_into(p, p.v, p.t, 1.f, nullptr, 0.f, st));
+            PP_TRY_CUDA(cudaEventRecord(e1, st));
+            PP_TRY_CUDA(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            PP_TRY_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            best[cand] = std::min(best[cand], ms);
+        }
+    p.tune_c3 = best[1] < best[0] ? 1 : 0;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return PP_OK;
@@ -1170,6 +1199,10 @@ pp_status pp_plan_create(pp_plan** out, pp_dims dims, int coils, const pp_c64* s
             if (e != cudaSuccess) rc = cuda_status(e, "cudaStreamCreate");
         }
     }
+    if (rc == PP_OK && p.kind == PP_CARTESIAN && p.ndim == 3) {
+        p.c3cl_clusters = c3cl_prepare(p);
+        rc = tune_cart3d(p, st);
+    }
     if (rc == PP_OK && p.kind == PP_NONCARTESIAN) rc = setup_ci(p, st);
     if (rc == PP_OK && p.kind == PP_NONCARTESIAN) rc = tune_noncartesian(p, st);
     if (rc == PP_OK && power_iters > 0) rc = power_iteration(p, seed, power_iters, st);
@@ -1221,7 +1254,13 @@ pp_status pp_plan_tuning(const pp_plan* plan, int* row_ifft_variant, int* stenci
         set_error("pp_plan_tuning: NULL plan");
         return PP_ERR_INVALID_ARG;
     }
-    if (row_ifft_variant) *row_ifft_variant = plan->impl.tune_rows_adj_cl ? plan->impl.tune_rows_adj_cl : 1;
+    if (row_ifft_variant) {
+        const Plan& p = plan->impl;
+        if (p.kind == PP_CARTESIAN && p.ndim == 3)
+            *row_ifft_variant = p.tune_c3 ? 16 : 1;
+        else
+            *row_ifft_variant = p.tune_rows_adj_cl ? p.tune_rows_adj_cl : 1;
+    }
     if (stencil_kind) *stencil_kind = plan->impl.tune_stencil_kind;
     if (stencil_coils) *stencil_coils = plan->impl.tune_stencil_cpc ? plan->impl.tune_stencil_cpc : 8;
     return PP_OK;
@@ -1229,13 +1268,19 @@ pp_status pp_plan_tuning(const pp_plan* plan, int* row_ifft_variant, int* stenci
 
 pp_status pp_plan_set_tuning(pp_plan* plan, int row_ifft_variant, int stencil_kind, int stencil_coils) {
     if (!plan || !(row_ifft_variant == 1 || row_ifft_variant == 2 || row_ifft_variant == 4 ||
-                   row_ifft_variant == -1) ||
+                   row_ifft_variant == -1 || row_ifft_variant == 16) ||
         stencil_kind < 0 || stencil_kind > 8 || stencil_coils < 1 || stencil_coils > 64) {
-        set_error("pp_plan_set_tuning: row variant must be 1, 2, 4 or -1; stencil kind 0..8; "
+        set_error("pp_plan_set_tuning: row variant must be 1, 2, 4, -1 or 16; stencil kind 0..8; "
                   "stencil coils 1..64");
         return PP_ERR_INVALID_ARG;
     }
     Plan& p = plan->impl;
+    if (row_ifft_variant == 16 && p.c3cl_clusters <= 0) {
+        set_error("pp_plan_set_tuning: the one-kernel cluster operator needs a 3-D Cartesian plan "
+                  "with nz = 128, ny in {128, 192, 256} and a device that fits 16-CTA clusters");
+        return PP_ERR_UNSUPPORTED;
+    }
+    if (p.kind == PP_CARTESIAN && p.ndim == 3) p.tune_c3 = row_ifft_variant == 16;
     if (row_ifft_variant == -1 && (p.kind != PP_NONCARTESIAN || !fft4_n2(p.G_x))) {
         set_error("pp_plan_set_tuning: the split row IFFT needs a non-Cartesian plan with a "
                   "register-FFT grid length");

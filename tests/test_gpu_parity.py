@@ -164,6 +164,44 @@ def test_coil_innermost_pipeline(pp, case):
         plan.destroy()
 
 
+C3_CASES = [((128, 128, 8), 3), ((128, 256, 12), 2), ((128, 192, 20), 5)]
+
+
+@pytest.mark.parametrize("case", range(len(C3_CASES)), ids=["128x128x8_c3", "128x256x12_c2",
+                                                           "128x192x20_c5"])
+def test_cart3d_cluster_operator(pp, case):
+    # nz = 128 and ny in {128, 192, 256}: the one-kernel cluster operator
+    # (row variant 16) against the three-pass one (1), both against the oracle
+    shape, C = C3_CASES[case]
+    sens = synth.coil_maps(shape, C, 500 + case)
+    mask = synth.poisson_disc_mask(shape, 4, 8, 500 + case)
+    plan = pp.pp_plan_create(shape, C, dev(sens), mask=mask, seed=2, power_iters=0)
+    try:
+        x = synth.crandn(shape, 7)
+        op = synth.crandn(shape, 8)
+        L = 1.7
+        pp.pp_plan_set_scale(plan, L)
+        ref = O.cart_normal(x, sens, mask) / L
+        for rv in (16, 1):
+            try:
+                pp.pp_plan_set_tuning(plan, rv, 0, 8)
+            except pp.PPError:
+                assert rv == 16
+                pytest.skip("no 16-CTA cluster fits this device")
+            out = empty(shape)
+            pp.pp_normal_apply(plan, dev(x), out)
+            assert rel(host(out), ref) <= TOL_APPLY, rv
+        # the Horner axpy epilogue (operand, alpha) through the cluster kernel
+        pp.pp_plan_set_tuning(plan, 16, 0, 8)
+        c = [float(v) for v in O.poly_coeffs_l2(2)]
+        out = empty(shape)
+        pp.pp_poly_apply(plan, c, 2, dev(op), out)
+        refp = O.horner_apply(c, lambda v: O.cart_normal(v, sens, mask) / L, op.astype(np.complex128))
+        assert rel(host(out), refp) <= TOL_APPLY
+    finally:
+        plan.destroy()
+
+
 def test_forward_parity(pp, prob):
     x = synth.crandn(prob.shape, 1)
     y = empty(prob.kshape)
