@@ -27,6 +27,47 @@ pp_status cuda_status(cudaError_t e, const char* what);
 
 constexpr int kThreads = 256;
 
+// Programmatic dependent launch.  A kernel launched with
+// launch_ex(..., pdl = true) may be scheduled while its predecessor in the
+// stream is still running; it runs its independent prologue (plan constants
+// only), then pdl_wait() blocks until the predecessor has completed and its
+// writes are visible, before any access to data that other kernels write.
+// pdl_trigger() lets this grid's own successor be scheduled.  Both are no-ops
+// for kernels launched without the attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+
+// cudaLaunchKernelEx with optional programmatic stream serialization and an
+// optional 1-D cluster of `cluster_x` CTAs (0: none).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_ex(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                      cudaStream_t st, bool pdl, int cluster_x, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[2];
+    int na = 0;
+    if (pdl) {
+        attr[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[na].val.programmaticStreamSerializationAllowed = 1;
+        ++na;
+    }
+    if (cluster_x > 0) {
+        attr[na].id = cudaLaunchAttributeClusterDimension;
+        attr[na].val.clusterDim.x = cluster_x;
+        attr[na].val.clusterDim.y = 1;
+        attr[na].val.clusterDim.z = 1;
+        ++na;
+    }
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = na;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // Device FFT: stage plan plus the table w^t = exp(-2 pi i t / n), t < n.
 struct DevFft {
     FftDesc d;
@@ -138,6 +179,7 @@ struct Plan {
     int stencil_rb_grid[4] = {0, 0, 0, 0};   // persistent grid of kinds 2..5 (0: unavailable)
     int c3cl_clusters = 0;      // 3-D: resident 16-CTA clusters of the one-kernel operator (0: n/a)
     int tune_c3 = 0;            // 3-D: 1 = one-kernel cluster operator, 0 = three passes per coil
+    int pdl = 1;                // programmatic dependent launch in the solve's kernel chain
     std::vector<void*> allocs;
 };
 

@@ -962,6 +962,8 @@ prox_fista_kernel(int nx, int ny, int nz, float lam, float gamma, float beta,
                   const float2* __restrict__ ref, double* __restrict__ hist) {
     constexpr int TS = 1 << LEVELS;
     constexpr int ZS = (NDIM == 3) ? TS : 1;
+    pdl_trigger();
+    pdl_wait();
     bool ok;
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t o = tile_origin<NDIM, LEVELS>(t, nx, ny, nz, ok);
@@ -1382,14 +1384,19 @@ pp_status launch_prox_fista(const Plan& p, int levels, float lambda, float gamma
     const int ts = 1 << levels;
     const int64_t ntiles = (int64_t)(p.nx / ts) * (p.ny / ts) * (p.ndim == 3 ? p.nz / ts : 1);
     const int blocks = (int)((ntiles + kThreads - 1) / kThreads);
+    const bool pdl = p.pdl != 0;
+#define PP_PF(ND_, LV_)                                                                         \
+    PP_TRY_CUDA(launch_ex(prox_fista_kernel<ND_, LV_>, dim3(blocks), dim3(kThreads), 0, st, pdl, 0, \
+                          p.nx, p.ny, p.nz, lambda, gamma, beta, p.z, u, p.y, ref, hist_slot))
     if (p.ndim == 2 && levels == 1)
-        prox_fista_kernel<2, 1><<<blocks, kThreads, 0, st>>>(p.nx, p.ny, p.nz, lambda, gamma, beta, p.z, u, p.y, ref, hist_slot);
+        PP_PF(2, 1);
     else if (p.ndim == 2)
-        prox_fista_kernel<2, 2><<<blocks, kThreads, 0, st>>>(p.nx, p.ny, p.nz, lambda, gamma, beta, p.z, u, p.y, ref, hist_slot);
+        PP_PF(2, 2);
     else if (levels == 1)
-        prox_fista_kernel<3, 1><<<blocks, kThreads, 0, st>>>(p.nx, p.ny, p.nz, lambda, gamma, beta, p.z, u, p.y, ref, hist_slot);
+        PP_PF(3, 1);
     else
-        prox_fista_kernel<3, 2><<<blocks, kThreads, 0, st>>>(p.nx, p.ny, p.nz, lambda, gamma, beta, p.z, u, p.y, ref, hist_slot);
+        PP_PF(3, 2);
+#undef PP_PF
     return check_launch("prox_fista_kernel");
 }
 

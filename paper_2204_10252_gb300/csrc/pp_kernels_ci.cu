@@ -67,8 +67,10 @@ ci_rows_fwd_kernel(const float2* __restrict__ tw, RowArgs a, const float2* __res
     constexpr int n = N1 * N2, YP = ypitch<N2>();
     __shared__ float2 tws[n];
     __shared__ float2 Y[N1 * YP];
+    pdl_trigger();
     for (int i = threadIdx.x; i < n; i += blockDim.x) tws[i] = tw[i];
     __syncthreads();
+    pdl_wait();
     const int j = threadIdx.x & (CB - 1), r = threadIdx.x / CB;
     const int row = blockIdx.x, c = blockIdx.y * CB + j;
     if (r < N2) {
@@ -115,8 +117,10 @@ ci_cols_kernel(const float2* __restrict__ tw, int Hin, int Hout, int off_in, int
     constexpr int n = N1 * N2, YP = ypitch<N2>();
     __shared__ float2 tws[n];
     __shared__ float2 Y[N1 * YP];
+    pdl_trigger();
     for (int i = threadIdx.x; i < n; i += blockDim.x) tws[i] = tw[i];
     __syncthreads();
+    pdl_wait();
     const int j = threadIdx.x & (CB - 1), r = threadIdx.x / CB;
     const int64_t rs = (int64_t)Gx * CP;
     const int64_t cofs = (int64_t)blockIdx.x * CP + blockIdx.y * CB + j;
@@ -169,13 +173,7 @@ ci_stencil_kernel(const float* __restrict__ T8, int Gx, int Gy, int nxb,
     float4* wts = sm4 + S::HALO / sizeof(float4);
     const int ntx = (Gx + TX - 1) / TX;
     const int tx0 = (blockIdx.x % ntx) * TX, ty0 = (blockIdx.x / ntx) * TY;
-    // halo: HY rows of HX points x 32 coils = 16 sixteen-byte chunks per point
-    for (int e = threadIdx.x; e < HY * HX * 16; e += blockDim.x) {
-        const int hp = e >> 4, q = e & 15;
-        const int hy = hp / HX, hx = hp - hy * HX;
-        const int gy = wrap1(ty0 - H + hy, Gy), gx = wrap1(tx0 - H + hx, Gx);
-        cp_async16(halo + (size_t)hp * CP + 2 * q, in + ((int64_t)gy * Gx + gx) * CP + 2 * q, true);
-    }
+    pdl_trigger();
     // weights: per tile row, blocks xb0 and xb0 + 1 are 2 x 49 x 8 contiguous floats
     const int xb0 = tx0 / 8;
     for (int e = threadIdx.x; e < TY * 196; e += blockDim.x) {
@@ -183,6 +181,14 @@ ci_stencil_kernel(const float* __restrict__ T8, int Gx, int Gy, int nxb,
         const int y = ty0 + yy;
         const bool ok = y < Gy && xb0 + s < nxb;
         cp_async16(wts + e, T8 + (ok ? ((int64_t)y * nxb + xb0) * 392 + rem * 4 : 0), ok);
+    }
+    pdl_wait();
+    // halo: HY rows of HX points x 32 coils = 16 sixteen-byte chunks per point
+    for (int e = threadIdx.x; e < HY * HX * 16; e += blockDim.x) {
+        const int hp = e >> 4, q = e & 15;
+        const int hy = hp / HX, hx = hp - hy * HX;
+        const int gy = wrap1(ty0 - H + hy, Gy), gx = wrap1(tx0 - H + hx, Gx);
+        cp_async16(halo + (size_t)hp * CP + 2 * q, in + ((int64_t)gy * Gx + gx) * CP + 2 * q, true);
     }
     cp_async_commit_wait_all();
     __syncthreads();
@@ -242,8 +248,10 @@ __device__ __forceinline__ void ci_rows_inv_body(const float2* __restrict__ tw, 
                                                  const float* __restrict__ wcol, int row, int cb,
                                                  float2* tws, float2* Y) {
     constexpr int n = N1 * N2, YP = ypitch<N2>();
+    pdl_trigger();
     for (int i = threadIdx.x; i < n; i += blockDim.x) tws[i] = tw[i];
     __syncthreads();
+    pdl_wait();
     const int j = threadIdx.x & (CB - 1), r = threadIdx.x / CB;
     const int c = cb * CB + j;
     if (r < N2) {
@@ -339,6 +347,8 @@ ci_rows_inv_cl_kernel(const float2* __restrict__ tw, RowArgs a, const float2* __
 // out[o] = scale * sum_b P[b][o] + alpha * operand[o]
 __global__ void ci_sum_kernel(const float2* __restrict__ P, int64_t n, float scale,
                               const float2* operand, float alpha, float2* out) {
+    pdl_trigger();
+    pdl_wait();
     for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < n;
          o += (int64_t)gridDim.x * blockDim.x) {
         float2 acc = P[o];
@@ -385,19 +395,22 @@ pp_status ci_normal(const Plan& p, const float2* x, float2* out, float scale, co
                     float alpha, int ry, cudaStream_t st) {
     const int nx = p.nx, ny = p.ny, Gx = p.G_x, Gy = p.G_y;
     const int n2x = fft4_n2(Gx), n2y = fft4_n2(Gy);
+    const bool pdl = p.pdl != 0;
     RowArgs rf{};
     rf.n = nx; rf.G = Gx; rf.off_in = nx / 2; rf.off_out = 0; rf.nrows = ny; rf.scale = 1.f;
 #define PP_CIR(N2_)                                                                                \
     if (n2x == N2_)                                                                                \
-        ci_rows_fwd_kernel<N2_><<<dim3(ny, NCB), CB * tpr<N2_>(), 0, st>>>(                        \
-            p.gx.tw, rf, x, p.ci_sens, p.deapod_y, p.deapod_x, p.ci_a);
+        PP_TRY_CUDA(launch_ex(ci_rows_fwd_kernel<N2_>, dim3(ny, NCB), dim3(CB * tpr<N2_>()), 0, st, \
+                              pdl, 0, (const float2*)p.gx.tw, rf, x, (const float2*)p.ci_sens,    \
+                              (const float*)p.deapod_y, (const float*)p.deapod_x, p.ci_a));
     PP_CIR(8) PP_CIR(12) PP_CIR(16) PP_CIR(20) PP_CIR(24)
 #undef PP_CIR
     PP_TRY(check_ci("ci_rows_fwd_kernel"));
 #define PP_CIC(N2_, INV_, HIN, HOUT, OIN, OOUT, SRC, DST)                                          \
     if (n2y == N2_)                                                                                \
-        ci_cols_kernel<N2_, INV_><<<dim3(Gx, NCB), CB * tpr<N2_>(), 0, st>>>(                      \
-            p.gy.tw, HIN, HOUT, OIN, OOUT, Gx, SRC, DST);
+        PP_TRY_CUDA(launch_ex(ci_cols_kernel<N2_, INV_>, dim3(Gx, NCB), dim3(CB * tpr<N2_>()), 0,   \
+                              st, pdl, 0, (const float2*)p.gy.tw, (int)(HIN), (int)(HOUT),        \
+                              (int)(OIN), (int)(OOUT), Gx, (const float2*)(SRC), (float2*)(DST)));
     PP_CIC(8, false, ny, Gy, ny / 2, 0, p.ci_a, p.ci_b)
     PP_CIC(12, false, ny, Gy, ny / 2, 0, p.ci_a, p.ci_b)
     PP_CIC(16, false, ny, Gy, ny / 2, 0, p.ci_a, p.ci_b)
@@ -406,11 +419,13 @@ pp_status ci_normal(const Plan& p, const float2* x, float2* out, float scale, co
     PP_TRY(check_ci("ci_cols_kernel"));
     const int ntiles = ((Gx + 15) / 16) * ((Gy + 4 * ry - 1) / (4 * ry));
     if (ry == 2)
-        ci_stencil_kernel<2><<<ntiles, 256, CiStencil<2>::SMEM, st>>>(p.gtg8, Gx, Gy, (Gx + 7) / 8,
-                                                                     p.ci_b, p.ci_c);
+        PP_TRY_CUDA(launch_ex(ci_stencil_kernel<2>, dim3(ntiles), dim3(256), CiStencil<2>::SMEM, st,
+                              pdl, 0, (const float*)p.gtg8, Gx, Gy, (Gx + 7) / 8,
+                              (const float2*)p.ci_b, p.ci_c));
     else
-        ci_stencil_kernel<1><<<ntiles, 256, CiStencil<1>::SMEM, st>>>(p.gtg8, Gx, Gy, (Gx + 7) / 8,
-                                                                     p.ci_b, p.ci_c);
+        PP_TRY_CUDA(launch_ex(ci_stencil_kernel<1>, dim3(ntiles), dim3(256), CiStencil<1>::SMEM, st,
+                              pdl, 0, (const float*)p.gtg8, Gx, Gy, (Gx + 7) / 8,
+                              (const float2*)p.ci_b, p.ci_c));
     PP_TRY(check_ci("ci_stencil_kernel"));
     PP_CIC(8, true, Gy, ny, 0, ny / 2, p.ci_c, p.ci_a)
     PP_CIC(12, true, Gy, ny, 0, ny / 2, p.ci_c, p.ci_a)
@@ -422,26 +437,13 @@ pp_status ci_normal(const Plan& p, const float2* x, float2* out, float scale, co
     RowArgs ra = rf;
     ra.off_in = 0; ra.off_out = nx / 2;
     if (p.tune_rows_adj_cl == 4) {
-        cudaLaunchConfig_t cfg = {};
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = NCB;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.gridDim = dim3(NCB, ny);
-        cfg.dynamicSmemBytes = 0;
-        cfg.stream = st;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
         cudaError_t e = cudaSuccess;
 #define PP_CIL(N2_)                                                                          \
-        if (n2x == N2_) {                                                                    \
-            cfg.blockDim = dim3(CB * tpr<N2_>());                                            \
-            e = cudaLaunchKernelEx(&cfg, ci_rows_inv_cl_kernel<N2_>, (const float2*)p.gx.tw, \
-                                   ra, (const float2*)p.ci_a, (const float2*)p.ci_sens,      \
-                                   (const float*)p.deapod_y, (const float*)p.deapod_x, out,  \
-                                   scale, operand, alpha);                                   \
-        }
+        if (n2x == N2_)                                                                      \
+            e = launch_ex(ci_rows_inv_cl_kernel<N2_>, dim3(NCB, ny), dim3(CB * tpr<N2_>()), 0, \
+                          st, pdl, NCB, (const float2*)p.gx.tw, ra, (const float2*)p.ci_a,   \
+                          (const float2*)p.ci_sens, (const float*)p.deapod_y,                \
+                          (const float*)p.deapod_x, out, scale, operand, alpha);
         PP_CIL(8) PP_CIL(12) PP_CIL(16) PP_CIL(20) PP_CIL(24)
 #undef PP_CIL
         if (e != cudaSuccess) return cuda_status(e, "ci_rows_inv_cl_kernel launch");
@@ -449,14 +451,17 @@ pp_status ci_normal(const Plan& p, const float2* x, float2* out, float scale, co
     }
 #define PP_CII(N2_)                                                                                \
     if (n2x == N2_)                                                                                \
-        ci_rows_inv_kernel<N2_><<<dim3(ny, NCB), CB * tpr<N2_>(), 0, st>>>(                        \
-            p.gx.tw, ra, p.ci_a, p.ci_sens, p.deapod_y, p.deapod_x, p.ci_part);
+        PP_TRY_CUDA(launch_ex(ci_rows_inv_kernel<N2_>, dim3(ny, NCB), dim3(CB * tpr<N2_>()), 0, st,  \
+                              pdl, 0, (const float2*)p.gx.tw, ra, (const float2*)p.ci_a,          \
+                              (const float2*)p.ci_sens, (const float*)p.deapod_y,                 \
+                              (const float*)p.deapod_x, p.ci_part));
     PP_CII(8) PP_CII(12) PP_CII(16) PP_CII(20) PP_CII(24)
 #undef PP_CII
     PP_TRY(check_ci("ci_rows_inv_kernel"));
     const int64_t n = (int64_t)ny * nx;
     const int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 8);
-    ci_sum_kernel<<<blocks, 256, 0, st>>>(p.ci_part, n, scale, operand, alpha, out);
+    PP_TRY_CUDA(launch_ex(ci_sum_kernel, dim3(blocks), dim3(256), 0, st, pdl, 0,
+                          (const float2*)p.ci_part, n, scale, operand, alpha, out));
     return check_ci("ci_sum_kernel");
 }
 
