@@ -124,7 +124,8 @@ pp_status pp_plan_sizes(const pp_plan* plan, int64_t* image_elems, int64_t* kspa
  *    a persistent grid; 6 = coil-lane, the 32 lanes of a warp being 32
  *    coils of 8 adjacent outputs; 7, 8 = the whole normal operator on
  *    coil-innermost ([row][col][coil], 32-coil pitch) copies with a
- *    coil-lane stencil of 1 or 2 rows per warp (plans with at most 32
+ *    coil-lane stencil of 1 or 2 rows per warp, 9 = the same with a
+ *    coil-pair stencil (two coils per lane) (plans with at most 32
  *    coils and register-FFT grid lengths); there row_ifft_variant 4 sums
  *    the four 8-coil blocks of a row in a thread-block cluster, any other
  *    value through a partial-sum buffer;

@@ -180,7 +180,8 @@ static pp_status normal_into(const Plan& p, const float2* x, float2* out, float 
     }
     // non-Cartesian: rows -> cols -> G^T G stencil -> cols^H -> rows^H
     if (p.tune_stencil_kind >= 7 && p.ci_sens)
-        return ci_normal(p, x, out, scale, operand, alpha, p.tune_stencil_kind == 8 ? 2 : 1, st);
+        return ci_normal(p, x, out, scale, operand, alpha,
+                         p.tune_stencil_kind == 9 ? 0 : (p.tune_stencil_kind == 8 ? 2 : 1), st);
     const int Gx = p.G_x, Gy = p.G_y;
     RowArgs rf = row_args(nx, Gx, nx / 2, 0, ny, (int64_t)ny * nx, 1.f);
     PP_TRY(launch_rows_fwd(p, p.gx, rf, x, p.sens, p.deapod_y, p.deapod_x, p.wk_a, p.C, 0, st));
@@ -527,7 +528,7 @@ static pp_status tune_noncartesian(Plan& p, cudaStream_t st) {
         // (stencil kind, row variant): for kinds 7 and 8 the row variant 4
         // reduces the four 8-coil blocks of a row in a thread-block cluster
         std::vector<std::pair<int, int>> whole = {{p.tune_stencil_kind, p.tune_rows_adj_cl},
-                                                  {7, 1}, {7, 4}, {8, 1}, {8, 4}};
+                                                  {7, 1}, {7, 4}, {8, 1}, {8, 4}, {9, 1}, {9, 4}};
         PP_TRY_CUDA(cudaMemsetAsync(p.v, 0, sizeof(float2) * (size_t)p.nimg, st));
         std::vector<float> wbest(whole.size(), 1e30f);
         for (int round = 0; round < kRounds; ++round)
@@ -1269,8 +1270,8 @@ pp_status pp_plan_tuning(const pp_plan* plan, int* row_ifft_variant, int* stenci
 pp_status pp_plan_set_tuning(pp_plan* plan, int row_ifft_variant, int stencil_kind, int stencil_coils) {
     if (!plan || !(row_ifft_variant == 1 || row_ifft_variant == 2 || row_ifft_variant == 4 ||
                    row_ifft_variant == -1 || row_ifft_variant == 16) ||
-        stencil_kind < 0 || stencil_kind > 8 || stencil_coils < 1 || stencil_coils > 64) {
-        set_error("pp_plan_set_tuning: row variant must be 1, 2, 4, -1 or 16; stencil kind 0..8; "
+        stencil_kind < 0 || stencil_kind > 9 || stencil_coils < 1 || stencil_coils > 64) {
+        set_error("pp_plan_set_tuning: row variant must be 1, 2, 4, -1 or 16; stencil kind 0..9; "
                   "stencil coils 1..64");
         return PP_ERR_INVALID_ARG;
     }

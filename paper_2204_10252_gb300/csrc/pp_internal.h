@@ -173,8 +173,8 @@ struct Plan {
                                 // into per-coil IFFTs plus a coil sum (normal operator only)
     int tune_stencil_kind = 0;  // G^T G stencil kernel: 0 one output per thread, 1 two,
                                 // 2..5 register-blocked (R x CG = 4x4, 8x4, 4x8, 2x8),
-                                // 6 coil-lane, 7 / 8 coil-innermost pipeline with a
-                                // 1- / 2-row coil-lane stencil
+                                // 6 coil-lane, 7 / 8 / 9 coil-innermost pipeline with
+                                // a 1- / 2-row coil-lane or a coil-pair stencil
     int tune_stencil_cpc = 0;   // coils per CTA of kinds 0 and 1
     int stencil_rb_grid[4] = {0, 0, 0, 0};   // persistent grid of kinds 2..5 (0: unavailable)
     int c3cl_clusters = 0;      // 3-D: resident 16-CTA clusters of the one-kernel operator (0: n/a)
@@ -250,7 +250,7 @@ size_t ci_sens_elems(const Plan& p);
 size_t ci_partial_elems(const Plan& p);
 pp_status ci_prepare(Plan& p, cudaStream_t st);
 pp_status ci_normal(const Plan& p, const float2* x, float2* out, float scale, const float2* operand,
-                    float alpha, int ry, cudaStream_t st);
+                    float alpha, int ry, cudaStream_t st);   // ry 0: coil-pair stencil
 pp_status launch_nufft_degrid(const Plan& p, const float2* grid_in, float2* ksp, cudaStream_t st);
 pp_status launch_prox(int ndim, int nx, int ny, int nz, int levels, float lambda,
                       const float2* in, float2* out, cudaStream_t st);

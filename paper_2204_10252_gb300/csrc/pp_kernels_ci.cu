@@ -237,6 +237,83 @@ template <int N2> __host__ __device__ constexpr int inv_buf() {
     return N1 * ypitch<N2>() > N1 * N2 * 9 ? N1 * ypitch<N2>() : N1 * N2 * 9;
 }
 
+// Coil-pair variant of the coil-innermost stencil: lane = (segment h =
+// lane / 16, coil pair cp = lane % 16), so a warp covers 16 adjacent outputs
+// of one row for all 32 coils and each lane two coils of 8 outputs.  One
+// 16-byte halo read serves both coils and each weight is duplicated once for
+// two packed FMAs.  CTA: 16 x 8 output tile, one warp per row.
+constexpr int CPS_TX = 16, CPS_TY = 8, CPS_HX = CPS_TX + 6, CPS_HY = CPS_TY + 6;
+constexpr size_t CPS_HALO = sizeof(float2) * CPS_HY * CPS_HX * CP;
+constexpr size_t CPS_SMEM = CPS_HALO + sizeof(float) * CPS_TY * CPS_TX * 49;
+
+__global__ void __launch_bounds__(256, 2)
+ci_stencil_cp_kernel(const float* __restrict__ T8, int Gx, int Gy, int nxb,
+                     const float2* __restrict__ in, float2* __restrict__ out) {
+    constexpr int D = 7, H = 3;
+    extern __shared__ float4 sm4[];
+    float4* halo4 = sm4;                                  // [hy][hx][16 coil pairs]
+    float4* wts = sm4 + CPS_HALO / sizeof(float4);        // [row][2][49][2]
+    const int ntx = (Gx + CPS_TX - 1) / CPS_TX;
+    const int tx0 = (blockIdx.x % ntx) * CPS_TX, ty0 = (blockIdx.x / ntx) * CPS_TY;
+    pdl_trigger();
+    const int xb0 = tx0 / 8;
+    for (int e = threadIdx.x; e < CPS_TY * 196; e += blockDim.x) {
+        const int yy = e / 196, rem = e - yy * 196, s = rem / 98;
+        const int y = ty0 + yy;
+        const bool ok = y < Gy && xb0 + s < nxb;
+        cp_async16(wts + e, T8 + (ok ? ((int64_t)y * nxb + xb0) * 392 + rem * 4 : 0), ok);
+    }
+    pdl_wait();
+    {
+        // thread = (column group g, coil pair q): columns g and g + 16 of every halo row
+        const int q = threadIdx.x & 15, g = threadIdx.x >> 4;
+        const int gx0 = wrap1(tx0 - H + g, Gx);
+        const int gx1 = g + 16 < CPS_HX ? wrap1(tx0 - H + g + 16, Gx) : 0;
+        for (int hy = 0; hy < CPS_HY; ++hy) {
+            const float2* row = in + (int64_t)wrap1(ty0 - H + hy, Gy) * Gx * CP + 2 * q;
+            cp_async16(halo4 + (hy * CPS_HX + g) * 16 + q, row + (int64_t)gx0 * CP, true);
+            if (g + 16 < CPS_HX)
+                cp_async16(halo4 + (hy * CPS_HX + g + 16) * 16 + q, row + (int64_t)gx1 * CP, true);
+        }
+    }
+    cp_async_commit_wait_all();
+    __syncthreads();
+    const int yy = threadIdx.x >> 5, lane = threadIdx.x & 31, h = lane >> 4, cp = lane & 15;
+    const float4* wq = wts + (yy * 2 + h) * 98;
+    float2 a0[8], a1[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) a0[r] = a1[r] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int dy = 0; dy < D; ++dy) {
+        const float4* hrow = halo4 + ((yy + dy) * CPS_HX + 8 * h) * 16 + cp;
+        float4 xv[14];
+#pragma unroll
+        for (int j = 0; j < 14; ++j) xv[j] = hrow[j * 16];
+#pragma unroll
+        for (int dx = 0; dx < D; ++dx) {
+            const float4 wa = wq[(dy * D + dx) * 2], wb = wq[(dy * D + dx) * 2 + 1];
+            const float wr[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                const float2 wd = make_float2(wr[r], wr[r]);
+                const float4 v = xv[r + dx];
+                a0[r] = __ffma2_rn(wd, make_float2(v.x, v.y), a0[r]);
+                a1[r] = __ffma2_rn(wd, make_float2(v.z, v.w), a1[r]);
+            }
+        }
+    }
+    const int gy = ty0 + yy;
+    if (gy < Gy) {
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int gx = tx0 + 8 * h + r;
+            if (gx < Gx)
+                reinterpret_cast<float4*>(out)[((int64_t)gy * Gx + gx) * 16 + cp] =
+                    make_float4(a0[r].x, a0[r].y, a1[r].x, a1[r].y);
+        }
+    }
+}
+
 // Body shared by both row-IFFT kernels: leaves R[i * 9 + j] = w conj(S_c)
 // IFFT(src_c[row])[place(i)] for the CTA's 8 coils c = cb * 8 + j, and
 // R[i * 9 + 8] = their sum (i < a.n); ends with a barrier.
@@ -385,6 +462,8 @@ pp_status ci_prepare(Plan& p, cudaStream_t st) {
                                      (int)CiStencil<1>::SMEM));
     PP_TRY_CUDA(cudaFuncSetAttribute(ci_stencil_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)CiStencil<2>::SMEM));
+    PP_TRY_CUDA(cudaFuncSetAttribute(ci_stencil_cp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)CPS_SMEM));
     const int64_t n = (int64_t)p.ny * p.nx;
     ci_pack_sens_kernel<<<152 * 4, 256, 0, st>>>(p.sens, p.C, n, p.ci_sens);
     return check_ci("ci_pack_sens_kernel");
@@ -417,8 +496,13 @@ pp_status ci_normal(const Plan& p, const float2* x, float2* out, float scale, co
     PP_CIC(20, false, ny, Gy, ny / 2, 0, p.ci_a, p.ci_b)
     PP_CIC(24, false, ny, Gy, ny / 2, 0, p.ci_a, p.ci_b)
     PP_TRY(check_ci("ci_cols_kernel"));
-    const int ntiles = ((Gx + 15) / 16) * ((Gy + 4 * ry - 1) / (4 * ry));
-    if (ry == 2)
+    const int ntiles = ry ? ((Gx + 15) / 16) * ((Gy + 4 * ry - 1) / (4 * ry)) : 0;
+    if (ry == 0)
+        PP_TRY_CUDA(launch_ex(ci_stencil_cp_kernel,
+                              dim3(((Gx + CPS_TX - 1) / CPS_TX) * ((Gy + CPS_TY - 1) / CPS_TY)), dim3(256),
+                              CPS_SMEM, st, pdl, 0, (const float*)p.gtg8, Gx, Gy, (Gx + 7) / 8,
+                              (const float2*)p.ci_b, p.ci_c));
+    else if (ry == 2)
         PP_TRY_CUDA(launch_ex(ci_stencil_kernel<2>, dim3(ntiles), dim3(256), CiStencil<2>::SMEM, st,
                               pdl, 0, (const float*)p.gtg8, Gx, Gy, (Gx + 7) / 8,
                               (const float2*)p.ci_b, p.ci_c));

@@ -148,7 +148,7 @@ def test_coil_innermost_pipeline(pp, case):
         L = float(O.power_iteration(normal, shape, 9, iters=10))
         pp.pp_plan_set_scale(plan, L)
         ref = normal(x) / L
-        for kind, rv in ((7, 1), (8, 1), (7, 4), (8, 4), (2, 1)):
+        for kind, rv in ((7, 1), (8, 1), (7, 4), (8, 4), (9, 1), (9, 4), (2, 1)):
             pp.pp_plan_set_tuning(plan, rv, kind, 8)
             out = empty(shape)
             pp.pp_normal_apply(plan, dev(x), out)
@@ -371,7 +371,7 @@ def test_full_size_spiral_normal_apply(pp, full_spiral):
 
 @pytest.mark.parametrize("row_variant,kind,cpc", [
     (1, 0, 8), (2, 0, 4), (4, 0, 16), (-1, 0, 32), (-1, 0, 2), (1, 1, 8), (2, 1, 3),
-    (1, 2, 8), (-1, 3, 8), (2, 4, 8), (-1, 5, 8), (1, 6, 8), (-1, 6, 8), (1, 7, 8), (1, 8, 8), (4, 7, 8), (4, 8, 8)])
+    (1, 2, 8), (-1, 3, 8), (2, 4, 8), (-1, 5, 8), (1, 6, 8), (-1, 6, 8), (1, 7, 8), (1, 8, 8), (4, 7, 8), (4, 8, 8), (1, 9, 8), (4, 9, 8)])
 def test_full_size_spiral_every_launch_variant(pp, full_spiral, row_variant, kind, cpc):
     plan, x, ref = full_spiral
     tuned = pp.pp_plan_tuning(plan)
