@@ -359,7 +359,14 @@ nufft_spread_tile_kernel(const TileEntry* __restrict__ entries, const int* __res
     for (int c = c0; c < c1; ++c) {
         for (int idx = threadIdx.x; idx < 2 * T * T; idx += blockDim.x) acc[idx] = 0.f;
         __syncthreads();
-        for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+        // lane l of a warp takes entries l*S, l*S + 1, ... of the tile's list
+        // (trajectory order), so the 32 samples spread at one time lie far
+        // apart along the trajectory and their shared-memory atomics rarely
+        // hit the same grid point
+        const int ne = e1 - e0, S = (ne + 31) / 32;
+        for (int i = threadIdx.x; i < 32 * S; i += blockDim.x) {
+            const int e = e0 + (i & 31) * S + (i >> 5);
+            if (e >= e1) continue;
             const TileEntry te = entries[e];
             const float wx[4] = {te.wx.x, te.wx.y, te.wx.z, te.wx.w};
             const float wy[4] = {te.wy.x, te.wy.y, te.wy.z, te.wy.w};
@@ -1031,6 +1038,112 @@ prox_fista_kernel(int nx, int ny, int nz, float lam, float gamma, float beta,
     }
 }
 
+// 2-D, 2-level variant of prox_fista_kernel with four threads per 4x4 tile:
+// a thread owns one 2x2 block (level 1 in registers); the level-2 transform
+// of the tile's four approximation coefficients runs across the four
+// threads with shuffles (x partner lane ^ 1, y partner lane ^ 16), in the
+// same operation order as haar2x2.  A warp covers 2 block rows x 16 block
+// columns (one tile row of 8 tiles).  Needs nx % 32 == 0 and ny % 4 == 0.
+__device__ __forceinline__ float2 haar_l2_shfl(float2 a, int qx, int qy) {
+    float2 p;
+    p.x = __shfl_xor_sync(0xffffffffu, a.x, 1);
+    p.y = __shfl_xor_sync(0xffffffffu, a.y, 1);
+    const float2 t = qx ? csub(p, a) : cadd(a, p);      // row sum (qx 0) or difference (qx 1)
+    float2 u;
+    u.x = __shfl_xor_sync(0xffffffffu, t.x, 16);
+    u.y = __shfl_xor_sync(0xffffffffu, t.y, 16);
+    return cscale(qy ? csub(u, t) : cadd(t, u), 0.5f);
+}
+
+__global__ void __launch_bounds__(kThreads)
+prox_fista2q_kernel(int nx, int ny, float lam, float gamma, float beta, float2* __restrict__ z,
+                    const float2* __restrict__ u, float2* __restrict__ y,
+                    const float2* __restrict__ ref, double* __restrict__ hist) {
+    pdl_trigger();
+    pdl_wait();
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31, qx = lane & 1, qy = (lane >> 4) & 1;
+    const int nwc = nx / 32;
+    const int64_t W = g >> 5;
+    const bool ok = W < (int64_t)(ny / 4) * nwc;   // warp-uniform
+    double dd = 0.0, yy = 0.0, rr = 0.0;
+    if (ok) {
+        const int wr = (int)(W / nwc), wc = (int)(W - (int64_t)wr * nwc);
+        const int by = 2 * wr + (lane >> 4), bx = 16 * wc + (lane & 15);
+        const int64_t o0 = (int64_t)(2 * by) * nx + 2 * bx, o1 = o0 + nx;
+        const float4 z0 = *reinterpret_cast<const float4*>(z + o0);
+        const float4 z1 = *reinterpret_cast<const float4*>(z + o1);
+        const float4 u0 = *reinterpret_cast<const float4*>(u + o0);
+        const float4 u1 = *reinterpret_cast<const float4*>(u + o1);
+        float2 a = make_float2(z0.x - gamma * u0.x, z0.y - gamma * u0.y);
+        float2 b = make_float2(z0.z - gamma * u0.z, z0.w - gamma * u0.w);
+        float2 c = make_float2(z1.x - gamma * u1.x, z1.y - gamma * u1.y);
+        float2 d = make_float2(z1.z - gamma * u1.z, z1.w - gamma * u1.w);
+        haar2x2(a, b, c, d);
+        a = haar_l2_shfl(a, qx, qy);
+        a = soft(a, lam);
+        b = soft(b, lam);
+        c = soft(c, lam);
+        d = soft(d, lam);
+        a = haar_l2_shfl(a, qx, qy);
+        haar2x2(a, b, c, d);
+        const float4 y0 = *reinterpret_cast<const float4*>(y + o0);
+        const float4 y1 = *reinterpret_cast<const float4*>(y + o1);
+        const float2 yo[4] = {make_float2(y0.x, y0.y), make_float2(y0.z, y0.w),
+                              make_float2(y1.x, y1.y), make_float2(y1.z, y1.w)};
+        const float2 yn[4] = {a, b, c, d};
+        float2 zn[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float2 df = csub(yn[k], yo[k]);
+            zn[k] = make_float2(yn[k].x + beta * df.x, yn[k].y + beta * df.y);
+            dd += (double)df.x * df.x + (double)df.y * df.y;
+            yy += (double)yn[k].x * yn[k].x + (double)yn[k].y * yn[k].y;
+        }
+        *reinterpret_cast<float4*>(z + o0) = make_float4(zn[0].x, zn[0].y, zn[1].x, zn[1].y);
+        *reinterpret_cast<float4*>(z + o1) = make_float4(zn[2].x, zn[2].y, zn[3].x, zn[3].y);
+        *reinterpret_cast<float4*>(y + o0) = make_float4(a.x, a.y, b.x, b.y);
+        *reinterpret_cast<float4*>(y + o1) = make_float4(c.x, c.y, d.x, d.y);
+        if (ref) {
+            const float4 r0 = *reinterpret_cast<const float4*>(ref + o0);
+            const float4 r1 = *reinterpret_cast<const float4*>(ref + o1);
+            const float rv[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const double ex = (double)yn[k].x - rv[2 * k], ey = (double)yn[k].y - rv[2 * k + 1];
+                rr += ex * ex + ey * ey;
+            }
+        }
+    }
+    if (hist) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            dd += __shfl_down_sync(0xffffffffu, dd, off);
+            yy += __shfl_down_sync(0xffffffffu, yy, off);
+            rr += __shfl_down_sync(0xffffffffu, rr, off);
+        }
+        __shared__ double sd[kThreads / 32], sy[kThreads / 32], sr[kThreads / 32];
+        const int wid = threadIdx.x >> 5;
+        if (lane == 0) {
+            sd[wid] = dd;
+            sy[wid] = yy;
+            sr[wid] = rr;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+            for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+                s0 += sd[i];
+                s1 += sy[i];
+                s2 += sr[i];
+            }
+            atomicAdd(&hist[0], s0);
+            atomicAdd(&hist[1], s1);
+            atomicAdd(&hist[2], s2);
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // FP64 reductions (deterministic: fixed grid, per-block partials, one
 // finishing block).  partial layout [nblocks][3] = Re<a,b>, Im<a,b>, |b|^2.
@@ -1385,6 +1498,14 @@ pp_status launch_prox_fista(const Plan& p, int levels, float lambda, float gamma
     const int64_t ntiles = (int64_t)(p.nx / ts) * (p.ny / ts) * (p.ndim == 3 ? p.nz / ts : 1);
     const int blocks = (int)((ntiles + kThreads - 1) / kThreads);
     const bool pdl = p.pdl != 0;
+    if (p.ndim == 2 && levels == 2 && p.nx % 32 == 0 && p.ny % 4 == 0 &&
+        ((uintptr_t)ref & 15) == 0 && ((uintptr_t)u & 15) == 0) {
+        const int64_t nthr = (int64_t)p.nx * p.ny / 4;
+        PP_TRY_CUDA(launch_ex(prox_fista2q_kernel, dim3((unsigned)((nthr + kThreads - 1) / kThreads)),
+                              dim3(kThreads), 0, st, pdl, 0, p.nx, p.ny, lambda, gamma, beta, p.z, u,
+                              p.y, ref, hist_slot));
+        return check_launch("prox_fista2q_kernel");
+    }
 #define PP_PF(ND_, LV_)                                                                         \
     PP_TRY_CUDA(launch_ex(prox_fista_kernel<ND_, LV_>, dim3(blocks), dim3(kThreads), 0, st, pdl, 0, \
                           p.nx, p.ny, p.nz, lambda, gamma, beta, p.z, u, p.y, ref, hist_slot))
