@@ -65,17 +65,31 @@ ci_rows_fwd_kernel(const float2* __restrict__ tw, RowArgs a, const float2* __res
                    const float2* __restrict__ S, const float* __restrict__ wrow,
                    const float* __restrict__ wcol, float2* __restrict__ out) {
     constexpr int n = N1 * N2, YP = ypitch<N2>();
+    static_assert(N1 * YP >= n * CB, "the coil-map row must fit the transpose buffer");
     __shared__ float2 tws[n];
-    __shared__ float2 Y[N1 * YP];
+    __shared__ __align__(16) float2 Y[N1 * YP];
     pdl_trigger();
+    const int row = blockIdx.x;
+    // The CTA's 8-coil run of the map row (a plan constant) streams into Y
+    // while the previous kernel finishes: Ss[i * 8 + j] = S_ci[row][i][cb * 8 + j].
+    float2* Ss = Y;
+    {
+        const float2* Srow = S + (int64_t)row * a.n * CP + blockIdx.y * CB;
+        for (int e = threadIdx.x; e < a.n * 4; e += blockDim.x) {
+            const int i = e >> 2, q = e & 3;
+            cp_async16(Ss + i * CB + 2 * q, Srow + (int64_t)i * CP + 2 * q, true);
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    }
     for (int i = threadIdx.x; i < n; i += blockDim.x) tws[i] = tw[i];
-    __syncthreads();
     pdl_wait();
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    __syncthreads();
     const int j = threadIdx.x & (CB - 1), r = threadIdx.x / CB;
-    const int row = blockIdx.x, c = blockIdx.y * CB + j;
+    const int c = blockIdx.y * CB + j;
+    float2 v[N1];
     if (r < N2) {
         const float wr = a.scale * (wrow ? wrow[row] : 1.f);
-        float2 v[N1];
 #pragma unroll
         for (int m1 = 0; m1 < N1; ++m1) {
             int i = N2 * m1 + r + a.off_in;
@@ -83,10 +97,13 @@ ci_rows_fwd_kernel(const float2* __restrict__ tw, RowArgs a, const float2* __res
             float2 val = make_float2(0.f, 0.f);
             if (i < a.n) {
                 const int64_t o = (int64_t)row * a.n + i;
-                val = cscale(cmul(x[o], S[o * CP + c]), wcol ? wr * wcol[i] : wr);
+                val = cscale(cmul(x[o], Ss[i * CB + j]), wcol ? wr * wcol[i] : wr);
             }
             v[m1] = val;
         }
+    }
+    __syncthreads();   // Ss (aliasing Y) is consumed
+    if (r < N2) {
         fft4_phase1<N1, N2, false>(v, r, tws);
 #pragma unroll
         for (int k1 = 0; k1 < N1; ++k1) Y[k1 * YP + r * CB + j] = v[k1];
