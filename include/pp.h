@@ -116,7 +116,8 @@ pp_status pp_plan_sizes(const pp_plan* plan, int64_t* image_elems, int64_t* kspa
  *    through distributed shared memory; -1 = one IFFT per coil and row
  *    followed by a coil sum); for 3-D Cartesian plans 16 = the whole normal
  *    operator as one kernel on 16-CTA clusters (nz = 128, ny in {128, 192,
- *    256}), 1 = three passes per coil;
+ *    256}), 1 = three passes per coil; for 2-D Cartesian plans 1, 2, 4 or 8
+ *    = CTAs per 8-column group, the coils split over a cluster of that size;
  *  - stencil_kind: the G^T G stencil kernel (0 = one output per thread,
  *    1 = two outputs per thread, both staging one coil at a time with
  *    stencil_coils coils per CTA; 2..5 = register-blocked, a thread holding

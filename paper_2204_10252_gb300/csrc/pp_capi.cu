@@ -576,6 +576,38 @@ static pp_status tune_cart3d(Plan& p, cudaStream_t st) {
     return PP_OK;
 }
 
+// 2-D Cartesian: one CTA per 8-column group against the coils split over a
+// cluster of 2, 4 or 8 CTAs per group (narrow images leave most SMs idle
+// otherwise), timed on the plan's buffers; the fastest is kept.
+static pp_status tune_cart2d(Plan& p, cudaStream_t st) {
+    if (!fft4_n2(p.ny)) return PP_OK;
+    cudaEvent_t e0, e1;
+    PP_TRY_CUDA(cudaEventCreate(&e0));
+    PP_TRY_CUDA(cudaEventCreate(&e1));
+    PP_TRY_CUDA(cudaMemsetAsync(p.v, 0, sizeof(float2) * (size_t)p.nimg, st));
+    std::vector<int> cand = {1};
+    for (int cl : {2, 4, 8})
+        if (cl <= p.C) cand.push_back(cl);
+    std::vector<float> best(cand.size(), 1e30f);
+    for (int round = 0; round < 3; ++round)
+        for (size_t i = 0; i < cand.size(); ++i) {
+            p.tune_c2 = cand[i];
+            PP_TRY(normal_into(p, p.v, p.t, 1.f, nullptr, 0.f, st));
+            PP_TRY(normal_into(p, p.v, p.t, 1.f, nullptr, 0.f, st));
+            PP_TRY_CUDA(cudaEventRecord(e0, st));
+            for (int r = 0; r < 10; ++r) PP_TRY(normal_into(p, p.v, p.t, 1.f, nullptr, 0.f, st));
+            PP_TRY_CUDA(cudaEventRecord(e1, st));
+            PP_TRY_CUDA(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            PP_TRY_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            best[i] = std::min(best[i], ms);
+        }
+    p.tune_c2 = cand[std::min_element(best.begin(), best.end()) - best.begin()];
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return PP_OK;
+}
+
 // Buffers of the coil-innermost pipeline (when the plan supports it).
 static pp_status setup_ci(Plan& p, cudaStream_t st) {
     if (!ci_supported(p)) return PP_OK;
@@ -1200,6 +1232,7 @@ pp_status pp_plan_create(pp_plan** out, pp_dims dims, int coils, const pp_c64* s
             if (e != cudaSuccess) rc = cuda_status(e, "cudaStreamCreate");
         }
     }
+    if (rc == PP_OK && p.kind == PP_CARTESIAN && p.ndim == 2) rc = tune_cart2d(p, st);
     if (rc == PP_OK && p.kind == PP_CARTESIAN && p.ndim == 3) {
         p.c3cl_clusters = c3cl_prepare(p);
         rc = tune_cart3d(p, st);
@@ -1259,6 +1292,8 @@ pp_status pp_plan_tuning(const pp_plan* plan, int* row_ifft_variant, int* stenci
         const Plan& p = plan->impl;
         if (p.kind == PP_CARTESIAN && p.ndim == 3)
             *row_ifft_variant = p.tune_c3 ? 16 : 1;
+        else if (p.kind == PP_CARTESIAN)
+            *row_ifft_variant = p.tune_c2;
         else
             *row_ifft_variant = p.tune_rows_adj_cl ? p.tune_rows_adj_cl : 1;
     }
@@ -1269,9 +1304,9 @@ pp_status pp_plan_tuning(const pp_plan* plan, int* row_ifft_variant, int* stenci
 
 pp_status pp_plan_set_tuning(pp_plan* plan, int row_ifft_variant, int stencil_kind, int stencil_coils) {
     if (!plan || !(row_ifft_variant == 1 || row_ifft_variant == 2 || row_ifft_variant == 4 ||
-                   row_ifft_variant == -1 || row_ifft_variant == 16) ||
+                   row_ifft_variant == -1 || row_ifft_variant == 8 || row_ifft_variant == 16) ||
         stencil_kind < 0 || stencil_kind > 9 || stencil_coils < 1 || stencil_coils > 64) {
-        set_error("pp_plan_set_tuning: row variant must be 1, 2, 4, -1 or 16; stencil kind 0..9; "
+        set_error("pp_plan_set_tuning: row variant must be 1, 2, 4, 8, -1 or 16; stencil kind 0..9; "
                   "stencil coils 1..64");
         return PP_ERR_INVALID_ARG;
     }
@@ -1281,7 +1316,21 @@ pp_status pp_plan_set_tuning(pp_plan* plan, int row_ifft_variant, int stencil_ki
                   "with nz = 128, ny in {128, 192, 256} and a device that fits 16-CTA clusters");
         return PP_ERR_UNSUPPORTED;
     }
+    if (row_ifft_variant == 8 && !(p.kind == PP_CARTESIAN && p.ndim == 2)) {
+        set_error("pp_plan_set_tuning: row variant 8 (coils split over 8-CTA clusters) applies to "
+                  "2-D Cartesian plans");
+        return PP_ERR_UNSUPPORTED;
+    }
     if (p.kind == PP_CARTESIAN && p.ndim == 3) p.tune_c3 = row_ifft_variant == 16;
+    if (p.kind == PP_CARTESIAN && p.ndim == 2) {
+        if (row_ifft_variant == -1 || row_ifft_variant == 16) {
+            set_error("pp_plan_set_tuning: 2-D Cartesian plans take row variant 1, 2, 4 or 8");
+            return PP_ERR_UNSUPPORTED;
+        }
+        p.tune_c2 = row_ifft_variant;
+        p.gkey.clear();
+        return PP_OK;
+    }
     if (row_ifft_variant == -1 && (p.kind != PP_NONCARTESIAN || !fft4_n2(p.G_x))) {
         set_error("pp_plan_set_tuning: the split row IFFT needs a non-Cartesian plan with a "
                   "register-FFT grid length");

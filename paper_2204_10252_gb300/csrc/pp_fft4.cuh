@@ -154,44 +154,37 @@ __device__ __forceinline__ void stage_s_tile(float2* dst, const float2* __restri
     asm volatile("cp.async.commit_group;\n" ::: "memory");
 }
 
-// Fused Cartesian normal-operator work item on the four-step FFT:
-//   out[:, col] = sc * sum_c conj(S_c) F^H (mask_fo . F (S_c x)) + alpha * operand
-// for TXF = 8 columns col0.. of an ny x nx image, ny = 16 * N2, transform
-// along y.  Forward: phase 1 by (m2, col) threads, phase 2 by (k1, col)
-// threads, which then hold X[k1 + 16 k2].  Inverse, with the mirrored
-// decomposition (input k = k1 + 16 k2, output m = N2 m1 + m2):
-//   I1 (same (k1, col) threads): inverse length-N2 DFT over k2, times
-//      W_n^(-m2 k1);   I2 ((m2, col) threads): inverse length-16 DFT over k1,
-// which leaves x'[N2 m1 + m2] with the thread that loaded S_c at those rows.
-// The coil maps' n x 8 tiles are double-buffered in shared memory: coil
-// c + 1's tile streams in by cp.async while coil c is transformed.
-// Shared memory: tws[n] twiddles, pm[n] mask (FFT order, 1/ny folded in),
-// Y[16 * N2 * 8], Sb[2 * n * 8].  Threads: 8 * max(16, N2); all threads
-// must call it.
+// Coil loop of the fused Cartesian item for coils c_first, c_first + c_step,
+// ... < C: acc[m1] (rows N2 m1 + r of column col0 + lane, threads r < N2)
+// accumulates conj(S_c) F^H (mask_fo . F (S_c x)).  Ends with a barrier.
 template <int N2>
-__device__ __forceinline__ void cart_item4(const float2* __restrict__ tws,
-                                           const float* __restrict__ pm, float2* Y, float2* Sb,
-                                           const float2* __restrict__ x,
-                                           const float2* __restrict__ sens, int C, int nx,
-                                           int col0, float2* out, float sc,
-                                           const float2* operand, float alpha) {
+__device__ __forceinline__ void cart_item4_acc(const float2* __restrict__ tws,
+                                               const float* __restrict__ pm, float2* Y, float2* Sb,
+                                               const float2* __restrict__ x,
+                                               const float2* __restrict__ sens, int C, int nx,
+                                               int col0, int c_first, int c_step, float2* acc) {
     constexpr int N1 = 16, n = N1 * N2;
     const int lane = threadIdx.x & 7, r = threadIdx.x >> 3, col = col0 + lane;
     const bool colok = col < nx;
     const bool p1 = r < N2, p2 = r < N1;
     const int64_t cs = (int64_t)n * nx;
-    float2 xr[N1], acc[N1];
-    stage_s_tile<N2>(Sb, sens, nx, col0);
+    float2 xr[N1];
 #pragma unroll
-    for (int m1 = 0; m1 < N1; ++m1) {
-        xr[m1] = (p1 && colok) ? x[(int64_t)(N2 * m1 + r) * nx + col] : make_float2(0.f, 0.f);
-        acc[m1] = make_float2(0.f, 0.f);
+    for (int m1 = 0; m1 < N1; ++m1) acc[m1] = make_float2(0.f, 0.f);
+    if (c_first >= C) {
+        __syncthreads();
+        return;
     }
-    for (int c = 0; c < C; ++c) {
-        const float2* St = Sb + (c & 1) * n * 8;
-        // the other buffer was last read in coil c - 1, before its final barrier
-        if (c + 1 < C)
-            stage_s_tile<N2>(Sb + ((c + 1) & 1) * n * 8, sens + (c + 1) * cs, nx, col0);
+    stage_s_tile<N2>(Sb, sens + c_first * cs, nx, col0);
+#pragma unroll
+    for (int m1 = 0; m1 < N1; ++m1)
+        xr[m1] = (p1 && colok) ? x[(int64_t)(N2 * m1 + r) * nx + col] : make_float2(0.f, 0.f);
+    int it = 0;
+    for (int c = c_first; c < C; c += c_step, ++it) {
+        const float2* St = Sb + (it & 1) * n * 8;
+        // the other buffer was last read in the previous coil, before its final barrier
+        if (c + c_step < C)
+            stage_s_tile<N2>(Sb + ((it + 1) & 1) * n * 8, sens + (c + c_step) * cs, nx, col0);
         else
             asm volatile("cp.async.commit_group;\n" ::: "memory");
         asm volatile("cp.async.wait_group 1;\n" ::: "memory");
@@ -234,7 +227,34 @@ __device__ __forceinline__ void cart_item4(const float2* __restrict__ tws,
         }
         __syncthreads();
     }
-    if (p1 && colok) {
+}
+
+// Fused Cartesian normal-operator work item on the four-step FFT:
+//   out[:, col] = sc * sum_c conj(S_c) F^H (mask_fo . F (S_c x)) + alpha * operand
+// for TXF = 8 columns col0.. of an ny x nx image, ny = 16 * N2, transform
+// along y.  Forward: phase 1 by (m2, col) threads, phase 2 by (k1, col)
+// threads, which then hold X[k1 + 16 k2].  Inverse, with the mirrored
+// decomposition (input k = k1 + 16 k2, output m = N2 m1 + m2):
+//   I1 (same (k1, col) threads): inverse length-N2 DFT over k2, times
+//      W_n^(-m2 k1);   I2 ((m2, col) threads): inverse length-16 DFT over k1,
+// which leaves x'[N2 m1 + m2] with the thread that loaded S_c at those rows.
+// The coil maps' n x 8 tiles are double-buffered in shared memory: coil
+// c + 1's tile streams in by cp.async while coil c is transformed.
+// Shared memory: tws[n] twiddles, pm[n] mask (FFT order, 1/ny folded in),
+// Y[16 * N2 * 8], Sb[2 * n * 8].  Threads: 8 * max(16, N2); all threads
+// must call it.
+template <int N2>
+__device__ __forceinline__ void cart_item4(const float2* __restrict__ tws,
+                                           const float* __restrict__ pm, float2* Y, float2* Sb,
+                                           const float2* __restrict__ x,
+                                           const float2* __restrict__ sens, int C, int nx,
+                                           int col0, float2* out, float sc,
+                                           const float2* operand, float alpha) {
+    constexpr int N1 = 16;
+    const int lane = threadIdx.x & 7, r = threadIdx.x >> 3, col = col0 + lane;
+    float2 acc[N1];
+    cart_item4_acc<N2>(tws, pm, Y, Sb, x, sens, C, nx, col0, 0, 1, acc);
+    if (r < N2 && col < nx) {
 #pragma unroll
         for (int m1 = 0; m1 < N1; ++m1) {
             const int64_t o = (int64_t)(N2 * m1 + r) * nx + col;

@@ -180,6 +180,7 @@ struct Plan {
     int c3cl_clusters = 0;      // 3-D: resident 16-CTA clusters of the one-kernel operator (0: n/a)
     int tune_c3 = 0;            // 3-D: 1 = one-kernel cluster operator, 0 = three passes per coil
     int pdl = 1;                // programmatic dependent launch in the solve's kernel chain
+    int tune_c2 = 1;            // 2-D Cartesian: CTAs per 8-column group (coils split over a cluster)
     std::vector<void*> allocs;
 };
 

@@ -422,6 +422,54 @@ cart2d4_normal_kernel(const float2* __restrict__ tw, const float2* __restrict__ 
                    scale, operand, alpha);
 }
 
+// The same with the coils split over a cluster of CL CTAs per 8-column
+// group (for images too narrow to fill the GPU with column groups alone):
+// CTA q takes coils q, q + CL, ...; the CL partial sums meet in distributed
+// shared memory, CTA q summing rows [q n / CL, (q + 1) n / CL) in rank order.
+// grid (CL * ceil(nx / 8)), cluster (CL, 1, 1).
+template <int N2>
+__global__ void __launch_bounds__(8 * tpr<N2>(), 2)
+cart2d4_cluster_kernel(const float2* __restrict__ tw, const float2* __restrict__ x,
+                       const float2* __restrict__ sens, int C, int nx,
+                       const float* __restrict__ mask_fo, float2* out, float scale,
+                       const float2* operand, float alpha) {
+    constexpr int n = N1 * N2;
+    __shared__ float2 tws[n];
+    __shared__ float pm[n];
+    __shared__ float2 Y[N1 * N2 * 8];
+    extern __shared__ float4 sb4[];
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int q = (int)cluster.block_rank(), CL = (int)cluster.num_blocks();
+    const int col0 = (int)(blockIdx.x / CL) * 8;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        tws[i] = tw[i];
+        pm[i] = mask_fo[i];
+    }
+    __syncthreads();
+    float2 acc[N1];
+    cart_item4_acc<N2>(tws, pm, Y, reinterpret_cast<float2*>(sb4), x, sens, C, nx, col0, q, CL, acc);
+    const int lane = threadIdx.x & 7, r = threadIdx.x >> 3;
+    if (r < N2) {
+#pragma unroll
+        for (int m1 = 0; m1 < N1; ++m1) Y[(N2 * m1 + r) * 8 + lane] = acc[m1];   // Y[row][lane]
+    }
+    cluster.sync();
+    const int rpr = n / CL;
+    for (int idx = threadIdx.x; idx < rpr * 8; idx += blockDim.x) {
+        const int row = q * rpr + (idx >> 3), l = idx & 7, col = col0 + l;
+        float2 v = cluster.map_shared_rank(Y, 0)[row * 8 + l];
+        for (int b = 1; b < CL; ++b) v = cadd(v, cluster.map_shared_rank(Y, b)[row * 8 + l]);
+        if (col < nx) {
+            const int64_t o = (int64_t)row * nx + col;
+            v = cscale(v, scale);
+            if (operand) v = cadd(v, cscale(operand[o], alpha));
+            out[o] = v;
+        }
+    }
+    cluster.sync();   // keep every CTA's partials alive until the others have read them
+}
+
 template <int N2> constexpr size_t cart4_dyn_smem() { return sizeof(float2) * 2 * 16 * N2 * 8; }
 
 // ---------------------------------------------------------------------------
@@ -662,6 +710,12 @@ pp_status prepare_cart4() {
                                      (int)cart4_dyn_smem<N2_>()));
     PP_P4(8) PP_P4(12) PP_P4(16) PP_P4(20) PP_P4(24)
 #undef PP_P4
+#define PP_P4C(N2_)                                                                               \
+    PP_TRY_CUDA(cudaFuncSetAttribute(cart2d4_cluster_kernel<N2_>,                                 \
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize,               \
+                                     (int)cart4_dyn_smem<N2_>()));
+    PP_P4C(8) PP_P4C(12) PP_P4C(16) PP_P4C(20) PP_P4C(24)
+#undef PP_P4C
     return PP_OK;
 }
 
@@ -671,6 +725,21 @@ pp_status launch_cart2d4_normal(const Plan& p, const float2* x, float2* out, flo
     const int n2 = fft4_n2(p.ny);
     if (!n2) return PP_OK;
     const int grid = (p.nx + 7) / 8;
+    const int CL = p.tune_c2;
+    if (CL == 2 || CL == 4 || CL == 8) {
+        cudaError_t e = cudaSuccess;
+#define PP_K4C(N2_)                                                                              \
+        if (n2 == N2_)                                                                           \
+            e = launch_ex(cart2d4_cluster_kernel<N2_>, dim3(grid * CL), dim3(8 * tpr<N2_>()),    \
+                          cart4_dyn_smem<N2_>(), st, false, CL, (const float2*)p.fy.tw, x,       \
+                          (const float2*)p.sens, p.C, p.nx, (const float*)p.mask_fo, out, scale, \
+                          operand, alpha);
+        PP_K4C(8) PP_K4C(12) PP_K4C(16) PP_K4C(20) PP_K4C(24)
+#undef PP_K4C
+        if (e != cudaSuccess) return cuda_status(e, "cart2d4_cluster_kernel launch");
+        *done = true;
+        return check4("cart2d4_cluster_kernel");
+    }
 #define PP_K4(N2_)                                                                                 \
     if (n2 == N2_)                                                                                 \
         cart2d4_normal_kernel<N2_><<<grid, 8 * tpr<N2_>(), cart4_dyn_smem<N2_>(), st>>>(           \

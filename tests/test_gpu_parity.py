@@ -202,6 +202,40 @@ def test_cart3d_cluster_operator(pp, case):
         plan.destroy()
 
 
+C2_CASES = [((128, 128), 8), ((192, 256), 3), ((384, 128), 5), ((256, 36), 16)]
+
+
+@pytest.mark.parametrize("case", range(len(C2_CASES)), ids=["128_c8", "192x256_c3", "384x128_c5",
+                                                           "256x36_c16"])
+def test_cart2d_coil_split_clusters(pp, case):
+    # Coils split over 1, 2, 4 or 8 CTAs per 8-column group (cluster partial
+    # sums); more CTAs than coils leaves some with no coil.  36 columns end
+    # inside a column group.
+    shape, C = C2_CASES[case]
+    sens = synth.coil_maps(shape, C, 600 + case)
+    mask = synth.line_mask(shape, 4, 8, 600 + case)
+    plan = pp.pp_plan_create(shape, C, dev(sens), mask=mask, seed=3, power_iters=0)
+    try:
+        x = synth.crandn(shape, 9)
+        op = synth.crandn(shape, 10)
+        L = 0.9
+        pp.pp_plan_set_scale(plan, L)
+        ref = O.cart_normal(x, sens, mask) / L
+        for cl in (1, 2, 4, 8):
+            pp.pp_plan_set_tuning(plan, cl, 0, 8)
+            assert pp.pp_plan_tuning(plan)[0] == cl
+            out = empty(shape)
+            pp.pp_normal_apply(plan, dev(x), out)
+            assert rel(host(out), ref) <= TOL_APPLY, cl
+            c = [float(v) for v in O.poly_coeffs_l2(2)]
+            out = empty(shape)
+            pp.pp_poly_apply(plan, c, 2, dev(op), out)
+            refp = O.horner_apply(c, lambda v: O.cart_normal(v, sens, mask) / L, op.astype(np.complex128))
+            assert rel(host(out), refp) <= TOL_APPLY, cl
+    finally:
+        plan.destroy()
+
+
 def test_forward_parity(pp, prob):
     x = synth.crandn(prob.shape, 1)
     y = empty(prob.kshape)
