@@ -343,6 +343,14 @@ __device__ __forceinline__ void ci_rows_inv_body(const float2* __restrict__ tw, 
                                                  float2* tws, float2* Y) {
     constexpr int n = N1 * N2, YP = ypitch<N2>();
     pdl_trigger();
+    {
+        // pull the CTA's 8-coil runs of the map row (a plan constant, read in
+        // the epilogue) into L2 while the previous kernel finishes: one
+        // 64-byte run, inside one 128-byte line, per image column
+        const float2* Srow = S + (int64_t)row * a.n * CP + cb * CB;
+        for (int i = threadIdx.x; i < a.n; i += blockDim.x)
+            asm volatile("prefetch.global.L2 [%0];\n" ::"l"(Srow + (int64_t)i * CP));
+    }
     for (int i = threadIdx.x; i < n; i += blockDim.x) tws[i] = tw[i];
     __syncthreads();
     pdl_wait();
