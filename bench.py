@@ -57,6 +57,11 @@ def parse():
                     choices=[WORKLOAD, "cart2d_128_c8", "cart3d_256x256x128_c32", "batched2d_64",
                              "unrolled2d_8x256_c16"],
                     help="benchmark line to produce (the default is the headline workload)")
+    ap.add_argument("--apply-only", type=int, default=0, metavar="K",
+                    help="profiling aid: build the headline workload's plan (no power iteration), "
+                         "apply its normal operator K times and exit without a bench line")
+    ap.add_argument("--tuning", default="",
+                    help="with --apply-only: row_ifft_variant,stencil_kind,stencil_coils to force")
     return ap.parse_args()
 
 
@@ -304,6 +309,23 @@ def main():
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
     c = cfg()
+    if args.apply_only:
+        # one plan, a forced launch shape, K normal-operator applies: a small,
+        # deterministic launch sequence for an ncu capture of one apply
+        sens = synth.coil_maps(c["shape"], c["coils"], c["seed"])
+        traj = synth.spiral_traj(c["interleaves"], c["samples"], c["turns"], c["shape"][1] / 2.0)
+        plan = pp.pp_plan_create(c["shape"], c["coils"], torch.from_numpy(sens).to(dev), traj=traj,
+                                 kb_width=c["kb_width"], oversamp=c["oversamp"], power_iters=0)
+        if args.tuning:
+            pp.pp_plan_set_tuning(plan, *[int(v) for v in args.tuning.split(",")])
+        xa = torch.from_numpy(synth.crandn(c["shape"], 3)).to(dev)
+        ya = torch.empty_like(xa)
+        for _ in range(args.apply_only):
+            pp.pp_normal_apply(plan, xa, ya)
+        torch.cuda.synchronize()
+        print(json.dumps({"apply_only": args.apply_only, "tuning": pp.pp_plan_tuning(plan)}))
+        plan.destroy()
+        return
     seed, sens, traj, x_true, noise = make_inputs(c, rank)
     shape, C, d, iters, lam = c["shape"], c["coils"], c["d"], c["iters"], c["lam"]
     K = len(traj)
