@@ -256,11 +256,13 @@ pp_status pp_batch_offsets(const pp_batch* batch, int64_t* image_off, int64_t* k
 pp_status pp_batch_scales(const pp_batch* batch, double* L);
 pp_status pp_batch_set_scales(pp_batch* batch, const double* L);
 /* autotuned column tile width and persistent grid size (either may be NULL);
- * a negative width -w means w columns per item on the register four-step
- * FFT kernel, a positive one the shared-memory Stockham kernel */
+ * a positive width is the shared-memory Stockham kernel's columns per item;
+ * -8, -16, -32 mean the register four-step FFT kernel on 8-column items
+ * with 1, 2 or 4 CTAs per item (the item's coils split over a thread-block
+ * cluster) */
 pp_status pp_batch_tile(const pp_batch* batch, int* cols_per_cta, int* persistent_ctas);
-/* override the autotuner: 4, 8 or 16 (Stockham) or -8 (register four-step,
- * every slice length must be 16 * {8, 12, 16, 20, 24}) */
+/* override the autotuner: 4, 8 or 16 (Stockham) or -8, -16, -32 (register
+ * four-step, every slice length must be 16 * {8, 12, 16, 20, 24}) */
 pp_status pp_batch_set_tile(pp_batch* batch, int cols_per_cta);
 /* per-slice A x and A^H y (one launch sequence per slice; set-up work) */
 pp_status pp_batch_forward_apply(const pp_batch* batch, const pp_c64* x, pp_c64* y, pp_stream stream);

@@ -29,6 +29,7 @@ struct BatchDev {
     int2* items = nullptr;   // (slice, first column), most expensive first
     int nitems = 0, ny_max = 0, km = 0, lgt = 3, grid = 0;
     int fast4 = 0;           // 1: the four-step register-FFT kernel runs the items
+    int cl = 1;              // fast4: CTAs per item, the item's coils split over a cluster
     Segments img, ksp, tiles;
 };
 

@@ -7,6 +7,8 @@
 
 #include <algorithm>
 
+#include <cooperative_groups.h>
+
 #include "pp_batch.h"
 #include "pp_fft4.cuh"
 
@@ -432,6 +434,84 @@ cart2d_batch4_kernel(const SliceDesc* __restrict__ descs, const int2* __restrict
     }
 }
 
+// One item of cart2d_batch4_cl_kernel: CTA q of the cluster runs coils q,
+// q + CL, ... of the slice; the partial sums meet in distributed shared
+// memory and CTA q writes rows [q n / CL, (q + 1) n / CL) (sum in rank order).
+template <int N2>
+__device__ __forceinline__ void batch_item_cl(const float2* tws, const float* pm, float2* Y, float2* Sb,
+                                              const SliceDesc& D, int col0, const float2* xs,
+                                              float2* os, float sc, const float2* ops, float alpha,
+                                              int q, int CL) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    constexpr int n = 16 * N2;
+    float2 acc[16];
+    cart_item4_acc<N2>(tws, pm, Y, Sb, xs, D.sens, D.C, D.nx, col0, q, CL, acc);
+    const int lane = threadIdx.x & 7, r = threadIdx.x >> 3;
+    if (r < N2) {
+#pragma unroll
+        for (int m1 = 0; m1 < 16; ++m1) Y[(N2 * m1 + r) * 8 + lane] = acc[m1];
+    }
+    cluster.sync();
+    const int rpr = n / CL;
+    for (int idx = threadIdx.x; idx < rpr * 8; idx += blockDim.x) {
+        const int row = q * rpr + (idx >> 3), l = idx & 7, col = col0 + l;
+        float2 v = cluster.map_shared_rank(Y, 0)[row * 8 + l];
+        for (int b = 1; b < CL; ++b) v = cadd(v, cluster.map_shared_rank(Y, b)[row * 8 + l]);
+        if (col < D.nx) {
+            const int64_t o = (int64_t)row * D.nx + col;
+            v = cscale(v, sc);
+            if (ops) v = cadd(v, cscale(ops[o], alpha));
+            os[o] = v;
+        }
+    }
+    cluster.sync();   // Y is rewritten by the next item only after every CTA has read it
+}
+
+// cart2d_batch4_kernel with the coils of every item split over a cluster of
+// CL CTAs (batches with fewer column items than resident CTAs).
+// grid CL * clusters, cluster (CL, 1, 1); the clusters walk the item list.
+__global__ void __launch_bounds__(192, 2)
+cart2d_batch4_cl_kernel(const SliceDesc* __restrict__ descs, const int2* __restrict__ items,
+                        int nitems, const float2* __restrict__ x, float2* out, float coef,
+                        const float2* operand, float alpha) {
+    __shared__ float2 tws[384];
+    __shared__ float pm[384];
+    __shared__ float2 Y[16 * 24 * 8];
+    extern __shared__ float4 sb4[];
+    float2* Sb = reinterpret_cast<float2*>(sb4);
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int q = (int)cluster.block_rank(), CL = (int)cluster.num_blocks();
+    const int cid = blockIdx.x / CL, ncid = gridDim.x / CL;
+    int cur = -1;
+    for (int it = cid; it < nitems; it += ncid) {
+        const int2 item = items[it];
+        const int s = item.x;
+        const SliceDesc D = descs[s];
+        if (s != cur) {
+            __syncthreads();
+            for (int i = threadIdx.x; i < D.ny; i += blockDim.x) {
+                tws[i] = D.tw[i];
+                pm[i] = D.mask_fo[i];
+            }
+            __syncthreads();
+            cur = s;
+        }
+        const float2* xs = x + D.img_off;
+        float2* os = out + D.img_off;
+        const float2* ops = operand ? operand + D.img_off : nullptr;
+        const float sc = coef * D.invL;
+        switch (D.n2) {
+            case 8: batch_item_cl<8>(tws, pm, Y, Sb, D, item.y, xs, os, sc, ops, alpha, q, CL); break;
+            case 12: batch_item_cl<12>(tws, pm, Y, Sb, D, item.y, xs, os, sc, ops, alpha, q, CL); break;
+            case 16: batch_item_cl<16>(tws, pm, Y, Sb, D, item.y, xs, os, sc, ops, alpha, q, CL); break;
+            case 20: batch_item_cl<20>(tws, pm, Y, Sb, D, item.y, xs, os, sc, ops, alpha, q, CL); break;
+            default: batch_item_cl<24>(tws, pm, Y, Sb, D, item.y, xs, os, sc, ops, alpha, q, CL); break;
+        }
+    }
+}
+
 }  // namespace
 
 extern thread_local int64_t g_launches;
@@ -481,6 +561,8 @@ int batch4_grid() {
     int occ = 0, nsm = 0;
     cudaFuncSetAttribute(cart2d_batch4_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)kBatch4Dyn);
+    cudaFuncSetAttribute(cart2d_batch4_cl_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kBatch4Dyn);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, cart2d_batch4_kernel, 192, kBatch4Dyn) !=
         cudaSuccess)
         occ = 1;
@@ -490,6 +572,13 @@ int batch4_grid() {
 
 pp_status launch_batch_normal(const BatchDev& b, const float2* x, float2* out, float coef,
                               const float2* operand, float alpha, cudaStream_t st) {
+    if (b.fast4 && b.cl > 1) {
+        const int ncl = std::max(1, std::min(b.grid / b.cl, b.nitems));
+        PP_TRY_CUDA(launch_ex(cart2d_batch4_cl_kernel, dim3(ncl * b.cl), dim3(192), kBatch4Dyn, st,
+                              false, b.cl, (const SliceDesc*)b.descs, (const int2*)b.items, b.nitems,
+                              x, out, coef, operand, alpha));
+        return check_launch_b("cart2d_batch4_cl_kernel");
+    }
     if (b.fast4) {
         cart2d_batch4_kernel<<<std::min(b.grid, b.nitems), 192, kBatch4Dyn, st>>>(
             b.descs, b.items, b.nitems, x, out, coef, operand, alpha);

@@ -820,7 +820,7 @@ static pp_status upload_descs(Batch& b) {
 // and keep the fastest.
 static pp_status autotune(Batch& b, cudaStream_t st) {
     std::vector<int2> items;
-    int best = -1;
+    int best = -1, best_cl = 1;
     float best_ms = 1e30f;
     cudaEvent_t e0, e1;
     PP_TRY_CUDA(cudaEventCreate(&e0));
@@ -829,29 +829,35 @@ static pp_status autotune(Batch& b, cudaStream_t st) {
     for (const SliceDesc& d : b.hdesc) all_fast = all_fast && d.n2 != 0;
     // candidates: Stockham kernels with 4, 8 or 16 columns per item (lgt 2..4)
     // and, when every slice length has one, the register four-step kernel (5)
-    for (int lgt = 2; lgt <= 5; ++lgt) {
-        if (lgt == 5) {
-            if (!all_fast) continue;
-            PP_TRY(set_items(b, 3, &items));
-            b.dev.fast4 = 1;
-            b.dev.grid = batch4_grid();
-        } else {
-            if (!km_for(b.dev.ny_max, lgt)) continue;
-            b.dev.fast4 = 0;
-            PP_TRY(set_items(b, lgt, &items));
+    // with 1, 2 or 4 CTAs per item (coils split over a cluster)
+    for (int lgt = 2; lgt <= 5; ++lgt)
+        for (int cl : {1, 2, 4}) {
+            if (lgt < 5 && cl > 1) continue;
+            if (lgt == 5) {
+                if (!all_fast) continue;
+                PP_TRY(set_items(b, 3, &items));
+                b.dev.fast4 = 1;
+                b.dev.cl = cl;
+                b.dev.grid = batch4_grid();
+            } else {
+                if (!km_for(b.dev.ny_max, lgt)) continue;
+                b.dev.fast4 = 0;
+                b.dev.cl = 1;
+                PP_TRY(set_items(b, lgt, &items));
+            }
+            PP_TRY(launch_batch_normal(b.dev, b.v, b.t, 1.f, nullptr, 0.f, st));
+            PP_TRY_CUDA(cudaEventRecord(e0, st));
+            for (int r = 0; r < 3; ++r) PP_TRY(launch_batch_normal(b.dev, b.v, b.t, 1.f, nullptr, 0.f, st));
+            PP_TRY_CUDA(cudaEventRecord(e1, st));
+            PP_TRY_CUDA(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = lgt;
+                best_cl = cl;
+            }
         }
-        PP_TRY(launch_batch_normal(b.dev, b.v, b.t, 1.f, nullptr, 0.f, st));
-        PP_TRY_CUDA(cudaEventRecord(e0, st));
-        for (int r = 0; r < 3; ++r) PP_TRY(launch_batch_normal(b.dev, b.v, b.t, 1.f, nullptr, 0.f, st));
-        PP_TRY_CUDA(cudaEventRecord(e1, st));
-        PP_TRY_CUDA(cudaEventSynchronize(e1));
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < best_ms) {
-            best_ms = ms;
-            best = lgt;
-        }
-    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (best < 0) {
@@ -861,10 +867,12 @@ static pp_status autotune(Batch& b, cudaStream_t st) {
     if (best == 5) {
         PP_TRY(set_items(b, 3, &items));
         b.dev.fast4 = 1;
+        b.dev.cl = best_cl;
         b.dev.grid = batch4_grid();
         return PP_OK;
     }
     b.dev.fast4 = 0;
+    b.dev.cl = 1;
     return set_items(b, best, &items);
 }
 
@@ -1747,7 +1755,8 @@ pp_status pp_batch_tile(const pp_batch* batch, int* cols_per_cta, int* persisten
         set_error("pp_batch_tile: NULL batch");
         return PP_ERR_INVALID_ARG;
     }
-    if (cols_per_cta) *cols_per_cta = batch->impl.dev.fast4 ? -8 : 1 << batch->impl.dev.lgt;
+    if (cols_per_cta)
+        *cols_per_cta = batch->impl.dev.fast4 ? -8 * batch->impl.dev.cl : 1 << batch->impl.dev.lgt;
     if (persistent_ctas) *persistent_ctas = batch->impl.dev.grid;
     return PP_OK;
 }
@@ -1759,7 +1768,7 @@ pp_status pp_batch_set_tile(pp_batch* batch, int cols_per_cta) {
     }
     Batch& b = batch->impl;
     std::vector<int2> items;
-    if (cols_per_cta == -8) {
+    if (cols_per_cta == -8 || cols_per_cta == -16 || cols_per_cta == -32) {
         for (const SliceDesc& d : b.hdesc)
             if (!d.n2) {
                 set_error("pp_batch_set_tile: slice length %d has no register FFT kernel", d.ny);
@@ -1767,8 +1776,10 @@ pp_status pp_batch_set_tile(pp_batch* batch, int cols_per_cta) {
             }
         PP_TRY(set_items(b, 3, &items));
         b.dev.fast4 = 1;
+        b.dev.cl = -cols_per_cta / 8;
         b.dev.grid = batch4_grid();
     } else {
+        b.dev.cl = 1;
         const int lgt = cols_per_cta == 4 ? 2 : cols_per_cta == 8 ? 3 : cols_per_cta == 16 ? 4 : -1;
         if (lgt < 0 || !km_for(b.dev.ny_max, lgt)) {
             set_error("pp_batch_set_tile: unsupported tile width %d", cols_per_cta);
