@@ -115,8 +115,9 @@ pp_status pp_plan_sizes(const pp_plan* plan, int64_t* image_elems, int64_t* kspa
  *    normal operator (1, 2 or 4 = CTAs per image row, coil groups reduced
  *    through distributed shared memory; -1 = one IFFT per coil and row
  *    followed by a coil sum); for 3-D Cartesian plans 16 = the whole normal
- *    operator as one kernel on 16-CTA clusters (nz = 128, ny in {128, 192,
- *    256}), 1 = three passes per coil; for 2-D Cartesian plans 1, 2, 4 or 8
+ *    operator as one kernel on 16-CTA clusters, 4 x columns per cluster task
+ *    (nz = 128, ny in {128, 192, 256}), -16 = the same with 2 columns per
+ *    task and two CTAs per SM, 1 = three passes per coil; for 2-D Cartesian plans 1, 2, 4 or 8
  *    = CTAs per 8-column group, the coils split over a cluster of that size;
  *  - stencil_kind: the G^T G stencil kernel (0 = one output per thread,
  *    1 = two outputs per thread, both staging one coil at a time with

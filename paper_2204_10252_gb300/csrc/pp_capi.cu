@@ -160,7 +160,10 @@ static pp_status normal_into(const Plan& p, const float2* x, float2* out, float 
     if (p.kind == PP_CARTESIAN && p.ndim == 2)
         return launch_cart2d_normal(p, x, out, scale, operand, alpha, st);
     if (p.kind == PP_CARTESIAN) {
-        if (p.tune_c3 && p.c3cl_clusters > 0) return c3cl_normal(p, x, out, scale, operand, alpha, st);
+        if (p.tune_c3 == 1 && p.c3cl_clusters > 0)
+            return c3cl_normal(p, 4, x, out, scale, operand, alpha, st);
+        if (p.tune_c3 == 2 && p.c3cl2_clusters > 0)
+            return c3cl_normal(p, 2, x, out, scale, operand, alpha, st);
         bool done = false;
         PP_TRY(cart3d4_normal(p, x, out, scale, operand, alpha, p.wk_a, st, &done));
         if (done) return PP_OK;
@@ -552,15 +555,18 @@ static pp_status tune_noncartesian(Plan& p, cudaStream_t st) {
 // per coil, timed on the plan's buffers (two rounds of 3 applies after one
 // warm-up); the faster is kept.
 static pp_status tune_cart3d(Plan& p, cudaStream_t st) {
-    if (p.c3cl_clusters <= 0) return PP_OK;
+    if (p.c3cl_clusters <= 0 && p.c3cl2_clusters <= 0) return PP_OK;
     cudaEvent_t e0, e1;
     PP_TRY_CUDA(cudaEventCreate(&e0));
     PP_TRY_CUDA(cudaEventCreate(&e1));
     PP_TRY_CUDA(cudaMemsetAsync(p.v, 0, sizeof(float2) * (size_t)p.nimg, st));
-    float best[2] = {1e30f, 1e30f};
+    std::vector<int> cand = {0};
+    if (p.c3cl_clusters > 0) cand.push_back(1);
+    if (p.c3cl2_clusters > 0) cand.push_back(2);
+    std::vector<float> best(cand.size(), 1e30f);
     for (int round = 0; round < 2; ++round)
-        for (int cand = 0; cand < 2; ++cand) {
-            p.tune_c3 = cand;
+        for (size_t i = 0; i < cand.size(); ++i) {
+            p.tune_c3 = cand[i];
             PP_TRY(normal_into(p, p.v, p.t, 1.f, nullptr, 0.f, st));
             PP_TRY_CUDA(cudaEventRecord(e0, st));
             for (int r = 0; r < 3; ++r) PP_TRY(normal_into(p, p.v, p.t, 1.f, nullptr, 0.f, st));
@@ -568,9 +574,9 @@ static pp_status tune_cart3d(Plan& p, cudaStream_t st) {
             PP_TRY_CUDA(cudaEventSynchronize(e1));
             float ms = 0.f;
             PP_TRY_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-            best[cand] = std::min(best[cand], ms);
+            best[i] = std::min(best[i], ms);
         }
-    p.tune_c3 = best[1] < best[0] ? 1 : 0;
+    p.tune_c3 = cand[std::min_element(best.begin(), best.end()) - best.begin()];
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return PP_OK;
@@ -1242,7 +1248,8 @@ pp_status pp_plan_create(pp_plan** out, pp_dims dims, int coils, const pp_c64* s
     }
     if (rc == PP_OK && p.kind == PP_CARTESIAN && p.ndim == 2) rc = tune_cart2d(p, st);
     if (rc == PP_OK && p.kind == PP_CARTESIAN && p.ndim == 3) {
-        p.c3cl_clusters = c3cl_prepare(p);
+        p.c3cl_clusters = c3cl_prepare(p, 4);
+        p.c3cl2_clusters = c3cl_prepare(p, 2);
         rc = tune_cart3d(p, st);
     }
     if (rc == PP_OK && p.kind == PP_NONCARTESIAN) rc = setup_ci(p, st);
@@ -1299,7 +1306,7 @@ pp_status pp_plan_tuning(const pp_plan* plan, int* row_ifft_variant, int* stenci
     if (row_ifft_variant) {
         const Plan& p = plan->impl;
         if (p.kind == PP_CARTESIAN && p.ndim == 3)
-            *row_ifft_variant = p.tune_c3 ? 16 : 1;
+            *row_ifft_variant = p.tune_c3 == 1 ? 16 : (p.tune_c3 == 2 ? -16 : 1);
         else if (p.kind == PP_CARTESIAN)
             *row_ifft_variant = p.tune_c2;
         else
@@ -1312,14 +1319,16 @@ pp_status pp_plan_tuning(const pp_plan* plan, int* row_ifft_variant, int* stenci
 
 pp_status pp_plan_set_tuning(pp_plan* plan, int row_ifft_variant, int stencil_kind, int stencil_coils) {
     if (!plan || !(row_ifft_variant == 1 || row_ifft_variant == 2 || row_ifft_variant == 4 ||
-                   row_ifft_variant == -1 || row_ifft_variant == 8 || row_ifft_variant == 16) ||
+                   row_ifft_variant == -1 || row_ifft_variant == 8 || row_ifft_variant == 16 ||
+                   row_ifft_variant == -16) ||
         stencil_kind < 0 || stencil_kind > 9 || stencil_coils < 1 || stencil_coils > 64) {
-        set_error("pp_plan_set_tuning: row variant must be 1, 2, 4, 8, -1 or 16; stencil kind 0..9; "
+        set_error("pp_plan_set_tuning: row variant must be 1, 2, 4, 8, -1, 16 or -16; stencil kind 0..9; "
                   "stencil coils 1..64");
         return PP_ERR_INVALID_ARG;
     }
     Plan& p = plan->impl;
-    if (row_ifft_variant == 16 && p.c3cl_clusters <= 0) {
+    if ((row_ifft_variant == 16 && p.c3cl_clusters <= 0) ||
+        (row_ifft_variant == -16 && p.c3cl2_clusters <= 0)) {
         set_error("pp_plan_set_tuning: the one-kernel cluster operator needs a 3-D Cartesian plan "
                   "with nz = 128, ny in {128, 192, 256} and a device that fits 16-CTA clusters");
         return PP_ERR_UNSUPPORTED;
@@ -1329,9 +1338,10 @@ pp_status pp_plan_set_tuning(pp_plan* plan, int row_ifft_variant, int stencil_ki
                   "2-D Cartesian plans");
         return PP_ERR_UNSUPPORTED;
     }
-    if (p.kind == PP_CARTESIAN && p.ndim == 3) p.tune_c3 = row_ifft_variant == 16;
+    if (p.kind == PP_CARTESIAN && p.ndim == 3)
+        p.tune_c3 = row_ifft_variant == 16 ? 1 : (row_ifft_variant == -16 ? 2 : 0);
     if (p.kind == PP_CARTESIAN && p.ndim == 2) {
-        if (row_ifft_variant == -1 || row_ifft_variant == 16) {
+        if (row_ifft_variant == -1 || row_ifft_variant == 16 || row_ifft_variant == -16) {
             set_error("pp_plan_set_tuning: 2-D Cartesian plans take row variant 1, 2, 4 or 8");
             return PP_ERR_UNSUPPORTED;
         }

@@ -177,8 +177,10 @@ struct Plan {
                                 // a 1- / 2-row coil-lane or a coil-pair stencil
     int tune_stencil_cpc = 0;   // coils per CTA of kinds 0 and 1
     int stencil_rb_grid[4] = {0, 0, 0, 0};   // persistent grid of kinds 2..5 (0: unavailable)
-    int c3cl_clusters = 0;      // 3-D: resident 16-CTA clusters of the one-kernel operator (0: n/a)
-    int tune_c3 = 0;            // 3-D: 1 = one-kernel cluster operator, 0 = three passes per coil
+    int c3cl_clusters = 0;      // 3-D: resident 16-CTA clusters of the one-kernel operator, 4 columns
+    int c3cl2_clusters = 0;     //      the same with 2 columns per task (0: n/a)
+    int tune_c3 = 0;            // 3-D: 0 = three passes per coil, 1 / 2 = one-kernel cluster operator
+                                //      with 4 / 2 columns per task
     int pdl = 1;                // programmatic dependent launch in the solve's kernel chain
     int tune_c2 = 1;            // 2-D Cartesian: CTAs per 8-column group (coils split over a cluster)
     std::vector<void*> allocs;
@@ -241,8 +243,8 @@ pp_status launch_nufft_spread(const Plan& p, const float2* ksp, float2* grid_out
 pp_status launch_gtg_stencil(const Plan& p, const float2* grid_in, float2* grid_out, cudaStream_t st);
 pp_status prepare_gtg_stencil(Plan& p);
 pp_status prepare_cart4();
-int c3cl_prepare(const Plan& p);
-pp_status c3cl_normal(const Plan& p, const float2* x, float2* out, float scale,
+int c3cl_prepare(const Plan& p, int xb);
+pp_status c3cl_normal(const Plan& p, int xb, const float2* x, float2* out, float scale,
                       const float2* operand, float alpha, cudaStream_t st);
 bool ci_supported(const Plan& p);
 size_t ci_grid_elems(const Plan& p);

@@ -182,22 +182,23 @@ def test_cart3d_cluster_operator(pp, case):
         L = 1.7
         pp.pp_plan_set_scale(plan, L)
         ref = O.cart_normal(x, sens, mask) / L
-        for rv in (16, 1):
+        for rv in (16, -16, 1):
             try:
                 pp.pp_plan_set_tuning(plan, rv, 0, 8)
             except pp.PPError:
-                assert rv == 16
+                assert rv in (16, -16)
                 pytest.skip("no 16-CTA cluster fits this device")
             out = empty(shape)
             pp.pp_normal_apply(plan, dev(x), out)
             assert rel(host(out), ref) <= TOL_APPLY, rv
-        # the Horner axpy epilogue (operand, alpha) through the cluster kernel
-        pp.pp_plan_set_tuning(plan, 16, 0, 8)
+        # the Horner axpy epilogue (operand, alpha) through the cluster kernels
         c = [float(v) for v in O.poly_coeffs_l2(2)]
-        out = empty(shape)
-        pp.pp_poly_apply(plan, c, 2, dev(op), out)
         refp = O.horner_apply(c, lambda v: O.cart_normal(v, sens, mask) / L, op.astype(np.complex128))
-        assert rel(host(out), refp) <= TOL_APPLY
+        for rv in (16, -16):
+            pp.pp_plan_set_tuning(plan, rv, 0, 8)
+            out = empty(shape)
+            pp.pp_poly_apply(plan, c, 2, dev(op), out)
+            assert rel(host(out), refp) <= TOL_APPLY, rv
     finally:
         plan.destroy()
 
