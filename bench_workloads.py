@@ -115,6 +115,12 @@ def cart3d(args, pp, rank, world, local):
     gbs = bytes_apply / (ms / args.steps / 1e3) / 1e9
     peak, src = _hbm_peak()
     stages = pp.pp_profile_normal(plan, x, y, reps=2)
+    # the 3-D Haar prox of the solve (2 levels, 4x4x4 tiles) on the same image:
+    # one read and one write of the 67 MB volume per call, HBM-bound
+    prox_ms, _ = _timed(lambda: pp.pp_prox_l1_haar(shape, 2, float(c["lam"]), x, y), args.steps, dev,
+                        local)
+    prox_bytes = 16.0 * n
+    prox_gbs = prox_bytes / (prox_ms / args.steps / 1e3) / 1e9
     plan.destroy()
     return _base(args, world, "A^H A applies/s (3-D Cartesian normal operator)", "applies/s",
                  bench.job_throughput(args.steps, world, ms / 1e3), ms / args.steps,
@@ -125,7 +131,10 @@ def cart3d(args, pp, rank, world, local):
                                "peak": peak, "unit": "GB/s", "frac": gbs / peak, "traffic": None,
                                "peak_source": src,
                                "algorithmic_bytes_per_apply": bytes_apply},
-                  "stage_ms_per_apply": stages})
+                  "stage_ms_per_apply": stages,
+                  "prox": {"kernel": "prox3q_kernel", "bound": "hbm", "achieved": prox_gbs, "peak": peak,
+                           "unit": "GB/s", "frac": prox_gbs / peak, "bytes_per_call": prox_bytes,
+                           "ms_per_call": prox_ms / args.steps}})
 
 
 def batched(args, pp, rank, world, local):

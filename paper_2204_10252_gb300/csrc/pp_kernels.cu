@@ -1144,6 +1144,130 @@ prox_fista2q_kernel(int nx, int ny, float lam, float gamma, float beta, float2* 
     }
 }
 
+// 3-D, 2-level Haar prox with eight threads per 4x4x4 tile: a thread owns one
+// 2x2x2 block (level 1 in registers); the level-2 transform of the tile's
+// eight approximation coefficients runs across the eight threads with
+// shuffles (x partner lane ^ 1, y partner lane ^ 8, z partner lane ^ 16), in
+// haar2x2x2's operation order.  A warp covers 8 block columns x 2 block rows
+// x 2 block planes.  Needs nx % 16 == 0 and ny, nz % 4 == 0.
+__device__ __forceinline__ float2 haar3_l2_shfl(float2 a, int qx, int qy, int qz) {
+    float2 p;
+    p.x = __shfl_xor_sync(0xffffffffu, a.x, 1);
+    p.y = __shfl_xor_sync(0xffffffffu, a.y, 1);
+    const float2 t = qx ? csub(p, a) : cadd(a, p);
+    float2 u;
+    u.x = __shfl_xor_sync(0xffffffffu, t.x, 8);
+    u.y = __shfl_xor_sync(0xffffffffu, t.y, 8);
+    const float2 v = cscale(qy ? csub(u, t) : cadd(t, u), 0.5f);
+    float2 w;
+    w.x = __shfl_xor_sync(0xffffffffu, v.x, 16);
+    w.y = __shfl_xor_sync(0xffffffffu, v.y, 16);
+    return cscale(qz ? csub(w, v) : cadd(v, w), 0.70710678118654752f);
+}
+
+// FISTA = false: out = prox(in).  FISTA = true: the fused step of
+// prox_fista_kernel with z read from `in` and written to `out` (same array).
+template <bool FISTA>
+__global__ void __launch_bounds__(kThreads)
+prox3q_kernel(int nx, int ny, int nz, float lam, float gamma, float beta, const float2* in,
+              const float2* __restrict__ u, float2* out, float2* __restrict__ y,
+              const float2* __restrict__ ref, double* __restrict__ hist) {
+    pdl_trigger();
+    pdl_wait();
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31, qx = lane & 1, qy = (lane >> 3) & 1, qz = lane >> 4;
+    const int nwx = nx / 16, nwy = ny / 4;
+    const int64_t W = g >> 5;
+    const bool ok = W < (int64_t)nwx * nwy * (nz / 4);   // warp-uniform
+    double dd = 0.0, yy = 0.0, rr = 0.0;
+    if (ok) {
+        const int wx = (int)(W % nwx);
+        const int64_t rest = W / nwx;
+        const int wy = (int)(rest % nwy), wz = (int)(rest / nwy);
+        const int bx = 8 * wx + (lane & 7), by = 2 * wy + qy, bz = 2 * wz + qz;
+        int64_t o[4];
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+#pragma unroll
+            for (int j = 0; j < 2; ++j)
+                o[k * 2 + j] = ((int64_t)(2 * bz + k) * ny + (2 * by + j)) * nx + 2 * bx;
+        float2 t[8];   // [z][y][x]
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float4 a = *reinterpret_cast<const float4*>(in + o[q]);
+            float2 e0 = make_float2(a.x, a.y), e1 = make_float2(a.z, a.w);
+            if (FISTA) {
+                const float4 b = *reinterpret_cast<const float4*>(u + o[q]);
+                e0 = make_float2(a.x - gamma * b.x, a.y - gamma * b.y);
+                e1 = make_float2(a.z - gamma * b.z, a.w - gamma * b.w);
+            }
+            t[2 * q] = e0;
+            t[2 * q + 1] = e1;
+        }
+        haar2x2x2(t);
+        t[0] = haar3_l2_shfl(t[0], qx, qy, qz);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) t[q] = soft(t[q], lam);
+        t[0] = haar3_l2_shfl(t[0], qx, qy, qz);
+        haar2x2x2(t);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (FISTA) {
+                const float4 yo4 = *reinterpret_cast<const float4*>(y + o[q]);
+                const float2 yo[2] = {make_float2(yo4.x, yo4.y), make_float2(yo4.z, yo4.w)};
+                float2 zn[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const float2 yn = t[2 * q + h];
+                    const float2 df = csub(yn, yo[h]);
+                    zn[h] = make_float2(yn.x + beta * df.x, yn.y + beta * df.y);
+                    dd += (double)df.x * df.x + (double)df.y * df.y;
+                    yy += (double)yn.x * yn.x + (double)yn.y * yn.y;
+                }
+                if (ref) {
+                    const float4 rv = *reinterpret_cast<const float4*>(ref + o[q]);
+                    const double e0 = (double)t[2 * q].x - rv.x, e1 = (double)t[2 * q].y - rv.y;
+                    const double e2 = (double)t[2 * q + 1].x - rv.z, e3 = (double)t[2 * q + 1].y - rv.w;
+                    rr += e0 * e0 + e1 * e1 + e2 * e2 + e3 * e3;
+                }
+                *reinterpret_cast<float4*>(out + o[q]) = make_float4(zn[0].x, zn[0].y, zn[1].x, zn[1].y);
+                *reinterpret_cast<float4*>(y + o[q]) =
+                    make_float4(t[2 * q].x, t[2 * q].y, t[2 * q + 1].x, t[2 * q + 1].y);
+            } else {
+                *reinterpret_cast<float4*>(out + o[q]) =
+                    make_float4(t[2 * q].x, t[2 * q].y, t[2 * q + 1].x, t[2 * q + 1].y);
+            }
+        }
+    }
+    if (FISTA && hist) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            dd += __shfl_down_sync(0xffffffffu, dd, off);
+            yy += __shfl_down_sync(0xffffffffu, yy, off);
+            rr += __shfl_down_sync(0xffffffffu, rr, off);
+        }
+        __shared__ double sd[kThreads / 32], sy[kThreads / 32], sr[kThreads / 32];
+        const int wid = threadIdx.x >> 5;
+        if (lane == 0) {
+            sd[wid] = dd;
+            sy[wid] = yy;
+            sr[wid] = rr;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+            for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+                s0 += sd[i];
+                s1 += sy[i];
+                s2 += sr[i];
+            }
+            atomicAdd(&hist[0], s0);
+            atomicAdd(&hist[1], s1);
+            atomicAdd(&hist[2], s2);
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // FP64 reductions (deterministic: fixed grid, per-block partials, one
 // finishing block).  partial layout [nblocks][3] = Re<a,b>, Im<a,b>, |b|^2.
@@ -1485,6 +1609,15 @@ pp_status launch_prox(int ndim, int nx, int ny, int nz, int levels, float lambda
     const int64_t ntiles = (int64_t)(nx / ts) * (ny / ts) * (ndim == 3 ? nz / ts : 1);
     const int blocks = (int)((ntiles + kThreads - 1) / kThreads);
     if (blocks == 0) return PP_OK;
+    if (ndim == 3 && levels == 2 && nx % 16 == 0 && ny % 4 == 0 && nz % 4 == 0 &&
+        ((uintptr_t)in & 15) == 0 && ((uintptr_t)out & 15) == 0) {
+        const int64_t nthr = (int64_t)nx * ny * nz / 8;
+        PP_TRY_CUDA(launch_ex(prox3q_kernel<false>, dim3((unsigned)((nthr + kThreads - 1) / kThreads)),
+                              dim3(kThreads), 0, st, false, 0, nx, ny, nz, lambda, 0.f, 0.f, in,
+                              (const float2*)nullptr, out, (float2*)nullptr, (const float2*)nullptr,
+                              (double*)nullptr));
+        return check_launch("prox3q_kernel");
+    }
     if (ndim == 2 && levels == 1) prox_kernel<2, 1><<<blocks, kThreads, 0, st>>>(nx, ny, nz, lambda, in, out);
     else if (ndim == 2) prox_kernel<2, 2><<<blocks, kThreads, 0, st>>>(nx, ny, nz, lambda, in, out);
     else if (levels == 1) prox_kernel<3, 1><<<blocks, kThreads, 0, st>>>(nx, ny, nz, lambda, in, out);
@@ -1498,6 +1631,14 @@ pp_status launch_prox_fista(const Plan& p, int levels, float lambda, float gamma
     const int64_t ntiles = (int64_t)(p.nx / ts) * (p.ny / ts) * (p.ndim == 3 ? p.nz / ts : 1);
     const int blocks = (int)((ntiles + kThreads - 1) / kThreads);
     const bool pdl = p.pdl != 0;
+    if (p.ndim == 3 && levels == 2 && p.nx % 16 == 0 && p.ny % 4 == 0 && p.nz % 4 == 0 &&
+        ((uintptr_t)ref & 15) == 0 && ((uintptr_t)u & 15) == 0) {
+        const int64_t nthr = (int64_t)p.nx * p.ny * p.nz / 8;
+        PP_TRY_CUDA(launch_ex(prox3q_kernel<true>, dim3((unsigned)((nthr + kThreads - 1) / kThreads)),
+                              dim3(kThreads), 0, st, pdl, 0, p.nx, p.ny, p.nz, lambda, gamma, beta,
+                              (const float2*)p.z, u, p.z, p.y, ref, hist_slot));
+        return check_launch("prox_fista3q_kernel");
+    }
     if (p.ndim == 2 && levels == 2 && p.nx % 32 == 0 && p.ny % 4 == 0 &&
         ((uintptr_t)ref & 15) == 0 && ((uintptr_t)u & 15) == 0) {
         const int64_t nthr = (int64_t)p.nx * p.ny / 4;

@@ -88,9 +88,10 @@ CASES = [
     ("cart", (192, 256), 4, dict(R=3, acs=12)),
     ("cart", (384, 128), 5, dict(R=4, acs=16)),
     ("cart", (128, 192, 20), 2, dict(R=4, calib=8)),
+    ("cart", (16, 24, 32), 2, dict(R=3, calib=4)),
 ]
 IDS = ["cart2d_64x48", "cart2d_128", "cart3d_16x24x20", "spiral_64", "spiral_72x80_ragged",
-       "cart2d_192x256", "cart2d_384x128", "cart3d_128x192x20"]
+       "cart2d_192x256", "cart2d_384x128", "cart3d_128x192x20", "cart3d_16x24x32"]
 
 
 @pytest.fixture(scope="module", params=list(range(len(CASES))), ids=IDS)
@@ -327,7 +328,8 @@ def test_ppgd_without_momentum(pp, prob, coeffs):
 
 
 @pytest.mark.parametrize("shape,levels", [((64, 48), 2), ((64, 48), 1), ((8, 16, 12), 2),
-                                          ((6, 10, 14), 1), ((4, 4), 2)])
+                                          ((6, 10, 14), 1), ((4, 4), 2), ((8, 12, 48), 2),
+                                          ((16, 32, 64), 2), ((12, 8, 32), 1)])
 @pytest.mark.parametrize("inplace", [False, True])
 def test_prox_parity(pp, shape, levels, inplace):
     x = synth.crandn(shape, 7)
