@@ -30,6 +30,8 @@ struct BatchDev {
     int nitems = 0, ny_max = 0, km = 0, lgt = 3, grid = 0;
     int fast4 = 0;           // 1: the four-step register-FFT kernel runs the items
     int cl = 1;              // fast4: CTAs per item, the item's coils split over a cluster
+    int un2 = 0;             // fast4: the slices' common N2 (0: mixed lengths)
+    int ugrid = 0;           //   and the persistent grid of the uniform-length kernel
     Segments img, ksp, tiles;
 };
 
@@ -44,6 +46,7 @@ size_t batch_normal_smem(int ny_max, int lgt);
 void* batch_normal_fn(int km, int lgt);
 pp_status configure_batch_kernels();
 int batch4_grid();   // persistent grid of the four-step batched kernel
+int batch4u_grid(int n2);   // the same for the uniform-length kernel (0: none)
 pp_status launch_batch_normal(const BatchDev& b, const float2* x, float2* out, float coef,
                               const float2* operand, float alpha, cudaStream_t st);
 pp_status launch_seg_dot(const float2* a, const float2* bv, const Segments& sg, double* partials,

@@ -512,6 +512,77 @@ cart2d_batch4_cl_kernel(const SliceDesc* __restrict__ descs, const int2* __restr
     }
 }
 
+// cart2d_batch4_kernel for a batch whose slices all share one length
+// ny = 16 N2: a block of 8 * max(16, N2) threads (no idle threads for the
+// shorter lengths) and shared memory sized for that length, so more CTAs
+// fit an SM.
+template <int N2>
+__global__ void __launch_bounds__(8 * (N2 > 16 ? N2 : 16), N2 <= 16 ? 4 : 2)
+cart2d_batch4u_kernel(const SliceDesc* __restrict__ descs, const int2* __restrict__ items,
+                      int nitems, const float2* __restrict__ x, float2* out, float coef,
+                      const float2* operand, float alpha) {
+    constexpr int n = 16 * N2;
+    __shared__ float2 tws[n];
+    __shared__ float pm[n];
+    __shared__ float2 Y[16 * N2 * 8];
+    extern __shared__ float4 sb4[];   // 2 * n * 8 float2
+    float2* Sb = reinterpret_cast<float2*>(sb4);
+    int cur = -1;
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const int2 item = items[it];
+        const int s = item.x;
+        const SliceDesc D = descs[s];
+        if (s != cur) {
+            __syncthreads();
+            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                tws[i] = D.tw[i];
+                pm[i] = D.mask_fo[i];
+            }
+            __syncthreads();
+            cur = s;
+        }
+        cart_item4<N2>(tws, pm, Y, Sb, x + D.img_off, D.sens, D.C, D.nx, item.y, out + D.img_off,
+                       coef * D.invL, operand ? operand + D.img_off : nullptr, alpha);
+    }
+}
+
+// The uniform-length kernel with each item's coils split over a cluster of
+// CL CTAs (batches with fewer items than resident CTAs: one pass over the
+// items instead of several coil-serial rounds).  grid CL * clusters.
+template <int N2>
+__global__ void __launch_bounds__(8 * (N2 > 16 ? N2 : 16), N2 <= 16 ? 4 : 2)
+cart2d_batch4u_cl_kernel(const SliceDesc* __restrict__ descs, const int2* __restrict__ items,
+                         int nitems, const float2* __restrict__ x, float2* out, float coef,
+                         const float2* operand, float alpha) {
+    constexpr int n = 16 * N2;
+    __shared__ float2 tws[n];
+    __shared__ float pm[n];
+    __shared__ float2 Y[16 * N2 * 8];
+    extern __shared__ float4 sb4[];
+    float2* Sb = reinterpret_cast<float2*>(sb4);
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int q = (int)cluster.block_rank(), CL = (int)cluster.num_blocks();
+    const int cid = blockIdx.x / CL, ncid = gridDim.x / CL;
+    int cur = -1;
+    for (int it = cid; it < nitems; it += ncid) {
+        const int2 item = items[it];
+        const int s = item.x;
+        const SliceDesc D = descs[s];
+        if (s != cur) {
+            __syncthreads();
+            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                tws[i] = D.tw[i];
+                pm[i] = D.mask_fo[i];
+            }
+            __syncthreads();
+            cur = s;
+        }
+        batch_item_cl<N2>(tws, pm, Y, Sb, D, item.y, x + D.img_off, out + D.img_off, coef * D.invL,
+                          operand ? operand + D.img_off : nullptr, alpha, q, CL);
+    }
+}
+
 }  // namespace
 
 extern thread_local int64_t g_launches;
@@ -557,6 +628,30 @@ pp_status configure_batch_kernels() {
 
 constexpr size_t kBatch4Dyn = sizeof(float2) * 2 * 384 * 8;
 
+// Persistent grid of the uniform-length kernel (0 when n2 has none).
+int batch4u_grid(int n2) {
+    int occ = 0, nsm = 0;
+    cudaError_t e = cudaErrorInvalidValue;
+#define PP_G4U(N2_)                                                                                \
+    if (n2 == N2_) {                                                                               \
+        const size_t dyn = sizeof(float2) * 2 * 16 * N2_ * 8;                                      \
+        cudaFuncSetAttribute(cart2d_batch4u_kernel<N2_>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                             (int)dyn);                                                            \
+        cudaFuncSetAttribute(cart2d_batch4u_cl_kernel<N2_>,                                        \
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);               \
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, cart2d_batch4u_kernel<N2_>,        \
+                                                          8 * (N2_ > 16 ? N2_ : 16), dyn);         \
+    }
+    PP_G4U(8) PP_G4U(12) PP_G4U(16) PP_G4U(20) PP_G4U(24)
+#undef PP_G4U
+    if (e != cudaSuccess || occ < 1) {
+        cudaGetLastError();
+        return 0;
+    }
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, 0) != cudaSuccess) nsm = 152;
+    return occ * nsm;
+}
+
 int batch4_grid() {
     int occ = 0, nsm = 0;
     cudaFuncSetAttribute(cart2d_batch4_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -572,6 +667,33 @@ int batch4_grid() {
 
 pp_status launch_batch_normal(const BatchDev& b, const float2* x, float2* out, float coef,
                               const float2* operand, float alpha, cudaStream_t st) {
+    if (b.fast4 && b.cl == 1 && b.un2) {
+        cudaError_t e = cudaErrorInvalidValue;
+#define PP_B4U(N2_)                                                                                \
+        if (b.un2 == N2_)                                                                          \
+            e = launch_ex(cart2d_batch4u_kernel<N2_>, dim3(std::min(b.ugrid, b.nitems)),           \
+                          dim3(8 * (N2_ > 16 ? N2_ : 16)), sizeof(float2) * 2 * 16 * N2_ * 8, st,  \
+                          false, 0, (const SliceDesc*)b.descs, (const int2*)b.items, b.nitems, x, \
+                          out, coef, operand, alpha);
+        PP_B4U(8) PP_B4U(12) PP_B4U(16) PP_B4U(20) PP_B4U(24)
+#undef PP_B4U
+        if (e != cudaSuccess) return cuda_status(e, "cart2d_batch4u_kernel launch");
+        return check_launch_b("cart2d_batch4u_kernel");
+    }
+    if (b.fast4 && b.cl > 1 && b.un2) {
+        const int ncl = std::max(1, std::min(b.ugrid / b.cl, b.nitems));
+        cudaError_t e = cudaErrorInvalidValue;
+#define PP_B4UC(N2_)                                                                               \
+        if (b.un2 == N2_)                                                                          \
+            e = launch_ex(cart2d_batch4u_cl_kernel<N2_>, dim3(ncl * b.cl),                          \
+                          dim3(8 * (N2_ > 16 ? N2_ : 16)), sizeof(float2) * 2 * 16 * N2_ * 8, st,  \
+                          false, b.cl, (const SliceDesc*)b.descs, (const int2*)b.items, b.nitems, \
+                          x, out, coef, operand, alpha);
+        PP_B4UC(8) PP_B4UC(12) PP_B4UC(16) PP_B4UC(20) PP_B4UC(24)
+#undef PP_B4UC
+        if (e != cudaSuccess) return cuda_status(e, "cart2d_batch4u_cl_kernel launch");
+        return check_launch_b("cart2d_batch4u_cl_kernel");
+    }
     if (b.fast4 && b.cl > 1) {
         const int ncl = std::max(1, std::min(b.grid / b.cl, b.nitems));
         PP_TRY_CUDA(launch_ex(cart2d_batch4_cl_kernel, dim3(ncl * b.cl), dim3(192), kBatch4Dyn, st,

@@ -458,6 +458,16 @@ static pp_status build_noncartesian(Plan& p, const pp_sampling* s) {
     return PP_OK;
 }
 
+// Plan-time candidates that launch on thread-block clusters may not fit
+// another device: a candidate whose first launch fails (a launch-time error,
+// which does not poison the context) is skipped instead of failing the plan.
+template <typename F>
+static bool launches_ok(F&& fn) {
+    if (fn() == PP_OK) return true;
+    cudaGetLastError();
+    return false;
+}
+
 // Plan-time autotuning of the non-Cartesian operator's launch shapes: the
 // row-IFFT variant and the stencil kernel are each timed on the plan's own
 // buffers (10 launches after two warm-ups, three rounds over all candidates,
@@ -538,6 +548,10 @@ static pp_status tune_noncartesian(Plan& p, cudaStream_t st) {
             for (size_t i = 0; i < whole.size(); ++i) {
                 p.tune_stencil_kind = whole[i].first;
                 p.tune_rows_adj_cl = whole[i].second;
+                if (round == 0 && i > 0 && !launches_ok([&]() {
+                        return normal_into(p, p.v, p.t, 1.f, nullptr, 0.f, st); }))
+                    wbest[i] = 2e30f;   // a cluster shape this device cannot place
+                if (wbest[i] > 1.5e30f) continue;
                 float ms = 0.f;
                 PP_TRY(timeit([&]() { return normal_into(p, p.v, p.t, 1.f, nullptr, 0.f, st); }, &ms));
                 wbest[i] = std::min(wbest[i], ms);
@@ -567,7 +581,11 @@ static pp_status tune_cart3d(Plan& p, cudaStream_t st) {
     for (int round = 0; round < 2; ++round)
         for (size_t i = 0; i < cand.size(); ++i) {
             p.tune_c3 = cand[i];
-            PP_TRY(normal_into(p, p.v, p.t, 1.f, nullptr, 0.f, st));
+            if (best[i] > 1.5e30f) continue;
+            if (!launches_ok([&]() { return normal_into(p, p.v, p.t, 1.f, nullptr, 0.f, st); })) {
+                best[i] = 2e30f;
+                continue;
+            }
             PP_TRY_CUDA(cudaEventRecord(e0, st));
             for (int r = 0; r < 3; ++r) PP_TRY(normal_into(p, p.v, p.t, 1.f, nullptr, 0.f, st));
             PP_TRY_CUDA(cudaEventRecord(e1, st));
@@ -598,7 +616,11 @@ static pp_status tune_cart2d(Plan& p, cudaStream_t st) {
     for (int round = 0; round < 3; ++round)
         for (size_t i = 0; i < cand.size(); ++i) {
             p.tune_c2 = cand[i];
-            PP_TRY(normal_into(p, p.v, p.t, 1.f, nullptr, 0.f, st));
+            if (best[i] > 1.5e30f) continue;
+            if (!launches_ok([&]() { return normal_into(p, p.v, p.t, 1.f, nullptr, 0.f, st); })) {
+                best[i] = 2e30f;
+                continue;
+            }
             PP_TRY(normal_into(p, p.v, p.t, 1.f, nullptr, 0.f, st));
             PP_TRY_CUDA(cudaEventRecord(e0, st));
             for (int r = 0; r < 10; ++r) PP_TRY(normal_into(p, p.v, p.t, 1.f, nullptr, 0.f, st));
@@ -720,6 +742,7 @@ struct Batch {
     cudaGraphExec_t gexec = nullptr;
     std::vector<double> gkey;
     int64_t graph_kernels = 0;
+    int uni_n2 = 0;   // common N2 of all slices when the uniform-length kernel applies, else 0
     // differentiable unrolled solve: arena of image vectors and FP64 slots
     float2* arena = nullptr;
     size_t arena_vecs = 0;
@@ -844,14 +867,17 @@ static pp_status autotune(Batch& b, cudaStream_t st) {
                 PP_TRY(set_items(b, 3, &items));
                 b.dev.fast4 = 1;
                 b.dev.cl = cl;
+                b.dev.un2 = b.uni_n2;
                 b.dev.grid = batch4_grid();
             } else {
                 if (!km_for(b.dev.ny_max, lgt)) continue;
                 b.dev.fast4 = 0;
                 b.dev.cl = 1;
+                b.dev.un2 = 0;
                 PP_TRY(set_items(b, lgt, &items));
             }
-            PP_TRY(launch_batch_normal(b.dev, b.v, b.t, 1.f, nullptr, 0.f, st));
+            if (!launches_ok([&]() { return launch_batch_normal(b.dev, b.v, b.t, 1.f, nullptr, 0.f, st); }))
+                continue;   // a cluster shape this device cannot place
             PP_TRY_CUDA(cudaEventRecord(e0, st));
             for (int r = 0; r < 3; ++r) PP_TRY(launch_batch_normal(b.dev, b.v, b.t, 1.f, nullptr, 0.f, st));
             PP_TRY_CUDA(cudaEventRecord(e1, st));
@@ -874,11 +900,13 @@ static pp_status autotune(Batch& b, cudaStream_t st) {
         PP_TRY(set_items(b, 3, &items));
         b.dev.fast4 = 1;
         b.dev.cl = best_cl;
+        b.dev.un2 = b.uni_n2;
         b.dev.grid = batch4_grid();
         return PP_OK;
     }
     b.dev.fast4 = 0;
     b.dev.cl = 1;
+    b.dev.un2 = 0;
     return set_items(b, best, &items);
 }
 
@@ -1688,6 +1716,14 @@ pp_status pp_batch_create(pp_batch** out, int nslices, const pp_dims* dims, cons
         cudaError_t e = cudaMemsetAsync(b.v, 0, n * sizeof(float2), st);
         if (e != cudaSuccess) rc = cuda_status(e, "cudaMemsetAsync");
     }
+    if (rc == PP_OK) {
+        // a batch of one slice length can run the uniform-length kernel
+        int un2 = b.hdesc.empty() ? 0 : b.hdesc[0].n2;
+        for (const SliceDesc& d : b.hdesc)
+            if (d.n2 != un2) un2 = 0;
+        b.dev.ugrid = un2 ? batch4u_grid(un2) : 0;
+        b.uni_n2 = b.dev.ugrid > 0 ? un2 : 0;
+    }
     if (rc == PP_OK) rc = autotune(b, st);
     if (rc == PP_OK && power_iters > 0) rc = batch_power_iteration(b, seed, power_iters, st);
     if (rc != PP_OK) {
@@ -1787,9 +1823,11 @@ pp_status pp_batch_set_tile(pp_batch* batch, int cols_per_cta) {
         PP_TRY(set_items(b, 3, &items));
         b.dev.fast4 = 1;
         b.dev.cl = -cols_per_cta / 8;
+        b.dev.un2 = b.uni_n2;
         b.dev.grid = batch4_grid();
     } else {
         b.dev.cl = 1;
+        b.dev.un2 = 0;
         const int lgt = cols_per_cta == 4 ? 2 : cols_per_cta == 8 ? 3 : cols_per_cta == 16 ? 4 : -1;
         if (lgt < 0 || !km_for(b.dev.ny_max, lgt)) {
             set_error("pp_batch_set_tile: unsupported tile width %d", cols_per_cta);

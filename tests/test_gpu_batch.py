@@ -144,3 +144,30 @@ def test_batch_variants_agree_with_oracle(pp, tile):
             assert rel(got[i], O.cart_normal(xs[i], sens[i], masks[i]) / L[i]) <= 1e-5
     finally:
         b.destroy()
+
+
+@pytest.mark.parametrize("tile", [-8, -16, -32])
+def test_uniform_length_batch(pp, tile):
+    # every slice 256 rows (one register-FFT length): the uniform-length
+    # kernels, one CTA per item (-8) or the coils split over 2 or 4 CTAs
+    import torch
+    shapes = [(256, 36), (256, 64), (256, 20)]
+    coils = [4, 8, 2]
+    sens = [synth.coil_maps(s, c, 170 + i) for i, (s, c) in enumerate(zip(shapes, coils))]
+    masks = [synth.line_mask(s, 4, 8, 180 + i) for i, s in enumerate(shapes)]
+    b = pp.pp_batch_create(shapes, coils, [dev(x) for x in sens], masks, seed=1, power_iters=0)
+    try:
+        pp.pp_batch_set_tile(b, tile)
+        assert pp.pp_batch_tile(b)[0] == tile
+        L = np.array([0.8, 1.1, 1.3])
+        pp.pp_batch_set_scales(b, L)
+        xs = [synth.crandn(s, 190 + i) for i, s in enumerate(shapes)]
+        x = dev(np.concatenate([v.ravel() for v in xs]))
+        y = torch.empty_like(x)
+        for _ in range(2):
+            pp.pp_batch_normal_apply(b, x, y)
+            got = split(host(y), b.image_off, shapes)
+            for i in range(b.n):
+                assert rel(got[i], O.cart_normal(xs[i], sens[i], masks[i]) / L[i]) <= 1e-5
+    finally:
+        b.destroy()
