@@ -58,8 +58,8 @@ def parse():
                              "unrolled2d_8x256_c16"],
                     help="benchmark line to produce (the default is the headline workload)")
     ap.add_argument("--apply-only", type=int, default=0, metavar="K",
-                    help="profiling aid: build the headline workload's plan (no power iteration), "
-                         "apply its normal operator K times and exit without a bench line")
+                    help="profiling aid: build the workload's plan (no power iteration), apply "
+                         "its operator K times and exit without a bench line")
     ap.add_argument("--tuning", default="",
                     help="with --apply-only: row_ifft_variant,stencil_kind,stencil_coils to force")
     return ap.parse_args()
