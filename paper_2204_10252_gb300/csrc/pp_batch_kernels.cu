@@ -262,8 +262,10 @@ batch_prox_fista_kernel(const SliceDesc* __restrict__ descs, const int64_t* __re
                 const float2 df = csub(yn, yo);
                 z[a] = make_float2(yn.x + beta * df.x, yn.y + beta * df.y);
                 y[a] = yn;
-                dd += (double)df.x * df.x + (double)df.y * df.y;
-                yy += (double)yn.x * yn.x + (double)yn.y * yn.y;
+                if (hist) {   // FP64 arithmetic is slow on this part: only when asked for
+                    dd += (double)df.x * df.x + (double)df.y * df.y;
+                    yy += (double)yn.x * yn.x + (double)yn.y * yn.y;
+                }
                 if (ref) {
                     const float2 rv = ref[a];
                     const double ex = (double)yn.x - rv.x, ey = (double)yn.y - rv.y;

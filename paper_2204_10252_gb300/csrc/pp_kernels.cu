@@ -1000,8 +1000,10 @@ prox_fista_kernel(int nx, int ny, int nz, float lam, float gamma, float beta,
                     const float2 df = csub(yn, yo);
                     z[a] = make_float2(yn.x + beta * df.x, yn.y + beta * df.y);
                     y[a] = yn;
-                    dd += (double)df.x * df.x + (double)df.y * df.y;
-                    yy += (double)yn.x * yn.x + (double)yn.y * yn.y;
+                    if (hist) {
+                        dd += (double)df.x * df.x + (double)df.y * df.y;
+                        yy += (double)yn.x * yn.x + (double)yn.y * yn.y;
+                    }
                     if (ref) {
                         const float2 rv = ref[a];
                         const double ex = (double)yn.x - rv.x, ey = (double)yn.y - rv.y;
@@ -1097,8 +1099,10 @@ prox_fista2q_kernel(int nx, int ny, float lam, float gamma, float beta, float2* 
         for (int k = 0; k < 4; ++k) {
             const float2 df = csub(yn[k], yo[k]);
             zn[k] = make_float2(yn[k].x + beta * df.x, yn[k].y + beta * df.y);
-            dd += (double)df.x * df.x + (double)df.y * df.y;
-            yy += (double)yn[k].x * yn[k].x + (double)yn[k].y * yn[k].y;
+            if (hist) {   // FP64 arithmetic is slow on this part: only when asked for
+                dd += (double)df.x * df.x + (double)df.y * df.y;
+                yy += (double)yn[k].x * yn[k].x + (double)yn[k].y * yn[k].y;
+            }
         }
         *reinterpret_cast<float4*>(z + o0) = make_float4(zn[0].x, zn[0].y, zn[1].x, zn[1].y);
         *reinterpret_cast<float4*>(z + o1) = make_float4(zn[2].x, zn[2].y, zn[3].x, zn[3].y);
@@ -1221,8 +1225,10 @@ prox3q_kernel(int nx, int ny, int nz, float lam, float gamma, float beta, const 
                     const float2 yn = t[2 * q + h];
                     const float2 df = csub(yn, yo[h]);
                     zn[h] = make_float2(yn.x + beta * df.x, yn.y + beta * df.y);
-                    dd += (double)df.x * df.x + (double)df.y * df.y;
-                    yy += (double)yn.x * yn.x + (double)yn.y * yn.y;
+                    if (hist) {
+                        dd += (double)df.x * df.x + (double)df.y * df.y;
+                        yy += (double)yn.x * yn.x + (double)yn.y * yn.y;
+                    }
                 }
                 if (ref) {
                     const float4 rv = *reinterpret_cast<const float4*>(ref + o[q]);
