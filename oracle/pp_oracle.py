@@ -10,6 +10,9 @@ Problem (Eq. "ucopt", Sec. 1):  min_x 1/2 ||A x - b||_2^2 + lambda ||W x||_1
   A = [M F S_1; ...; M F S_C]      Cartesian SENSE (Sec. 5.1 operator)
   A = [N S_1; ...; N S_C]          non-Cartesian SENSE with a Kaiser-Bessel
                                    gridding NUFFT N (Sec. 5.2 operator)
+  A^H A with the exact NDFT F:     sum_c conj(S_c) F^H F S_c, the normal
+                                   operator evaluated through the Toeplitz
+                                   structure of F^H F (Sec. 2 remark, Sec. 5.2)
   W = orthonormal Haar wavelet (the paper's experiments use Daubechies-4;
       the workload here fixes a 2-level Haar).
 Method: Algorithm "pfista" (Sec. 3.1) with p from Eq. "l2cost", evaluated by
@@ -215,6 +218,64 @@ def ndft_forward(x, traj):
     ey = np.exp(-2j * math.pi * np.outer(t[:, 1], ry) / ny)   # [K, ny]
     ex = np.exp(-2j * math.pi * np.outer(t[:, 0], rx) / nx)   # [K, nx]
     return np.einsum("ky,yx,kx->k", ey, x, ex) / math.sqrt(ny * nx)
+
+
+def ndft_adjoint(y, traj, shape):
+    """Exact adjoint of ndft_forward: x(r) = 1/sqrt(n) sum_k y_k exp(+2 pi i (kx rx/nx + ky ry/ny)),
+    r centred.  O(K n); for small pins only."""
+    y = np.asarray(y, dtype=np.complex128)
+    ny, nx = shape
+    ry = (np.arange(ny) - ny // 2).astype(np.float64)
+    rx = (np.arange(nx) - nx // 2).astype(np.float64)
+    t = np.asarray(traj, dtype=np.float64)
+    ey = np.exp(2j * math.pi * np.outer(t[:, 1], ry) / ny)    # [K, ny]
+    ex = np.exp(2j * math.pi * np.outer(t[:, 0], rx) / nx)    # [K, nx]
+    return np.einsum("k,ky,kx->yx", y, ey, ex) / math.sqrt(ny * nx)
+
+
+def nc_normal_exact(x, sens, traj):
+    """A^H A with the exact non-uniform DFT F in place of the gridding NUFFT:
+    sum_c conj(S_c) F^H F (S_c x).  This is the operator that the Toeplitz
+    structure of F^H F (the remark of Sec. 2 and the spiral experiment of
+    Sec. 5.2) evaluates exactly, without gridding.  O(C K n); small sizes."""
+    s = np.asarray(sens, dtype=np.complex128)
+    x = np.asarray(x, dtype=np.complex128)
+    shape = s.shape[1:]
+    out = np.zeros(shape, dtype=np.complex128)
+    for c in range(s.shape[0]):
+        out += np.conj(s[c]) * ndft_adjoint(ndft_forward(s[c] * x, traj), traj, shape)
+    return out
+
+
+def ndft_gram_offsets(traj, shape):
+    """Entries of F^H F: (F^H F)[r, r'] = h(r - r') with
+    h(dy, dx) = 1/n sum_k exp(2 pi i (kx dx/nx + ky dy/ny)), returned as
+    h[dy + ny - 1, dx + nx - 1] for |dy| < ny, |dx| < nx.  The sum over k is
+    separable per axis, so it is one matrix product (a library primitive)."""
+    ny, nx = shape
+    t = np.asarray(traj, dtype=np.float64)
+    dy = np.arange(-(ny - 1), ny).astype(np.float64)
+    dx = np.arange(-(nx - 1), nx).astype(np.float64)
+    ey = np.exp(2j * math.pi * np.outer(t[:, 1], dy) / ny)    # [K, 2ny-1]
+    ex = np.exp(2j * math.pi * np.outer(t[:, 0], dx) / nx)    # [K, 2nx-1]
+    return (ey.T @ ex) / (ny * nx)
+
+
+def nc_normal_exact_at(x, sens, traj, pixels, gram=None):
+    """Selected outputs of nc_normal_exact, one by one from the entries of
+    F^H F: out(r) = sum_c conj(S_c(r)) sum_r' h(r - r') S_c(r') x(r').
+    pixels: list of (row, col); returns the values in that order."""
+    s = np.asarray(sens, dtype=np.complex128)
+    x = np.asarray(x, dtype=np.complex128)
+    ny, nx = x.shape
+    h = ndft_gram_offsets(traj, (ny, nx)) if gram is None else gram
+    sx = s * x[None]
+    out = []
+    for (r, q) in pixels:
+        # h(r - r') for every r': rows r - r' + ny - 1, columns q - q' + nx - 1
+        hr = h[r + ny - 1 - np.arange(ny)][:, q + nx - 1 - np.arange(nx)]
+        out.append(sum(np.conj(s[c, r, q]) * np.sum(hr * sx[c]) for c in range(s.shape[0])))
+    return np.array(out)
 
 
 def nc_forward(x, sens, traj, width=4, oversamp=1.25):

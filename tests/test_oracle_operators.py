@@ -110,3 +110,82 @@ def test_nufft_on_grid_points_matches_cartesian():
     x = synth.crandn((n, n), 7).astype(np.complex128)
     ref = O.cfft(x, axes=(0, 1)).ravel()
     assert np.linalg.norm(O.ndft_forward(x, traj) - ref) <= 1e-12 * np.linalg.norm(ref)
+
+
+# ---- exact NDFT normal operator (evaluated on the GPU through the Toeplitz
+# structure of F^H F: remark of Sec. 2, spiral experiment of Sec. 5.2) ----
+
+
+def test_ndft_adjoint_identity():
+    shape = (12, 10)
+    traj = synth.spiral_traj(3, 40, 2.0, 5.0)
+    x = synth.crandn(shape, 1).astype(np.complex128)
+    y = synth.crandn((len(traj),), 2).astype(np.complex128)
+    lhs = np.vdot(O.ndft_forward(x, traj), y)
+    rhs = np.vdot(x, O.ndft_adjoint(y, traj, shape))
+    assert _rel(lhs, rhs) <= 1e-12
+
+
+def test_ndft_adjoint_on_grid_points_is_centred_inverse_dft():
+    ny, nx = 8, 12
+    ky, kx = np.meshgrid(np.arange(ny) - ny // 2, np.arange(nx) - nx // 2, indexing="ij")
+    traj = np.stack([kx.ravel(), ky.ravel()], axis=1).astype(np.float32)
+    Y = synth.crandn((ny, nx), 3).astype(np.complex128)
+    ref = O.cifft(Y, axes=(0, 1))
+    got = O.ndft_adjoint(Y.ravel(), traj, (ny, nx))
+    assert np.linalg.norm(got - ref) <= 1e-12 * np.linalg.norm(ref)
+
+
+def test_exact_normal_full_grid_is_identity():
+    # every grid point sampled once and sum_c |S_c|^2 = 1  =>  A^H A = I
+    ny, nx = 8, 10
+    ky, kx = np.meshgrid(np.arange(ny) - ny // 2, np.arange(nx) - nx // 2, indexing="ij")
+    traj = np.stack([kx.ravel(), ky.ravel()], axis=1).astype(np.float32)
+    s = synth.coil_maps((ny, nx), 3, 0).astype(np.complex128)
+    s /= np.sqrt(np.sum(np.abs(s) ** 2, axis=0))
+    x = synth.crandn((ny, nx), 5).astype(np.complex128)
+    got = O.nc_normal_exact(x, s, traj)
+    assert np.linalg.norm(got - x) <= 1e-12 * np.linalg.norm(x)
+
+
+def test_exact_normal_is_hermitian_and_close_to_gridding():
+    shape = (24, 20)
+    traj = synth.spiral_traj(4, 300, 3.0, 10.0)
+    s = synth.coil_maps(shape, 3, 4)
+    x = synth.phantom(shape, 1).astype(np.complex128)
+    y = synth.crandn(shape, 6).astype(np.complex128)
+    assert _rel(np.vdot(O.nc_normal_exact(x, s, traj), y), np.vdot(x, O.nc_normal_exact(y, s, traj))) <= 1e-12
+    exact = O.nc_normal_exact(x, s, traj)
+    grid = O.nc_normal(x, s, traj)
+    # the W = 4, sigma = 1.25 gridding operator approximates it at the 1e-3 level
+    assert np.linalg.norm(grid - exact) <= 1e-2 * np.linalg.norm(exact)
+
+
+def test_gram_offsets_are_the_columns_of_the_brute_force_matrix():
+    shape = (6, 8)
+    ny, nx = shape
+    traj = synth.spiral_traj(2, 15, 1.5, 3.0)
+    h = O.ndft_gram_offsets(traj, shape)
+    assert h.shape == (2 * ny - 1, 2 * nx - 1)
+    # h(0) = K / n; h(-d) = conj(h(d))
+    assert abs(h[ny - 1, nx - 1] - len(traj) / (ny * nx)) <= 1e-14
+    assert np.max(np.abs(h[::-1, ::-1] - np.conj(h))) <= 1e-14
+    for (r0, q0) in [(0, 0), (2, 5), (5, 7), (3, 0)]:
+        e = np.zeros(shape, dtype=np.complex128)
+        e[r0, q0] = 1.0
+        col = O.ndft_adjoint(O.ndft_forward(e, traj), traj, shape)   # column r' = (r0, q0)
+        for r in range(ny):
+            for q in range(nx):
+                assert abs(col[r, q] - h[r - r0 + ny - 1, q - q0 + nx - 1]) <= 1e-14
+
+
+def test_sampled_exact_normal_matches_full():
+    shape = (10, 12)
+    traj = synth.spiral_traj(3, 60, 2.0, 5.0)
+    s = synth.coil_maps(shape, 2, 1)
+    x = synth.crandn(shape, 2).astype(np.complex128)
+    full = O.nc_normal_exact(x, s, traj)
+    pix = [(0, 0), (9, 11), (4, 7), (5, 0)]
+    got = O.nc_normal_exact_at(x, s, traj, pix)
+    ref = np.array([full[r, q] for r, q in pix])
+    assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(full))
