@@ -62,6 +62,9 @@ def parse():
                          "its operator K times and exit without a bench line")
     ap.add_argument("--tuning", default="",
                     help="with --apply-only: row_ifft_variant,stencil_kind,stencil_coils to force")
+    ap.add_argument("--operator", choices=["gridding", "toeplitz"], default="gridding",
+                    help="spiral workload: the gridding normal operator (G^T G stencil) or the "
+                         "exact F^H F through its Toeplitz embedding")
     return ap.parse_args()
 
 
@@ -166,13 +169,22 @@ class ClockSampler:
 # roofline bookkeeping: algorithmic FLOPs per launch of each normal-operator
 # kernel (conventional 5 N log2 N per complex FFT of length N)
 # ---------------------------------------------------------------------------
-def kernel_flops(c, K):
+def kernel_flops(c, K, toeplitz=False):
     ny, nx = c["shape"]
     C = c["coils"]
     G = int(math.ceil(c["oversamp"] * nx))
     n = nx * ny
     fft = lambda N: 5.0 * N * math.log2(N)
     W = c["kb_width"]
+    if toeplitz:
+        # rows: ny length-2nx FFTs per coil; columns: 2nx pairs of length-2ny
+        # FFTs per coil plus the real spectrum product
+        Mx, My = 2 * nx, 2 * ny
+        return {
+            "ci_rows_fwd_kernel": C * ny * fft(Mx) + 6.0 * C * n,
+            "toep_cols_kernel": C * Mx * 2 * fft(My) + 2.0 * C * Mx * My,
+            "ci_rows_inv_cl_kernel": C * ny * fft(Mx) + 8.0 * C * n + 4.0 * n,
+        }
     return {
         "rows_fwd_kernel": C * ny * fft(G) + 8.0 * C * n,
         "cols_kernel": C * G * fft(G),
@@ -186,6 +198,7 @@ def kernel_flops(c, K):
         "ci_cols_kernel": C * G * fft(G),
         "ci_stencil_kernel": 4.0 * (2 * W - 1) ** 2 * C * G * G,
         "ci_rows_inv_kernel": C * ny * fft(G) + 10.0 * C * n,
+        "ci_rows_inv_cl_kernel": C * ny * fft(G) + 10.0 * C * n,
         "ci_sum_kernel": 4.0 * 2.0 * n,
         "rows_adj_cb_kernel": C * ny * fft(G) + 10.0 * C * n,
         "rows_adj_kernel": C * ny * fft(G) + 10.0 * C * n,
@@ -219,30 +232,43 @@ def ncu_traffic(kernel):
     return e.get("dram_bytes_per_launch")
 
 
-def oracle_sample(c, sens, traj, coils):
+EXACT_SAMPLES = 4096
+
+
+def oracle_sample(c, sens, traj, coils, exact=False):
     """One bounded sample of the workload on the FP64 oracle: the normal
     operator restricted to the first `coils` coils (a fraction coils/C of one
-    full A^H A apply).  Returns (seconds, fraction)."""
+    full A^H A apply); for the exact (Toeplitz-evaluated) operator, one coil
+    and the first EXACT_SAMPLES samples, whose direct sums cost a fraction
+    (1/C)(EXACT_SAMPLES/K) of the full apply.  Returns (seconds, fraction)."""
     from oracle import pp_oracle as O
     x = synth.crandn(c["shape"], 3).astype(np.complex128)
     t0 = time.perf_counter()
+    if exact:
+        O.nc_normal_exact(x, sens[:1], traj[:EXACT_SAMPLES])
+        return time.perf_counter() - t0, EXACT_SAMPLES / float(len(traj) * c["coils"])
     O.nc_normal(x, sens[:coils], traj, c["kb_width"], c["oversamp"])
     return time.perf_counter() - t0, coils / float(c["coils"])
 
 
-def cpu_baseline(c, sens, traj, budget_s=15.0, coils=2):
+def cpu_baseline(c, sens, traj, budget_s=15.0, coils=2, exact=False):
     """The oracle as it stands, timed on the host cores on ~budget_s of
     bounded samples; reported in full-apply units."""
     el, frac, n = 0.0, 0.0, 0
     while el < budget_s:
-        t, f = oracle_sample(c, sens, traj, coils)
+        t, f = oracle_sample(c, sens, traj, coils, exact)
         el += t
         frac += f
         n += 1
-    return {"value": frac / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "%d samples, each the A^H A apply of %d of the 32 coils (256x256, 65536-sample "
-                      "spiral) on the numpy FP64 oracle, scaled to full applies; numpy's FFT and "
-                      "scatter-add run single-threaded" % (n, coils)}
+    if exact:
+        what = ("%d samples, each the exact-NDFT A^H A of 1 of the 32 coils over the first %d of the "
+                "65536 spiral samples (256x256) on the numpy FP64 oracle (direct sums), scaled to "
+                "full applies" % (n, EXACT_SAMPLES))
+    else:
+        what = ("%d samples, each the A^H A apply of %d of the 32 coils (256x256, 65536-sample "
+                "spiral) on the numpy FP64 oracle, scaled to full applies; numpy's FFT and "
+                "scatter-add run single-threaded" % (n, coils))
+    return {"value": frac / el, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": what}
 
 
 # ---------------------------------------------------------------------------
@@ -315,7 +341,8 @@ def main():
         sens = synth.coil_maps(c["shape"], c["coils"], c["seed"])
         traj = synth.spiral_traj(c["interleaves"], c["samples"], c["turns"], c["shape"][1] / 2.0)
         plan = pp.pp_plan_create(c["shape"], c["coils"], torch.from_numpy(sens).to(dev), traj=traj,
-                                 kb_width=c["kb_width"], oversamp=c["oversamp"], power_iters=0)
+                                 kb_width=c["kb_width"], oversamp=c["oversamp"], power_iters=0,
+                                 toeplitz=args.operator == "toeplitz")
         if args.tuning:
             pp.pp_plan_set_tuning(plan, *[int(v) for v in args.tuning.split(",")])
         xa = torch.from_numpy(synth.crandn(c["shape"], 3)).to(dev)
@@ -333,8 +360,9 @@ def main():
     sens_t = torch.from_numpy(sens).to(dev)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
+    toep = args.operator == "toeplitz"
     plan = pp.pp_plan_create(shape, C, sens_t, traj=traj, kb_width=c["kb_width"],
-                             oversamp=c["oversamp"], seed=seed, power_iters=50)
+                             oversamp=c["oversamp"], seed=seed, power_iters=50, toeplitz=toep)
     torch.cuda.synchronize()
     setup_plan_s = time.perf_counter() - t0
     L = pp.pp_plan_scale(plan)
@@ -382,7 +410,7 @@ def main():
     yout = torch.empty_like(xin)
     stages = pp.pp_profile_normal(plan, xin, yout, reps=50)
     apply_ms = sum(stages.values())
-    flops = kernel_flops(c, K)
+    flops = kernel_flops(c, K, toep)
     # cols_kernel runs twice per apply (forward and inverse): per-launch time is half
     launches_per_apply = {"cols_kernel": 2, "cols4_kernel": 2, "ci_cols_kernel": 2}
     per_launch_ms = {k: v / launches_per_apply.get(k, 1) for k, v in stages.items()}
@@ -403,7 +431,10 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded phantom, coil maps, spiral, noise); no datasets",
-        "config": {"workload": WORKLOAD, "image": list(shape), "coils": C, "samples": K,
+        "config": {"workload": WORKLOAD + ("_toeplitz" if toep else ""), "image": list(shape),
+                   "coils": C, "samples": K,
+                   "normal_operator": ("exact F^H F by its 2ny x 2nx Toeplitz embedding" if toep else
+                                       "Kaiser-Bessel gridding, precomputed G^T G stencil"),
                    "kb_width": c["kb_width"], "oversamp": c["oversamp"], "lambda": lam, "d": d,
                    "iters": iters, "applies_per_step": applies_per_step,
                    "l2": "flushed between timed steps (256 MB write)", "parallelism":
@@ -435,7 +466,7 @@ def main():
         # --- time to NRMSE <= 1e-3 against each method's own converged solution ---
         out["time_to_nrmse"] = time_to_target(pp, plan, b, c, coeffs, setup_plan_s, stream)
         if rank == 0 and world == 1:
-            out["cpu_baseline"] = cpu_baseline(c, sens, traj)
+            out["cpu_baseline"] = cpu_baseline(c, sens, traj, exact=toep)
     if rank == 0:
         print(json.dumps(out))
     plan.destroy()

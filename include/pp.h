@@ -53,7 +53,7 @@ typedef void* pp_stream;
 /* Image size: n[0] = nx (fastest), n[1] = ny, n[2] = nz (used when ndim == 3). */
 typedef struct { int ndim; int n[3]; } pp_dims;
 
-enum { PP_CARTESIAN = 0, PP_NONCARTESIAN = 1 };
+enum { PP_CARTESIAN = 0, PP_NONCARTESIAN = 1, PP_NONCARTESIAN_TOEPLITZ = 2 };
 
 /* Sampling pattern (the M of Sec. 5.1, or the trajectory of Sec. 5.2).
  *  kind == PP_CARTESIAN:    mask = host uint8 [nz][ny][nx], centred order,
@@ -66,6 +66,19 @@ enum { PP_CARTESIAN = 0, PP_NONCARTESIAN = 1 };
  *                           ceil(oversamp * n) points per axis (oversamp in
  *                           [1.125, 2]); the grid size must be even, have no
  *                           prime factor above 5 and be at least 40.
+ *  kind == PP_NONCARTESIAN_TOEPLITZ: the same trajectory and gridding
+ *                           parameters (used by the forward and adjoint
+ *                           applies), but the normal operator is the exact
+ *                           F^H F of the non-uniform DFT, evaluated through
+ *                           its Toeplitz structure (the remark on Toeplitz
+ *                           normal operators in Sec. 2; the spiral experiment
+ *                           of Sec. 5.2): an FFT convolution on the 2ny x 2nx
+ *                           circulant embedding, with no gridding in the
+ *                           loop.  The embedded kernel's spectrum is computed
+ *                           at plan time from the trajectory.  Needs coils
+ *                           <= 32 and nx, ny in {64, 96, 128, 160, 192, 256};
+ *                           else PP_ERR_UNSUPPORTED.  pp_plan_set_tuning does
+ *                           not affect it.
  *  The plan copies what it needs; the host arrays may be freed on return. */
 typedef struct {
     int kind;

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(PKG, "libpp.so")
 
 PP_OK, PP_ERR_INVALID_ARG, PP_ERR_UNSUPPORTED, PP_ERR_OOM, PP_ERR_CUDA, PP_ERR_NONFINITE, \
     PP_ERR_TIMEOUT = range(7)
-PP_CARTESIAN, PP_NONCARTESIAN = 0, 1
+PP_CARTESIAN, PP_NONCARTESIAN, PP_NONCARTESIAN_TOEPLITZ = 0, 1, 2
 STATUS_NAMES = {0: "PP_OK", 1: "PP_ERR_INVALID_ARG", 2: "PP_ERR_UNSUPPORTED", 3: "PP_ERR_OOM",
                 4: "PP_ERR_CUDA", 5: "PP_ERR_NONFINITE", 6: "PP_ERR_TIMEOUT"}
 
@@ -206,10 +206,11 @@ class Plan:
 
 def pp_plan_create(shape, coils: int, sens, mask=None, traj=None, kb_width: int = 4,
                    oversamp: float = 1.25, seed: int = 0, power_iters: int = 50,
-                   stream=None) -> Plan:
+                   stream=None, toeplitz: bool = False) -> Plan:
     """shape: image shape [ny, nx] or [nz, ny, nx]; sens: CUDA complex64
     [C, *shape]; mask: uint8 array of the image shape (Cartesian) or
-    traj: float32 [K, 2] (non-Cartesian)."""
+    traj: float32 [K, 2] (non-Cartesian; toeplitz=True evaluates the normal
+    operator as the exact F^H F through its Toeplitz embedding)."""
     s = pp_sampling()
     keep = []
     if mask is not None:
@@ -223,7 +224,7 @@ def pp_plan_create(shape, coils: int, sens, mask=None, traj=None, kb_width: int 
     elif traj is not None:
         t = np.ascontiguousarray(traj, dtype=np.float32)
         keep.append(t)
-        s.kind = PP_NONCARTESIAN
+        s.kind = PP_NONCARTESIAN_TOEPLITZ if toeplitz else PP_NONCARTESIAN
         s.mask = None
         s.traj = t.ctypes.data
         s.K = int(t.shape[0])

@@ -181,6 +181,7 @@ static pp_status normal_into(const Plan& p, const float2* x, float2* out, float 
         }
         return PP_OK;
     }
+    if (p.toep) return toep_normal(p, x, out, scale, operand, alpha, st);
     // non-Cartesian: rows -> cols -> G^T G stencil -> cols^H -> rows^H
     if (p.tune_stencil_kind >= 7 && p.ci_sens)
         return ci_normal(p, x, out, scale, operand, alpha,
@@ -413,7 +414,7 @@ static pp_status build_noncartesian(Plan& p, const pp_sampling* s) {
     // G^T G as (2W-1)^2 weight planes: for every sample and every pair of its
     // taps j, j' (offset delta = j' - j), T[delta][j] += phi_j phi_j'
     // (accumulated in FP64, stored FP32).
-    {
+    if (!p.toep) {   // (a Toeplitz plan's normal operator needs no stencil)
         const int D = 2 * W - 1;
         std::vector<double> T((size_t)D * D * Gx * Gy, 0.0);
         const size_t plane = (size_t)Gx * Gy;
@@ -634,6 +635,25 @@ static pp_status tune_cart2d(Plan& p, cudaStream_t st) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return PP_OK;
+}
+
+// Toeplitz-embedded normal operator: twiddles of the 2n transforms, the
+// coil-innermost maps, the two [ny][2nx][32] arrays (zeroed once, so that
+// coil blocks past C read zeros) and the kernel spectrum.
+static pp_status setup_toeplitz(Plan& p, const pp_sampling* s, cudaStream_t st) {
+    PP_TRY(make_fft(p, 2 * p.nx, p.tx));
+    PP_TRY(make_fft(p, 2 * p.ny, p.ty));
+    if (!p.ci_sens) {
+        PP_TRY(alloc_n(p, &p.ci_sens, ci_sens_elems(p)));
+        PP_TRY(ci_prepare(p, st));
+    }
+    const size_t nr = toep_rows_elems(p);
+    PP_TRY(alloc_n(p, &p.toep_a, nr));
+    PP_TRY(alloc_n(p, &p.toep_b, nr));
+    PP_TRY_CUDA(cudaMemsetAsync(p.toep_a, 0, sizeof(float2) * nr, st));
+    PP_TRY_CUDA(cudaMemsetAsync(p.toep_b, 0, sizeof(float2) * nr, st));
+    PP_TRY(alloc_n(p, &p.toep_T, (size_t)4 * p.nx * p.ny));
+    return toep_build_kernel(p, s->traj, s->K, st);
 }
 
 // Buffers of the coil-innermost pipeline (when the plan supports it).
@@ -1234,13 +1254,18 @@ pp_status pp_plan_create(pp_plan** out, pp_dims dims, int coils, const pp_c64* s
             set_error("pp_plan_create: FFT lengths need prime factors <= 5");
             return PP_ERR_UNSUPPORTED;
         }
-    } else if (s->kind == PP_NONCARTESIAN) {
+    } else if (s->kind == PP_NONCARTESIAN || s->kind == PP_NONCARTESIAN_TOEPLITZ) {
         if (!s->traj) {
             set_error("pp_plan_create: non-Cartesian sampling needs a trajectory");
             return PP_ERR_INVALID_ARG;
         }
         if (dims.ndim != 2) {
             set_error("pp_plan_create: non-Cartesian plans are 2-D only");
+            return PP_ERR_UNSUPPORTED;
+        }
+        if (s->kind == PP_NONCARTESIAN_TOEPLITZ && !toep_supported(nx, ny, coils)) {
+            set_error("pp_plan_create: the Toeplitz normal operator needs coils <= 32 and "
+                      "nx, ny in {64, 96, 128, 160, 192, 256}");
             return PP_ERR_UNSUPPORTED;
         }
     } else {
@@ -1254,7 +1279,9 @@ pp_status pp_plan_create(pp_plan** out, pp_dims dims, int coils, const pp_c64* s
 
     pp_plan* h = new pp_plan();
     Plan& p = h->impl;
-    p.ndim = dims.ndim; p.nx = nx; p.ny = ny; p.nz = nz; p.C = coils; p.kind = s->kind;
+    p.ndim = dims.ndim; p.nx = nx; p.ny = ny; p.nz = nz; p.C = coils;
+    p.kind = s->kind == PP_NONCARTESIAN_TOEPLITZ ? PP_NONCARTESIAN : s->kind;
+    p.toep = s->kind == PP_NONCARTESIAN_TOEPLITZ;
     p.nimg = (int64_t)nx * ny * nz;
     p.sens = reinterpret_cast<const float2*>(sens);
     cudaGetDevice(&p.dev);
@@ -1281,7 +1308,8 @@ pp_status pp_plan_create(pp_plan** out, pp_dims dims, int coils, const pp_c64* s
         rc = tune_cart3d(p, st);
     }
     if (rc == PP_OK && p.kind == PP_NONCARTESIAN) rc = setup_ci(p, st);
-    if (rc == PP_OK && p.kind == PP_NONCARTESIAN) rc = tune_noncartesian(p, st);
+    if (rc == PP_OK && p.toep) rc = setup_toeplitz(p, s, st);
+    if (rc == PP_OK && p.kind == PP_NONCARTESIAN && !p.toep) rc = tune_noncartesian(p, st);
     if (rc == PP_OK && power_iters > 0) rc = power_iteration(p, seed, power_iters, st);
     if (rc != PP_OK) {
         cudaStreamSynchronize(st);

@@ -148,6 +148,11 @@ struct Plan {
     float2* ci_sens = nullptr;   // [ny][nx][32]
     float2 *ci_a = nullptr, *ci_b = nullptr, *ci_c = nullptr;
     float2* ci_part = nullptr;   // [4][ny][nx] coil-block partial sums
+    // Toeplitz-embedded normal operator (exact F^H F on the 2ny x 2nx circulant)
+    int toep = 0;                // 1: the normal operator takes the Toeplitz path
+    DevFft tx, ty;               // length-2nx / 2ny twiddle tables
+    float* toep_T = nullptr;     // [2nx][2ny] kernel spectrum, column-major, 1/(n M) folded in
+    float2 *toep_a = nullptr, *toep_b = nullptr;   // [ny][2nx][32] row-transformed arrays
 
     // Workspace
     float2* wk_a = nullptr;   // C * ny * G_x (rows) or C * n (Cartesian)
@@ -252,6 +257,11 @@ size_t ci_rows_elems(const Plan& p);
 size_t ci_sens_elems(const Plan& p);
 size_t ci_partial_elems(const Plan& p);
 pp_status ci_prepare(Plan& p, cudaStream_t st);
+bool toep_supported(int nx, int ny, int C);
+size_t toep_rows_elems(const Plan& p);
+pp_status toep_normal(const Plan& p, const float2* x, float2* out, float scale,
+                      const float2* operand, float alpha, cudaStream_t st);
+pp_status toep_build_kernel(Plan& p, const float* traj, int64_t K, cudaStream_t st);
 pp_status ci_normal(const Plan& p, const float2* x, float2* out, float scale, const float2* operand,
                     float alpha, int ry, cudaStream_t st);   // ry 0: coil-pair stencil
 pp_status launch_nufft_degrid(const Plan& p, const float2* grid_in, float2* ksp, cudaStream_t st);

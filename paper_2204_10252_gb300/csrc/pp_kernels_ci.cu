@@ -462,6 +462,81 @@ __global__ void ci_sum_kernel(const float2* __restrict__ P, int64_t n, float sca
     }
 }
 
+// Column stage of the Toeplitz-embedded normal operator: for column q of
+// the [H][M][CP] row-transformed array, the length-n (= 2H) column transform,
+// the product with the embedded kernel's spectrum Tc[q][k] (real, the
+// 1/(n_img M) normalisation folded in), and the inverse transform, in
+// registers: forward phase 1 by (m2, coil) threads, phase 2 by (k1, coil)
+// threads, then the mirrored inverse (input k = k1 + 16 k2, output
+// m = N2 m1 + m2): inverse length-N2 DFT over k2 and W_n^(-m2 k1) by the
+// same (k1) threads, inverse length-16 DFT over k1 by the (m2) threads.
+// Rows: transform position p <-> row (p + off) mod n, stored when below H.
+// grid (M, coil blocks), block CB * tpr(N2).
+template <int N2>
+__global__ void __launch_bounds__(CB * tpr<N2>(), 1)
+toep_cols_kernel(const float2* __restrict__ tw, const float* __restrict__ Tc, int H, int off, int M,
+                 const float2* __restrict__ src, float2* __restrict__ dst) {
+    constexpr int n = N1 * N2, YP = ypitch<N2>();
+    __shared__ float2 tws[n];
+    __shared__ float Ts[n];
+    __shared__ float2 Y[N1 * YP];
+    pdl_trigger();
+    // twiddles and this column's kernel spectrum are plan constants
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        tws[i] = tw[i];
+        Ts[i] = Tc[(int64_t)blockIdx.x * n + i];
+    }
+    __syncthreads();
+    pdl_wait();
+    const int j = threadIdx.x & (CB - 1), r = threadIdx.x / CB;
+    const int64_t rs = (int64_t)M * CP;
+    const int64_t cofs = (int64_t)blockIdx.x * CP + blockIdx.y * CB + j;
+    if (r < N2) {
+        float2 v[N1];
+#pragma unroll
+        for (int m1 = 0; m1 < N1; ++m1) {
+            int row = N2 * m1 + r + off;
+            if (row >= n) row -= n;
+            v[m1] = row < H ? src[row * rs + cofs] : make_float2(0.f, 0.f);
+        }
+        fft4_phase1<N1, N2, false>(v, r, tws);
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) Y[k1 * YP + r * CB + j] = v[k1];
+    }
+    __syncthreads();
+    if (r < N1) {
+        float2 u[N2];
+#pragma unroll
+        for (int m2 = 0; m2 < N2; ++m2) u[m2] = Y[r * YP + m2 * CB + j];
+        fft4_phase2<N1, N2, false>(u, tws);
+#pragma unroll
+        for (int k2 = 0; k2 < N2; ++k2) u[k2] = cscale(u[k2], Ts[r + N1 * k2]);
+        RegFft<N2, true>::run(u, tws, N1);
+#pragma unroll
+        for (int m2 = 1; m2 < N2; ++m2) {
+            float2 w = tws[m2 * r];
+            w.y = -w.y;
+            u[m2] = cmul(u[m2], w);
+        }
+        // the same (k1, coil) slots this thread read: no other thread touches them
+#pragma unroll
+        for (int m2 = 0; m2 < N2; ++m2) Y[r * YP + m2 * CB + j] = u[m2];
+    }
+    __syncthreads();
+    if (r < N2) {
+        float2 v[N1];
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) v[k1] = Y[k1 * YP + r * CB + j];
+        RegFft<N1, true>::run(v, tws, N2);
+#pragma unroll
+        for (int m1 = 0; m1 < N1; ++m1) {
+            int q = N2 * m1 + r + off;
+            if (q >= n) q -= n;
+            if (q < H) dst[q * rs + cofs] = v[m1];
+        }
+    }
+}
+
 static pp_status check_ci(const char* what) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_status(e, what);
@@ -572,6 +647,61 @@ pp_status ci_normal(const Plan& p, const float2* x, float2* out, float scale, co
     PP_TRY_CUDA(launch_ex(ci_sum_kernel, dim3(blocks), dim3(256), 0, st, pdl, 0,
                           (const float2*)p.ci_part, n, scale, operand, alpha, out));
     return check_ci("ci_sum_kernel");
+}
+
+bool toep_supported(int nx, int ny, int C) {
+    return C >= 1 && C <= CP && toep_n2(2 * nx) && toep_n2(2 * ny);
+}
+
+size_t toep_rows_elems(const Plan& p) { return (size_t)p.ny * 2 * p.nx * CP; }
+
+// out = scale * A^H A x + alpha * operand with F^H F evaluated through its
+// Toeplitz structure: embed in the 2ny x 2nx circulant, so that
+//   F^H F v = crop(IFFT(Tk . FFT(zero-pad(v))))
+// with Tk the spectrum of the embedded kernel.  Three kernels: coil expand +
+// row FFT, column FFT * Tk * column IFFT, row IFFT + conj(S) coil reduction
+// (4-CTA cluster) + Horner axpy.
+pp_status toep_normal(const Plan& p, const float2* x, float2* out, float scale,
+                      const float2* operand, float alpha, cudaStream_t st) {
+    const int nx = p.nx, ny = p.ny, Mx = 2 * nx, My = 2 * ny;
+    const int n2x = toep_n2(Mx), n2y = toep_n2(My);
+    const int ncb = (p.C + CB - 1) / CB;
+    const bool pdl = p.pdl != 0;
+    RowArgs rf{};
+    rf.n = nx; rf.G = Mx; rf.off_in = nx / 2; rf.off_out = 0; rf.nrows = ny; rf.scale = 1.f;
+    cudaError_t e = cudaErrorInvalidValue;
+#define PP_TR(N2_)                                                                              \
+    if (n2x == N2_)                                                                             \
+        e = launch_ex(ci_rows_fwd_kernel<N2_>, dim3(ny, ncb), dim3(CB * tpr<N2_>()), 0, st, pdl, 0, \
+                      (const float2*)p.tx.tw, rf, x, (const float2*)p.ci_sens, (const float*)nullptr, \
+                      (const float*)nullptr, p.toep_a);
+    PP_TR(8) PP_TR(12) PP_TR(16) PP_TR(20) PP_TR(24) PP_TR(32)
+#undef PP_TR
+    if (e != cudaSuccess) return cuda_status(e, "ci_rows_fwd_kernel (Toeplitz) launch");
+    PP_TRY(check_ci("ci_rows_fwd_kernel"));
+    e = cudaErrorInvalidValue;
+#define PP_TC(N2_)                                                                              \
+    if (n2y == N2_)                                                                             \
+        e = launch_ex(toep_cols_kernel<N2_>, dim3(Mx, ncb), dim3(CB * tpr<N2_>()), 0, st, pdl, 0,   \
+                      (const float2*)p.ty.tw, (const float*)p.toep_T, ny, ny / 2, Mx,            \
+                      (const float2*)p.toep_a, p.toep_b);
+    PP_TC(8) PP_TC(12) PP_TC(16) PP_TC(20) PP_TC(24) PP_TC(32)
+#undef PP_TC
+    if (e != cudaSuccess) return cuda_status(e, "toep_cols_kernel launch");
+    PP_TRY(check_ci("toep_cols_kernel"));
+    RowArgs ra = rf;
+    ra.off_in = 0; ra.off_out = nx / 2;
+    e = cudaErrorInvalidValue;
+#define PP_TI(N2_)                                                                              \
+    if (n2x == N2_)                                                                             \
+        e = launch_ex(ci_rows_inv_cl_kernel<N2_>, dim3(NCB, ny), dim3(CB * tpr<N2_>()), 0, st, pdl, \
+                      NCB, (const float2*)p.tx.tw, ra, (const float2*)p.toep_b,                  \
+                      (const float2*)p.ci_sens, (const float*)nullptr, (const float*)nullptr, out,  \
+                      scale, operand, alpha);
+    PP_TI(8) PP_TI(12) PP_TI(16) PP_TI(20) PP_TI(24) PP_TI(32)
+#undef PP_TI
+    if (e != cudaSuccess) return cuda_status(e, "ci_rows_inv_cl_kernel (Toeplitz) launch");
+    return check_ci("ci_rows_inv_cl_kernel");
 }
 
 }  // namespace pp

@@ -79,6 +79,22 @@ def test_invalid_arguments_are_rejected_without_device_work(L):
     d.n[0] = 66
     assert L.pp_plan_create(ctypes.byref(out), d, 4, ctypes.c_void_p(16), ctypes.byref(s), 0, 0, None) == 2
     assert out.value is None
+    # Toeplitz-embedded normal operator: coils <= 32 and 2n a register transform length
+    traj = (ctypes.c_float * 2)(0.0, 0.0)
+    st = pp_sampling()
+    st.kind = 2
+    st.traj = ctypes.cast(traj, ctypes.c_void_p)
+    st.K = 1
+    st.kb_width = 4
+    st.oversamp = 1.25
+    d.n[0] = d.n[1] = 80
+    assert L.pp_plan_create(ctypes.byref(out), d, 4, ctypes.c_void_p(16), ctypes.byref(st), 0, 0, None) == 2
+    assert "Toeplitz" in pp.pp_last_error()
+    d.n[0] = d.n[1] = 64
+    assert L.pp_plan_create(ctypes.byref(out), d, 33, ctypes.c_void_p(16), ctypes.byref(st), 0, 0, None) == 2
+    assert out.value is None
+    st.kind = 3
+    assert L.pp_plan_create(ctypes.byref(out), d, 4, ctypes.c_void_p(16), ctypes.byref(st), 0, 0, None) == 1
     # prox: levels outside 1..2 and axes not multiples of 2^levels
     d.n[0] = 64
     assert L.pp_prox_l1_haar(d, 3, ctypes.c_float(0.1), ctypes.c_void_p(16), ctypes.c_void_p(16), None) == 2
