@@ -218,10 +218,10 @@ def csrc_digest():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel):
+def ncu_traffic(kernel, summary="ncu_traffic.json"):
     """Per-launch DRAM bytes of `kernel` from the committed ncu summary, or
     None when missing or taken on different kernel sources."""
-    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    p = os.path.join(ROOT, "profiles", summary)
     try:
         d = json.load(open(p))
     except Exception:
@@ -420,7 +420,8 @@ def main():
     ach = flops.get(dom, float("nan")) / (per_launch_ms[dom] / 1e3) / 1e12
     roofline = {
         "bound": "alu", "kernel": dom, "achieved": ach, "peak": peak_tflops, "unit": "TFLOP/s",
-        "frac": ach / peak_tflops, "traffic": ncu_traffic(dom),
+        "frac": ach / peak_tflops,
+        "traffic": ncu_traffic(dom, "ncu_traffic_toeplitz.json" if toep else "ncu_traffic.json"),
         "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop/FMA x 2070 MHz (FP32 CUDA cores)",
         "stage_ms_per_apply": {k: round(v, 5) for k, v in stages.items()},
         "stage_share": {k: round(v / apply_ms, 4) for k, v in stages.items()},

@@ -31,7 +31,7 @@ template <int N2> __host__ __device__ constexpr int tpr() { return N2 > N1 ? N2 
 // k1 pitch of the transpose buffer Y[k1][m2][coil]: an odd multiple of 8
 // float2 apart, so the two k1 rows of a half-warp fall on disjoint banks
 template <int N2> __host__ __device__ constexpr int ypitch() { return N2 * CB + 8; }
-template <int N2> __host__ __device__ constexpr int min_ctas() { return N2 == 20 ? 7 : 1; }
+template <int N2> __host__ __device__ constexpr int min_ctas() { return N2 == 20 ? 7 : (N2 == 32 ? 2 : 1); }
 
 __device__ __forceinline__ int wrap1(int a, int G) { return a < 0 ? a + G : (a >= G ? a - G : a); }
 
