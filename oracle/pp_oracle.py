@@ -361,6 +361,84 @@ def prox_l1_haar(v, lam, levels=2):
 
 
 # --------------------------------------------------------------------------
+# Daubechies-4 wavelet (the W of the experiments, Sec. 5.1 and Sec. 5.2) and
+# its l1 prox.  Reading: the four-coefficient orthonormal Daubechies filter
+# (two vanishing moments), periodic boundary, Mallat layout, every
+# coefficient thresholded.
+# --------------------------------------------------------------------------
+
+
+def db4_filters():
+    """Analysis low-pass h[0..3] = ((1+s3), (3+s3), (3-s3), (1-s3)) / (4 sqrt 2),
+    s3 = sqrt 3 (Daubechies' four-coefficient solution), and the high-pass
+    g[k] = (-1)^k h[3-k]."""
+    s3 = math.sqrt(3.0)
+    h = np.array([1 + s3, 3 + s3, 3 - s3, 1 - s3]) / (4.0 * math.sqrt(2.0))
+    g = np.array([(-1) ** k * h[3 - k] for k in range(4)])
+    return h, g
+
+
+def dwt1(x, axis):
+    """One periodic analysis step along `axis` (even length n):
+    a[i] = sum_k h[k] x[(2i+k) mod n], d[i] = sum_k g[k] x[(2i+k) mod n],
+    returned as [a, d] concatenated along the axis."""
+    h, g = db4_filters()
+    x = np.moveaxis(np.asarray(x, dtype=np.complex128), axis, 0)
+    n = x.shape[0]
+    a = np.zeros((n // 2,) + x.shape[1:], dtype=np.complex128)
+    d = np.zeros_like(a)
+    for i in range(n // 2):
+        for k in range(4):
+            a[i] += h[k] * x[(2 * i + k) % n]
+            d[i] += g[k] * x[(2 * i + k) % n]
+    return np.moveaxis(np.concatenate([a, d], axis=0), 0, axis)
+
+
+def idwt1(c, axis):
+    """Transpose of dwt1: x[j] = sum_i h[j - 2i] a[i] + g[j - 2i] d[i] over the
+    i with (j - 2i) mod n in 0..3."""
+    h, g = db4_filters()
+    c = np.moveaxis(np.asarray(c, dtype=np.complex128), axis, 0)
+    n = c.shape[0]
+    a, d = c[: n // 2], c[n // 2:]
+    x = np.zeros_like(c)
+    for i in range(n // 2):
+        for k in range(4):
+            x[(2 * i + k) % n] += h[k] * a[i] + g[k] * d[i]
+    return np.moveaxis(x, 0, axis)
+
+
+def db4_fwd(x, levels):
+    """2-D separable Daubechies-4 transform, `levels` levels, Mallat layout:
+    at each level rows (x) then columns (y) of the approximation band."""
+    out = np.array(x, dtype=np.complex128, copy=True)
+    for lev in range(levels):
+        h, w = out.shape[0] >> lev, out.shape[1] >> lev
+        out[:h, :w] = dwt1(dwt1(out[:h, :w], 1), 0)
+    return out
+
+
+def db4_inv(c, levels):
+    """Inverse (transpose) of db4_fwd."""
+    out = np.array(c, dtype=np.complex128, copy=True)
+    for lev in reversed(range(levels)):
+        h, w = out.shape[0] >> lev, out.shape[1] >> lev
+        out[:h, :w] = idwt1(idwt1(out[:h, :w], 0), 1)
+    return out
+
+
+def prox_l1_db4(v, lam, levels=2):
+    """prox_{lam ||W .||_1}(v) = W^T soft_lam(W v), W the orthonormal 2-D
+    Daubechies-4 transform."""
+    return db4_inv(soft_threshold(db4_fwd(v, levels), lam), levels)
+
+
+def wavelet_prox(wavelet):
+    """The prox of the chosen sparsifying transform (Eq. "proxdef")."""
+    return prox_l1_db4 if wavelet == "db4" else prox_l1_haar
+
+
+# --------------------------------------------------------------------------
 # Polynomial preconditioner: Eq. "l2cost" and the recursion of Listing "pcode"
 # --------------------------------------------------------------------------
 
@@ -453,7 +531,7 @@ def power_iteration(normal, shape, seed, iters=50):
 
 
 def pfista(normal, adjoint, b, lam, coeffs, iters, L, levels=2, normalize_b=True,
-           momentum=True, history=None):
+           momentum=True, history=None, wavelet="haar"):
     """Polynomial-preconditioned FISTA on the normalised problem.
 
     A_hat = A/sqrt(L), b_hat = b/||b|| (when normalize_b), N_hat = A_hat^H A_hat.
@@ -463,7 +541,8 @@ def pfista(normal, adjoint, b, lam, coeffs, iters, L, levels=2, normalize_b=True
         y_{k+1} = prox_{lam ||W.||_1}(z_k - u)
         beta_k  = k/(k+3)               (0 when momentum is False: Alg. "ppgd")
         z_{k+1} = y_{k+1} + beta_k (y_{k+1} - y_k)
-    Returns y_iters.  `history`, if a list, receives every y_{k+1}."""
+    Returns y_iters.  `history`, if a list, receives every y_{k+1}.
+    wavelet: "haar" (default) or "db4" for W in the prox."""
     b = np.asarray(b, dtype=np.complex128)
     bn = float(np.linalg.norm(b)) if normalize_b else 1.0
     ahb = adjoint(b) / (math.sqrt(L) * bn)
@@ -476,7 +555,7 @@ def pfista(normal, adjoint, b, lam, coeffs, iters, L, levels=2, normalize_b=True
     for k in range(iters):
         g = nhat(z) - ahb
         u = g if coeffs is None else horner_apply(coeffs, nhat, g)
-        y_new = prox_l1_haar(z - u, lam, levels)
+        y_new = wavelet_prox(wavelet)(z - u, lam, levels)
         beta = k / (k + 3.0) if momentum else 0.0
         z = y_new + beta * (y_new - y)
         y = y_new

@@ -99,3 +99,70 @@ def test_prox_non_expansive():
         b = synth.crandn((8, 8), 200 + s).astype(np.complex128)
         lhs = np.linalg.norm(O.prox_l1_haar(a, lam) - O.prox_l1_haar(b, lam))
         assert lhs <= np.linalg.norm(a - b) + 1e-14
+
+
+# ---- Daubechies-4 (the W of the paper's experiments, Sec. 5.1 / 5.2) ----
+
+
+def test_db4_filter_defining_properties():
+    # orthonormality to even shifts, unit DC gain sqrt 2, and two vanishing
+    # moments of the high-pass (it annihilates constants and ramps)
+    h, g = O.db4_filters()
+    assert abs(np.sum(h) - math.sqrt(2.0)) <= 1e-15
+    assert abs(np.sum(h * h) - 1.0) <= 1e-15
+    assert abs(h[0] * h[2] + h[1] * h[3]) <= 1e-16
+    k = np.arange(4)
+    assert abs(np.sum(g)) <= 1e-15
+    assert abs(np.sum(k * g)) <= 1e-14
+    assert abs(np.sum(k * k * g)) > 1e-3          # exactly two moments vanish
+    assert abs(np.sum(g * h)) <= 1e-16 and abs(g[0] * h[2] + g[1] * h[3]) <= 1e-16
+
+
+def test_db4_one_level_matrix_is_orthogonal():
+    n = 8
+    M = np.stack([O.dwt1(np.eye(n)[:, j], 0) for j in range(n)], axis=1)
+    assert np.max(np.abs(M.T @ M - np.eye(n))) <= 1e-14
+    assert np.max(np.abs(M @ M.T - np.eye(n))) <= 1e-14
+    # the inverse is the transpose
+    Minv = np.stack([O.idwt1(np.eye(n)[:, j], 0) for j in range(n)], axis=1)
+    assert np.max(np.abs(Minv - M.T)) <= 1e-14
+
+
+def test_db4_detail_of_a_ramp_vanishes_away_from_the_wrap():
+    n = 32
+    x = 0.3 * np.arange(n) - 1.7
+    c = O.dwt1(x, 0)
+    d = c[n // 2:]
+    assert np.max(np.abs(d[: n // 2 - 1])) <= 1e-13     # the last one straddles the wrap
+    assert abs(d[-1]) > 1e-3
+
+
+@pytest.mark.parametrize("shape,levels", [((16, 12), 1), ((16, 16), 2), ((32, 24), 3)])
+def test_db4_norm_and_inverse(shape, levels):
+    x = synth.crandn(shape, 3).astype(np.complex128)
+    c = O.db4_fwd(x, levels)
+    assert abs(np.linalg.norm(c) - np.linalg.norm(x)) <= 1e-13 * np.linalg.norm(x)
+    assert np.max(np.abs(O.db4_inv(c, levels) - x)) <= 1e-13
+
+
+def test_db4_differs_from_haar_and_keeps_constants_in_the_coarse_band():
+    x = np.full((16, 16), 2.0 + 1.0j)
+    c = O.db4_fwd(x, 2)
+    mask = np.zeros((16, 16), bool)
+    mask[:4, :4] = True
+    assert np.max(np.abs(c[~mask])) <= 1e-13
+    y = synth.crandn((16, 16), 4).astype(np.complex128)
+    assert np.linalg.norm(O.db4_fwd(y, 1) - O.haar_fwd(y, 1)) > 0.1 * np.linalg.norm(y)
+
+
+def test_db4_prox_optimality_and_non_expansiveness():
+    lam = 0.3
+    v = synth.crandn((16, 24), 5).astype(np.complex128)
+    y = O.prox_l1_db4(v, lam, 2)
+    cv, cy = O.db4_fwd(v, 2), O.db4_fwd(y, 2)
+    on = np.abs(cy) > 1e-12     # zeros come back from the round trip at the 1e-16 level
+    # v - y = lam W^T s with s_i = c_i/|c_i| where c_i != 0, |s_i| <= 1 elsewhere
+    assert np.max(np.abs((cv - cy)[on] - lam * cy[on] / np.abs(cy[on]))) <= 1e-12
+    assert np.max(np.abs(cv[~on])) <= lam + 1e-12
+    w = synth.crandn((16, 24), 6).astype(np.complex128)
+    assert np.linalg.norm(O.prox_l1_db4(v, lam, 2) - O.prox_l1_db4(w, lam, 2)) <= np.linalg.norm(v - w) + 1e-12
