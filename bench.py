@@ -62,6 +62,9 @@ def parse():
                          "its operator K times and exit without a bench line")
     ap.add_argument("--tuning", default="",
                     help="with --apply-only: row_ifft_variant,stencil_kind,stencil_coils to force")
+    ap.add_argument("--wavelet", choices=["haar", "db4"], default="haar",
+                    help="spiral workload: W of the prox, the 2-level Haar or the Daubechies-4 "
+                         "(the paper's choice)")
     ap.add_argument("--operator", choices=["gridding", "toeplitz"], default="gridding",
                     help="spiral workload: the gridding normal operator (G^T G stencil) or the "
                          "exact F^H F through its Toeplitz embedding")
@@ -377,7 +380,7 @@ def main():
     applies_per_step = iters * (d + 1)
 
     for _ in range(args.warmup):
-        pp.pp_fista_solve(plan, b, lam, iters, coeffs, d, x_out)
+        pp.pp_fista_solve(plan, b, lam, iters, coeffs, d, x_out, wavelet=args.wavelet)
     torch.cuda.synchronize()
 
     # L2 is 129 MB and the solve's working set (~80 MB) fits in it: flush it
@@ -393,7 +396,7 @@ def main():
         for i in range(args.steps):
             flush.zero_()
             ev[i][0].record(stream)
-            r = pp.pp_fista_solve(plan, b, lam, iters, coeffs, d, x_out)
+            r = pp.pp_fista_solve(plan, b, lam, iters, coeffs, d, x_out, wavelet=args.wavelet)
             ev[i][1].record(stream)
             launches += r.launches
         torch.cuda.synchronize()
@@ -432,7 +435,9 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded phantom, coil maps, spiral, noise); no datasets",
-        "config": {"workload": WORKLOAD + ("_toeplitz" if toep else ""), "image": list(shape),
+        "config": {"workload": WORKLOAD + ("_toeplitz" if toep else "") +
+                               ("_db4" if args.wavelet == "db4" else ""), "image": list(shape),
+                   "wavelet": ("Daubechies-4, 2 levels" if args.wavelet == "db4" else "Haar, 2 levels"),
                    "coils": C, "samples": K,
                    "normal_operator": ("exact F^H F by its 2ny x 2nx Toeplitz embedding" if toep else
                                        "Kaiser-Bessel gridding, precomputed G^T G stencil"),
@@ -456,7 +461,7 @@ def main():
             flush.zero_()
             ee[i][0].record(stream)
             b_dev.copy_(b_host, non_blocking=True)
-            pp.pp_fista_solve(plan, b_dev, lam, iters, coeffs, d, x_out)
+            pp.pp_fista_solve(plan, b_dev, lam, iters, coeffs, d, x_out, wavelet=args.wavelet)
             x_host.copy_(x_out, non_blocking=True)
             ee[i][1].record(stream)
         torch.cuda.synchronize()
@@ -465,7 +470,8 @@ def main():
                       "unit": UNIT, "h2d_bytes_per_step": b_host.numel() * 8,
                       "d2h_bytes_per_step": x_host.numel() * 8}
         # --- time to NRMSE <= 1e-3 against each method's own converged solution ---
-        out["time_to_nrmse"] = time_to_target(pp, plan, b, c, coeffs, setup_plan_s, stream)
+        out["time_to_nrmse"] = time_to_target(pp, plan, b, c, coeffs, setup_plan_s, stream,
+                                              wavelet=args.wavelet)
         if rank == 0 and world == 1:
             out["cpu_baseline"] = cpu_baseline(c, sens, traj, exact=toep)
     if rank == 0:
@@ -475,7 +481,7 @@ def main():
         dist.destroy_process_group()
 
 
-def time_to_target(pp, plan, b, c, coeffs, setup_s, stream, target=1e-3):
+def time_to_target(pp, plan, b, c, coeffs, setup_s, stream, target=1e-3, wavelet="haar"):
     """Per method: converged y_inf (20x the iteration count), the first k
     with ||y_k - y_inf|| / ||y_inf|| <= target, per-iteration time from a
     timed graph replay, and time = setup + k * T_iter."""
@@ -485,20 +491,20 @@ def time_to_target(pp, plan, b, c, coeffs, setup_s, stream, target=1e-3):
     for name, cc, dd in (("preconditioned_d%d" % d, coeffs, d), ("plain_fista", None, 0)):
         n_inf = 20 * iters
         y_inf = torch.empty(shape, dtype=torch.complex64, device=b.device)
-        pp.pp_fista_solve(plan, b, lam, n_inf, cc, dd, y_inf)
+        pp.pp_fista_solve(plan, b, lam, n_inf, cc, dd, y_inf, wavelet=wavelet)
         y = torch.empty_like(y_inf)
-        r = pp.pp_fista_solve(plan, b, lam, n_inf, cc, dd, y, history=True, ref=y_inf)
+        r = pp.pp_fista_solve(plan, b, lam, n_inf, cc, dd, y, history=True, ref=y_inf, wavelet=wavelet)
         nrm = float(torch.linalg.vector_norm(y_inf.to(torch.complex128)).item())
         err = np.sqrt(np.maximum(r.history[:, 2], 0.0)) / nrm
         hit = np.flatnonzero(err <= target)
         k_star = int(hit[0]) + 1 if hit.size else None
         # per-iteration time: timed replay of `iters` iterations
-        pp.pp_fista_solve(plan, b, lam, iters, cc, dd, y)
+        pp.pp_fista_solve(plan, b, lam, iters, cc, dd, y, wavelet=wavelet)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         e0.record(stream)
         for _ in range(5):
-            pp.pp_fista_solve(plan, b, lam, iters, cc, dd, y)
+            pp.pp_fista_solve(plan, b, lam, iters, cc, dd, y, wavelet=wavelet)
         e1.record(stream)
         torch.cuda.synchronize()
         t_iter = e0.elapsed_time(e1) / 1e3 / (5 * iters)

@@ -215,6 +215,20 @@ pp_status pp_poly_apply(const pp_plan* plan, const double* c, int d, const pp_c6
 pp_status pp_prox_l1_haar(pp_dims dims, int levels, float lambda, const pp_c64* in, pp_c64* out,
                           pp_stream stream);
 
+/* prox_{lambda ||W.||_1}(in) = W^T soft_lambda(W in) (Eq. "proxdef") with W the
+ * orthonormal Daubechies-4 wavelet, the transform of the paper's experiments
+ * (Sec. 5.1, Sec. 5.2): the four-coefficient Daubechies filter
+ * h = ((1+sqrt3), (3+sqrt3), (3-sqrt3), (1-sqrt3)) / (4 sqrt2), high-pass
+ * g[k] = (-1)^k h[3-k], periodic boundary, separable, `levels` levels in
+ * Mallat layout; every coefficient is soft-thresholded.
+ *   dims    2-D only; nx, ny <= 512 and multiples of 2^levels; levels 1..4
+ *           (else PP_ERR_UNSUPPORTED).
+ *   in/out  device [ny][nx] complex64; out may equal in.
+ * Runs as 4 * levels kernels on `stream` (each level couples neighbouring
+ * rows and columns, so the transform is not tile-local like the Haar). */
+pp_status pp_prox_l1_db4(pp_dims dims, int levels, float lambda, const pp_c64* in, pp_c64* out,
+                         pp_stream stream);
+
 /* Optional solve inputs/outputs.
  *  history  host double [iters][3] or NULL.  Row k receives, as FP64
  *           reductions on the device, ||y_{k+1} - y_k||^2, ||y_{k+1}||^2 and
@@ -232,6 +246,9 @@ typedef struct {
     double bnorm;        /* out: ||b||_2 (valid when history != NULL)        */
     double L;            /* out: the L used                                  */
     int64_t launches;    /* out: kernels enqueued by this call               */
+    int wavelet;         /* in: W of the prox: 0 = orthonormal Haar (levels
+                            1..2), 1 = Daubechies-4 (2-D, levels 1..4), see
+                            pp_prox_l1_db4; else PP_ERR_INVALID_ARG         */
 } pp_solve_info;
 
 /* Algorithm "pfista" on the normalised problem (Sec. 5): A_hat = A/sqrt(L),

@@ -43,7 +43,8 @@ class pp_sampling(ctypes.Structure):
 class pp_solve_info(ctypes.Structure):
     _fields_ = [("rescale", ctypes.c_int), ("levels", ctypes.c_int), ("no_momentum", ctypes.c_int),
                 ("history", ctypes.c_void_p), ("ref", ctypes.c_void_p),
-                ("bnorm", ctypes.c_double), ("L", ctypes.c_double), ("launches", ctypes.c_int64)]
+                ("bnorm", ctypes.c_double), ("L", ctypes.c_double), ("launches", ctypes.c_int64),
+                ("wavelet", ctypes.c_int)]
 
 
 _lib = None
@@ -70,6 +71,8 @@ _SIGS = {
                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "pp_prox_l1_haar": (ctypes.c_int, [pp_dims, ctypes.c_int, ctypes.c_float, ctypes.c_void_p,
                                        ctypes.c_void_p, ctypes.c_void_p]),
+    "pp_prox_l1_db4": (ctypes.c_int, [pp_dims, ctypes.c_int, ctypes.c_float, ctypes.c_void_p,
+                                      ctypes.c_void_p, ctypes.c_void_p]),
     "pp_fista_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_float, ctypes.c_int,
                                       ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_void_p,
                                       ctypes.POINTER(pp_solve_info), ctypes.c_void_p]),
@@ -328,6 +331,16 @@ def pp_prox_l1_haar(shape, levels: int, lam: float, x_in, x_out, stream=None):
                                  _dev_ptr(x_out, "out"), _stream(stream)), "pp_prox_l1_haar")
 
 
+def pp_prox_l1_db4(shape, levels: int, lam: float, x_in, x_out, stream=None):
+    _numel(x_in, int(np.prod(shape)), "in")
+    _numel(x_out, int(np.prod(shape)), "out")
+    _check(lib().pp_prox_l1_db4(_dims(shape), int(levels), float(lam), _dev_ptr(x_in, "in"),
+                                _dev_ptr(x_out, "out"), _stream(stream)), "pp_prox_l1_db4")
+
+
+WAVELETS = {"haar": 0, "db4": 1}
+
+
 class SolveResult:
     """What pp_fista_solve reports besides x_out."""
 
@@ -340,10 +353,12 @@ class SolveResult:
 
 def pp_fista_solve(plan: Plan, b, lam: float, iters: int, c, d: int, x_out, stream=None,
                    history: bool = False, rescale: bool = False, levels: int = 2,
-                   ref=None, momentum: bool = True) -> SolveResult:
+                   ref=None, momentum: bool = True, wavelet: str = "haar") -> SolveResult:
     """c None with d = 0: plain FISTA.  history: per-iteration FP64
-    ||y_{k+1}-y_k||^2, ||y_{k+1}||^2, ||y_{k+1}-ref||^2 (ref optional)."""
+    ||y_{k+1}-y_k||^2, ||y_{k+1}||^2, ||y_{k+1}-ref||^2 (ref optional).
+    wavelet: "haar" or "db4" (Daubechies-4, 2-D) for the prox's W."""
     info = pp_solve_info()
+    info.wavelet = WAVELETS[wavelet]
     info.rescale = 1 if rescale else 0
     info.levels = int(levels)
     info.no_momentum = 0 if momentum else 1

@@ -721,7 +721,7 @@ static pp_status horner_into(const Plan& p, const double* c, int d, const float2
 
 static pp_status fista_iterations(Plan& p, float lambda, int iters, const double* c, int d,
                                   int levels, bool hist, const float2* ref, bool momentum,
-                                  cudaStream_t st) {
+                                  int wavelet, cudaStream_t st) {
     const float invL = (float)(1.0 / p.L);
     for (int k = 0; k < iters; ++k) {
         // g = N_hat z - A_hat^H b_hat
@@ -735,8 +735,12 @@ static pp_status fista_iterations(Plan& p, float lambda, int iters, const double
             gamma = (float)c[0];
         }
         const float beta = momentum ? (float)((double)k / (k + 3.0)) : 0.f;
-        PP_TRY(launch_prox_fista(p, levels, lambda, gamma, beta, u, hist ? ref : nullptr,
-                                 hist ? p.hist + 3 * k : nullptr, st));
+        if (wavelet == 1)   // Daubechies-4: multi-pass, p.t (free after Horner) holds the coefficients
+            PP_TRY(launch_prox_fista_db4(p, levels, lambda, gamma, beta, u, p.t, hist ? ref : nullptr,
+                                         hist ? p.hist + 3 * k : nullptr, st));
+        else
+            PP_TRY(launch_prox_fista(p, levels, lambda, gamma, beta, u, hist ? ref : nullptr,
+                                     hist ? p.hist + 3 * k : nullptr, st));
     }
     return PP_OK;
 }
@@ -1497,6 +1501,20 @@ pp_status pp_prox_l1_haar(pp_dims dims, int levels, float lambda, const pp_c64* 
                        reinterpret_cast<float2*>(out), (cudaStream_t)stream);
 }
 
+pp_status pp_prox_l1_db4(pp_dims dims, int levels, float lambda, const pp_c64* in, pp_c64* out,
+                         pp_stream stream) {
+    if (!in || !out || (dims.ndim != 2 && dims.ndim != 3) || !(lambda >= 0.f) || !isfinite(lambda)) {
+        set_error("pp_prox_l1_db4: bad argument");
+        return PP_ERR_INVALID_ARG;
+    }
+    if (!db4_supported(dims.ndim, dims.n[0], dims.n[1], levels)) {
+        set_error("pp_prox_l1_db4: 2-D only, levels 1..4, axes <= 512 and multiples of 2^levels");
+        return PP_ERR_UNSUPPORTED;
+    }
+    return launch_prox_db4(dims.n[0], dims.n[1], levels, lambda, reinterpret_cast<const float2*>(in),
+                           reinterpret_cast<float2*>(out), (cudaStream_t)stream);
+}
+
 pp_status pp_fista_solve(pp_plan* plan, const pp_c64* b, float lambda, int iters, const double* c,
                          int d, pp_c64* x_out, pp_solve_info* info, pp_stream stream) {
     if (!plan || !b || !x_out || iters < 0 || iters > 1000000 || !(lambda >= 0.f) ||
@@ -1507,8 +1525,18 @@ pp_status pp_fista_solve(pp_plan* plan, const pp_c64* b, float lambda, int iters
     Plan& p = plan->impl;
     cudaStream_t st = (cudaStream_t)stream;
     const int levels = (info && info->levels) ? info->levels : 2;
-    if (levels < 1 || levels > 2 || p.nx % (1 << levels) || p.ny % (1 << levels) ||
-        (p.ndim == 3 && p.nz % (1 << levels))) {
+    const int wavelet = info ? info->wavelet : 0;
+    if (wavelet != 0 && wavelet != 1) {
+        set_error("pp_fista_solve: wavelet must be 0 (Haar) or 1 (Daubechies-4)");
+        return PP_ERR_INVALID_ARG;
+    }
+    if (wavelet == 1 && !db4_supported(p.ndim, p.nx, p.ny, levels)) {
+        set_error("pp_fista_solve: the Daubechies-4 prox is 2-D with levels 1..4 and axes "
+                  "multiples of 2^levels");
+        return PP_ERR_UNSUPPORTED;
+    }
+    if (wavelet == 0 && (levels < 1 || levels > 2 || p.nx % (1 << levels) || p.ny % (1 << levels) ||
+                         (p.ndim == 3 && p.nz % (1 << levels)))) {
         set_error("pp_fista_solve: unsupported Haar levels");
         return PP_ERR_UNSUPPORTED;
     }
@@ -1541,7 +1569,7 @@ pp_status pp_fista_solve(pp_plan* plan, const pp_c64* b, float lambda, int iters
         std::vector<double> key = {(double)iters, (double)d, (double)lambda, (double)levels,
                                    hist ? 1.0 : 0.0, c ? 1.0 : 0.0, p.L,
                                    (double)(uintptr_t)p.hist, (double)(uintptr_t)ref,
-                                   momentum ? 1.0 : 0.0};
+                                   momentum ? 1.0 : 0.0, (double)wavelet};
         if (c)
             for (int i = 0; i <= d; ++i) key.push_back(c[i]);
         if (!p.gexec || key != p.gkey) {
@@ -1554,7 +1582,7 @@ pp_status pp_fista_solve(pp_plan* plan, const pp_c64* b, float lambda, int iters
             PP_TRY_CUDA(cudaStreamBeginCapture(p.cap_stream, cudaStreamCaptureModeThreadLocal));
             const int64_t before = g_launches;
             pp_status rc = fista_iterations(p, lambda, iters, c, d, levels, hist, ref, momentum,
-                                            p.cap_stream);
+                                            wavelet, p.cap_stream);
             cudaError_t e = cudaStreamEndCapture(p.cap_stream, &graph);
             p.graph_kernels = g_launches - before;
             g_launches = before;
@@ -1911,6 +1939,10 @@ pp_status pp_batch_fista_solve(pp_batch* batch, const pp_c64* bk, float lambda, 
     }
     if (info && info->levels && info->levels != 2) {
         set_error("pp_batch_fista_solve: batched prox supports 2 Haar levels only");
+        return PP_ERR_UNSUPPORTED;
+    }
+    if (info && info->wavelet) {
+        set_error("pp_batch_fista_solve: the batched prox is the 2-level Haar");
         return PP_ERR_UNSUPPORTED;
     }
     Batch& b = batch->impl;

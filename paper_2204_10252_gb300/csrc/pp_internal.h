@@ -262,6 +262,12 @@ size_t toep_rows_elems(const Plan& p);
 pp_status toep_normal(const Plan& p, const float2* x, float2* out, float scale,
                       const float2* operand, float alpha, cudaStream_t st);
 pp_status toep_build_kernel(Plan& p, const float* traj, int64_t K, cudaStream_t st);
+bool db4_supported(int ndim, int nx, int ny, int levels);
+pp_status launch_prox_db4(int nx, int ny, int levels, float lambda, const float2* in, float2* out,
+                          cudaStream_t st);
+pp_status launch_prox_fista_db4(const Plan& p, int levels, float lambda, float gamma, float beta,
+                                const float2* u, float2* scratch, const float2* ref, double* hist_slot,
+                                cudaStream_t st);
 pp_status ci_normal(const Plan& p, const float2* x, float2* out, float scale, const float2* operand,
                     float alpha, int ry, cudaStream_t st);   // ry 0: coil-pair stencil
 pp_status launch_nufft_degrid(const Plan& p, const float2* grid_in, float2* ksp, cudaStream_t st);

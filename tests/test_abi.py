@@ -101,6 +101,20 @@ def test_invalid_arguments_are_rejected_without_device_work(L):
     d.n[0] = 62
     assert L.pp_prox_l1_haar(d, 2, ctypes.c_float(0.1), ctypes.c_void_p(16), ctypes.c_void_p(16), None) == 2
     assert L.pp_prox_l1_haar(d, 1, ctypes.c_float(-1.0), ctypes.c_void_p(16), ctypes.c_void_p(16), None) == 1
+    # Daubechies-4 prox: 2-D, levels 1..4, axes <= 512 and multiples of 2^levels
+    d.n[0] = 64
+    assert L.pp_prox_l1_db4(d, 5, ctypes.c_float(0.1), ctypes.c_void_p(16), ctypes.c_void_p(16), None) == 2
+    d.n[0] = 40
+    assert L.pp_prox_l1_db4(d, 4, ctypes.c_float(0.1), ctypes.c_void_p(16), ctypes.c_void_p(16), None) == 2
+    d.n[0] = 1024
+    assert L.pp_prox_l1_db4(d, 1, ctypes.c_float(0.1), ctypes.c_void_p(16), ctypes.c_void_p(16), None) == 2
+    d.ndim = 3
+    d.n[0] = d.n[2] = 16
+    assert L.pp_prox_l1_db4(d, 1, ctypes.c_float(0.1), ctypes.c_void_p(16), ctypes.c_void_p(16), None) == 2
+    d.ndim = 2
+    d.n[0] = 64
+    assert L.pp_prox_l1_db4(d, 2, ctypes.c_float(-0.5), ctypes.c_void_p(16), ctypes.c_void_p(16), None) == 1
+    d.n[0] = 62
     # solve / applies with NULL plans
     assert L.pp_normal_apply(None, ctypes.c_void_p(16), ctypes.c_void_p(32), None) == 1
     assert L.pp_fista_solve(None, ctypes.c_void_p(16), ctypes.c_float(0.1), 1, None, 0,
