@@ -462,6 +462,25 @@ def poly_coeffs_l2(d):
     return [a[i][n] / a[i][i] for i in range(n)]
 
 
+def poly_coeffs_wl2(d, moments):
+    """Minimiser c[0..d] of the weighted cost of Eq. "wl2cost",
+    int_0^1 w(z) (1 - z sum_i c_i z^i)^2 dz, from the weight's moments
+    m_k = int_0^1 w(z) z^k dz (k = 0..2d+2).  Expanding the square, the
+    normal equations are G c = h with G_ij = m_{i+j+2} and h_i = m_{i+1};
+    with rational moments (Fractions) they are solved exactly."""
+    n = d + 1
+    m = list(moments)
+    a = [[m[i + j + 2] for j in range(n)] + [m[i + 1]] for i in range(n)]
+    for col in range(n):
+        piv = max(range(col, n), key=lambda r: abs(a[r][col]))
+        a[col], a[piv] = a[piv], a[col]
+        for r in range(n):
+            if r != col and a[r][col] != 0:
+                f = a[r][col] / a[col][col]
+                a[r] = [a[r][k] - f * a[col][k] for k in range(n + 1)]
+    return [a[i][n] / a[i][i] for i in range(n)]
+
+
 def poly_eval(c, z):
     """p(z) = sum_i c[i] z^i (coefficient order of Sec. 3.6)."""
     z = np.asarray(z, dtype=np.float64)

@@ -140,3 +140,44 @@ def test_chebyshev_beats_l2_in_the_max_norm_on_mu_1(d):
     cheb = np.max(np.abs(1 - zz * O.poly_eval(O.poly_coeffs_cheb(d, mu), zz)))
     l2 = np.max(np.abs(1 - zz * O.poly_eval(O.poly_coeffs_l2(d), zz)))
     assert cheb < l2
+
+
+# ---- weighted l2 design, Eq. "wl2cost" ----
+
+
+def _moments(weight_terms, d):
+    # w(z) = sum_t a_t z^e_t  ->  m_k = sum_t a_t / (k + e_t + 1), exact
+    return [sum(Fraction(a) / (k + e + 1) for a, e in weight_terms) for k in range(2 * d + 3)]
+
+
+@pytest.mark.parametrize("d", range(0, 9))
+def test_wl2_with_unit_weight_is_the_l2_design(d):
+    assert O.poly_coeffs_wl2(d, _moments([(1, 0)], d)) == O.poly_coeffs_l2(d)
+
+
+@pytest.mark.parametrize("d", [1, 3, 5])
+@pytest.mark.parametrize("terms", [[(1, 1)], [(1, 0), (3, 2)], [(2, 0), (-1, 1)]])
+def test_wl2_matches_weighted_least_squares_by_quadrature(d, terms):
+    # independent route: Gauss-Legendre nodes on [0, 1] (exact for these
+    # polynomial integrands), weighted least squares on the discretised cost
+    c = np.array([float(v) for v in O.poly_coeffs_wl2(d, _moments(terms, d))])
+    xg, wg = np.polynomial.legendre.leggauss(40)
+    z, wq = (xg + 1) / 2, wg / 2
+    w = sum(a * z ** e for a, e in terms)
+    assert np.all(w > 0)
+    A = np.stack([z ** (i + 1) for i in range(d + 1)], axis=1) * np.sqrt(wq * w)[:, None]
+    rhs = np.sqrt(wq * w)
+    ref, *_ = np.linalg.lstsq(A, rhs, rcond=None)
+    assert np.max(np.abs(c - ref)) <= 1e-7 * np.max(np.abs(ref))
+
+
+def test_wl2_weight_shifts_the_residual_where_it_is_heavy():
+    # a weight concentrated near z = 1 lowers |1 - z p(z)| there relative to
+    # the unweighted design
+    d = 3
+    cw = [float(v) for v in O.poly_coeffs_wl2(d, _moments([(1, 6)], d))]
+    cu = [float(v) for v in O.poly_coeffs_l2(d)]
+    z = np.linspace(0.8, 1.0, 50)
+    rw = np.abs(1 - z * O.poly_eval(cw, z))
+    ru = np.abs(1 - z * O.poly_eval(cu, z))
+    assert np.mean(rw) < np.mean(ru)
