@@ -201,6 +201,17 @@ pp_status pp_poly_coeffs_l2(int d, double* c);
  * Host only. */
 pp_status pp_poly_coeffs_cheb(int d, double mu, double* c);
 
+/* c[0..d] (host double) minimising the weighted cost of Eq. "wl2cost",
+ * int_0^1 w(z) (1 - z p(z))^2 dz, for a weight given by its moments
+ * moments[k] = int_0^1 w(z) z^k dz, k = 0..2d+2 (host double; moments[0] is
+ * not used).  The paper leaves the choice of w open (a prior on the spectrum
+ * of A^H A); w = 1 (moments 1/(k+1)) gives pp_poly_coeffs_l2.  Solves the
+ * normal equations sum_j m_{i+j+2} c_j = m_{i+1} by LU with partial
+ * pivoting and compensated iterative refinement.  0 <= d <= 8; moments that
+ * give singular equations (no positive weight) -> PP_ERR_INVALID_ARG.  Host
+ * only; no device work. */
+pp_status pp_poly_coeffs_wl2(int d, const double* moments, double* c);
+
 /* out = p(N_hat) v by the recursion of Listing "pcode": u = c_d v, then
  * u = c_i v + N_hat u for i = d-1..0 (d applies of N_hat).  c host double
  * [d+1], 0 <= d <= 16.  v, out device images. */

@@ -67,6 +67,8 @@ _SIGS = {
     "pp_normal_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "pp_poly_coeffs_l2": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "pp_poly_coeffs_cheb": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]),
+    "pp_poly_coeffs_wl2": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                          ctypes.POINTER(ctypes.c_double)]),
     "pp_poly_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int,
                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "pp_prox_l1_haar": (ctypes.c_int, [pp_dims, ctypes.c_int, ctypes.c_float, ctypes.c_void_p,
@@ -311,6 +313,17 @@ def pp_poly_coeffs_l2(d: int) -> np.ndarray:
 def pp_poly_coeffs_cheb(d: int, mu: float) -> np.ndarray:
     c = (ctypes.c_double * (max(d, 0) + 1))()
     _check(lib().pp_poly_coeffs_cheb(int(d), float(mu), c), "pp_poly_coeffs_cheb")
+    return np.array(list(c), dtype=np.float64)
+
+
+def pp_poly_coeffs_wl2(d: int, moments) -> np.ndarray:
+    """Eq. "wl2cost" design; moments[k] = int_0^1 w(z) z^k dz, k = 0..2d+2."""
+    m = np.ascontiguousarray(moments, dtype=np.float64)
+    if m.ndim != 1 or m.size < 2 * max(d, 0) + 3:
+        raise ValueError("need the moments m_0 .. m_{2d+2}")
+    c = (ctypes.c_double * (max(d, 0) + 1))()
+    mv = (ctypes.c_double * m.size)(*m.tolist())
+    _check(lib().pp_poly_coeffs_wl2(int(d), mv, c), "pp_poly_coeffs_wl2")
     return np.array(list(c), dtype=np.float64)
 
 

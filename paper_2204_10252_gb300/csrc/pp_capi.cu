@@ -2,6 +2,8 @@
 // Horner recursion of Listing "pcode" and Algorithm "pfista" (Sec. 3.1, 3.6).
 #include <cuda_runtime.h>
 #include <math.h>
+
+#include <cmath>
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
@@ -1176,6 +1178,94 @@ pp_status pp_poly_coeffs_l2(int d, double* c) {
         for (int j = k; j <= m; ++j) S += (long long)(2 * j + 1) * binom(j, k) * binom(j + k, k);
         c[i] = ((k + 1) % 2 == 0 ? 1.0 : -1.0) * (double)S / den;
     }
+    return PP_OK;
+}
+
+// r_i = h_i - sum_j G_ij c_j with the products' rounding errors (fma) and the
+// sum's (two-sum) carried in a second word: the residual of a Hankel system
+// whose condition grows like that of the Hilbert matrix.
+static double residual_dd(const double* G, const double* h, const double* c, int n, int i) {
+    double hi = h[i], lo = 0.0;
+    for (int j = 0; j < n; ++j) {
+        const double p = G[i * n + j] * c[j];
+        const double pe = std::fma(G[i * n + j], c[j], -p);
+        const double s = hi - p;
+        const double bb = s - hi;
+        lo += ((hi - (s - bb)) + (-p - bb)) - pe;
+        hi = s;
+    }
+    return hi + lo;
+}
+
+pp_status pp_poly_coeffs_wl2(int d, const double* moments, double* c) {
+    if (!c || !moments || d < 0 || d > 8) {
+        set_error("pp_poly_coeffs_wl2: need 0 <= d <= 8 and non-NULL moments, c");
+        return PP_ERR_INVALID_ARG;
+    }
+    for (int k = 0; k <= 2 * d + 2; ++k)
+        if (!std::isfinite(moments[k])) {
+            set_error("pp_poly_coeffs_wl2: moment %d is not finite", k);
+            return PP_ERR_INVALID_ARG;
+        }
+    // normal equations of int_0^1 w (1 - z p)^2: sum_j m_{i+j+2} c_j = m_{i+1}
+    const int n = d + 1;
+    double G[81], h[9], LU[81];
+    int piv[9];
+    for (int i = 0; i < n; ++i) {
+        h[i] = moments[i + 1];
+        for (int j = 0; j < n; ++j) G[i * n + j] = LU[i * n + j] = moments[i + j + 2];
+    }
+    double gmax = 0.0;
+    for (int i = 0; i < n * n; ++i) gmax = std::max(gmax, std::fabs(G[i]));
+    // LU with partial pivoting
+    for (int k = 0; k < n; ++k) {
+        int p = k;
+        for (int r = k + 1; r < n; ++r)
+            if (std::fabs(LU[r * n + k]) > std::fabs(LU[p * n + k])) p = r;
+        piv[k] = p;
+        if (!(std::fabs(LU[p * n + k]) > 1e-15 * gmax)) {
+            set_error("pp_poly_coeffs_wl2: the moments do not define a positive weight "
+                      "(singular normal equations)");
+            return PP_ERR_INVALID_ARG;
+        }
+        if (p != k)
+            for (int j = 0; j < n; ++j) std::swap(LU[k * n + j], LU[p * n + j]);
+        for (int r = k + 1; r < n; ++r) {
+            LU[r * n + k] /= LU[k * n + k];
+            for (int j = k + 1; j < n; ++j) LU[r * n + j] -= LU[r * n + k] * LU[k * n + j];
+        }
+    }
+    auto lu_solve = [&](double* x) {
+        for (int k = 0; k < n; ++k) std::swap(x[k], x[piv[k]]);
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < i; ++j) x[i] -= LU[i * n + j] * x[j];
+        for (int i = n - 1; i >= 0; --i) {
+            for (int j = i + 1; j < n; ++j) x[i] -= LU[i * n + j] * x[j];
+            x[i] /= LU[i * n + i];
+        }
+    };
+    for (int i = 0; i < n; ++i) c[i] = h[i];
+    lu_solve(c);
+    // iterative refinement with compensated residuals: each step multiplies
+    // the error by about cond(G) * 2^-53, which stays below 1 up to d = 8 for
+    // weights that are not extremely concentrated; stop once the correction
+    // no longer changes c
+    for (int it = 0; it < 60; ++it) {
+        double r[9], dmax = 0.0, cmax = 0.0;
+        for (int i = 0; i < n; ++i) r[i] = residual_dd(G, h, c, n, i);
+        lu_solve(r);
+        for (int i = 0; i < n; ++i) {
+            c[i] += r[i];
+            dmax = std::max(dmax, std::fabs(r[i]));
+            cmax = std::max(cmax, std::fabs(c[i]));
+        }
+        if (!(dmax > 1e-17 * cmax)) break;
+    }
+    for (int i = 0; i < n; ++i)
+        if (!std::isfinite(c[i])) {
+            set_error("pp_poly_coeffs_wl2: non-finite coefficients");
+            return PP_ERR_NONFINITE;
+        }
     return PP_OK;
 }
 

@@ -164,3 +164,31 @@ def test_chebyshev_coefficients_match_oracle(L, d, mu):
     assert np.max(np.abs(got - ref)) <= 1e-10 * np.max(np.abs(ref))
     with pytest.raises(pp.PPError):
         pp.pp_poly_coeffs_cheb(3, 1.5)
+
+
+@pytest.mark.parametrize("d", [0, 1, 3, 5, 8])
+@pytest.mark.parametrize("terms", [[(1, 0)], [(1, 1)], [(1, 0), (3, 2)], [(2, 0), (-1, 1)], [(1, 6)]])
+def test_weighted_l2_coefficients_match_oracle(L, d, terms):
+    # host-only entry point: the library's LU + refinement against the
+    # oracle's exact rational solution of Eq. "wl2cost"
+    import paper_2204_10252_gb300 as pp
+    from oracle import pp_oracle as O
+    # the normal equations are Hankel (Hilbert-like: condition ~1e13 at d = 8),
+    # so rounding the moments to double already moves the solution by up to
+    # cond * 1e-16; the oracle therefore solves, exactly, the system of the
+    # same double moments the library receives
+    mom = [float(sum(Fraction(a) / (k + e + 1) for a, e in terms)) for k in range(2 * d + 3)]
+    ref = np.array([float(v) for v in O.poly_coeffs_wl2(d, [Fraction(m) for m in mom])])
+    got = pp.pp_poly_coeffs_wl2(d, mom)
+    assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
+    if terms == [(1, 0)] and d <= 3:
+        assert np.max(np.abs(got - pp.pp_poly_coeffs_l2(d))) <= 1e-10 * np.max(np.abs(ref))
+
+
+def test_weighted_l2_rejects_a_zero_weight(L):
+    import paper_2204_10252_gb300 as pp
+    with pytest.raises(pp.PPError) as e:
+        pp.pp_poly_coeffs_wl2(3, np.zeros(9))
+    assert e.value.status == 1
+    with pytest.raises(ValueError):
+        pp.pp_poly_coeffs_wl2(3, np.ones(5))
