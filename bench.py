@@ -187,6 +187,10 @@ def kernel_flops(c, K, toeplitz=False):
             "ci_rows_fwd_kernel": C * ny * fft(Mx) + 6.0 * C * n,
             "toep_cols_kernel": C * Mx * 2 * fft(My) + 2.0 * C * Mx * My,
             "ci_rows_inv_cl_kernel": C * ny * fft(Mx) + 8.0 * C * n + 4.0 * n,
+            # the same rows as two length-nx halves (the algorithmic count stays that of
+            # the length-2nx transform, so the two forms compare directly)
+            "toep_rows_fwd_half_kernel": C * ny * fft(Mx) + 6.0 * C * n,
+            "toep_rows_inv_half_cl_kernel": C * ny * fft(Mx) + 8.0 * C * n + 4.0 * n,
         }
     return {
         "rows_fwd_kernel": C * ny * fft(G) + 8.0 * C * n,

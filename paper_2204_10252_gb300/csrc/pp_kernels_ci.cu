@@ -537,6 +537,177 @@ toep_cols_kernel(const float2* __restrict__ tw, const float* __restrict__ Tc, in
     }
 }
 
+// Toeplitz row stages on length-n halves.  The row of the M = 2n embedding
+// holds the n image samples at positions [-n/2, n/2) mod M and zeros
+// elsewhere, so its length-M DFT splits into two length-n DFTs of the folded
+// row y[p] = x[(p + n/2) mod n] (p < n):
+//   X[2k]     = FFT_n(y)[k],
+//   X[2k + 1] = FFT_n(s W_M^p y)[k],   s = +1 for p < n/2, -1 above,
+// and, mirrored, the cropped inverse is
+//   v[p] = IFFT_n(X[2k])[p] + s(p) W_M^(-p) IFFT_n(X[2k + 1])[p],
+// with image sample (p + n/2) mod n.  Each CTA runs both halves for its 8
+// coils at once (thread group par = 0 even, 1 odd), on the balanced
+// register four-step of length n = 16 N2.
+template <int N2> __host__ __device__ constexpr int half_threads() { return 2 * CB * tpr<N2>(); }
+
+// A[row][k][c] = FFT_M(place(S_c x[row]))[k] for the CTA's 8 coils.
+// grid (ny, coil blocks), block half_threads.
+template <int N2>
+__global__ void __launch_bounds__(half_threads<N2>())
+toep_rows_fwd_half_kernel(const float2* __restrict__ tw, const float2* __restrict__ twM,
+                          const float2* __restrict__ x, const float2* __restrict__ S,
+                          float2* __restrict__ out) {
+    constexpr int n = N1 * N2, YP = ypitch<N2>(), T = CB * tpr<N2>(), M = 2 * n;
+    static_assert(2 * N1 * YP >= n * CB, "the coil-map row must fit the transpose buffers");
+    __shared__ float2 tws[n], twm[n];
+    __shared__ __align__(16) float2 Y[2 * N1 * YP];
+    pdl_trigger();
+    const int row = blockIdx.x;
+    float2* Ss = Y;   // Ss[i * 8 + j] = S_ci[row][i][cb * 8 + j], streamed in before the wait
+    {
+        const float2* Srow = S + (int64_t)row * n * CP + blockIdx.y * CB;
+        for (int e = threadIdx.x; e < n * 4; e += blockDim.x) {
+            const int i = e >> 2, q = e & 3;
+            cp_async16(Ss + i * CB + 2 * q, Srow + (int64_t)i * CP + 2 * q, true);
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        tws[i] = tw[i];
+        twm[i] = twM[i];
+    }
+    pdl_wait();
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    __syncthreads();
+    const int par = threadIdx.x / T, t = threadIdx.x - par * T, j = t & (CB - 1), r = t / CB;
+    const int c = blockIdx.y * CB + j;
+    float2 v[N1];
+    if (r < N2) {
+#pragma unroll
+        for (int m1 = 0; m1 < N1; ++m1) {
+            const int p = N2 * m1 + r;
+            int i = p + n / 2;
+            if (i >= n) i -= n;
+            float2 val = cmul(x[(int64_t)row * n + i], Ss[i * CB + j]);
+            if (par) {
+                float2 w = twm[p];
+                if (p >= n / 2) w = make_float2(-w.x, -w.y);
+                val = cmul(val, w);
+            }
+            v[m1] = val;
+        }
+    }
+    __syncthreads();   // Ss (aliasing Y) is consumed
+    float2* Yp = Y + par * N1 * YP;
+    if (r < N2) {
+        fft4_phase1<N1, N2, false>(v, r, tws);
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) Yp[k1 * YP + r * CB + j] = v[k1];
+    }
+    __syncthreads();
+    if (r < N1) {
+        float2 u[N2];
+#pragma unroll
+        for (int m2 = 0; m2 < N2; ++m2) u[m2] = Yp[r * YP + m2 * CB + j];
+        fft4_phase2<N1, N2, false>(u, tws);
+        float2* orow = out + (int64_t)row * M * CP + c;
+#pragma unroll
+        for (int k2 = 0; k2 < N2; ++k2) orow[(int64_t)(2 * (r + N1 * k2) + par) * CP] = u[k2];
+    }
+}
+
+// out[row][i] = scale * sum_c conj(S_c) v_c[(i + n/2) mod n ...] + alpha * operand,
+// v_c the cropped inverse of src_c[row] (length M = 2n), the four coil blocks
+// of a row summed in a 4-CTA cluster through distributed shared memory.
+// grid (NCB, ny), cluster (NCB, 1, 1), block half_threads.
+template <int N2>
+__global__ void __launch_bounds__(half_threads<N2>())
+toep_rows_inv_half_cl_kernel(const float2* __restrict__ tw, const float2* __restrict__ twM,
+                             const float2* __restrict__ src, const float2* __restrict__ S,
+                             float2* out, float scale, const float2* operand, float alpha) {
+    constexpr int n = N1 * N2, YP = ypitch<N2>(), T = CB * tpr<N2>(), M = 2 * n;
+    constexpr int RZ = n * 9;   // R[i * 9 + j] (j < 8 coils, 8 = their sum), then Z[p * 8 + j]
+    static_assert(2 * N1 * YP >= RZ + n * CB, "R and Z must fit the transpose buffers");
+    __shared__ float2 tws[n], twm[n];
+    __shared__ __align__(16) float2 Y[2 * N1 * YP];
+    cg::cluster_group cluster = cg::this_cluster();
+    const int q = (int)cluster.block_rank(), row = blockIdx.y;
+    pdl_trigger();
+    {
+        const float2* Srow = S + (int64_t)row * n * CP + q * CB;
+        for (int i = threadIdx.x; i < n; i += blockDim.x)
+            asm volatile("prefetch.global.L2 [%0];\n" ::"l"(Srow + (int64_t)i * CP));
+    }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        tws[i] = tw[i];
+        twm[i] = twM[i];
+    }
+    __syncthreads();
+    pdl_wait();
+    const int par = threadIdx.x / T, t = threadIdx.x - par * T, j = t & (CB - 1), r = t / CB;
+    const int c = q * CB + j;
+    float2* Yp = Y + par * N1 * YP;
+    if (r < N2) {
+        float2 v[N1];
+        const float2* srow = src + (int64_t)row * M * CP + c;
+#pragma unroll
+        for (int m1 = 0; m1 < N1; ++m1) v[m1] = srow[(int64_t)(2 * (N2 * m1 + r) + par) * CP];
+        fft4_phase1<N1, N2, true>(v, r, tws);
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) Yp[k1 * YP + r * CB + j] = v[k1];
+    }
+    __syncthreads();
+    float2 u[N2];
+    if (r < N1) {
+#pragma unroll
+        for (int m2 = 0; m2 < N2; ++m2) u[m2] = Yp[r * YP + m2 * CB + j];
+        fft4_phase2<N1, N2, true>(u, tws);   // u[k2] = IFFT_n(X_par)[r + 16 k2]
+    }
+    __syncthreads();   // Y is reused below as R and Z
+    float2* R = Y;
+    float2* Z = Y + RZ;
+    if (par == 1 && r < N1) {
+#pragma unroll
+        for (int k2 = 0; k2 < N2; ++k2) {
+            const int p = r + N1 * k2;
+            float2 w = twm[p];                       // W_M^(-p) = conj(twm[p]), sign s(p)
+            w = p >= n / 2 ? make_float2(-w.x, w.y) : make_float2(w.x, -w.y);
+            Z[p * CB + j] = cmul(u[k2], w);
+        }
+    }
+    __syncthreads();
+    if (par == 0 && r < N1) {
+        const float2* srow = S + (int64_t)row * n * CP + c;
+#pragma unroll
+        for (int k2 = 0; k2 < N2; ++k2) {
+            const int p = r + N1 * k2;
+            int i = p + n / 2;
+            if (i >= n) i -= n;
+            R[i * 9 + j] = cmulc(srow[(int64_t)i * CP], cadd(u[k2], Z[p * CB + j]));
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        float2 acc = R[i * 9];
+#pragma unroll
+        for (int jj = 1; jj < CB; ++jj) acc = cadd(acc, R[i * 9 + jj]);
+        R[i * 9 + 8] = acc;
+    }
+    cluster.sync();
+    const int chunk = (n + NCB - 1) / NCB;
+    const int i0 = q * chunk, i1 = min(n, i0 + chunk);
+    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+        float2 v = cluster.map_shared_rank(Y, 0)[i * 9 + 8];
+#pragma unroll
+        for (int b = 1; b < NCB; ++b) v = cadd(v, cluster.map_shared_rank(Y, b)[i * 9 + 8]);
+        v = cscale(v, scale);
+        const int64_t o = (int64_t)row * n + i;
+        if (operand) v = cadd(v, cscale(operand[o], alpha));
+        out[o] = v;
+    }
+    cluster.sync();   // keep every CTA's partials alive until the others have read them
+}
+
 static pp_status check_ci(const char* what) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_status(e, what);
@@ -670,15 +841,23 @@ pp_status toep_normal(const Plan& p, const float2* x, float2* out, float scale,
     RowArgs rf{};
     rf.n = nx; rf.G = Mx; rf.off_in = nx / 2; rf.off_out = 0; rf.nrows = ny; rf.scale = 1.f;
     cudaError_t e = cudaErrorInvalidValue;
+    const int n2h = fft4_n2(nx);   // rows of a register length: two length-nx halves
+#define PP_TH(N2_)                                                                              \
+    if (n2h == N2_)                                                                             \
+        e = launch_ex(toep_rows_fwd_half_kernel<N2_>, dim3(ny, ncb), dim3(half_threads<N2_>()), 0, \
+                      st, pdl, 0, (const float2*)p.toep_hx.tw, (const float2*)p.tx.tw, x,        \
+                      (const float2*)p.ci_sens, p.toep_a);
+    PP_TH(8) PP_TH(12) PP_TH(16)
+#undef PP_TH
 #define PP_TR(N2_)                                                                              \
     if (n2x == N2_)                                                                             \
         e = launch_ex(ci_rows_fwd_kernel<N2_>, dim3(ny, ncb), dim3(CB * tpr<N2_>()), 0, st, pdl, 0, \
                       (const float2*)p.tx.tw, rf, x, (const float2*)p.ci_sens, (const float*)nullptr, \
                       (const float*)nullptr, p.toep_a);
-    PP_TR(8) PP_TR(12) PP_TR(16) PP_TR(20) PP_TR(24) PP_TR(32)
+    if (!n2h) { PP_TR(8) PP_TR(12) PP_TR(16) PP_TR(20) PP_TR(24) PP_TR(32) }
 #undef PP_TR
-    if (e != cudaSuccess) return cuda_status(e, "ci_rows_fwd_kernel (Toeplitz) launch");
-    PP_TRY(check_ci("ci_rows_fwd_kernel"));
+    if (e != cudaSuccess) return cuda_status(e, "Toeplitz row FFT launch");
+    PP_TRY(check_ci(n2h ? "toep_rows_fwd_half_kernel" : "ci_rows_fwd_kernel"));
     e = cudaErrorInvalidValue;
 #define PP_TC(N2_)                                                                              \
     if (n2y == N2_)                                                                             \
@@ -692,16 +871,24 @@ pp_status toep_normal(const Plan& p, const float2* x, float2* out, float scale,
     RowArgs ra = rf;
     ra.off_in = 0; ra.off_out = nx / 2;
     e = cudaErrorInvalidValue;
+#define PP_TJ(N2_)                                                                              \
+    if (n2h == N2_)                                                                             \
+        e = launch_ex(toep_rows_inv_half_cl_kernel<N2_>, dim3(NCB, ny), dim3(half_threads<N2_>()),  \
+                      0, st, pdl, NCB, (const float2*)p.toep_hx.tw, (const float2*)p.tx.tw,      \
+                      (const float2*)p.toep_b, (const float2*)p.ci_sens, out, scale, operand,   \
+                      alpha);
+    PP_TJ(8) PP_TJ(12) PP_TJ(16)
+#undef PP_TJ
 #define PP_TI(N2_)                                                                              \
     if (n2x == N2_)                                                                             \
         e = launch_ex(ci_rows_inv_cl_kernel<N2_>, dim3(NCB, ny), dim3(CB * tpr<N2_>()), 0, st, pdl, \
                       NCB, (const float2*)p.tx.tw, ra, (const float2*)p.toep_b,                  \
                       (const float2*)p.ci_sens, (const float*)nullptr, (const float*)nullptr, out,  \
                       scale, operand, alpha);
-    PP_TI(8) PP_TI(12) PP_TI(16) PP_TI(20) PP_TI(24) PP_TI(32)
+    if (!n2h) { PP_TI(8) PP_TI(12) PP_TI(16) PP_TI(20) PP_TI(24) PP_TI(32) }
 #undef PP_TI
-    if (e != cudaSuccess) return cuda_status(e, "ci_rows_inv_cl_kernel (Toeplitz) launch");
-    return check_ci("ci_rows_inv_cl_kernel");
+    if (e != cudaSuccess) return cuda_status(e, "Toeplitz row IFFT launch");
+    return check_ci(n2h ? "toep_rows_inv_half_cl_kernel" : "ci_rows_inv_cl_kernel");
 }
 
 }  // namespace pp
