@@ -190,6 +190,7 @@ def kernel_flops(c, K, toeplitz=False):
             # the same rows as two length-nx halves (the algorithmic count stays that of
             # the length-2nx transform, so the two forms compare directly)
             "toep_rows_fwd_half_kernel": C * ny * fft(Mx) + 6.0 * C * n,
+            "toep_cols_half_kernel": C * Mx * 2 * fft(My) + 2.0 * C * Mx * My,
             "toep_rows_inv_half_cl_kernel": C * ny * fft(Mx) + 8.0 * C * n + 4.0 * n,
         }
     return {

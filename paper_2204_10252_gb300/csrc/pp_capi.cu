@@ -646,6 +646,7 @@ static pp_status setup_toeplitz(Plan& p, const pp_sampling* s, cudaStream_t st) 
     PP_TRY(make_fft(p, 2 * p.nx, p.tx));
     PP_TRY(make_fft(p, 2 * p.ny, p.ty));
     PP_TRY(make_fft(p, p.nx, p.toep_hx));
+    PP_TRY(make_fft(p, p.ny, p.toep_hy));
     if (!p.ci_sens) {
         PP_TRY(alloc_n(p, &p.ci_sens, ci_sens_elems(p)));
         PP_TRY(ci_prepare(p, st));

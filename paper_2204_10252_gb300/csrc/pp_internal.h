@@ -151,7 +151,7 @@ struct Plan {
     // Toeplitz-embedded normal operator (exact F^H F on the 2ny x 2nx circulant)
     int toep = 0;                // 1: the normal operator takes the Toeplitz path
     DevFft tx, ty;               // length-2nx / 2ny twiddle tables
-    DevFft toep_hx;              // length-nx table (rows as two length-nx halves)
+    DevFft toep_hx, toep_hy;     // length-nx / ny tables (two half-length transforms)
     float* toep_T = nullptr;     // [2nx][2ny] kernel spectrum, column-major, 1/(n M) folded in
     float2 *toep_a = nullptr, *toep_b = nullptr;   // [ny][2nx][32] row-transformed arrays
 

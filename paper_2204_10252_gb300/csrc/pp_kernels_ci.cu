@@ -708,6 +708,104 @@ toep_rows_inv_half_cl_kernel(const float2* __restrict__ tw, const float2* __rest
     cluster.sync();   // keep every CTA's partials alive until the others have read them
 }
 
+// Column stage of the Toeplitz operator on length-n halves (n = ny = 16 N2,
+// M = 2n): the column's n image rows sit at positions [-n/2, n/2) mod M, so
+// X[2k + par] = FFT_n(f_par)[k] as in the row stage; the product with the
+// kernel spectrum Tc[q][2k + par]; the mirrored inverse of each half
+// (length-N2 DFT over k2 and W_n^(-m2 k1) by the (k1) threads, length-16
+// DFT over k1 by the (m2) threads); and the cropped combination
+// v[p] = F_0[p] + s(p) W_M^(-p) F_1[p] stored at row (p + n/2) mod n.
+// grid (Mx, coil blocks), block half_threads; rows of src/dst: [ny][Mx][CP].
+template <int N2>
+__global__ void __launch_bounds__(half_threads<N2>(), 3)
+toep_cols_half_kernel(const float2* __restrict__ tw, const float2* __restrict__ twM,
+                      const float* __restrict__ Tc, int Mx, const float2* __restrict__ src,
+                      float2* __restrict__ dst) {
+    constexpr int n = N1 * N2, YP = ypitch<N2>(), T = CB * tpr<N2>(), M = 2 * n;
+    static_assert(2 * N1 * YP >= n * CB, "Z must fit the transpose buffers");
+    __shared__ float2 tws[n], twm[n];
+    __shared__ float Ts[M];
+    __shared__ float2 Y[2 * N1 * YP];
+    pdl_trigger();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        tws[i] = tw[i];
+        twm[i] = twM[i];
+    }
+    for (int i = threadIdx.x; i < M; i += blockDim.x) Ts[i] = Tc[(int64_t)blockIdx.x * M + i];
+    __syncthreads();
+    pdl_wait();
+    const int par = threadIdx.x / T, t = threadIdx.x - par * T, j = t & (CB - 1), r = t / CB;
+    const int64_t rs = (int64_t)Mx * CP;
+    const int64_t cofs = (int64_t)blockIdx.x * CP + blockIdx.y * CB + j;
+    float2* Yp = Y + par * N1 * YP;
+    if (r < N2) {
+        float2 v[N1];
+#pragma unroll
+        for (int m1 = 0; m1 < N1; ++m1) {
+            const int p = N2 * m1 + r;
+            int i = p + n / 2;
+            if (i >= n) i -= n;
+            float2 val = src[i * rs + cofs];
+            if (par) {
+                float2 w = twm[p];
+                if (p >= n / 2) w = make_float2(-w.x, -w.y);
+                val = cmul(val, w);
+            }
+            v[m1] = val;
+        }
+        fft4_phase1<N1, N2, false>(v, r, tws);
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) Yp[k1 * YP + r * CB + j] = v[k1];
+    }
+    __syncthreads();
+    if (r < N1) {
+        float2 u[N2];
+#pragma unroll
+        for (int m2 = 0; m2 < N2; ++m2) u[m2] = Yp[r * YP + m2 * CB + j];
+        fft4_phase2<N1, N2, false>(u, tws);          // u[k2] = X[2 (r + 16 k2) + par]
+#pragma unroll
+        for (int k2 = 0; k2 < N2; ++k2) u[k2] = cscale(u[k2], Ts[2 * (r + N1 * k2) + par]);
+        RegFft<N2, true>::run(u, tws, N1);
+#pragma unroll
+        for (int m2 = 1; m2 < N2; ++m2) {
+            float2 w = tws[m2 * r];
+            w.y = -w.y;
+            u[m2] = cmul(u[m2], w);
+        }
+        // the same (k1, coil) slots this thread read: no other thread touches them
+#pragma unroll
+        for (int m2 = 0; m2 < N2; ++m2) Yp[r * YP + m2 * CB + j] = u[m2];
+    }
+    __syncthreads();
+    float2 f[N1];
+    if (r < N2) {
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) f[k1] = Yp[k1 * YP + r * CB + j];
+        RegFft<N1, true>::run(f, tws, N2);           // f[m1] = F_par[N2 m1 + r]
+    }
+    __syncthreads();   // Y is reused as Z
+    float2* Z = Y;
+    if (par == 1 && r < N2) {
+#pragma unroll
+        for (int m1 = 0; m1 < N1; ++m1) {
+            const int p = N2 * m1 + r;
+            float2 w = twm[p];
+            w = p >= n / 2 ? make_float2(-w.x, w.y) : make_float2(w.x, -w.y);
+            Z[p * CB + j] = cmul(f[m1], w);
+        }
+    }
+    __syncthreads();
+    if (par == 0 && r < N2) {
+#pragma unroll
+        for (int m1 = 0; m1 < N1; ++m1) {
+            const int p = N2 * m1 + r;
+            int i = p + n / 2;
+            if (i >= n) i -= n;
+            dst[i * rs + cofs] = cadd(f[m1], Z[p * CB + j]);
+        }
+    }
+}
+
 static pp_status check_ci(const char* what) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_status(e, what);
@@ -859,15 +957,23 @@ pp_status toep_normal(const Plan& p, const float2* x, float2* out, float scale,
     if (e != cudaSuccess) return cuda_status(e, "Toeplitz row FFT launch");
     PP_TRY(check_ci(n2h ? "toep_rows_fwd_half_kernel" : "ci_rows_fwd_kernel"));
     e = cudaErrorInvalidValue;
+    const int n2hy = fft4_n2(ny);   // columns of a register length: two length-ny halves
+#define PP_TD(N2_)                                                                              \
+    if (n2hy == N2_)                                                                            \
+        e = launch_ex(toep_cols_half_kernel<N2_>, dim3(Mx, ncb), dim3(half_threads<N2_>()), 0, st,  \
+                      pdl, 0, (const float2*)p.toep_hy.tw, (const float2*)p.ty.tw,              \
+                      (const float*)p.toep_T, Mx, (const float2*)p.toep_a, p.toep_b);
+    PP_TD(8) PP_TD(12) PP_TD(16)
+#undef PP_TD
 #define PP_TC(N2_)                                                                              \
     if (n2y == N2_)                                                                             \
         e = launch_ex(toep_cols_kernel<N2_>, dim3(Mx, ncb), dim3(CB * tpr<N2_>()), 0, st, pdl, 0,   \
                       (const float2*)p.ty.tw, (const float*)p.toep_T, ny, ny / 2, Mx,            \
                       (const float2*)p.toep_a, p.toep_b);
-    PP_TC(8) PP_TC(12) PP_TC(16) PP_TC(20) PP_TC(24) PP_TC(32)
+    if (!n2hy) { PP_TC(8) PP_TC(12) PP_TC(16) PP_TC(20) PP_TC(24) PP_TC(32) }
 #undef PP_TC
-    if (e != cudaSuccess) return cuda_status(e, "toep_cols_kernel launch");
-    PP_TRY(check_ci("toep_cols_kernel"));
+    if (e != cudaSuccess) return cuda_status(e, "Toeplitz column stage launch");
+    PP_TRY(check_ci(n2hy ? "toep_cols_half_kernel" : "toep_cols_kernel"));
     RowArgs ra = rf;
     ra.off_in = 0; ra.off_out = nx / 2;
     e = cudaErrorInvalidValue;
