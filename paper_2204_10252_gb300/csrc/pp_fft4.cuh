@@ -1,5 +1,5 @@
 // Register-resident FFTs for the transform lengths of the workloads
-// (n = N1 * N2 with N1 = 16 and N2 in {8, 12, 16, 20, 24, 32}: 128 ... 512).
+// (n = N1 * N2 with N1 = 16 and N2 in {8, 12, 16, 20, 24}: 128 ... 384).
 //
 // Four-step decomposition, input index m = N2*m1 + m2, output k = k1 + N1*k2:
 //   X[k] = sum_m2 W_N2^(m2 k2) [ W_n^(m2 k1) sum_m1 x[N2 m1 + m2] W_N1^(m1 k1) ]
@@ -24,14 +24,11 @@ static __constant__ float2 c_w16[16] = {{1.000000000e+00f, -0.000000000e+00f}, {
 static __constant__ float2 c_w20[20] = {{1.000000000e+00f, -0.000000000e+00f}, {9.510565163e-01f, -3.090169944e-01f}, {8.090169944e-01f, -5.877852523e-01f}, {5.877852523e-01f, -8.090169944e-01f}, {3.090169944e-01f, -9.510565163e-01f}, {6.123233996e-17f, -1.000000000e+00f}, {-3.090169944e-01f, -9.510565163e-01f}, {-5.877852523e-01f, -8.090169944e-01f}, {-8.090169944e-01f, -5.877852523e-01f}, {-9.510565163e-01f, -3.090169944e-01f}, {-1.000000000e+00f, -1.224646799e-16f}, {-9.510565163e-01f, 3.090169944e-01f}, {-8.090169944e-01f, 5.877852523e-01f}, {-5.877852523e-01f, 8.090169944e-01f}, {-3.090169944e-01f, 9.510565163e-01f}, {-1.836970199e-16f, 1.000000000e+00f}, {3.090169944e-01f, 9.510565163e-01f}, {5.877852523e-01f, 8.090169944e-01f}, {8.090169944e-01f, 5.877852523e-01f}, {9.510565163e-01f, 3.090169944e-01f}};
 static __constant__ float2 c_w24[24] = {{1.000000000e+00f, -0.000000000e+00f}, {9.659258263e-01f, -2.588190451e-01f}, {8.660254038e-01f, -5.000000000e-01f}, {7.071067812e-01f, -7.071067812e-01f}, {5.000000000e-01f, -8.660254038e-01f}, {2.588190451e-01f, -9.659258263e-01f}, {6.123233996e-17f, -1.000000000e+00f}, {-2.588190451e-01f, -9.659258263e-01f}, {-5.000000000e-01f, -8.660254038e-01f}, {-7.071067812e-01f, -7.071067812e-01f}, {-8.660254038e-01f, -5.000000000e-01f}, {-9.659258263e-01f, -2.588190451e-01f}, {-1.000000000e+00f, -1.224646799e-16f}, {-9.659258263e-01f, 2.588190451e-01f}, {-8.660254038e-01f, 5.000000000e-01f}, {-7.071067812e-01f, 7.071067812e-01f}, {-5.000000000e-01f, 8.660254038e-01f}, {-2.588190451e-01f, 9.659258263e-01f}, {-1.836970199e-16f, 1.000000000e+00f}, {2.588190451e-01f, 9.659258263e-01f}, {5.000000000e-01f, 8.660254038e-01f}, {7.071067812e-01f, 7.071067812e-01f}, {8.660254038e-01f, 5.000000000e-01f}, {9.659258263e-01f, 2.588190451e-01f}};
 
-static __constant__ float2 c_w32[32] = {{1.000000000e+00f, -0.000000000e+00f}, {9.807852804e-01f, -1.950903220e-01f}, {9.238795325e-01f, -3.826834324e-01f}, {8.314696123e-01f, -5.555702330e-01f}, {7.071067812e-01f, -7.071067812e-01f}, {5.555702330e-01f, -8.314696123e-01f}, {3.826834324e-01f, -9.238795325e-01f}, {1.950903220e-01f, -9.807852804e-01f}, {6.123233996e-17f, -1.000000000e+00f}, {-1.950903220e-01f, -9.807852804e-01f}, {-3.826834324e-01f, -9.238795325e-01f}, {-5.555702330e-01f, -8.314696123e-01f}, {-7.071067812e-01f, -7.071067812e-01f}, {-8.314696123e-01f, -5.555702330e-01f}, {-9.238795325e-01f, -3.826834324e-01f}, {-9.807852804e-01f, -1.950903220e-01f}, {-1.000000000e+00f, -1.224646799e-16f}, {-9.807852804e-01f, 1.950903220e-01f}, {-9.238795325e-01f, 3.826834324e-01f}, {-8.314696123e-01f, 5.555702330e-01f}, {-7.071067812e-01f, 7.071067812e-01f}, {-5.555702330e-01f, 8.314696123e-01f}, {-3.826834324e-01f, 9.238795325e-01f}, {-1.950903220e-01f, 9.807852804e-01f}, {-1.836970199e-16f, 1.000000000e+00f}, {1.950903220e-01f, 9.807852804e-01f}, {3.826834324e-01f, 9.238795325e-01f}, {5.555702330e-01f, 8.314696123e-01f}, {7.071067812e-01f, 7.071067812e-01f}, {8.314696123e-01f, 5.555702330e-01f}, {9.238795325e-01f, 3.826834324e-01f}, {9.807852804e-01f, 1.950903220e-01f}};
-
 template <int L> __device__ __forceinline__ float2 cw(int m);
 template <> __device__ __forceinline__ float2 cw<12>(int m) { return c_w12[m]; }
 template <> __device__ __forceinline__ float2 cw<16>(int m) { return c_w16[m]; }
 template <> __device__ __forceinline__ float2 cw<20>(int m) { return c_w20[m]; }
 template <> __device__ __forceinline__ float2 cw<24>(int m) { return c_w24[m]; }
-template <> __device__ __forceinline__ float2 cw<32>(int m) { return c_w32[m]; }
 
 template <int N, bool INV> struct RegFft;
 
@@ -95,20 +92,12 @@ template <bool INV> struct RegFft<20, INV> {
 template <bool INV> struct RegFft<24, INV> {
     static __device__ __forceinline__ void run(float2* v, const float2* tw, int s) { reg_fft_ab<8, 3, INV>(v, tw, s); }
 };
-template <bool INV> struct RegFft<32, INV> {
-    static __device__ __forceinline__ void run(float2* v, const float2* tw, int s) { reg_fft_ab<8, 4, INV>(v, tw, s); }
-};
 
 // Fast lengths: returns N2 for n = 16 * N2 with a register kernel, else 0.
-// (N2 = 32, n = 512, is instantiated only by the Toeplitz-embedded normal
-// operator, whose lengths toep_n2 checks.)
 __host__ __device__ __forceinline__ int fft4_n2(int n) {
     if (n % 16) return 0;
     const int n2 = n / 16;
     return (n2 == 8 || n2 == 12 || n2 == 16 || n2 == 20 || n2 == 24) ? n2 : 0;
-}
-__host__ __device__ __forceinline__ int toep_n2(int n) {
-    return (n == 512) ? 32 : fft4_n2(n);
 }
 
 // Phase 1 for one (transform, m2): v holds x[N2*m1 + m2], m1 < N1, on entry;

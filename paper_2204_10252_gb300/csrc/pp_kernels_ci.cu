@@ -31,7 +31,7 @@ template <int N2> __host__ __device__ constexpr int tpr() { return N2 > N1 ? N2 
 // k1 pitch of the transpose buffer Y[k1][m2][coil]: an odd multiple of 8
 // float2 apart, so the two k1 rows of a half-warp fall on disjoint banks
 template <int N2> __host__ __device__ constexpr int ypitch() { return N2 * CB + 8; }
-template <int N2> __host__ __device__ constexpr int min_ctas() { return N2 == 20 ? 7 : (N2 == 32 ? 2 : 1); }
+template <int N2> __host__ __device__ constexpr int min_ctas() { return N2 == 20 ? 7 : 1; }
 
 __device__ __forceinline__ int wrap1(int a, int G) { return a < 0 ? a + G : (a >= G ? a - G : a); }
 
@@ -919,7 +919,8 @@ pp_status ci_normal(const Plan& p, const float2* x, float2* out, float scale, co
 }
 
 bool toep_supported(int nx, int ny, int C) {
-    return C >= 1 && C <= CP && toep_n2(2 * nx) && toep_n2(2 * ny);
+    // each axis: n itself a register length (two length-n halves) or 2n
+    return C >= 1 && C <= CP && (fft4_n2(nx) || fft4_n2(2 * nx)) && (fft4_n2(ny) || fft4_n2(2 * ny));
 }
 
 size_t toep_rows_elems(const Plan& p) { return (size_t)p.ny * 2 * p.nx * CP; }
@@ -933,7 +934,7 @@ size_t toep_rows_elems(const Plan& p) { return (size_t)p.ny * 2 * p.nx * CP; }
 pp_status toep_normal(const Plan& p, const float2* x, float2* out, float scale,
                       const float2* operand, float alpha, cudaStream_t st) {
     const int nx = p.nx, ny = p.ny, Mx = 2 * nx, My = 2 * ny;
-    const int n2x = toep_n2(Mx), n2y = toep_n2(My);
+    const int n2x = fft4_n2(Mx), n2y = fft4_n2(My);
     const int ncb = (p.C + CB - 1) / CB;
     const bool pdl = p.pdl != 0;
     RowArgs rf{};
@@ -952,7 +953,7 @@ pp_status toep_normal(const Plan& p, const float2* x, float2* out, float scale,
         e = launch_ex(ci_rows_fwd_kernel<N2_>, dim3(ny, ncb), dim3(CB * tpr<N2_>()), 0, st, pdl, 0, \
                       (const float2*)p.tx.tw, rf, x, (const float2*)p.ci_sens, (const float*)nullptr, \
                       (const float*)nullptr, p.toep_a);
-    if (!n2h) { PP_TR(8) PP_TR(12) PP_TR(16) PP_TR(20) PP_TR(24) PP_TR(32) }
+    if (!n2h) { PP_TR(8) PP_TR(12) PP_TR(16) PP_TR(20) PP_TR(24) }
 #undef PP_TR
     if (e != cudaSuccess) return cuda_status(e, "Toeplitz row FFT launch");
     PP_TRY(check_ci(n2h ? "toep_rows_fwd_half_kernel" : "ci_rows_fwd_kernel"));
@@ -970,7 +971,7 @@ pp_status toep_normal(const Plan& p, const float2* x, float2* out, float scale,
         e = launch_ex(toep_cols_kernel<N2_>, dim3(Mx, ncb), dim3(CB * tpr<N2_>()), 0, st, pdl, 0,   \
                       (const float2*)p.ty.tw, (const float*)p.toep_T, ny, ny / 2, Mx,            \
                       (const float2*)p.toep_a, p.toep_b);
-    if (!n2hy) { PP_TC(8) PP_TC(12) PP_TC(16) PP_TC(20) PP_TC(24) PP_TC(32) }
+    if (!n2hy) { PP_TC(8) PP_TC(12) PP_TC(16) PP_TC(20) PP_TC(24) }
 #undef PP_TC
     if (e != cudaSuccess) return cuda_status(e, "Toeplitz column stage launch");
     PP_TRY(check_ci(n2hy ? "toep_cols_half_kernel" : "toep_cols_kernel"));
@@ -991,7 +992,7 @@ pp_status toep_normal(const Plan& p, const float2* x, float2* out, float scale,
                       NCB, (const float2*)p.tx.tw, ra, (const float2*)p.toep_b,                  \
                       (const float2*)p.ci_sens, (const float*)nullptr, (const float*)nullptr, out,  \
                       scale, operand, alpha);
-    if (!n2h) { PP_TI(8) PP_TI(12) PP_TI(16) PP_TI(20) PP_TI(24) PP_TI(32) }
+    if (!n2h) { PP_TI(8) PP_TI(12) PP_TI(16) PP_TI(20) PP_TI(24) }
 #undef PP_TI
     if (e != cudaSuccess) return cuda_status(e, "Toeplitz row IFFT launch");
     return check_ci(n2h ? "toep_rows_inv_half_cl_kernel" : "ci_rows_inv_cl_kernel");

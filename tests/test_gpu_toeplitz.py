@@ -45,11 +45,10 @@ def empty(shape):
     return torch.zeros(tuple(shape), dtype=torch.complex64, device="cuda")
 
 
-# (shape (ny, nx), coils, interleaves, samples): every register transform
-# length of the embedding (2n = 128 ... 512) on rows and on columns, coil
-# counts with a ragged last block of 8 and the full 32.
-# Rows of register length (nx = 128, 192, 256) run as two length-nx halves,
-# the others (nx = 64, 96, 160) as one length-2nx transform: both covered.
+# (shape (ny, nx), coils, interleaves, samples): every supported side on rows
+# and on columns, coil counts with a ragged last block of 8 and the full 32.
+# Sides of register length (n = 128, 192, 256) run as two length-n halves,
+# the others (n = 64, 96, 160) as one length-2n transform: both covered.
 CASES = [((64, 64), 4, 8, 256), ((96, 128), 5, 8, 400), ((256, 160), 3, 8, 512),
          ((64, 256), 32, 6, 300), ((192, 96), 9, 8, 300), ((128, 192), 7, 6, 300)]
 IDS = ["64_c4", "96x128_c5", "256x160_c3", "64x256_c32", "192x96_c9", "128x192_c7"]
