@@ -61,7 +61,8 @@ def parse():
                     help="profiling aid: build the workload's plan (no power iteration), apply "
                          "its operator K times and exit without a bench line")
     ap.add_argument("--tuning", default="",
-                    help="with --apply-only: row_ifft_variant,stencil_kind,stencil_coils to force")
+                    help="with --apply-only: row_ifft_variant,stencil_kind,stencil_coils to force "
+                         "(batched2d_64: the batch tile code)")
     ap.add_argument("--wavelet", choices=["haar", "db4"], default="haar",
                     help="spiral workload: W of the prox, the 2-level Haar or the Daubechies-4 "
                          "(the paper's choice)")

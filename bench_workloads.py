@@ -195,7 +195,8 @@ def batched(args, pp, rank, world, local):
                   "autotuned_cols_per_cta": tile, "persistent_ctas": grid, "setup_s": setup_s}, clk,
                  {"roofline": {"bound": "hbm", "kernel": "cart2d_batch_normal_kernel (one launch per apply)",
                                "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
-                               "traffic": None, "peak_source": src,
+                               "traffic": bench.ncu_traffic("cart2d_batch_normal", "ncu_traffic_batched.json"),
+                               "peak_source": src,
                                "algorithmic_bytes_per_apply": bytes_apply},
                   "batched_apply_ms": apply_ms})
 
@@ -238,7 +239,8 @@ def apply_only(args, pp, local):
     """Profiling aid (--apply-only K): the workload's operator K times, no
     bench line.  cart2d: K normal applies; cart3d: the workload's volume with
     4 of its coils (a capture small enough for ncu), K normal applies, then K
-    3-D Haar prox calls; batched2d_64: K batched normal applies."""
+    3-D Haar prox calls; batched2d_64: K batched normal applies (--tuning T
+    forces the batch tile code T)."""
     dev = torch.device("cuda", local)
     K = args.apply_only
     if args.workload == "batched2d_64":
@@ -251,6 +253,8 @@ def apply_only(args, pp, local):
                  for i, (ny, nx, _, R) in enumerate(slices)]
         batch = pp.pp_batch_create(shapes, [C for _, _, C, _ in slices], sens, masks, seed=c["seed"],
                                    power_iters=0)
+        if args.tuning:   # force the tile the plan-time tuner picks without a profiler attached
+            pp.pp_batch_set_tile(batch, int(args.tuning))
         x = torch.from_numpy(synth.crandn((int(batch.image_off[-1]),), 3)).to(dev)
         y = torch.empty_like(x)
         for _ in range(K):
