@@ -171,3 +171,108 @@ def test_cartesian_pgd_with_db4_prox_is_monotone_and_reaches_a_fixed_point():
     # and it is not the Haar solution
     yh = O.pfista(nrm, adj, b, lam, c, 3000, L)
     assert np.linalg.norm(yh - y) > 1e-6 * np.linalg.norm(y)
+
+
+# ---------------------------------------------------------------------------
+# Momentum schedule of Algorithm "pfista" (Sec. 3.1), pinned by iterates
+# derived by hand.  With lambda = 0 the prox is the identity (W orthonormal),
+# and with a diagonal normal operator N_hat = diag(m) every pixel runs the
+# scalar recursion y_{k+1} = q z_k + r, where p is the preconditioner,
+# q = 1 - m p(m) and r = p(m) a (a = A_hat^H b_hat).  Unrolling by hand with
+# beta_k = k/(k+3) (beta_0 = 0, beta_1 = 1/4, beta_2 = 2/5, beta_3 = 1/2) and
+# z_{k+1} = y_{k+1} + beta_k (y_{k+1} - y_k), y_0 = z_0 = 0:
+#   y_1 = r
+#   y_2 = r (1 + q)
+#   y_3 = r (1 + q + 5/4 q^2)                    (z_2 = r (1 + 5/4 q))
+#   y_4 = r (1 + q + q^2 + 7/4 q^3)              (z_3 = r (1 + q + 7/4 q^2))
+#   y_5 = r (1 + q + q^2 + 7/8 q^3 + 21/8 q^4)   (z_4 = r (1 + q + 7/8 q^2 + 21/8 q^3))
+# and without momentum (Algorithm "ppgd") the geometric sums
+#   y_k = r (1 + q + ... + q^(k-1)).
+# A schedule shifted by one, (k-1)/(k+2), or the printed
+# z_{k+1} = y_k + beta_k (y_k - y_{k-1}) each change y_2 or y_3.
+# ---------------------------------------------------------------------------
+
+_MOM = lambda q, r: [r,
+                     r * (1 + q),
+                     r * (1 + q + 1.25 * q ** 2),
+                     r * (1 + q + q ** 2 + 1.75 * q ** 3),
+                     r * (1 + q + q ** 2 + 0.875 * q ** 3 + 2.625 * q ** 4)]
+
+
+def _diag_problem(seed=11):
+    rng = np.random.default_rng(seed)
+    m = rng.uniform(0.05, 0.95, (4, 4))                       # spectrum of N_hat
+    b = rng.standard_normal((4, 4)) + 1j * rng.standard_normal((4, 4))
+    normal = lambda v: m * v                                  # L = 1: N_hat = N
+    adjoint = lambda y: np.asarray(y).reshape(4, 4)           # A^H b = b
+    return m, b, normal, adjoint
+
+
+@pytest.mark.parametrize("coeffs", [[4.0, -10.0 / 3.0], [1.5, 0.25]])
+def test_momentum_schedule_matches_hand_derived_iterates(coeffs):
+    m, b, normal, adjoint = _diag_problem()
+    p = coeffs[0] + coeffs[1] * m
+    q, r = 1.0 - m * p, p * b
+    hist = []
+    O.pfista(normal, adjoint, b, 0.0, coeffs, 5, 1.0, normalize_b=False, history=hist)
+    for k, (got, want) in enumerate(zip(hist, _MOM(q, r))):
+        assert np.max(np.abs(got - want)) <= 1e-14 * np.max(np.abs(want)), "y_%d" % (k + 1)
+    # the same with b normalised to unit norm (Sec. 5): a = b / ||b||
+    hist = []
+    O.pfista(normal, adjoint, b, 0.0, coeffs, 5, 1.0, normalize_b=True, history=hist)
+    rn = r / np.linalg.norm(b)
+    for got, want in zip(hist, _MOM(q, rn)):
+        assert np.max(np.abs(got - want)) <= 1e-14 * np.max(np.abs(want))
+
+
+def test_plain_fista_momentum_and_ppgd_geometric_sums():
+    # p = 1 (coeffs None, Algorithm "fista") follows the same closed forms
+    # with q = 1 - m, r = a; beta = 0 (Algorithm "pgd") gives geometric sums
+    m, b, normal, adjoint = _diag_problem(12)
+    q, r = 1.0 - m, b
+    hist = []
+    O.pfista(normal, adjoint, b, 0.0, None, 5, 1.0, normalize_b=False, history=hist)
+    for got, want in zip(hist, _MOM(q, r)):
+        assert np.max(np.abs(got - want)) <= 1e-14 * np.max(np.abs(want))
+    hist = []
+    O.pfista(normal, adjoint, b, 0.0, [2.0, -1.0], 6, 1.0, normalize_b=False, momentum=False,
+             history=hist)
+    p = 2.0 - m
+    q, r = 1.0 - m * p, p * b
+    for k, got in enumerate(hist, start=1):
+        want = r * sum(q ** j for j in range(k))
+        assert np.max(np.abs(got - want)) <= 1e-14 * np.max(np.abs(want))
+
+
+def test_unrolled_forward_follows_the_same_iterates():
+    # the differentiable solve's forward (raw b, fixed L) runs the same
+    # iteration: its y_K equals the hand-derived iterates for K = 1..5 ...
+    m, b, normal, adjoint = _diag_problem(13)
+    c = [4.0, -10.0 / 3.0]
+    p = c[0] + c[1] * m
+    want = _MOM(1.0 - m * p, p * b)
+    for K in range(1, 6):
+        got = O.pfista_unrolled(normal, adjoint, b, 0.0, c, K, 1.0)
+        assert np.max(np.abs(got - want[K - 1])) <= 1e-14 * np.max(np.abs(want[K - 1]))
+
+
+def test_unrolled_forward_equals_pfista_without_b_normalisation():
+    # ... and, on a Cartesian SENSE problem with an active soft threshold,
+    # every y_K equals pfista(..., normalize_b=False)
+    shape, C = (16, 16), 4
+    s = synth.coil_maps(shape, C, 5)
+    msk = synth.line_mask(shape, 3, 4, 5)
+    b = O.cart_forward(synth.phantom(shape, 5), s, msk)
+    nrm = lambda v: O.cart_normal(v, s, msk)
+    adj = lambda y: O.cart_adjoint(y, s, msk)
+    L = O.power_iteration(nrm, shape, 5)
+    c = O.poly_coeffs_l2(3)
+    lam = 0.02 * float(np.max(np.abs(adj(b)))) / math.sqrt(L)
+    hist = []
+    O.pfista(nrm, adj, b, lam, c, 8, L, normalize_b=False, history=hist)
+    for K in (1, 2, 5, 8):
+        yk = O.pfista_unrolled(nrm, adj, b, lam, c, K, L)
+        assert np.max(np.abs(yk - hist[K - 1])) <= 1e-14 * np.max(np.abs(hist[K - 1]))
+    # the threshold is active: some Haar coefficients are set to zero
+    wc = O.haar_fwd(hist[-1], 2)
+    assert np.sum(np.abs(wc) == 0) > 0
