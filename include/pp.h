@@ -119,6 +119,18 @@ pp_status pp_plan_scale(const pp_plan* plan, double* L);
 /* Replace L (L > 0, finite); used to share one estimate between runs. */
 pp_status pp_plan_set_scale(pp_plan* plan, double L);
 
+/* Estimate mu, the smallest eigenvalue of N_hat = A^H A / L, for the
+ * Chebyshev preconditioner (pp_poly_coeffs_cheb): `iters` steps of power
+ * iteration on I - N_hat from a SplitMix64 start vector drawn from `seed`
+ * (the remark closing the Chebyshev design of Sec. 3.4: when A^H A is
+ * injective, the largest eigenvalue of I - N_hat is 1 - mu), FP64
+ * reductions; *mu (host) = 1 - the last Rayleigh quotient.  The estimate
+ * approaches mu from above.  A value at or below 0 (up to rounding) means
+ * A^H A has a null space or near-null directions: no Chebyshev interval
+ * [mu, 1] with mu > 0 exists, and the l2 design of Eq. "l2cost" applies.
+ * Uses the plan's L and workspace; synchronises `stream`. */
+pp_status pp_plan_mu(pp_plan* plan, int iters, uint64_t seed, double* mu, pp_stream stream);
+
 /* Element counts of the image ([nz][ny][nx]) and of the k-space array
  * ([C][...] as above); either pointer may be NULL. */
 pp_status pp_plan_sizes(const pp_plan* plan, int64_t* image_elems, int64_t* kspace_elems);
@@ -166,15 +178,20 @@ pp_status pp_adjoint_apply(const pp_plan* plan, const pp_c64* y, pp_c64* x, pp_s
  * intermediate buffer lives in a fixed 16 MiB array of device memory that
  * is part of the library (each GPU that loads the library holds it until the
  * process exits).  For callers that must not allocate device memory when
- * they call -- e.g. while a stream capture in global mode is open, inside a
- * host application that owns all device memory through its own pool, or in
- * a real-time loop that forbids allocation after start-up.  The plan is
- * built beforehand with pp_plan_create.  The paper has no counterpart.
+ * they call: a plug-in whose host application owns all device memory through
+ * its own pool (an allocation behind its back can fail or upset the host's
+ * accounting), or a real-time loop that forbids allocation after start-up
+ * (an allocation can stall or fail on fragmented memory).  The plan is built
+ * beforehand with pp_plan_create.  Runs the same kernels as
+ * pp_adjoint_apply.  The paper has no counterpart.
  *  - Plans whose adjoint needs more than 16 MiB of scratch (Cartesian 2-D:
  *    8*C*ny*nx bytes; 3-D: 16*nz*ny*nx; non-Cartesian: 8*C*G*(ny+G))
  *    return PP_ERR_UNSUPPORTED.
- *  - The first call on a device looks up the array's device address; make
- *    that first call before any stream capture.
+ *  - The first call on a device looks up the array's device address (and,
+ *    with lazy module loading, is when the runtime commits the array's
+ *    memory); make that first call before any stream capture.  The address
+ *    is kept for the life of the process: after a cudaDeviceReset of that
+ *    device (which also frees every plan) the library is not usable there.
  *  - All calls share the one array and it keeps the last call's contents
  *    (nothing in it needs clearing: every element read is written first in
  *    the same call).  Calls that overlap on the GPU (other streams, other
@@ -271,7 +288,11 @@ typedef struct {
  * with d == 0 is plain FISTA (Algorithm "fista", p = 1).  b device k-space,
  * x_out device image (y_iters).  info may be NULL.  The iteration loop runs
  * as one CUDA graph, captured on first use and reused while iters, c, d,
- * lambda and levels are unchanged. */
+ * lambda and levels are unchanged.
+ * b = 0 gives x_out = 0 (the solution for b = 0).  A NaN or infinite value
+ * in b makes every iterate NaN; with info->history set the call (which then
+ * synchronises) returns PP_ERR_NONFINITE, x_out still written.  Without a
+ * history the call does not synchronise and cannot report it. */
 pp_status pp_fista_solve(pp_plan* plan, const pp_c64* b, float lambda, int iters, const double* c,
                          int d, pp_c64* x_out, pp_solve_info* info, pp_stream stream);
 
@@ -313,7 +334,8 @@ pp_status pp_batch_adjoint_apply(const pp_batch* batch, const pp_c64* y, pp_c64*
 pp_status pp_batch_normal_apply(const pp_batch* batch, const pp_c64* x, pp_c64* y, pp_stream stream);
 /* Algorithm "pfista" on every slice's normalised problem, one shared lambda,
  * iteration count and polynomial; as pp_fista_solve otherwise (history sums
- * over the batch; levels must be 0 or 2). */
+ * over the batch, so a non-finite value in any slice's b gives
+ * PP_ERR_NONFINITE when history is set; levels must be 0 or 2). */
 pp_status pp_batch_fista_solve(pp_batch* batch, const pp_c64* b, float lambda, int iters,
                                const double* c, int d, pp_c64* x_out, pp_solve_info* info,
                                pp_stream stream);
@@ -330,8 +352,11 @@ pp_status pp_batch_unrolled_forward(pp_batch* batch, const pp_c64* b, float lamb
 /* Reverse pass: for the real loss Re<grad_out, y_iters>, writes grad_b (device
  * k-space, dLoss/dRe b + i dLoss/dIm b), *grad_lambda and grad_c[0..d] (host).
  * Uses the checkpoints of the last pp_batch_unrolled_forward with the same
- * b pointer, lambda, iters, c, d and checkpoint_every, else reruns that
- * forward first.  Each segment is recomputed from its checkpoint; the
+ * b pointer, lambda, iters, c, d, checkpoint_every and per-slice L_s, else
+ * reruns that forward first (pp_batch_set_scales and pp_batch_set_tile
+ * discard the checkpoints).  The checkpoints are keyed by b's ADDRESS, not
+ * its contents: a caller that rewrites b in place between the forward and
+ * this call must run the forward again.  Each segment is recomputed from its checkpoint; the
  * Horner adjoint uses v_j = N_hat^j wbar (N_hat is self-adjoint), d+1
  * applies per iteration.  Synchronises `stream`. */
 pp_status pp_batch_unrolled_backward(pp_batch* batch, const pp_c64* b, float lambda, int iters,

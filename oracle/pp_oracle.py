@@ -94,6 +94,27 @@ def cart_normal(x, sens, mask):
     return cart_adjoint(cart_forward(x, sens, mask), sens, mask)
 
 
+def cart_normal_columns(x, sens, mask, cols):
+    """Readout columns `cols` (indices along the last axis x) of cart_normal
+    for a mask constant along x.  Then M commutes with the x transform and
+    F^H M F = F_rest^H M F_rest with F_rest the transform over the other
+    axes (F_x^H F_x = I), so every x column is its own problem:
+    out[..., j] = sum_c conj(S_c[..., x_j]) F_rest^H M[..., x_j] F_rest (S_c x)[..., x_j].
+    Returns [*img[:-1], len(cols)]; used to check single columns of large
+    volumes without transforming the whole volume."""
+    x = np.asarray(x, dtype=np.complex128)
+    cols = list(cols)
+    ax = tuple(range(-(x.ndim - 1), 0))
+    out = np.zeros(x.shape[:-1] + (len(cols),), dtype=np.complex128)
+    for j, q in enumerate(cols):
+        m = np.asarray(mask)[..., q].astype(np.float64)
+        xq = x[..., q]
+        for c in range(np.shape(sens)[0]):
+            sq = np.asarray(sens[c])[..., q].astype(np.complex128)
+            out[..., j] += np.conj(sq) * cifft(m * cfft(sq * xq, axes=ax), axes=ax)
+    return out
+
+
 # --------------------------------------------------------------------------
 # Kaiser-Bessel gridding NUFFT (Sec. 5.2 uses a NUFFT; parameters per the
 # workload: width W, oversampling sigma)
@@ -542,6 +563,23 @@ def power_iteration(normal, shape, seed, iters=50):
         lam = float(np.real(np.vdot(v, w)))
         v = w / np.linalg.norm(w)
     return lam
+
+
+def mu_estimate(normal, shape, seed, L, iters=50):
+    """Lower end mu of the spectrum of N_hat = A^H A / L for the Chebyshev
+    design of Sec. 3.4: when A^H A is injective, power iteration on
+    I - N_hat converges to its largest eigenvalue 1 - mu.  Start as
+    power_iteration (unit SplitMix64 vector from `seed`); w = v - N_hat v,
+    rho = Re<v, w>, v <- w / ||w||; returns mu = 1 - rho of the last step."""
+    n = int(np.prod(shape))
+    v = start_vector(seed, n).reshape(shape)
+    v = v / np.linalg.norm(v)
+    rho = 0.0
+    for _ in range(iters):
+        w = v - normal(v) / L
+        rho = float(np.real(np.vdot(v, w)))
+        v = w / np.linalg.norm(w)
+    return 1.0 - rho
 
 
 # --------------------------------------------------------------------------

@@ -56,6 +56,8 @@ _SIGS = {
     "pp_plan_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "pp_plan_scale": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     "pp_plan_set_scale": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
+    "pp_plan_mu": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64,
+                                  ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
     "pp_plan_tuning": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int),
                                       ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "pp_plan_set_tuning": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
@@ -260,6 +262,14 @@ def pp_plan_scale(plan: Plan) -> float:
 
 def pp_plan_set_scale(plan: Plan, L: float):
     _check(lib().pp_plan_set_scale(plan.handle, float(L)), "pp_plan_set_scale")
+
+
+def pp_plan_mu(plan: Plan, iters: int = 50, seed: int = 0, stream=None) -> float:
+    """mu = smallest eigenvalue of N_hat by power iteration on I - N_hat."""
+    mu = ctypes.c_double(0.0)
+    _check(lib().pp_plan_mu(plan.handle, int(iters), ctypes.c_uint64(seed), ctypes.byref(mu),
+                            _stream(stream)), "pp_plan_mu")
+    return mu.value
 
 
 def pp_plan_tuning(plan: Plan):

@@ -185,7 +185,8 @@ __global__ void seg_scale_kernel(const float2* __restrict__ in, float2* __restri
     const int64_t lo = seg_off[seg], hi = seg_off[seg + 1];
     const double nv = norm2 ? sqrt(norm2[seg * stride]) : 1.0;
     const double fs = factor ? factor[seg] : 1.0;
-    const float f = (float)(invert ? (nv > 0.0 ? fs / nv : 0.0) : fs * nv);
+    const double fi = isfinite(nv) ? (nv > 0.0 ? fs / nv : 0.0) : __longlong_as_double(0x7ff8000000000000ll);
+    const float f = (float)(invert ? fi : fs * nv);
     for (int64_t i = lo + (int64_t)j * blockDim.x + threadIdx.x; i < hi; i += (int64_t)nb * blockDim.x)
         out[i] = cscale(in[i], f);
 }
@@ -200,7 +201,9 @@ __device__ __forceinline__ void haar2x2_b(float2& a, float2& b, float2& c, float
 
 __device__ __forceinline__ float2 soft_b(float2 v, float lam) {
     const float m2 = v.x * v.x + v.y * v.y;
-    if (!(m2 > lam * lam)) return make_float2(0.f, 0.f);
+    // |v| <= lambda -> 0 (also v = 0, so no 0 * inf); a NaN fails the test and
+    // stays NaN instead of being thresholded to 0
+    if (m2 <= lam * lam) return make_float2(0.f, 0.f);
     return cscale(v, 1.f - lam * rsqrtf(m2));
 }
 

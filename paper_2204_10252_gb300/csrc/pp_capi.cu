@@ -235,17 +235,21 @@ static pp_status forward_into(const Plan& p, const float2* x, float2* y, cudaStr
     return launch_nufft_degrid(p, p.wk_b, y, st);
 }
 
-// x = A^H y (unscaled)
-static pp_status adjoint_into(const Plan& p, const float2* y, float2* x, cudaStream_t st) {
+// x = A^H y (unscaled) with the intermediates in wa and wb (plan workspace, or the
+// library's fixed scratch array for pp_adjoint_apply_static): Cartesian 2-D
+// needs C*n elements in wa; 3-D n in wa and n in wb; non-Cartesian C*ny*G_x
+// in wa and C*G_y*G_x in wb.
+pp_status adjoint_ws(const Plan& p, const float2* y, float2* x, float2* wa, float2* wb,
+                     cudaStream_t st) {
     const int nx = p.nx, ny = p.ny, nz = p.nz;
     const int64_t n = p.nimg;
     if (p.kind == PP_CARTESIAN && p.ndim == 2) {
         ColArgs ay = col_args(ny, ny, ny, ny / 2, ny / 2, nx, (int64_t)ny * nx, (int64_t)ny * nx, p.C,
                               (float)(1.0 / sqrt((double)ny)));
         ay.mul_in = p.mask_c;   // centred mask indexed by the input row ky
-        PP_TRY(launch_cols(p.fy, ay, y, p.wk_a, true, st));
+        PP_TRY(launch_cols(p.fy, ay, y, wa, true, st));
         RowArgs ra = row_args(nx, nx, nx / 2, nx / 2, ny, n, (float)(1.0 / sqrt((double)nx)));
-        return launch_rows_adj(p, p.fx, ra, p.wk_a, p.sens, nullptr, nullptr, x, nullptr, 0.f, p.C, st);
+        return launch_rows_adj(p, p.fx, ra, wa, p.sens, nullptr, nullptr, x, nullptr, 0.f, p.C, st);
     }
     if (p.kind == PP_CARTESIAN) {
         // 3-D, per coil: mask and inverse centred FFT along z, then y, then
@@ -255,23 +259,27 @@ static pp_status adjoint_into(const Plan& p, const float2* y, float2* x, cudaStr
             ColArgs az = col_args(nz, nz, nz, nz / 2, nz / 2, ny * nx, 0, 0, 1,
                                   (float)(1.0 / sqrt((double)nz)));
             az.mul_in = p.mask_c; az.mi_q = ny; az.mi_c = 1; az.mi_cdiv = nx;
-            PP_TRY(launch_cols(p.fz, az, yc, p.wk_a, true, st));
+            PP_TRY(launch_cols(p.fz, az, yc, wa, true, st));
             ColArgs ay = col_args(ny, ny, ny, ny / 2, ny / 2, nx, (int64_t)ny * nx, (int64_t)ny * nx,
                                   nz, (float)(1.0 / sqrt((double)ny)));
-            PP_TRY(launch_cols(p.fy, ay, p.wk_a, p.wk_b, true, st));
+            PP_TRY(launch_cols(p.fy, ay, wa, wb, true, st));
             RowArgs ra = row_args(nx, nx, nx / 2, nx / 2, ny * nz, 0, (float)(1.0 / sqrt((double)nx)));
-            PP_TRY(launch_rows_adj(p, p.fx, ra, p.wk_b, p.sens + (int64_t)c * n, nullptr, nullptr, x,
+            PP_TRY(launch_rows_adj(p, p.fx, ra, wb, p.sens + (int64_t)c * n, nullptr, nullptr, x,
                                    c == 0 ? nullptr : x, 1.f, 1, st));
         }
         return PP_OK;
     }
     const int Gx = p.G_x, Gy = p.G_y;
-    PP_TRY(launch_nufft_spread(p, y, p.wk_b, st));
+    PP_TRY(launch_nufft_spread(p, y, wb, st));
     ColArgs ci = col_args(Gy, ny, Gy, 0, ny / 2, Gx, (int64_t)Gy * Gx, (int64_t)ny * Gx, p.C, 1.f);
-    PP_TRY(launch_cols(p.gy, ci, p.wk_b, p.wk_a, true, st));
+    PP_TRY(launch_cols(p.gy, ci, wb, wa, true, st));
     RowArgs ra = row_args(nx, Gx, 0, nx / 2, ny, (int64_t)ny * nx, 1.f);
-    return launch_rows_adj(p, p.gx, ra, p.wk_a, p.sens, p.deapod_y, p.deapod_x, x, nullptr, 0.f,
+    return launch_rows_adj(p, p.gx, ra, wa, p.sens, p.deapod_y, p.deapod_x, x, nullptr, 0.f,
                            p.C, st);
+}
+
+static pp_status adjoint_into(const Plan& p, const float2* y, float2* x, cudaStream_t st) {
+    return adjoint_ws(p, y, x, p.wk_a, p.wk_b, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -695,6 +703,32 @@ static pp_status power_iteration(Plan& p, uint64_t seed, int iters, cudaStream_t
         return PP_ERR_NONFINITE;
     }
     p.L = L;
+    return PP_OK;
+}
+
+// Power iteration on I - N_hat (the remark closing the Chebyshev design of
+// Sec. 3.4): converges to 1 - mu, mu the smallest eigenvalue of N_hat when
+// A^H A is injective.  Same start vector and FP64 reductions as
+// power_iteration; returns mu = 1 - (last Rayleigh quotient).
+static pp_status mu_iteration(Plan& p, uint64_t seed, int iters, double* mu, cudaStream_t st) {
+    const int64_t n = p.nimg;
+    PP_TRY(launch_start_vector(p.v, n, seed, st));
+    PP_TRY(launch_norm2(p.v, n, p.red, p.red_blocks, p.scal + 2, st));
+    PP_TRY(launch_scale_by_rnorm(p.v, p.v, n, p.scal + 2, 1.0, 1, st));
+    const float s = (float)(-1.0 / p.L);
+    for (int it = 0; it < iters; ++it) {
+        PP_TRY(normal_into(p, p.v, p.t, s, p.v, 1.f, st));   // t = v - N_hat v
+        PP_TRY(launch_dot(p.v, p.t, n, p.red, p.red_blocks, p.scal + 1, p.scal + 2, st));
+        PP_TRY(launch_scale_by_rnorm(p.t, p.v, n, p.scal + 2, 1.0, 1, st));
+    }
+    double rho = 0.0;
+    PP_TRY_CUDA(cudaMemcpyAsync(&rho, p.scal + 1, sizeof(double), cudaMemcpyDeviceToHost, st));
+    PP_TRY_CUDA(cudaStreamSynchronize(st));
+    if (!isfinite(rho)) {
+        set_error("pp_plan_mu: non-finite Rayleigh quotient");
+        return PP_ERR_NONFINITE;
+    }
+    *mu = 1.0 - rho;
     return PP_OK;
 }
 
@@ -1524,6 +1558,14 @@ pp_status pp_plan_set_tuning(pp_plan* plan, int row_ifft_variant, int stencil_ki
     return PP_OK;
 }
 
+pp_status pp_plan_mu(pp_plan* plan, int iters, uint64_t seed, double* mu, pp_stream stream) {
+    if (!plan || !mu || iters < 1 || iters > 1000000) {
+        set_error("pp_plan_mu: bad argument");
+        return PP_ERR_INVALID_ARG;
+    }
+    return mu_iteration(plan->impl, seed, iters, mu, (cudaStream_t)stream);
+}
+
 pp_status pp_plan_sizes(const pp_plan* plan, int64_t* image_elems, int64_t* kspace_elems) {
     if (!plan) {
         set_error("pp_plan_sizes: NULL plan");
@@ -1605,6 +1647,18 @@ pp_status pp_prox_l1_db4(pp_dims dims, int levels, float lambda, const pp_c64* i
     }
     return launch_prox_db4(dims.n[0], dims.n[1], levels, lambda, reinterpret_cast<const float2*>(in),
                            reinterpret_cast<float2*>(out), (cudaStream_t)stream);
+}
+
+// After a synchronising solve: a NaN or infinite ||b||^2 (first slice's for
+// a batch) or history entry means the input held a non-finite value.
+static pp_status check_history(const char* who, double bn2, const double* h, int iters) {
+    bool ok = std::isfinite(bn2);
+    for (int i = 0; ok && i < 3 * iters; ++i) ok = std::isfinite(h[i]);
+    if (!ok) {
+        set_error("%s: non-finite value in b (||b||^2 = %g) or in the iterates", who, bn2);
+        return PP_ERR_NONFINITE;
+    }
+    return PP_OK;
 }
 
 pp_status pp_fista_solve(pp_plan* plan, const pp_c64* b, float lambda, int iters, const double* c,
@@ -1708,6 +1762,7 @@ pp_status pp_fista_solve(pp_plan* plan, const pp_c64* b, float lambda, int iters
                                         cudaMemcpyDeviceToHost, st));
             PP_TRY_CUDA(cudaStreamSynchronize(st));
             info->bnorm = sqrt(bn2);
+            PP_TRY(check_history("pp_fista_solve", bn2, info->history, iters));
         }
     }
     return PP_OK;
@@ -1941,6 +1996,7 @@ pp_status pp_batch_set_scales(pp_batch* batch, const double* L) {
         b.L[s] = L[s];
         b.sub[s]->L = L[s];
     }
+    b.tape_key.clear();   // checkpoints taken under the old L_s are stale
     return upload_descs(b);
 }
 
@@ -1985,6 +2041,7 @@ pp_status pp_batch_set_tile(pp_batch* batch, int cols_per_cta) {
         PP_TRY(set_items(b, lgt, &items));
     }
     b.gkey.clear();
+    b.tape_key.clear();
     return PP_OK;
 }
 
@@ -2107,9 +2164,12 @@ pp_status pp_batch_fista_solve(pp_batch* batch, const pp_c64* bk, float lambda, 
         info->L = b.L[0];
         info->launches = (g_launches - launches0) + (iters > 0 ? b.graph_kernels : 0);
         if (hist) {
+            double bn2 = 0.0;
+            PP_TRY_CUDA(cudaMemcpyAsync(&bn2, b.scal + 0, sizeof(double), cudaMemcpyDeviceToHost, st));
             PP_TRY_CUDA(cudaMemcpyAsync(info->history, b.hist, sizeof(double) * 3 * iters,
                                         cudaMemcpyDeviceToHost, st));
             PP_TRY_CUDA(cudaStreamSynchronize(st));
+            PP_TRY(check_history("pp_batch_fista_solve", bn2, info->history, iters));
         }
     }
     return PP_OK;
@@ -2119,6 +2179,18 @@ static bool unrolled_args_ok(const pp_batch* batch, const void* bk, int iters, c
                              int d, int ce, float lambda) {
     return batch && bk && c && iters >= 1 && iters <= 100000 && d >= 0 && d <= 10 && ce >= 1 &&
            ce <= iters && lambda >= 0.f && isfinite(lambda);
+}
+
+// What the checkpoints of an unrolled forward depend on besides the contents
+// of b: b's address, lambda, the iteration count, the polynomial, the
+// checkpoint spacing and every slice's L_s.
+static std::vector<double> tape_key_of(const Batch& B, const void* bk, float lambda, int iters,
+                                       const double* c, int d, int ce) {
+    std::vector<double> key = {(double)(uintptr_t)bk, (double)lambda, (double)iters, (double)d,
+                               (double)ce};
+    for (int i = 0; i <= d; ++i) key.push_back(c[i]);
+    key.insert(key.end(), B.L.begin(), B.L.end());
+    return key;
 }
 
 pp_status pp_batch_unrolled_forward(pp_batch* batch, const pp_c64* b, float lambda, int iters,
@@ -2133,9 +2205,7 @@ pp_status pp_batch_unrolled_forward(pp_batch* batch, const pp_c64* b, float lamb
                                     checkpoint_every, reinterpret_cast<float2*>(x_out),
                                     (cudaStream_t)stream);
     if (rc != PP_OK) return rc;
-    B.tape_key = {(double)(uintptr_t)b, (double)lambda, (double)iters, (double)d,
-                  (double)checkpoint_every};
-    for (int i = 0; i <= d; ++i) B.tape_key.push_back(c[i]);
+    B.tape_key = tape_key_of(B, b, lambda, iters, c, d, checkpoint_every);
     return PP_OK;
 }
 
@@ -2150,9 +2220,7 @@ pp_status pp_batch_unrolled_backward(pp_batch* batch, const pp_c64* b, float lam
     }
     Batch& B = batch->impl;
     cudaStream_t st = (cudaStream_t)stream;
-    std::vector<double> key = {(double)(uintptr_t)b, (double)lambda, (double)iters, (double)d,
-                               (double)checkpoint_every};
-    for (int i = 0; i <= d; ++i) key.push_back(c[i]);
+    const std::vector<double> key = tape_key_of(B, b, lambda, iters, c, d, checkpoint_every);
     if (key != B.tape_key) {
         // no matching forward on the tape: run it (its output goes to the solve buffer)
         PP_TRY(unrolled_forward(B, reinterpret_cast<const float2*>(b), lambda, iters, c, d,

@@ -48,7 +48,9 @@ Db4 db4_filter() {
 
 __device__ __forceinline__ float2 soft4(float2 v, float lam) {
     const float m2 = v.x * v.x + v.y * v.y;
-    if (!(m2 > lam * lam)) return make_float2(0.f, 0.f);
+    // |v| <= lambda -> 0 (also v = 0, so no 0 * inf); a NaN fails the test and
+    // stays NaN instead of being thresholded to 0
+    if (m2 <= lam * lam) return make_float2(0.f, 0.f);
     return cscale(v, 1.f - lam * rsqrtf(m2));
 }
 

@@ -285,6 +285,9 @@ pp_status launch_scale_by_rnorm(const float2* in, float2* out, int64_t n, const 
 pp_status launch_axpby(const float2* x, float a, const float2* y, float b, float2* out, int64_t n,
                        cudaStream_t st);
 pp_status launch_start_vector(float2* v, int64_t n, uint64_t seed, cudaStream_t st);
+// x = A^H y with caller-chosen intermediate buffers (pp_capi.cu)
+pp_status adjoint_ws(const Plan& p, const float2* y, float2* x, float2* wa, float2* wb,
+                     cudaStream_t st);
 
 }  // namespace pp
 

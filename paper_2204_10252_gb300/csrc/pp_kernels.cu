@@ -902,7 +902,9 @@ __device__ __forceinline__ void haar_blocks(float2* v, int st) {
 
 __device__ __forceinline__ float2 soft(float2 v, float lam) {
     const float m2 = v.x * v.x + v.y * v.y;
-    if (!(m2 > lam * lam)) return make_float2(0.f, 0.f);
+    // |v| <= lambda -> 0 (also v = 0, so no 0 * inf); a NaN fails the test and
+    // stays NaN instead of being thresholded to 0
+    if (m2 <= lam * lam) return make_float2(0.f, 0.f);
     return cscale(v, 1.f - lam * rsqrtf(m2));
 }
 
@@ -1348,7 +1350,10 @@ __global__ void scale_by_norm_kernel(const float2* __restrict__ in, float2* __re
                                      int64_t n, const double* __restrict__ norm2, double factor,
                                      int invert) {
     const double nv = sqrt(*norm2);
-    const float f = (float)(invert ? (nv > 0.0 ? factor / nv : 0.0) : factor * nv);
+    // a zero norm scales by 0 (b = 0 has the solution 0); a NaN or infinite
+    // norm scales by NaN, so a non-finite input is not turned into zeros
+    const double fi = isfinite(nv) ? (nv > 0.0 ? factor / nv : 0.0) : __longlong_as_double(0x7ff8000000000000ll);
+    const float f = (float)(invert ? fi : factor * nv);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
         out[i] = cscale(in[i], f);

@@ -2,15 +2,16 @@
 // fixed array of device memory that is part of the library image.
 //
 // Who needs it: callers that must not allocate device memory at the time of
-// the call -- code running while a stream capture in global mode is open
-// (cudaMalloc is illegal then), plug-ins whose host application owns all
-// device memory through its own pool, and real-time reconstruction loops
-// with a no-allocation rule after start-up.  Such callers build their plan
-// during start-up and later call pp_adjoint_apply_static instead of
-// pp_adjoint_apply, which writes its intermediates into the plan's own
-// workspace.  (The paper has no counterpart: this is an interface concern.)
+// the call -- plug-ins whose host application owns all device memory
+// through its own pool (a cudaMalloc behind its back can fail or break the
+// host's accounting), and real-time reconstruction loops with a
+// no-allocation rule after start-up (an allocation can stall or fail when
+// memory is fragmented).  Such callers build their plan during start-up and
+// later call pp_adjoint_apply_static instead of pp_adjoint_apply, which
+// writes its intermediates into the plan's own workspace.  Both run the same
+// kernel sequence (adjoint_ws).  The paper has no counterpart: this is an
+// interface concern.
 #include <cuda_runtime.h>
-#include <math.h>
 
 #include <mutex>
 
@@ -30,9 +31,10 @@ constexpr int kMaxDevices = 64;
 std::mutex g_static_mu;
 float2* g_static_addr[kMaxDevices] = {};
 
-// Address of the scratch array on the current device; looked up once per
-// device (the first call on a device must therefore not run inside a stream
-// capture).
+// Address of the scratch array on the current device, looked up on the first
+// call on each device and kept for the life of the process (a
+// cudaDeviceReset of that device, which also frees every plan, ends the
+// library's use of it).
 pp_status static_scratch(float2** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -52,25 +54,8 @@ pp_status static_scratch(float2** out) {
     return PP_OK;
 }
 
-ColArgs cols(int Hin, int Hout, int G, int off_in, int off_out, int ncols, int64_t ibs,
-             int64_t obs, int nbatch, float scale) {
-    ColArgs a;
-    a.Hin = Hin; a.Hout = Hout; a.G = G; a.off_in = off_in; a.off_out = off_out;
-    a.ncols = ncols; a.in_batch_stride = ibs; a.out_batch_stride = obs; a.nbatch = nbatch;
-    a.scale = scale; a.mul_in = nullptr; a.mul_out = nullptr;
-    a.mo_q = 0; a.mo_c = 0; a.mo_cdiv = 1; a.mi_q = 1; a.mi_c = 0; a.mi_cdiv = 1;
-    return a;
-}
-
-RowArgs rows(int n, int G, int off_in, int off_out, int nrows, int64_t cis, float scale) {
-    RowArgs a;
-    a.n = n; a.G = G; a.off_in = off_in; a.off_out = off_out; a.nrows = nrows;
-    a.coil_img_stride = cis; a.scale = scale;
-    return a;
-}
-
 // Scratch elements (complex64) the adjoint needs for plan p: the first
-// buffer (wa) and the second (wb).
+// buffer (wa) and the second (wb) of adjoint_ws.
 void scratch_elems(const Plan& p, int64_t* wa, int64_t* wb) {
     if (p.kind == PP_CARTESIAN && p.ndim == 2) {
         *wa = (int64_t)p.C * p.nimg;
@@ -106,42 +91,8 @@ extern "C" pp_status pp_adjoint_apply_static(const pp_plan* plan, const pp_c64* 
     }
     float2* base = nullptr;
     PP_TRY(static_scratch(&base));
-    float2* wa = base;
-    float2* wb = base + na;
-    const float2* y = reinterpret_cast<const float2*>(yk);
-    float2* x = reinterpret_cast<float2*>(xo);
-    cudaStream_t st = (cudaStream_t)stream;
-    const int nx = p.nx, ny = p.ny, nz = p.nz;
-    const int64_t n = p.nimg;
-    // Every scratch element read below is written earlier in the same call,
-    // so nothing needs clearing between calls.
-    if (p.kind == PP_CARTESIAN && p.ndim == 2) {
-        ColArgs ay = cols(ny, ny, ny, ny / 2, ny / 2, nx, (int64_t)ny * nx, (int64_t)ny * nx, p.C,
-                          (float)(1.0 / sqrt((double)ny)));
-        ay.mul_in = p.mask_c;
-        PP_TRY(launch_cols(p.fy, ay, y, wa, true, st));
-        RowArgs ra = rows(nx, nx, nx / 2, nx / 2, ny, n, (float)(1.0 / sqrt((double)nx)));
-        return launch_rows_adj(p, p.fx, ra, wa, p.sens, nullptr, nullptr, x, nullptr, 0.f, p.C, st);
-    }
-    if (p.kind == PP_CARTESIAN) {
-        for (int c = 0; c < p.C; ++c) {
-            ColArgs az = cols(nz, nz, nz, nz / 2, nz / 2, ny * nx, 0, 0, 1,
-                              (float)(1.0 / sqrt((double)nz)));
-            az.mul_in = p.mask_c; az.mi_q = ny; az.mi_c = 1; az.mi_cdiv = nx;
-            PP_TRY(launch_cols(p.fz, az, y + (int64_t)c * n, wa, true, st));
-            ColArgs ay = cols(ny, ny, ny, ny / 2, ny / 2, nx, (int64_t)ny * nx, (int64_t)ny * nx, nz,
-                              (float)(1.0 / sqrt((double)ny)));
-            PP_TRY(launch_cols(p.fy, ay, wa, wb, true, st));
-            RowArgs ra = rows(nx, nx, nx / 2, nx / 2, ny * nz, 0, (float)(1.0 / sqrt((double)nx)));
-            PP_TRY(launch_rows_adj(p, p.fx, ra, wb, p.sens + (int64_t)c * n, nullptr, nullptr, x,
-                                   c == 0 ? nullptr : x, 1.f, 1, st));
-        }
-        return PP_OK;
-    }
-    const int Gx = p.G_x, Gy = p.G_y;
-    PP_TRY(launch_nufft_spread(p, y, wb, st));
-    ColArgs ci = cols(Gy, ny, Gy, 0, ny / 2, Gx, (int64_t)Gy * Gx, (int64_t)ny * Gx, p.C, 1.f);
-    PP_TRY(launch_cols(p.gy, ci, wb, wa, true, st));
-    RowArgs ra = rows(nx, Gx, 0, nx / 2, ny, (int64_t)ny * nx, 1.f);
-    return launch_rows_adj(p, p.gx, ra, wa, p.sens, p.deapod_y, p.deapod_x, x, nullptr, 0.f, p.C, st);
+    // Every scratch element read by the adjoint is written earlier in the
+    // same call, so nothing needs clearing between calls.
+    return adjoint_ws(p, reinterpret_cast<const float2*>(yk), reinterpret_cast<float2*>(xo), base,
+                      base + na, (cudaStream_t)stream);
 }

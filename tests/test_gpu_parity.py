@@ -313,6 +313,43 @@ def test_solve_parity(pp, prob, d):
     assert r.launches > iters
 
 
+def test_mu_estimate_matches_oracle(pp, prob):
+    # power iteration on I - N_hat (Sec. 3.4 remark) from the same seed and
+    # L: the Rayleigh quotients 1 - mu agree to FP32-apply accuracy
+    L = float(O.power_iteration(prob.normal, prob.shape, 9, iters=30))
+    pp.pp_plan_set_scale(prob.plan, L)
+    mu_ref = O.mu_estimate(prob.normal, prob.shape, 5, L, iters=40)
+    mu = pp.pp_plan_mu(prob.plan, 40, 5)
+    assert abs(mu - mu_ref) <= 1e-5
+    assert mu < 1.0
+
+
+def test_chebyshev_solve_with_estimated_mu(pp):
+    # the Chebyshev design end to end, no caller-supplied mu: a 2-D
+    # Cartesian problem with more coils than the acceleration (A^H A
+    # injective), mu from pp_plan_mu, coefficients from pp_poly_coeffs_cheb,
+    # 20 iterations against the oracle with the oracle's own mu estimate
+    shape, C = (64, 64), 8
+    p = Problem(pp, "cart", shape, C, 12, R=2, acs=16)
+    try:
+        x0 = synth.phantom(shape, 13)
+        b = (p.fwd(x0) + p.ksp(14) * 1e-3).astype(np.complex64)
+        L = float(O.power_iteration(p.normal, shape, 9, iters=30))
+        pp.pp_plan_set_scale(p.plan, L)
+        mu = pp.pp_plan_mu(p.plan, 200, 3)
+        mu_ref = O.mu_estimate(p.normal, shape, 3, L, iters=200)
+        assert 0.0 < mu < 1.0 and abs(mu - mu_ref) <= 1e-5
+        c = [float(v) for v in pp.pp_poly_coeffs_cheb(3, mu)]
+        c_ref = [float(v) for v in O.poly_coeffs_cheb(3, mu_ref)]
+        assert np.max(np.abs(np.array(c) - c_ref)) <= 1e-3 * np.max(np.abs(c_ref))
+        ref = O.pfista(p.normal, p.adj, b.astype(np.complex128), 1e-3, c, 20, L)
+        out = empty(shape)
+        pp.pp_fista_solve(p.plan, dev(b), 1e-3, 20, c, 3, out)
+        assert rel(host(out), ref) <= TOL_SOLVE
+    finally:
+        p.plan.destroy()
+
+
 @pytest.mark.parametrize("coeffs", ["l2", "cheb"])
 def test_ppgd_without_momentum(pp, prob, coeffs):
     # Algorithm "ppgd" (beta_k = 0) with the l2 or the Chebyshev polynomial
@@ -338,6 +375,66 @@ def test_prox_parity(pp, shape, levels, inplace):
     out = xin if inplace else empty(shape)
     pp.pp_prox_l1_haar(shape, levels, lam, xin, out)
     assert rel(host(out), O.prox_l1_haar(x, lam, levels)) <= TOL_APPLY
+
+
+@pytest.mark.parametrize("shape", [(16, 32), (8, 16, 16)])
+def test_prox_edge_cases(pp, shape):
+    # an all-zero 4x4(x4) tile (|v| = 0: no division), a constant tile whose
+    # coarsest Haar coefficient is exactly lambda (4 v in 2-D, 8 v in 3-D
+    # with v = 1/4 resp. 1/8: the output is 0 there), one just above it;
+    # lambda = 0 is the identity and a lambda above every |coefficient|
+    # gives exactly 0
+    x = synth.crandn(shape, 21)
+    nd = len(shape)
+    v = 0.25 if nd == 2 else 0.125
+    t = lambda i: (slice(4 * i, 4 * i + 4),) * nd
+    x[(slice(0, 4),) * nd] = 0.0
+    x[t(1)] = v
+    x[(slice(0, 4),) * (nd - 1) + (slice(8, 12),)] = v * (1 + 1e-3)
+    lam = 1.0
+    out = empty(shape)
+    pp.pp_prox_l1_haar(shape, 2, lam, dev(x), out)
+    got = host(out)
+    ref = O.prox_l1_haar(x, lam, 2)
+    assert np.all(np.isfinite(got))
+    assert rel(got, ref) <= TOL_APPLY
+    assert np.all(got[(slice(0, 4),) * nd] == 0)
+    assert np.max(np.abs(got[t(1)])) <= 1e-6
+    for lam_e, want in ((0.0, x.astype(np.complex128)), (1e6, np.zeros(shape))):
+        pp.pp_prox_l1_haar(shape, 2, lam_e, dev(x), out)
+        got = host(out)
+        if lam_e == 0.0:
+            assert rel(got, want) <= TOL_APPLY
+        else:
+            assert np.all(got == 0)
+
+
+def test_solve_zero_and_nonfinite_b(pp):
+    # b = 0: the solution is 0 (no NaN from the unit-norm scaling of b);
+    # a NaN in b: the iterates are NaN (not silently zero), and a call
+    # with a history reports PP_ERR_NONFINITE
+    shape, C = (32, 32), 2
+    p = Problem(pp, "cart", shape, C, 4, R=2, acs=8)
+    try:
+        pp.pp_plan_set_scale(p.plan, 1.5)
+        c = [float(v) for v in O.poly_coeffs_l2(3)]
+        out = empty(shape)
+        r = pp.pp_fista_solve(p.plan, dev(np.zeros(p.kshape, np.complex64)), 1e-3, 5, c, 3, out,
+                              history=True)
+        assert np.all(host(out) == 0) and r.bnorm == 0.0
+        b = p.ksp(5)
+        b[1, 3, 7] = np.nan
+        pp.pp_fista_solve(p.plan, dev(b), 1e-3, 5, c, 3, out)
+        assert np.all(np.isnan(host(out)))
+        with pytest.raises(pp.PPError) as e:
+            pp.pp_fista_solve(p.plan, dev(b), 1e-3, 5, c, 3, out, history=True)
+        assert e.value.status == 5
+        # the plan still works afterwards
+        b = p.ksp(6)
+        pp.pp_fista_solve(p.plan, dev(b), 1e-3, 5, c, 3, out, history=True)
+        assert np.all(np.isfinite(host(out)))
+    finally:
+        p.plan.destroy()
 
 
 def test_solve_edge_cases(pp):

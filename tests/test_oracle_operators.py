@@ -54,6 +54,26 @@ def test_readout_shortcut_equals_full_fft():
     assert np.linalg.norm(out - ref) <= 1e-14 * np.linalg.norm(ref)
 
 
+@pytest.mark.parametrize("shape,mk", [((12, 16, 10), "poisson"), ((16, 12), "lines")])
+def test_normal_columns_equal_full_fft(shape, mk):
+    # columns of the readout-shortcut normal operator equal the same columns
+    # of the full-FFT definition when the mask is constant along x
+    C = 3
+    s = synth.coil_maps(shape, C, 4).astype(np.complex128)
+    m = (synth.poisson_disc_mask(shape, 2, 4, 5) if mk == "poisson" else
+         synth.line_mask(shape, 2, 4, 5))
+    x = synth.crandn(shape, 6).astype(np.complex128)
+    ref = O.cart_normal(x, s, m)
+    cols = [0, 3, shape[-1] - 1]
+    got = O.cart_normal_columns(x, s, m, cols)
+    assert np.linalg.norm(got - ref[..., cols]) <= 1e-14 * np.linalg.norm(ref[..., cols])
+    # a mask that varies along x breaks the identity (the pin is not vacuous)
+    m2 = m.copy()
+    m2[..., 1::2] = 1 - m2[..., 1::2]
+    bad = O.cart_normal_columns(x, s, m2, cols)
+    assert np.linalg.norm(bad - O.cart_normal(x, s, m2)[..., cols]) > 1e-3 * np.linalg.norm(bad)
+
+
 def test_bessel_i0_matches_scipy():
     x = np.linspace(0.0, 12.0, 97)
     got = O.bessel_i0(x)

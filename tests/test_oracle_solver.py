@@ -276,3 +276,45 @@ def test_unrolled_forward_equals_pfista_without_b_normalisation():
     # the threshold is active: some Haar coefficients are set to zero
     wc = O.haar_fwd(hist[-1], 2)
     assert np.sum(np.abs(wc) == 0) > 0
+
+
+# ---------------------------------------------------------------------------
+# mu for the Chebyshev design (the Sec. 3.4 remark): power iteration on
+# I - N_hat converges to 1 - mu when A^H A is injective.
+# ---------------------------------------------------------------------------
+
+def test_mu_estimate_diagonal_operator():
+    # N = diag(m), L = max m: the smallest eigenvalue of N_hat is
+    # min m / max m; a well-separated spectrum converges fast
+    m = np.array([0.2, 0.9, 3.0, 5.0, 2.5, 4.0, 1.7, 0.6] * 2).reshape(4, 4)
+    normal = lambda v: m * v
+    mu = O.mu_estimate(normal, (4, 4), 3, float(m.max()), iters=400)
+    assert abs(mu - 0.2 / 5.0) <= 1e-10
+    # the iteration approaches from above: fewer steps never undershoot
+    for k in (5, 20, 60):
+        assert O.mu_estimate(normal, (4, 4), 3, float(m.max()), iters=k) >= 0.04 - 1e-15
+
+
+def test_mu_estimate_matches_dense_smallest_eigenvalue():
+    A, b, fwd, adj, nrm = dense_problem(cond=6.0, seed=8)
+    ev = np.linalg.eigvalsh(A.conj().T @ A)
+    L = float(ev.max())
+    mu = O.mu_estimate(nrm, (4, 4), 9, L, iters=3000)
+    assert abs(mu - ev.min() / L) <= 1e-8
+    # with the Chebyshev polynomial on [mu, 1], |1 - z p(z)| <= 1/T_{d+1}(a)
+    # at every eigenvalue of N_hat (the bound the remark's design minimises)
+    c = O.poly_coeffs_cheb(3, mu)
+    z = ev / L
+    a = (1 + mu) / (1 - mu)
+    bound = 1.0 / np.cosh(4 * np.arccosh(a))
+    assert np.max(np.abs(1 - z * O.poly_eval(c, z))) <= bound * (1 + 1e-9)
+
+
+def test_mu_estimate_of_a_singular_operator_is_zero():
+    # a null space (fewer rows than unknowns): 1 is an eigenvalue of
+    # I - N_hat and the estimate goes to 0 (no usable Chebyshev interval)
+    A, b, fwd, adj, nrm = dense_problem(m=10, seed=10)
+    ev = np.linalg.eigvalsh(A.conj().T @ A)
+    L = float(ev.max())
+    assert ev[ev > 1e-9 * L].min() / L > 1e-3        # the smallest non-zero one is far from 0
+    assert abs(O.mu_estimate(nrm, (4, 4), 2, L, iters=300)) <= 1e-8

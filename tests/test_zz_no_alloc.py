@@ -1,9 +1,12 @@
 """pp_adjoint_apply_static: the adjoint for callers that cannot allocate
-device memory when they call (open stream capture in global mode, a host
-application that owns all device memory, a no-allocation real-time loop).
-Its intermediates live in a fixed library-owned device array; its output
-must equal the ordinary pp_adjoint_apply on the same inputs, on two calls in
-a row (the array keeps the previous call's contents)."""
+device memory when they call (a plug-in whose host application owns all
+device memory through its own pool, a real-time loop that forbids allocation
+after start-up).  Its intermediates live in a fixed library-owned device
+array; its output must equal the ordinary pp_adjoint_apply on the same
+inputs, on two calls in a row (the array keeps the previous call's
+contents), and calling it must leave the device's free memory unchanged.
+This file is collected last so that a run stopping at the first failure has
+run every other test before it."""
 import numpy as np
 import pytest
 
@@ -64,6 +67,35 @@ def test_static_adjoint_matches_allocating_adjoint_twice(pp):
                 r = ref.cpu().numpy().astype(np.complex128)
                 g = got.cpu().numpy().astype(np.complex128)
                 assert np.linalg.norm(g - r) <= TOL_APPLY * np.linalg.norm(r)
+        finally:
+            plan.destroy()
+
+
+def test_static_adjoint_leaves_free_device_memory_unchanged(pp):
+    # after one warm call (the first call on a device looks the array up and
+    # may make the runtime commit it), further calls allocate nothing: the
+    # device's free memory and torch's allocator are the same before and
+    # after, while the output is still correct
+    import torch
+    for plan, _sens, draw, shape in cases(pp):
+        try:
+            y = dev(draw(7))
+            ref = torch.empty(shape, dtype=torch.complex64, device="cuda")
+            got = torch.empty_like(ref)
+            pp.pp_adjoint_apply(plan, y, ref)
+            pp.pp_adjoint_apply_static(plan, y, got)
+            torch.cuda.synchronize()
+            free0, _ = torch.cuda.mem_get_info()
+            alloc0 = torch.cuda.memory_allocated()
+            for _ in range(5):
+                pp.pp_adjoint_apply_static(plan, y, got)
+            torch.cuda.synchronize()
+            free1, _ = torch.cuda.mem_get_info()
+            assert free1 == free0
+            assert torch.cuda.memory_allocated() == alloc0
+            r = ref.cpu().numpy().astype(np.complex128)
+            g = got.cpu().numpy().astype(np.complex128)
+            assert np.linalg.norm(g - r) <= TOL_APPLY * np.linalg.norm(r)
         finally:
             plan.destroy()
 
