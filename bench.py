@@ -41,8 +41,7 @@ import synth  # noqa: E402
 WORKLOAD = "spiral2d_256_c32"
 METRIC = "A^H A applies/s (preconditioned FISTA solve, d=5, 100 iterations)"
 UNIT = "applies/s"
-FP32_LANES_PER_SM = 128
-NUM_SMS = 152
+FP32_LANES_PER_SM = 128   # FP32 FMA lanes per SM on this architecture (4 x 32)
 
 
 def parse():
@@ -57,6 +56,8 @@ def parse():
                     choices=[WORKLOAD, "cart2d_128_c8", "cart3d_256x256x128_c32", "batched2d_64",
                              "unrolled2d_8x256_c16"],
                     help="benchmark line to produce (the default is the headline workload)")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the 3-D and batched lines that the default run appends")
     ap.add_argument("--apply-only", type=int, default=0, metavar="K",
                     help="profiling aid: build the workload's plan (no power iteration), apply "
                          "its operator K times and exit without a bench line")
@@ -219,6 +220,30 @@ def kernel_flops(c, K, toeplitz=False):
     }
 
 
+def fp32_peak(dev, clocks):
+    """FP32 CUDA-core peak of this device: SMs (from the device) x 128 FMA
+    lanes x 2 flop x the median SM clock sampled during the timed region
+    (the maximum clock when no sample was taken)."""
+    import torch
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = clocks.get("sm_mhz") or clocks.get("sm_max_mhz")
+    src = "median SM clock sampled during the timed region"
+    if not mhz:
+        mhz, src = 2070.0, "maximum SM clock (no clock samples)"
+    peak = sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+    return peak, "derived: %d SMs x %d FP32 lanes x 2 flop/FMA x %.0f MHz (%s)" % (
+        sms, FP32_LANES_PER_SM, mhz, src)
+
+
+def hbm_peak_gbs():
+    """Measured HBM copy bandwidth of this machine's GPUs, else the fallback."""
+    try:
+        d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(d["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except Exception:
+        return 6800.0, "fallback 6.8 TB/s"
+
+
 def csrc_digest():
     h = hashlib.sha256()
     for f in sorted(glob.glob(os.path.join(ROOT, "paper_2204_10252_gb300", "csrc", "*"))):
@@ -242,6 +267,19 @@ def ncu_traffic(kernel, summary="ncu_traffic.json"):
 
 
 EXACT_SAMPLES = 4096
+_SAMPLE = {}
+
+
+def _sample_init(seed_rank, exact):
+    """Worker start-up: the replica's inputs, generated in the worker."""
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    c = cfg()
+    _, sens, traj, _, _ = make_inputs(c, seed_rank)
+    _SAMPLE.update(c=c, sens=sens, traj=traj, exact=exact)
+
+
+def _sample_run(coils):
+    return oracle_sample(_SAMPLE["c"], _SAMPLE["sens"], _SAMPLE["traj"], coils, _SAMPLE["exact"])
 
 
 def oracle_sample(c, sens, traj, coils, exact=False):
@@ -260,24 +298,51 @@ def oracle_sample(c, sens, traj, coils, exact=False):
     return time.perf_counter() - t0, coils / float(c["coils"])
 
 
-def cpu_baseline(c, sens, traj, budget_s=15.0, coils=2, exact=False):
-    """The oracle as it stands, timed on the host cores on ~budget_s of
+class OraclePool:
+    """The oracle as it stands on every host core: one spawned worker per
+    core (numpy's FFT and scatter-add are single-threaded, so workers are the
+    way to use the cores), each running bounded samples of the workload."""
+
+    def __init__(self, exact=False, workers=None):
+        import multiprocessing as mp
+        self.cores = int(workers or os.cpu_count() or 1)
+        self.pool = mp.get_context("spawn").Pool(self.cores, initializer=_sample_init,
+                                                 initargs=(0, exact))
+        self.pool.map(_sample_run, [1] * self.cores)   # start-up and first touch, untimed
+
+    def step(self, coils):
+        """One concurrent sample per worker: (wall seconds, full applies done)."""
+        t0 = time.perf_counter()
+        res = self.pool.map(_sample_run, [coils] * self.cores)
+        return time.perf_counter() - t0, sum(f for _, f in res)
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def cpu_baseline(c, budget_s=15.0, coils=2, exact=False):
+    """The oracle as it stands, timed on all host cores on ~budget_s of
     bounded samples; reported in full-apply units."""
-    el, frac, n = 0.0, 0.0, 0
-    while el < budget_s:
-        t, f = oracle_sample(c, sens, traj, coils, exact)
-        el += t
-        frac += f
-        n += 1
+    op = OraclePool(exact)
+    try:
+        el, frac, n = 0.0, 0.0, 0
+        while el < budget_s:
+            t, f = op.step(coils)
+            el += t
+            frac += f
+            n += 1
+    finally:
+        op.close()
     if exact:
-        what = ("%d samples, each the exact-NDFT A^H A of 1 of the 32 coils over the first %d of the "
-                "65536 spiral samples (256x256) on the numpy FP64 oracle (direct sums), scaled to "
-                "full applies" % (n, EXACT_SAMPLES))
+        what = ("%d rounds of %d concurrent samples (one per host core), each the exact-NDFT A^H A "
+                "of 1 of the 32 coils over the first %d of the 65536 spiral samples (256x256) on the "
+                "numpy FP64 oracle (direct sums), scaled to full applies" % (n, op.cores, EXACT_SAMPLES))
     else:
-        what = ("%d samples, each the A^H A apply of %d of the 32 coils (256x256, 65536-sample "
-                "spiral) on the numpy FP64 oracle, scaled to full applies; numpy's FFT and "
-                "scatter-add run single-threaded" % (n, coils))
-    return {"value": frac / el, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": what}
+        what = ("%d rounds of %d concurrent samples (one worker process per host core), each the "
+                "A^H A apply of %d of the 32 coils (256x256, 65536-sample spiral) on the numpy FP64 "
+                "oracle, scaled to full applies" % (n, op.cores, coils))
+    return {"value": frac / el, "unit": UNIT, "cores": op.cores, "kind": "oracle", "sample": what}
 
 
 # ---------------------------------------------------------------------------
@@ -286,24 +351,28 @@ def cpu_baseline(c, sens, traj, budget_s=15.0, coils=2, exact=False):
 def run_reference(args, rank, world, coils=2):
     if rank != 0:
         return
-    c = cfg()
-    seed, sens, traj, x_true, noise = make_inputs(c, 0)
-    for _ in range(args.warmup):
-        oracle_sample(c, sens, traj, coils)
-    el, frac = 0.0, 0.0
-    for _ in range(args.steps):
-        t, f = oracle_sample(c, sens, traj, coils)
-        el += t
-        frac += f
+    op = OraclePool()
+    try:
+        for _ in range(args.warmup):
+            op.step(coils)
+        el, frac = 0.0, 0.0
+        for _ in range(args.steps):
+            t, f = op.step(coils)
+            el += t
+            frac += f
+    finally:
+        op.close()
     v = frac / el
-    sample = "each step is the A^H A apply of %d of the 32 coils (256x256, 65536-sample spiral) " \
-             "on the numpy FP64 oracle, scaled to full applies" % coils
+    sample = ("each step is one A^H A apply of %d of the 32 coils (256x256, 65536-sample spiral) per "
+              "host core, %d worker processes running concurrently, on the numpy FP64 oracle, scaled "
+              "to full applies" % (coils, op.cores))
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": op.cores, "kind": "oracle",
+                         "sample": sample},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
@@ -424,14 +493,20 @@ def main():
     launches_per_apply = {"cols_kernel": 2, "cols4_kernel": 2, "ci_cols_kernel": 2}
     per_launch_ms = {k: v / launches_per_apply.get(k, 1) for k, v in stages.items()}
     dom = max(stages, key=stages.get)
-    sm_clock = clocks["sm_max_mhz"] or 2070.0
-    peak_tflops = NUM_SMS * FP32_LANES_PER_SM * 2 * 2070.0e6 / 1e12
+    peak_tflops, peak_src = fp32_peak(dev, clocks)
     ach = flops.get(dom, float("nan")) / (per_launch_ms[dom] / 1e3) / 1e12
+    traffic = ncu_traffic(dom, "ncu_traffic_toeplitz.json" if toep else "ncu_traffic.json")
+    hbm_peak, hbm_src = hbm_peak_gbs()
     roofline = {
         "bound": "alu", "kernel": dom, "achieved": ach, "peak": peak_tflops, "unit": "TFLOP/s",
-        "frac": ach / peak_tflops,
-        "traffic": ncu_traffic(dom, "ncu_traffic_toeplitz.json" if toep else "ncu_traffic.json"),
-        "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop/FMA x 2070 MHz (FP32 CUDA cores)",
+        "frac": ach / peak_tflops, "traffic": traffic, "peak_source": peak_src,
+        # the same launch against HBM: its DRAM bytes (ncu, cold cache) over
+        # its live per-launch time, for reference (the working set is
+        # L2-resident, so this is not the bound)
+        "hbm_gbs_of_dominant": None if traffic is None else traffic / (per_launch_ms[dom] / 1e3) / 1e9,
+        "hbm_frac_of_dominant": None if traffic is None else
+        traffic / (per_launch_ms[dom] / 1e3) / 1e9 / hbm_peak,
+        "hbm_peak_gbs": hbm_peak, "hbm_peak_source": hbm_src,
         "stage_ms_per_apply": {k: round(v, 5) for k, v in stages.items()},
         "stage_share": {k: round(v / apply_ms, 4) for k, v in stages.items()},
     }
@@ -479,12 +554,38 @@ def main():
         out["time_to_nrmse"] = time_to_target(pp, plan, b, c, coeffs, setup_plan_s, stream,
                                               wavelet=args.wavelet)
         if rank == 0 and world == 1:
-            out["cpu_baseline"] = cpu_baseline(c, sens, traj, exact=toep)
+            out["cpu_baseline"] = cpu_baseline(c, exact=toep)
+    plan.destroy()
+    if world == 1 and not args.no_extras and not args.no_secondary:
+        del sens_t, b, x_out, flush
+        torch.cuda.empty_cache()
+        out["secondary"] = secondary_lines(args, local)
     if rank == 0:
         print(json.dumps(out))
-    plan.destroy()
     if world > 1:
         dist.destroy_process_group()
+
+
+SECONDARY = (("cart3d_256x256x128_c32", 20), ("batched2d_64", 5))
+SECONDARY_KEYS = ("metric", "value", "unit", "ms_per_step", "steps", "warmup", "config", "clocks",
+                  "roofline", "prox", "batched_apply_ms", "stage_ms_per_apply")
+
+
+def secondary_lines(args, local):
+    """The HBM-bound workloads, measured in the same run with the same timing
+    rules (bench_workloads): the 256x256x128, 32-coil normal operator with
+    the 3-D Haar prox, and the 64-slice batched solve and apply."""
+    import torch
+    import paper_2204_10252_gb300 as pp
+    import bench_workloads
+    sec = {}
+    for wl, steps in SECONDARY:
+        a = argparse.Namespace(**vars(args))
+        a.workload, a.steps, a.warmup, a.apply_only = wl, steps, max(3, min(args.warmup, 5)), 0
+        r = bench_workloads.run(a, pp, 0, 1, local)
+        sec[wl] = {k: r[k] for k in SECONDARY_KEYS if k in r}
+        torch.cuda.empty_cache()
+    return sec
 
 
 def time_to_target(pp, plan, b, c, coeffs, setup_s, stream, target=1e-3, wavelet="haar"):

@@ -38,13 +38,7 @@ def _timed(fn, steps, dev, local):
 
 
 def _hbm_peak():
-    try:
-        import json
-        import os
-        d = json.load(open(os.path.join(bench.ROOT, "MEASURED_PEAKS.json")))
-        return float(d["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
-    except Exception:
-        return 6800.0, "fallback 6.8 TB/s"
+    return bench.hbm_peak_gbs()
 
 
 def _base(args, world, metric, unit, value, ms_per_step, cfg, clocks, extra=None):
@@ -115,6 +109,13 @@ def cart3d(args, pp, rank, world, local):
     gbs = bytes_apply / (ms / args.steps / 1e3) / 1e9
     peak, src = _hbm_peak()
     stages = pp.pp_profile_normal(plan, x, y, reps=2)
+    # FFT work per apply: per coil and x column, nz length-ny transforms and
+    # ny pairs of length-nz transforms each way (5 N log2 N per transform)
+    nz, ny, nx = shape
+    fft = lambda N: 5.0 * N * math.log2(N)
+    flops_apply = C * nx * 2.0 * (nz * fft(ny) + ny * fft(nz))
+    tflops = flops_apply / (ms / args.steps / 1e3) / 1e12
+    fp32_peak, fp32_src = bench.fp32_peak(dev, clk)
     # the 3-D Haar prox of the solve (2 levels, 4x4x4 tiles): one read and one
     # write of a 67 MB volume per call, HBM-bound.  Calls alternate between two
     # (input, output) pairs, 268 MB in all (twice the L2), back to back.
@@ -139,9 +140,13 @@ def cart3d(args, pp, rank, world, local):
                   "l2": "inputs larger than L2 (2 GiB of coil maps) and flushed between steps",
                   "input_generation_s": gen_s}, clk,
                  {"roofline": {"bound": "hbm", "kernel": "whole normal apply", "achieved": gbs,
-                               "peak": peak, "unit": "GB/s", "frac": gbs / peak, "traffic": None,
+                               "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                               "traffic": bench.ncu_traffic("cart3d_normal", "ncu_traffic_3d.json"),
                                "peak_source": src,
-                               "algorithmic_bytes_per_apply": bytes_apply},
+                               "algorithmic_bytes_per_apply": bytes_apply,
+                               "fft_flops_per_apply": flops_apply, "tflops": tflops,
+                               "fp32_peak": fp32_peak, "fp32_frac": tflops / fp32_peak,
+                               "fp32_peak_source": fp32_src},
                   "stage_ms_per_apply": stages,
                   "prox": {"kernel": "prox3q_kernel", "bound": "hbm", "achieved": prox_gbs, "peak": peak,
                            "unit": "GB/s", "frac": prox_gbs / peak, "bytes_per_call": prox_bytes,

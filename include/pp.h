@@ -44,7 +44,8 @@ typedef enum {
     PP_ERR_OOM = 3,          /* device allocation failed                  */
     PP_ERR_CUDA = 4,         /* a CUDA runtime call failed                */
     PP_ERR_NONFINITE = 5,    /* NaN/Inf met in a reduction                */
-    PP_ERR_TIMEOUT = 6       /* reserved: a bounded device wait expired   */
+    PP_ERR_TIMEOUT = 6       /* a bounded device wait expired (see the
+                                3-D dataflow operator, pp_selftest_wait) */
 } pp_status;
 
 typedef struct { float re, im; } pp_c64;
@@ -142,7 +143,10 @@ pp_status pp_plan_sizes(const pp_plan* plan, int64_t* image_elems, int64_t* kspa
  *    followed by a coil sum); for 3-D Cartesian plans 16 = the whole normal
  *    operator as one kernel on 16-CTA clusters, 4 x columns per cluster task
  *    (nz = 128, ny in {128, 192, 256}), -16 = the same with 2 columns per
- *    task and two CTAs per SM, 1 = three passes per coil; for 2-D Cartesian plans 1, 2, 4 or 8
+ *    task and two CTAs per SM, 1 = three passes per coil, 3 = one persistent
+ *    kernel whose blocks claim y-FFT, z round-trip and y-IFFT work items of
+ *    16-column x-blocks and stencil_coils-coil groups in dependency order
+ *    (ny, nz register-FFT lengths; up to 8 coils per group); for 2-D Cartesian plans 1, 2, 4 or 8
  *    = CTAs per 8-column group, the coils split over a cluster of that size;
  *  - stencil_kind: the G^T G stencil kernel (0 = one output per thread,
  *    1 = two outputs per thread, both staging one coil at a time with
@@ -372,6 +376,16 @@ pp_status pp_batch_unrolled_backward(pp_batch* batch, const pp_c64* b, float lam
 pp_status pp_profile_normal(const pp_plan* plan, const pp_c64* x, pp_c64* y, int reps,
                             int max_stages, char* names, double* ms, int* nstages,
                             pp_stream stream);
+
+/* Self-test of the bounded device wait (no counterpart in the paper).  Kernels
+ * that wait on work of other thread blocks (the 3-D dataflow normal operator)
+ * poll with a time limit and, past it, record the failure and return instead
+ * of hanging; the next synchronising call on the plan reports
+ * PP_ERR_TIMEOUT.  This call runs one block that waits on a counter nothing
+ * increments, with a limit of limit_ns (1e6 .. 1e9 ns), and returns
+ * PP_ERR_TIMEOUT when the wait gave up as it must; the device stays usable.
+ * Allocates 8 bytes of device memory; synchronises `stream`. */
+pp_status pp_selftest_wait(int64_t limit_ns, pp_stream stream);
 
 /* Message for the last failing call on this thread ("" if none). */
 const char* pp_last_error(void);

@@ -106,6 +106,7 @@ _SIGS = {
                                                   ctypes.c_void_p, ctypes.c_void_p,
                                                   ctypes.POINTER(ctypes.c_double),
                                                   ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
+    "pp_selftest_wait": (ctypes.c_int, [ctypes.c_int64, ctypes.c_void_p]),
     "pp_last_error": (ctypes.c_char_p, []),
 }
 
@@ -566,6 +567,12 @@ def pp_batch_unrolled_backward(batch: Batch, b, lam: float, iters: int, c, d: in
                                             ctypes.byref(gl), gc, _stream(stream)),
            "pp_batch_unrolled_backward")
     return gl.value, np.array(list(gc), dtype=np.float64)
+
+
+def pp_selftest_wait(limit_ns: int, stream=None):
+    """One block waits on a counter nothing increments; raises PPError with
+    PP_ERR_TIMEOUT when the bounded wait gives up (the expected outcome)."""
+    _check(lib().pp_selftest_wait(int(limit_ns), _stream(stream)), "pp_selftest_wait")
 
 
 def pp_last_error() -> str:

@@ -166,6 +166,8 @@ static pp_status normal_into(const Plan& p, const float2* x, float2* out, float 
             return c3cl_normal(p, 4, x, out, scale, operand, alpha, st);
         if (p.tune_c3 == 2 && p.c3cl2_clusters > 0)
             return c3cl_normal(p, 2, x, out, scale, operand, alpha, st);
+        if (p.tune_c3 == 3 && p.c3df_ctas > 0)
+            return c3df_normal(p, x, out, scale, operand, alpha, st);
         bool done = false;
         PP_TRY(cart3d4_normal(p, x, out, scale, operand, alpha, p.wk_a, st, &done));
         if (done) return PP_OK;
@@ -576,24 +578,32 @@ static pp_status tune_noncartesian(Plan& p, cudaStream_t st) {
     return PP_OK;
 }
 
-// 3-D Cartesian: the one-kernel cluster operator against the three passes
-// per coil, timed on the plan's buffers (two rounds of 3 applies after one
-// warm-up); the faster is kept.
+// 3-D Cartesian: the three passes per coil, the one-kernel cluster operator
+// and the dataflow operator with 2, 4 or 8 coils per group, timed on the
+// plan's buffers (two rounds of 3 applies after one warm-up); the fastest is
+// kept.
 static pp_status tune_cart3d(Plan& p, cudaStream_t st) {
-    if (p.c3cl_clusters <= 0 && p.c3cl2_clusters <= 0) return PP_OK;
+    std::vector<std::pair<int, int>> cand = {{0, 0}};
+    if (p.c3cl_clusters > 0) cand.push_back({1, 0});
+    if (p.c3cl2_clusters > 0) cand.push_back({2, 0});
+    if (p.c3df_ctas > 0)
+        for (int cgc : {2, 4, 8})
+            if (cgc <= std::max(2, p.C) && (cgc == 2 || cgc <= p.C) &&
+                2 * c3df_slot_elems(p, cgc) <= p.c3df_w_elems)
+                cand.push_back({3, cgc});
+    if (cand.size() == 1) return PP_OK;
     cudaEvent_t e0, e1;
     PP_TRY_CUDA(cudaEventCreate(&e0));
     PP_TRY_CUDA(cudaEventCreate(&e1));
     PP_TRY_CUDA(cudaMemsetAsync(p.v, 0, sizeof(float2) * (size_t)p.nimg, st));
-    std::vector<int> cand = {0};
-    if (p.c3cl_clusters > 0) cand.push_back(1);
-    if (p.c3cl2_clusters > 0) cand.push_back(2);
     std::vector<float> best(cand.size(), 1e30f);
     for (int round = 0; round < 2; ++round)
         for (size_t i = 0; i < cand.size(); ++i) {
-            p.tune_c3 = cand[i];
+            p.tune_c3 = cand[i].first;
+            if (cand[i].second) p.c3df_cg = cand[i].second;
             if (best[i] > 1.5e30f) continue;
-            if (!launches_ok([&]() { return normal_into(p, p.v, p.t, 1.f, nullptr, 0.f, st); })) {
+            if (!launches_ok([&]() { return normal_into(p, p.v, p.t, 1.f, nullptr, 0.f, st); }) ||
+                (p.tune_c3 == 3 && c3df_check(p, st) != PP_OK)) {
                 best[i] = 2e30f;
                 continue;
             }
@@ -603,9 +613,12 @@ static pp_status tune_cart3d(Plan& p, cudaStream_t st) {
             PP_TRY_CUDA(cudaEventSynchronize(e1));
             float ms = 0.f;
             PP_TRY_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            if (p.tune_c3 == 3 && c3df_check(p, st) != PP_OK) ms = 2e30f;
             best[i] = std::min(best[i], ms);
         }
-    p.tune_c3 = cand[std::min_element(best.begin(), best.end()) - best.begin()];
+    const size_t bi = std::min_element(best.begin(), best.end()) - best.begin();
+    p.tune_c3 = cand[bi].first;
+    if (cand[bi].second) p.c3df_cg = cand[bi].second;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return PP_OK;
@@ -698,6 +711,7 @@ static pp_status power_iteration(Plan& p, uint64_t seed, int iters, cudaStream_t
     double L = 0.0;
     PP_TRY_CUDA(cudaMemcpyAsync(&L, p.scal + 1, sizeof(double), cudaMemcpyDeviceToHost, st));
     PP_TRY_CUDA(cudaStreamSynchronize(st));
+    PP_TRY(c3df_check(p, st));
     if (!(L > 0.0) || !isfinite(L)) {
         set_error("power iteration gave a non-positive or non-finite norm estimate (%g)", L);
         return PP_ERR_NONFINITE;
@@ -724,6 +738,7 @@ static pp_status mu_iteration(Plan& p, uint64_t seed, int iters, double* mu, cud
     double rho = 0.0;
     PP_TRY_CUDA(cudaMemcpyAsync(&rho, p.scal + 1, sizeof(double), cudaMemcpyDeviceToHost, st));
     PP_TRY_CUDA(cudaStreamSynchronize(st));
+    PP_TRY(c3df_check(p, st));
     if (!isfinite(rho)) {
         set_error("pp_plan_mu: non-finite Rayleigh quotient");
         return PP_ERR_NONFINITE;
@@ -1435,7 +1450,20 @@ pp_status pp_plan_create(pp_plan** out, pp_dims dims, int coils, const pp_c64* s
     if (rc == PP_OK && p.kind == PP_CARTESIAN && p.ndim == 3) {
         p.c3cl_clusters = c3cl_prepare(p, 4);
         p.c3cl2_clusters = c3cl_prepare(p, 2);
-        rc = tune_cart3d(p, st);
+        p.c3df_ctas = c3df_prepare(p);
+        if (p.c3df_ctas > 0) {
+            // two phase slots for up to 8 coils per group; counters for 1
+            p.c3df_w_elems = 2 * c3df_slot_elems(p, std::min(8, std::max(2, p.C)));
+            p.c3df_cnt_ints = 0;
+            for (int cgc = 1; cgc <= 8; ++cgc)
+                p.c3df_cnt_ints = std::max(p.c3df_cnt_ints, c3df_counter_ints(p, cgc));
+            if ((rc = alloc_n(p, &p.c3df_w, p.c3df_w_elems)) == PP_OK &&
+                (rc = alloc_n(p, &p.c3df_cnt, p.c3df_cnt_ints)) == PP_OK)
+                rc = cudaMemsetAsync(p.c3df_cnt, 0, sizeof(int) * p.c3df_cnt_ints, st) == cudaSuccess
+                         ? PP_OK : cuda_status(cudaGetLastError(), "cudaMemsetAsync");
+            p.c3df_cg = std::min(4, p.C);
+        }
+        if (rc == PP_OK) rc = tune_cart3d(p, st);
     }
     if (rc == PP_OK && p.kind == PP_NONCARTESIAN) rc = setup_ci(p, st);
     if (rc == PP_OK && p.toep) rc = setup_toeplitz(p, s, st);
@@ -1492,27 +1520,45 @@ pp_status pp_plan_tuning(const pp_plan* plan, int* row_ifft_variant, int* stenci
     if (row_ifft_variant) {
         const Plan& p = plan->impl;
         if (p.kind == PP_CARTESIAN && p.ndim == 3)
-            *row_ifft_variant = p.tune_c3 == 1 ? 16 : (p.tune_c3 == 2 ? -16 : 1);
+            *row_ifft_variant = p.tune_c3 == 1 ? 16 : (p.tune_c3 == 2 ? -16 : (p.tune_c3 == 3 ? 3 : 1));
         else if (p.kind == PP_CARTESIAN)
             *row_ifft_variant = p.tune_c2;
         else
             *row_ifft_variant = p.tune_rows_adj_cl ? p.tune_rows_adj_cl : 1;
     }
     if (stencil_kind) *stencil_kind = plan->impl.tune_stencil_kind;
-    if (stencil_coils) *stencil_coils = plan->impl.tune_stencil_cpc ? plan->impl.tune_stencil_cpc : 8;
+    if (stencil_coils) {
+        const Plan& p = plan->impl;
+        *stencil_coils = (p.kind == PP_CARTESIAN && p.ndim == 3 && p.tune_c3 == 3)
+                             ? p.c3df_cg : (p.tune_stencil_cpc ? p.tune_stencil_cpc : 8);
+    }
     return PP_OK;
 }
 
 pp_status pp_plan_set_tuning(pp_plan* plan, int row_ifft_variant, int stencil_kind, int stencil_coils) {
     if (!plan || !(row_ifft_variant == 1 || row_ifft_variant == 2 || row_ifft_variant == 4 ||
                    row_ifft_variant == -1 || row_ifft_variant == 8 || row_ifft_variant == 16 ||
-                   row_ifft_variant == -16) ||
+                   row_ifft_variant == -16 || row_ifft_variant == 3) ||
         stencil_kind < 0 || stencil_kind > 9 || stencil_coils < 1 || stencil_coils > 64) {
-        set_error("pp_plan_set_tuning: row variant must be 1, 2, 4, 8, -1, 16 or -16; stencil kind 0..9; "
-                  "stencil coils 1..64");
+        set_error("pp_plan_set_tuning: row variant must be 1, 2, 3, 4, 8, -1, 16 or -16; stencil "
+                  "kind 0..9; stencil coils 1..64");
         return PP_ERR_INVALID_ARG;
     }
     Plan& p = plan->impl;
+    if (row_ifft_variant == 3) {
+        const int cgv = std::min(stencil_coils, std::max(1, p.C));   // the kernel's group size
+        if (!(p.kind == PP_CARTESIAN && p.ndim == 3) || p.c3df_ctas <= 0 ||
+            2 * c3df_slot_elems(p, cgv) > p.c3df_w_elems ||
+            c3df_counter_ints(p, cgv) > p.c3df_cnt_ints) {
+            set_error("pp_plan_set_tuning: row variant 3 (the 3-D dataflow operator) needs a 3-D "
+                      "Cartesian plan with register-FFT lengths ny, nz and at most 8 coils per group");
+            return PP_ERR_UNSUPPORTED;
+        }
+        p.tune_c3 = 3;
+        p.c3df_cg = stencil_coils;
+        p.gkey.clear();
+        return PP_OK;
+    }
     if ((row_ifft_variant == 16 && p.c3cl_clusters <= 0) ||
         (row_ifft_variant == -16 && p.c3cl2_clusters <= 0)) {
         set_error("pp_plan_set_tuning: the one-kernel cluster operator needs a 3-D Cartesian plan "
@@ -1564,6 +1610,14 @@ pp_status pp_plan_mu(pp_plan* plan, int iters, uint64_t seed, double* mu, pp_str
         return PP_ERR_INVALID_ARG;
     }
     return mu_iteration(plan->impl, seed, iters, mu, (cudaStream_t)stream);
+}
+
+pp_status pp_selftest_wait(int64_t limit_ns, pp_stream stream) {
+    if (limit_ns < 1000000 || limit_ns > 1000000000) {
+        set_error("pp_selftest_wait: limit must be 1 ms .. 1 s");
+        return PP_ERR_INVALID_ARG;
+    }
+    return selftest_wait((long long)limit_ns, (cudaStream_t)stream);
 }
 
 pp_status pp_plan_sizes(const pp_plan* plan, int64_t* image_elems, int64_t* kspace_elems) {
@@ -1762,6 +1816,7 @@ pp_status pp_fista_solve(pp_plan* plan, const pp_c64* b, float lambda, int iters
                                         cudaMemcpyDeviceToHost, st));
             PP_TRY_CUDA(cudaStreamSynchronize(st));
             info->bnorm = sqrt(bn2);
+            PP_TRY(c3df_check(p, st));
             PP_TRY(check_history("pp_fista_solve", bn2, info->history, iters));
         }
     }

@@ -1,0 +1,415 @@
+// 3-D Cartesian normal operator (Sec. 5.1) as ONE persistent kernel whose
+// CTAs claim work items in dependency order:
+//   out[:, :, x] = scale * sum_c conj(S_c) F_yz^H M F_yz (S_c x)[:, :, x] + alpha * operand
+// The readout axis x is never transformed (M is constant along it), so every
+// x column is its own (z, y) problem.  The volume is cut into x-blocks of 16
+// columns (128-byte rows of every map) and the coils into groups of CG; a
+// phase k = (x-block b, coil group g) runs three kinds of item:
+//   A (c, z):  y FFT of S_c x on z-plane z            -> W[c][z][ky][16]
+//   B (c, ky): z FFT, mask M[kz][ky], z IFFT in place  on W[c][:, ky][16]
+//   C (z):     y IFFT of W[c][z] for c in the group, times conj(S_c),
+//              summed over the group in registers; added to the partial sum
+//              of the earlier groups in `out` (the last group applies scale
+//              and the Horner axpy epilogue)
+// W holds two phases (slots k mod 2) and stays in L2 with the group's maps,
+// which the C items re-read.  Items are numbered phase by phase (A, then B,
+// then C, coil-major), and a CTA takes the next number from a global counter
+// once it has finished its current item, so every item waits only on items
+// with smaller numbers that running CTAs hold:
+//   A(k)      after C(k-2)  (slot reuse)
+//   B(k, c)   after all A(k, c)
+//   C(k, z)   after all B(k, c) of each coil c, and after C(k-1) (the partial
+//             sum in `out`) when g > 0
+// The smallest unfinished number is therefore always runnable, and the HBM
+// stream of phase k+1's maps (A items) overlaps phase k's transforms.
+// Completion is counted per (phase, coil) with release atomics; a wait is an
+// acquire poll bounded in time: past the limit the CTA records a timeout in
+// the error word and every CTA leaves (the host reports PP_ERR_TIMEOUT).
+// Data made by other items (W, the partial sums) is read with ld.global.cg
+// (L2, never a stale L1 line).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "pp_fft4.cuh"
+#include "pp_internal.h"
+
+namespace pp {
+namespace {
+
+constexpr int DN1 = 16;   // first factor of every register FFT
+constexpr int DTX = 16;   // x columns per item
+constexpr unsigned long long kWaitNs = 1000000000ull;   // 1 s bound on one wait
+
+template <int N2Y, int N2Z> struct Df {
+    static constexpr int NY = 16 * N2Y, NZ = 16 * N2Z;
+    static constexpr int RMAX = (N2Y > N2Z ? (N2Y > DN1 ? N2Y : DN1) : (N2Z > DN1 ? N2Z : DN1));
+    static constexpr int THREADS = DTX * RMAX;
+    static constexpr int YE = DN1 * (N2Y > N2Z ? N2Y : N2Z) * DTX;   // transpose buffer elements
+    static constexpr size_t SMEM = sizeof(float2) * (YE + NY + NZ);
+};
+
+struct DfArgs {
+    const float2* x;
+    const float2* S;
+    float2* out;
+    const float2* operand;
+    float scale, alpha;
+    const float* mask_fo;   // [nz][ny], FFT order, 1/(ny nz) folded in
+    const float2* twy;
+    const float2* twz;
+    float2* W;              // 2 slots of CG * nz * ny * 16
+    int* cnt;               // cntA[P*CG], cntB[P*CG], cntC[P], next, err
+    int nx, C, CG, ng, nb;
+    int64_t slot;           // elements per slot
+};
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void red_release_add(int* p, int v) {
+    asm volatile("red.release.gpu.global.add.s32 [%0], %1;\n" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+    return t;
+}
+
+// Block-wide: wait until *cnt >= target (thread 0 polls).  Returns false when
+// the error word is set (by this wait's time limit or by another CTA).
+__device__ __forceinline__ bool df_wait(const int* cnt, int target, int* err,
+                                        unsigned long long limit_ns = kWaitNs) {
+    int good = 1;
+    if (threadIdx.x == 0) {
+        if (ld_acquire(cnt) < target) {
+            const unsigned long long t0 = gtimer();
+            while (ld_acquire(cnt) < target) {
+                if (*(volatile int*)err) {
+                    good = 0;
+                    break;
+                }
+                if (gtimer() - t0 > limit_ns) {
+                    atomicExch(err, 1);
+                    good = 0;
+                    break;
+                }
+                __nanosleep(200);
+            }
+        }
+        if (good && *(volatile int*)err) good = 0;
+    }
+    return __syncthreads_and(good) != 0;
+}
+
+// Block-wide: the item's stores are done; count it (release).
+__device__ __forceinline__ void df_signal(int* cnt) {
+    __syncthreads();
+    if (threadIdx.x == 0) red_release_add(cnt, 1);
+}
+
+template <int N2Y, int N2Z>
+__global__ void __launch_bounds__(Df<N2Y, N2Z>::THREADS, Df<N2Y, N2Z>::THREADS <= 256 ? 2 : 1)
+c3_dataflow_kernel(DfArgs a) {
+    constexpr int NY = Df<N2Y, N2Z>::NY, NZ = Df<N2Y, N2Z>::NZ;
+    extern __shared__ float4 df_sm4[];
+    float2* Y = reinterpret_cast<float2*>(df_sm4);
+    float2* twy = Y + Df<N2Y, N2Z>::YE;
+    float2* twz = twy + NY;
+    __shared__ int s_item;
+    for (int i = threadIdx.x; i < NY; i += blockDim.x) twy[i] = a.twy[i];
+    for (int i = threadIdx.x; i < NZ; i += blockDim.x) twz[i] = a.twz[i];
+    const int lane = threadIdx.x % DTX, r = threadIdx.x / DTX;
+    const int P = a.nb * a.ng;
+    int* cntA = a.cnt;
+    int* cntB = cntA + (int64_t)P * a.CG;
+    int* cntC = cntB + (int64_t)P * a.CG;
+    int* next = cntC + P;
+    int* err = next + 1;
+    const int cg_last = a.C - (a.ng - 1) * a.CG;
+    const int per_full = a.CG * (NZ + NY) + NZ;
+    const int per_last = cg_last * (NZ + NY) + NZ;
+    const int per_blk = (a.ng - 1) * per_full + per_last;
+    const int total = a.nb * per_blk;
+    const int64_t plane = (int64_t)NY * a.nx, vol = (int64_t)NZ * plane;
+    if (threadIdx.x == 0) s_item = atomicAdd(next, 1);
+    __syncthreads();
+    for (;;) {
+        const int item = s_item;
+        // block-uniform stop test; the barrier also ends every read of s_item
+        if (__syncthreads_or(item >= total || (threadIdx.x == 0 && *(volatile int*)err))) break;
+        if (threadIdx.x == 0) s_item = atomicAdd(next, 1);   // claim the next one early
+        // ---- decode (x-block b, group g, kind, index)
+        const int b = item / per_blk;
+        int rr = item - b * per_blk;
+        const int g = min(rr / per_full, a.ng - 1);
+        rr -= g * per_full;
+        const int k = b * a.ng + g;
+        const int cg = (g == a.ng - 1) ? cg_last : a.CG;
+        const int c0 = g * a.CG;
+        const int x0 = b * DTX, col = x0 + lane;
+        const bool ok = col < a.nx;
+        float2* Wk = a.W + (k & 1) * a.slot;
+        if (rr < cg * NZ) {
+            // ---- A (c, z): y FFT of S_c x on plane z -> W[c][z][ky]
+            const int c = rr / NZ, z = rr - c * NZ;
+            if (k >= 2 && !df_wait(cntC + (k - 2), NZ, err)) break;
+            const float2* Sc = a.S + (int64_t)(c0 + c) * vol + (int64_t)z * plane;
+            const float2* xz = a.x + (int64_t)z * plane;
+            if (r < N2Y) {
+                float2 v[DN1];
+#pragma unroll
+                for (int m1 = 0; m1 < DN1; ++m1) {
+                    const int64_t o = (int64_t)(N2Y * m1 + r) * a.nx + col;
+                    v[m1] = ok ? cmul(__ldg(Sc + o), __ldg(xz + o)) : make_float2(0.f, 0.f);
+                }
+                fft4_phase1<DN1, N2Y, false>(v, r, twy);
+#pragma unroll
+                for (int k1 = 0; k1 < DN1; ++k1) Y[(k1 * N2Y + r) * DTX + lane] = v[k1];
+            }
+            __syncthreads();
+            if (r < DN1) {
+                float2 u[N2Y];
+#pragma unroll
+                for (int m2 = 0; m2 < N2Y; ++m2) u[m2] = Y[(r * N2Y + m2) * DTX + lane];
+                fft4_phase2<DN1, N2Y, false>(u, twy);
+                float2* Wz = Wk + ((int64_t)(c * NZ + z) * NY) * DTX + lane;
+#pragma unroll
+                for (int k2 = 0; k2 < N2Y; ++k2) __stcg(Wz + (r + DN1 * k2) * DTX, u[k2]);
+            }
+            df_signal(cntA + (int64_t)k * a.CG + c);
+        } else if (rr < cg * (NZ + NY)) {
+            // ---- B (c, ky): z FFT, mask, z IFFT of W[c][:, ky] in place
+            const int q = rr - cg * NZ;
+            const int c = q / NY, ky = q - c * NY;
+            if (!df_wait(cntA + (int64_t)k * a.CG + c, NZ, err)) break;
+            float2* Wl = Wk + ((int64_t)c * NZ * NY + ky) * DTX + lane;
+            constexpr int ZS = NY * DTX;
+            if (r < N2Z) {
+                float2 v[DN1];
+#pragma unroll
+                for (int m1 = 0; m1 < DN1; ++m1) v[m1] = __ldcg(Wl + (int64_t)(N2Z * m1 + r) * ZS);
+                fft4_phase1<DN1, N2Z, false>(v, r, twz);
+#pragma unroll
+                for (int k1 = 0; k1 < DN1; ++k1) Y[(k1 * N2Z + r) * DTX + lane] = v[k1];
+            }
+            __syncthreads();
+            float2 u[N2Z];
+            if (r < DN1) {
+#pragma unroll
+                for (int m2 = 0; m2 < N2Z; ++m2) u[m2] = Y[(r * N2Z + m2) * DTX + lane];
+                fft4_phase2<DN1, N2Z, false>(u, twz);
+#pragma unroll
+                for (int k2 = 0; k2 < N2Z; ++k2) u[k2] = cscale(u[k2], __ldg(a.mask_fo + (r + DN1 * k2) * NY + ky));
+                // inverse with the mirrored decomposition: length-N2Z DFT over
+                // k2, twiddle W_nz^(-m2 k1), then the length-16 DFT over k1
+                RegFft<N2Z, true>::run(u, twz, DN1);
+#pragma unroll
+                for (int m2 = 1; m2 < N2Z; ++m2) {
+                    float2 w = twz[m2 * r];
+                    w.y = -w.y;
+                    u[m2] = cmul(u[m2], w);
+                }
+            }
+            __syncthreads();   // every phase-2 read of Y is done
+            if (r < DN1) {
+#pragma unroll
+                for (int m2 = 0; m2 < N2Z; ++m2) Y[(r * N2Z + m2) * DTX + lane] = u[m2];
+            }
+            __syncthreads();
+            if (r < N2Z) {
+                float2 v[DN1];
+#pragma unroll
+                for (int k1 = 0; k1 < DN1; ++k1) v[k1] = Y[(k1 * N2Z + r) * DTX + lane];
+                RegFft<DN1, true>::run(v, twz, N2Z);
+#pragma unroll
+                for (int m1 = 0; m1 < DN1; ++m1) __stcg(Wl + (int64_t)(N2Z * m1 + r) * ZS, v[m1]);
+            }
+            df_signal(cntB + (int64_t)k * a.CG + c);
+        } else {
+            // ---- C (z): y IFFT, conj(S_c), sum over the group, partial sum
+            const int z = rr - cg * (NZ + NY);
+            float2 acc[N2Y];
+#pragma unroll
+            for (int k2 = 0; k2 < N2Y; ++k2) acc[k2] = make_float2(0.f, 0.f);
+            bool alive = true;
+            for (int c = 0; c < cg; ++c) {
+                if (!df_wait(cntB + (int64_t)k * a.CG + c, NY, err)) {
+                    alive = false;
+                    break;
+                }
+                const float2* Wz = Wk + ((int64_t)(c * NZ + z) * NY) * DTX + lane;
+                if (r < N2Y) {
+                    float2 v[DN1];
+#pragma unroll
+                    for (int m1 = 0; m1 < DN1; ++m1) v[m1] = __ldcg(Wz + (N2Y * m1 + r) * DTX);
+                    fft4_phase1<DN1, N2Y, true>(v, r, twy);
+#pragma unroll
+                    for (int k1 = 0; k1 < DN1; ++k1) Y[(k1 * N2Y + r) * DTX + lane] = v[k1];
+                }
+                __syncthreads();
+                if (r < DN1 && ok) {
+                    float2 u[N2Y];
+#pragma unroll
+                    for (int m2 = 0; m2 < N2Y; ++m2) u[m2] = Y[(r * N2Y + m2) * DTX + lane];
+                    fft4_phase2<DN1, N2Y, true>(u, twy);
+                    const float2* Sc = a.S + (int64_t)(c0 + c) * vol + (int64_t)z * plane + col;
+#pragma unroll
+                    for (int k2 = 0; k2 < N2Y; ++k2)
+                        acc[k2] = cadd(acc[k2], cmulc(__ldg(Sc + (int64_t)(r + DN1 * k2) * a.nx), u[k2]));
+                }
+                __syncthreads();   // Y is rewritten by the next coil
+            }
+            if (!alive) break;
+            if (g > 0 && !df_wait(cntC + (k - 1), NZ, err)) break;
+            if (r < DN1 && ok) {
+                float2* oz = a.out + (int64_t)z * plane + col;
+                const bool last = g == a.ng - 1;
+#pragma unroll
+                for (int k2 = 0; k2 < N2Y; ++k2) {
+                    const int64_t o = (int64_t)(r + DN1 * k2) * a.nx;
+                    float2 v = acc[k2];
+                    if (g > 0) v = cadd(v, __ldcg(oz + o));
+                    if (last) {
+                        v = cscale(v, a.scale);
+                        if (a.operand) v = cadd(v, cscale(__ldg(a.operand + (int64_t)z * plane + col + o), a.alpha));
+                    }
+                    __stcg(oz + o, v);
+                }
+            }
+            df_signal(cntC + k);
+        }
+        __syncthreads();   // s_item (the claim made at the top) is visible
+    }
+}
+
+template <int N2Y, int N2Z>
+int df_resident() {
+    auto fn = c3_dataflow_kernel<N2Y, N2Z>;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)Df<N2Y, N2Z>::SMEM) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    int per_sm = 0, dev = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, Df<N2Y, N2Z>::THREADS,
+                                                      Df<N2Y, N2Z>::SMEM) != cudaSuccess ||
+        cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return per_sm * sms;
+}
+
+// One block waits for a counter that nothing increments: the bounded wait
+// must give up after limit_ns and leave the error word set.
+__global__ void selftest_wait_kernel(int* words, unsigned long long limit_ns) {
+    df_wait(words, 1, words + 1, limit_ns);
+}
+
+}  // namespace
+
+extern thread_local int64_t g_launches;
+extern thread_local Profiler* g_profiler;
+
+#define PP_DF_CASES(X) X(8, 8) X(12, 8) X(16, 8) X(20, 8) X(24, 8) \
+    X(8, 12) X(12, 12) X(16, 12) X(8, 16) X(12, 16) X(16, 16)
+
+// Resident CTAs of the dataflow kernel for this plan's (ny, nz), 0 when the
+// kernel does not apply (a length without a register FFT).
+int c3df_prepare(const Plan& p) {
+    if (p.kind != PP_CARTESIAN || p.ndim != 3) return 0;
+    const int n2y = fft4_n2(p.ny), n2z = fft4_n2(p.nz);
+#define PP_DF_PREP(Y_, Z_) if (n2y == Y_ && n2z == Z_) return df_resident<Y_, Z_>();
+    PP_DF_CASES(PP_DF_PREP)
+#undef PP_DF_PREP
+    return 0;
+}
+
+size_t c3df_slot_elems(const Plan& p, int cg) { return (size_t)cg * p.nz * p.ny * DTX; }
+size_t c3df_counter_ints(const Plan& p, int cg) {
+    const int nb = (p.nx + DTX - 1) / DTX, ng = (p.C + cg - 1) / cg;
+    return (size_t)nb * ng * (2 * (size_t)cg + 1) + 2;
+}
+
+pp_status c3df_normal(const Plan& p, const float2* x, float2* out, float scale,
+                      const float2* operand, float alpha, cudaStream_t st) {
+    const int cg = std::max(1, std::min(p.c3df_cg, p.C));
+    DfArgs a;
+    a.x = x; a.S = p.sens; a.out = out; a.operand = operand; a.scale = scale; a.alpha = alpha;
+    a.mask_fo = p.mask_fo; a.twy = p.fy.tw; a.twz = p.fz.tw;
+    a.W = p.c3df_w; a.cnt = p.c3df_cnt;
+    a.nx = p.nx; a.C = p.C; a.CG = cg; a.ng = (p.C + cg - 1) / cg; a.nb = (p.nx + DTX - 1) / DTX;
+    a.slot = (int64_t)c3df_slot_elems(p, cg);
+    if ((size_t)2 * a.slot > p.c3df_w_elems || c3df_counter_ints(p, cg) > p.c3df_cnt_ints) {
+        set_error("c3df_normal: coil group %d exceeds the plan's dataflow buffers", cg);
+        return PP_ERR_INVALID_ARG;
+    }
+    PP_TRY_CUDA(cudaMemsetAsync(p.c3df_cnt, 0, sizeof(int) * c3df_counter_ints(p, cg), st));
+    const int n2y = fft4_n2(p.ny), n2z = fft4_n2(p.nz);
+    const int per_full = cg * (p.nz + p.ny) + p.nz;
+    const int64_t total = (int64_t)a.nb * a.ng * per_full;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(p.c3df_ctas, total));
+    cudaError_t e = cudaErrorInvalidValue;
+#define PP_DF_LAUNCH(Y_, Z_)                                                                    \
+    if (n2y == Y_ && n2z == Z_)                                                                 \
+        e = launch_ex(c3_dataflow_kernel<Y_, Z_>, dim3(grid), dim3(Df<Y_, Z_>::THREADS),        \
+                      Df<Y_, Z_>::SMEM, st, false, 0, a);
+    PP_DF_CASES(PP_DF_LAUNCH)
+#undef PP_DF_LAUNCH
+    if (e != cudaSuccess) return cuda_status(e, "c3_dataflow_kernel launch");
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_status(e, "c3_dataflow_kernel");
+    ++g_launches;
+    if (g_profiler) g_profiler->mark("c3_dataflow_kernel");
+    return PP_OK;
+}
+
+// The error word of the last dataflow launch (host, after a synchronisation):
+// nonzero when a wait ran out of time.
+pp_status c3df_check(const Plan& p, cudaStream_t st) {
+    if (!p.c3df_cnt) return PP_OK;
+    int errw = 0;
+    const int cg = std::max(1, std::min(p.c3df_cg, p.C));
+    const size_t off = c3df_counter_ints(p, cg) - 1;
+    PP_TRY_CUDA(cudaMemcpyAsync(&errw, p.c3df_cnt + off, sizeof(int), cudaMemcpyDeviceToHost, st));
+    PP_TRY_CUDA(cudaStreamSynchronize(st));
+    if (errw) {
+        set_error("3-D normal operator: a dependency wait ran past its time limit");
+        return PP_ERR_TIMEOUT;
+    }
+    return PP_OK;
+}
+
+}  // namespace pp
+
+namespace pp {
+
+pp_status selftest_wait(long long limit_ns, cudaStream_t st) {
+    int* words = nullptr;
+    PP_TRY_CUDA(cudaMalloc(&words, 2 * sizeof(int)));
+    pp_status rc = PP_OK;
+    int h[2] = {0, 0};
+    cudaError_t e = cudaMemsetAsync(words, 0, 2 * sizeof(int), st);
+    if (e == cudaSuccess) {
+        selftest_wait_kernel<<<1, 32, 0, st>>>(words, (unsigned long long)limit_ns);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, words, sizeof(h), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) rc = cuda_status(e, "selftest_wait_kernel");
+    cudaFree(words);
+    if (rc != PP_OK) return rc;
+    ++g_launches;
+    if (h[1]) {
+        set_error("pp_selftest_wait: the wait gave up after its limit (counter %d, expected 1)", h[0]);
+        return PP_ERR_TIMEOUT;
+    }
+    return PP_OK;
+}
+
+}  // namespace pp

@@ -185,6 +185,13 @@ struct Plan {
     int stencil_rb_grid[4] = {0, 0, 0, 0};   // persistent grid of kinds 2..5 (0: unavailable)
     int c3cl_clusters = 0;      // 3-D: resident 16-CTA clusters of the one-kernel operator, 4 columns
     int c3cl2_clusters = 0;     //      the same with 2 columns per task (0: n/a)
+    // 3-D dataflow operator (one persistent kernel per apply, pp_cart3d_df.cu)
+    int c3df_ctas = 0;          // resident CTAs (0: not available for this plan)
+    int c3df_cg = 4;            // coils per group
+    float2* c3df_w = nullptr;   // two phase slots
+    size_t c3df_w_elems = 0;
+    int* c3df_cnt = nullptr;    // completion counters, claim counter, error word
+    size_t c3df_cnt_ints = 0;
     int tune_c3 = 0;            // 3-D: 0 = three passes per coil, 1 / 2 = one-kernel cluster operator
                                 //      with 4 / 2 columns per task
     int pdl = 1;                // programmatic dependent launch in the solve's kernel chain
@@ -250,6 +257,13 @@ pp_status launch_gtg_stencil(const Plan& p, const float2* grid_in, float2* grid_
 pp_status prepare_gtg_stencil(Plan& p);
 pp_status prepare_cart4();
 int c3cl_prepare(const Plan& p, int xb);
+int c3df_prepare(const Plan& p);
+size_t c3df_slot_elems(const Plan& p, int cg);
+size_t c3df_counter_ints(const Plan& p, int cg);
+pp_status c3df_normal(const Plan& p, const float2* x, float2* out, float scale,
+                      const float2* operand, float alpha, cudaStream_t st);
+pp_status c3df_check(const Plan& p, cudaStream_t st);
+pp_status selftest_wait(long long limit_ns, cudaStream_t st);
 pp_status c3cl_normal(const Plan& p, int xb, const float2* x, float2* out, float scale,
                       const float2* operand, float alpha, cudaStream_t st);
 bool ci_supported(const Plan& p);

@@ -166,9 +166,10 @@ def test_batched_five_uneven_slices_50_iterations(pp):
 
 def test_cart3d_full_volume_one_apply_sampled_columns(pp):
     # the whole 256x256x128 volume with 32 coils (2 GiB of maps): one
-    # normal apply, then x columns checked against the oracle computed
-    # column by column (readout cancellation, pinned against the full-FFT
-    # definition in the CPU tests)
+    # normal apply with the launch shape the plan picked and with every
+    # other operator variant, then x columns checked against the oracle
+    # computed column by column (readout cancellation, pinned against the
+    # full-FFT definition in the CPU tests)
     cfg = synth.CONFIGS["cart3d_256x256x128_c32"]
     shape, C, seed = cfg["shape"], cfg["coils"], cfg["seed"]
     sens = synth.coil_maps(shape, C, seed)
@@ -179,14 +180,19 @@ def test_cart3d_full_volume_one_apply_sampled_columns(pp):
     try:
         L = 3.7
         pp.pp_plan_set_scale(plan, L)
-        out = empty(shape)
-        pp.pp_normal_apply(plan, dev(x), out)
         cols = [0, 1, 63, 128, 200, 255]
-        got = host(out)[..., cols]
         ref = O.cart_normal_columns(x, sens, mask, cols) / L
-        assert rel(got, ref) <= TOL_APPLY
-        for j in range(len(cols)):
-            assert rel(got[..., j], ref[..., j]) <= TOL_APPLY, cols[j]
+        xd = dev(x)
+        tuned = pp.pp_plan_tuning(plan)
+        for tuning in [tuned, (3, 0, 2), (3, 0, 4), (3, 0, 8), (1, 0, 8)]:
+            pp.pp_plan_set_tuning(plan, *tuning)
+            out = empty(shape)
+            pp.pp_normal_apply(plan, xd, out)
+            got = host(out)[..., cols]
+            assert rel(got, ref) <= TOL_APPLY, tuning
+            for j in range(len(cols)):
+                assert rel(got[..., j], ref[..., j]) <= TOL_APPLY, (tuning, cols[j])
+            del out
     finally:
         plan.destroy()
 

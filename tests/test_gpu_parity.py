@@ -204,6 +204,70 @@ def test_cart3d_cluster_operator(pp, case):
         plan.destroy()
 
 
+DF_CASES = [((128, 256, 40), 5), ((128, 128, 8), 3), ((192, 192, 20), 9), ((128, 384, 16), 2),
+            ((256, 128, 36), 7), ((128, 256, 4), 1)]
+
+
+@pytest.mark.parametrize("case", range(len(DF_CASES)), ids=["128x256x40_c5", "128x128x8_c3",
+                                                           "192x192x20_c9", "128x384x16_c2",
+                                                           "256x128x36_c7", "128x256x4_c1"])
+def test_cart3d_dataflow_operator(pp, case):
+    # the 3-D persistent dataflow operator (row variant 3) for every coil
+    # group size 1..8: full and ragged x-blocks (nx not a multiple of 16),
+    # ragged last coil groups, nz and ny of 128 ... 384, and the Horner axpy
+    # epilogue; against the oracle
+    shape, C = DF_CASES[case]
+    sens = synth.coil_maps(shape, C, 520 + case)
+    mask = synth.poisson_disc_mask(shape, 4, 8, 520 + case)
+    plan = pp.pp_plan_create(shape, C, dev(sens), mask=mask, seed=2, power_iters=0)
+    try:
+        x = synth.crandn(shape, 17)
+        op = synth.crandn(shape, 18)
+        L = 1.3
+        pp.pp_plan_set_scale(plan, L)
+        nrm = lambda v: O.cart_normal(v, sens, mask) / L
+        ref = nrm(x)
+        c = [float(v) for v in O.poly_coeffs_l2(2)]
+        refp = O.horner_apply(c, nrm, op.astype(np.complex128))
+        for cg in sorted({1, 2, 3, 4, 8, min(C, 8)}):
+            pp.pp_plan_set_tuning(plan, 3, 0, cg)
+            assert pp.pp_plan_tuning(plan) == (3, 0, cg)
+            out = empty(shape)
+            pp.pp_normal_apply(plan, dev(x), out)
+            assert rel(host(out), ref) <= TOL_APPLY, cg
+            out = empty(shape)
+            pp.pp_poly_apply(plan, c, 2, dev(op), out)
+            assert rel(host(out), refp) <= TOL_APPLY, cg
+        # the bounded waits never ran out: a synchronising call reports no timeout
+        pp.pp_plan_mu(plan, 2, 1)
+    finally:
+        plan.destroy()
+
+
+def test_bounded_wait_gives_up_and_the_device_stays_usable(pp):
+    # a block waits on a counter nothing increments: the wait must give up
+    # after its limit (50 ms), the call must report PP_ERR_TIMEOUT, and the
+    # device must still run a normal apply correctly afterwards
+    import time
+    t0 = time.perf_counter()
+    with pytest.raises(pp.PPError) as e:
+        pp.pp_selftest_wait(50_000_000)
+    assert e.value.status == 6
+    assert time.perf_counter() - t0 < 5.0
+    shape, C = (128, 128, 8), 2
+    sens = synth.coil_maps(shape, C, 3)
+    mask = synth.poisson_disc_mask(shape, 4, 8, 3)
+    plan = pp.pp_plan_create(shape, C, dev(sens), mask=mask, power_iters=0)
+    try:
+        pp.pp_plan_set_tuning(plan, 3, 0, 2)
+        x = synth.crandn(shape, 4)
+        out = empty(shape)
+        pp.pp_normal_apply(plan, dev(x), out)
+        assert rel(host(out), O.cart_normal(x, sens, mask)) <= TOL_APPLY
+    finally:
+        plan.destroy()
+
+
 C2_CASES = [((128, 128), 8), ((192, 256), 3), ((384, 128), 5), ((256, 36), 16)]
 
 
