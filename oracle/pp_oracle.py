@@ -460,6 +460,58 @@ def wavelet_prox(wavelet):
 
 
 # --------------------------------------------------------------------------
+# Locally-low-rank regulariser (the LLR term of the MRF experiment, Sec. 5.3,
+# block size 8 x 8 x 8): LLR(x) = sum over blocks of the nuclear norm of the
+# block's Casorati matrix (one row per voxel, one column per coefficient
+# image).  Its prox is singular-value soft thresholding block by block.
+# Reading: non-overlapping blocks tiling the volume after a circular shift
+# (the shift lets a caller move the block grid between iterations).
+# --------------------------------------------------------------------------
+
+
+def llr_blocks(x, block, shift=None):
+    """Casorati matrices of the blocks: returns [nblocks, block^ndim, T] for
+    x of shape [T, *img] (every image axis a multiple of `block`), after
+    rolling the image axes by -shift, and the inverse map."""
+    x = np.asarray(x, dtype=np.complex128)
+    T, img = x.shape[0], x.shape[1:]
+    nd = len(img)
+    sh = [0] * nd if shift is None else [int(v) for v in shift][:nd]
+    xr = np.roll(x, [-v for v in sh], axis=tuple(range(1, nd + 1)))
+    nb = [n // block for n in img]
+    # [T, nb0, b, nb1, b, ...] -> [nb0, nb1, ..., b, b, ..., T]
+    shp = [T]
+    for n in nb:
+        shp += [n, block]
+    y = xr.reshape(shp)
+    perm = [1 + 2 * i for i in range(nd)] + [2 + 2 * i for i in range(nd)] + [0]
+    M = np.transpose(y, perm).reshape(int(np.prod(nb)), block ** nd, T)
+
+    def back(Mb):
+        z = Mb.reshape(nb + [block] * nd + [T])
+        z = np.transpose(z, np.argsort(perm)).reshape(x.shape)
+        return np.roll(z, sh, axis=tuple(range(1, nd + 1)))
+    return M, back
+
+
+def prox_llr(x, lam, block=8, shift=None):
+    """prox_{lam LLR}(x): for every block's Casorati matrix M = U S V^H (SVD),
+    U max(S - lam, 0) V^H."""
+    M, back = llr_blocks(x, block, shift)
+    out = np.empty_like(M)
+    for i in range(M.shape[0]):
+        U, sv, Vh = np.linalg.svd(M[i], full_matrices=False)
+        out[i] = (U * np.maximum(sv - lam, 0.0)) @ Vh
+    return back(out)
+
+
+def llr_norm(x, block=8, shift=None):
+    """LLR(x): the sum of the blocks' nuclear norms."""
+    M, _ = llr_blocks(x, block, shift)
+    return float(sum(np.linalg.svd(m, compute_uv=False).sum() for m in M))
+
+
+# --------------------------------------------------------------------------
 # Polynomial preconditioner: Eq. "l2cost" and the recursion of Listing "pcode"
 # --------------------------------------------------------------------------
 
