@@ -133,12 +133,16 @@ def cart3d(args, pp, rank, world, local):
     prox_ms, _ = _timed(prox_run, 1, dev, local)
     prox_bytes = 16.0 * n
     prox_gbs = prox_bytes * prox_calls / (prox_ms / 1e3) / 1e9
+    tuning = pp.pp_plan_tuning(plan)
     plan.destroy()
     return _base(args, world, "A^H A applies/s (3-D Cartesian normal operator)", "applies/s",
                  bench.job_throughput(args.steps, world, ms / 1e3), ms / args.steps,
                  {"workload": "cart3d_256x256x128_c32", "image": list(shape), "coils": C, "R": c["R"],
                   "l2": "inputs larger than L2 (2 GiB of coil maps) and flushed between steps",
-                  "input_generation_s": gen_s}, clk,
+                  "input_generation_s": gen_s,
+                  "tuning": {"row_variant": tuning[0], "coils_per_group": tuning[2],
+                             "meaning": "3 = persistent dataflow kernel, 16/-16 = cluster kernel, "
+                                        "1 = three passes per coil"}}, clk,
                  {"roofline": {"bound": "hbm", "kernel": "whole normal apply", "achieved": gbs,
                                "peak": peak, "unit": "GB/s", "frac": gbs / peak,
                                "traffic": bench.ncu_traffic("cart3d_normal", "ncu_traffic_3d.json"),
@@ -275,6 +279,8 @@ def apply_only(args, pp, local):
     mask = (synth.line_mask(shape, c["R"], c["acs"], c["seed"]) if len(shape) == 2 else
             synth.poisson_disc_mask(shape, c["R"], c["calib"], c["seed"]))
     plan = pp.pp_plan_create(shape, C, sens, mask=mask, seed=c["seed"], power_iters=0)
+    if args.tuning:   # force a launch shape (row_variant,stencil_kind,stencil_coils)
+        pp.pp_plan_set_tuning(plan, *[int(v) for v in args.tuning.split(",")])
     x = torch.from_numpy(synth.crandn(shape, 3)).to(dev)
     y = torch.empty_like(x)
     for _ in range(K):

@@ -261,6 +261,23 @@ pp_status pp_prox_l1_haar(pp_dims dims, int levels, float lambda, const pp_c64* 
 pp_status pp_prox_l1_db4(pp_dims dims, int levels, float lambda, const pp_c64* in, pp_c64* out,
                          pp_stream stream);
 
+/* prox_{lambda LLR}(in) for the locally-low-rank regulariser of the MRF
+ * experiment (Sec. 5.3; Tamir et al.): LLR(x) = the sum over blocks of the
+ * nuclear norm of the block's Casorati matrix, one row per voxel of the
+ * block and one column per coefficient image.  The prox replaces each
+ * block's matrix M = U S V^H by U max(S - lambda, 0) V^H.
+ *   dims    2-D or 3-D image size of ONE coefficient image; every axis a
+ *           multiple of `block`.
+ *   T       coefficient images, 1..8.
+ *   block   block edge: 4 or 8 (3-D: 64 or 512 voxels), or 16 in 2-D.
+ *   shift   host int[3] (x, y, z) or NULL: the block grid starts at voxel
+ *           shift (circularly), so a caller can move it between iterations.
+ *   in/out  device [T][nz][ny][nx] complex64; out may equal in.
+ * FP32 one-sided Jacobi SVD per block (one thread block each); else
+ * PP_ERR_UNSUPPORTED. */
+pp_status pp_prox_llr(pp_dims dims, int T, int block, const int* shift, float lambda,
+                      const pp_c64* in, pp_c64* out, pp_stream stream);
+
 /* Optional solve inputs/outputs.
  *  history  host double [iters][3] or NULL.  Row k receives, as FP64
  *           reductions on the device, ||y_{k+1} - y_k||^2, ||y_{k+1}||^2 and

@@ -107,6 +107,8 @@ _SIGS = {
                                                   ctypes.POINTER(ctypes.c_double),
                                                   ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
     "pp_selftest_wait": (ctypes.c_int, [ctypes.c_int64, ctypes.c_void_p]),
+    "pp_prox_llr": (ctypes.c_int, [pp_dims, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_float,
+                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "pp_last_error": (ctypes.c_char_p, []),
 }
 
@@ -360,6 +362,21 @@ def pp_prox_l1_db4(shape, levels: int, lam: float, x_in, x_out, stream=None):
     _numel(x_out, int(np.prod(shape)), "out")
     _check(lib().pp_prox_l1_db4(_dims(shape), int(levels), float(lam), _dev_ptr(x_in, "in"),
                                 _dev_ptr(x_out, "out"), _stream(stream)), "pp_prox_l1_db4")
+
+
+def pp_prox_llr(shape, T: int, block: int, lam: float, x_in, x_out, shift=None, stream=None):
+    """Locally-low-rank prox of T coefficient images of `shape` ([ny, nx] or
+    [nz, ny, nx]); x_in/x_out are complex64 CUDA tensors of T * prod(shape)
+    elements; shift (x, y, z) moves the block grid circularly."""
+    n = int(T) * int(np.prod(shape))
+    _numel(x_in, n, "in")
+    _numel(x_out, n, "out")
+    sh = None
+    if shift is not None:
+        sv = [int(v) for v in shift] + [0] * (3 - len(shift))
+        sh = (ctypes.c_int * 3)(*sv[:3])
+    _check(lib().pp_prox_llr(_dims(shape), int(T), int(block), sh, float(lam), _dev_ptr(x_in, "in"),
+                             _dev_ptr(x_out, "out"), _stream(stream)), "pp_prox_llr")
 
 
 WAVELETS = {"haar": 0, "db4": 1}

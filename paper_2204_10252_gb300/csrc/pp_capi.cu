@@ -1612,6 +1612,24 @@ pp_status pp_plan_mu(pp_plan* plan, int iters, uint64_t seed, double* mu, pp_str
     return mu_iteration(plan->impl, seed, iters, mu, (cudaStream_t)stream);
 }
 
+pp_status pp_prox_llr(pp_dims dims, int T, int block, const int* shift, float lambda,
+                      const pp_c64* in, pp_c64* out, pp_stream stream) {
+    if (!in || !out || !(lambda >= 0.f) || !isfinite(lambda) || (dims.ndim != 2 && dims.ndim != 3)) {
+        set_error("pp_prox_llr: bad argument");
+        return PP_ERR_INVALID_ARG;
+    }
+    const int nz = dims.ndim == 3 ? dims.n[2] : 1;
+    if (T < 1 || T > 8 || !(block == 4 || block == 8 || (block == 16 && dims.ndim == 2)) ||
+        dims.n[0] < 1 || dims.n[1] < 1 || nz < 1 || dims.n[0] % block || dims.n[1] % block ||
+        (dims.ndim == 3 && nz % block)) {
+        set_error("pp_prox_llr: need 1 <= T <= 8, block 4 or 8 (16 in 2-D) dividing every axis");
+        return PP_ERR_UNSUPPORTED;
+    }
+    return launch_prox_llr(dims.ndim, dims.n[0], dims.n[1], nz, T, block, shift, lambda,
+                           reinterpret_cast<const float2*>(in), reinterpret_cast<float2*>(out),
+                           (cudaStream_t)stream);
+}
+
 pp_status pp_selftest_wait(int64_t limit_ns, pp_stream stream) {
     if (limit_ns < 1000000 || limit_ns > 1000000000) {
         set_error("pp_selftest_wait: limit must be 1 ms .. 1 s");

@@ -264,6 +264,8 @@ pp_status c3df_normal(const Plan& p, const float2* x, float2* out, float scale,
                       const float2* operand, float alpha, cudaStream_t st);
 pp_status c3df_check(const Plan& p, cudaStream_t st);
 pp_status selftest_wait(long long limit_ns, cudaStream_t st);
+pp_status launch_prox_llr(int ndim, int nx, int ny, int nz, int T, int block, const int* shift,
+                          float lambda, const float2* in, float2* out, cudaStream_t st);
 pp_status c3cl_normal(const Plan& p, int xb, const float2* x, float2* out, float scale,
                       const float2* operand, float alpha, cudaStream_t st);
 bool ci_supported(const Plan& p);
