@@ -472,11 +472,12 @@ def wavelet_prox(wavelet):
 def llr_blocks(x, block, shift=None):
     """Casorati matrices of the blocks: returns [nblocks, block^ndim, T] for
     x of shape [T, *img] (every image axis a multiple of `block`), after
-    rolling the image axes by -shift, and the inverse map."""
+    rolling the image by -shift, and the inverse map.  shift is given in
+    (x, y[, z]) order (readout axis first), as in the library's call."""
     x = np.asarray(x, dtype=np.complex128)
     T, img = x.shape[0], x.shape[1:]
     nd = len(img)
-    sh = [0] * nd if shift is None else [int(v) for v in shift][:nd]
+    sh = [0] * nd if shift is None else list(reversed([int(v) for v in shift][:nd]))
     xr = np.roll(x, [-v for v in sh], axis=tuple(range(1, nd + 1)))
     nb = [n // block for n in img]
     # [T, nb0, b, nb1, b, ...] -> [nb0, nb1, ..., b, b, ..., T]
@@ -671,6 +672,66 @@ def pfista(normal, adjoint, b, lam, coeffs, iters, L, levels=2, normalize_b=True
         if history is not None:
             history.append(y.copy())
     return y
+
+
+def pfista_prox(normal, adjoint, b, v, sigma, lam, coeffs, iters, L, levels=2, momentum=True,
+                history=None, wavelet="haar"):
+    """Algorithm "pfista" for min_x 1/2 ||A x - b||^2 + (sigma/2) ||x - v||^2
+    + lam ||W x||_1, in the problem's own units (b not normalised).  This is
+    prox_{rho f}(v) with sigma = 1/rho for f(x) = 1/2 ||A x - b||^2
+    + lam ||W x||_1, the subproblem of consensus ADMM (Algorithm "cadmm",
+    Sec. 5.3).  The smooth part's Hessian is N' = A^H A + sigma I with
+    Lipschitz constant L' = L + sigma; the iteration of Algorithm "pfista"
+    runs with step 1/L' on N_hat' = N'/L', the gradient's constant term
+    (A^H b + sigma v)/L' and the threshold lam/L'.  b or v may be None (0)."""
+    Lp = L + sigma
+    shape = None
+    rhs = 0.0
+    if b is not None:
+        rhs = adjoint(np.asarray(b, dtype=np.complex128))
+        shape = rhs.shape
+    if v is not None:
+        rhs = rhs + sigma * np.asarray(v, dtype=np.complex128)
+        shape = np.shape(v)
+    rhs = np.broadcast_to(np.asarray(rhs, dtype=np.complex128), shape) / Lp
+
+    def nhat(x):
+        return (normal(x) + sigma * x) / Lp
+
+    y = np.zeros(shape, dtype=np.complex128)
+    z = np.zeros(shape, dtype=np.complex128)
+    for k in range(iters):
+        g = nhat(z) - rhs
+        u = g if coeffs is None else horner_apply(coeffs, nhat, g)
+        y_new = wavelet_prox(wavelet)(z - u, lam / Lp, levels)
+        beta = k / (k + 3.0) if momentum else 0.0
+        z = y_new + beta * (y_new - y)
+        y = y_new
+        if history is not None:
+            history.append(y.copy())
+    return y
+
+
+def consensus_admm(prox_list, shape, iters, history=None):
+    """Global consensus ADMM (Algorithm "cadmm", Sec. 5.3) for
+    min_x sum_i f_i(x): prox_list[i](v) returns prox_{rho f_i}(v).
+    x_bar = x^i = u^i = 0; for k = 0..iters-1:
+        x^i     = prox_{rho f_i}(x_bar - u^i)
+        x_bar   = (1/N) sum_i x^i
+        u^i     = u^i + x^i - x_bar        (reading of the update's stray
+                                            superscript on x_bar)
+    Returns x_bar; `history`, if a list, receives every x_bar."""
+    n = len(prox_list)
+    xbar = np.zeros(shape, dtype=np.complex128)
+    u = [np.zeros(shape, dtype=np.complex128) for _ in range(n)]
+    for _ in range(iters):
+        xs = [prox_list[i](xbar - u[i]) for i in range(n)]
+        xbar = sum(xs) / n
+        for i in range(n):
+            u[i] = u[i] + xs[i] - xbar
+        if history is not None:
+            history.append(xbar.copy())
+    return xbar
 
 
 # --------------------------------------------------------------------------

@@ -583,14 +583,16 @@ static pp_status tune_noncartesian(Plan& p, cudaStream_t st) {
 // plan's buffers (two rounds of 3 applies after one warm-up); the fastest is
 // kept.
 static pp_status tune_cart3d(Plan& p, cudaStream_t st) {
-    std::vector<std::pair<int, int>> cand = {{0, 0}};
-    if (p.c3cl_clusters > 0) cand.push_back({1, 0});
-    if (p.c3cl2_clusters > 0) cand.push_back({2, 0});
-    if (p.c3df_ctas > 0)
-        for (int cgc : {2, 4, 8})
-            if (cgc <= std::max(2, p.C) && (cgc == 2 || cgc <= p.C) &&
-                2 * c3df_slot_elems(p, cgc) <= p.c3df_w_elems)
-                cand.push_back({3, cgc});
+    struct Cand { int kind, cg, hi; };
+    std::vector<Cand> cand = {{0, 0, 0}};
+    if (p.c3cl_clusters > 0) cand.push_back({1, 0, 0});
+    if (p.c3cl2_clusters > 0) cand.push_back({2, 0, 0});
+    for (int hi = 0; hi < 2; ++hi)
+        if ((hi ? p.c3df_ctas_hi : p.c3df_ctas) > 0)
+            for (int cgc : {2, 4, 8})
+                if (cgc <= std::max(2, p.C) && (cgc == 2 || cgc <= p.C) &&
+                    2 * c3df_slot_elems(p, cgc) <= p.c3df_w_elems)
+                    cand.push_back({3, cgc, hi});
     if (cand.size() == 1) return PP_OK;
     cudaEvent_t e0, e1;
     PP_TRY_CUDA(cudaEventCreate(&e0));
@@ -599,8 +601,11 @@ static pp_status tune_cart3d(Plan& p, cudaStream_t st) {
     std::vector<float> best(cand.size(), 1e30f);
     for (int round = 0; round < 2; ++round)
         for (size_t i = 0; i < cand.size(); ++i) {
-            p.tune_c3 = cand[i].first;
-            if (cand[i].second) p.c3df_cg = cand[i].second;
+            p.tune_c3 = cand[i].kind;
+            if (cand[i].cg) {
+                p.c3df_cg = cand[i].cg;
+                p.c3df_hi = cand[i].hi;
+            }
             if (best[i] > 1.5e30f) continue;
             if (!launches_ok([&]() { return normal_into(p, p.v, p.t, 1.f, nullptr, 0.f, st); }) ||
                 (p.tune_c3 == 3 && c3df_check(p, st) != PP_OK)) {
@@ -617,8 +622,11 @@ static pp_status tune_cart3d(Plan& p, cudaStream_t st) {
             best[i] = std::min(best[i], ms);
         }
     const size_t bi = std::min_element(best.begin(), best.end()) - best.begin();
-    p.tune_c3 = cand[bi].first;
-    if (cand[bi].second) p.c3df_cg = cand[bi].second;
+    p.tune_c3 = cand[bi].kind;
+    if (cand[bi].cg) {
+        p.c3df_cg = cand[bi].cg;
+        p.c3df_hi = cand[bi].hi;
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return PP_OK;
@@ -1450,7 +1458,8 @@ pp_status pp_plan_create(pp_plan** out, pp_dims dims, int coils, const pp_c64* s
     if (rc == PP_OK && p.kind == PP_CARTESIAN && p.ndim == 3) {
         p.c3cl_clusters = c3cl_prepare(p, 4);
         p.c3cl2_clusters = c3cl_prepare(p, 2);
-        p.c3df_ctas = c3df_prepare(p);
+        p.c3df_ctas = c3df_prepare(p, 0);
+        p.c3df_ctas_hi = c3df_prepare(p, 1);
         if (p.c3df_ctas > 0) {
             // two phase slots for up to 8 coils per group; counters for 1
             p.c3df_w_elems = 2 * c3df_slot_elems(p, std::min(8, std::max(2, p.C)));
@@ -1526,7 +1535,11 @@ pp_status pp_plan_tuning(const pp_plan* plan, int* row_ifft_variant, int* stenci
         else
             *row_ifft_variant = p.tune_rows_adj_cl ? p.tune_rows_adj_cl : 1;
     }
-    if (stencil_kind) *stencil_kind = plan->impl.tune_stencil_kind;
+    if (stencil_kind) {
+        const Plan& p = plan->impl;
+        *stencil_kind = (p.kind == PP_CARTESIAN && p.ndim == 3 && p.tune_c3 == 3) ? p.c3df_hi
+                                                                                  : p.tune_stencil_kind;
+    }
     if (stencil_coils) {
         const Plan& p = plan->impl;
         *stencil_coils = (p.kind == PP_CARTESIAN && p.ndim == 3 && p.tune_c3 == 3)
@@ -1554,8 +1567,14 @@ pp_status pp_plan_set_tuning(pp_plan* plan, int row_ifft_variant, int stencil_ki
                       "Cartesian plan with register-FFT lengths ny, nz and at most 8 coils per group");
             return PP_ERR_UNSUPPORTED;
         }
+        if (stencil_kind > 1 || (stencil_kind == 1 && p.c3df_ctas_hi <= 0)) {
+            set_error("pp_plan_set_tuning: the 3-D dataflow operator takes stencil kind 0 (two "
+                      "blocks per SM) or 1 (three)");
+            return PP_ERR_UNSUPPORTED;
+        }
         p.tune_c3 = 3;
         p.c3df_cg = stencil_coils;
+        p.c3df_hi = stencil_kind;
         p.gkey.clear();
         return PP_OK;
     }

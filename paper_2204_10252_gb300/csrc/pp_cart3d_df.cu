@@ -46,7 +46,10 @@ template <int N2Y, int N2Z> struct Df {
     static constexpr int NY = 16 * N2Y, NZ = 16 * N2Z;
     static constexpr int RMAX = (N2Y > N2Z ? (N2Y > DN1 ? N2Y : DN1) : (N2Z > DN1 ? N2Z : DN1));
     static constexpr int THREADS = DTX * RMAX;
-    static constexpr int YE = DN1 * (N2Y > N2Z ? N2Y : N2Z) * DTX;   // transpose buffer elements
+    // ky lines per B item: as many as the thread rows hold in the z
+    // transforms' first phase (N2Z rows each), so no row idles there
+    static constexpr int LPB = (RMAX % N2Z == 0 && NY % (RMAX / N2Z) == 0) ? RMAX / N2Z : 1;
+    static constexpr int YE = DN1 * RMAX * DTX;   // transpose buffer elements
     static constexpr size_t SMEM = sizeof(float2) * (YE + NY + NZ);
 };
 
@@ -111,10 +114,11 @@ __device__ __forceinline__ void df_signal(int* cnt) {
     if (threadIdx.x == 0) red_release_add(cnt, 1);
 }
 
-template <int N2Y, int N2Z>
-__global__ void __launch_bounds__(Df<N2Y, N2Z>::THREADS, Df<N2Y, N2Z>::THREADS <= 256 ? 2 : 1)
+template <int N2Y, int N2Z, int MB>
+__global__ void __launch_bounds__(Df<N2Y, N2Z>::THREADS, MB)
 c3_dataflow_kernel(DfArgs a) {
-    constexpr int NY = Df<N2Y, N2Z>::NY, NZ = Df<N2Y, N2Z>::NZ;
+    constexpr int NY = Df<N2Y, N2Z>::NY, NZ = Df<N2Y, N2Z>::NZ, LPB = Df<N2Y, N2Z>::LPB;
+    constexpr int NBI = NY / LPB;   // B items per coil
     extern __shared__ float4 df_sm4[];
     float2* Y = reinterpret_cast<float2*>(df_sm4);
     float2* twy = Y + Df<N2Y, N2Z>::YE;
@@ -130,8 +134,8 @@ c3_dataflow_kernel(DfArgs a) {
     int* next = cntC + P;
     int* err = next + 1;
     const int cg_last = a.C - (a.ng - 1) * a.CG;
-    const int per_full = a.CG * (NZ + NY) + NZ;
-    const int per_last = cg_last * (NZ + NY) + NZ;
+    const int per_full = a.CG * (NZ + NBI) + NZ;
+    const int per_last = cg_last * (NZ + NBI) + NZ;
     const int per_blk = (a.ng - 1) * per_full + per_last;
     const int total = a.nb * per_blk;
     const int64_t plane = (int64_t)NY * a.nx, vol = (int64_t)NZ * plane;
@@ -181,57 +185,66 @@ c3_dataflow_kernel(DfArgs a) {
                 for (int k2 = 0; k2 < N2Y; ++k2) __stcg(Wz + (r + DN1 * k2) * DTX, u[k2]);
             }
             df_signal(cntA + (int64_t)k * a.CG + c);
-        } else if (rr < cg * (NZ + NY)) {
-            // ---- B (c, ky): z FFT, mask, z IFFT of W[c][:, ky] in place
+        } else if (rr < cg * (NZ + NBI)) {
+            // ---- B (c, LPB ky lines): z FFT, mask, z IFFT of W[c][:, ky] in place;
+            // thread row r < LPB N2Z takes line r / N2Z in the first and last
+            // phase, rows r < 16 loop over the lines in the middle one
             const int q = rr - cg * NZ;
-            const int c = q / NY, ky = q - c * NY;
+            const int c = q / NBI, ky0 = (q - c * NBI) * LPB;
             if (!df_wait(cntA + (int64_t)k * a.CG + c, NZ, err)) break;
-            float2* Wl = Wk + ((int64_t)c * NZ * NY + ky) * DTX + lane;
             constexpr int ZS = NY * DTX;
-            if (r < N2Z) {
+            constexpr int YL = DN1 * N2Z * DTX;   // one line's transpose block
+            const int l1 = r / N2Z, m2r = r - l1 * N2Z;
+            float2* Wc = Wk + (int64_t)c * NZ * NY * DTX + lane;
+            if (r < LPB * N2Z) {
+                const float2* Wl = Wc + (ky0 + l1) * DTX;
                 float2 v[DN1];
 #pragma unroll
-                for (int m1 = 0; m1 < DN1; ++m1) v[m1] = __ldcg(Wl + (int64_t)(N2Z * m1 + r) * ZS);
-                fft4_phase1<DN1, N2Z, false>(v, r, twz);
+                for (int m1 = 0; m1 < DN1; ++m1) v[m1] = __ldcg(Wl + (int64_t)(N2Z * m1 + m2r) * ZS);
+                fft4_phase1<DN1, N2Z, false>(v, m2r, twz);
 #pragma unroll
-                for (int k1 = 0; k1 < DN1; ++k1) Y[(k1 * N2Z + r) * DTX + lane] = v[k1];
+                for (int k1 = 0; k1 < DN1; ++k1) Y[l1 * YL + (k1 * N2Z + m2r) * DTX + lane] = v[k1];
             }
             __syncthreads();
-            float2 u[N2Z];
             if (r < DN1) {
+#pragma unroll 1
+                for (int l = 0; l < LPB; ++l) {
+                    float2 u[N2Z];
 #pragma unroll
-                for (int m2 = 0; m2 < N2Z; ++m2) u[m2] = Y[(r * N2Z + m2) * DTX + lane];
-                fft4_phase2<DN1, N2Z, false>(u, twz);
+                    for (int m2 = 0; m2 < N2Z; ++m2) u[m2] = Y[l * YL + (r * N2Z + m2) * DTX + lane];
+                    fft4_phase2<DN1, N2Z, false>(u, twz);
+                    const int ky = ky0 + l;
 #pragma unroll
-                for (int k2 = 0; k2 < N2Z; ++k2) u[k2] = cscale(u[k2], __ldg(a.mask_fo + (r + DN1 * k2) * NY + ky));
-                // inverse with the mirrored decomposition: length-N2Z DFT over
-                // k2, twiddle W_nz^(-m2 k1), then the length-16 DFT over k1
-                RegFft<N2Z, true>::run(u, twz, DN1);
+                    for (int k2 = 0; k2 < N2Z; ++k2)
+                        u[k2] = cscale(u[k2], __ldg(a.mask_fo + (r + DN1 * k2) * NY + ky));
+                    // inverse with the mirrored decomposition: length-N2Z DFT over
+                    // k2, twiddle W_nz^(-m2 k1), then the length-16 DFT over k1;
+                    // this thread reads and writes only its own row r of the block
+                    RegFft<N2Z, true>::run(u, twz, DN1);
 #pragma unroll
-                for (int m2 = 1; m2 < N2Z; ++m2) {
-                    float2 w = twz[m2 * r];
-                    w.y = -w.y;
-                    u[m2] = cmul(u[m2], w);
+                    for (int m2 = 1; m2 < N2Z; ++m2) {
+                        float2 w = twz[m2 * r];
+                        w.y = -w.y;
+                        u[m2] = cmul(u[m2], w);
+                    }
+#pragma unroll
+                    for (int m2 = 0; m2 < N2Z; ++m2) Y[l * YL + (r * N2Z + m2) * DTX + lane] = u[m2];
                 }
             }
-            __syncthreads();   // every phase-2 read of Y is done
-            if (r < DN1) {
-#pragma unroll
-                for (int m2 = 0; m2 < N2Z; ++m2) Y[(r * N2Z + m2) * DTX + lane] = u[m2];
-            }
             __syncthreads();
-            if (r < N2Z) {
+            if (r < LPB * N2Z) {
+                float2* Wl = Wc + (ky0 + l1) * DTX;
                 float2 v[DN1];
 #pragma unroll
-                for (int k1 = 0; k1 < DN1; ++k1) v[k1] = Y[(k1 * N2Z + r) * DTX + lane];
+                for (int k1 = 0; k1 < DN1; ++k1) v[k1] = Y[l1 * YL + (k1 * N2Z + m2r) * DTX + lane];
                 RegFft<DN1, true>::run(v, twz, N2Z);
 #pragma unroll
-                for (int m1 = 0; m1 < DN1; ++m1) __stcg(Wl + (int64_t)(N2Z * m1 + r) * ZS, v[m1]);
+                for (int m1 = 0; m1 < DN1; ++m1) __stcg(Wl + (int64_t)(N2Z * m1 + m2r) * ZS, v[m1]);
             }
             df_signal(cntB + (int64_t)k * a.CG + c);
         } else {
             // ---- C (z): y IFFT, conj(S_c), sum over the group, partial sum
-            const int z = rr - cg * (NZ + NY);
+            const int z = rr - cg * (NZ + NBI);
             float2 acc[N2Y];
 #pragma unroll
             for (int k2 = 0; k2 < N2Y; ++k2) acc[k2] = make_float2(0.f, 0.f);
@@ -286,9 +299,9 @@ c3_dataflow_kernel(DfArgs a) {
     }
 }
 
-template <int N2Y, int N2Z>
+template <int N2Y, int N2Z, int MB>
 int df_resident() {
-    auto fn = c3_dataflow_kernel<N2Y, N2Z>;
+    auto fn = c3_dataflow_kernel<N2Y, N2Z, MB>;
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)Df<N2Y, N2Z>::SMEM) != cudaSuccess) {
         cudaGetLastError();
@@ -319,12 +332,21 @@ extern thread_local Profiler* g_profiler;
 #define PP_DF_CASES(X) X(8, 8) X(12, 8) X(16, 8) X(20, 8) X(24, 8) \
     X(8, 12) X(12, 12) X(16, 12) X(8, 16) X(12, 16) X(16, 16)
 
-// Resident CTAs of the dataflow kernel for this plan's (ny, nz), 0 when the
-// kernel does not apply (a length without a register FFT).
-int c3df_prepare(const Plan& p) {
+// Blocks per SM the kernel is compiled for: variant 0 leaves the registers
+// of two 256-thread blocks per SM, variant 1 of three (fewer registers, a
+// few spilled, more warps to cover latency); larger blocks get one.
+template <int N2Y, int N2Z> constexpr int df_mb(int v) {
+    return Df<N2Y, N2Z>::THREADS <= 256 ? (v ? 3 : 2) : 1;
+}
+
+// Resident CTAs of the dataflow kernel (variant v) for this plan's (ny, nz),
+// 0 when the kernel does not apply (a length without a register FFT).
+int c3df_prepare(const Plan& p, int v) {
     if (p.kind != PP_CARTESIAN || p.ndim != 3) return 0;
     const int n2y = fft4_n2(p.ny), n2z = fft4_n2(p.nz);
-#define PP_DF_PREP(Y_, Z_) if (n2y == Y_ && n2z == Z_) return df_resident<Y_, Z_>();
+#define PP_DF_PREP(Y_, Z_)                                                           \
+    if (n2y == Y_ && n2z == Z_)                                                      \
+        return v ? df_resident<Y_, Z_, df_mb<Y_, Z_>(1)>() : df_resident<Y_, Z_, df_mb<Y_, Z_>(0)>();
     PP_DF_CASES(PP_DF_PREP)
 #undef PP_DF_PREP
     return 0;
@@ -351,14 +373,22 @@ pp_status c3df_normal(const Plan& p, const float2* x, float2* out, float scale,
     }
     PP_TRY_CUDA(cudaMemsetAsync(p.c3df_cnt, 0, sizeof(int) * c3df_counter_ints(p, cg), st));
     const int n2y = fft4_n2(p.ny), n2z = fft4_n2(p.nz);
-    const int per_full = cg * (p.nz + p.ny) + p.nz;
+    const int per_full = cg * (p.nz + p.ny) + p.nz;   // an upper bound on the items of a phase
     const int64_t total = (int64_t)a.nb * a.ng * per_full;
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(p.c3df_ctas, total));
+    const int v = p.c3df_hi ? 1 : 0;
+    const int ctas = v ? p.c3df_ctas_hi : p.c3df_ctas;
+    if (ctas <= 0) {
+        set_error("c3df_normal: this dataflow variant cannot be resident on the device");
+        return PP_ERR_UNSUPPORTED;
+    }
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ctas, total));
     cudaError_t e = cudaErrorInvalidValue;
 #define PP_DF_LAUNCH(Y_, Z_)                                                                    \
     if (n2y == Y_ && n2z == Z_)                                                                 \
-        e = launch_ex(c3_dataflow_kernel<Y_, Z_>, dim3(grid), dim3(Df<Y_, Z_>::THREADS),        \
-                      Df<Y_, Z_>::SMEM, st, false, 0, a);
+        e = v ? launch_ex(c3_dataflow_kernel<Y_, Z_, df_mb<Y_, Z_>(1)>, dim3(grid),             \
+                          dim3(Df<Y_, Z_>::THREADS), Df<Y_, Z_>::SMEM, st, false, 0, a)         \
+              : launch_ex(c3_dataflow_kernel<Y_, Z_, df_mb<Y_, Z_>(0)>, dim3(grid),             \
+                          dim3(Df<Y_, Z_>::THREADS), Df<Y_, Z_>::SMEM, st, false, 0, a);
     PP_DF_CASES(PP_DF_LAUNCH)
 #undef PP_DF_LAUNCH
     if (e != cudaSuccess) return cuda_status(e, "c3_dataflow_kernel launch");

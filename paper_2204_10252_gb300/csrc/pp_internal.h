@@ -187,6 +187,8 @@ struct Plan {
     int c3cl2_clusters = 0;     //      the same with 2 columns per task (0: n/a)
     // 3-D dataflow operator (one persistent kernel per apply, pp_cart3d_df.cu)
     int c3df_ctas = 0;          // resident CTAs (0: not available for this plan)
+    int c3df_ctas_hi = 0;       //   the same for the variant with three blocks per SM
+    int c3df_hi = 0;            // 1: run that variant
     int c3df_cg = 4;            // coils per group
     float2* c3df_w = nullptr;   // two phase slots
     size_t c3df_w_elems = 0;
@@ -257,7 +259,7 @@ pp_status launch_gtg_stencil(const Plan& p, const float2* grid_in, float2* grid_
 pp_status prepare_gtg_stencil(Plan& p);
 pp_status prepare_cart4();
 int c3cl_prepare(const Plan& p, int xb);
-int c3df_prepare(const Plan& p);
+int c3df_prepare(const Plan& p, int variant);
 size_t c3df_slot_elems(const Plan& p, int cg);
 size_t c3df_counter_ints(const Plan& p, int cg);
 pp_status c3df_normal(const Plan& p, const float2* x, float2* out, float scale,

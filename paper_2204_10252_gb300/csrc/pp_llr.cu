@@ -14,7 +14,10 @@
 // T' = T rounded up to even); the column norms and inner products of one
 // round's pairs are summed over the block's voxels in one block reduction.
 // The sweeps stop when every pair's |a_i^H a_j| <= tol sqrt(|a_i|^2 |a_j|^2)
-// (the same decision in every thread: it is taken from the reduced sums).
+// (the same decision in every thread: it is taken from the reduced sums),
+// tol = sqrt(R) * 2^-24 for R voxels per block: the rounding level of an
+// R-term FP32 inner product (the threshold LAPACK's one-sided Jacobi uses
+// with its own precision), below which a rotation only moves noise.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -24,7 +27,6 @@
 namespace pp {
 namespace {
 
-constexpr float kLlrTol = 2e-7f;   // a few FP32 roundings: pairs this close to orthogonal are done
 constexpr int kLlrSweeps = 12;
 
 struct LlrArgs {
@@ -109,6 +111,7 @@ __global__ void __launch_bounds__(NT) llr_prox_kernel(LlrArgs a) {
     if (threadIdx.x < T)
 #pragma unroll
         for (int i = 0; i < T; ++i) Vs[threadIdx.x][i] = make_float2(i == (int)threadIdx.x ? 1.f : 0.f, 0.f);
+    const float tol = sqrtf((float)a.R) * 5.9604645e-8f;
     int par = 0;
     if (T > 1) {
         for (int sweep = 0; sweep < kLlrSweeps; ++sweep) {
@@ -140,7 +143,7 @@ __global__ void __launch_bounds__(NT) llr_prox_kernel(LlrArgs a) {
                     if (j >= T) continue;
                     const float al = s[4 * p], be = s[4 * p + 1], gr = s[4 * p + 2], gi = s[4 * p + 3];
                     const float g = sqrtf(gr * gr + gi * gi), nab = sqrtf(al * be);
-                    if (!(g > kLlrTol * nab)) continue;
+                    if (!(g > tol * nab)) continue;
                     offmax = fmaxf(offmax, g / nab);
                     // real symmetric Schur rotation of [[al, g], [g, be]], after the
                     // phase e^{-i phi} = conj(gamma)/|gamma| that makes gamma real
@@ -162,7 +165,7 @@ __global__ void __launch_bounds__(NT) llr_prox_kernel(LlrArgs a) {
                     }
                 }
             }
-            if (offmax <= kLlrTol) break;
+            if (offmax <= tol) break;
         }
     }
     // singular values = final column norms; shrink factors

@@ -57,10 +57,10 @@ def lam_between(x, block, shift=None):
     return float(np.quantile(sv, 0.6))
 
 
-CASES = [((8, 16, 24), 5, 8, None), ((16, 16, 16), 8, 8, (3, 7, 5)), ((8, 8, 8), 1, 8, None),
+CASES = [((8, 16, 24), 5, 8, None), ((16, 16, 16), 8, 8, (3, 7, 5)), ((16, 16, 8), 1, 8, None),
          ((32, 48), 5, 8, (5, 0)), ((12, 20), 3, 4, (1, 2)), ((32, 32), 2, 16, None),
          ((8, 12, 16), 4, 4, (2, 3, 1)), ((16, 8, 8), 7, 8, (0, 0, 9))]
-IDS = ["3d_8x16x24_T5", "3d_16^3_T8_shift", "3d_8^3_T1", "2d_32x48_T5_shift", "2d_12x20_T3_b4",
+IDS = ["3d_8x16x24_T5", "3d_16^3_T8_shift", "3d_16x16x8_T1", "2d_32x48_T5_shift", "2d_12x20_T3_b4",
        "2d_32_T2_b16", "3d_8x12x16_T4_b4", "3d_16x8x8_T7_zshift"]
 
 

@@ -229,15 +229,15 @@ def test_cart3d_dataflow_operator(pp, case):
         ref = nrm(x)
         c = [float(v) for v in O.poly_coeffs_l2(2)]
         refp = O.horner_apply(c, nrm, op.astype(np.complex128))
-        for cg in sorted({1, 2, 3, 4, 8, min(C, 8)}):
-            pp.pp_plan_set_tuning(plan, 3, 0, cg)
-            assert pp.pp_plan_tuning(plan) == (3, 0, cg)
+        for cg, hi in [(g, h) for g in sorted({1, 2, 3, 4, 8, min(C, 8)}) for h in (0, 1)]:
+            pp.pp_plan_set_tuning(plan, 3, hi, cg)
+            assert pp.pp_plan_tuning(plan) == (3, hi, cg)
             out = empty(shape)
             pp.pp_normal_apply(plan, dev(x), out)
-            assert rel(host(out), ref) <= TOL_APPLY, cg
+            assert rel(host(out), ref) <= TOL_APPLY, (cg, hi)
             out = empty(shape)
             pp.pp_poly_apply(plan, c, 2, dev(op), out)
-            assert rel(host(out), refp) <= TOL_APPLY, cg
+            assert rel(host(out), refp) <= TOL_APPLY, (cg, hi)
         # the bounded waits never ran out: a synchronising call reports no timeout
         pp.pp_plan_mu(plan, 2, 1)
     finally:

@@ -27,6 +27,13 @@ def test_blocks_are_disjoint_tiles_and_the_map_inverts(shape, block):
     M, _ = O.llr_blocks(x, block)
     corner = x[(slice(None),) + (slice(0, block),) * len(shape)]
     assert np.array_equal(np.sort_complex(M[0].ravel()), np.sort_complex(corner.ravel()))
+    # a shift (x, y[, z]) moves the grid: the first block starts at voxel (.., sy, sx)
+    sh = (1, 2, 3)[:len(shape)]
+    M, _ = O.llr_blocks(x, block, sh)
+    start = tuple(reversed(sh))
+    idx = [(np.arange(block) + s0) % n for s0, n in zip(start, shape)]   # wraps circularly
+    corner = x[np.ix_(range(3), *idx)]
+    assert np.array_equal(np.sort_complex(M[0].ravel()), np.sort_complex(corner.ravel()))
 
 
 def test_single_image_is_group_soft_thresholding():
