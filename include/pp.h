@@ -318,6 +318,26 @@ typedef struct {
 pp_status pp_fista_solve(pp_plan* plan, const pp_c64* b, float lambda, int iters, const double* c,
                          int d, pp_c64* x_out, pp_solve_info* info, pp_stream stream);
 
+/* Algorithm "pfista" for the proximal subproblem of consensus ADMM
+ * (Algorithm "cadmm", Sec. 5.3):
+ *   x_out = argmin_x 1/2 ||A x - b||^2 + (sigma/2) ||x - v||^2 + lambda ||W x||_1,
+ * i.e. prox_{rho f}(v) with rho = 1/sigma for f = 1/2 ||A x - b||^2 +
+ * lambda ||W x||_1, in the problem's own units (b is NOT normalised; lambda
+ * is in the units of the objective above).  With N' = A^H A + sigma I and
+ * L' = L + sigma the iteration runs with step 1 on N'/L', the gradient's
+ * constant term (A^H b + sigma v)/L' and the threshold lambda/L'; the
+ * preconditioner p(N'/L') (coefficients c[0..d] designed on (0, 1], as for
+ * pp_fista_solve) is applied as the same-degree polynomial in N/L with
+ * coefficients expanded on the host, so every apply is the plan's normal
+ * operator.  y_0 = z_0 = 0.
+ *   b  device k-space or NULL (no data term); v device image or NULL (0);
+ *   sigma >= 0 (0: the plain problem in its own units).
+ * info as for pp_fista_solve (rescale is ignored).  The iteration loop runs
+ * as a cached CUDA graph like pp_fista_solve's. */
+pp_status pp_fista_solve_prox(pp_plan* plan, const pp_c64* b, const pp_c64* v, double sigma,
+                              float lambda, int iters, const double* c, int d, pp_c64* x_out,
+                              pp_solve_info* info, pp_stream stream);
+
 /* ---- Batches of independent 2-D Cartesian problems of uneven size ----
  * Slice s is its own problem (Sec. 5.1 operator, its own L_s, its own ||b_s||)
  * of size dims[s] (2-D, axes multiples of 4, FFT lengths with prime factors

@@ -80,6 +80,10 @@ _SIGS = {
     "pp_fista_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_float, ctypes.c_int,
                                       ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_void_p,
                                       ctypes.POINTER(pp_solve_info), ctypes.c_void_p]),
+    "pp_fista_solve_prox": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
+                                           ctypes.c_float, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                           ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(pp_solve_info),
+                                           ctypes.c_void_p]),
     "pp_profile_normal": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                          ctypes.c_int, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_int), ctypes.c_void_p]),
@@ -414,6 +418,31 @@ def pp_fista_solve(plan: Plan, b, lam: float, iters: int, c, d: int, x_out, stre
     _check(lib().pp_fista_solve(plan.handle, _ksp(plan, b, "b"), float(lam), int(iters), cptr, int(d),
                                 _img(plan, x_out, "x_out"), ctypes.byref(info), _stream(stream)),
            "pp_fista_solve")
+    return SolveResult(hist[:iters] if hist is not None else None, info.bnorm, info.L,
+                       int(info.launches))
+
+
+def pp_fista_solve_prox(plan: Plan, b, v, sigma: float, lam: float, iters: int, c, d: int, x_out,
+                        stream=None, history: bool = False, levels: int = 2, ref=None,
+                        momentum: bool = True, wavelet: str = "haar") -> SolveResult:
+    """argmin_x 1/2||A x - b||^2 + sigma/2 ||x - v||^2 + lam ||W x||_1 (the
+    consensus-ADMM subproblem, rho = 1/sigma); b or v may be None."""
+    info = pp_solve_info()
+    info.wavelet = WAVELETS[wavelet]
+    info.levels = int(levels)
+    info.no_momentum = 0 if momentum else 1
+    hist = None
+    if history:
+        hist = np.zeros((max(iters, 1), 3), dtype=np.float64)
+        info.history = hist.ctypes.data
+    else:
+        info.history = None
+    info.ref = _img(plan, ref, "ref") if ref is not None else None
+    cptr = _cvec(c) if c is not None else None
+    _check(lib().pp_fista_solve_prox(plan.handle, _ksp(plan, b, "b") if b is not None else None,
+                                     _img(plan, v, "v") if v is not None else None, float(sigma),
+                                     float(lam), int(iters), cptr, int(d), _img(plan, x_out, "x_out"),
+                                     ctypes.byref(info), _stream(stream)), "pp_fista_solve_prox")
     return SolveResult(hist[:iters] if hist is not None else None, info.bnorm, info.L,
                        int(info.launches))
 

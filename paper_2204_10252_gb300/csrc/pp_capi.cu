@@ -780,13 +780,27 @@ static pp_status horner_into(const Plan& p, const double* c, int d, const float2
     return PP_OK;
 }
 
+// `shift` (sh_a, sh_b): the iteration runs on a N_hat + sh_b I instead of
+// N_hat (the proximal subproblem of pp_fista_solve_prox); the caller then
+// passes the preconditioner already rewritten as a polynomial in N_hat.
+struct Shift {
+    bool on = false;
+    float a = 1.f, b = 0.f;
+};
+
 static pp_status fista_iterations(Plan& p, float lambda, int iters, const double* c, int d,
                                   int levels, bool hist, const float2* ref, bool momentum,
-                                  int wavelet, cudaStream_t st) {
+                                  int wavelet, cudaStream_t st, Shift sh = Shift()) {
     const float invL = (float)(1.0 / p.L);
     for (int k = 0; k < iters; ++k) {
-        // g = N_hat z - A_hat^H b_hat
-        PP_TRY(normal_into(p, p.z, p.g, invL, p.ahb, -1.f, st));
+        if (sh.on) {
+            // g = (a N_hat + b I) z - rhs: u = b z - rhs, then g = a N_hat z + u
+            PP_TRY(launch_axpby(p.z, sh.b, p.ahb, -1.f, p.u, p.nimg, st));
+            PP_TRY(normal_into(p, p.z, p.g, sh.a * invL, p.u, 1.f, st));
+        } else {
+            // g = N_hat z - A_hat^H b_hat
+            PP_TRY(normal_into(p, p.z, p.g, invL, p.ahb, -1.f, st));
+        }
         const float2* u = p.g;
         float gamma = 1.f;
         if (c && d >= 1) {
@@ -1803,8 +1817,8 @@ pp_status pp_fista_solve(pp_plan* plan, const pp_c64* b, float lambda, int iters
         PP_TRY_CUDA(cudaMemsetAsync(p.hist, 0, sizeof(double) * 3 * std::max(iters, 1), st));
     }
     if (iters > 0) {
-        std::vector<double> key = {(double)iters, (double)d, (double)lambda, (double)levels,
-                                   hist ? 1.0 : 0.0, c ? 1.0 : 0.0, p.L,
+        std::vector<double> key = {0.0 /* normalised solve */, (double)iters, (double)d,
+                                   (double)lambda, (double)levels, hist ? 1.0 : 0.0, c ? 1.0 : 0.0, p.L,
                                    (double)(uintptr_t)p.hist, (double)(uintptr_t)ref,
                                    momentum ? 1.0 : 0.0, (double)wavelet};
         if (c)
@@ -1855,6 +1869,136 @@ pp_status pp_fista_solve(pp_plan* plan, const pp_c64* b, float lambda, int iters
             info->bnorm = sqrt(bn2);
             PP_TRY(c3df_check(p, st));
             PP_TRY(check_history("pp_fista_solve", bn2, info->history, iters));
+        }
+    }
+    return PP_OK;
+}
+
+pp_status pp_fista_solve_prox(pp_plan* plan, const pp_c64* b, const pp_c64* v, double sigma,
+                              float lambda, int iters, const double* c, int d, pp_c64* x_out,
+                              pp_solve_info* info, pp_stream stream) {
+    if (!plan || !x_out || iters < 0 || iters > 1000000 || !(lambda >= 0.f) || !isfinite(lambda) ||
+        !(sigma >= 0.0) || !isfinite(sigma) || d < 0 || d > 16 || (!c && d != 0)) {
+        set_error("pp_fista_solve_prox: bad argument");
+        return PP_ERR_INVALID_ARG;
+    }
+    Plan& p = plan->impl;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int levels = (info && info->levels) ? info->levels : 2;
+    const int wavelet = info ? info->wavelet : 0;
+    if (wavelet != 0 && wavelet != 1) {
+        set_error("pp_fista_solve_prox: wavelet must be 0 (Haar) or 1 (Daubechies-4)");
+        return PP_ERR_INVALID_ARG;
+    }
+    if ((wavelet == 1 && !db4_supported(p.ndim, p.nx, p.ny, levels)) ||
+        (wavelet == 0 && (levels < 1 || levels > 2 || p.nx % (1 << levels) || p.ny % (1 << levels) ||
+                          (p.ndim == 3 && p.nz % (1 << levels))))) {
+        set_error("pp_fista_solve_prox: unsupported wavelet levels for this image");
+        return PP_ERR_UNSUPPORTED;
+    }
+    const bool hist = info && info->history;
+    const bool momentum = !(info && info->no_momentum);
+    const float2* ref = info ? reinterpret_cast<const float2*>(info->ref) : nullptr;
+    const int64_t n = p.nimg;
+    const int64_t launches0 = g_launches;
+    // L' = L + sigma; the iteration runs on N_hat' = a N_hat + b I with
+    // a = L/L', b = sigma/L', gradient constant rhs = (A^H b + sigma v)/L'
+    // and threshold lambda/L'; p(N_hat') = q(N_hat) with
+    // q_j = sum_{i >= j} c_i C(i, j) a^j b^(i-j) (binomial expansion, FP64)
+    const double Lp = p.L + sigma, sa = p.L / Lp, sb = sigma / Lp;
+    std::vector<double> q;
+    if (c) {
+        q.assign(d + 1, 0.0);
+        std::vector<double> binom(d + 1, 0.0);
+        for (int i = 0; i <= d; ++i) {
+            // binom[j] = C(i, j), row i of Pascal's triangle
+            for (int j = i; j >= 1; --j) binom[j] += binom[j - 1];
+            binom[0] = 1.0;
+            for (int j = 0; j <= i; ++j) q[j] += c[i] * binom[j] * std::pow(sa, j) * std::pow(sb, i - j);
+        }
+    }
+    if (b) {
+        PP_TRY(launch_norm2(reinterpret_cast<const float2*>(b), p.nksp, p.red, p.red_blocks, p.scal + 0, st));
+        PP_TRY(adjoint_into(p, reinterpret_cast<const float2*>(b), p.ahb, st));
+        PP_TRY(launch_axpby(p.ahb, (float)(1.0 / Lp), reinterpret_cast<const float2*>(v),
+                            (float)(sigma / Lp), p.ahb, n, st));
+    } else if (v) {
+        PP_TRY(launch_axpby(reinterpret_cast<const float2*>(v), (float)(sigma / Lp), nullptr, 0.f, p.ahb,
+                            n, st));
+    } else {
+        PP_TRY_CUDA(cudaMemsetAsync(p.ahb, 0, n * sizeof(float2), st));
+    }
+    if (!b) PP_TRY_CUDA(cudaMemsetAsync(p.scal, 0, sizeof(double), st));
+    PP_TRY_CUDA(cudaMemsetAsync(p.y, 0, n * sizeof(float2), st));
+    PP_TRY_CUDA(cudaMemsetAsync(p.z, 0, n * sizeof(float2), st));
+    if (hist) {
+        if (p.hist_cap < iters) {
+            if (p.hist) {
+                cudaStreamSynchronize(st);
+                cudaFree(p.hist);
+                p.allocs.erase(std::remove(p.allocs.begin(), p.allocs.end(), (void*)p.hist), p.allocs.end());
+                p.hist = nullptr;
+            }
+            PP_TRY(alloc_n(p, &p.hist, (size_t)3 * std::max(iters, 1)));
+            p.hist_cap = iters;
+            p.gkey.clear();
+        }
+        PP_TRY_CUDA(cudaMemsetAsync(p.hist, 0, sizeof(double) * 3 * std::max(iters, 1), st));
+    }
+    Shift sh;
+    sh.on = true;
+    sh.a = (float)sa;
+    sh.b = (float)sb;
+    const float lam_hat = (float)(lambda / Lp);
+    if (iters > 0) {
+        // the graph cache is shared with pp_fista_solve: the key tells the two apart
+        std::vector<double> key = {1.0 /* proximal subproblem */, (double)iters, (double)d,
+                                   (double)lam_hat, (double)levels, hist ? 1.0 : 0.0, c ? 1.0 : 0.0,
+                                   p.L, (double)(uintptr_t)p.hist, (double)(uintptr_t)ref,
+                                   momentum ? 1.0 : 0.0, (double)wavelet, sa, sb};
+        for (double qj : q) key.push_back(qj);
+        if (!p.gexec || key != p.gkey) {
+            if (p.gexec) {
+                cudaGraphExecDestroy(p.gexec);
+                p.gexec = nullptr;
+            }
+            p.gkey.clear();
+            cudaGraph_t graph = nullptr;
+            PP_TRY_CUDA(cudaStreamBeginCapture(p.cap_stream, cudaStreamCaptureModeThreadLocal));
+            const int64_t before = g_launches;
+            pp_status rc = fista_iterations(p, lam_hat, iters, c ? q.data() : nullptr, d, levels, hist,
+                                            ref, momentum, wavelet, p.cap_stream, sh);
+            cudaError_t e = cudaStreamEndCapture(p.cap_stream, &graph);
+            p.graph_kernels = g_launches - before;
+            g_launches = before;
+            if (rc != PP_OK) {
+                if (graph) cudaGraphDestroy(graph);
+                return rc;
+            }
+            if (e != cudaSuccess) return cuda_status(e, "cudaStreamEndCapture");
+            e = cudaGraphInstantiate(&p.gexec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) {
+                p.gexec = nullptr;
+                return cuda_status(e, "cudaGraphInstantiate");
+            }
+            p.gkey = key;
+        }
+        PP_TRY_CUDA(cudaGraphLaunch(p.gexec, st));
+    }
+    PP_TRY_CUDA(cudaMemcpyAsync(x_out, p.y, n * sizeof(float2), cudaMemcpyDeviceToDevice, st));
+    if (info) {
+        info->L = p.L;
+        info->launches = (g_launches - launches0) + (iters > 0 ? p.graph_kernels : 0);
+        if (hist) {
+            double bn2 = 0.0;
+            PP_TRY_CUDA(cudaMemcpyAsync(&bn2, p.scal + 0, sizeof(double), cudaMemcpyDeviceToHost, st));
+            PP_TRY_CUDA(cudaMemcpyAsync(info->history, p.hist, sizeof(double) * 3 * iters,
+                                        cudaMemcpyDeviceToHost, st));
+            PP_TRY_CUDA(cudaStreamSynchronize(st));
+            info->bnorm = sqrt(bn2);
+            PP_TRY(c3df_check(p, st));
+            PP_TRY(check_history("pp_fista_solve_prox", bn2, info->history, iters));
         }
     }
     return PP_OK;

@@ -250,7 +250,7 @@ c3_dataflow_kernel(DfArgs a) {
             for (int k2 = 0; k2 < N2Y; ++k2) acc[k2] = make_float2(0.f, 0.f);
             bool alive = true;
             for (int c = 0; c < cg; ++c) {
-                if (!df_wait(cntB + (int64_t)k * a.CG + c, NY, err)) {
+                if (!df_wait(cntB + (int64_t)k * a.CG + c, NBI, err)) {
                     alive = false;
                     break;
                 }
