@@ -56,6 +56,10 @@ def parse():
                     choices=[WORKLOAD, "cart2d_128_c8", "cart3d_256x256x128_c32", "batched2d_64",
                              "unrolled2d_8x256_c16"],
                     help="benchmark line to produce (the default is the headline workload)")
+    ap.add_argument("--poly", choices=["l2", "cheb"], default="l2",
+                    help="spiral workload: the preconditioner, Eq. l2cost (default) or the Chebyshev "
+                         "minimax design of Sec. 3.4 with mu estimated by pp_plan_mu (set-up time "
+                         "includes that estimate)")
     ap.add_argument("--no-secondary", action="store_true",
                     help="skip the 3-D and batched lines that the default run appends")
     ap.add_argument("--apply-only", type=int, default=0, metavar="K",
@@ -450,7 +454,17 @@ def main():
     b = torch.empty((C, K), dtype=torch.complex64, device=dev)
     pp.pp_forward_apply(plan, xt, b)
     b += torch.from_numpy(noise).to(dev)
-    coeffs = [float(v) for v in pp.pp_poly_coeffs_l2(d)]
+    mu = None
+    if args.poly == "cheb":
+        # the Chebyshev interval [mu, 1]: mu by power iteration on I - N_hat
+        t0 = time.perf_counter()
+        mu = pp.pp_plan_mu(plan, 50, seed)
+        setup_plan_s += time.perf_counter() - t0
+        if not 0.0 < mu < 1.0:
+            raise RuntimeError("the mu estimate %g leaves no Chebyshev interval" % mu)
+        coeffs = [float(v) for v in pp.pp_poly_coeffs_cheb(d, mu)]
+    else:
+        coeffs = [float(v) for v in pp.pp_poly_coeffs_l2(d)]
     x_out = torch.empty(shape, dtype=torch.complex64, device=dev)
     applies_per_step = iters * (d + 1)
 
@@ -517,7 +531,11 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded phantom, coil maps, spiral, noise); no datasets",
         "config": {"workload": WORKLOAD + ("_toeplitz" if toep else "") +
-                               ("_db4" if args.wavelet == "db4" else ""), "image": list(shape),
+                               ("_db4" if args.wavelet == "db4" else "") +
+                               ("_cheb" if args.poly == "cheb" else ""), "image": list(shape),
+                   "preconditioner": ("Chebyshev minimax on [mu, 1] (Sec. 3.4), mu = %.6g from 50 "
+                                      "power-iteration steps on I - N_hat" % mu) if mu is not None
+                   else "l2-optimal (Eq. l2cost)",
                    "wavelet": ("Daubechies-4, 2 levels" if args.wavelet == "db4" else "Haar, 2 levels"),
                    "coils": C, "samples": K,
                    "normal_operator": ("exact F^H F by its 2ny x 2nx Toeplitz embedding" if toep else

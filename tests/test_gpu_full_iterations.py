@@ -8,11 +8,16 @@ image, degree 5), 60 (3-D Cartesian with the workload's nz = 128 and
 ny in {192, 256}, few x columns), 50 (five uneven slices).  Soft-threshold
 support flips over many iterations are where FP32 rounding could drift from
 the FP64 oracle; these runs cover them at the counts the workloads use."""
+import importlib.util
+import os
+
 import numpy as np
 import pytest
 
 import synth
 from oracle import pp_oracle as O
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 
 pytestmark = pytest.mark.gpu
 
@@ -221,3 +226,30 @@ def test_batched_64_slices_one_apply(pp):
             assert rel(got[io[i]:io[i + 1]].reshape(s), ref) <= TOL_APPLY, i
     finally:
         batch.destroy()
+
+
+def test_spiral_full_size_100_iterations_against_golden(pp):
+    # the benchmark's workload itself: 256^2, 32 coils, 16 x 4096 spiral,
+    # lambda = 5e-4, d = 5, 100 iterations, against the FP64 oracle's solution
+    # written by tests/golden/make_spiral_golden.py (same inputs, same L)
+    spec = importlib.util.spec_from_file_location("make_spiral_golden",
+                                                  os.path.join(GOLDEN, "make_spiral_golden.py"))
+    mk = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mk)
+    g = np.load(os.path.join(GOLDEN, "spiral2d_256_c32_pfista100.npz"))
+    cfg = mk.CFG
+    sens, traj, x_true, noise = mk.inputs()
+    b = mk.measurements(sens, traj, x_true, noise)
+    L = float(g["L"])
+    plan = pp.pp_plan_create(cfg["shape"], cfg["coils"], dev(sens), traj=traj, seed=cfg["seed"],
+                             power_iters=50)
+    try:
+        # the device power iteration from the same seed agrees with the oracle's L
+        assert abs(pp.pp_plan_scale(plan) - L) <= 1e-5 * L
+        pp.pp_plan_set_scale(plan, L)
+        c = [float(v) for v in O.poly_coeffs_l2(int(g["d"]))]
+        out = empty(cfg["shape"])
+        pp.pp_fista_solve(plan, dev(b), float(g["lam"]), int(g["iters"]), c, int(g["d"]), out)
+        assert rel(host(out), g["y"].astype(np.complex128)) <= TOL_SOLVE
+    finally:
+        plan.destroy()
