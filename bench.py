@@ -463,6 +463,11 @@ def main():
         if not 0.0 < mu < 1.0:
             raise RuntimeError("the mu estimate %g leaves no Chebyshev interval" % mu)
         coeffs = [float(v) for v in pp.pp_poly_coeffs_cheb(d, mu)]
+        # the minimax residual reaches -1/T_{d+1}(a) on [mu, 1], so z p(z) peaks
+        # at 1 + 1/T_{d+1}(a) (near 2 here): scale p so the step keeps FISTA's
+        # rule (max z p(z) = 1); unscaled, the momentum iteration diverges
+        zp_max = pp.pp_poly_max_zp(coeffs, d)
+        coeffs = [v / zp_max for v in coeffs]
     else:
         coeffs = [float(v) for v in pp.pp_poly_coeffs_l2(d)]
     x_out = torch.empty(shape, dtype=torch.complex64, device=dev)
@@ -534,7 +539,8 @@ def main():
                                ("_db4" if args.wavelet == "db4" else "") +
                                ("_cheb" if args.poly == "cheb" else ""), "image": list(shape),
                    "preconditioner": ("Chebyshev minimax on [mu, 1] (Sec. 3.4), mu = %.6g from 50 "
-                                      "power-iteration steps on I - N_hat" % mu) if mu is not None
+                                      "power-iteration steps on I - N_hat, scaled by 1/max z p(z) = "
+                                      "1/%.4f" % (mu, zp_max)) if mu is not None
                    else "l2-optimal (Eq. l2cost)",
                    "wavelet": ("Daubechies-4, 2 levels" if args.wavelet == "db4" else "Haar, 2 levels"),
                    "coils": C, "samples": K,

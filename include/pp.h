@@ -234,6 +234,17 @@ pp_status pp_poly_coeffs_cheb(int d, double mu, double* c);
  * only; no device work. */
 pp_status pp_poly_coeffs_wl2(int d, const double* moments, double* c);
 
+/* *m (host) = max over z in [0, 1] of z p(z), p(z) = sum_i c[i] z^i: the
+ * Lipschitz constant of the preconditioned gradient step on the normalised
+ * problem (spectrum of N_hat in (0, 1]).  FISTA's step rule wants it <= 1;
+ * the l2 polynomials exceed it mildly (1.2, 1.15, 1.14 for d = 1, 3, 5) and
+ * the Chebyshev ones reach 1 + 1/T_{d+1}((1 + mu)/(1 - mu)) on [mu, 1]
+ * (near 2 for small mu), which diverges under momentum; dividing c by m
+ * gives a step within the rule (the paper applies p unscaled).  Dense
+ * sampling of [0, 1] refined by golden-section search.  Host only.
+ * 0 <= d <= 16. */
+pp_status pp_poly_max_zp(const double* c, int d, double* m);
+
 /* out = p(N_hat) v by the recursion of Listing "pcode": u = c_d v, then
  * u = c_i v + N_hat u for i = d-1..0 (d applies of N_hat).  c host double
  * [d+1], 0 <= d <= 16.  v, out device images. */

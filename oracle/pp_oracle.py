@@ -564,6 +564,13 @@ def poly_eval(c, z):
     return out
 
 
+def poly_max_zp(c, samples=200001):
+    """max over z in [0, 1] of z p(z) on a dense grid (the Lipschitz constant
+    of the preconditioned step on a spectrum in (0, 1])."""
+    z = np.linspace(0.0, 1.0, samples)
+    return float(np.max(z * poly_eval(c, z)))
+
+
 def horner_apply(c, normal, g):
     """p(N) g = c0 g + N(c1 g + N(c2 g + ...)) by the recursion of Listing
     "pcode": u = c_d g, then u = c_i g + N u for i = d-1 .. 0."""

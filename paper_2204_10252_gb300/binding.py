@@ -71,6 +71,8 @@ _SIGS = {
     "pp_poly_coeffs_cheb": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]),
     "pp_poly_coeffs_wl2": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_double)]),
+    "pp_poly_max_zp": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.c_int,
+                                      ctypes.POINTER(ctypes.c_double)]),
     "pp_poly_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int,
                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "pp_prox_l1_haar": (ctypes.c_int, [pp_dims, ctypes.c_int, ctypes.c_float, ctypes.c_void_p,
@@ -342,6 +344,15 @@ def pp_poly_coeffs_wl2(d: int, moments) -> np.ndarray:
     mv = (ctypes.c_double * m.size)(*m.tolist())
     _check(lib().pp_poly_coeffs_wl2(int(d), mv, c), "pp_poly_coeffs_wl2")
     return np.array(list(c), dtype=np.float64)
+
+
+def pp_poly_max_zp(c, d: int) -> float:
+    """max over z in [0, 1] of z p(z) (the preconditioned step's Lipschitz constant)."""
+    m = ctypes.c_double(0.0)
+    cc = np.ascontiguousarray(c, dtype=np.float64)
+    cv = (ctypes.c_double * len(cc))(*cc.tolist())
+    _check(lib().pp_poly_max_zp(cv, int(d), ctypes.byref(m)), "pp_poly_max_zp")
+    return m.value
 
 
 def _cvec(c):

@@ -1226,6 +1226,43 @@ extern "C" {
 
 const char* pp_last_error(void) { return g_last_error.c_str(); }
 
+pp_status pp_poly_max_zp(const double* c, int d, double* m) {
+    if (!c || !m || d < 0 || d > 16) {
+        set_error("pp_poly_max_zp: need c != NULL, m != NULL, 0 <= d <= 16");
+        return PP_ERR_INVALID_ARG;
+    }
+    // z p(z) on 4096 equal steps of [0, 1], then golden-section refinement
+    // of the best bracket (z p(z) is a polynomial: one smooth maximum there)
+    auto f = [&](double z) {
+        double acc = 0.0;
+        for (int i = d; i >= 0; --i) acc = acc * z + c[i];
+        return z * acc;
+    };
+    const int n = 4096;
+    int best = 0;
+    double fb = f(0.0);
+    for (int i = 1; i <= n; ++i) {
+        const double v = f((double)i / n);
+        if (v > fb) {
+            fb = v;
+            best = i;
+        }
+    }
+    double a = std::max(0.0, (best - 1.0) / n), b = std::min(1.0, (best + 1.0) / n);
+    const double g = 0.5 * (sqrt(5.0) - 1.0);
+    for (int it = 0; it < 80; ++it) {
+        const double x1 = b - g * (b - a), x2 = a + g * (b - a);
+        if (f(x1) < f(x2)) a = x1;
+        else b = x2;
+    }
+    *m = std::max(fb, f(0.5 * (a + b)));
+    if (!std::isfinite(*m)) {
+        set_error("pp_poly_max_zp: non-finite value");
+        return PP_ERR_NONFINITE;
+    }
+    return PP_OK;
+}
+
 pp_status pp_poly_coeffs_l2(int d, double* c) {
     if (!c || d < 0 || d > 8) {
         set_error("pp_poly_coeffs_l2: need 0 <= d <= 8 and c != NULL");

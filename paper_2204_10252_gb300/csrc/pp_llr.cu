@@ -54,25 +54,47 @@ __host__ __device__ constexpr int rr_j(int r, int k) {
                                                                                   : (r + k) % (TP - 1));
 }
 
-// Sum `n` floats per thread over the block (NT threads, NT/32 warps): the
-// result in every thread.  `buf` holds [NT/32][n] floats.
+// Sum N <= 16 floats per thread over the block (NT threads, NT/32 warps):
+// the result in every thread.  Within a warp a butterfly reduce-scatter
+// halves the values each step (16 shuffles for 16 values instead of 5 per
+// value): after the step with offset o a lane keeps the half its bit o
+// selects, so lanes 2i and 2i+1 end with the warp sum of value i.  One lane
+// per value writes it to `buf` ([NT/32][16] floats), and after the barrier
+// every thread adds the warps' rows with 16-byte reads.
 template <int NT, int N>
 __device__ __forceinline__ void block_sum(float* v, float* buf) {
+    static_assert(N <= 16, "block_sum handles up to 16 values");
+    float t[16];
 #pragma unroll
-    for (int i = 0; i < N; ++i)
+    for (int i = 0; i < 16; ++i) t[i] = i < N ? v[i] : 0.f;
+    const int lane = threadIdx.x & 31;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+    for (int h = 8, o = 16; h >= 1; h >>= 1, o >>= 1) {
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < h; ++i) {
+            const float send = up ? t[i] : t[i + h];
+            const float keep = up ? t[i + h] : t[i];
+            t[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+    t[0] += __shfl_xor_sync(0xffffffffu, t[0], 1);
     const int w = threadIdx.x >> 5;
-    if ((threadIdx.x & 31) == 0)
-#pragma unroll
-        for (int i = 0; i < N; ++i) buf[w * N + i] = v[i];
+    if ((lane & 1) == 0) buf[w * 16 + (lane >> 1)] = t[0];
     __syncthreads();
+    const float4* b4 = reinterpret_cast<const float4*>(buf);
 #pragma unroll
-    for (int i = 0; i < N; ++i) {
-        float s = 0.f;
+    for (int q = 0; q < (N + 3) / 4; ++q) {
+        float4 acc = b4[q];
 #pragma unroll
-        for (int ww = 0; ww < NT / 32; ++ww) s += buf[ww * N + i];
-        v[i] = s;
+        for (int ww = 1; ww < NT / 32; ++ww) {
+            const float4 u = b4[ww * 4 + q];
+            acc.x += u.x; acc.y += u.y; acc.z += u.z; acc.w += u.w;
+        }
+        if (4 * q + 0 < N) v[4 * q + 0] = acc.x;
+        if (4 * q + 1 < N) v[4 * q + 1] = acc.y;
+        if (4 * q + 2 < N) v[4 * q + 2] = acc.z;
+        if (4 * q + 3 < N) v[4 * q + 3] = acc.w;
     }
 }
 
@@ -95,7 +117,7 @@ __global__ void __launch_bounds__(NT) llr_prox_kernel(LlrArgs a) {
     constexpr int TP = T + (T & 1);
     constexpr int NPR = TP / 2;                       // pairs per round
     __shared__ float2 Vs[T][T];                       // Vs[k][i] = V(k, i)
-    __shared__ float red[2][NT / 32][4 * NPR > T ? 4 * NPR : T];
+    __shared__ __align__(16) float red[2][NT / 32][16];
     const int b = blockIdx.x;
     float2 m[RPT][T];
     int64_t off[RPT];

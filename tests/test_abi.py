@@ -166,6 +166,22 @@ def test_chebyshev_coefficients_match_oracle(L, d, mu):
         pp.pp_poly_coeffs_cheb(3, 1.5)
 
 
+@pytest.mark.parametrize("kind,d,mu", [("l2", 0, 0), ("l2", 3, 0), ("l2", 5, 0), ("cheb", 5, 1e-3),
+                                        ("cheb", 3, 0.2), ("cheb", 8, 0.05)])
+def test_poly_max_zp_matches_oracle(L, kind, d, mu):
+    # host-only entry point: max over [0, 1] of z p(z) against the oracle's
+    # dense grid, and 1 + 1/T_{d+1}(a) for the Chebyshev design
+    import math
+    import paper_2204_10252_gb300 as pp
+    from oracle import pp_oracle as O
+    c = [float(v) for v in (O.poly_coeffs_l2(d) if kind == "l2" else O.poly_coeffs_cheb(d, mu))]
+    got = pp.pp_poly_max_zp(c, d)
+    assert abs(got - O.poly_max_zp(c)) <= 1e-8 * got
+    if kind == "cheb":
+        a = (1 + mu) / (1 - mu)
+        assert abs(got - (1 + 1 / math.cosh((d + 1) * math.acosh(a)))) <= 1e-8
+
+
 @pytest.mark.parametrize("d", [0, 1, 3, 5, 8])
 @pytest.mark.parametrize("terms", [[(1, 0)], [(1, 1)], [(1, 0), (3, 2)], [(2, 0), (-1, 1)], [(1, 6)]])
 def test_weighted_l2_coefficients_match_oracle(L, d, terms):

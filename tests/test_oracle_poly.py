@@ -1,6 +1,7 @@
 """Pins for the polynomial preconditioner: Eq. "l2cost" (Sec. 3.1),
 Thm. "ppos" (Sec. 3.4), the recursion of Listing "pcode" (Sec. 3.6),
 Lemma "permute" (Sec. 3.3) and Fig. "complexity" (Sec. 3.6)."""
+import math
 import os
 from fractions import Fraction
 
@@ -181,3 +182,20 @@ def test_wl2_weight_shifts_the_residual_where_it_is_heavy():
     rw = np.abs(1 - z * O.poly_eval(cw, z))
     ru = np.abs(1 - z * O.poly_eval(cu, z))
     assert np.mean(rw) < np.mean(ru)
+
+
+@pytest.mark.parametrize("mu", [1e-3, 0.05, 0.3])
+@pytest.mark.parametrize("d", [1, 3, 5])
+def test_max_zp_of_chebyshev_is_one_plus_reciprocal_t(d, mu):
+    # on [mu, 1] the Chebyshev residual r = 1 - z p(z) equioscillates between
+    # +-1/T_{d+1}(a), a = (1 + mu)/(1 - mu), and below mu it stays in (0, 1],
+    # so max z p(z) = 1 + 1/T_{d+1}(a) (the step overshoot under FISTA)
+    a = (1 + mu) / (1 - mu)
+    want = 1 + 1 / math.cosh((d + 1) * math.acosh(a))
+    assert abs(O.poly_max_zp(O.poly_coeffs_cheb(d, mu)) - want) <= 1e-6
+
+
+def test_max_zp_of_the_l2_polynomials():
+    # d = 0: z p(z) = 3z/2 peaks at z = 1; d = 1: z (4 - 10 z/3) peaks at z = 3/5
+    assert abs(O.poly_max_zp([1.5]) - 1.5) <= 1e-12
+    assert abs(O.poly_max_zp(O.poly_coeffs_l2(1)) - 1.2) <= 1e-9
