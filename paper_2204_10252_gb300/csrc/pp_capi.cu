@@ -423,45 +423,14 @@ static pp_status build_noncartesian(Plan& p, const pp_sampling* s) {
     if (flat.empty()) flat.push_back(TileEntry());
     PP_TRY(upload(p, &p.tiles, flat));
     PP_TRY(upload(p, &p.tile_start, start));
-    // G^T G as (2W-1)^2 weight planes: for every sample and every pair of its
-    // taps j, j' (offset delta = j' - j), T[delta][j] += phi_j phi_j'
-    // (accumulated in FP64, stored FP32).
+    // G^T G as (2W-1)^2 weight planes (FP64 sums of the taps' pairwise
+    // products, stored FP32), in both layouts, built on the device
     if (!p.toep) {   // (a Toeplitz plan's normal operator needs no stencil)
-        const int D = 2 * W - 1;
-        std::vector<double> T((size_t)D * D * Gx * Gy, 0.0);
-        const size_t plane = (size_t)Gx * Gy;
-        for (int k = 0; k < K; ++k) {
-            const float wx[4] = {st[k].wx.x, st[k].wx.y, st[k].wx.z, st[k].wx.w};
-            const float wy[4] = {st[k].wy.x, st[k].wy.y, st[k].wy.z, st[k].wy.w};
-            double ph[4][4];
-            int gyy[4], gxx[4];
-            for (int b = 0; b < W; ++b) {
-                gyy[b] = wrap_host(st[k].iy0 + b, Gy);
-                gxx[b] = wrap_host(st[k].ix0 + b, Gx);
-                for (int a = 0; a < W; ++a) ph[b][a] = (double)wy[b] * (double)wx[a];
-            }
-            for (int b = 0; b < W; ++b)
-                for (int a = 0; a < W; ++a) {
-                    const size_t j = (size_t)gyy[b] * Gx + gxx[a];
-                    for (int b2 = 0; b2 < W; ++b2)
-                        for (int a2 = 0; a2 < W; ++a2) {
-                            const int d = (b2 - b + W - 1) * D + (a2 - a + W - 1);
-                            T[(size_t)d * plane + j] += ph[b][a] * ph[b2][a2];
-                        }
-                }
-        }
-        std::vector<float> Tf(T.size());
-        for (size_t i = 0; i < T.size(); ++i) Tf[i] = (float)T[i];
-        PP_TRY(upload(p, &p.gtg, Tf));
-        // [row][col/8][tap][8] copy for the coil-lane kernel (zero past G_x)
-        const int nxb = (Gx + 7) / 8;
-        std::vector<float> T8((size_t)Gy * nxb * D * D * 8, 0.f);
-        for (int y = 0; y < Gy; ++y)
-            for (int x = 0; x < Gx; ++x)
-                for (int d = 0; d < D * D; ++d)
-                    T8[(((size_t)y * nxb + x / 8) * D * D + d) * 8 + (x & 7)] =
-                        Tf[(size_t)d * plane + (size_t)y * Gx + x];
-        PP_TRY(upload(p, &p.gtg8, T8));
+        const int D = 2 * W - 1, nxb = (Gx + 7) / 8;
+        PP_TRY(alloc_n(p, &p.gtg, (size_t)D * D * Gx * Gy));
+        PP_TRY(alloc_n(p, &p.gtg8, (size_t)Gy * nxb * D * D * 8));
+        PP_TRY(build_gtg_device(p, 0));
+        PP_TRY_CUDA(cudaStreamSynchronize(0));   // weights complete before any use on another stream
         PP_TRY(prepare_gtg_stencil(p));
     }
     PP_TRY(alloc_n(p, &p.wk_a, (size_t)p.C * ny * Gx));
@@ -503,7 +472,13 @@ static pp_status tune_noncartesian(Plan& p, cudaStream_t st) {
     PP_TRY_CUDA(cudaMemsetAsync(p.wk_b, 0, sizeof(float2) * (size_t)p.C * p.G_y * p.G_x, st));
     const int nx = p.nx, ny = p.ny, Gx = p.G_x;
     RowArgs ra = row_args(nx, Gx, 0, nx / 2, ny, (int64_t)ny * nx, 1.f);
-    constexpr int kRounds = 3;
+    // With the coil-innermost pipeline available the choice is made on the
+    // whole operator below, where the [coil][row][col] pipeline enters with one
+    // default launch shape per stage (it lost to the coil-innermost one on
+    // every measured shape): the per-stage sweeps, which dominate plan time,
+    // run only for plans without that pipeline.
+    const bool sweep = !p.ci_sens;
+    const int kRounds = sweep ? 3 : 0;
     std::vector<int> rows;
     for (int cl : {1, 2, 4, -1})
         if (cl != -1 || fft4_n2(Gx)) rows.push_back(cl);
@@ -526,7 +501,7 @@ static pp_status tune_noncartesian(Plan& p, cudaStream_t st) {
             }
             rbest[i] = std::min(rbest[i], ms);
         }
-    p.tune_rows_adj_cl = rows[std::min_element(rbest.begin(), rbest.end()) - rbest.begin()];
+    p.tune_rows_adj_cl = sweep ? rows[std::min_element(rbest.begin(), rbest.end()) - rbest.begin()] : 1;
     std::vector<std::pair<int, int>> sten;   // (kind, coils per CTA)
     for (int kind = 0; kind <= 6; ++kind)
         for (int cpc : {2, 4, 8, 16, 32}) {
@@ -546,8 +521,8 @@ static pp_status tune_noncartesian(Plan& p, cudaStream_t st) {
             sbest[i] = std::min(sbest[i], ms);
         }
     const size_t bi = std::min_element(sbest.begin(), sbest.end()) - sbest.begin();
-    p.tune_stencil_kind = sten[bi].first;
-    p.tune_stencil_cpc = sten[bi].second;
+    p.tune_stencil_kind = sweep ? sten[bi].first : 1;
+    p.tune_stencil_cpc = sweep ? sten[bi].second : 8;
     // whole operator: the tuned [coil][row][col] pipeline against the
     // coil-innermost one (kinds 7, 8)
     if (p.ci_sens) {
@@ -557,7 +532,7 @@ static pp_status tune_noncartesian(Plan& p, cudaStream_t st) {
                                                   {7, 1}, {7, 4}, {8, 1}, {8, 4}, {9, 1}, {9, 4}};
         PP_TRY_CUDA(cudaMemsetAsync(p.v, 0, sizeof(float2) * (size_t)p.nimg, st));
         std::vector<float> wbest(whole.size(), 1e30f);
-        for (int round = 0; round < kRounds; ++round)
+        for (int round = 0; round < 2; ++round)
             for (size_t i = 0; i < whole.size(); ++i) {
                 p.tune_stencil_kind = whole[i].first;
                 p.tune_rows_adj_cl = whole[i].second;

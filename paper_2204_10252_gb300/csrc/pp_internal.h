@@ -257,6 +257,7 @@ pp_status launch_conj_accum(const float2* s, const float2* wv, float2* out, int6
 pp_status launch_nufft_spread(const Plan& p, const float2* ksp, float2* grid_out, cudaStream_t st);
 pp_status launch_gtg_stencil(const Plan& p, const float2* grid_in, float2* grid_out, cudaStream_t st);
 pp_status prepare_gtg_stencil(Plan& p);
+pp_status build_gtg_device(Plan& p, cudaStream_t st);
 pp_status prepare_cart4();
 int c3cl_prepare(const Plan& p, int xb);
 int c3df_prepare(const Plan& p, int variant);

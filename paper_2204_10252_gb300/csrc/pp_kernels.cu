@@ -1558,6 +1558,80 @@ static pp_status rb_launch(const Plan& p, int grid, const float2* in, float2* ou
     return check_launch("gtg_stencil_rb_kernel");
 }
 
+// G^T G of the gridding pair as (2W-1)^2 weight planes, built on the device:
+// for every sample and every pair of its taps j, j' (offset d = j' - j),
+// T[d][j] += phi_j phi_j' with the products and sums in FP64 (atomic adds:
+// only the order of the additions differs from a sequential build).
+__global__ void gtg_accumulate_kernel(const SampleTaps* __restrict__ samp, int K, int Gx, int Gy,
+                                      double* __restrict__ T) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= K) return;
+    const SampleTaps s = samp[k];
+    const double wx[4] = {s.wx.x, s.wx.y, s.wx.z, s.wx.w};
+    const double wy[4] = {s.wy.x, s.wy.y, s.wy.z, s.wy.w};
+    const int64_t plane = (int64_t)Gx * Gy;
+    int gy[4], gx[4];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        int yv = (s.iy0 + b) % Gy, xv = (s.ix0 + b) % Gx;
+        gy[b] = yv < 0 ? yv + Gy : yv;
+        gx[b] = xv < 0 ? xv + Gx : xv;
+    }
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const double pj = wy[b] * wx[a];
+            double* Tj = T + (int64_t)gy[b] * Gx + gx[a];
+#pragma unroll
+            for (int b2 = 0; b2 < 4; ++b2)
+#pragma unroll
+                for (int a2 = 0; a2 < 4; ++a2)
+                    atomicAdd(Tj + (int64_t)((b2 - b + 3) * 7 + (a2 - a + 3)) * plane, pj * (wy[b2] * wx[a2]));
+        }
+}
+
+// FP32 copies of the planes: Tf[d][y][x], and T8[y][x/8][d][x%8] (zero past Gx).
+__global__ void gtg_convert_kernel(const double* __restrict__ T, int Gx, int Gy, int nxb,
+                                   float* __restrict__ Tf, float* __restrict__ T8) {
+    const int64_t plane = (int64_t)Gx * Gy, n8 = (int64_t)Gy * nxb * 49 * 8;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n8;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int xl = (int)(e & 7);
+        int64_t r = e >> 3;
+        const int d = (int)(r % 49);
+        r /= 49;
+        const int xb = (int)(r % nxb), y = (int)(r / nxb), x = xb * 8 + xl;
+        float v = 0.f;
+        if (x < Gx) {
+            const int64_t i = (int64_t)d * plane + (int64_t)y * Gx + x;
+            v = (float)T[i];
+            Tf[i] = v;
+        }
+        T8[e] = v;
+    }
+}
+
+pp_status build_gtg_device(Plan& p, cudaStream_t st) {
+    const int Gx = p.G_x, Gy = p.G_y, nxb = (Gx + 7) / 8;
+    const size_t planes = (size_t)49 * Gx * Gy;
+    double* T = nullptr;
+    PP_TRY_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&T), planes * sizeof(double), st));
+    pp_status rc = PP_OK;
+    cudaError_t e = cudaMemsetAsync(T, 0, planes * sizeof(double), st);
+    if (e == cudaSuccess) {
+        gtg_accumulate_kernel<<<(p.K + 127) / 128, 128, 0, st>>>(p.samp, p.K, Gx, Gy, T);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        gtg_convert_kernel<<<152 * 8, kThreads, 0, st>>>(T, Gx, Gy, nxb, p.gtg, p.gtg8);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) rc = cuda_status(e, "gtg build");
+    cudaFreeAsync(T, st);
+    return rc;
+}
+
 pp_status prepare_gtg_stencil(Plan& p) {
     // the register-blocked kernels index the weight planes with 32-bit offsets
     if ((int64_t)49 * p.G_x * p.G_y >= ((int64_t)1 << 31)) return PP_OK;
