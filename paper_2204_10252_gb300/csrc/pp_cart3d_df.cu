@@ -27,6 +27,13 @@
 // the error word and every CTA leaves (the host reports PP_ERR_TIMEOUT).
 // Data made by other items (W, the partial sums) is read with ld.global.cg
 // (L2, never a stale L1 line).
+// TMA variant: a block claims its next item while it starts the current one;
+// when that next item is an A item, one thread issues a tensor-map bulk copy
+// (cp.async.bulk.tensor, completion on an mbarrier) of its ny x 16 coil-map
+// tile into the spare of two shared buffers, so the map's HBM stream overlaps
+// the current item's transforms; the A item then reads the map from shared
+// memory.  The mbarrier wait is bounded in time like the dependency waits.
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -51,6 +58,11 @@ template <int N2Y, int N2Z> struct Df {
     static constexpr int LPB = (RMAX % N2Z == 0 && NY % (RMAX / N2Z) == 0) ? RMAX / N2Z : 1;
     static constexpr int YE = DN1 * RMAX * DTX;   // transpose buffer elements
     static constexpr size_t SMEM = sizeof(float2) * (YE + NY + NZ);
+    // TMA variant: two ny x 16 map tiles after the above, 1024-byte aligned
+    static constexpr size_t TILE = sizeof(float2) * NY * DTX;
+    static constexpr size_t SOFF = (SMEM + 1023) / 1024 * 1024;
+    static constexpr size_t SMEM_TMA = SOFF + 2 * TILE + 1024;   // + slack to align the base
+    static constexpr int BOXR = NY <= 256 ? NY : NY / 2;        // tensor-map box rows (<= 256)
 };
 
 struct DfArgs {
@@ -80,6 +92,32 @@ __device__ __forceinline__ unsigned long long gtimer() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
     return t;
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                 " selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+// 2-D tensor-map tile load into shared memory, completing on `bar`
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int c0, int c1, uint64_t* bar) {
+    asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+                 " [%0], [%1, {%2, %3}], [%4];\n"
+                 ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1),
+                   "r"(smem_u32(bar))
+                 : "memory");
 }
 
 // Block-wide: wait until *cnt >= target (thread 0 polls).  Returns false when
@@ -114,9 +152,9 @@ __device__ __forceinline__ void df_signal(int* cnt) {
     if (threadIdx.x == 0) red_release_add(cnt, 1);
 }
 
-template <int N2Y, int N2Z, int MB>
+template <int N2Y, int N2Z, int MB, bool TMA>
 __global__ void __launch_bounds__(Df<N2Y, N2Z>::THREADS, MB)
-c3_dataflow_kernel(DfArgs a) {
+c3_dataflow_kernel(DfArgs a, const __grid_constant__ CUtensorMap tmS) {
     constexpr int NY = Df<N2Y, N2Z>::NY, NZ = Df<N2Y, N2Z>::NZ, LPB = Df<N2Y, N2Z>::LPB;
     constexpr int NBI = NY / LPB;   // B items per coil
     extern __shared__ float4 df_sm4[];
@@ -124,6 +162,25 @@ c3_dataflow_kernel(DfArgs a) {
     float2* twy = Y + Df<N2Y, N2Z>::YE;
     float2* twz = twy + NY;
     __shared__ int s_item;
+    // TMA variant: two map-tile buffers (1024-byte aligned), their mbarriers,
+    // the item each holds (-1: none) and each barrier's phase
+    __shared__ __align__(8) uint64_t s_bar[2];
+    __shared__ int s_pref[2], s_pending[2];
+    float2* Sb = nullptr;
+    if (TMA) {
+        const uint32_t base = smem_u32(df_sm4) + (uint32_t)Df<N2Y, N2Z>::SOFF;
+        Sb = reinterpret_cast<float2*>(reinterpret_cast<char*>(df_sm4) + Df<N2Y, N2Z>::SOFF +
+                                       ((1024u - (base & 1023u)) & 1023u));
+        if (threadIdx.x == 0) {
+            mbar_init(&s_bar[0]);
+            mbar_init(&s_bar[1]);
+            s_pref[0] = s_pref[1] = -1;
+            s_pending[0] = s_pending[1] = 0;
+            asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        }
+    }
+    uint32_t phase[2] = {0u, 0u};
+    int iter = 0;
     for (int i = threadIdx.x; i < NY; i += blockDim.x) twy[i] = a.twy[i];
     for (int i = threadIdx.x; i < NZ; i += blockDim.x) twz[i] = a.twz[i];
     const int lane = threadIdx.x % DTX, r = threadIdx.x / DTX;
@@ -141,11 +198,45 @@ c3_dataflow_kernel(DfArgs a) {
     const int64_t plane = (int64_t)NY * a.nx, vol = (int64_t)NZ * plane;
     if (threadIdx.x == 0) s_item = atomicAdd(next, 1);
     __syncthreads();
+    // TMA: the A item `it` (if it is one) -> its map tile's coordinates
+    auto a_tile = [&](int it, int* cx, int* cy) -> bool {
+        if (it >= total) return false;
+        const int bb = it / per_blk;
+        int q = it - bb * per_blk;
+        const int gg = min(q / per_full, a.ng - 1);
+        q -= gg * per_full;
+        const int cgg = (gg == a.ng - 1) ? cg_last : a.CG;
+        if (q >= cgg * NZ) return false;
+        const int cc = q / NZ, zz = q - cc * NZ;
+        *cx = bb * DTX;
+        *cy = ((gg * a.CG + cc) * NZ + zz) * NY;
+        return true;
+    };
+    auto issue = [&](int it, int buf) {   // thread 0 only
+        int cx, cy;
+        if (!a_tile(it, &cx, &cy)) return;
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");   // earlier reads of the buffer
+        mbar_expect_tx(&s_bar[buf], (uint32_t)Df<N2Y, N2Z>::TILE);
+        for (int h = 0; h < NY / Df<N2Y, N2Z>::BOXR; ++h)
+            tma_load_2d(Sb + buf * NY * DTX + h * Df<N2Y, N2Z>::BOXR * DTX, &tmS, cx,
+                        cy + h * Df<N2Y, N2Z>::BOXR, &s_bar[buf]);
+        s_pref[buf] = it;
+        s_pending[buf] = 1;
+    };
     for (;;) {
         const int item = s_item;
         // block-uniform stop test; the barrier also ends every read of s_item
         if (__syncthreads_or(item >= total || (threadIdx.x == 0 && *(volatile int*)err))) break;
-        if (threadIdx.x == 0) s_item = atomicAdd(next, 1);   // claim the next one early
+        const int cur_buf = iter & 1;
+        if (threadIdx.x == 0) {
+            const int nxt = atomicAdd(next, 1);   // claim the next one early
+            s_item = nxt;
+            if (TMA) {
+                if (s_pref[cur_buf] != item) issue(item, cur_buf);   // not prefetched: load it now
+                issue(nxt, cur_buf ^ 1);   // the next item's map tile, if it is an A item
+            }
+        }
+        ++iter;
         // ---- decode (x-block b, group g, kind, index)
         const int b = item / per_blk;
         int rr = item - b * per_blk;
@@ -163,12 +254,35 @@ c3_dataflow_kernel(DfArgs a) {
             if (k >= 2 && !df_wait(cntC + (k - 2), NZ, err)) break;
             const float2* Sc = a.S + (int64_t)(c0 + c) * vol + (int64_t)z * plane;
             const float2* xz = a.x + (int64_t)z * plane;
+            const float2* St = nullptr;
+            if (TMA) {
+                // the tile is in Sb[cur_buf] (issued now or one item ago): bounded wait
+                int good = 1;
+                if (threadIdx.x == 0) {
+                    if (!mbar_try_wait(&s_bar[cur_buf], phase[cur_buf])) {
+                        const unsigned long long t0 = gtimer();
+                        while (!mbar_try_wait(&s_bar[cur_buf], phase[cur_buf])) {
+                            if (gtimer() - t0 > kWaitNs) {
+                                atomicExch(err, 1);
+                                good = 0;
+                                break;
+                            }
+                        }
+                    }
+                }
+                if (!__syncthreads_and(good)) break;
+                mbar_try_wait(&s_bar[cur_buf], phase[cur_buf]);   // this thread's acquire of the tile
+                phase[cur_buf] ^= 1u;
+                if (threadIdx.x == 0) s_pending[cur_buf] = 0;
+                St = Sb + cur_buf * NY * DTX;
+            }
             if (r < N2Y) {
                 float2 v[DN1];
 #pragma unroll
                 for (int m1 = 0; m1 < DN1; ++m1) {
                     const int64_t o = (int64_t)(N2Y * m1 + r) * a.nx + col;
-                    v[m1] = ok ? cmul(__ldg(Sc + o), __ldg(xz + o)) : make_float2(0.f, 0.f);
+                    const float2 sv = TMA ? St[(N2Y * m1 + r) * DTX + lane] : (ok ? __ldg(Sc + o) : make_float2(0.f, 0.f));
+                    v[m1] = ok ? cmul(sv, __ldg(xz + o)) : make_float2(0.f, 0.f);
                 }
                 fft4_phase1<DN1, N2Y, false>(v, r, twy);
 #pragma unroll
@@ -297,19 +411,27 @@ c3_dataflow_kernel(DfArgs a) {
         }
         __syncthreads();   // s_item (the claim made at the top) is visible
     }
+    if (TMA && threadIdx.x == 0) {
+        // after an early exit, wait (bounded) for this block's copies still in flight
+        for (int b2 = 0; b2 < 2; ++b2) {
+            if (!s_pending[b2]) continue;
+            const unsigned long long t0 = gtimer();
+            while (!mbar_try_wait(&s_bar[b2], phase[b2]) && gtimer() - t0 < kWaitNs) {
+            }
+        }
+    }
 }
 
-template <int N2Y, int N2Z, int MB>
+template <int N2Y, int N2Z, int MB, bool TMA>
 int df_resident() {
-    auto fn = c3_dataflow_kernel<N2Y, N2Z, MB>;
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)Df<N2Y, N2Z>::SMEM) != cudaSuccess) {
+    auto fn = c3_dataflow_kernel<N2Y, N2Z, MB, TMA>;
+    const size_t smem = TMA ? Df<N2Y, N2Z>::SMEM_TMA : Df<N2Y, N2Z>::SMEM;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
     int per_sm = 0, dev = 0, sms = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, Df<N2Y, N2Z>::THREADS,
-                                                      Df<N2Y, N2Z>::SMEM) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, Df<N2Y, N2Z>::THREADS, smem) != cudaSuccess ||
         cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
         cudaGetLastError();
@@ -339,17 +461,49 @@ template <int N2Y, int N2Z> constexpr int df_mb(int v) {
     return Df<N2Y, N2Z>::THREADS <= 256 ? (v ? 3 : 2) : 1;
 }
 
-// Resident CTAs of the dataflow kernel (variant v) for this plan's (ny, nz),
-// 0 when the kernel does not apply (a length without a register FFT).
+// Resident CTAs of the dataflow kernel (variant v: 0 two blocks per SM, 1
+// three, 2 TMA-staged map tiles) for this plan's (ny, nz), 0 when the kernel
+// does not apply (a length without a register FFT).
 int c3df_prepare(const Plan& p, int v) {
     if (p.kind != PP_CARTESIAN || p.ndim != 3) return 0;
     const int n2y = fft4_n2(p.ny), n2z = fft4_n2(p.nz);
 #define PP_DF_PREP(Y_, Z_)                                                           \
     if (n2y == Y_ && n2z == Z_)                                                      \
-        return v ? df_resident<Y_, Z_, df_mb<Y_, Z_>(1)>() : df_resident<Y_, Z_, df_mb<Y_, Z_>(0)>();
+        return v == 2 ? df_resident<Y_, Z_, df_mb<Y_, Z_>(0), true>()                \
+                      : (v ? df_resident<Y_, Z_, df_mb<Y_, Z_>(1), false>()          \
+                           : df_resident<Y_, Z_, df_mb<Y_, Z_>(0), false>());
     PP_DF_CASES(PP_DF_PREP)
 #undef PP_DF_PREP
     return 0;
+}
+
+// The coil maps as a 2-D tensor map for the TMA variant: [C nz ny] rows of nx
+// 8-byte elements, boxes of 16 columns x BOXR rows (BOXR = ny, or ny/2 when
+// ny > 256); columns past nx read as zero.  false when the driver entry
+// point or the encoding is unavailable (the variant is then not offered).
+bool c3df_make_tensor_map(Plan& p) {
+    using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
+                                CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                CUtensorMapFloatOOBfill);
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) {
+        cudaGetLastError();
+        return false;
+    }
+    if ((p.nx * 8) % 16 || ((uintptr_t)p.sens & 15)) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)p.nx, (cuuint64_t)p.C * p.nz * p.ny};
+    const cuuint64_t strides[1] = {(cuuint64_t)p.nx * 8};
+    const cuuint32_t box[2] = {(cuuint32_t)DTX, (cuuint32_t)(p.ny <= 256 ? p.ny : p.ny / 2)};
+    const cuuint32_t estr[2] = {1, 1};
+    if (box[1] > 256 || p.ny % box[1]) return false;
+    const CUresult r = reinterpret_cast<Encode>(fn)(
+        &p.c3df_tmS, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<float2*>(p.sens), dims, strides, box,
+        estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
 }
 
 size_t c3df_slot_elems(const Plan& p, int cg) { return (size_t)cg * p.nz * p.ny * DTX; }
@@ -375,8 +529,8 @@ pp_status c3df_normal(const Plan& p, const float2* x, float2* out, float scale,
     const int n2y = fft4_n2(p.ny), n2z = fft4_n2(p.nz);
     const int per_full = cg * (p.nz + p.ny) + p.nz;   // an upper bound on the items of a phase
     const int64_t total = (int64_t)a.nb * a.ng * per_full;
-    const int v = p.c3df_hi ? 1 : 0;
-    const int ctas = v ? p.c3df_ctas_hi : p.c3df_ctas;
+    const int v = p.c3df_hi;
+    const int ctas = v == 2 ? p.c3df_ctas_tma : (v ? p.c3df_ctas_hi : p.c3df_ctas);
     if (ctas <= 0) {
         set_error("c3df_normal: this dataflow variant cannot be resident on the device");
         return PP_ERR_UNSUPPORTED;
@@ -385,10 +539,15 @@ pp_status c3df_normal(const Plan& p, const float2* x, float2* out, float scale,
     cudaError_t e = cudaErrorInvalidValue;
 #define PP_DF_LAUNCH(Y_, Z_)                                                                    \
     if (n2y == Y_ && n2z == Z_)                                                                 \
-        e = v ? launch_ex(c3_dataflow_kernel<Y_, Z_, df_mb<Y_, Z_>(1)>, dim3(grid),             \
-                          dim3(Df<Y_, Z_>::THREADS), Df<Y_, Z_>::SMEM, st, false, 0, a)         \
-              : launch_ex(c3_dataflow_kernel<Y_, Z_, df_mb<Y_, Z_>(0)>, dim3(grid),             \
-                          dim3(Df<Y_, Z_>::THREADS), Df<Y_, Z_>::SMEM, st, false, 0, a);
+        e = v == 2 ? launch_ex(c3_dataflow_kernel<Y_, Z_, df_mb<Y_, Z_>(0), true>, dim3(grid),  \
+                               dim3(Df<Y_, Z_>::THREADS), Df<Y_, Z_>::SMEM_TMA, st, false, 0, a, \
+                               p.c3df_tmS)                                                      \
+            : v ? launch_ex(c3_dataflow_kernel<Y_, Z_, df_mb<Y_, Z_>(1), false>, dim3(grid),    \
+                            dim3(Df<Y_, Z_>::THREADS), Df<Y_, Z_>::SMEM, st, false, 0, a,       \
+                            p.c3df_tmS)                                                         \
+                : launch_ex(c3_dataflow_kernel<Y_, Z_, df_mb<Y_, Z_>(0), false>, dim3(grid),    \
+                            dim3(Df<Y_, Z_>::THREADS), Df<Y_, Z_>::SMEM, st, false, 0, a,       \
+                            p.c3df_tmS);
     PP_DF_CASES(PP_DF_LAUNCH)
 #undef PP_DF_LAUNCH
     if (e != cudaSuccess) return cuda_status(e, "c3_dataflow_kernel launch");

@@ -1,5 +1,6 @@
 // Internal declarations shared by the libpp translation units.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -188,7 +189,9 @@ struct Plan {
     // 3-D dataflow operator (one persistent kernel per apply, pp_cart3d_df.cu)
     int c3df_ctas = 0;          // resident CTAs (0: not available for this plan)
     int c3df_ctas_hi = 0;       //   the same for the variant with three blocks per SM
-    int c3df_hi = 0;            // 1: run that variant
+    int c3df_ctas_tma = 0;      //   the same for the variant that stages map tiles by TMA
+    int c3df_hi = 0;            // variant: 0 two blocks per SM, 1 three, 2 TMA-staged map tiles
+    CUtensorMap c3df_tmS;       // the coil maps as a 2-D tensor [C nz ny][nx] of 8-byte elements
     int c3df_cg = 4;            // coils per group
     float2* c3df_w = nullptr;   // two phase slots
     size_t c3df_w_elems = 0;
@@ -261,6 +264,7 @@ pp_status build_gtg_device(Plan& p, cudaStream_t st);
 pp_status prepare_cart4();
 int c3cl_prepare(const Plan& p, int xb);
 int c3df_prepare(const Plan& p, int variant);
+bool c3df_make_tensor_map(Plan& p);
 size_t c3df_slot_elems(const Plan& p, int cg);
 size_t c3df_counter_ints(const Plan& p, int cg);
 pp_status c3df_normal(const Plan& p, const float2* x, float2* out, float scale,
