@@ -16,10 +16,14 @@
 // then C, coil-major), and a CTA takes the next number from a global counter
 // once it has finished its current item, so every item waits only on items
 // with smaller numbers that running CTAs hold:
-//   A(k)      after C(k-2)  (slot reuse)
-//   B(k, c)   after all A(k, c)
-//   C(k, z)   after all B(k, c) of each coil c, and after C(k-1) (the partial
-//             sum in `out`) when g > 0
+//   A(k, c, z) after C(k-2, z)  (slot reuse: plane z of the slot is free once
+//                                that item, which itself waited for every
+//                                B item of phase k-2, is done)
+//   B(k, c)    after all A(k, c)
+//   C(k, z)    after all B(k, c) of each coil c, and after C(k-1, z) (the
+//              partial sum of plane z in `out`) when g > 0
+// The cross-phase waits are per z plane, so consecutive coil groups of an
+// x-block overlap instead of running their C items one group after another.
 // The smallest unfinished number is therefore always runnable, and the HBM
 // stream of phase k+1's maps (A items) overlaps phase k's transforms.
 // Completion is counted per (phase, coil) with release atomics; a wait is an
@@ -75,7 +79,7 @@ struct DfArgs {
     const float2* twy;
     const float2* twz;
     float2* W;              // 2 slots of CG * nz * ny * 16
-    int* cnt;               // cntA[P*CG], cntB[P*CG], cntC[P], next, err
+    int* cnt;               // cntA[P*CG], cntB[P*CG], cntCz[P*NZ], next, err
     int nx, C, CG, ng, nb;
     int64_t slot;           // elements per slot
 };
@@ -187,8 +191,8 @@ c3_dataflow_kernel(DfArgs a, const __grid_constant__ CUtensorMap tmS) {
     const int P = a.nb * a.ng;
     int* cntA = a.cnt;
     int* cntB = cntA + (int64_t)P * a.CG;
-    int* cntC = cntB + (int64_t)P * a.CG;
-    int* next = cntC + P;
+    int* cntCz = cntB + (int64_t)P * a.CG;   // [phase][z]: C item done
+    int* next = cntCz + (int64_t)P * NZ;
     int* err = next + 1;
     const int cg_last = a.C - (a.ng - 1) * a.CG;
     const int per_full = a.CG * (NZ + NBI) + NZ;
@@ -251,7 +255,7 @@ c3_dataflow_kernel(DfArgs a, const __grid_constant__ CUtensorMap tmS) {
         if (rr < cg * NZ) {
             // ---- A (c, z): y FFT of S_c x on plane z -> W[c][z][ky]
             const int c = rr / NZ, z = rr - c * NZ;
-            if (k >= 2 && !df_wait(cntC + (k - 2), NZ, err)) break;
+            if (k >= 2 && !df_wait(cntCz + (int64_t)(k - 2) * NZ + z, 1, err)) break;
             const float2* Sc = a.S + (int64_t)(c0 + c) * vol + (int64_t)z * plane;
             const float2* xz = a.x + (int64_t)z * plane;
             const float2* St = nullptr;
@@ -391,7 +395,7 @@ c3_dataflow_kernel(DfArgs a, const __grid_constant__ CUtensorMap tmS) {
                 __syncthreads();   // Y is rewritten by the next coil
             }
             if (!alive) break;
-            if (g > 0 && !df_wait(cntC + (k - 1), NZ, err)) break;
+            if (g > 0 && !df_wait(cntCz + (int64_t)(k - 1) * NZ + z, 1, err)) break;
             if (r < DN1 && ok) {
                 float2* oz = a.out + (int64_t)z * plane + col;
                 const bool last = g == a.ng - 1;
@@ -407,7 +411,7 @@ c3_dataflow_kernel(DfArgs a, const __grid_constant__ CUtensorMap tmS) {
                     __stcg(oz + o, v);
                 }
             }
-            df_signal(cntC + k);
+            df_signal(cntCz + (int64_t)k * NZ + z);
         }
         __syncthreads();   // s_item (the claim made at the top) is visible
     }
@@ -509,7 +513,7 @@ bool c3df_make_tensor_map(Plan& p) {
 size_t c3df_slot_elems(const Plan& p, int cg) { return (size_t)cg * p.nz * p.ny * DTX; }
 size_t c3df_counter_ints(const Plan& p, int cg) {
     const int nb = (p.nx + DTX - 1) / DTX, ng = (p.C + cg - 1) / cg;
-    return (size_t)nb * ng * (2 * (size_t)cg + 1) + 2;
+    return (size_t)nb * ng * (2 * (size_t)cg + p.nz) + 2;
 }
 
 pp_status c3df_normal(const Plan& p, const float2* x, float2* out, float scale,
