@@ -65,6 +65,9 @@ def parse():
     ap.add_argument("--apply-only", type=int, default=0, metavar="K",
                     help="profiling aid: build the workload's plan (no power iteration), apply "
                          "its operator K times and exit without a bench line")
+    ap.add_argument("--apply-coils", type=int, default=4, metavar="C",
+                    help="with --apply-only on the 3-D workload: how many of its coils the "
+                         "capture case keeps (default 4; 32 is the whole workload, 2 GiB of maps)")
     ap.add_argument("--tuning", default="",
                     help="with --apply-only: row_ifft_variant,stencil_kind,stencil_coils to force "
                          "(batched2d_64: the batch tile code)")

@@ -247,7 +247,8 @@ def unrolled(args, pp, rank, world, local):
 def apply_only(args, pp, local):
     """Profiling aid (--apply-only K): the workload's operator K times, no
     bench line.  cart2d: K normal applies; cart3d: the workload's volume with
-    4 of its coils (a capture small enough for ncu), K normal applies, then K
+    --apply-coils of its coils (4 by default: a capture small enough for
+    ncu), K normal applies, then K
     3-D Haar prox calls; batched2d_64: K batched normal applies (--tuning T
     forces the batch tile code T)."""
     dev = torch.device("cuda", local)
@@ -274,7 +275,7 @@ def apply_only(args, pp, local):
     c = dict(synth.CONFIGS[args.workload])
     shape, C = c["shape"], c["coils"]
     if len(shape) == 3:
-        C = min(C, 4)
+        C = min(C, max(1, args.apply_coils))
     sens = torch.from_numpy(synth.coil_maps(shape, C, c["seed"])).to(dev)
     mask = (synth.line_mask(shape, c["R"], c["acs"], c["seed"]) if len(shape) == 2 else
             synth.poisson_disc_mask(shape, c["R"], c["calib"], c["seed"]))

@@ -124,6 +124,50 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
                  : "memory");
 }
 
+// L2 residency.  W (two slots) is written and re-read four times per element
+// within about one phase, while the maps stream through: W's accesses carry
+// an evict_last policy, the C items' map reads (the maps' last use) an
+// evict_first one.  kDfL2: 0 no hints, 1 W evict_last, 2 C maps evict_first,
+// 3 both.
+constexpr int kDfL2 = 2;
+__device__ __forceinline__ uint64_t l2_policy_last() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;\n" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ uint64_t l2_policy_first() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;\n" : "=l"(pol));
+    return pol;
+}
+// W element store / load (L2 only, never L1: other blocks produce and consume W)
+__device__ __forceinline__ void w_store(float2* p, float2 v, uint64_t pol) {
+    if (kDfL2 & 1)
+        asm volatile("st.global.cg.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;\n"
+                     ::"l"(p), "f"(v.x), "f"(v.y), "l"(pol) : "memory");
+    else
+        __stcg(p, v);
+}
+__device__ __forceinline__ float2 w_load(const float2* p, uint64_t pol) {
+    float2 v;
+    if (kDfL2 & 1)
+        asm volatile("ld.global.cg.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;\n"
+                     : "=f"(v.x), "=f"(v.y) : "l"(p), "l"(pol) : "memory");
+    else
+        v = __ldcg(p);
+    return v;
+}
+// read-only map element at its last use in the apply
+__device__ __forceinline__ float2 s_load_last(const float2* p, uint64_t pol) {
+    float2 v;
+    if (kDfL2 & 2)
+        asm("ld.global.nc.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;\n"
+            : "=f"(v.x), "=f"(v.y) : "l"(p), "l"(pol));
+    else
+        v = __ldg(p);
+    return v;
+}
+
 // Block-wide: wait until *cnt >= target (thread 0 polls).  Returns false when
 // the error word is set (by this wait's time limit or by another CTA).
 __device__ __forceinline__ bool df_wait(const int* cnt, int target, int* err,
@@ -185,6 +229,7 @@ c3_dataflow_kernel(DfArgs a, const __grid_constant__ CUtensorMap tmS) {
     }
     uint32_t phase[2] = {0u, 0u};
     int iter = 0;
+    const uint64_t pol_w = l2_policy_last(), pol_s = l2_policy_first();
     for (int i = threadIdx.x; i < NY; i += blockDim.x) twy[i] = a.twy[i];
     for (int i = threadIdx.x; i < NZ; i += blockDim.x) twz[i] = a.twz[i];
     const int lane = threadIdx.x % DTX, r = threadIdx.x / DTX;
@@ -300,7 +345,7 @@ c3_dataflow_kernel(DfArgs a, const __grid_constant__ CUtensorMap tmS) {
                 fft4_phase2<DN1, N2Y, false>(u, twy);
                 float2* Wz = Wk + ((int64_t)(c * NZ + z) * NY) * DTX + lane;
 #pragma unroll
-                for (int k2 = 0; k2 < N2Y; ++k2) __stcg(Wz + (r + DN1 * k2) * DTX, u[k2]);
+                for (int k2 = 0; k2 < N2Y; ++k2) w_store(Wz + (r + DN1 * k2) * DTX, u[k2], pol_w);
             }
             df_signal(cntA + (int64_t)k * a.CG + c);
         } else if (rr < cg * (NZ + NBI)) {
@@ -318,7 +363,7 @@ c3_dataflow_kernel(DfArgs a, const __grid_constant__ CUtensorMap tmS) {
                 const float2* Wl = Wc + (ky0 + l1) * DTX;
                 float2 v[DN1];
 #pragma unroll
-                for (int m1 = 0; m1 < DN1; ++m1) v[m1] = __ldcg(Wl + (int64_t)(N2Z * m1 + m2r) * ZS);
+                for (int m1 = 0; m1 < DN1; ++m1) v[m1] = w_load(Wl + (int64_t)(N2Z * m1 + m2r) * ZS, pol_w);
                 fft4_phase1<DN1, N2Z, false>(v, m2r, twz);
 #pragma unroll
                 for (int k1 = 0; k1 < DN1; ++k1) Y[l1 * YL + (k1 * N2Z + m2r) * DTX + lane] = v[k1];
@@ -357,7 +402,7 @@ c3_dataflow_kernel(DfArgs a, const __grid_constant__ CUtensorMap tmS) {
                 for (int k1 = 0; k1 < DN1; ++k1) v[k1] = Y[l1 * YL + (k1 * N2Z + m2r) * DTX + lane];
                 RegFft<DN1, true>::run(v, twz, N2Z);
 #pragma unroll
-                for (int m1 = 0; m1 < DN1; ++m1) __stcg(Wl + (int64_t)(N2Z * m1 + m2r) * ZS, v[m1]);
+                for (int m1 = 0; m1 < DN1; ++m1) w_store(Wl + (int64_t)(N2Z * m1 + m2r) * ZS, v[m1], pol_w);
             }
             df_signal(cntB + (int64_t)k * a.CG + c);
         } else {
@@ -376,7 +421,7 @@ c3_dataflow_kernel(DfArgs a, const __grid_constant__ CUtensorMap tmS) {
                 if (r < N2Y) {
                     float2 v[DN1];
 #pragma unroll
-                    for (int m1 = 0; m1 < DN1; ++m1) v[m1] = __ldcg(Wz + (N2Y * m1 + r) * DTX);
+                    for (int m1 = 0; m1 < DN1; ++m1) v[m1] = w_load(Wz + (N2Y * m1 + r) * DTX, pol_w);
                     fft4_phase1<DN1, N2Y, true>(v, r, twy);
 #pragma unroll
                     for (int k1 = 0; k1 < DN1; ++k1) Y[(k1 * N2Y + r) * DTX + lane] = v[k1];
@@ -390,7 +435,7 @@ c3_dataflow_kernel(DfArgs a, const __grid_constant__ CUtensorMap tmS) {
                     const float2* Sc = a.S + (int64_t)(c0 + c) * vol + (int64_t)z * plane + col;
 #pragma unroll
                     for (int k2 = 0; k2 < N2Y; ++k2)
-                        acc[k2] = cadd(acc[k2], cmulc(__ldg(Sc + (int64_t)(r + DN1 * k2) * a.nx), u[k2]));
+                        acc[k2] = cadd(acc[k2], cmulc(s_load_last(Sc + (int64_t)(r + DN1 * k2) * a.nx, pol_s), u[k2]));
                 }
                 __syncthreads();   // Y is rewritten by the next coil
             }
