@@ -678,6 +678,7 @@ static pp_status setup_ci(Plan& p, cudaStream_t st) {
         PP_TRY(alloc_n(p, &p.ci_b, ci_grid_elems(p)));
         PP_TRY(alloc_n(p, &p.ci_c, ci_grid_elems(p)));
     }
+    PP_TRY(alloc_n(p, &p.ci_tile_nz, ci_stencil_tiles(p)));
     return ci_prepare(p, st);
 }
 

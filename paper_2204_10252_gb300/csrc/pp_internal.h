@@ -148,6 +148,7 @@ struct Plan {
     // coil-innermost pipeline ([row][col][32 coils]; ci_a/b/c alias wk_a/b/c when C = 32)
     float2* ci_sens = nullptr;   // [ny][nx][32]
     float2 *ci_a = nullptr, *ci_b = nullptr, *ci_c = nullptr;
+    int* ci_tile_nz = nullptr;   // per 16 x 8 stencil tile: any G^T G weight nonzero
     float2* ci_part = nullptr;   // [4][ny][nx] coil-block partial sums
     // Toeplitz-embedded normal operator (exact F^H F on the 2ny x 2nx circulant)
     int toep = 0;                // 1: the normal operator takes the Toeplitz path
@@ -277,6 +278,7 @@ pp_status c3cl_normal(const Plan& p, int xb, const float2* x, float2* out, float
                       const float2* operand, float alpha, cudaStream_t st);
 bool ci_supported(const Plan& p);
 size_t ci_grid_elems(const Plan& p);
+size_t ci_stencil_tiles(const Plan& p);
 size_t ci_rows_elems(const Plan& p);
 size_t ci_sens_elems(const Plan& p);
 size_t ci_partial_elems(const Plan& p);

@@ -263,8 +263,26 @@ constexpr int CPS_TX = 16, CPS_TY = 8, CPS_HX = CPS_TX + 6, CPS_HY = CPS_TY + 6;
 constexpr size_t CPS_HALO = sizeof(float2) * CPS_HY * CPS_HX * CP;
 constexpr size_t CPS_SMEM = CPS_HALO + sizeof(float) * CPS_TY * CPS_TX * 49;
 
+// Tiles whose 16 x 8 points carry no G^T G weight (grid points that no
+// sample's kernel reaches: the corners outside the trajectory's disc) have an
+// exactly zero output; tile_nz marks the others (null: every tile is live).
+__global__ void __launch_bounds__(256)
+ci_tile_flags_kernel(const float* __restrict__ T8, int Gx, int Gy, int nxb, int* __restrict__ tile_nz) {
+    const int ntx = (Gx + CPS_TX - 1) / CPS_TX;
+    const int tx0 = (blockIdx.x % ntx) * CPS_TX, ty0 = (blockIdx.x / ntx) * CPS_TY;
+    const int xb0 = tx0 / 8;
+    int any = 0;
+    for (int e = threadIdx.x; e < CPS_TY * 784; e += blockDim.x) {
+        const int yy = e / 784, rem = e - yy * 784, s = rem / 392;
+        const int y = ty0 + yy;
+        if (y < Gy && xb0 + s < nxb && T8[((int64_t)y * nxb + xb0) * 392 + rem] != 0.f) any = 1;
+    }
+    any = __syncthreads_or(any);
+    if (threadIdx.x == 0) tile_nz[blockIdx.x] = any;
+}
+
 __global__ void __launch_bounds__(256, 2)
-ci_stencil_cp_kernel(const float* __restrict__ T8, int Gx, int Gy, int nxb,
+ci_stencil_cp_kernel(const float* __restrict__ T8, int Gx, int Gy, int nxb, const int* __restrict__ tile_nz,
                      const float2* __restrict__ in, float2* __restrict__ out) {
     constexpr int D = 7, H = 3;
     extern __shared__ float4 sm4[];
@@ -273,6 +291,18 @@ ci_stencil_cp_kernel(const float* __restrict__ T8, int Gx, int Gy, int nxb,
     const int ntx = (Gx + CPS_TX - 1) / CPS_TX;
     const int tx0 = (blockIdx.x % ntx) * CPS_TX, ty0 = (blockIdx.x / ntx) * CPS_TY;
     pdl_trigger();
+    if (tile_nz && !tile_nz[blockIdx.x]) {
+        // no weight in the tile: its output is zero (written once the
+        // predecessor is done, like every other store of this kernel)
+        pdl_wait();
+        for (int e = threadIdx.x; e < CPS_TY * CPS_TX * 16; e += blockDim.x) {
+            const int pt = e >> 4, q = e & 15;
+            const int gy = ty0 + pt / CPS_TX, gx = tx0 + pt % CPS_TX;
+            if (gy < Gy && gx < Gx)
+                reinterpret_cast<float4*>(out)[((int64_t)gy * Gx + gx) * 16 + q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        return;
+    }
     const int xb0 = tx0 / 8;
     for (int e = threadIdx.x; e < CPS_TY * 196; e += blockDim.x) {
         const int yy = e / 196, rem = e - yy * 196, s = rem / 98;
@@ -822,6 +852,9 @@ bool ci_supported(const Plan& p) {
 }
 
 size_t ci_grid_elems(const Plan& p) { return (size_t)p.G_y * p.G_x * CP; }
+size_t ci_stencil_tiles(const Plan& p) {
+    return (size_t)((p.G_x + CPS_TX - 1) / CPS_TX) * ((p.G_y + CPS_TY - 1) / CPS_TY);
+}
 size_t ci_rows_elems(const Plan& p) { return (size_t)p.ny * p.G_x * CP; }
 size_t ci_sens_elems(const Plan& p) { return (size_t)p.ny * p.nx * CP; }
 size_t ci_partial_elems(const Plan& p) { return (size_t)NCB * p.ny * p.nx; }
@@ -835,7 +868,13 @@ pp_status ci_prepare(Plan& p, cudaStream_t st) {
                                      (int)CPS_SMEM));
     const int64_t n = (int64_t)p.ny * p.nx;
     ci_pack_sens_kernel<<<152 * 4, 256, 0, st>>>(p.sens, p.C, n, p.ci_sens);
-    return check_ci("ci_pack_sens_kernel");
+    PP_TRY(check_ci("ci_pack_sens_kernel"));
+    if (p.ci_tile_nz && p.gtg8) {
+        ci_tile_flags_kernel<<<(unsigned)ci_stencil_tiles(p), 256, 0, st>>>(p.gtg8, p.G_x, p.G_y,
+                                                                           (p.G_x + 7) / 8, p.ci_tile_nz);
+        PP_TRY(check_ci("ci_tile_flags_kernel"));
+    }
+    return PP_OK;
 }
 
 // out = scale * A^H A x + alpha * operand on the coil-innermost buffers
@@ -870,7 +909,7 @@ pp_status ci_normal(const Plan& p, const float2* x, float2* out, float scale, co
         PP_TRY_CUDA(launch_ex(ci_stencil_cp_kernel,
                               dim3(((Gx + CPS_TX - 1) / CPS_TX) * ((Gy + CPS_TY - 1) / CPS_TY)), dim3(256),
                               CPS_SMEM, st, pdl, 0, (const float*)p.gtg8, Gx, Gy, (Gx + 7) / 8,
-                              (const float2*)p.ci_b, p.ci_c));
+                              (const int*)p.ci_tile_nz, (const float2*)p.ci_b, p.ci_c));
     else if (ry == 2)
         PP_TRY_CUDA(launch_ex(ci_stencil_kernel<2>, dim3(ntiles), dim3(256), CiStencil<2>::SMEM, st,
                               pdl, 0, (const float*)p.gtg8, Gx, Gy, (Gx + 7) / 8,
