@@ -52,6 +52,7 @@ namespace {
 constexpr int DN1 = 16;   // first factor of every register FFT
 constexpr int DTX = 16;   // x columns per item
 constexpr unsigned long long kWaitNs = 1000000000ull;   // 1 s bound on one wait
+constexpr int kClaimT = 32;   // the thread (warp 1) that claims items and issues tile copies
 
 template <int N2Y, int N2Z> struct Df {
     static constexpr int NY = 16 * N2Y, NZ = 16 * N2Z;
@@ -168,6 +169,16 @@ __device__ __forceinline__ float2 s_load_last(const float2* p, uint64_t pol) {
     return v;
 }
 
+// the same with an L2 eviction policy (createpolicy) for the loaded lines
+__device__ __forceinline__ void tma_load_2d_hint(void* dst, const CUtensorMap* map, int c0, int c1, uint64_t* bar,
+                                                 uint64_t pol) {
+    asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+                 " [%0], [%1, {%2, %3}], [%4], %5;\n"
+                 ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1),
+                   "r"(smem_u32(bar)), "l"(pol)
+                 : "memory");
+}
+
 // Block-wide: wait until *cnt >= target (thread 0 polls).  Returns false when
 // the error word is set (by this wait's time limit or by another CTA).
 __device__ __forceinline__ bool df_wait(const int* cnt, int target, int* err,
@@ -245,7 +256,7 @@ c3_dataflow_kernel(DfArgs a, const __grid_constant__ CUtensorMap tmS) {
     const int per_blk = (a.ng - 1) * per_full + per_last;
     const int total = a.nb * per_blk;
     const int64_t plane = (int64_t)NY * a.nx, vol = (int64_t)NZ * plane;
-    if (threadIdx.x == 0) s_item = atomicAdd(next, 1);
+    if (threadIdx.x == kClaimT) s_item = atomicAdd(next, 1);
     __syncthreads();
     // TMA: the A item `it` (if it is one) -> its map tile's coordinates
     auto a_tile = [&](int it, int* cx, int* cy) -> bool {
@@ -261,31 +272,51 @@ c3_dataflow_kernel(DfArgs a, const __grid_constant__ CUtensorMap tmS) {
         *cy = ((gg * a.CG + cc) * NZ + zz) * NY;
         return true;
     };
-    auto issue = [&](int it, int buf) {   // thread 0 only
-        int cx, cy;
-        if (!a_tile(it, &cx, &cy)) return;
+    // one thread: load the map tile at (cx, cy) into buffer buf; `tag` is
+    // the A item it serves (-2: a coil of a C item, the maps' last use)
+    auto issue_at = [&](int buf, int cx, int cy, int tag) {
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");   // earlier reads of the buffer
         mbar_expect_tx(&s_bar[buf], (uint32_t)Df<N2Y, N2Z>::TILE);
-        for (int h = 0; h < NY / Df<N2Y, N2Z>::BOXR; ++h)
-            tma_load_2d(Sb + buf * NY * DTX + h * Df<N2Y, N2Z>::BOXR * DTX, &tmS, cx,
-                        cy + h * Df<N2Y, N2Z>::BOXR, &s_bar[buf]);
-        s_pref[buf] = it;
+        for (int h = 0; h < NY / Df<N2Y, N2Z>::BOXR; ++h) {
+            float2* dst = Sb + buf * NY * DTX + h * Df<N2Y, N2Z>::BOXR * DTX;
+            if (tag == -2 && (kDfL2 & 2))
+                tma_load_2d_hint(dst, &tmS, cx, cy + h * Df<N2Y, N2Z>::BOXR, &s_bar[buf], pol_s);
+            else
+                tma_load_2d(dst, &tmS, cx, cy + h * Df<N2Y, N2Z>::BOXR, &s_bar[buf]);
+        }
+        s_pref[buf] = tag;
         s_pending[buf] = 1;
+    };
+    auto issue = [&](int it, int buf) {   // one thread
+        int cx, cy;
+        if (a_tile(it, &cx, &cy)) issue_at(buf, cx, cy, it);
+    };
+    // block-wide: the tile in buffer buf has landed (bounded wait); false on
+    // a timeout (error word set)
+    auto tile_wait = [&](int buf) -> bool {
+        int good = 1;
+        if (threadIdx.x == 0) {
+            if (!mbar_try_wait(&s_bar[buf], phase[buf])) {
+                const unsigned long long t0 = gtimer();
+                while (!mbar_try_wait(&s_bar[buf], phase[buf])) {
+                    if (gtimer() - t0 > kWaitNs) {
+                        atomicExch(err, 1);
+                        good = 0;
+                        break;
+                    }
+                }
+            }
+        }
+        if (!__syncthreads_and(good)) return false;
+        mbar_try_wait(&s_bar[buf], phase[buf]);   // this thread's acquire of the tile
+        phase[buf] ^= 1u;
+        if (threadIdx.x == 0) s_pending[buf] = 0;
+        return true;
     };
     for (;;) {
         const int item = s_item;
         // block-uniform stop test; the barrier also ends every read of s_item
         if (__syncthreads_or(item >= total || (threadIdx.x == 0 && *(volatile int*)err))) break;
-        const int cur_buf = iter & 1;
-        if (threadIdx.x == 0) {
-            const int nxt = atomicAdd(next, 1);   // claim the next one early
-            s_item = nxt;
-            if (TMA) {
-                if (s_pref[cur_buf] != item) issue(item, cur_buf);   // not prefetched: load it now
-                issue(nxt, cur_buf ^ 1);   // the next item's map tile, if it is an A item
-            }
-        }
-        ++iter;
         // ---- decode (x-block b, group g, kind, index)
         const int b = item / per_blk;
         int rr = item - b * per_blk;
@@ -293,6 +324,22 @@ c3_dataflow_kernel(DfArgs a, const __grid_constant__ CUtensorMap tmS) {
         rr -= g * per_full;
         const int k = b * a.ng + g;
         const int cg = (g == a.ng - 1) ? cg_last : a.CG;
+        const bool c_item = rr >= cg * (NZ + NBI);
+        const int cur_buf = iter & 1;
+        // the claim and the tile copies are issued by warp 1, so that their
+        // round trips overlap thread 0's dependency polls
+        if (threadIdx.x == kClaimT) {
+            if (TMA && s_pref[cur_buf] != item) issue(item, cur_buf);   // not prefetched: load it now
+            // claim the next item early (its map tile streams in meanwhile),
+            // except under a C item: that one runs for the whole coil group,
+            // and an item claimed that early would hold up its dependants
+            if (!c_item) {
+                const int nxt = atomicAdd(next, 1);
+                s_item = nxt;
+                if (TMA) issue(nxt, cur_buf ^ 1);   // the next item's map tile, if it is an A item
+            }
+        }
+        ++iter;
         const int c0 = g * a.CG;
         const int x0 = b * DTX, col = x0 + lane;
         const bool ok = col < a.nx;
@@ -300,29 +347,19 @@ c3_dataflow_kernel(DfArgs a, const __grid_constant__ CUtensorMap tmS) {
         if (rr < cg * NZ) {
             // ---- A (c, z): y FFT of S_c x on plane z -> W[c][z][ky]
             const int c = rr / NZ, z = rr - c * NZ;
-            if (k >= 2 && !df_wait(cntCz + (int64_t)(k - 2) * NZ + z, 1, err)) break;
             const float2* Sc = a.S + (int64_t)(c0 + c) * vol + (int64_t)z * plane;
             const float2* xz = a.x + (int64_t)z * plane;
+            // the image is read-only in the apply: its loads go out before the
+            // slot-reuse wait, which only orders this item's W stores
+            float2 xv[DN1];
+#pragma unroll
+            for (int m1 = 0; m1 < DN1; ++m1)
+                xv[m1] = (r < N2Y && ok) ? __ldg(xz + (int64_t)(N2Y * m1 + r) * a.nx + col) : make_float2(0.f, 0.f);
+            if (k >= 2 && !df_wait(cntCz + (int64_t)(k - 2) * NZ + z, 1, err)) break;
             const float2* St = nullptr;
             if (TMA) {
-                // the tile is in Sb[cur_buf] (issued now or one item ago): bounded wait
-                int good = 1;
-                if (threadIdx.x == 0) {
-                    if (!mbar_try_wait(&s_bar[cur_buf], phase[cur_buf])) {
-                        const unsigned long long t0 = gtimer();
-                        while (!mbar_try_wait(&s_bar[cur_buf], phase[cur_buf])) {
-                            if (gtimer() - t0 > kWaitNs) {
-                                atomicExch(err, 1);
-                                good = 0;
-                                break;
-                            }
-                        }
-                    }
-                }
-                if (!__syncthreads_and(good)) break;
-                mbar_try_wait(&s_bar[cur_buf], phase[cur_buf]);   // this thread's acquire of the tile
-                phase[cur_buf] ^= 1u;
-                if (threadIdx.x == 0) s_pending[cur_buf] = 0;
+                // the tile is in Sb[cur_buf] (issued now or one item ago)
+                if (!tile_wait(cur_buf)) break;
                 St = Sb + cur_buf * NY * DTX;
             }
             if (r < N2Y) {
@@ -331,7 +368,7 @@ c3_dataflow_kernel(DfArgs a, const __grid_constant__ CUtensorMap tmS) {
                 for (int m1 = 0; m1 < DN1; ++m1) {
                     const int64_t o = (int64_t)(N2Y * m1 + r) * a.nx + col;
                     const float2 sv = TMA ? St[(N2Y * m1 + r) * DTX + lane] : (ok ? __ldg(Sc + o) : make_float2(0.f, 0.f));
-                    v[m1] = ok ? cmul(sv, __ldg(xz + o)) : make_float2(0.f, 0.f);
+                    v[m1] = ok ? cmul(sv, xv[m1]) : make_float2(0.f, 0.f);
                 }
                 fft4_phase1<DN1, N2Y, false>(v, r, twy);
 #pragma unroll
@@ -412,11 +449,17 @@ c3_dataflow_kernel(DfArgs a, const __grid_constant__ CUtensorMap tmS) {
 #pragma unroll
             for (int k2 = 0; k2 < N2Y; ++k2) acc[k2] = make_float2(0.f, 0.f);
             bool alive = true;
+            // TMA: coil c's map tile goes to buffer cur_buf ^ (c & 1), coil
+            // c + 1's is issued before coil c is transformed (no item was
+            // claimed ahead, so both buffers are free)
+            if (TMA && threadIdx.x == 0) issue_at(cur_buf, x0, (c0 * NZ + z) * NY, -2);
             for (int c = 0; c < cg; ++c) {
                 if (!df_wait(cntB + (int64_t)k * a.CG + c, NBI, err)) {
                     alive = false;
                     break;
                 }
+                const int cb = cur_buf ^ (c & 1);
+                if (TMA && threadIdx.x == 0 && c + 1 < cg) issue_at(cb ^ 1, x0, ((c0 + c + 1) * NZ + z) * NY, -2);
                 const float2* Wz = Wk + ((int64_t)(c * NZ + z) * NY) * DTX + lane;
                 if (r < N2Y) {
                     float2 v[DN1];
@@ -426,18 +469,32 @@ c3_dataflow_kernel(DfArgs a, const __grid_constant__ CUtensorMap tmS) {
 #pragma unroll
                     for (int k1 = 0; k1 < DN1; ++k1) Y[(k1 * N2Y + r) * DTX + lane] = v[k1];
                 }
-                __syncthreads();
+                if (TMA) {
+                    if (!tile_wait(cb)) {   // also the barrier before Y is read
+                        alive = false;
+                        break;
+                    }
+                } else {
+                    __syncthreads();
+                }
                 if (r < DN1 && ok) {
                     float2 u[N2Y];
 #pragma unroll
                     for (int m2 = 0; m2 < N2Y; ++m2) u[m2] = Y[(r * N2Y + m2) * DTX + lane];
                     fft4_phase2<DN1, N2Y, true>(u, twy);
-                    const float2* Sc = a.S + (int64_t)(c0 + c) * vol + (int64_t)z * plane + col;
+                    if (TMA) {
+                        const float2* St = Sb + cb * NY * DTX + lane;
 #pragma unroll
-                    for (int k2 = 0; k2 < N2Y; ++k2)
-                        acc[k2] = cadd(acc[k2], cmulc(s_load_last(Sc + (int64_t)(r + DN1 * k2) * a.nx, pol_s), u[k2]));
+                        for (int k2 = 0; k2 < N2Y; ++k2)
+                            acc[k2] = cadd(acc[k2], cmulc(St[(r + DN1 * k2) * DTX], u[k2]));
+                    } else {
+                        const float2* Sc = a.S + (int64_t)(c0 + c) * vol + (int64_t)z * plane + col;
+#pragma unroll
+                        for (int k2 = 0; k2 < N2Y; ++k2)
+                            acc[k2] = cadd(acc[k2], cmulc(s_load_last(Sc + (int64_t)(r + DN1 * k2) * a.nx, pol_s), u[k2]));
+                    }
                 }
-                __syncthreads();   // Y is rewritten by the next coil
+                __syncthreads();   // Y and the tile buffer are rewritten by the next coil
             }
             if (!alive) break;
             if (g > 0 && !df_wait(cntCz + (int64_t)(k - 1) * NZ + z, 1, err)) break;
@@ -457,8 +514,9 @@ c3_dataflow_kernel(DfArgs a, const __grid_constant__ CUtensorMap tmS) {
                 }
             }
             df_signal(cntCz + (int64_t)k * NZ + z);
+            if (threadIdx.x == kClaimT) s_item = atomicAdd(next, 1);   // the claim, made late
         }
-        __syncthreads();   // s_item (the claim made at the top) is visible
+        __syncthreads();   // s_item (the claim made at the top, or after a C item) is visible
     }
     if (TMA && threadIdx.x == 0) {
         // after an early exit, wait (bounded) for this block's copies still in flight
