@@ -251,9 +251,14 @@ def hbm_peak_gbs():
         return 6800.0, "fallback 6.8 TB/s"
 
 
-def csrc_digest():
+def csrc_digest(files=None):
+    """Digest of the kernel sources: the named files of csrc/ (the kernel's
+    translation unit and the headers it includes), or all of csrc/."""
+    d = os.path.join(ROOT, "paper_2204_10252_gb300", "csrc")
+    paths = ([os.path.join(d, f) for f in sorted(files)] if files else
+             sorted(glob.glob(os.path.join(d, "*"))))
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2204_10252_gb300", "csrc", "*"))):
+    for f in paths:
         with open(f, "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -261,14 +266,19 @@ def csrc_digest():
 
 def ncu_traffic(kernel, summary="ncu_traffic.json"):
     """Per-launch DRAM bytes of `kernel` from the committed ncu summary, or
-    None when missing or taken on different kernel sources."""
+    None when missing or taken on different kernel sources (the digest covers
+    the files the summary lists in csrc_files, else all of csrc/)."""
     p = os.path.join(ROOT, "profiles", summary)
     try:
         d = json.load(open(p))
     except Exception:
         return None
     e = d.get("kernels", {}).get(kernel)
-    if not e or d.get("csrc_sha") != csrc_digest():
+    try:
+        same = d.get("csrc_sha") == csrc_digest(d.get("csrc_files"))
+    except OSError:
+        same = False
+    if not e or not same:
         return None
     return e.get("dram_bytes_per_launch")
 
