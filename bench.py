@@ -605,13 +605,14 @@ def main():
 
 SECONDARY = (("cart3d_256x256x128_c32", 20), ("batched2d_64", 5))
 SECONDARY_KEYS = ("metric", "value", "unit", "ms_per_step", "steps", "warmup", "config", "clocks",
-                  "roofline", "prox", "batched_apply_ms", "stage_ms_per_apply")
+                  "roofline", "prox", "llr_prox", "batched_apply_ms", "stage_ms_per_apply")
 
 
 def secondary_lines(args, local):
     """The HBM-bound workloads, measured in the same run with the same timing
     rules (bench_workloads): the 256x256x128, 32-coil normal operator with
-    the 3-D Haar prox, and the 64-slice batched solve and apply."""
+    the 3-D Haar and locally-low-rank proxes, and the 64-slice batched solve
+    and apply."""
     import torch
     import paper_2204_10252_gb300 as pp
     import bench_workloads

@@ -133,6 +133,28 @@ def cart3d(args, pp, rank, world, local):
     prox_ms, _ = _timed(prox_run, 1, dev, local)
     prox_bytes = 16.0 * n
     prox_gbs = prox_bytes * prox_calls / (prox_ms / 1e3) / 1e9
+    # the locally-low-rank prox of Sec. 5.3 on T = 5 coefficient images of the
+    # volume (8^3 blocks: 512 x 5 complex matrices), alternating over two
+    # input/output pairs (4 x 335 MB); lambda near the blocks' middle singular
+    # values, so the threshold keeps some and drops others
+    T_llr, lam_llr = 5, 20.0
+    del x2, y2, pairs
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(seed + 7)
+    llr_pairs = [(torch.randn(T_llr * n, dtype=torch.complex64, device=dev, generator=gen),
+                  torch.empty(T_llr * n, dtype=torch.complex64, device=dev)) for _ in range(2)]
+    llr_calls = 2 * args.steps
+
+    def llr_run():
+        for i in range(llr_calls):
+            xi, yi = llr_pairs[i & 1]
+            pp.pp_prox_llr(shape, T_llr, 8, lam_llr, xi, yi)
+
+    llr_run()
+    llr_ms, _ = _timed(llr_run, 1, dev, local)
+    llr_bytes = 2.0 * 8 * T_llr * n
+    llr_gbs = llr_bytes * llr_calls / (llr_ms / 1e3) / 1e9
+    del llr_pairs
     tuning = pp.pp_plan_tuning(plan)
     plan.destroy()
     return _base(args, world, "A^H A applies/s (3-D Cartesian normal operator)", "applies/s",
@@ -156,7 +178,14 @@ def cart3d(args, pp, rank, world, local):
                            "unit": "GB/s", "frac": prox_gbs / peak, "bytes_per_call": prox_bytes,
                            "ms_per_call": prox_ms / prox_calls,
                            "timing": "back-to-back calls alternating over two 67 MB input/output "
-                                     "pairs (268 MB, larger than L2)"}})
+                                     "pairs (268 MB, larger than L2)"},
+                  "llr_prox": {"kernel": "llr_prox_kernel", "images": T_llr, "block": 8, "lambda": lam_llr,
+                               "bound": "alu", "achieved_gbs": llr_gbs, "hbm_peak": peak,
+                               "hbm_frac": llr_gbs / peak, "bytes_per_call": llr_bytes,
+                               "ms_per_call": llr_ms / llr_calls,
+                               "timing": "back-to-back calls alternating over two 335 MB input/output "
+                                         "pairs (1.3 GB, larger than L2); one-sided Jacobi SVD per "
+                                         "512 x 5 block, instruction bound"}})
 
 
 def batched(args, pp, rank, world, local):
@@ -249,7 +278,8 @@ def apply_only(args, pp, local):
     bench line.  cart2d: K normal applies; cart3d: the workload's volume with
     --apply-coils of its coils (4 by default: a capture small enough for
     ncu), K normal applies, then K
-    3-D Haar prox calls; batched2d_64: K batched normal applies (--tuning T
+    3-D Haar prox calls, then K locally-low-rank prox calls on 5 images of the
+    volume; batched2d_64: K batched normal applies (--tuning T
     forces the batch tile code T)."""
     dev = torch.device("cuda", local)
     K = args.apply_only
@@ -289,6 +319,13 @@ def apply_only(args, pp, local):
     if len(shape) == 3:
         for _ in range(K):
             pp.pp_prox_l1_haar(shape, 2, float(c["lam"]), x, y)
+        # the bench line's LLR prox case: 5 coefficient images, 8^3 blocks
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(c["seed"] + 7)
+        xl = torch.randn(5 * x.numel(), dtype=torch.complex64, device=dev, generator=gen)
+        yl = torch.empty_like(xl)
+        for _ in range(K):
+            pp.pp_prox_llr(shape, 5, 8, 20.0, xl, yl)
     torch.cuda.synchronize()
     plan.destroy()
     return {"apply_only": K, "workload": args.workload}
