@@ -562,8 +562,8 @@ static pp_status tune_cart3d(Plan& p, cudaStream_t st) {
     std::vector<Cand> cand = {{0, 0, 0}};
     if (p.c3cl_clusters > 0) cand.push_back({1, 0, 0});
     if (p.c3cl2_clusters > 0) cand.push_back({2, 0, 0});
-    for (int hi = 0; hi < 3; ++hi)
-        if ((hi == 2 ? p.c3df_ctas_tma : (hi ? p.c3df_ctas_hi : p.c3df_ctas)) > 0)
+    for (int hi = 0; hi < 4; ++hi)
+        if ((hi == 3 ? p.c3df_ctas_tma1 : hi == 2 ? p.c3df_ctas_tma : (hi ? p.c3df_ctas_hi : p.c3df_ctas)) > 0)
             for (int cgc : {2, 4, 8})
                 if (cgc <= std::max(2, p.C) && (cgc == 2 || cgc <= p.C) &&
                     2 * c3df_slot_elems(p, cgc) <= p.c3df_w_elems)
@@ -1488,6 +1488,7 @@ pp_status pp_plan_create(pp_plan** out, pp_dims dims, int coils, const pp_c64* s
         p.c3df_ctas = c3df_prepare(p, 0);
         p.c3df_ctas_hi = c3df_prepare(p, 1);
         p.c3df_ctas_tma = (p.c3df_ctas > 0 && c3df_make_tensor_map(p)) ? c3df_prepare(p, 2) : 0;
+        p.c3df_ctas_tma1 = p.c3df_ctas_tma > 0 ? c3df_prepare(p, 3) : 0;
         if (p.c3df_ctas > 0) {
             // two phase slots for up to 8 coils per group; counters for 1
             p.c3df_w_elems = 2 * c3df_slot_elems(p, std::min(8, std::max(2, p.C)));
@@ -1595,10 +1596,11 @@ pp_status pp_plan_set_tuning(pp_plan* plan, int row_ifft_variant, int stencil_ki
                       "Cartesian plan with register-FFT lengths ny, nz and at most 8 coils per group");
             return PP_ERR_UNSUPPORTED;
         }
-        if (stencil_kind > 2 || (stencil_kind == 1 && p.c3df_ctas_hi <= 0) ||
-            (stencil_kind == 2 && p.c3df_ctas_tma <= 0)) {
+        if (stencil_kind < 0 || stencil_kind > 3 || (stencil_kind == 1 && p.c3df_ctas_hi <= 0) ||
+            (stencil_kind == 2 && p.c3df_ctas_tma <= 0) || (stencil_kind == 3 && p.c3df_ctas_tma1 <= 0)) {
             set_error("pp_plan_set_tuning: the 3-D dataflow operator takes stencil kind 0 (two "
-                      "blocks per SM), 1 (three) or 2 (map tiles staged by TMA)");
+                      "blocks per SM), 1 (three), 2 (map tiles staged by TMA) or 3 (staged by TMA "
+                      "into one buffer, three blocks per SM)");
             return PP_ERR_UNSUPPORTED;
         }
         p.tune_c3 = 3;

@@ -67,6 +67,7 @@ template <int N2Y, int N2Z> struct Df {
     static constexpr size_t TILE = sizeof(float2) * NY * DTX;
     static constexpr size_t SOFF = (SMEM + 1023) / 1024 * 1024;
     static constexpr size_t SMEM_TMA = SOFF + 2 * TILE + 1024;   // + slack to align the base
+    static constexpr size_t SMEM_TMA1 = SOFF + TILE + 1024;      // one tile buffer (three blocks per SM)
     static constexpr int BOXR = NY <= 256 ? NY : NY / 2;        // tensor-map box rows (<= 256)
 };
 
@@ -216,11 +217,15 @@ __global__ void __launch_bounds__(Df<N2Y, N2Z>::THREADS, MB)
 c3_dataflow_kernel(DfArgs a, const __grid_constant__ CUtensorMap tmS) {
     constexpr int NY = Df<N2Y, N2Z>::NY, NZ = Df<N2Y, N2Z>::NZ, LPB = Df<N2Y, N2Z>::LPB;
     constexpr int NBI = NY / LPB;   // B items per coil
+    // TMA tile buffers: two, or one when three blocks share an SM (the next
+    // tile is then issued once the current one has been read)
+    constexpr int NBUF = (TMA && MB >= 3) ? 1 : 2;
     extern __shared__ float4 df_sm4[];
     float2* Y = reinterpret_cast<float2*>(df_sm4);
     float2* twy = Y + Df<N2Y, N2Z>::YE;
     float2* twz = twy + NY;
     __shared__ int s_item;
+    __shared__ unsigned s_bdone;   // C item: coils of the group whose B items were all done at its start
     // TMA variant: two map-tile buffers (1024-byte aligned), their mbarriers,
     // the item each holds (-1: none) and each barrier's phase
     __shared__ __align__(8) uint64_t s_bar[2];
@@ -324,8 +329,8 @@ c3_dataflow_kernel(DfArgs a, const __grid_constant__ CUtensorMap tmS) {
         rr -= g * per_full;
         const int k = b * a.ng + g;
         const int cg = (g == a.ng - 1) ? cg_last : a.CG;
-        const bool c_item = rr >= cg * (NZ + NBI);
-        const int cur_buf = iter & 1;
+        const bool a_item = rr < cg * NZ, c_item = rr >= cg * (NZ + NBI);
+        const int cur_buf = NBUF == 2 ? (iter & 1) : 0;
         // the claim and the tile copies are issued by warp 1, so that their
         // round trips overlap thread 0's dependency polls
         if (threadIdx.x == kClaimT) {
@@ -336,7 +341,9 @@ c3_dataflow_kernel(DfArgs a, const __grid_constant__ CUtensorMap tmS) {
             if (!c_item) {
                 const int nxt = atomicAdd(next, 1);
                 s_item = nxt;
-                if (TMA) issue(nxt, cur_buf ^ 1);   // the next item's map tile, if it is an A item
+                // the next item's map tile, if it is an A item: into the spare
+                // buffer, or with one buffer only when this item holds none
+                if (TMA && (NBUF == 2 || !a_item)) issue(nxt, cur_buf ^ (NBUF - 1));
             }
         }
         ++iter;
@@ -375,6 +382,8 @@ c3_dataflow_kernel(DfArgs a, const __grid_constant__ CUtensorMap tmS) {
                 for (int k1 = 0; k1 < DN1; ++k1) Y[(k1 * N2Y + r) * DTX + lane] = v[k1];
             }
             __syncthreads();
+            // one buffer: the tile has been read, so the next item's may land
+            if (TMA && NBUF == 1 && threadIdx.x == kClaimT) issue(s_item, 0);
             if (r < DN1) {
                 float2 u[N2Y];
 #pragma unroll
@@ -453,13 +462,24 @@ c3_dataflow_kernel(DfArgs a, const __grid_constant__ CUtensorMap tmS) {
             // c + 1's is issued before coil c is transformed (no item was
             // claimed ahead, so both buffers are free)
             if (TMA && threadIdx.x == 0) issue_at(cur_buf, x0, (c0 * NZ + z) * NY, -2);
+            // the group's B counters are read once, in parallel (one acquire per
+            // coil by warp 0, published by the barrier); only coils still
+            // running their B items are waited for one by one
+            if (threadIdx.x < 32) {
+                const bool done =
+                    (int)threadIdx.x < cg && ld_acquire(cntB + (int64_t)k * a.CG + threadIdx.x) >= NBI;
+                const unsigned m = __ballot_sync(0xffffffffu, done);
+                if (threadIdx.x == 0) s_bdone = m;
+            }
+            __syncthreads();
             for (int c = 0; c < cg; ++c) {
-                if (!df_wait(cntB + (int64_t)k * a.CG + c, NBI, err)) {
+                if (!((s_bdone >> c) & 1u) && !df_wait(cntB + (int64_t)k * a.CG + c, NBI, err)) {
                     alive = false;
                     break;
                 }
-                const int cb = cur_buf ^ (c & 1);
-                if (TMA && threadIdx.x == 0 && c + 1 < cg) issue_at(cb ^ 1, x0, ((c0 + c + 1) * NZ + z) * NY, -2);
+                const int cb = NBUF == 2 ? (cur_buf ^ (c & 1)) : 0;
+                if (TMA && NBUF == 2 && threadIdx.x == 0 && c + 1 < cg)
+                    issue_at(cb ^ 1, x0, ((c0 + c + 1) * NZ + z) * NY, -2);
                 const float2* Wz = Wk + ((int64_t)(c * NZ + z) * NY) * DTX + lane;
                 if (r < N2Y) {
                     float2 v[DN1];
@@ -495,6 +515,8 @@ c3_dataflow_kernel(DfArgs a, const __grid_constant__ CUtensorMap tmS) {
                     }
                 }
                 __syncthreads();   // Y and the tile buffer are rewritten by the next coil
+                if (TMA && NBUF == 1 && threadIdx.x == 0 && c + 1 < cg)
+                    issue_at(0, x0, ((c0 + c + 1) * NZ + z) * NY, -2);
             }
             if (!alive) break;
             if (g > 0 && !df_wait(cntCz + (int64_t)(k - 1) * NZ + z, 1, err)) break;
@@ -520,7 +542,7 @@ c3_dataflow_kernel(DfArgs a, const __grid_constant__ CUtensorMap tmS) {
     }
     if (TMA && threadIdx.x == 0) {
         // after an early exit, wait (bounded) for this block's copies still in flight
-        for (int b2 = 0; b2 < 2; ++b2) {
+        for (int b2 = 0; b2 < NBUF; ++b2) {
             if (!s_pending[b2]) continue;
             const unsigned long long t0 = gtimer();
             while (!mbar_try_wait(&s_bar[b2], phase[b2]) && gtimer() - t0 < kWaitNs) {
@@ -529,10 +551,14 @@ c3_dataflow_kernel(DfArgs a, const __grid_constant__ CUtensorMap tmS) {
     }
 }
 
+template <int N2Y, int N2Z, int MB, bool TMA> constexpr size_t df_smem() {
+    return TMA ? (MB >= 3 ? Df<N2Y, N2Z>::SMEM_TMA1 : Df<N2Y, N2Z>::SMEM_TMA) : Df<N2Y, N2Z>::SMEM;
+}
+
 template <int N2Y, int N2Z, int MB, bool TMA>
 int df_resident() {
     auto fn = c3_dataflow_kernel<N2Y, N2Z, MB, TMA>;
-    const size_t smem = TMA ? Df<N2Y, N2Z>::SMEM_TMA : Df<N2Y, N2Z>::SMEM;
+    const size_t smem = df_smem<N2Y, N2Z, MB, TMA>();
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
         cudaGetLastError();
         return 0;
@@ -568,17 +594,36 @@ template <int N2Y, int N2Z> constexpr int df_mb(int v) {
     return Df<N2Y, N2Z>::THREADS <= 256 ? (v ? 3 : 2) : 1;
 }
 
+template <int N2Y, int N2Z, int MB, bool TMA>
+cudaError_t df_launch(int grid, cudaStream_t st, const DfArgs& a, const CUtensorMap& tm) {
+    return launch_ex(c3_dataflow_kernel<N2Y, N2Z, MB, TMA>, dim3(grid), dim3(Df<N2Y, N2Z>::THREADS),
+                     df_smem<N2Y, N2Z, MB, TMA>(), st, false, 0, a, tm);
+}
+// variant v of the kernel for (N2Y, N2Z): the numbering of c3df_prepare
+template <int N2Y, int N2Z>
+cudaError_t df_launch_v(int v, int grid, cudaStream_t st, const DfArgs& a, const CUtensorMap& tm) {
+    constexpr int m0 = df_mb<N2Y, N2Z>(0), m1 = df_mb<N2Y, N2Z>(1);
+    switch (v) {
+        case 3: return df_launch<N2Y, N2Z, m1, true>(grid, st, a, tm);
+        case 2: return df_launch<N2Y, N2Z, m0, true>(grid, st, a, tm);
+        case 1: return df_launch<N2Y, N2Z, m1, false>(grid, st, a, tm);
+        default: return df_launch<N2Y, N2Z, m0, false>(grid, st, a, tm);
+    }
+}
+
 // Resident CTAs of the dataflow kernel (variant v: 0 two blocks per SM, 1
-// three, 2 TMA-staged map tiles) for this plan's (ny, nz), 0 when the kernel
-// does not apply (a length without a register FFT).
+// three, 2 TMA-staged map tiles in two buffers, 3 TMA-staged tiles in one
+// buffer with three blocks per SM) for this plan's (ny, nz), 0 when the
+// kernel does not apply (a length without a register FFT).
 int c3df_prepare(const Plan& p, int v) {
     if (p.kind != PP_CARTESIAN || p.ndim != 3) return 0;
     const int n2y = fft4_n2(p.ny), n2z = fft4_n2(p.nz);
 #define PP_DF_PREP(Y_, Z_)                                                           \
     if (n2y == Y_ && n2z == Z_)                                                      \
-        return v == 2 ? df_resident<Y_, Z_, df_mb<Y_, Z_>(0), true>()                \
-                      : (v ? df_resident<Y_, Z_, df_mb<Y_, Z_>(1), false>()          \
-                           : df_resident<Y_, Z_, df_mb<Y_, Z_>(0), false>());
+        return v == 3   ? df_resident<Y_, Z_, df_mb<Y_, Z_>(1), true>()              \
+               : v == 2 ? df_resident<Y_, Z_, df_mb<Y_, Z_>(0), true>()              \
+               : v      ? df_resident<Y_, Z_, df_mb<Y_, Z_>(1), false>()             \
+                        : df_resident<Y_, Z_, df_mb<Y_, Z_>(0), false>();
     PP_DF_CASES(PP_DF_PREP)
 #undef PP_DF_PREP
     return 0;
@@ -637,24 +682,15 @@ pp_status c3df_normal(const Plan& p, const float2* x, float2* out, float scale,
     const int per_full = cg * (p.nz + p.ny) + p.nz;   // an upper bound on the items of a phase
     const int64_t total = (int64_t)a.nb * a.ng * per_full;
     const int v = p.c3df_hi;
-    const int ctas = v == 2 ? p.c3df_ctas_tma : (v ? p.c3df_ctas_hi : p.c3df_ctas);
+    const int ctas = v == 3 ? p.c3df_ctas_tma1 : v == 2 ? p.c3df_ctas_tma : (v ? p.c3df_ctas_hi : p.c3df_ctas);
     if (ctas <= 0) {
         set_error("c3df_normal: this dataflow variant cannot be resident on the device");
         return PP_ERR_UNSUPPORTED;
     }
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ctas, total));
     cudaError_t e = cudaErrorInvalidValue;
-#define PP_DF_LAUNCH(Y_, Z_)                                                                    \
-    if (n2y == Y_ && n2z == Z_)                                                                 \
-        e = v == 2 ? launch_ex(c3_dataflow_kernel<Y_, Z_, df_mb<Y_, Z_>(0), true>, dim3(grid),  \
-                               dim3(Df<Y_, Z_>::THREADS), Df<Y_, Z_>::SMEM_TMA, st, false, 0, a, \
-                               p.c3df_tmS)                                                      \
-            : v ? launch_ex(c3_dataflow_kernel<Y_, Z_, df_mb<Y_, Z_>(1), false>, dim3(grid),    \
-                            dim3(Df<Y_, Z_>::THREADS), Df<Y_, Z_>::SMEM, st, false, 0, a,       \
-                            p.c3df_tmS)                                                         \
-                : launch_ex(c3_dataflow_kernel<Y_, Z_, df_mb<Y_, Z_>(0), false>, dim3(grid),    \
-                            dim3(Df<Y_, Z_>::THREADS), Df<Y_, Z_>::SMEM, st, false, 0, a,       \
-                            p.c3df_tmS);
+#define PP_DF_LAUNCH(Y_, Z_) \
+    if (n2y == Y_ && n2z == Z_) e = df_launch_v<Y_, Z_>(v, grid, st, a, p.c3df_tmS);
     PP_DF_CASES(PP_DF_LAUNCH)
 #undef PP_DF_LAUNCH
     if (e != cudaSuccess) return cuda_status(e, "c3_dataflow_kernel launch");

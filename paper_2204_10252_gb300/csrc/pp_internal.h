@@ -191,7 +191,9 @@ struct Plan {
     int c3df_ctas = 0;          // resident CTAs (0: not available for this plan)
     int c3df_ctas_hi = 0;       //   the same for the variant with three blocks per SM
     int c3df_ctas_tma = 0;      //   the same for the variant that stages map tiles by TMA
-    int c3df_hi = 0;            // variant: 0 two blocks per SM, 1 three, 2 TMA-staged map tiles
+    int c3df_ctas_tma1 = 0;     //   ... by TMA into one buffer, three blocks per SM
+    int c3df_hi = 0;            // variant: 0 two blocks per SM, 1 three, 2 TMA-staged map tiles,
+                                // 3 TMA-staged tiles in one buffer with three blocks per SM
     CUtensorMap c3df_tmS;       // the coil maps as a 2-D tensor [C nz ny][nx] of 8-byte elements
     int c3df_cg = 4;            // coils per group
     float2* c3df_w = nullptr;   // two phase slots

@@ -189,7 +189,8 @@ def test_cart3d_full_volume_one_apply_sampled_columns(pp):
         ref = O.cart_normal_columns(x, sens, mask, cols) / L
         xd = dev(x)
         tuned = pp.pp_plan_tuning(plan)
-        for tuning in [tuned, (3, 0, 2), (3, 0, 4), (3, 1, 4), (3, 1, 8), (3, 2, 4), (3, 2, 8), (1, 0, 8)]:
+        for tuning in [tuned, (3, 0, 2), (3, 0, 4), (3, 1, 4), (3, 1, 8), (3, 2, 4), (3, 2, 8), (3, 3, 4),
+                       (3, 3, 8), (1, 0, 8)]:
             pp.pp_plan_set_tuning(plan, *tuning)
             out = empty(shape)
             pp.pp_normal_apply(plan, xd, out)
