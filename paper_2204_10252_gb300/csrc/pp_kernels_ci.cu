@@ -248,6 +248,39 @@ ci_stencil_kernel(const float* __restrict__ T8, int Gx, int Gy, int nxb,
     }
 }
 
+// Tail of the cluster row-IFFT kernels: every CTA of the row's 4-CTA cluster
+// holds its coil block's partial row in Y[i * 9 + 8]; CTA q sums the four
+// partials of its quarter [q n/4, (q + 1) n/4) through distributed shared
+// memory and writes scale * sum + alpha * operand.  The cluster barrier is
+// split: the release-arrive publishes this CTA's partials, and the operand
+// of the quarter (written by earlier kernels, independent of the cluster) is
+// loaded before the acquire-wait.  The closing barrier only keeps the
+// partials alive until every CTA has read them; its arrive is relaxed (the
+// remote loads have fed the stores before it).
+__device__ __forceinline__ void cluster_row_sum(const float2* Y, int n, int row, int q, float scale,
+                                                const float2* operand, float alpha, float2* out) {
+    namespace cgx = cooperative_groups;
+    cgx::cluster_group cluster = cgx::this_cluster();
+    asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+    const int chunk = (n + NCB - 1) / NCB;
+    const int i0 = q * chunk, i1 = min(n, i0 + chunk);
+    const int ifirst = i0 + (int)threadIdx.x;
+    float2 op0 = make_float2(0.f, 0.f);
+    if (operand && ifirst < i1) op0 = operand[(int64_t)row * n + ifirst];
+    asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+    for (int i = ifirst; i < i1; i += blockDim.x) {
+        float2 v = cluster.map_shared_rank(Y, 0)[i * 9 + 8];
+#pragma unroll
+        for (int b = 1; b < NCB; ++b) v = cadd(v, cluster.map_shared_rank(Y, b)[i * 9 + 8]);
+        v = cscale(v, scale);
+        const int64_t o = (int64_t)row * n + i;
+        if (operand) v = cadd(v, cscale(i == ifirst ? op0 : operand[o], alpha));
+        out[o] = v;
+    }
+    asm volatile("barrier.cluster.arrive.relaxed.aligned;\n" ::: "memory");
+    asm volatile("barrier.cluster.wait.aligned;\n" ::: "memory");
+}
+
 // Row stage k rows -> image with the coil reduction of one coil block:
 // P[cb][row][i] = sum_{c in block cb} w conj(S_c) IFFT(src_c[row])[place(i)].
 template <int N2> __host__ __device__ constexpr int inv_buf() {
@@ -461,19 +494,7 @@ ci_rows_inv_cl_kernel(const float2* __restrict__ tw, RowArgs a, const float2* __
     const int q = (int)cluster.block_rank();
     const int row = blockIdx.y;
     ci_rows_inv_body<N2>(tw, a, src, S, wrow, wcol, row, q, tws, Y);
-    cluster.sync();
-    const int chunk = (a.n + NCB - 1) / NCB;
-    const int i0 = q * chunk, i1 = min(a.n, i0 + chunk);
-    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-        float2 v = cluster.map_shared_rank(Y, 0)[i * 9 + 8];
-#pragma unroll
-        for (int b = 1; b < NCB; ++b) v = cadd(v, cluster.map_shared_rank(Y, b)[i * 9 + 8]);
-        v = cscale(v, scale);
-        const int64_t o = (int64_t)row * a.n + i;
-        if (operand) v = cadd(v, cscale(operand[o], alpha));
-        out[o] = v;
-    }
-    cluster.sync();   // keep every CTA's partials alive until the others have read them
+    cluster_row_sum(Y, a.n, row, q, scale, operand, alpha, out);
 }
 
 // out[o] = scale * sum_b P[b][o] + alpha * operand[o]
@@ -723,19 +744,7 @@ toep_rows_inv_half_cl_kernel(const float2* __restrict__ tw, const float2* __rest
         for (int jj = 1; jj < CB; ++jj) acc = cadd(acc, R[i * 9 + jj]);
         R[i * 9 + 8] = acc;
     }
-    cluster.sync();
-    const int chunk = (n + NCB - 1) / NCB;
-    const int i0 = q * chunk, i1 = min(n, i0 + chunk);
-    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-        float2 v = cluster.map_shared_rank(Y, 0)[i * 9 + 8];
-#pragma unroll
-        for (int b = 1; b < NCB; ++b) v = cadd(v, cluster.map_shared_rank(Y, b)[i * 9 + 8]);
-        v = cscale(v, scale);
-        const int64_t o = (int64_t)row * n + i;
-        if (operand) v = cadd(v, cscale(operand[o], alpha));
-        out[o] = v;
-    }
-    cluster.sync();   // keep every CTA's partials alive until the others have read them
+    cluster_row_sum(Y, n, row, q, scale, operand, alpha, out);
 }
 
 // Column stage of the Toeplitz operator on length-n halves (n = ny = 16 N2,
