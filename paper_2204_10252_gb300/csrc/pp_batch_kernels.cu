@@ -470,7 +470,10 @@ __device__ __forceinline__ void batch_item_cl(const float2* tws, const float* pm
             os[o] = v;
         }
     }
-    cluster.sync();   // Y is rewritten by the next item only after every CTA has read it
+    // Y is rewritten by the next item only after every CTA has read it (the
+    // remote loads have fed the stores above: the arrive needs no release)
+    cluster_arrive_relaxed();
+    cluster_wait_acquire();
 }
 
 // cart2d_batch4_kernel with the coils of every item split over a cluster of

@@ -131,6 +131,20 @@ __device__ __forceinline__ void fft4_phase2(float2* u, const float2* __restrict_
 
 namespace pp {
 
+// Split thread-block-cluster barrier.  arrive_release publishes this CTA's
+// earlier shared-memory writes to the cluster, wait_acquire makes the other
+// CTAs' visible; arrive_relaxed orders nothing (for a barrier that only
+// says "done reading").  All threads of the CTA execute each of them.
+__device__ __forceinline__ void cluster_arrive_release() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ void cluster_arrive_relaxed() {
+    asm volatile("barrier.cluster.arrive.relaxed.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait_acquire() {
+    asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+
 // 16-byte asynchronous global -> shared copy, zero-filled when !valid.
 __device__ __forceinline__ void cpa16(void* smem, const void* gmem, bool valid) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);

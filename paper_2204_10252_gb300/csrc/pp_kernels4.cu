@@ -322,7 +322,10 @@ rows4_adj_cl_kernel(const float2* __restrict__ tw, RowArgs a, const float2* __re
             }
         }
     }
-    cluster.sync();   // keep every CTA's partial sums alive until rank 0 has read them
+    // keep every CTA's partial sums alive until rank 0 has read them (rank 0's
+    // remote loads have fed its stores: the arrive needs no release)
+    cluster_arrive_relaxed();
+    cluster_wait_acquire();
 }
 
 // Row IFFT per (coil, row) with the crop, deapodisation and conj(S_c)
@@ -454,8 +457,16 @@ cart2d4_cluster_kernel(const float2* __restrict__ tw, const float2* __restrict__
 #pragma unroll
         for (int m1 = 0; m1 < N1; ++m1) Y[(N2 * m1 + r) * 8 + lane] = acc[m1];   // Y[row][lane]
     }
-    cluster.sync();
+    // split barrier: publish the partials, load the first operand value of
+    // this CTA's rows (independent of the cluster) while the others arrive
+    cluster_arrive_release();
     const int rpr = n / CL;
+    float2 op0 = make_float2(0.f, 0.f);
+    {
+        const int row = q * rpr + ((int)threadIdx.x >> 3), col = col0 + ((int)threadIdx.x & 7);
+        if (operand && (int)threadIdx.x < rpr * 8 && col < nx) op0 = operand[(int64_t)row * nx + col];
+    }
+    cluster_wait_acquire();
     for (int idx = threadIdx.x; idx < rpr * 8; idx += blockDim.x) {
         const int row = q * rpr + (idx >> 3), l = idx & 7, col = col0 + l;
         float2 v = cluster.map_shared_rank(Y, 0)[row * 8 + l];
@@ -463,11 +474,14 @@ cart2d4_cluster_kernel(const float2* __restrict__ tw, const float2* __restrict__
         if (col < nx) {
             const int64_t o = (int64_t)row * nx + col;
             v = cscale(v, scale);
-            if (operand) v = cadd(v, cscale(operand[o], alpha));
+            if (operand) v = cadd(v, cscale(idx == (int)threadIdx.x ? op0 : operand[o], alpha));
             out[o] = v;
         }
     }
-    cluster.sync();   // keep every CTA's partials alive until the others have read them
+    // keep every CTA's partials alive until the others have read them (their
+    // remote loads have fed their stores: the arrive needs no release)
+    cluster_arrive_relaxed();
+    cluster_wait_acquire();
 }
 
 template <int N2> constexpr size_t cart4_dyn_smem() { return sizeof(float2) * 2 * 16 * N2 * 8; }

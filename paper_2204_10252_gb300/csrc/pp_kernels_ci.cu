@@ -261,13 +261,13 @@ __device__ __forceinline__ void cluster_row_sum(const float2* Y, int n, int row,
                                                 const float2* operand, float alpha, float2* out) {
     namespace cgx = cooperative_groups;
     cgx::cluster_group cluster = cgx::this_cluster();
-    asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+    cluster_arrive_release();
     const int chunk = (n + NCB - 1) / NCB;
     const int i0 = q * chunk, i1 = min(n, i0 + chunk);
     const int ifirst = i0 + (int)threadIdx.x;
     float2 op0 = make_float2(0.f, 0.f);
     if (operand && ifirst < i1) op0 = operand[(int64_t)row * n + ifirst];
-    asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+    cluster_wait_acquire();
     for (int i = ifirst; i < i1; i += blockDim.x) {
         float2 v = cluster.map_shared_rank(Y, 0)[i * 9 + 8];
 #pragma unroll
@@ -277,8 +277,8 @@ __device__ __forceinline__ void cluster_row_sum(const float2* Y, int n, int row,
         if (operand) v = cadd(v, cscale(i == ifirst ? op0 : operand[o], alpha));
         out[o] = v;
     }
-    asm volatile("barrier.cluster.arrive.relaxed.aligned;\n" ::: "memory");
-    asm volatile("barrier.cluster.wait.aligned;\n" ::: "memory");
+    cluster_arrive_relaxed();
+    cluster_wait_acquire();
 }
 
 // Row stage k rows -> image with the coil reduction of one coil block:
