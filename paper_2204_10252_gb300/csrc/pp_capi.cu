@@ -397,20 +397,23 @@ static pp_status build_noncartesian(Plan& p, const pp_sampling* s) {
             st[k].iy0 = iy0;
         }
     };
-    {
-        const int nth = std::max(1, std::min({16, (int)std::thread::hardware_concurrency(), K / 4096 + 1}));
+    // runs body(k0, k1) over nth contiguous ranges of [0, K) on host threads
+    const int nth = std::max(1, std::min({16, (int)std::thread::hardware_concurrency(), K / 4096 + 1}));
+    auto on_threads = [&](auto&& body) {
         std::vector<std::thread> pool;
+        size_t handed = 1;
         try {
-            for (int t = 1; t < nth; ++t)
-                pool.emplace_back(taps, (int)((int64_t)K * t / nth), (int)((int64_t)K * (t + 1) / nth));
+            for (int t = 1; t < nth; ++t, ++handed)
+                pool.emplace_back(body, t, (int)((int64_t)K * t / nth), (int)((int64_t)K * (t + 1) / nth));
         } catch (const std::exception&) {
-            // no more threads: the calling thread takes what was not handed out
-            const int k0 = (int)((int64_t)K * (pool.size() + 1) / nth);
-            taps(k0, K);
+            // no more threads: the calling thread takes the ranges not handed out
+            for (int t = (int)handed; t < nth; ++t)
+                body(t, (int)((int64_t)K * t / nth), (int)((int64_t)K * (t + 1) / nth));
         }
-        taps(0, (int)((int64_t)K / nth));
+        body(0, 0, (int)((int64_t)K / nth));
         for (auto& th : pool) th.join();
-    }
+    };
+    on_threads([&](int, int k0, int k1) { taps(k0, k1); });
     if (bad.load() < K) {
         const int k = bad.load();
         set_error("trajectory sample %d (%g, %g) outside [-n/2, n/2)", k, s->traj[2 * k], s->traj[2 * k + 1]);
@@ -422,34 +425,38 @@ static pp_status build_noncartesian(Plan& p, const pp_sampling* s) {
     p.ntx = (Gx + T - 1) / T;
     p.nty = (Gy + T - 1) / T;
     const int ntiles = p.ntx * p.nty;
-    std::vector<std::vector<TileEntry>> lists(ntiles);
-    for (int k = 0; k < K; ++k) {
-        int trow[4], tcol[4], nr = 0, nc = 0;
-        for (int b = 0; b < W; ++b) {
-            const int ty = wrap_host(st[k].iy0 + b, Gy) / T;
-            if (std::find(trow, trow + nr, ty) == trow + nr) trow[nr++] = ty;
-            const int tx = wrap_host(st[k].ix0 + b, Gx) / T;
-            if (std::find(tcol, tcol + nc, tx) == tcol + nc) tcol[nc++] = tx;
-        }
-        for (int i = 0; i < nr; ++i)
-            for (int j = 0; j < nc; ++j) {
-                const int ty0 = trow[i] * T, tx0 = tcol[j] * T;
-                const int ly0 = wrap_host(st[k].iy0 - ty0 + H, Gy);
-                const int lx0 = wrap_host(st[k].ix0 - tx0 + H, Gx);
-                TileEntry e;
-                e.wx = st[k].wx;
-                e.wy = st[k].wy;
-                e.lyx = ly0 | (lx0 << 16);
-                e.k = k;
-                lists[trow[i] * p.ntx + tcol[j]].push_back(e);
+    // per-tile lists in ascending sample order: each thread fills the lists of
+    // its sample range, and the ranges are concatenated in order
+    std::vector<std::vector<std::vector<TileEntry>>> lists(nth, std::vector<std::vector<TileEntry>>(ntiles));
+    on_threads([&](int t, int k0, int k1) {
+        for (int k = k0; k < k1; ++k) {
+            int trow[4], tcol[4], nr = 0, nc = 0;
+            for (int b = 0; b < W; ++b) {
+                const int ty = wrap_host(st[k].iy0 + b, Gy) / T;
+                if (std::find(trow, trow + nr, ty) == trow + nr) trow[nr++] = ty;
+                const int tx = wrap_host(st[k].ix0 + b, Gx) / T;
+                if (std::find(tcol, tcol + nc, tx) == tcol + nc) tcol[nc++] = tx;
             }
-    }
+            for (int i = 0; i < nr; ++i)
+                for (int j = 0; j < nc; ++j) {
+                    const int ty0 = trow[i] * T, tx0 = tcol[j] * T;
+                    const int ly0 = wrap_host(st[k].iy0 - ty0 + H, Gy);
+                    const int lx0 = wrap_host(st[k].ix0 - tx0 + H, Gx);
+                    TileEntry e;
+                    e.wx = st[k].wx;
+                    e.wy = st[k].wy;
+                    e.lyx = ly0 | (lx0 << 16);
+                    e.k = k;
+                    lists[t][trow[i] * p.ntx + tcol[j]].push_back(e);
+                }
+        }
+    });
     std::vector<int> start(ntiles + 1, 0);
     std::vector<TileEntry> flat;
     for (int t = 0; t < ntiles; ++t) {
         start[t] = (int)flat.size();
-        p.max_tile_len = std::max(p.max_tile_len, (int)lists[t].size());
-        flat.insert(flat.end(), lists[t].begin(), lists[t].end());
+        for (int r = 0; r < nth; ++r) flat.insert(flat.end(), lists[r][t].begin(), lists[r][t].end());
+        p.max_tile_len = std::max(p.max_tile_len, (int)flat.size() - start[t]);
     }
     start[ntiles] = (int)flat.size();
     if (flat.empty()) flat.push_back(TileEntry());
