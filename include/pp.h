@@ -106,7 +106,14 @@ typedef struct pp_plan pp_plan;
  *          PP_ERR_INVALID_ARG), BORROWED: it must stay valid and unchanged
  *          until pp_plan_destroy.
  *   s      sampling pattern, see pp_sampling.
- * Synchronises `stream` once (to read L).  On failure *out is NULL. */
+ * Set-up times the plan's candidate launch shapes on its own buffers and
+ * keeps the fastest (see pp_plan_tuning); the choice is remembered for the
+ * life of the process per device, shape, coil count and sampling (the
+ * trajectory's or the mask's bytes), so a later plan of the same geometry
+ * takes it without timing again.  Non-Cartesian set-up computes the
+ * per-sample gridding taps and tile lists on up to 16 host threads.
+ * Synchronises `stream` (to read L and the stencil's tile flags).  On
+ * failure *out is NULL. */
 pp_status pp_plan_create(pp_plan** out, pp_dims dims, int coils, const pp_c64* sens,
                          const pp_sampling* s, uint64_t seed, int power_iters, pp_stream stream);
 
