@@ -112,7 +112,7 @@ typedef struct pp_plan pp_plan;
  * trajectory's or the mask's bytes), so a later plan of the same geometry
  * takes it without timing again.  Non-Cartesian set-up computes the
  * per-sample gridding taps and tile lists on up to 16 host threads.
- * Synchronises `stream` (to read L and the stencil's tile flags).  On
+ * Synchronises `stream` (the set-up work is complete on return).  On
  * failure *out is NULL. */
 pp_status pp_plan_create(pp_plan** out, pp_dims dims, int coils, const pp_c64* sens,
                          const pp_sampling* s, uint64_t seed, int power_iters, pp_stream stream);
