@@ -157,7 +157,9 @@ pp_status pp_plan_sizes(const pp_plan* plan, int64_t* image_elems, int64_t* kspa
  *    or 1 = compiled for two or three resident blocks per SM, 2 = two blocks
  *    per SM with the coil-map tiles of the y-FFT and y-IFFT items streamed
  *    into two shared buffers by tensor-map bulk copies (TMA), 3 = the same
- *    with one buffer and three blocks per SM); for 2-D Cartesian plans 1, 2, 4 or 8
+ *    with one buffer and three blocks per SM, 4 or 5 = 0 or 1 with two z
+ *    planes per y-FFT item and two line units per z item); for 2-D
+ *    Cartesian plans 1, 2, 4 or 8
  *    = CTAs per 8-column group, the coils split over a cluster of that size;
  *  - stencil_kind: the G^T G stencil kernel (0 = one output per thread,
  *    1 = two outputs per thread, both staging one coil at a time with

@@ -654,8 +654,9 @@ static pp_status tune_cart3d(Plan& p, cudaStream_t st) {
     std::vector<Cand> cand = {{0, 0, 0}};
     if (p.c3cl_clusters > 0) cand.push_back({1, 0, 0});
     if (p.c3cl2_clusters > 0) cand.push_back({2, 0, 0});
-    for (int hi = 0; hi < 4; ++hi)
-        if ((hi == 3 ? p.c3df_ctas_tma1 : hi == 2 ? p.c3df_ctas_tma : (hi ? p.c3df_ctas_hi : p.c3df_ctas)) > 0)
+    for (int hi = 0; hi < 6; ++hi)
+        if ((hi == 3 ? p.c3df_ctas_tma1 : hi == 2 ? p.c3df_ctas_tma
+             : (hi == 1 || hi == 5) ? p.c3df_ctas_hi : p.c3df_ctas) > 0)
             for (int cgc : {2, 4, 8})
                 if (cgc <= std::max(2, p.C) && (cgc == 2 || cgc <= p.C) &&
                     2 * c3df_slot_elems(p, cgc) <= p.c3df_w_elems)
@@ -1695,11 +1696,12 @@ pp_status pp_plan_set_tuning(pp_plan* plan, int row_ifft_variant, int stencil_ki
                       "Cartesian plan with register-FFT lengths ny, nz and at most 8 coils per group");
             return PP_ERR_UNSUPPORTED;
         }
-        if (stencil_kind < 0 || stencil_kind > 3 || (stencil_kind == 1 && p.c3df_ctas_hi <= 0) ||
+        if (stencil_kind < 0 || stencil_kind > 5 || ((stencil_kind == 1 || stencil_kind == 5) && p.c3df_ctas_hi <= 0) ||
             (stencil_kind == 2 && p.c3df_ctas_tma <= 0) || (stencil_kind == 3 && p.c3df_ctas_tma1 <= 0)) {
             set_error("pp_plan_set_tuning: the 3-D dataflow operator takes stencil kind 0 (two "
-                      "blocks per SM), 1 (three), 2 (map tiles staged by TMA) or 3 (staged by TMA "
-                      "into one buffer, three blocks per SM)");
+                      "blocks per SM), 1 (three), 2 (map tiles staged by TMA), 3 (staged by TMA "
+                      "into one buffer, three blocks per SM), 4 or 5 (0 or 1 with two z planes "
+                      "per y-FFT item and two line units per z item)");
             return PP_ERR_UNSUPPORTED;
         }
         p.tune_c3 = 3;

@@ -83,6 +83,7 @@ struct DfArgs {
     float2* W;              // 2 slots of CG * nz * ny * 16
     int* cnt;               // cntA[P*CG], cntB[P*CG], cntCz[P*NZ], next, err
     int nx, C, CG, ng, nb;
+    int ma, mb;             // z planes per A item, LPB-line units per B item (1 or 2)
     int64_t slot;           // elements per slot
 };
 
@@ -206,10 +207,10 @@ __device__ __forceinline__ bool df_wait(const int* cnt, int target, int* err,
     return __syncthreads_and(good) != 0;
 }
 
-// Block-wide: the item's stores are done; count it (release).
-__device__ __forceinline__ void df_signal(int* cnt) {
+// Block-wide: the item's stores are done; count its v units (release).
+__device__ __forceinline__ void df_signal(int* cnt, int v = 1) {
     __syncthreads();
-    if (threadIdx.x == 0) red_release_add(cnt, 1);
+    if (threadIdx.x == 0) red_release_add(cnt, v);
 }
 
 template <int N2Y, int N2Z, int MB, bool TMA>
@@ -256,8 +257,11 @@ c3_dataflow_kernel(DfArgs a, const __grid_constant__ CUtensorMap tmS) {
     int* next = cntCz + (int64_t)P * NZ;
     int* err = next + 1;
     const int cg_last = a.C - (a.ng - 1) * a.CG;
-    const int per_full = a.CG * (NZ + NBI) + NZ;
-    const int per_last = cg_last * (NZ + NBI) + NZ;
+    // items per coil: NA A items of ma planes, NBm B items of mb line units
+    // (the counters count planes and units, so their targets do not change)
+    const int NA = NZ / a.ma, NBm = NBI / a.mb;
+    const int per_full = a.CG * (NA + NBm) + NZ;
+    const int per_last = cg_last * (NA + NBm) + NZ;
     const int per_blk = (a.ng - 1) * per_full + per_last;
     const int total = a.nb * per_blk;
     const int64_t plane = (int64_t)NY * a.nx, vol = (int64_t)NZ * plane;
@@ -271,8 +275,8 @@ c3_dataflow_kernel(DfArgs a, const __grid_constant__ CUtensorMap tmS) {
         const int gg = min(q / per_full, a.ng - 1);
         q -= gg * per_full;
         const int cgg = (gg == a.ng - 1) ? cg_last : a.CG;
-        if (q >= cgg * NZ) return false;
-        const int cc = q / NZ, zz = q - cc * NZ;
+        if (q >= cgg * NA) return false;
+        const int cc = q / NA, zz = (q - cc * NA) * a.ma;
         *cx = bb * DTX;
         *cy = ((gg * a.CG + cc) * NZ + zz) * NY;
         return true;
@@ -329,7 +333,7 @@ c3_dataflow_kernel(DfArgs a, const __grid_constant__ CUtensorMap tmS) {
         rr -= g * per_full;
         const int k = b * a.ng + g;
         const int cg = (g == a.ng - 1) ? cg_last : a.CG;
-        const bool a_item = rr < cg * NZ, c_item = rr >= cg * (NZ + NBI);
+        const bool a_item = rr < cg * NA, c_item = rr >= cg * (NA + NBm);
         const int cur_buf = NBUF == 2 ? (iter & 1) : 0;
         // the claim and the tile copies are issued by warp 1, so that their
         // round trips overlap thread 0's dependency polls
@@ -351,109 +355,127 @@ c3_dataflow_kernel(DfArgs a, const __grid_constant__ CUtensorMap tmS) {
         const int x0 = b * DTX, col = x0 + lane;
         const bool ok = col < a.nx;
         float2* Wk = a.W + (k & 1) * a.slot;
-        if (rr < cg * NZ) {
-            // ---- A (c, z): y FFT of S_c x on plane z -> W[c][z][ky]
-            const int c = rr / NZ, z = rr - c * NZ;
-            const float2* Sc = a.S + (int64_t)(c0 + c) * vol + (int64_t)z * plane;
-            const float2* xz = a.x + (int64_t)z * plane;
-            // the image is read-only in the apply: its loads go out before the
-            // slot-reuse wait, which only orders this item's W stores
-            float2 xv[DN1];
+        if (rr < cg * NA) {
+            // ---- A (c, z .. z + ma - 1): y FFT of S_c x on each plane -> W[c][z][ky]
+            const int c = rr / NA, z0 = (rr - c * NA) * a.ma;
+            bool fail = false;
+            for (int j = 0; j < a.ma; ++j) {
+                const int z = z0 + j;
+                const float2* Sc = a.S + (int64_t)(c0 + c) * vol + (int64_t)z * plane;
+                const float2* xz = a.x + (int64_t)z * plane;
+                // the image is read-only in the apply: its loads go out before the
+                // slot-reuse wait, which only orders this item's W stores
+                float2 xv[DN1];
 #pragma unroll
-            for (int m1 = 0; m1 < DN1; ++m1)
-                xv[m1] = (r < N2Y && ok) ? __ldg(xz + (int64_t)(N2Y * m1 + r) * a.nx + col) : make_float2(0.f, 0.f);
-            if (k >= 2 && !df_wait(cntCz + (int64_t)(k - 2) * NZ + z, 1, err)) break;
-            const float2* St = nullptr;
-            if (TMA) {
-                // the tile is in Sb[cur_buf] (issued now or one item ago)
-                if (!tile_wait(cur_buf)) break;
-                St = Sb + cur_buf * NY * DTX;
-            }
-            if (r < N2Y) {
-                float2 v[DN1];
-#pragma unroll
-                for (int m1 = 0; m1 < DN1; ++m1) {
-                    const int64_t o = (int64_t)(N2Y * m1 + r) * a.nx + col;
-                    const float2 sv = TMA ? St[(N2Y * m1 + r) * DTX + lane] : (ok ? __ldg(Sc + o) : make_float2(0.f, 0.f));
-                    v[m1] = ok ? cmul(sv, xv[m1]) : make_float2(0.f, 0.f);
+                for (int m1 = 0; m1 < DN1; ++m1)
+                    xv[m1] = (r < N2Y && ok) ? __ldg(xz + (int64_t)(N2Y * m1 + r) * a.nx + col) : make_float2(0.f, 0.f);
+                if (k >= 2 && !df_wait(cntCz + (int64_t)(k - 2) * NZ + z, 1, err)) {
+                    fail = true;
+                    break;
                 }
-                fft4_phase1<DN1, N2Y, false>(v, r, twy);
-#pragma unroll
-                for (int k1 = 0; k1 < DN1; ++k1) Y[(k1 * N2Y + r) * DTX + lane] = v[k1];
-            }
-            __syncthreads();
-            // one buffer: the tile has been read, so the next item's may land
-            if (TMA && NBUF == 1 && threadIdx.x == kClaimT) issue(s_item, 0);
-            if (r < DN1) {
-                float2 u[N2Y];
-#pragma unroll
-                for (int m2 = 0; m2 < N2Y; ++m2) u[m2] = Y[(r * N2Y + m2) * DTX + lane];
-                fft4_phase2<DN1, N2Y, false>(u, twy);
-                float2* Wz = Wk + ((int64_t)(c * NZ + z) * NY) * DTX + lane;
-#pragma unroll
-                for (int k2 = 0; k2 < N2Y; ++k2) w_store(Wz + (r + DN1 * k2) * DTX, u[k2], pol_w);
-            }
-            df_signal(cntA + (int64_t)k * a.CG + c);
-        } else if (rr < cg * (NZ + NBI)) {
-            // ---- B (c, LPB ky lines): z FFT, mask, z IFFT of W[c][:, ky] in place;
-            // thread row r < LPB N2Z takes line r / N2Z in the first and last
-            // phase, rows r < 16 loop over the lines in the middle one
-            const int q = rr - cg * NZ;
-            const int c = q / NBI, ky0 = (q - c * NBI) * LPB;
-            if (!df_wait(cntA + (int64_t)k * a.CG + c, NZ, err)) break;
-            constexpr int ZS = NY * DTX;
-            constexpr int YL = DN1 * N2Z * DTX;   // one line's transpose block
-            const int l1 = r / N2Z, m2r = r - l1 * N2Z;
-            float2* Wc = Wk + (int64_t)c * NZ * NY * DTX + lane;
-            if (r < LPB * N2Z) {
-                const float2* Wl = Wc + (ky0 + l1) * DTX;
-                float2 v[DN1];
-#pragma unroll
-                for (int m1 = 0; m1 < DN1; ++m1) v[m1] = w_load(Wl + (int64_t)(N2Z * m1 + m2r) * ZS, pol_w);
-                fft4_phase1<DN1, N2Z, false>(v, m2r, twz);
-#pragma unroll
-                for (int k1 = 0; k1 < DN1; ++k1) Y[l1 * YL + (k1 * N2Z + m2r) * DTX + lane] = v[k1];
-            }
-            __syncthreads();
-            if (r < DN1) {
-#pragma unroll 1
-                for (int l = 0; l < LPB; ++l) {
-                    float2 u[N2Z];
-#pragma unroll
-                    for (int m2 = 0; m2 < N2Z; ++m2) u[m2] = Y[l * YL + (r * N2Z + m2) * DTX + lane];
-                    fft4_phase2<DN1, N2Z, false>(u, twz);
-                    const int ky = ky0 + l;
-#pragma unroll
-                    for (int k2 = 0; k2 < N2Z; ++k2)
-                        u[k2] = cscale(u[k2], __ldg(a.mask_fo + (r + DN1 * k2) * NY + ky));
-                    // inverse with the mirrored decomposition: length-N2Z DFT over
-                    // k2, twiddle W_nz^(-m2 k1), then the length-16 DFT over k1;
-                    // this thread reads and writes only its own row r of the block
-                    RegFft<N2Z, true>::run(u, twz, DN1);
-#pragma unroll
-                    for (int m2 = 1; m2 < N2Z; ++m2) {
-                        float2 w = twz[m2 * r];
-                        w.y = -w.y;
-                        u[m2] = cmul(u[m2], w);
+                const float2* St = nullptr;
+                if (TMA) {
+                    // the tile is in Sb[cur_buf] (issued now or one item ago; TMA
+                    // launches take one plane per A item)
+                    if (!tile_wait(cur_buf)) {
+                        fail = true;
+                        break;
                     }
-#pragma unroll
-                    for (int m2 = 0; m2 < N2Z; ++m2) Y[l * YL + (r * N2Z + m2) * DTX + lane] = u[m2];
+                    St = Sb + cur_buf * NY * DTX;
                 }
-            }
-            __syncthreads();
-            if (r < LPB * N2Z) {
-                float2* Wl = Wc + (ky0 + l1) * DTX;
-                float2 v[DN1];
+                if (r < N2Y) {
+                    float2 v[DN1];
 #pragma unroll
-                for (int k1 = 0; k1 < DN1; ++k1) v[k1] = Y[l1 * YL + (k1 * N2Z + m2r) * DTX + lane];
-                RegFft<DN1, true>::run(v, twz, N2Z);
+                    for (int m1 = 0; m1 < DN1; ++m1) {
+                        const int64_t o = (int64_t)(N2Y * m1 + r) * a.nx + col;
+                        const float2 sv = TMA ? St[(N2Y * m1 + r) * DTX + lane] : (ok ? __ldg(Sc + o) : make_float2(0.f, 0.f));
+                        v[m1] = ok ? cmul(sv, xv[m1]) : make_float2(0.f, 0.f);
+                    }
+                    fft4_phase1<DN1, N2Y, false>(v, r, twy);
 #pragma unroll
-                for (int m1 = 0; m1 < DN1; ++m1) w_store(Wl + (int64_t)(N2Z * m1 + m2r) * ZS, v[m1], pol_w);
+                    for (int k1 = 0; k1 < DN1; ++k1) Y[(k1 * N2Y + r) * DTX + lane] = v[k1];
+                }
+                __syncthreads();
+                // one buffer: the tile has been read, so the next item's may land
+                if (TMA && NBUF == 1 && threadIdx.x == kClaimT) issue(s_item, 0);
+                if (r < DN1) {
+                    float2 u[N2Y];
+#pragma unroll
+                    for (int m2 = 0; m2 < N2Y; ++m2) u[m2] = Y[(r * N2Y + m2) * DTX + lane];
+                    fft4_phase2<DN1, N2Y, false>(u, twy);
+                    float2* Wz = Wk + ((int64_t)(c * NZ + z) * NY) * DTX + lane;
+#pragma unroll
+                    for (int k2 = 0; k2 < N2Y; ++k2) w_store(Wz + (r + DN1 * k2) * DTX, u[k2], pol_w);
+                }
+                if (j + 1 < a.ma) __syncthreads();   // Y is rewritten by the next plane
             }
-            df_signal(cntB + (int64_t)k * a.CG + c);
+            if (fail) break;
+            df_signal(cntA + (int64_t)k * a.CG + c, a.ma);
+        } else if (rr < cg * (NA + NBm)) {
+            // ---- B (c, mb units of LPB ky lines): z FFT, mask, z IFFT of
+            // W[c][:, ky] in place; thread row r < LPB N2Z takes line r / N2Z in
+            // the first and last phase, rows r < 16 loop over the lines in the
+            // middle one
+            const int q = rr - cg * NA;
+            const int c = q / NBm, u0 = (q - c * NBm) * a.mb;
+            if (!df_wait(cntA + (int64_t)k * a.CG + c, NZ, err)) break;
+            for (int j = 0; j < a.mb; ++j) {
+                const int ky0 = (u0 + j) * LPB;
+                constexpr int ZS = NY * DTX;
+                constexpr int YL = DN1 * N2Z * DTX;   // one line's transpose block
+                const int l1 = r / N2Z, m2r = r - l1 * N2Z;
+                float2* Wc = Wk + (int64_t)c * NZ * NY * DTX + lane;
+                if (r < LPB * N2Z) {
+                    const float2* Wl = Wc + (ky0 + l1) * DTX;
+                    float2 v[DN1];
+#pragma unroll
+                    for (int m1 = 0; m1 < DN1; ++m1) v[m1] = w_load(Wl + (int64_t)(N2Z * m1 + m2r) * ZS, pol_w);
+                    fft4_phase1<DN1, N2Z, false>(v, m2r, twz);
+#pragma unroll
+                    for (int k1 = 0; k1 < DN1; ++k1) Y[l1 * YL + (k1 * N2Z + m2r) * DTX + lane] = v[k1];
+                }
+                __syncthreads();
+                if (r < DN1) {
+#pragma unroll 1
+                    for (int l = 0; l < LPB; ++l) {
+                        float2 u[N2Z];
+#pragma unroll
+                        for (int m2 = 0; m2 < N2Z; ++m2) u[m2] = Y[l * YL + (r * N2Z + m2) * DTX + lane];
+                        fft4_phase2<DN1, N2Z, false>(u, twz);
+                        const int ky = ky0 + l;
+#pragma unroll
+                        for (int k2 = 0; k2 < N2Z; ++k2)
+                            u[k2] = cscale(u[k2], __ldg(a.mask_fo + (r + DN1 * k2) * NY + ky));
+                        // inverse with the mirrored decomposition: length-N2Z DFT over
+                        // k2, twiddle W_nz^(-m2 k1), then the length-16 DFT over k1;
+                        // this thread reads and writes only its own row r of the block
+                        RegFft<N2Z, true>::run(u, twz, DN1);
+#pragma unroll
+                        for (int m2 = 1; m2 < N2Z; ++m2) {
+                            float2 w = twz[m2 * r];
+                            w.y = -w.y;
+                            u[m2] = cmul(u[m2], w);
+                        }
+#pragma unroll
+                        for (int m2 = 0; m2 < N2Z; ++m2) Y[l * YL + (r * N2Z + m2) * DTX + lane] = u[m2];
+                    }
+                }
+                __syncthreads();
+                if (r < LPB * N2Z) {
+                    float2* Wl = Wc + (ky0 + l1) * DTX;
+                    float2 v[DN1];
+#pragma unroll
+                    for (int k1 = 0; k1 < DN1; ++k1) v[k1] = Y[l1 * YL + (k1 * N2Z + m2r) * DTX + lane];
+                    RegFft<DN1, true>::run(v, twz, N2Z);
+#pragma unroll
+                    for (int m1 = 0; m1 < DN1; ++m1) w_store(Wl + (int64_t)(N2Z * m1 + m2r) * ZS, v[m1], pol_w);
+                }
+                if (j + 1 < a.mb) __syncthreads();   // Y is rewritten by the next unit
+            }
+            df_signal(cntB + (int64_t)k * a.CG + c, a.mb);
         } else {
             // ---- C (z): y IFFT, conj(S_c), sum over the group, partial sum
-            const int z = rr - cg * (NZ + NBI);
+            const int z = rr - cg * (NA + NBm);
             float2 acc[N2Y];
 #pragma unroll
             for (int k2 = 0; k2 < N2Y; ++k2) acc[k2] = make_float2(0.f, 0.f);
@@ -673,6 +695,10 @@ pp_status c3df_normal(const Plan& p, const float2* x, float2* out, float scale,
     a.W = p.c3df_w; a.cnt = p.c3df_cnt;
     a.nx = p.nx; a.C = p.C; a.CG = cg; a.ng = (p.C + cg - 1) / cg; a.nb = (p.nx + DTX - 1) / DTX;
     a.slot = (int64_t)c3df_slot_elems(p, cg);
+    // variants 4 and 5: variants 0 and 1 with two planes per A item and two
+    // line units per B item (half the items, each twice the work)
+    const int v = p.c3df_hi >= 4 ? p.c3df_hi - 4 : p.c3df_hi;
+    a.ma = a.mb = p.c3df_hi >= 4 ? 2 : 1;
     if ((size_t)2 * a.slot > p.c3df_w_elems || c3df_counter_ints(p, cg) > p.c3df_cnt_ints) {
         set_error("c3df_normal: coil group %d exceeds the plan's dataflow buffers", cg);
         return PP_ERR_INVALID_ARG;
@@ -681,7 +707,6 @@ pp_status c3df_normal(const Plan& p, const float2* x, float2* out, float scale,
     const int n2y = fft4_n2(p.ny), n2z = fft4_n2(p.nz);
     const int per_full = cg * (p.nz + p.ny) + p.nz;   // an upper bound on the items of a phase
     const int64_t total = (int64_t)a.nb * a.ng * per_full;
-    const int v = p.c3df_hi;
     const int ctas = v == 3 ? p.c3df_ctas_tma1 : v == 2 ? p.c3df_ctas_tma : (v ? p.c3df_ctas_hi : p.c3df_ctas);
     if (ctas <= 0) {
         set_error("c3df_normal: this dataflow variant cannot be resident on the device");

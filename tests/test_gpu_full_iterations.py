@@ -190,7 +190,7 @@ def test_cart3d_full_volume_one_apply_sampled_columns(pp):
         xd = dev(x)
         tuned = pp.pp_plan_tuning(plan)
         for tuning in [tuned, (3, 0, 2), (3, 0, 4), (3, 1, 4), (3, 1, 8), (3, 2, 4), (3, 2, 8), (3, 3, 4),
-                       (3, 3, 8), (1, 0, 8)]:
+                       (3, 3, 8), (3, 4, 8), (3, 5, 4), (3, 5, 8), (1, 0, 8)]:
             pp.pp_plan_set_tuning(plan, *tuning)
             out = empty(shape)
             pp.pp_normal_apply(plan, xd, out)

@@ -229,7 +229,7 @@ def test_cart3d_dataflow_operator(pp, case):
         ref = nrm(x)
         c = [float(v) for v in O.poly_coeffs_l2(2)]
         refp = O.horner_apply(c, nrm, op.astype(np.complex128))
-        for cg, hi in [(g, h) for g in sorted({1, 2, 3, 4, 8, min(C, 8)}) for h in (0, 1, 2, 3)]:
+        for cg, hi in [(g, h) for g in sorted({1, 2, 3, 4, 8, min(C, 8)}) for h in (0, 1, 2, 3, 4, 5)]:
             pp.pp_plan_set_tuning(plan, 3, hi, cg)
             assert pp.pp_plan_tuning(plan) == (3, hi, cg)
             out = empty(shape)
