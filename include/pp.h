@@ -322,6 +322,11 @@ typedef struct {
     int wavelet;         /* in: W of the prox: 0 = orthonormal Haar (levels
                             1..2), 1 = Daubechies-4 (2-D, levels 1..4), see
                             pp_prox_l1_db4; else PP_ERR_INVALID_ARG         */
+    int safe_scale;      /* in: 1 = divide c by max over [0, 1] of z p(z)
+                            (pp_poly_max_zp) before the solve, so that the
+                            preconditioned step keeps FISTA's step rule; 0 =
+                            apply c as given, as the paper does.  Used by
+                            pp_fista_solve and pp_batch_fista_solve         */
 } pp_solve_info;
 
 /* Algorithm "pfista" on the normalised problem (Sec. 5): A_hat = A/sqrt(L),

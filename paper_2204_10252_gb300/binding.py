@@ -44,7 +44,7 @@ class pp_solve_info(ctypes.Structure):
     _fields_ = [("rescale", ctypes.c_int), ("levels", ctypes.c_int), ("no_momentum", ctypes.c_int),
                 ("history", ctypes.c_void_p), ("ref", ctypes.c_void_p),
                 ("bnorm", ctypes.c_double), ("L", ctypes.c_double), ("launches", ctypes.c_int64),
-                ("wavelet", ctypes.c_int)]
+                ("wavelet", ctypes.c_int), ("safe_scale", ctypes.c_int)]
 
 
 _lib = None
@@ -409,12 +409,15 @@ class SolveResult:
 
 def pp_fista_solve(plan: Plan, b, lam: float, iters: int, c, d: int, x_out, stream=None,
                    history: bool = False, rescale: bool = False, levels: int = 2,
-                   ref=None, momentum: bool = True, wavelet: str = "haar") -> SolveResult:
+                   ref=None, momentum: bool = True, wavelet: str = "haar",
+                   safe_scale: bool = False) -> SolveResult:
     """c None with d = 0: plain FISTA.  history: per-iteration FP64
     ||y_{k+1}-y_k||^2, ||y_{k+1}||^2, ||y_{k+1}-ref||^2 (ref optional).
-    wavelet: "haar" or "db4" (Daubechies-4, 2-D) for the prox's W."""
+    wavelet: "haar" or "db4" (Daubechies-4, 2-D) for the prox's W.
+    safe_scale: divide c by max over [0, 1] of z p(z) (FISTA's step rule)."""
     info = pp_solve_info()
     info.wavelet = WAVELETS[wavelet]
+    info.safe_scale = 1 if safe_scale else 0
     info.rescale = 1 if rescale else 0
     info.levels = int(levels)
     info.no_momentum = 0 if momentum else 1
@@ -585,9 +588,10 @@ def pp_batch_normal_apply(batch: Batch, x, y, stream=None):
 
 def pp_batch_fista_solve(batch: Batch, b, lam: float, iters: int, c, d: int, x_out, stream=None,
                          history: bool = False, rescale: bool = False, ref=None,
-                         momentum: bool = True) -> SolveResult:
+                         momentum: bool = True, safe_scale: bool = False) -> SolveResult:
     info = pp_solve_info()
     info.rescale = 1 if rescale else 0
+    info.safe_scale = 1 if safe_scale else 0
     info.levels = 2
     info.no_momentum = 0 if momentum else 1
     hist = None

@@ -1884,6 +1884,21 @@ static pp_status check_history(const char* who, double bn2, const double* h, int
     return PP_OK;
 }
 
+// info->safe_scale: c divided by max_{z in [0, 1]} z p(z), in buf
+static pp_status safe_coeffs(const pp_solve_info* info, const double*& c, int d, std::vector<double>& buf) {
+    if (!info || !info->safe_scale || !c) return PP_OK;
+    double m = 0.0;
+    PP_TRY(pp_poly_max_zp(c, d, &m));
+    if (!(m > 0.0)) {
+        set_error("safe_scale: max of z p(z) on [0, 1] is not positive");
+        return PP_ERR_INVALID_ARG;
+    }
+    buf.assign(c, c + d + 1);
+    for (double& v : buf) v /= m;
+    c = buf.data();
+    return PP_OK;
+}
+
 pp_status pp_fista_solve(pp_plan* plan, const pp_c64* b, float lambda, int iters, const double* c,
                          int d, pp_c64* x_out, pp_solve_info* info, pp_stream stream) {
     if (!plan || !b || !x_out || iters < 0 || iters > 1000000 || !(lambda >= 0.f) ||
@@ -1893,6 +1908,8 @@ pp_status pp_fista_solve(pp_plan* plan, const pp_c64* b, float lambda, int iters
     }
     Plan& p = plan->impl;
     cudaStream_t st = (cudaStream_t)stream;
+    std::vector<double> c_safe;
+    PP_TRY(safe_coeffs(info, c, d, c_safe));
     const int levels = (info && info->levels) ? info->levels : 2;
     const int wavelet = info ? info->wavelet : 0;
     if (wavelet != 0 && wavelet != 1) {
@@ -2448,6 +2465,8 @@ pp_status pp_batch_fista_solve(pp_batch* batch, const pp_c64* bk, float lambda, 
         set_error("pp_batch_fista_solve: the batched prox is the 2-level Haar");
         return PP_ERR_UNSUPPORTED;
     }
+    std::vector<double> c_safe;
+    PP_TRY(safe_coeffs(info, c, d, c_safe));
     Batch& b = batch->impl;
     cudaStream_t st = (cudaStream_t)stream;
     const bool hist = info && info->history;

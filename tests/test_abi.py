@@ -208,3 +208,35 @@ def test_weighted_l2_rejects_a_zero_weight(L):
     assert e.value.status == 1
     with pytest.raises(ValueError):
         pp.pp_poly_coeffs_wl2(3, np.ones(5))
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    # the ctypes structures of the binding against the C compiler's layout of
+    # the same structs in include/pp.h (sizes and field offsets)
+    import shutil
+    import subprocess
+    from paper_2204_10252_gb300 import binding as B
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    checks = {"pp_dims": ["ndim", "n"], "pp_sampling": ["kind", "mask", "traj", "K", "kb_width", "oversamp"],
+              "pp_solve_info": ["rescale", "levels", "no_momentum", "history", "ref", "bnorm", "L",
+                                "launches", "wavelet", "safe_scale"]}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "pp.h"', "int main(void) {"]
+    for st, fields in checks.items():
+        lines.append('    printf("%%zu\\n", sizeof(%s));' % st)
+        for f in fields:
+            lines.append('    printf("%%zu\\n", offsetof(%s, %s));' % (st, f))
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(root, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    want = []
+    for st, fields in checks.items():
+        cls = getattr(B, st)
+        want.append(ctypes.sizeof(cls))
+        want += [getattr(cls, f).offset for f in fields]
+    assert got == want

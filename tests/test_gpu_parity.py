@@ -377,6 +377,32 @@ def test_solve_parity(pp, prob, d):
     assert r.launches > iters
 
 
+def test_safe_scale_divides_the_polynomial_by_its_step_bound(pp, prob):
+    # pp_solve_info.safe_scale: the solve with c divided by max z p(z) on
+    # [0, 1] (the reading that keeps FISTA's step rule); the same as passing
+    # the divided coefficients, and equal to the oracle's solve with them
+    x0 = synth.phantom(prob.shape, 5)
+    b = (prob.fwd(x0) + prob.ksp(6) * 1e-3).astype(np.complex64)
+    L = float(O.power_iteration(prob.normal, prob.shape, 9, iters=30))
+    pp.pp_plan_set_scale(prob.plan, L)
+    lam, iters, d = 1e-3, 12, 3
+    c = [float(v) for v in O.poly_coeffs_l2(d)]
+    m = pp.pp_poly_max_zp(c, d)
+    assert abs(m - O.poly_max_zp(np.array(c))) <= 1e-9
+    cs = [v / m for v in c]
+    out_flag, out_div = empty(prob.shape), empty(prob.shape)
+    pp.pp_fista_solve(prob.plan, dev(b), lam, iters, c, d, out_flag, safe_scale=True)
+    pp.pp_fista_solve(prob.plan, dev(b), lam, iters, cs, d, out_div)
+    if prob.kind == "cart":
+        # the same coefficients, the same kernels: bit for bit (the
+        # non-Cartesian adjoint accumulates each tile with shared-memory
+        # atomics, whose order varies from call to call)
+        assert np.array_equal(host(out_flag), host(out_div))
+    ref = O.pfista(prob.normal, prob.adj, b.astype(np.complex128), lam, cs, iters, L)
+    assert rel(host(out_flag), ref) <= TOL_SOLVE
+    assert rel(host(out_div), ref) <= TOL_SOLVE
+
+
 def test_mu_estimate_matches_oracle(pp, prob):
     # power iteration on I - N_hat (Sec. 3.4 remark) from the same seed and
     # L: the Rayleigh quotients 1 - mu agree to FP32-apply accuracy
