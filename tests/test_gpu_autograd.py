@@ -111,7 +111,10 @@ def test_backward_after_set_scales_uses_the_new_scales(pp):
         g_new = torch.empty_like(b)
         gl_n, gc_n = pp.pp_batch_unrolled_backward(batch, b, lam, iters, c, 3, ce, yb, g_new)
         assert torch.equal(g_stale, g_new)
-        assert gl_s == gl_n and np.array_equal(gc_s, gc_n)
+        # d loss / d lambda sums per-block FP64 partials with atomics (order
+        # not fixed): equal to the last bits, not necessarily bit for bit
+        assert abs(gl_s - gl_n) <= 1e-12 * max(abs(gl_n), 1e-300)
+        assert np.array_equal(gc_s, gc_n)
         # and both are the oracle's gradient under the new scales
         outs, gbr, glr, gcr = oracle_grads(batch, sens, masks, bs, ybar, lam, c, iters, L1)
         ko = batch.kspace_off
