@@ -5,7 +5,7 @@ operator stop at 32, so these take the coil-major kernels) up to the
 64-coil maximum, one coil, FFT lengths with factors 3 and 5, the smallest
 gridding grid (40 points), every oversampling the gridding accepts from
 1.125 to 2, a one-sample trajectory and samples on the -n/2 edge of the
-k-space box."""
+k-space box; and batches of uneven slices at the same corners."""
 import numpy as np
 import pytest
 
@@ -132,3 +132,55 @@ def test_normal(pp, case):
     out = empty(case["shape"])
     pp.pp_normal_apply(case["plan"], dev(x), out)
     assert rel(host(out), case["normal"](x) / L) <= TOL_APPLY
+
+
+# Batches at the same corners: a 4 x 4 slice, 512-point axes (no register FFT
+# at that length), 33 to 64 coils per slice, a one-slice batch; each under
+# every column tile the batch accepts
+BATCHES = [
+    ("generic_lengths", [((4, 4), 1, 2), ((12, 512), 33, 3), ((512, 20), 64, 4), ((60, 100), 17, 3)]),
+    ("register_lengths", [((384, 384), 64, 6), ((128, 36), 33, 3), ((320, 256), 40, 5)]),
+    ("one_slice", [((192, 192), 1, 4)]),
+]
+
+
+@pytest.mark.parametrize("which", range(len(BATCHES)), ids=[b[0] for b in BATCHES])
+def test_batch_apply_at_the_limits(pp, which):
+    import torch
+    slices = BATCHES[which][1]
+    shapes = [s for s, _, _ in slices]
+    coils = [c for _, c, _ in slices]
+    sens = [synth.coil_maps(s, c, 950 + i) for i, (s, c, _) in enumerate(slices)]
+    masks = [synth.line_mask(s, R, 4, 960 + i) for i, (s, _, R) in enumerate(slices)]
+    b = pp.pp_batch_create(shapes, coils, [dev(v) for v in sens], masks, seed=7, power_iters=0)
+    try:
+        L = np.linspace(0.7, 1.3, len(slices))
+        pp.pp_batch_set_scales(b, L)
+        xs = [synth.crandn(s, 970 + i) for i, s in enumerate(shapes)]
+        ks = [synth.crandn((c,) + s, 980 + i) * m[None] for i, (s, c, m) in
+              enumerate(zip(shapes, coils, masks))]
+        ref_n = [O.cart_normal(xs[i], sens[i], masks[i]) / L[i] for i in range(len(slices))]
+        ref_a = [O.cart_adjoint(ks[i], sens[i], masks[i]) for i in range(len(slices))]
+        x = dev(np.concatenate([v.ravel() for v in xs]))
+        k = dev(np.concatenate([v.ravel() for v in ks]))
+        off = b.image_off
+        tried = 0
+        for tile in (4, 8, 16, -8, -16, -32):
+            try:
+                pp.pp_batch_set_tile(b, tile)
+            except pp.PPError:
+                continue
+            tried += 1
+            y = torch.empty_like(x)
+            pp.pp_batch_normal_apply(b, x, y)
+            got = host(y)
+            for i, s in enumerate(shapes):
+                assert rel(got[off[i]:off[i + 1]].reshape(s), ref_n[i]) <= TOL_APPLY, (tile, i)
+            xa = torch.empty_like(x)
+            pp.pp_batch_adjoint_apply(b, k, xa)
+            got = host(xa)
+            for i, s in enumerate(shapes):
+                assert rel(got[off[i]:off[i + 1]].reshape(s), ref_a[i]) <= TOL_APPLY, (tile, i)
+        assert tried >= 1
+    finally:
+        b.destroy()
