@@ -112,19 +112,41 @@ static pp_status upload(Plan& p, T** dst, const std::vector<T>& src) {
 // Kaiser-Bessel pieces (width W, shape beta):
 //   kernel  phi(u) = I0(beta sqrt(1 - (2u/W)^2)), |u| <= W/2
 //   its Fourier transform psi(nu) = W sinh(sqrt(a))/sqrt(a), a = beta^2 - (pi W nu)^2
-static double bessel_i0(double x) {
-    const double q = 0.25 * x * x;
-    double term = 1.0, sum = 1.0;
-    for (int k = 1; k < 200; ++k) {
-        term *= q / ((double)k * k);
-        sum += term;
-        if (term < 1e-17 * sum) break;
+// Kaiser-Bessel kernel phi(u) = I0(beta sqrt(1 - (2u/W)^2)) for |u| <= W/2,
+// 0 outside, by the power series I0(x) = sum_k q^k / (k!)^2, q = x^2 / 4.
+// Every argument of a plan is at most beta, so one term count serves all:
+// the first k at which q_max^k / (k!)^2 < 1e-17 (the sum is >= 1, and past
+// the largest term each term shrinks by q / (k + 1)^2 < 1).
+static int kb_series_terms(double beta) {
+    const double q = 0.25 * beta * beta;
+    double t = 1.0;
+    int k = 1;
+    for (; k < 200; ++k) {
+        t *= q / ((double)k * k);
+        if (t < 1e-17) break;
     }
-    return sum;
+    return k;
 }
-static double kb_phi(double u, double W, double beta) {
-    const double t = 1.0 - (2.0 * u / W) * (2.0 * u / W);
-    return t < 0.0 ? 0.0 : bessel_i0(beta * sqrt(t));
+// phi at the 8 offsets u[0..7] (a sample's 4 x-taps and 4 y-taps), the 8
+// series summed side by side; inv_k2[k - 1] = 1 / k^2
+static void kb_phi8(const double* u, double W, double beta, int nterms, const double* inv_k2,
+                    float* out) {
+    double q[8], term[8], sum[8];
+    for (int i = 0; i < 8; ++i) {
+        const double r = 2.0 * u[i] / W, t = 1.0 - r * r;
+        q[i] = t < 0.0 ? 0.0 : 0.25 * beta * beta * t;
+        term[i] = 1.0;
+        sum[i] = 1.0;
+    }
+    for (int k = 0; k < nterms; ++k)
+        for (int i = 0; i < 8; ++i) {
+            term[i] *= q[i] * inv_k2[k];
+            sum[i] += term[i];
+        }
+    for (int i = 0; i < 8; ++i) {
+        const double r = 2.0 * u[i] / W;
+        out[i] = 1.0 - r * r < 0.0 ? 0.f : (float)sum[i];
+    }
 }
 static double kb_psi(double nu, double W, double beta) {
     const double a = beta * beta - (M_PI * W * nu) * (M_PI * W * nu);
@@ -372,6 +394,9 @@ static pp_status build_noncartesian(Plan& p, const pp_sampling* s) {
     // of samples, so contiguous sample ranges run on the host's cores (each
     // sample's taps depend on that sample alone: the result is the same for
     // any thread count)
+    const int nterms = kb_series_terms(beta);
+    double inv_k2[200];
+    for (int k = 1; k <= nterms; ++k) inv_k2[k - 1] = 1.0 / ((double)k * k);
     const int K = p.K;
     std::vector<SampleTaps> st(K);
     std::atomic<int> bad(K);   // the first sample outside the grid, if any
@@ -386,13 +411,15 @@ static pp_status build_noncartesian(Plan& p, const pp_sampling* s) {
             }
             const double sx = kx * Gx / nx, sy = ky * Gy / ny;
             const int ix0 = (int)floor(sx - W / 2.0) + 1, iy0 = (int)floor(sy - W / 2.0) + 1;
-            float w[2][4];
+            double u[8];
             for (int a = 0; a < 4; ++a) {
-                w[0][a] = (float)kb_phi(sx - (ix0 + a), W, beta);
-                w[1][a] = (float)kb_phi(sy - (iy0 + a), W, beta);
+                u[a] = sx - (ix0 + a);
+                u[4 + a] = sy - (iy0 + a);
             }
-            st[k].wx = make_float4(w[0][0], w[0][1], w[0][2], w[0][3]);
-            st[k].wy = make_float4(w[1][0], w[1][1], w[1][2], w[1][3]);
+            float w[8];
+            kb_phi8(u, W, beta, nterms, inv_k2, w);
+            st[k].wx = make_float4(w[0], w[1], w[2], w[3]);
+            st[k].wy = make_float4(w[4], w[5], w[6], w[7]);
             st[k].ix0 = ix0;
             st[k].iy0 = iy0;
         }
@@ -574,18 +601,23 @@ static pp_status tune_noncartesian(Plan& p, cudaStream_t st) {
                                                   {7, 1}, {7, 4}, {8, 1}, {8, 4}, {9, 1}, {9, 4}};
         PP_TRY_CUDA(cudaMemsetAsync(p.v, 0, sizeof(float2) * (size_t)p.nimg, st));
         std::vector<float> wbest(whole.size(), 1e30f);
-        for (int round = 0; round < 2; ++round)
+        for (int round = 0; round < 2; ++round) {
+            // the second round re-times only the candidates within 10 % of
+            // the first round's best
+            const float cut = round == 0 ? 1.5e30f
+                                         : 1.1f * *std::min_element(wbest.begin(), wbest.end());
             for (size_t i = 0; i < whole.size(); ++i) {
                 p.tune_stencil_kind = whole[i].first;
                 p.tune_rows_adj_cl = whole[i].second;
                 if (round == 0 && i > 0 && !launches_ok([&]() {
                         return normal_into(p, p.v, p.t, 1.f, nullptr, 0.f, st); }))
                     wbest[i] = 2e30f;   // a cluster shape this device cannot place
-                if (wbest[i] > 1.5e30f) continue;
+                if (wbest[i] > cut) continue;
                 float ms = 0.f;
                 PP_TRY(timeit([&]() { return normal_into(p, p.v, p.t, 1.f, nullptr, 0.f, st); }, &ms, 1, 5));
                 wbest[i] = std::min(wbest[i], ms);
             }
+        }
         const size_t wi = std::min_element(wbest.begin(), wbest.end()) - wbest.begin();
         p.tune_stencil_kind = whole[wi].first;
         p.tune_rows_adj_cl = whole[wi].second;
