@@ -26,6 +26,16 @@
  *    thread-local message.  No call throws, aborts or traps.
  *  - Input and output arrays of one call must not overlap unless the call
  *    says otherwise.
+ *  - Calls on different plans or batches may run at the same time from
+ *    different host threads (the library's shared state, the launch-shape
+ *    cache and the one-time kernel set-up, is locked); calls on one plan or
+ *    batch share its workspaces and must be serialised by the caller.
+ *    The first solve of a plan or batch with given parameters captures its
+ *    iterations into a CUDA graph, and CUDA forbids, in every thread, a
+ *    synchronisation of the whole device while a capture is open
+ *    (cudaDeviceSynchronize, and the implicit one of cudaFree, which
+ *    pp_plan_destroy and pp_batch_destroy call): such a call made during
+ *    that capture fails, and so does the capturing solve (PP_ERR_CUDA).
  */
 #ifndef PP_H
 #define PP_H

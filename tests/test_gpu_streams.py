@@ -201,3 +201,79 @@ def test_batch_and_prox_on_a_side_stream(pp):
     out3 = torch.zeros((3, 16, 16, 16), dtype=torch.complex64, device="cuda")
     on(s, lambda: pp.pp_prox_llr((16, 16, 16), 3, 8, 2.0, sin, out3))
     assert rel(host(out3), O.prox_llr(stack, 2.0, 8)) <= TOL_APPLY
+
+
+def test_plans_used_from_concurrent_host_threads(pp):
+    # Three plans, each with its own stream: made and first solved one after
+    # the other (the first solve captures the plan's CUDA graph, and CUDA
+    # forbids a device-wide synchronisation in any thread while a capture
+    # is open), then used by three host threads at once -- applies, solves
+    # (graph replays) and second plans of the same geometry made while the
+    # other threads compute.  Each thread synchronises only its own stream.
+    # The results equal the serial run's bits (no atomics on this path).
+    import threading
+    import torch
+    specs = [((64, 48), 3, 1500), ((48, 64), 4, 1501), ((64, 64), 2, 1502)]
+    c = [float(v) for v in O.poly_coeffs_l2(3)]
+    st = {}
+    for shape, C, seed in specs:
+        s = torch.cuda.Stream()
+        sens = synth.coil_maps(shape, C, seed)
+        mask = synth.line_mask(shape, 3, 6, seed)
+        b = (O.cart_forward(synth.phantom(shape, seed), sens, mask) +
+             1e-3 * synth.crandn((C,) + shape, seed + 1) * mask[None]).astype(np.complex64)
+        with torch.cuda.stream(s):
+            sd = torch.from_numpy(sens.astype(np.complex64)).cuda()
+            plan = pp.pp_plan_create(shape, C, sd, mask=mask, seed=seed, power_iters=30)
+            x = torch.from_numpy(synth.crandn(shape, seed + 2).astype(np.complex64)).cuda()
+            bd = torch.from_numpy(b).cuda()
+        st[seed] = dict(s=s, sd=sd, mask=mask, plan=plan, x=x, b=bd, shape=shape, C=C)
+
+    def run(seed, out, errors, make_second):
+        try:
+            d = st[seed]
+            s = d["s"]
+            with torch.cuda.stream(s):
+                y = torch.zeros_like(d["x"])
+                for _ in range(20):
+                    pp.pp_normal_apply(d["plan"], d["x"], y)
+                xo = torch.zeros_like(d["x"])
+                pp.pp_fista_solve(d["plan"], d["b"], 1e-3, 15, c, 3, xo)
+                L2 = None
+                if make_second:
+                    second = pp.pp_plan_create(d["shape"], d["C"], d["sd"], mask=d["mask"], seed=seed,
+                                               power_iters=30)
+                    L2 = pp.pp_plan_scale(second)
+                    d.setdefault("extra", []).append(second)
+                s.synchronize()
+                out[seed] = (y.cpu().numpy(), xo.cpu().numpy(), L2)
+                s.synchronize()
+        except Exception as e:   # reported by the main thread
+            errors.append(repr(e))
+
+    try:
+        serial, errors = {}, []
+        for _, _, seed in specs:
+            run(seed, serial, errors, False)
+        assert not errors, errors
+        for rep in range(2):
+            conc = {}
+            threads = [threading.Thread(target=run, args=(seed, conc, errors, rep == 1))
+                       for _, _, seed in specs]
+            for t in threads:
+                t.start()
+            for t in threads:
+                t.join()
+            assert not errors, errors
+            for _, _, seed in specs:
+                y, xo, _ = serial[seed]
+                y2, xo2, L2 = conc[seed]
+                assert np.array_equal(y2, y) and np.array_equal(xo2, xo), (rep, seed)
+                if L2 is not None:
+                    assert L2 == pp.pp_plan_scale(st[seed]["plan"]), (rep, seed)
+    finally:
+        torch.cuda.synchronize()
+        for d in st.values():
+            for q in d.get("extra", []):
+                q.destroy()
+            d["plan"].destroy()
