@@ -240,3 +240,20 @@ def test_binding_structs_match_the_header_layout(tmp_path):
         want.append(ctypes.sizeof(cls))
         want += [getattr(cls, f).offset for f in fields]
     assert got == want
+
+
+def test_readme_example_uses_the_binding_as_declared():
+    # every pp.* call in the README's Python example names a function of the
+    # package, and its keyword arguments are parameters of that function
+    import inspect
+    import paper_2204_10252_gb300 as pkg
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    text = open(os.path.join(root, "README.md")).read()
+    code = re.search(r"```python\n(.*?)```", text, re.S).group(1)
+    calls = re.findall(r"pp\.(\w+)\(([^)]*)\)", code)
+    assert calls
+    for name, args in calls:
+        fn = getattr(pkg, name)
+        params = inspect.signature(fn).parameters
+        for kw in re.findall(r"(\w+)=", args):
+            assert kw in params, (name, kw)
